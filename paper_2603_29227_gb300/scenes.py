@@ -1,0 +1,262 @@
+"""Seeded synthetic inputs for the Kernel-SDF back-end query.
+
+This module only makes inputs: analytic scenes, noisy surface samples with per-sample variances and
+outward normals, query points and their true signs.  It holds none of the method's arithmetic, and it
+is the only module that both the CUDA path's tests and the CPU oracle's tests draw inputs from.
+
+The paper's datasets (Replica, Cow&Lady, Newer College) are not available; these scenes stand in for
+them with the paper's setting: surface samples a few centimetres apart on planar and curved surfaces,
+noise of about a centimetre, lambda of 300-500 and cells of tens to hundreds of samples.
+
+Recipes (numpy PCG64, one seed per workload):
+  plane2d   "2D plain FP64": a 10 x 10 m box border (free inside) and 20 circles (centres U[0,10]^2,
+            radius U[0.2,1]); 2,000 samples uniform in arc length over all visible boundaries, isotropic
+            N(0, 0.01^2) noise; 1 m cells, n_max 64, lambda 500; queries at the centres of a 128 x 128
+            grid over the box.
+  room3d    "3D": a 20 x 20 x 5 m room (walls, floor, ceiling) with 50 primitives (spheres and axis-
+            aligned boxes, 50/50, sizes U[0.2,2] m) inside it; 200,000 samples uniform in area,
+            N(0, 0.01^2) noise; 0.5 m cells, n_max 256, lambda 300; 1,000,000 queries uniform in the room.
+  scale3d   "mixed-precision scale": a 50 x 50 x 10 m scene with 1,000 primitives and 2,000,000 samples;
+            0.5 m cells, n_max 512; queries on a 256^3 grid over the bounding box.
+  traj3d    "differentiation": the room3d scene; 4,096 cubic Bezier trajectories x 64 waypoints x 8
+            collision-sphere centres (corners of a 0.3 m cube around each waypoint) = 2,097,152 queries.
+Per-sample variance fed to the GP: sigma_i^2 = (sigma_noise * U[0.5, 2])^2, standing in for the
+front-end's per-point uncertainty.  Normals point from the obstacle into free space.  Samples that fall
+inside another obstacle (or outside the room) are rejected and redrawn.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = ["Scene", "make_plane2d", "make_room3d", "make_scale3d", "Workload", "workload", "WORKLOADS"]
+
+
+@dataclass
+class Scene:
+    """Analytic scene: a free box (room) minus solid spheres/circles and axis-aligned boxes."""
+
+    dim: int
+    room_lo: np.ndarray
+    room_hi: np.ndarray
+    centres: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    radii: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    box_lo: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    box_hi: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+
+    # ---- ground truth (used by tests for sanity checks and by the generators for rejection) ----
+    def occupied(self, x: np.ndarray) -> np.ndarray:
+        x = np.asarray(x, dtype=np.float64)
+        occ = np.any((x < self.room_lo) | (x > self.room_hi), axis=1)
+        for c, r in zip(self.centres, self.radii):
+            occ |= np.sum((x - c) ** 2, axis=1) < r * r
+        for lo, hi in zip(self.box_lo, self.box_hi):
+            occ |= np.all((x > lo) & (x < hi), axis=1)
+        return occ
+
+    def sign(self, x: np.ndarray) -> np.ndarray:
+        """+1 in free space, -1 inside an obstacle (int8)."""
+        return np.where(self.occupied(x), -1, 1).astype(np.int8)
+
+    def dist_free(self, x: np.ndarray) -> np.ndarray:
+        """Exact distance to the occupied set for points in free space (Sec. III definition)."""
+        x = np.asarray(x, dtype=np.float64)
+        d = np.min(np.minimum(x - self.room_lo, self.room_hi - x), axis=1)
+        for c, r in zip(self.centres, self.radii):
+            d = np.minimum(d, np.sqrt(np.sum((x - c) ** 2, axis=1)) - r)
+        for lo, hi in zip(self.box_lo, self.box_hi):
+            e = np.maximum(np.maximum(lo - x, 0.0), x - hi)
+            d = np.minimum(d, np.sqrt(np.sum(e * e, axis=1)))
+        return d
+
+    # ---- surface sampling ----
+    def _pieces(self):
+        """(kind, index, area-or-length) for every boundary piece."""
+        out = []
+        L = self.room_hi - self.room_lo
+        for ax in range(self.dim):
+            other = np.prod(np.delete(L, ax)) if self.dim == 3 else np.delete(L, ax)[0]
+            out.append(("room_lo", ax, other))
+            out.append(("room_hi", ax, other))
+        for i, r in enumerate(self.radii):
+            out.append(("ball", i, 4 * np.pi * r * r if self.dim == 3 else 2 * np.pi * r))
+        for i, (lo, hi) in enumerate(zip(self.box_lo, self.box_hi)):
+            e = hi - lo
+            for ax in range(self.dim):
+                other = np.prod(np.delete(e, ax)) if self.dim == 3 else np.delete(e, ax)[0]
+                out.append(("box_lo", (i, ax), other))
+                out.append(("box_hi", (i, ax), other))
+        return out
+
+    def _draw(self, rng: np.random.Generator, n: int):
+        pieces = self._pieces()
+        w = np.array([p[2] for p in pieces], dtype=np.float64)
+        pick = rng.choice(len(pieces), size=n, p=w / w.sum())
+        x = np.empty((n, self.dim))
+        nrm = np.zeros((n, self.dim))
+        for k, (kind, idx, _) in enumerate(pieces):
+            sel = np.nonzero(pick == k)[0]
+            m = sel.size
+            if m == 0:
+                continue
+            if kind in ("room_lo", "room_hi", "box_lo", "box_hi"):
+                if kind.startswith("room"):
+                    lo, hi, ax = self.room_lo, self.room_hi, idx
+                    inward = 1.0  # free space is inside the room
+                else:
+                    i, ax = idx
+                    lo, hi = self.box_lo[i], self.box_hi[i]
+                    inward = -1.0  # free space is outside the box
+                p = lo + rng.random((m, self.dim)) * (hi - lo)
+                if kind.endswith("lo"):
+                    p[:, ax] = lo[ax]
+                    nrm[sel, ax] = 1.0 * inward
+                else:
+                    p[:, ax] = hi[ax]
+                    nrm[sel, ax] = -1.0 * inward
+                x[sel] = p
+            else:  # ball / circle
+                v = rng.standard_normal((m, self.dim))
+                v /= np.linalg.norm(v, axis=1, keepdims=True)
+                x[sel] = self.centres[idx] + self.radii[idx] * v
+                nrm[sel] = v
+        return x, nrm
+
+    def sample_surface(self, rng: np.random.Generator, n: int, noise: float):
+        """n accepted samples: (x float64, var float32, normals float32)."""
+        xs, ns = [], []
+        have = 0
+        while have < n:
+            batch = max(1024, int(1.3 * (n - have)))
+            x, nrm = self._draw(rng, batch)
+            # reject points strictly inside another obstacle or outside the room (tolerance 1e-9 m keeps
+            # the point's own surface)
+            keep = ~self._inside_other(x, 1e-9)
+            xs.append(x[keep])
+            ns.append(nrm[keep])
+            have += int(keep.sum())
+        x = np.concatenate(xs)[:n]
+        nrm = np.concatenate(ns)[:n]
+        x = x + noise * rng.standard_normal(x.shape)
+        var = (noise * rng.uniform(0.5, 2.0, size=n)) ** 2
+        return x, var.astype(np.float32), nrm.astype(np.float32)
+
+    def _inside_other(self, x: np.ndarray, tol: float) -> np.ndarray:
+        bad = np.any((x < self.room_lo - tol) | (x > self.room_hi + tol), axis=1)
+        for c, r in zip(self.centres, self.radii):
+            bad |= np.sum((x - c) ** 2, axis=1) < (r - tol) ** 2
+        for lo, hi in zip(self.box_lo, self.box_hi):
+            bad |= np.all((x > lo + tol) & (x < hi - tol), axis=1)
+        return bad
+
+
+def make_plane2d(rng: np.random.Generator, n_circles: int = 20, size: float = 10.0) -> Scene:
+    c = rng.uniform(0.0, size, size=(n_circles, 2))
+    r = rng.uniform(0.2, 1.0, size=n_circles)
+    return Scene(dim=2, room_lo=np.zeros(2), room_hi=np.full(2, size), centres=c, radii=r,
+                 box_lo=np.zeros((0, 2)), box_hi=np.zeros((0, 2)))
+
+
+def _primitives3d(rng, n, room_hi):
+    is_ball = rng.random(n) < 0.5
+    cen, rad, blo, bhi = [], [], [], []
+    for b in is_ball:
+        if b:
+            r = 0.5 * rng.uniform(0.2, 2.0)
+            c = rng.uniform(r, room_hi - r)
+            cen.append(c)
+            rad.append(r)
+        else:
+            e = rng.uniform(0.2, 2.0, size=3)
+            lo = rng.uniform(0.0, room_hi - e)
+            blo.append(lo)
+            bhi.append(lo + e)
+    z3 = np.zeros((0, 3))
+    return (np.array(cen) if cen else z3, np.array(rad), np.array(blo) if blo else z3, np.array(bhi) if bhi else z3)
+
+
+def make_room3d(rng: np.random.Generator, room=(20.0, 20.0, 5.0), n_prims: int = 50) -> Scene:
+    hi = np.array(room, dtype=np.float64)
+    c, r, lo, bh = _primitives3d(rng, n_prims, hi)
+    return Scene(dim=3, room_lo=np.zeros(3), room_hi=hi, centres=c, radii=r, box_lo=lo, box_hi=bh)
+
+
+def make_scale3d(rng: np.random.Generator) -> Scene:
+    return make_room3d(rng, room=(50.0, 50.0, 10.0), n_prims=1000)
+
+
+@dataclass
+class Workload:
+    name: str
+    params: dict
+    scene: Scene
+    x: np.ndarray        # S x dim float64 sample positions
+    var: np.ndarray      # S float32 per-sample variance sigma_i^2
+    normals: np.ndarray  # S x dim float32 outward normals
+    xq: np.ndarray       # Q x dim float32 query points
+    sign: np.ndarray     # Q int8 true sign (+1 free, -1 occupied)
+
+
+def _grid_queries(lo, hi, n, dim):
+    axes = [lo[j] + (np.arange(n) + 0.5) * (hi[j] - lo[j]) / n for j in range(dim)]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    # x fastest in memory order (row = z, y, x in 3D)
+    pts = np.stack([m.ravel(order="F") for m in mesh], axis=1)
+    return pts
+
+
+def _bezier_queries(rng, scene: Scene, n_traj: int, n_way: int):
+    lo, hi = scene.room_lo + 0.3, scene.room_hi - 0.3
+    P = lo + rng.random((n_traj, 4, 3)) * (hi - lo)
+    t = (np.arange(n_way) + 0.5) / n_way
+    B = np.stack([(1 - t) ** 3, 3 * (1 - t) ** 2 * t, 3 * (1 - t) * t ** 2, t ** 3], axis=1)  # n_way x 4
+    way = np.einsum("wk,tkj->twj", B, P).reshape(-1, 3)
+    off = np.array([[sx, sy, sz] for sz in (-1, 1) for sy in (-1, 1) for sx in (-1, 1)], dtype=np.float64) * 0.15
+    return (way[:, None, :] + off[None, :, :]).reshape(-1, 3)
+
+
+def workload(name: str, seed: int | None = None, n_samples: int | None = None, n_queries: int | None = None,
+             grid: int | None = None) -> Workload:
+    """Build a named workload.  Optional overrides shrink it for tests (same recipe, smaller sizes)."""
+    if name == "plane2d":
+        rng = np.random.default_rng(1 if seed is None else seed)
+        sc = make_plane2d(rng)
+        S = 2000 if n_samples is None else n_samples
+        x, var, nrm = sc.sample_surface(rng, S, 0.01)
+        n = 128 if grid is None else grid
+        xq = _grid_queries(sc.room_lo, sc.room_hi, n, 2)
+        params = dict(dim=2, origin=(0.0, 0.0, 0.0), cell=1.0, margin=0.1, n_max=64, k_cand=4, **{"lambda": 500.0},
+                      softmin_alpha=500.0, sign_mode=0)
+    elif name in ("room3d", "traj3d"):
+        rng = np.random.default_rng((2 if name == "room3d" else 4) if seed is None else seed)
+        sc = make_room3d(np.random.default_rng(2 if seed is None else seed))
+        S = 200_000 if n_samples is None else n_samples
+        x, var, nrm = sc.sample_surface(np.random.default_rng(rng.integers(1 << 62)), S, 0.01)
+        if name == "room3d":
+            Q = 1_000_000 if n_queries is None else n_queries
+            xq = sc.room_lo + rng.random((Q, 3)) * (sc.room_hi - sc.room_lo)
+        else:
+            nt = 4096 if n_queries is None else max(1, n_queries // (64 * 8))
+            xq = _bezier_queries(rng, sc, nt, 64)
+        params = dict(dim=3, origin=(0.0, 0.0, 0.0), cell=0.5, margin=0.1, n_max=256, k_cand=8,
+                      **{"lambda": 300.0}, softmin_alpha=300.0, sign_mode=0)
+    elif name == "scale3d":
+        rng = np.random.default_rng(5 if seed is None else seed)
+        sc = make_scale3d(rng)
+        S = 2_000_000 if n_samples is None else n_samples
+        x, var, nrm = sc.sample_surface(rng, S, 0.01)
+        n = 256 if grid is None else grid
+        xq = _grid_queries(sc.room_lo, sc.room_hi, n, 3)
+        params = dict(dim=3, origin=(0.0, 0.0, 0.0), cell=0.5, margin=0.1, n_max=512, k_cand=8,
+                      **{"lambda": 300.0}, softmin_alpha=300.0, sign_mode=0)
+    else:
+        raise KeyError(name)
+    perm = np.random.default_rng(12345).permutation(x.shape[0])  # stream order, not surface order
+    x, var, nrm = x[perm], var[perm], nrm[perm]
+    xq = np.ascontiguousarray(xq, dtype=np.float32)
+    return Workload(name=name, params=params, scene=sc, x=np.ascontiguousarray(x), var=var,
+                    normals=np.ascontiguousarray(nrm), xq=xq, sign=sc.sign(xq.astype(np.float64)))
+
+
+WORKLOADS = ("plane2d", "room3d", "traj3d", "scale3d")
