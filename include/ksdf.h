@@ -1,0 +1,166 @@
+/*
+ * ksdf.h -- C ABI of the GB300 Kernel-SDF back-end query library (libksdf.so).
+ *
+ * Kernel-SDF (arXiv 2603.29227) learns the signed distance d(x) = s(x) u(x) of a scene from surface
+ * samples {x_i, sigma_i^2}.  Its back-end (Sec. IV-B) fits one log-GP per local region on the samples of
+ * an enlarged collection box, with labels f(x_i) = 1 and the RBF kernel k(r) = exp(-lambda r^2)
+ * (lambda = 1/(2 l^2), App. I), and answers a query x by min-fusing the K nearest local GPs:
+ *
+ *   f'(x)   = k'(x)^T (K + Sigma)^{-1} 1,   k'_i = exp(-lambda (|x - x_i|^2 - d^2))    (Sec. IV-B.1, App. D)
+ *   u(x)    = min over the K GPs of sqrt(-log f'(x) / lambda + d^2)                    (kernel table, App. D)
+ *   grad u  = -grad f' / |grad f'|                                                      (Sec. IV-B.1)
+ *   V[u]    = sum_i s_i^2 (a (h - z_i) + 1)^2 sigma_i^2, softmin s, h = s^T z            (Sec. IV-B.3)
+ *   V[f]    = 1 - k^T (K + Sigma)^{-1} k = 1 - e^{-2 lambda d^2} |L^{-1} k'|^2           (Sec. IV-B.1)
+ *
+ * where d is the distance to the GP's nearest training sample.  The library implements that path on one
+ * GPU: integer binning of samples and queries into a hash grid of cells of edge h, training-set
+ * assembly, a batched FP64 Cholesky fit, candidate lists of the K nearest cells, the fused query kernels
+ * and the adjoint.  Readings taken where the paper is silent are listed with the design notes; the main
+ * ones: a "local GP" is a grid cell that holds at least one sample, its collection box is the cell grown
+ * by a margin mu on every side (half open), a training set above n_max keeps ranks floor(j cnt / n_max),
+ * and "the K nearest GPs" are the K valid cells nearest to the query's cell by squared lattice distance,
+ * ties broken by the packed cell key (lexicographic (cz, cy, cx)).
+ *
+ * Conventions for every call:
+ *   - Pointers are plain host or device pointers; the library checks which (cudaPointerGetAttributes).
+ *     Device (or managed) arrays are used in place; host arrays are staged through the context's device
+ *     workspace inside the call.  When any output array is in host memory the call synchronises the
+ *     context's stream before it returns; otherwise every call is asynchronous on that stream.
+ *   - Arrays are dense and row-major: points are n x dim (x, y[, z]) interleaved.
+ *   - The caller owns every array it passes; the library keeps no pointer to them after the call returns
+ *     (ksdf_fit copies what it needs into the model).  The context owns the fitted model and workspaces.
+ *   - Errors are returned as ksdf_status; nothing is thrown across the ABI.  ksdf_last_error() gives a
+ *     message.  Failures detected on the device (bad query values, capacity overflow, a wait that timed
+ *     out) are accumulated in a device status word that ksdf_sync_status() reads and clears.
+ *   - One context is used by one host thread at a time.
+ */
+#ifndef KSDF_H
+#define KSDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KSDF_OK = 0,
+  KSDF_ERR_ARG = 1,         /* invalid argument (NULL, size, parameter out of range, bad pointer) */
+  KSDF_ERR_CUDA = 2,        /* a CUDA runtime call failed; see ksdf_last_error */
+  KSDF_ERR_NOT_PD = 3,      /* reported by ksdf_fit when some cell's K + Sigma is not positive definite
+                               in FP64 (those cells are excluded from every candidate list; the fit
+                               still succeeds for the others) */
+  KSDF_ERR_CAPACITY = 4,    /* a size exceeds a documented limit or the reserved capacity */
+  KSDF_ERR_NOT_FITTED = 5,  /* query before a successful fit */
+  KSDF_ERR_NONFINITE = 6,   /* NaN/Inf or out-of-grid coordinates in the input */
+  KSDF_ERR_TIMEOUT = 7      /* a bounded device-side wait gave up (the kernel returned early) */
+} ksdf_status;
+
+/* Parameters of the method.  Field meanings follow the paper's notation. */
+typedef struct {
+  int dim;              /* n in {2, 3} (Sec. III) */
+  double origin[3];     /* grid origin o; cell c covers [o + c h, o + (c+1) h) per axis */
+  double cell;          /* cell edge h > 0 (one local GP per non-empty cell, Sec. IV-B.1) */
+  double margin;        /* collection-box margin mu >= 0, mu < 8 h */
+  int n_max;            /* training-set cap per cell, 1..512 */
+  int k_cand;           /* K nearest GPs fused by min, 1..32 */
+  double lambda;        /* RBF scale lambda = 1/(2 l^2) > 0 (App. I) */
+  double softmin_alpha; /* softmin temperature of Sec. IV-B.3; <= 0 means lambda */
+  int sign_mode;        /* 0: sign from the caller's array (all +1 when it is NULL);
+                           1: when the caller passes no sign array, use a stand-in that is NOT the
+                           paper's BHM sign: s = +1 iff n_nn . (x - x_nn) >= 0 for the winner GP's
+                           nearest training sample x_nn and its normal n_nn (needs normals at fit) */
+} ksdf_params;
+
+/* out_mask bits for ksdf_query / ksdf_query_f64 (outputs whose bit is clear are not written and may be
+ * NULL). */
+enum {
+  KSDF_OUT_SDF = 1u,
+  KSDF_OUT_GRAD = 2u,
+  KSDF_OUT_VAR_SDF = 4u,
+  KSDF_OUT_VAR_F = 8u,
+  KSDF_OUT_WINNER = 16u,
+  KSDF_OUT_FLAGS = 32u,
+  KSDF_OUT_ALL = 63u
+};
+
+/* Per-query flag bits. */
+enum {
+  KSDF_FLAG_FALLBACK = 1u,   /* winner's f' <= 0: u is the distance to its nearest sample */
+  KSDF_FLAG_NO_GP = 2u,      /* no valid GP cell exists: sdf = +inf, grad 0, var_sdf 0, var_f 1 */
+  KSDF_FLAG_NEAR_TIE = 4u,   /* the second-best candidate's u is within 1e-5 m of the winner's */
+  KSDF_FLAG_ZERO_GRAD = 8u,  /* grad f' vanished: grad output 0 */
+  KSDF_FLAG_CLAMPED = 16u,   /* -log f'/lambda + d^2 < 0 was clamped: u = 0 */
+  KSDF_FLAG_INVALID = 32u    /* the query point was NaN/Inf or outside the grid: outputs NaN */
+};
+
+/* Cell status values (ksdf_get_cells). */
+enum { KSDF_CELL_OK = 0, KSDF_CELL_EMPTY = 1, KSDF_CELL_NOT_PD = 2 };
+
+typedef struct ksdf_ctx ksdf_ctx;
+
+/* Create a context on the current CUDA device; `stream` is a cudaStream_t (NULL = legacy default).
+ * Validates the parameters (KSDF_ERR_ARG).  Allocates only small bookkeeping buffers. */
+ksdf_status ksdf_create(const ksdf_params* params, void* stream, ksdf_ctx** out);
+ksdf_status ksdf_destroy(ksdf_ctx* ctx);
+ksdf_status ksdf_set_stream(ksdf_ctx* ctx, void* stream);
+
+/* Pre-size the workspaces for up to max_samples samples and max_queries queries per call, so that
+ * later calls within those sizes allocate nothing. */
+ksdf_status ksdf_reserve(ksdf_ctx* ctx, int64_t max_samples, int64_t max_queries);
+
+/* Fit (Sec. IV-B.1): bin the S samples x (S x dim, float64) into cells, assemble every cell's training
+ * set from its collection box, build A = K + diag(sigma^2) (var: S float32 sigma_i^2 >= 0, NULL = 0),
+ * factor A = L L^T in FP64, and store alpha = A^{-1} 1 and L^{-1} in FP64 and FP32.  normals (S x dim
+ * float32, may be NULL) feed the sign stand-in.  Replaces any previous model.  Synchronises the stream
+ * (cell counts decide allocation sizes).  Returns KSDF_ERR_NONFINITE for NaN/Inf/out-of-grid samples
+ * or a negative variance, KSDF_ERR_CAPACITY if a collection box holds more than 8192 samples before
+ * the cap, KSDF_ERR_NOT_PD if some cell failed the factorisation (the model is still usable). */
+ksdf_status ksdf_fit(ksdf_ctx* ctx, const double* x, const float* var, const float* normals, int64_t S);
+
+/* Mixed-precision query: Q points xq (Q x dim float32); sign (Q int8, +1/-1, may be NULL).  FP32 SIMT
+ * arithmetic in cell-local coordinates for the mean (compensated sum), gradient and softmin variance;
+ * the GP variance contraction is computed from L^{-1} stored as FP32 hi + lo.  Outputs (selected by
+ * out_mask): sdf[Q], grad[Q x dim] (gradient of d = s grad u), var_sdf[Q] (V[u], Sec. IV-B.3),
+ * var_f[Q] (V[f], Sec. IV-B.1), winner[Q] (cell id of the fused GP, -1 if none; keep it for the
+ * backward), flags[Q] (KSDF_FLAG_*). */
+ksdf_status ksdf_query(ksdf_ctx* ctx, const float* xq, int64_t Q, const int8_t* sign, uint32_t out_mask, float* sdf,
+                       float* grad, float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags);
+
+/* The same query in FP64 end to end on the GPU (the plain path): xq and the outputs are float64. */
+ksdf_status ksdf_query_f64(ksdf_ctx* ctx, const double* xq, int64_t Q, const int8_t* sign, uint32_t out_mask,
+                           double* sdf, double* grad, double* var_sdf, double* var_f, int32_t* winner, uint32_t* flags);
+
+/* Adjoint of the query (the spec differentiation path): given the cotangents d_sdf[Q] and
+ * (optionally, may be NULL) d_grad[Q x dim] of the sdf and grad outputs, write d_xq[Q x dim] (overwritten)
+ * and ADD the sample-position gradient into d_x[S x dim] (S of the last fit, ids in the fit's order).
+ * winner is the array the forward query returned for the same xq and sign.  Per-cell recomputation:
+ * nothing from the forward pass is stored.  The chain through alpha = A^{-1} 1 is taken with one FP64
+ * triangular-solve pair per touched cell; sign, sigma^2, the winner choice and the scaling distance are
+ * held constant (u does not depend on the scaling). */
+ksdf_status ksdf_query_backward(ksdf_ctx* ctx, const float* xq, int64_t Q, const int8_t* sign, const int32_t* winner,
+                                const float* d_sdf, const float* d_grad, float* d_xq, float* d_x);
+
+/* Synchronise the stream, read and clear the device status word (KSDF_OK if no device failure). */
+ksdf_status ksdf_sync_status(ksdf_ctx* ctx);
+const char* ksdf_last_error(const ksdf_ctx* ctx);
+
+/* ---- introspection of the fitted model (host outputs; synchronise the stream) ---- */
+
+/* Number of cells G and of training-set members (sum of N_g). */
+ksdf_status ksdf_model_size(ksdf_ctx* ctx, int64_t* n_cells, int64_t* n_members);
+/* keys[G] (packed (cz,cy,cx) as three biased 21-bit fields, z most significant), status[G], ts_off[G+1],
+ * members[n_members] (global sample ids, ascending within a cell).  Any pointer may be NULL. */
+ksdf_status ksdf_get_cells(ksdf_ctx* ctx, uint64_t* keys, int32_t* status, int64_t* ts_off, int64_t* members);
+/* alpha (n_members, float64) in training-set order; linv (sum N_g (N_g+1)/2, float64) packed row-major
+ * lower triangle per cell, cells in id order.  Either may be NULL. */
+ksdf_status ksdf_get_fit(ksdf_ctx* ctx, double* alpha, double* linv);
+/* Packed keys of points (n x dim float64) and the candidate lists (n x K int32, -1 padded; count[n]) of the
+ * cells those keys name.  Device or host arrays. */
+ksdf_status ksdf_bin(ksdf_ctx* ctx, const double* x, int64_t n, uint64_t* keys);
+ksdf_status ksdf_candidates(ksdf_ctx* ctx, const uint64_t* bin_keys, int64_t n, int32_t* cand, int32_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

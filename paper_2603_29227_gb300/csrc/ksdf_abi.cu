@@ -1,0 +1,348 @@
+// ksdf_abi.cu -- the extern "C" entry points of libksdf.so (declared and documented in include/ksdf.h):
+// argument checks, staging of host arrays through device workspaces, and dispatch to the fit, query and
+// backward pipelines.
+#include <cstdarg>
+#include <vector>
+
+#include "ksdf_internal.cuh"
+
+namespace ksdf {
+
+ksdf_status set_err(ksdf_ctx* c, ksdf_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+ksdf_status cuda_err(ksdf_ctx* c, cudaError_t e, const char* what) {
+  return set_err(c, KSDF_ERR_CUDA, "CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+}
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return cudaSuccess;
+  if (b.p) {
+    cudaError_t e = cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (e != cudaSuccess) return e;
+  }
+  size_t n = (bytes + 255) & ~size_t(255);
+  cudaError_t e = cudaMalloc(&b.p, n);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return e;
+  }
+  b.bytes = n;
+  return cudaSuccess;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+namespace {
+
+bool on_device(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// stage an input array: device pointers pass through, host arrays are copied into stage[slot]
+ksdf_status stage_in(ksdf_ctx* c, int slot, const void* p, size_t bytes, const void** out) {
+  if (!p || on_device(p)) {
+    *out = p;
+    return KSDF_OK;
+  }
+  KSDF_CUDA(c, ensure(c->stage[slot], bytes));
+  KSDF_CUDA(c, cudaMemcpyAsync(c->stage[slot].p, p, bytes, cudaMemcpyHostToDevice, c->stream));
+  *out = c->stage[slot].p;
+  return KSDF_OK;
+}
+
+struct OutStage {
+  void* host = nullptr;
+  void* dev = nullptr;
+  size_t bytes = 0;
+};
+
+ksdf_status stage_out(ksdf_ctx* c, int slot, void* p, size_t bytes, bool copy_in, OutStage* o) {
+  o->host = nullptr;
+  o->dev = p;
+  o->bytes = bytes;
+  if (!p || on_device(p)) return KSDF_OK;
+  KSDF_CUDA(c, ensure(c->stage[slot], bytes));
+  o->host = p;
+  o->dev = c->stage[slot].p;
+  if (copy_in) KSDF_CUDA(c, cudaMemcpyAsync(o->dev, p, bytes, cudaMemcpyHostToDevice, c->stream));
+  return KSDF_OK;
+}
+
+ksdf_status finish_out(ksdf_ctx* c, OutStage* o, int n) {
+  bool any = false;
+  for (int i = 0; i < n; ++i)
+    if (o[i].host) {
+      KSDF_CUDA(c, cudaMemcpyAsync(o[i].host, o[i].dev, o[i].bytes, cudaMemcpyDeviceToHost, c->stream));
+      any = true;
+    }
+  if (any) KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return KSDF_OK;
+}
+
+ksdf_status check_params(const ksdf_params* a) {
+  if (!a) return KSDF_ERR_ARG;
+  if (a->dim != 2 && a->dim != 3) return KSDF_ERR_ARG;
+  if (!(a->cell > 0) || !(a->margin >= 0) || !(a->margin < 8 * a->cell)) return KSDF_ERR_ARG;
+  if (a->n_max < 1 || a->n_max > kMaxNmax) return KSDF_ERR_ARG;
+  if (a->k_cand < 1 || a->k_cand > kMaxK) return KSDF_ERR_ARG;
+  if (!(a->lambda > 0) || !(a->lambda < 1e12)) return KSDF_ERR_ARG;
+  for (int j = 0; j < 3; ++j)
+    if (!(a->origin[j] == a->origin[j]) || a->origin[j] > 1e300 || a->origin[j] < -1e300) return KSDF_ERR_ARG;
+  if (a->sign_mode != 0 && a->sign_mode != 1) return KSDF_ERR_ARG;
+  return KSDF_OK;
+}
+
+}  // namespace
+}  // namespace ksdf
+
+using namespace ksdf;
+
+extern "C" {
+
+ksdf_status ksdf_create(const ksdf_params* params, void* stream, ksdf_ctx** out) {
+  if (!out) return KSDF_ERR_ARG;
+  *out = nullptr;
+  if (check_params(params) != KSDF_OK) return KSDF_ERR_ARG;
+  ksdf_ctx* c = new ksdf_ctx();
+  c->abi = *params;
+  c->p.dim = params->dim;
+  for (int j = 0; j < 3; ++j) c->p.o[j] = j < params->dim ? params->origin[j] : 0.0;
+  c->p.h = params->cell;
+  c->p.mu = params->margin;
+  c->p.n_max = params->n_max;
+  c->p.K = params->k_cand;
+  c->p.lambda = params->lambda;
+  c->p.alpha_s = params->softmin_alpha > 0 ? params->softmin_alpha : params->lambda;
+  c->p.sign_mode = params->sign_mode;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = ensure(c->status_word, 16);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status_word.p, 0, 16, c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return KSDF_ERR_CUDA;
+  }
+  *out = c;
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_destroy(ksdf_ctx* c) {
+  if (!c) return KSDF_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  Model& m = c->m;
+  DevBuf* bufs[] = {&m.key, &m.status, &m.n, &m.ts_off, &m.linv_off, &m.hkeys, &m.hvals, &m.cell_order, &m.mf4,
+                    &m.md4, &m.mvar, &m.mnrm, &m.mgid, &m.mpad, &m.linv64, &m.linv32, &m.linv32lo, &m.x,
+                    &c->status_word};
+  for (DevBuf* b : bufs) release(*b);
+  for (auto& b : c->ws) release(b);
+  for (auto& b : c->stage) release(b);
+  delete c;
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_set_stream(ksdf_ctx* c, void* stream) {
+  if (!c) return KSDF_ERR_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_reserve(ksdf_ctx* c, int64_t max_samples, int64_t max_queries) {
+  if (!c || max_samples < 0 || max_queries < 0) return KSDF_ERR_ARG;
+  c->reserved_s = max_samples;
+  c->reserved_q = max_queries;
+  if (max_queries > 0) return query_reserve(c, max_queries, c->m.G > 0 ? c->m.G : 1);
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_fit(ksdf_ctx* c, const double* x, const float* var, const float* normals, int64_t S) {
+  if (!c) return KSDF_ERR_ARG;
+  if (S <= 0 || !x) return set_err(c, KSDF_ERR_ARG, "ksdf_fit: need S > 0 samples");
+  const int dim = c->p.dim;
+  const void *dx, *dv, *dn;
+  ksdf_status s;
+  if ((s = stage_in(c, 0, x, sizeof(double) * S * dim, &dx))) return s;
+  if ((s = stage_in(c, 1, var, sizeof(float) * S, &dv))) return s;
+  if ((s = stage_in(c, 2, normals, sizeof(float) * S * dim, &dn))) return s;
+  return fit_model(c, static_cast<const double*>(dx), static_cast<const float*>(dv), static_cast<const float*>(dn), S);
+}
+
+static ksdf_status query_common(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const int8_t* sign,
+                                uint32_t mask, void* sdf, void* grad, void* var_sdf, void* var_f, int32_t* winner,
+                                uint32_t* flags) {
+  if (!c) return KSDF_ERR_ARG;
+  if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "query before a successful fit");
+  if (Q < 0 || (Q > 0 && !xq)) return set_err(c, KSDF_ERR_ARG, "query: bad Q or NULL points");
+  if (Q >= (1LL << 31)) return set_err(c, KSDF_ERR_CAPACITY, "query: Q must be < 2^31");
+  mask &= KSDF_OUT_ALL;
+  if (((mask & KSDF_OUT_SDF) && !sdf) || ((mask & KSDF_OUT_GRAD) && !grad) || ((mask & KSDF_OUT_VAR_SDF) && !var_sdf) ||
+      ((mask & KSDF_OUT_VAR_F) && !var_f) || ((mask & KSDF_OUT_WINNER) && !winner) ||
+      ((mask & KSDF_OUT_FLAGS) && !flags))
+    return set_err(c, KSDF_ERR_ARG, "query: an output selected by out_mask is NULL");
+  if (Q == 0) return KSDF_OK;
+  const int dim = c->p.dim;
+  const size_t fs = f64 ? sizeof(double) : sizeof(float);
+  const void *dxq, *dsg;
+  ksdf_status s;
+  if ((s = stage_in(c, 0, xq, fs * Q * dim, &dxq))) return s;
+  if ((s = stage_in(c, 1, sign, sizeof(int8_t) * Q, &dsg))) return s;
+  OutStage o[6];
+  if ((s = stage_out(c, 2, (mask & KSDF_OUT_SDF) ? sdf : nullptr, fs * Q, false, &o[0]))) return s;
+  if ((s = stage_out(c, 3, (mask & KSDF_OUT_GRAD) ? grad : nullptr, fs * Q * dim, false, &o[1]))) return s;
+  if ((s = stage_out(c, 4, (mask & KSDF_OUT_VAR_SDF) ? var_sdf : nullptr, fs * Q, false, &o[2]))) return s;
+  if ((s = stage_out(c, 5, (mask & KSDF_OUT_VAR_F) ? var_f : nullptr, fs * Q, false, &o[3]))) return s;
+  if ((s = stage_out(c, 6, (mask & KSDF_OUT_WINNER) ? winner : nullptr, sizeof(int32_t) * Q, false, &o[4]))) return s;
+  if ((s = stage_out(c, 7, (mask & KSDF_OUT_FLAGS) ? flags : nullptr, sizeof(uint32_t) * Q, false, &o[5]))) return s;
+  s = run_query(c, dxq, f64, Q, static_cast<const int8_t*>(dsg), mask, o[0].dev, o[1].dev, o[2].dev, o[3].dev,
+                static_cast<int32_t*>(o[4].dev), static_cast<uint32_t*>(o[5].dev));
+  if (s) return s;
+  return finish_out(c, o, 6);
+}
+
+ksdf_status ksdf_query(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, uint32_t out_mask, float* sdf,
+                       float* grad, float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags) {
+  return query_common(c, xq, false, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags);
+}
+
+ksdf_status ksdf_query_f64(ksdf_ctx* c, const double* xq, int64_t Q, const int8_t* sign, uint32_t out_mask,
+                           double* sdf, double* grad, double* var_sdf, double* var_f, int32_t* winner,
+                           uint32_t* flags) {
+  return query_common(c, xq, true, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags);
+}
+
+ksdf_status ksdf_query_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, const int32_t* winner,
+                                const float* d_sdf, const float* d_grad, float* d_xq, float* d_x) {
+  if (!c) return KSDF_ERR_ARG;
+  if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "backward before a successful fit");
+  if (Q < 0 || (Q > 0 && (!xq || !winner || !d_sdf || !d_xq || !d_x)))
+    return set_err(c, KSDF_ERR_ARG, "ksdf_query_backward: NULL argument");
+  if (Q == 0) return KSDF_OK;
+  const int dim = c->p.dim;
+  const int64_t S = c->m.S;
+  const void *dxq, *dsg, *dw, *dds, *ddg;
+  ksdf_status s;
+  if ((s = stage_in(c, 0, xq, sizeof(float) * Q * dim, &dxq))) return s;
+  if ((s = stage_in(c, 1, sign, Q, &dsg))) return s;
+  if ((s = stage_in(c, 2, winner, sizeof(int32_t) * Q, &dw))) return s;
+  if ((s = stage_in(c, 3, d_sdf, sizeof(float) * Q, &dds))) return s;
+  if ((s = stage_in(c, 4, d_grad, sizeof(float) * Q * dim, &ddg))) return s;
+  OutStage o[2];
+  if ((s = stage_out(c, 5, d_xq, sizeof(float) * Q * dim, false, &o[0]))) return s;
+  if ((s = stage_out(c, 6, d_x, sizeof(float) * S * dim, true, &o[1]))) return s;
+  s = run_backward(c, static_cast<const float*>(dxq), Q, static_cast<const int8_t*>(dsg),
+                   static_cast<const int32_t*>(dw), static_cast<const float*>(dds), static_cast<const float*>(ddg),
+                   static_cast<float*>(o[0].dev), static_cast<float*>(o[1].dev));
+  if (s) return s;
+  return finish_out(c, o, 2);
+}
+
+ksdf_status ksdf_sync_status(ksdf_ctx* c) {
+  if (!c) return KSDF_ERR_ARG;
+  uint32_t w = 0;
+  KSDF_CUDA(c, cudaMemcpyAsync(&w, c->status_word.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  KSDF_CUDA(c, cudaMemsetAsync(c->status_word.p, 0, sizeof(uint32_t), c->stream));
+  if (w & ST_TIMEOUT) return set_err(c, KSDF_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (w & ST_CAPACITY) return set_err(c, KSDF_ERR_CAPACITY, "a device-side capacity was exceeded");
+  if (w & ST_NONFINITE) return set_err(c, KSDF_ERR_NONFINITE, "NaN/Inf or out-of-grid query point(s)");
+  return KSDF_OK;
+}
+
+const char* ksdf_last_error(const ksdf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ksdf_status ksdf_model_size(ksdf_ctx* c, int64_t* n_cells, int64_t* n_members) {
+  if (!c) return KSDF_ERR_ARG;
+  if (!c->fitted) return KSDF_ERR_NOT_FITTED;
+  KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (n_cells) *n_cells = c->m.G;
+  if (n_members) *n_members = c->m.M;
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_get_cells(ksdf_ctx* c, uint64_t* keys, int32_t* status, int64_t* ts_off, int64_t* members) {
+  if (!c) return KSDF_ERR_ARG;
+  if (!c->fitted) return KSDF_ERR_NOT_FITTED;
+  Model& m = c->m;
+  KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (keys) KSDF_CUDA(c, cudaMemcpy(keys, m.key.p, sizeof(uint64_t) * m.G, cudaMemcpyDefault));
+  if (status) KSDF_CUDA(c, cudaMemcpy(status, m.status.p, sizeof(int32_t) * m.G, cudaMemcpyDefault));
+  if (ts_off) KSDF_CUDA(c, cudaMemcpy(ts_off, m.ts_off.p, sizeof(int64_t) * (m.G + 1), cudaMemcpyDefault));
+  if (members) {
+    std::vector<int32_t> tmp((size_t)m.M);
+    if (m.M) KSDF_CUDA(c, cudaMemcpy(tmp.data(), m.mgid.p, sizeof(int32_t) * m.M, cudaMemcpyDeviceToHost));
+    std::vector<int64_t> t64(tmp.begin(), tmp.end());
+    if (m.M) KSDF_CUDA(c, cudaMemcpy(members, t64.data(), sizeof(int64_t) * m.M, cudaMemcpyDefault));
+  }
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_get_fit(ksdf_ctx* c, double* alpha, double* linv) {
+  if (!c) return KSDF_ERR_ARG;
+  if (!c->fitted) return KSDF_ERR_NOT_FITTED;
+  Model& m = c->m;
+  KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (alpha && m.M) {
+    std::vector<D4> tmp((size_t)m.M);
+    KSDF_CUDA(c, cudaMemcpy(tmp.data(), m.md4.p, sizeof(D4) * m.M, cudaMemcpyDeviceToHost));
+    std::vector<double> a((size_t)m.M);
+    for (int64_t i = 0; i < m.M; ++i) a[i] = tmp[i].w;
+    KSDF_CUDA(c, cudaMemcpy(alpha, a.data(), sizeof(double) * m.M, cudaMemcpyDefault));
+  }
+  if (linv && m.linv_total)
+    KSDF_CUDA(c, cudaMemcpy(linv, m.linv64.p, sizeof(double) * m.linv_total, cudaMemcpyDefault));
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_bin(ksdf_ctx* c, const double* x, int64_t n, uint64_t* keys) {
+  if (!c || n < 0 || (n > 0 && (!x || !keys))) return KSDF_ERR_ARG;
+  if (n == 0) return KSDF_OK;
+  const void* dx;
+  ksdf_status s;
+  if ((s = stage_in(c, 0, x, sizeof(double) * n * c->p.dim, &dx))) return s;
+  OutStage o;
+  if ((s = stage_out(c, 1, keys, sizeof(uint64_t) * n, false, &o))) return s;
+  if ((s = bin_points(c, static_cast<const double*>(dx), n, static_cast<uint64_t*>(o.dev)))) return s;
+  return finish_out(c, &o, 1);
+}
+
+ksdf_status ksdf_candidates(ksdf_ctx* c, const uint64_t* bin_keys, int64_t n, int32_t* cand, int32_t* count) {
+  if (!c || n < 0 || (n > 0 && (!bin_keys || !cand || !count))) return KSDF_ERR_ARG;
+  if (!c->fitted) return KSDF_ERR_NOT_FITTED;
+  if (n == 0) return KSDF_OK;
+  const void* dk;
+  ksdf_status s;
+  if ((s = stage_in(c, 0, bin_keys, sizeof(uint64_t) * n, &dk))) return s;
+  OutStage o[2];
+  if ((s = stage_out(c, 1, cand, sizeof(int32_t) * n * c->p.K, false, &o[0]))) return s;
+  if ((s = stage_out(c, 2, count, sizeof(int32_t) * n, false, &o[1]))) return s;
+  if ((s = candidates_for_keys(c, static_cast<const uint64_t*>(dk), n, static_cast<int32_t*>(o[0].dev),
+                               static_cast<int32_t*>(o[1].dev))))
+    return s;
+  return finish_out(c, o, 2);
+}
+
+}  // extern "C"

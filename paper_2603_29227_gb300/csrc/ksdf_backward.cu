@@ -1,0 +1,376 @@
+// ksdf_backward.cu -- adjoint of the Kernel-SDF query with respect to the query points and the sample
+// positions (differentiation path; the paper states the SDF is differentiable, Sec. IV-B).
+//
+// With d held constant (u does not depend on the scaling of App. D), for a query q whose min-fusion
+// winner is cell g with training set {x_i, alpha_i}:
+//   u^2 = -log f'/lambda + d^2,  f' = sum_i alpha_i k'_i,  k'_i = exp(-lambda (|x - x_i|^2 - d^2))
+//   dL/df'  = -s dsdf / (2 lambda u f')                                   (sdf = s u)
+//   x_bar  += dL/df' grad_x f' = dL/df' (-2 lambda G),  G = sum_i alpha_i k'_i (x - x_i)
+//   X_bar_i += dL/df' 2 lambda alpha_i k'_i (x - x_i),   alpha_bar_i += dL/df' k'_i
+// For the gradient output s G/|G| with cotangent gb: v = s (I - g g^T) gb / |G|, and
+//   x_bar += sum_i alpha_i k'_i (v - 2 lambda r_i (r_i . v)),  X_bar_i -= the i-th term,
+//   alpha_bar_i += k'_i (r_i . v).
+// Through alpha = A^{-1} 1 (A = K + Sigma): b = A^{-1} alpha_bar = L^{-T} L^{-1} alpha_bar (FP64, with the
+// stored L^{-1}), X_bar_i += sum_j 2 lambda K_ij (b_i alpha_j + b_j alpha_i)(x_i - x_j).
+// Kernel 1 recomputes k' per (query, winner) tile and reduces alpha_bar / X_bar in shared memory; kernel 2
+// runs once per touched cell.
+#include "ksdf_internal.cuh"
+
+#include <algorithm>
+
+namespace ksdf {
+
+namespace {
+
+constexpr int kTW = 64;
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ inline float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__global__ void k_bw_count(const int32_t* winner, int64_t Q, int64_t G, int32_t* rank, int64_t* cnt, float* d_xq,
+                           int dim, uint32_t* st) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  int w = winner[q];
+  if (w >= G) {
+    atomicOr(st, ST_CAPACITY);
+    w = -1;
+  }
+  if (w < 0) {
+    for (int j = 0; j < dim; ++j) d_xq[q * dim + j] = 0.f;
+    rank[q] = -1;
+    return;
+  }
+  rank[q] = (int32_t)atomicAdd((unsigned long long*)&cnt[w], 1ull);
+}
+
+__global__ void k_bw_scatter(const int32_t* winner, const int32_t* rank, int64_t Q, int64_t G, const int64_t* off,
+                             int32_t* sorted) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  int w = winner[q];
+  if (w >= 0 && w < G && rank[q] >= 0) sorted[off[w] + rank[q]] = (int32_t)q;
+}
+
+__global__ void k_bw_tiles(const int64_t* cnt, const int64_t* off, const int64_t* toff, int64_t G, int4* tiles) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  int64_t c = cnt[g];
+  for (int64_t t = 0; t * kTW < c; ++t)
+    tiles[toff[g] + t] = make_int4((int)g, (int)(off[g] + t * kTW), (int)(c - t * kTW < kTW ? c - t * kTW : kTW), 0);
+}
+
+__global__ void k_ntiles_w(const int64_t* cnt, int64_t n, int64_t* nt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) nt[i] = (cnt[i] + kTW - 1) / kTW;
+}
+
+struct BwArgs {
+  const int4* tiles;
+  const int64_t* n_tiles;
+  int* counter;
+  const int32_t* sorted;
+  const int64_t* ts_off;
+  const int32_t* cell_n;
+  const uint64_t* cell_key;
+  const float4* mf4;
+  const int32_t* mgid;
+  const float4* mnrm;
+  int has_normals;
+  const int8_t* sign;
+  const float* d_sdf;
+  const float* d_grad;
+  float* d_xq;
+  float* d_x;
+  double* abar;  // per member
+};
+
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// per (winner, tile of queries): x_bar per query; alpha_bar and X_bar reduced over the tile
+__global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Params p) {
+  extern __shared__ __align__(16) float4 s_x[];  // [n_max] samples, then [n_max][4] accumulators
+  __shared__ int s_tile;
+  float* s_acc = reinterpret_cast<float*>(s_x + p.n_max);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const float lam = (float)p.lambda;
+  const float c1 = lam * kLog2e;
+  const int64_t ntiles = *a.n_tiles;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const int4 tile = a.tiles[t];
+    const int g = tile.x;
+    const int n = a.cell_n[g];
+    const int64_t m0 = a.ts_off[g];
+    for (int i = tid; i < n; i += blockDim.x) {
+      s_x[i] = a.mf4[m0 + i];
+      s_acc[4 * i] = s_acc[4 * i + 1] = s_acc[4 * i + 2] = s_acc[4 * i + 3] = 0.f;
+    }
+    int cc[3];
+    unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
+    const bool live = tid < tile.z;
+    const int q = live ? a.sorted[tile.y + tid] : 0;
+    float ql[3] = {0.f, 0.f, 0.f};
+    if (live)
+      for (int j = 0; j < p.dim; ++j)
+        ql[j] = (float)__dsub_rn((double)xq[(int64_t)q * p.dim + j], cell_base(p.o[j], cc[j], p.h));
+    __syncthreads();
+    // forward recomputation
+    float m = INFINITY;
+    int nn = 0;
+    float f = 0.f, comp = 0.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
+    if (live) {
+      for (int i = 0; i < n; ++i) {
+        const float4 v = s_x[i];
+        const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (r2 < m) {
+          m = r2;
+          nn = i;
+        }
+      }
+      const float cmn = c1 * m;
+      for (int i = 0; i < n; ++i) {
+        const float4 v = s_x[i];
+        const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+        const float kp = ex2(fmaf(-c1, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), cmn));
+        const float ak = v.w * kp;
+        const float y = ak - comp;
+        const float tt = f + y;
+        comp = (tt - f) - y;
+        f = tt;
+        G0 = fmaf(ak, dx, G0);
+        G1 = fmaf(ak, dy, G1);
+        G2 = fmaf(ak, dz, G2);
+      }
+      f -= comp;
+    }
+    float s = 1.f;
+    if (live) {
+      if (a.sign) {
+        s = a.sign[q] < 0 ? -1.f : 1.f;
+      } else if (p.sign_mode == 1 && a.has_normals) {
+        const float4 v = s_x[nn];
+        const float4 nv = a.mnrm[m0 + nn];
+        s = (nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z)) >= 0.f ? 1.f : -1.f;
+      }
+    }
+    const float ub = live ? s * a.d_sdf[q] : 0.f;
+    float fb = 0.f;
+    bool fallback = false;
+    if (live) {
+      if (f > 0.f) {
+        const float u2 = fmaf(-logf(f), 1.f / lam, m);
+        fb = u2 > 0.f ? -ub / (2.f * lam * sqrtf(u2) * f) : 0.f;
+      } else {
+        fallback = true;
+      }
+    }
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+    if (live && a.d_grad) {
+      const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
+      if (gn > 0.f) {
+        const float g0 = G0 / gn, g1 = G1 / gn, g2 = G2 / gn;
+        const float b0 = a.d_grad[(int64_t)q * p.dim + 0], b1 = a.d_grad[(int64_t)q * p.dim + 1];
+        const float b2 = p.dim == 3 ? a.d_grad[(int64_t)q * p.dim + 2] : 0.f;
+        const float dot = g0 * b0 + g1 * b1 + g2 * b2;
+        const float sc = s / gn;
+        v0 = sc * (b0 - g0 * dot);
+        v1 = sc * (b1 - g1 * dot);
+        v2 = sc * (b2 - g2 * dot);
+      }
+    }
+    float xb0 = fb * (-2.f * lam * G0), xb1 = fb * (-2.f * lam * G1), xb2 = fb * (-2.f * lam * G2);
+    if (live && fallback && m > 0.f) {
+      const float4 v = s_x[nn];
+      const float d = sqrtf(m);
+      xb0 += ub * (ql[0] - v.x) / d;
+      xb1 += ub * (ql[1] - v.y) / d;
+      xb2 += ub * (ql[2] - v.z) / d;
+    }
+    // per-sample contributions, reduced over the warp then into shared memory
+    const float cmn = c1 * m;
+    for (int i = 0; i < n; ++i) {
+      float ab = 0.f, X0 = 0.f, X1 = 0.f, X2 = 0.f;
+      if (live) {
+        const float4 v = s_x[i];
+        const float r0 = ql[0] - v.x, r1 = ql[1] - v.y, r2v = ql[2] - v.z;
+        const float kp = ex2(fmaf(-c1, fmaf(r0, r0, fmaf(r1, r1, r2v * r2v)), cmn));
+        const float ak = v.w * kp;
+        const float rv = r0 * v0 + r1 * v1 + r2v * v2;
+        ab = fb * kp + kp * rv;
+        const float tl = 2.f * lam * rv;
+        const float mv0 = ak * (v0 - tl * r0), mv1 = ak * (v1 - tl * r1), mv2 = ak * (v2 - tl * r2v);
+        xb0 += mv0;
+        xb1 += mv1;
+        xb2 += mv2;
+        const float dir = fb * 2.f * lam * ak;
+        X0 = dir * r0 - mv0;
+        X1 = dir * r1 - mv1;
+        X2 = dir * r2v - mv2;
+        if (fallback && i == nn && m > 0.f) {
+          const float d = sqrtf(m);
+          X0 -= ub * r0 / d;
+          X1 -= ub * r1 / d;
+          X2 -= ub * r2v / d;
+        }
+      }
+      ab = warp_sum(ab);
+      X0 = warp_sum(X0);
+      X1 = warp_sum(X1);
+      X2 = warp_sum(X2);
+      if (lane == 0) {
+        atomicAdd(&s_acc[4 * i], ab);
+        atomicAdd(&s_acc[4 * i + 1], X0);
+        atomicAdd(&s_acc[4 * i + 2], X1);
+        atomicAdd(&s_acc[4 * i + 3], X2);
+      }
+    }
+    if (live) {
+      a.d_xq[(int64_t)q * p.dim + 0] = xb0;
+      a.d_xq[(int64_t)q * p.dim + 1] = xb1;
+      if (p.dim == 3) a.d_xq[(int64_t)q * p.dim + 2] = xb2;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+      atomicAdd(&a.abar[m0 + i], (double)s_acc[4 * i]);
+      const int gid = a.mgid[m0 + i];
+      for (int j = 0; j < p.dim; ++j) atomicAdd(&a.d_x[(int64_t)gid * p.dim + j], s_acc[4 * i + 1 + j]);
+    }
+    __syncthreads();
+  }
+}
+
+// per touched cell: b = L^{-T} L^{-1} alpha_bar (FP64), then the alpha-path X_bar terms
+__global__ void __launch_bounds__(256) k_bw_cell(const int64_t* qcnt, int64_t G, const int64_t* ts_off,
+                                                 const int32_t* cell_n, const int64_t* linv_off, const double* linv64,
+                                                 const D4* md4, const float4* mf4, const int32_t* mgid,
+                                                 const double* abar, Params p, float* d_x) {
+  extern __shared__ double sh[];  // [n] abar, [n] y, [n] b
+  for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
+    if (qcnt[g] == 0) continue;
+    const int n = cell_n[g];
+    const int64_t m0 = ts_off[g];
+    const double* L = linv64 + linv_off[g];
+    double* sa = sh;
+    double* sy = sh + n;
+    double* sb = sh + 2 * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sa[i] = abar[m0 + i];
+    __syncthreads();
+    // y = L^{-1} abar (row j of the packed lower triangle)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double* r = L + (int64_t)j * (j + 1) / 2;
+      double acc = 0.0;
+      for (int i = 0; i <= j; ++i) acc = fma(r[i], sa[i], acc);
+      sy[j] = acc;
+    }
+    __syncthreads();
+    // b = L^{-T} y: b_i = sum_{j >= i} Linv_ji y_j
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double acc = 0.0;
+      for (int j = i; j < n; ++j) acc = fma(L[(int64_t)j * (j + 1) / 2 + i], sy[j], acc);
+      sb[i] = acc;
+    }
+    __syncthreads();
+    const float c1 = (float)p.lambda * kLog2e;
+    const float tl = 2.f * (float)p.lambda;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float4 xi = mf4[m0 + i];
+      const double bi = sb[i], ai = md4[m0 + i].w;
+      float X0 = 0.f, X1 = 0.f, X2 = 0.f;
+      for (int j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const float4 xj = mf4[m0 + j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float kij = ex2(-c1 * fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float cf = tl * kij * (float)(bi * md4[m0 + j].w + sb[j] * ai);
+        X0 = fmaf(cf, dx, X0);
+        X1 = fmaf(cf, dy, X1);
+        X2 = fmaf(cf, dz, X2);
+      }
+      const int gid = mgid[m0 + i];
+      atomicAdd(&d_x[(int64_t)gid * p.dim + 0], X0);
+      atomicAdd(&d_x[(int64_t)gid * p.dim + 1], X1);
+      if (p.dim == 3) atomicAdd(&d_x[(int64_t)gid * p.dim + 2], X2);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, const int32_t* winner,
+                         const float* d_sdf, const float* d_grad, float* d_xq, float* d_x) {
+  cudaStream_t st = c->stream;
+  const Params& p = c->p;
+  Model& m = c->m;
+  const int64_t G = m.G;
+  uint32_t* stw = ptr<uint32_t>(c->status_word);
+  KSDF_CUDA(c, ensure(c->ws[WS_QRANK], sizeof(int32_t) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_QWSORT], sizeof(int32_t) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_CELLQ], sizeof(int64_t) * (4 * G + 8)));
+  const int64_t max_tiles = Q / kTW + G + 1;
+  KSDF_CUDA(c, ensure(c->ws[WS_TILE], sizeof(int4) * max_tiles));
+  KSDF_CUDA(c, ensure(c->ws[WS_BW], sizeof(double) * (m.M + 1)));
+  int32_t* rank = ptr<int32_t>(c->ws[WS_QRANK]);
+  int32_t* sorted = ptr<int32_t>(c->ws[WS_QWSORT]);
+  int64_t* cb = ptr<int64_t>(c->ws[WS_CELLQ]);
+  int64_t *cnt = cb, *off = cb + G, *nt = cb + 2 * G, *toff = cb + 3 * G, *tot = cb + 4 * G;
+  int* counter = reinterpret_cast<int*>(tot + 2);
+  int4* tiles = ptr<int4>(c->ws[WS_TILE]);
+  double* abar = ptr<double>(c->ws[WS_BW]);
+  KSDF_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int64_t) * G, st));
+  KSDF_CUDA(c, cudaMemsetAsync(tot, 0, sizeof(int64_t) * 4, st));
+  KSDF_CUDA(c, cudaMemsetAsync(abar, 0, sizeof(double) * (m.M + 1), st));
+  k_bw_count<<<ceil_div(Q, 256), 256, 0, st>>>(winner, Q, G, rank, cnt, d_xq, p.dim, stw);
+  KSDF_CUDA(c, scan_i64(cnt, off, G, nullptr, c->ws[WS_SCAN], st));
+  k_ntiles_w<<<ceil_div(G, 256), 256, 0, st>>>(cnt, G, nt);
+  KSDF_CUDA(c, scan_i64(nt, toff, G, &tot[0], c->ws[WS_SCAN], st));
+  k_bw_scatter<<<ceil_div(Q, 256), 256, 0, st>>>(winner, rank, Q, G, off, sorted);
+  k_bw_tiles<<<ceil_div(G, 256), 256, 0, st>>>(cnt, off, toff, G, tiles);
+  BwArgs a;
+  a.tiles = tiles;
+  a.n_tiles = &tot[0];
+  a.counter = counter;
+  a.sorted = sorted;
+  a.ts_off = ptr<int64_t>(m.ts_off);
+  a.cell_n = ptr<int32_t>(m.n);
+  a.cell_key = ptr<uint64_t>(m.key);
+  a.mf4 = ptr<float4>(m.mf4);
+  a.mgid = ptr<int32_t>(m.mgid);
+  a.mnrm = m.has_normals ? ptr<float4>(m.mnrm) : nullptr;
+  a.has_normals = m.has_normals ? 1 : 0;
+  a.sign = sign;
+  a.d_sdf = d_sdf;
+  a.d_grad = d_grad;
+  a.d_xq = d_xq;
+  a.d_x = d_x;
+  a.abar = abar;
+  const size_t smem = sizeof(float4) * p.n_max + sizeof(float) * 4 * p.n_max;
+  KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bw_query, kTW, smem));
+  k_bw_query<<<std::max(1, occ) * c->num_sms, kTW, smem, st>>>(a, xq, p);
+  const size_t smem2 = sizeof(double) * 3 * p.n_max;
+  KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+  const unsigned grid2 = (unsigned)std::min<int64_t>(G, 4LL * c->num_sms);
+  k_bw_cell<<<std::max(1u, grid2), 256, smem2, st>>>(cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
+                                                     ptr<int64_t>(m.linv_off), ptr<double>(m.linv64),
+                                                     ptr<D4>(m.md4), ptr<float4>(m.mf4), ptr<int32_t>(m.mgid),
+                                                     abar, p, d_x);
+  KSDF_CUDA(c, cudaGetLastError());
+  return KSDF_OK;
+}
+
+}  // namespace ksdf

@@ -1,0 +1,208 @@
+// ksdf_internal.cuh -- shared definitions of the libksdf.so translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/ksdf.h"
+
+namespace ksdf {
+
+constexpr int64_t kBias = 1LL << 20;    // cell coordinates live in [-2^20, 2^20)
+constexpr int kMaxPre = 8192;           // collection-box members before the cap, per cell
+constexpr int kMaxK = 32;               // candidate list length limit
+constexpr int kMaxNmax = 512;           // training-set cap limit
+constexpr uint64_t kEmptyKey = ~0ull;   // empty hash slot
+constexpr unsigned kWaitLimit = 1u << 26;  // bounded spin on an mbarrier (~seconds)
+
+// device status word bits (ksdf_sync_status)
+enum : uint32_t { ST_NONFINITE = 1u, ST_CAPACITY = 2u, ST_TIMEOUT = 4u, ST_NOT_PD = 8u };
+
+// ------------------------------------------------------------------------------------------------
+// cell keys: three biased 21-bit fields, z most significant, so ascending key = (cz, cy, cx) order
+
+__host__ __device__ inline uint64_t pack_key(int64_t cx, int64_t cy, int64_t cz) {
+  return ((uint64_t)(cz + kBias) << 42) | ((uint64_t)(cy + kBias) << 21) | (uint64_t)(cx + kBias);
+}
+__host__ __device__ inline void unpack_key(uint64_t k, int& cx, int& cy, int& cz) {
+  cx = (int)((int64_t)(k & 0x1FFFFF) - kBias);
+  cy = (int)((int64_t)((k >> 21) & 0x1FFFFF) - kBias);
+  cz = (int)((int64_t)((k >> 42) & 0x1FFFFF) - kBias);
+}
+
+// bin of one coordinate: floor((x - o) / h) in IEEE binary64 with no contraction; false if out of range
+__device__ inline bool bin_coord(double x, double o, double h, int& c) {
+  double t = __ddiv_rn(__dsub_rn(x, o), h);
+  double f = floor(t);
+  if (!(f >= -(double)kBias && f < (double)kBias)) return false;
+  c = (int)f;
+  return true;
+}
+
+// lower corner o + c h of a cell along one axis, IEEE binary64, no contraction
+__device__ inline double cell_base(double o, int c, double h) { return __dadd_rn(o, __dmul_rn((double)c, h)); }
+
+// hash of a packed key (splitmix64 finaliser)
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// lookup in an open-addressing (linear probing) table of capacity cap (power of 2); -1 if absent
+__device__ inline int hash_find(const uint64_t* keys, const int32_t* vals, uint64_t cap, uint64_t k) {
+  uint64_t s = mix64(k) & (cap - 1);
+  for (uint64_t probe = 0; probe < cap; ++probe) {
+    uint64_t kk = keys[s];
+    if (kk == k) return vals[s];
+    if (kk == kEmptyKey) return -1;
+    s = (s + 1) & (cap - 1);
+  }
+  return -1;
+}
+
+// four doubles, 32-byte aligned (one TMA-friendly member record of the FP64 path)
+struct __align__(32) D4 {
+  double x, y, z, w;
+};
+__host__ __device__ inline D4 D4make(double x, double y, double z, double w) {
+  D4 r;
+  r.x = x;
+  r.y = y;
+  r.z = z;
+  r.w = w;
+  return r;
+}
+
+struct Params {
+  int dim;
+  double o[3];
+  double h;
+  double mu;
+  int n_max;
+  int K;
+  double lambda;
+  double alpha_s;  // softmin temperature
+  int sign_mode;
+};
+
+// ------------------------------------------------------------------------------------------------
+// device memory helper: grow-only buffer
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Model {
+  int64_t S = 0, G = 0, M = 0;    // samples, cells, training-set members
+  int64_t linv_total = 0;         // sum N (N+1) / 2
+  int max_n = 0;                  // largest training set
+  bool has_normals = false;
+  int n_not_pd = 0;
+  // per cell
+  DevBuf key, status, n, ts_off, linv_off;     // uint64, int32, int32, int64 (G+1), int64 (G+1)
+  DevBuf hkeys, hvals;                          // GP cell hash table
+  uint64_t hcap = 0;
+  DevBuf cell_order;                            // cells sorted by descending N (fit work order)
+  // per member (CSR by ts_off)
+  DevBuf mf4;      // float4 (x, y, z, alpha) cell-local, FP32
+  DevBuf md4;      // D4 (x, y, z, alpha) cell-local, FP64
+  DevBuf mvar;     // float sigma^2
+  DevBuf mnrm;     // float4 normal
+  DevBuf mgid;     // int32 global sample id
+  DevBuf mpad;     // int32 padded ids (G x n_max), assembly scratch
+  DevBuf linv64;   // double, packed lower rows
+  DevBuf linv32;   // float hi, packed lower rows
+  DevBuf linv32lo; // float lo = linv - hi
+  DevBuf x;        // sample positions (S x dim double), kept for the backward's scatter
+};
+
+}  // namespace ksdf
+
+struct ksdf_ctx {
+  ksdf::Params p;
+  ksdf_params abi;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  bool fitted = false;
+  ksdf::Model m;
+  // workspaces
+  ksdf::DevBuf status_word;       // uint32 device status
+  ksdf::DevBuf ws[24];            // general workspaces (grow only), indexed by role
+  ksdf::DevBuf stage[12];         // staging of host arrays
+  int64_t reserved_q = 0, reserved_s = 0;
+  int bb[6] = {0, 0, 0, 0, 0, 0};  // bounding box of the cells: min xyz, max xyz
+};
+
+namespace ksdf {
+
+// error helpers (host)
+ksdf_status set_err(ksdf_ctx* c, ksdf_status s, const char* fmt, ...);
+ksdf_status cuda_err(ksdf_ctx* c, cudaError_t e, const char* what);
+#define KSDF_CUDA(c, call)                                 \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ksdf::cuda_err(c, e_, #call); \
+  } while (0)
+
+cudaError_t ensure(DevBuf& b, size_t bytes);
+void release(DevBuf& b);
+template <class T> inline T* ptr(DevBuf& b) { return static_cast<T*>(b.p); }
+
+// ---- sorting and scanning (ksdf_sort.cu) ----
+// exclusive scan of n int64 values (in may equal out); total (optional) gets the sum on the device.
+cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, DevBuf& tmp, cudaStream_t st);
+// stable LSD radix sort by the low `bits` bits of 64-bit keys, with 32-bit values.  Result in keys/vals.
+cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, DevBuf& tmp, cudaStream_t st);
+
+// ---- fit (ksdf_fit.cu) ----
+ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const float* nrm, int64_t S);
+ksdf_status bin_points(ksdf_ctx* c, const double* x, int64_t n, uint64_t* keys);
+
+// ---- query (ksdf_query.cu) ----
+ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const int8_t* sign, uint32_t mask, void* sdf,
+                      void* grad, void* var_sdf, void* var_f, int32_t* winner, uint32_t* flags);
+ksdf_status candidates_for_keys(ksdf_ctx* c, const uint64_t* keys, int64_t n, int32_t* cand, int32_t* count);
+ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G);
+
+// ---- backward (ksdf_backward.cu) ----
+ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, const int32_t* winner,
+                         const float* d_sdf, const float* d_grad, float* d_xq, float* d_x);
+
+// workspace roles (indices into ksdf_ctx::ws)
+enum WsRole {
+  WS_SORT = 0,   // radix sort / scan temporaries
+  WS_SCAN = 1,
+  WS_A = 2,      // generic
+  WS_B = 3,
+  WS_C = 4,
+  WS_D = 5,
+  WS_E = 6,
+  WS_F = 7,
+  WS_QKEY = 8,   // per query
+  WS_QBIN = 9,
+  WS_QRANK = 10,
+  WS_QSORT = 11,
+  WS_QWIN = 12,
+  WS_QU = 13,
+  WS_QFLAG = 14,
+  WS_QWSORT = 15,
+  WS_BHKEY = 16,  // bin hash table
+  WS_BHVAL = 17,
+  WS_BIN = 18,    // per bin: keys, counts, offsets, candidates
+  WS_TILE = 19,
+  WS_CAND = 20,
+  WS_CELLQ = 21,  // per cell query counts / offsets
+  WS_FITSCR = 22, // FP64 fit scratch
+  WS_BW = 23      // backward accumulators
+};
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace ksdf

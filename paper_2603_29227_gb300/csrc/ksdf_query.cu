@@ -1,0 +1,1121 @@
+// ksdf_query.cu -- the batched local-GP signed-distance query of Kernel-SDF (arXiv 2603.29227, Sec. IV-B).
+//
+// Pipeline (all stream ordered, no host synchronisation; device-side counts drive persistent kernels):
+//   Q1  bin every query (binary64, same rounding as the fit) and insert its cell key in a hash table;
+//   Q2  number the distinct query bins, count and group the queries by bin, cut bins into tiles;
+//   Q3  candidate lists: per bin, the K valid GP cells nearest on the integer lattice (ring search over
+//       Chebyshev shells, exact (distance, key) order; brute force beyond 16 shells);
+//   Q4  phase A (per tile of one bin): the candidates' samples are staged to shared memory with TMA bulk
+//       copies; one thread per query evaluates every candidate GP
+//          f'_g = sum_i alpha_i exp(-lambda (r_i^2 - d_g^2)),   u_g = sqrt(-log f'_g / lambda + d_g^2)
+//       (App. D scaling; d_g^2 = min_i r_i^2 is tracked online, the sum is rescaled when the minimum
+//       drops, and accumulated with Kahan compensation) and keeps u = min_g u_g (min-fusion, Sec. IV-B.1);
+//   Q5  group the queries by winning cell;
+//   Q6  phase B (per tile of one winner): gradient grad u = -grad f'/|grad f'|, softmin variance
+//       (Sec. IV-B.3) and the GP variance V[f] = 1 - e^{-2 lambda d^2} |L^{-1} k'|^2 (Sec. IV-B.1).
+// The plain path runs Q4 and Q6 in binary64 with two-pass minima.
+#include "ksdf_internal.cuh"
+
+#include <algorithm>
+
+namespace ksdf {
+
+namespace {
+
+constexpr int kTA = 128;   // phase A threads (one query each)
+constexpr int kTB = 64;    // phase B threads, mixed path
+constexpr int kTB64 = 32;  // phase B threads, FP64 path
+constexpr int kRingMax = 16;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// ---------------------------------------------------------------------------------------------
+// small PTX helpers: mbarrier + 1D bulk copy global -> shared (TMA)
+
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; returns false (for every thread of the CTA) if any thread gave up
+__device__ inline bool mbar_wait_all(uint64_t* bar, uint32_t parity) {
+  bool done = false;
+  for (unsigned it = 0; it < (kWaitLimit >> 4); ++it)
+    if (mbar_try_wait(bar, parity)) {
+      done = true;
+      break;
+    }
+  return !__syncthreads_or(!done);
+}
+
+__device__ inline float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Q1/Q2: binning and grouping
+
+template <class T>
+__global__ void k_q_bin(const T* xq, int64_t Q, Params p, uint64_t* qkey, uint64_t* bhk, uint64_t bcap, uint32_t* st) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  int c[3] = {0, 0, 0};
+  bool ok = true;
+  for (int j = 0; j < p.dim; ++j) ok &= bin_coord((double)xq[q * p.dim + j], p.o[j], p.h, c[j]);
+  if (!ok) {
+    atomicOr(st, ST_NONFINITE);
+    qkey[q] = kEmptyKey;
+    return;
+  }
+  uint64_t k = pack_key(c[0], c[1], c[2]);
+  qkey[q] = k;
+  uint64_t s = mix64(k) & (bcap - 1);
+  for (uint64_t probe = 0; probe < bcap; ++probe) {
+    uint64_t cur = bhk[s];
+    if (cur == k) return;
+    if (cur == kEmptyKey) {
+      unsigned long long prev =
+          atomicCAS((unsigned long long*)&bhk[s], (unsigned long long)kEmptyKey, (unsigned long long)k);
+      if (prev == kEmptyKey || prev == k) return;
+    }
+    s = (s + 1) & (bcap - 1);
+  }
+  atomicOr(st, ST_CAPACITY);
+}
+
+__global__ void k_slot_flags(const uint64_t* bhk, uint64_t bcap, int64_t* flag) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < (int64_t)bcap) flag[s] = bhk[s] != kEmptyKey ? 1 : 0;
+}
+
+__global__ void k_bin_table(const uint64_t* bhk, uint64_t bcap, const int64_t* slot_id, uint64_t* bin_key) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < (int64_t)bcap && bhk[s] != kEmptyKey) bin_key[slot_id[s]] = bhk[s];
+}
+
+__global__ void k_q_rank(const uint64_t* qkey, int64_t Q, const uint64_t* bhk, const int64_t* slot_id, uint64_t bcap,
+                         int32_t* qbin, int32_t* qrank, int64_t* bin_cnt) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  uint64_t k = qkey[q];
+  if (k == kEmptyKey) {
+    qbin[q] = -1;
+    return;
+  }
+  uint64_t s = mix64(k) & (bcap - 1);
+  for (uint64_t probe = 0; probe < bcap; ++probe) {
+    if (bhk[s] == k) break;
+    s = (s + 1) & (bcap - 1);
+  }
+  int b = (int)slot_id[s];
+  qbin[q] = b;
+  qrank[q] = (int32_t)atomicAdd((unsigned long long*)&bin_cnt[b], 1ull);
+}
+
+__global__ void k_ntiles(const int64_t* cnt, int64_t n, int T, int64_t* ntiles) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ntiles[i] = (cnt[i] + T - 1) / T;
+}
+
+__global__ void k_scatter_grouped(const int32_t* grp, const int32_t* rank, int64_t Q, const int64_t* off,
+                                  int32_t* sorted) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  int g = grp[q];
+  if (g >= 0) sorted[off[g] + rank[q]] = (int32_t)q;
+}
+
+// tiles: for group i with cnt items starting at off[i]: tiles at tile_off[i] ...
+__global__ void k_make_tiles(const int64_t* cnt, const int64_t* off, const int64_t* tile_off, int64_t ngroups, int T,
+                             int4* tiles) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ngroups) return;
+  int64_t c = cnt[i];
+  for (int64_t t = 0; t * T < c; ++t)
+    tiles[tile_off[i] + t] = make_int4((int)i, (int)(off[i] + t * T), (int)(c - t * T < T ? c - t * T : T), 0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Q3: candidate lists (warp per bin)
+
+struct CandCtx {
+  const uint64_t* hk;
+  const int32_t* hv;
+  uint64_t hcap;
+  const int32_t* status;
+  const uint64_t* cell_key;
+  int64_t G;
+  int bb_lo[3], bb_hi[3];  // bounding box of all cells
+  int K, dim;
+};
+
+// insert (D, key, g) into a sorted top-K list (lane 0 only)
+__device__ inline void topk_insert(long long* D, uint64_t* Kk, int* Gg, int& n, int K, long long d, uint64_t key,
+                                   int g) {
+  int pos = n;
+  while (pos > 0 && (d < D[pos - 1] || (d == D[pos - 1] && key < Kk[pos - 1]))) --pos;
+  if (pos >= K) return;
+  int last = n < K ? n : K - 1;
+  for (int t = last; t > pos; --t) {
+    D[t] = D[t - 1];
+    Kk[t] = Kk[t - 1];
+    Gg[t] = Gg[t - 1];
+  }
+  D[pos] = d;
+  Kk[pos] = key;
+  Gg[pos] = g;
+  if (n < K) ++n;
+}
+
+constexpr int kCandWarps = 8;
+
+__global__ void __launch_bounds__(32 * kCandWarps)
+    k_candidates(const uint64_t* bin_key, const int64_t* n_bins_dev, int64_t n_bins_host, CandCtx cc, int32_t* cand,
+                 int32_t* ncand) {
+  __shared__ long long sD[kCandWarps][kMaxK];
+  __shared__ uint64_t sK[kCandWarps][kMaxK];
+  __shared__ int sG[kCandWarps][kMaxK];
+  __shared__ long long eD[kCandWarps][32];
+  __shared__ uint64_t eK[kCandWarps][32];
+  __shared__ int eG[kCandWarps][32];
+  __shared__ int sN[kCandWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t nb = n_bins_dev ? *n_bins_dev : n_bins_host;
+  const int K = cc.K;
+  for (int64_t b = (int64_t)blockIdx.x * kCandWarps + w; b < nb; b += (int64_t)gridDim.x * kCandWarps) {
+    int bx, by, bz;
+    unpack_key(bin_key[b], bx, by, bz);
+    const int bc[3] = {bx, by, bz};
+    if (lane == 0) sN[w] = 0;
+    __syncwarp();
+    int rstop = 0;  // Chebyshev radius beyond which no cell exists
+    for (int j = 0; j < 3; ++j) rstop = max(rstop, max(abs(bc[j] - cc.bb_lo[j]), abs(bc[j] - cc.bb_hi[j])));
+    bool done = false;
+    int R = 0;
+    for (; R <= min(rstop, kRingMax) && !done; ++R) {
+      const int side = 2 * R + 1;
+      const int64_t total = cc.dim == 3 ? (int64_t)side * side * side : (int64_t)side * side;
+      for (int64_t t0 = 0; t0 < total; t0 += 32) {
+        int64_t t = t0 + lane;
+        bool found = false;
+        long long d = 0;
+        uint64_t key = 0;
+        int g = -1;
+        if (t < total) {
+          int dx = (int)(t % side) - R;
+          int64_t r = t / side;
+          int dy = (int)(r % side) - R;
+          int dz = cc.dim == 3 ? (int)(r / side) - R : 0;
+          if (max(abs(dx), max(abs(dy), abs(dz))) == R) {
+            int64_t nx = (int64_t)bx + dx, ny = (int64_t)by + dy, nz = (int64_t)bz + dz;
+            if (nx >= -kBias && nx < kBias && ny >= -kBias && ny < kBias && nz >= -kBias && nz < kBias) {
+              key = pack_key(nx, ny, nz);
+              g = hash_find(cc.hk, cc.hv, cc.hcap, key);
+              if (g >= 0 && cc.status[g] == KSDF_CELL_OK) {
+                found = true;
+                d = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+              }
+            }
+          }
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, found);
+        if (found) {
+          eD[w][lane] = d;
+          eK[w][lane] = key;
+          eG[w][lane] = g;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          int n = sN[w];
+          while (mask) {
+            int l = __ffs(mask) - 1;
+            mask &= mask - 1;
+            topk_insert(sD[w], sK[w], sG[w], n, K, eD[w][l], eK[w][l], eG[w][l]);
+          }
+          sN[w] = n;
+        }
+        __syncwarp();
+      }
+      // every unseen cell has D >= (R+1)^2
+      if (sN[w] >= K && sD[w][K - 1] < (long long)(R + 1) * (R + 1)) done = true;
+    }
+    if (!done && rstop > kRingMax) {
+      // brute force over all cells (rare: bins far from every cell)
+      if (lane == 0) sN[w] = 0;
+      __syncwarp();
+      for (int64_t g0 = 0; g0 < cc.G; g0 += 32) {
+        int64_t g = g0 + lane;
+        bool found = false;
+        long long d = 0;
+        uint64_t key = 0;
+        if (g < cc.G && cc.status[g] == KSDF_CELL_OK) {
+          key = cc.cell_key[g];
+          int cx, cy, cz;
+          unpack_key(key, cx, cy, cz);
+          d = (long long)(cx - bx) * (cx - bx) + (long long)(cy - by) * (cy - by) + (long long)(cz - bz) * (cz - bz);
+          int n = sN[w];
+          found = n < K || d < sD[w][K - 1] || (d == sD[w][K - 1] && key < sK[w][K - 1]);
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, found);
+        if (found) {
+          eD[w][lane] = d;
+          eK[w][lane] = key;
+          eG[w][lane] = (int)g;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          int n = sN[w];
+          while (mask) {
+            int l = __ffs(mask) - 1;
+            mask &= mask - 1;
+            topk_insert(sD[w], sK[w], sG[w], n, K, eD[w][l], eK[w][l], eG[w][l]);
+          }
+          sN[w] = n;
+        }
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    const int n = sN[w];
+    if (lane < K) cand[b * K + lane] = lane < n ? sG[w][lane] : -1;
+    if (lane == 0) ncand[b] = n;
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Q4: phase A, mixed precision
+
+struct PhaseAArgs {
+  const int4* tiles;           // (bin, start, count)
+  const int64_t* n_tiles;      // device count
+  int* counter;
+  const int32_t* sorted_q;
+  const uint64_t* bin_key;
+  const int32_t* cand;
+  const int32_t* ncand;
+  const int64_t* ts_off;
+  const int32_t* cell_n;
+  const uint64_t* cell_key;
+  const float4* mf4;
+  const D4* md4;
+  int32_t* qwin;
+  float* qu;
+  double* qu64;
+  uint32_t* qflag;
+  uint32_t* st;
+};
+
+__global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, Params p) {
+  extern __shared__ __align__(128) float4 s_x[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_tile, s_nc, s_c[kMaxK], s_n[kMaxK], s_base[kMaxK];
+  __shared__ float s_off[kMaxK][3];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  const float c1 = (float)p.lambda * kLog2e;
+  const float inv_lam = (float)(1.0 / p.lambda);
+  uint32_t phase = 0;
+  const int64_t ntiles = *a.n_tiles;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const int4 tile = a.tiles[t];
+    const int b = tile.x;
+    int bc[3];
+    unpack_key(a.bin_key[b], bc[0], bc[1], bc[2]);
+    if (tid == 0) {
+      const int nc = a.ncand[b];
+      s_nc = nc;
+      uint32_t bytes = 0;
+      int base = 0;
+      for (int k = 0; k < nc; ++k) {
+        const int g = a.cand[(int64_t)b * p.K + k];
+        const int n = a.cell_n[g];
+        s_c[k] = g;
+        s_n[k] = n;
+        s_base[k] = base;
+        int cc[3];
+        unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
+        for (int j = 0; j < 3; ++j) s_off[k][j] = (float)((double)(bc[j] - cc[j]) * p.h);
+        base += n;
+        bytes += (uint32_t)n * 16u;
+      }
+      fence_proxy_async();
+      mbar_expect_tx(&bar, bytes);
+      for (int k = 0; k < nc; ++k)
+        bulk_g2s(s_x + s_base[k], a.mf4 + a.ts_off[s_c[k]], (uint32_t)s_n[k] * 16u, &bar);
+    }
+    // the query in the bin's frame: fl32(x - (o + b h)), binary64 subtraction
+    const bool live = tid < tile.z;
+    int q = 0;
+    float ql[3] = {0.f, 0.f, 0.f};
+    if (live) {
+      q = a.sorted_q[tile.y + tid];
+      for (int j = 0; j < p.dim; ++j)
+        ql[j] = (float)__dsub_rn((double)xq[(int64_t)q * p.dim + j], cell_base(p.o[j], bc[j], p.h));
+    }
+    if (!mbar_wait_all(&bar, phase)) {
+      if (tid == 0) atomicOr(a.st, ST_TIMEOUT);
+      return;
+    }
+    phase ^= 1;
+    const int nc = s_nc;
+    float bu = INFINITY, su = INFINITY;
+    int bk = -1;
+    uint32_t bflag = 0;
+    if (live) {
+      for (int k = 0; k < nc; ++k) {
+        const float qx = ql[0] + s_off[k][0], qy = ql[1] + s_off[k][1], qz = ql[2] + s_off[k][2];
+        const float4* xs = s_x + s_base[k];
+        const int n = s_n[k];
+        float m = INFINITY, s = 0.f, comp = 0.f;
+        for (int i0 = 0; i0 < n; i0 += 8) {
+          float r2[8], al[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (i0 + j < n) {
+              const float4 v = xs[i0 + j];
+              const float dx = qx - v.x, dy = qy - v.y, dz = qz - v.z;
+              r2[j] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              al[j] = v.w;
+            } else {
+              r2[j] = INFINITY;
+              al[j] = 0.f;
+            }
+          }
+          float cm = fminf(fminf(fminf(r2[0], r2[1]), fminf(r2[2], r2[3])), fminf(fminf(r2[4], r2[5]), fminf(r2[6], r2[7])));
+          const float mn = fminf(m, cm);
+          const float sc = ex2(c1 * (mn - m));
+          s *= sc;
+          comp *= sc;
+          const float cmn = c1 * mn;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float tj = al[j] * ex2(fmaf(-c1, r2[j], cmn));
+            const float y = tj - comp;
+            const float tt = s + y;
+            comp = (tt - s) - y;
+            s = tt;
+          }
+          m = mn;
+        }
+        const float f = s - comp;
+        float u;
+        uint32_t fl = 0;
+        if (f > 0.f) {
+          float u2 = fmaf(-logf(f), inv_lam, m);
+          if (u2 < 0.f) {
+            u2 = 0.f;
+            fl |= KSDF_FLAG_CLAMPED;
+          }
+          u = sqrtf(u2);
+        } else {
+          u = sqrtf(m);
+          fl |= KSDF_FLAG_FALLBACK;
+        }
+        if (u < bu) {
+          su = bu;
+          bu = u;
+          bk = k;
+          bflag = fl;
+        } else if (u < su) {
+          su = u;
+        }
+      }
+      uint32_t fl = bflag;
+      if (nc >= 2 && su - bu <= 1e-5f) fl |= KSDF_FLAG_NEAR_TIE;
+      if (nc == 0) fl |= KSDF_FLAG_NO_GP;
+      a.qwin[q] = bk >= 0 ? s_c[bk] : -1;
+      a.qu[q] = bu;
+      a.qflag[q] = fl;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Q4 (plain path): phase A in binary64, two passes per candidate
+
+__global__ void __launch_bounds__(kTA) k_phaseA64(PhaseAArgs a, const double* xq, Params p) {
+  extern __shared__ __align__(128) D4 s_d[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_tile, s_nc, s_c[kMaxK], s_n[kMaxK], s_base[kMaxK];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  const int64_t ntiles = *a.n_tiles;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const int4 tile = a.tiles[t];
+    const int b = tile.x;
+    if (tid == 0) {
+      const int nc = a.ncand[b];
+      s_nc = nc;
+      uint32_t bytes = 0;
+      int base = 0;
+      for (int k = 0; k < nc; ++k) {
+        const int g = a.cand[(int64_t)b * p.K + k];
+        s_c[k] = g;
+        s_n[k] = a.cell_n[g];
+        s_base[k] = base;
+        base += s_n[k];
+        bytes += (uint32_t)s_n[k] * 32u;
+      }
+      fence_proxy_async();
+      mbar_expect_tx(&bar, bytes);
+      for (int k = 0; k < nc; ++k)
+        bulk_g2s(s_d + s_base[k], a.md4 + a.ts_off[s_c[k]], (uint32_t)s_n[k] * 32u, &bar);
+    }
+    const bool live = tid < tile.z;
+    const int q = live ? a.sorted_q[tile.y + tid] : 0;
+    double xg[3] = {0, 0, 0};
+    if (live)
+      for (int j = 0; j < p.dim; ++j) xg[j] = xq[(int64_t)q * p.dim + j];
+    if (!mbar_wait_all(&bar, phase)) {
+      if (tid == 0) atomicOr(a.st, ST_TIMEOUT);
+      return;
+    }
+    phase ^= 1;
+    const int nc = s_nc;
+    if (live) {
+      double bu = INFINITY, su = INFINITY;
+      int bk = -1;
+      uint32_t bflag = 0;
+      for (int k = 0; k < nc; ++k) {
+        int cc[3];
+        unpack_key(a.cell_key[s_c[k]], cc[0], cc[1], cc[2]);
+        double ql[3];
+        for (int j = 0; j < 3; ++j) ql[j] = j < p.dim ? __dsub_rn(xg[j], cell_base(p.o[j], cc[j], p.h)) : 0.0;
+        const D4* xs = s_d + s_base[k];
+        const int n = s_n[k];
+        double m = INFINITY;
+        for (int i = 0; i < n; ++i) {
+          const D4 v = xs[i];
+          const double dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+          m = fmin(m, dx * dx + dy * dy + dz * dz);
+        }
+        double f = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const D4 v = xs[i];
+          const double dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+          f += v.w * exp(-p.lambda * ((dx * dx + dy * dy + dz * dz) - m));
+        }
+        double u;
+        uint32_t fl = 0;
+        if (f > 0.0) {
+          double u2 = -log(f) / p.lambda + m;
+          if (u2 < 0.0) {
+            u2 = 0.0;
+            fl |= KSDF_FLAG_CLAMPED;
+          }
+          u = sqrt(u2);
+        } else {
+          u = sqrt(m);
+          fl |= KSDF_FLAG_FALLBACK;
+        }
+        if (u < bu) {
+          su = bu;
+          bu = u;
+          bk = k;
+          bflag = fl;
+        } else if (u < su) {
+          su = u;
+        }
+      }
+      uint32_t fl = bflag;
+      if (nc >= 2 && su - bu <= 1e-5) fl |= KSDF_FLAG_NEAR_TIE;
+      if (nc == 0) fl |= KSDF_FLAG_NO_GP;
+      a.qwin[q] = bk >= 0 ? s_c[bk] : -1;
+      a.qu64[q] = bu;
+      a.qflag[q] = fl;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Q5: grouping by winner; queries without a winner get their final outputs here
+
+template <class T>
+__global__ void k_w_rank(const int32_t* qwin, const uint32_t* qflag, const int32_t* qbin, int64_t Q, int32_t* wrank,
+                         int64_t* wcnt, uint32_t mask, int dim, T* sdf, T* grad, T* var_sdf, T* var_f,
+                         int32_t* winner, uint32_t* flags) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const int w = qbin[q] < 0 ? -1 : qwin[q];
+  if (w >= 0) {
+    wrank[q] = (int32_t)atomicAdd((unsigned long long*)&wcnt[w], 1ull);
+    return;
+  }
+  const bool invalid = qbin[q] < 0;
+  const T nan = (T)NAN;
+  if (mask & KSDF_OUT_SDF) sdf[q] = invalid ? nan : (T)INFINITY;
+  if (mask & KSDF_OUT_GRAD)
+    for (int j = 0; j < dim; ++j) grad[q * dim + j] = invalid ? nan : (T)0;
+  if (mask & KSDF_OUT_VAR_SDF) var_sdf[q] = invalid ? nan : (T)0;
+  if (mask & KSDF_OUT_VAR_F) var_f[q] = invalid ? nan : (T)1;
+  if (mask & KSDF_OUT_WINNER) winner[q] = -1;
+  if (mask & KSDF_OUT_FLAGS) flags[q] = invalid ? KSDF_FLAG_INVALID : (qflag[q] | KSDF_FLAG_NO_GP);
+}
+
+__global__ void k_w_scatter(const int32_t* qwin, const int32_t* qbin, const int32_t* wrank, int64_t Q,
+                            const int64_t* woff, int32_t* sorted) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  if (qbin[q] < 0) return;
+  int w = qwin[q];
+  if (w >= 0) sorted[woff[w] + wrank[q]] = (int32_t)q;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Q6: phase B, mixed precision (tile of queries sharing the winner cell)
+
+struct PhaseBArgs {
+  const int4* tiles;
+  const int64_t* n_tiles;
+  int* counter;
+  const int32_t* sorted_w;
+  const int64_t* ts_off;
+  const int32_t* cell_n;
+  const uint64_t* cell_key;
+  const int64_t* linv_off;
+  const float4* mf4;
+  const D4* md4;
+  const float* mvar;
+  const float4* mnrm;
+  const float* linv32;
+  const float* linv32lo;
+  const double* linv64;
+  const float* qu;
+  const double* qu64;
+  const uint32_t* qflag;
+  const int8_t* sign;
+  int has_normals;
+  uint32_t mask;
+  uint32_t* st;
+};
+
+__global__ void __launch_bounds__(kTB) k_phaseB(PhaseBArgs a, const float* xq, Params p, float* sdf, float* grad,
+                                                float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags) {
+  extern __shared__ __align__(128) float4 s_x[];  // [n_max] samples, then [n_max] var, then [n_max][kTB] k'
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_tile;
+  const int tid = threadIdx.x;
+  float* s_var = reinterpret_cast<float*>(s_x + p.n_max);
+  float* s_k = s_var + p.n_max;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  const float c1 = (float)p.lambda * kLog2e;
+  const float as = (float)p.alpha_s;
+  const float c2 = as * kLog2e;
+  uint32_t phase = 0;
+  const int64_t ntiles = *a.n_tiles;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const int4 tile = a.tiles[t];
+    const int g = tile.x;
+    const int n = a.cell_n[g];
+    const int64_t m0 = a.ts_off[g];
+    if (tid == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&bar, (uint32_t)n * 16u);
+      bulk_g2s(s_x, a.mf4 + m0, (uint32_t)n * 16u, &bar);
+    }
+    for (int i = tid; i < n; i += blockDim.x) s_var[i] = a.mvar[m0 + i];  // not 16-byte aligned: plain loads
+    int cc[3];
+    unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
+    const bool live = tid < tile.z;
+    const int q = live ? a.sorted_w[tile.y + tid] : 0;
+    float ql[3] = {0.f, 0.f, 0.f};
+    if (live)
+      for (int j = 0; j < p.dim; ++j)
+        ql[j] = (float)__dsub_rn((double)xq[(int64_t)q * p.dim + j], cell_base(p.o[j], cc[j], p.h));
+    if (!mbar_wait_all(&bar, phase)) {
+      if (tid == 0) atomicOr(a.st, ST_TIMEOUT);
+      return;
+    }
+    phase ^= 1;
+    if (live) {
+      // pass 1: nearest sample (first minimum: training sets are in ascending global id)
+      float m = INFINITY;
+      int nn = 0;
+      for (int i = 0; i < n; ++i) {
+        const float4 v = s_x[i];
+        const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (r2 < m) {
+          m = r2;
+          nn = i;
+        }
+      }
+      const float zmin = sqrtf(m);
+      // pass 2: k'_i, grad f', softmin accumulators
+      float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
+      const float cmn = c1 * m;
+      for (int i = 0; i < n; ++i) {
+        const float4 v = s_x[i];
+        const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float kp = ex2(fmaf(-c1, r2, cmn));
+        s_k[i * kTB + tid] = kp;
+        const float ak = v.w * kp;
+        G0 = fmaf(ak, dx, G0);
+        G1 = fmaf(ak, dy, G1);
+        G2 = fmaf(ak, dz, G2);
+        const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+        const float y = fmaxf(z - zmin, 0.f);
+        const float w = ex2(-c2 * y);
+        W += w;
+        HY = fmaf(w, y, HY);
+        const float tw = w * w * s_var[i];
+        T0 += tw;
+        T1 = fmaf(tw, y, T1);
+        T2 = fmaf(tw * y, y, T2);
+      }
+      float vs = 0.f;
+      {
+        const float hy = HY / W;
+        const float B = fmaf(as, hy, 1.f);
+        vs = (B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W);
+        vs = fmaxf(vs, 0.f);
+      }
+      // GP variance: V = L^{-1} k' (rows of the packed lower triangle), FP32 hi + lo
+      float vf = 1.f;
+      if (a.mask & KSDF_OUT_VAR_F) {
+        const float* Lh = a.linv32 + a.linv_off[g];
+        const float* Ll = a.linv32lo + a.linv_off[g];
+        float acc = 0.f;
+        for (int j = 0; j < n; ++j) {
+          const float* rh = Lh + (int64_t)j * (j + 1) / 2;
+          const float* rl = Ll + (int64_t)j * (j + 1) / 2;
+          float v = 0.f, vl = 0.f;
+          for (int i = 0; i <= j; ++i) {
+            const float kk = s_k[i * kTB + tid];
+            v = fmaf(__ldg(rh + i), kk, v);
+            vl = fmaf(__ldg(rl + i), kk, vl);
+          }
+          v += vl;
+          acc = fmaf(v, v, acc);
+        }
+        vf = fmaxf(1.f - ex2(-2.f * c1 * m) * acc, 0.f);
+      }
+      // sign
+      float s = 1.f;
+      if (a.sign) {
+        s = a.sign[q] < 0 ? -1.f : 1.f;
+      } else if (p.sign_mode == 1 && a.has_normals) {
+        const float4 v = s_x[nn];
+        const float4 nv = a.mnrm[m0 + nn];
+        const float dot = nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z);
+        s = dot >= 0.f ? 1.f : -1.f;
+      }
+      uint32_t fl = a.qflag[q];
+      const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
+      if (a.mask & KSDF_OUT_SDF) sdf[q] = s * a.qu[q];
+      if (a.mask & KSDF_OUT_GRAD) {
+        float gv[3] = {G0, G1, G2};
+        if (gn > 0.f) {
+          const float ig = s / gn;
+          for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gv[j] * ig;
+        } else {
+          for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = 0.f;
+        }
+      }
+      if (!(gn > 0.f)) fl |= KSDF_FLAG_ZERO_GRAD;
+      if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
+      if (a.mask & KSDF_OUT_VAR_F) var_f[q] = vf;
+      if (a.mask & KSDF_OUT_WINNER) winner[q] = g;
+      if (a.mask & KSDF_OUT_FLAGS) flags[q] = fl;
+    }
+    __syncthreads();
+  }
+}
+
+// Q6 (plain path): binary64 throughout
+__global__ void __launch_bounds__(kTB64) k_phaseB64(PhaseBArgs a, const double* xq, Params p, double* sdf,
+                                                    double* grad, double* var_sdf, double* var_f, int32_t* winner,
+                                                    uint32_t* flags) {
+  extern __shared__ __align__(128) D4 s_d[];  // [n_max] samples, [n_max] var (double), [n_max][kTB64] k'
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_tile;
+  const int tid = threadIdx.x;
+  double* s_var = reinterpret_cast<double*>(s_d + p.n_max);
+  double* s_k = s_var + p.n_max;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  const double lam = p.lambda, as = p.alpha_s;
+  uint32_t phase = 0;
+  const int64_t ntiles = *a.n_tiles;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const int4 tile = a.tiles[t];
+    const int g = tile.x;
+    const int n = a.cell_n[g];
+    const int64_t m0 = a.ts_off[g];
+    if (tid == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&bar, (uint32_t)n * 32u);
+      bulk_g2s(s_d, a.md4 + m0, (uint32_t)n * 32u, &bar);
+    }
+    for (int i = tid; i < n; i += blockDim.x) s_var[i] = (double)a.mvar[m0 + i];
+    int cc[3];
+    unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
+    const bool live = tid < tile.z;
+    const int q = live ? a.sorted_w[tile.y + tid] : 0;
+    double ql[3] = {0, 0, 0};
+    if (live)
+      for (int j = 0; j < p.dim; ++j) ql[j] = __dsub_rn(xq[(int64_t)q * p.dim + j], cell_base(p.o[j], cc[j], p.h));
+    if (!mbar_wait_all(&bar, phase)) {
+      if (tid == 0) atomicOr(a.st, ST_TIMEOUT);
+      return;
+    }
+    phase ^= 1;
+    if (live) {
+      double m = INFINITY;
+      int nn = 0;
+      for (int i = 0; i < n; ++i) {
+        const D4 v = s_d[i];
+        const double dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < m) {
+          m = r2;
+          nn = i;
+        }
+      }
+      const double zmin = sqrt(m);
+      double G0 = 0, G1 = 0, G2 = 0, W = 0, HZ = 0;
+      for (int i = 0; i < n; ++i) {
+        const D4 v = s_d[i];
+        const double dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        const double kp = exp(-lam * (r2 - m));
+        s_k[i * kTB64 + tid] = kp;
+        const double ak = v.w * kp;
+        G0 += ak * dx;
+        G1 += ak * dy;
+        G2 += ak * dz;
+        const double z = sqrt(r2);
+        const double w = exp(-as * (z - zmin));
+        W += w;
+        HZ += w * z;
+      }
+      const double h = HZ / W;
+      double vs = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const D4 v = s_d[i];
+        const double dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+        const double z = sqrt(dx * dx + dy * dy + dz * dz);
+        const double si = exp(-as * (z - zmin)) / W;
+        const double tt = as * (h - z) + 1.0;
+        vs += si * si * tt * tt * s_var[i];
+      }
+      double vf = 1.0;
+      if (a.mask & KSDF_OUT_VAR_F) {
+        const double* L = a.linv64 + a.linv_off[g];
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) {
+          const double* r = L + (int64_t)j * (j + 1) / 2;
+          double v = 0.0;
+          for (int i = 0; i <= j; ++i) v = fma(r[i], s_k[i * kTB64 + tid], v);
+          acc = fma(v, v, acc);
+        }
+        vf = fmax(1.0 - exp(-2.0 * lam * m) * acc, 0.0);
+      }
+      double s = 1.0;
+      if (a.sign) {
+        s = a.sign[q] < 0 ? -1.0 : 1.0;
+      } else if (p.sign_mode == 1 && a.has_normals) {
+        const D4 v = s_d[nn];
+        const float4 nv = a.mnrm[m0 + nn];
+        const double dot = nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z);
+        s = dot >= 0.0 ? 1.0 : -1.0;
+      }
+      uint32_t fl = a.qflag[q];
+      const double gn = sqrt(G0 * G0 + G1 * G1 + G2 * G2);
+      if (a.mask & KSDF_OUT_SDF) sdf[q] = s * a.qu64[q];
+      if (a.mask & KSDF_OUT_GRAD) {
+        const double gv[3] = {G0, G1, G2};
+        for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gn > 0.0 ? s * gv[j] / gn : 0.0;
+      }
+      if (!(gn > 0.0)) fl |= KSDF_FLAG_ZERO_GRAD;
+      if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
+      if (a.mask & KSDF_OUT_VAR_F) var_f[q] = vf;
+      if (a.mask & KSDF_OUT_WINNER) winner[q] = g;
+      if (a.mask & KSDF_OUT_FLAGS) flags[q] = fl;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// host orchestration
+
+static CandCtx cand_ctx(ksdf_ctx* c) {
+  CandCtx cc;
+  Model& m = c->m;
+  cc.hk = ptr<uint64_t>(m.hkeys);
+  cc.hv = ptr<int32_t>(m.hvals);
+  cc.hcap = m.hcap;
+  cc.status = ptr<int32_t>(m.status);
+  cc.cell_key = ptr<uint64_t>(m.key);
+  cc.G = m.G;
+  for (int j = 0; j < 3; ++j) {
+    cc.bb_lo[j] = c->bb[j];
+    cc.bb_hi[j] = c->bb[3 + j];
+  }
+  cc.K = c->p.K;
+  cc.dim = c->p.dim;
+  return cc;
+}
+
+ksdf_status candidates_for_keys(ksdf_ctx* c, const uint64_t* keys, int64_t n, int32_t* cand, int32_t* count) {
+  if (n <= 0) return KSDF_OK;
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, kCandWarps), 8LL * c->num_sms);
+  k_candidates<<<grid, 32 * kCandWarps, 0, c->stream>>>(keys, nullptr, n, cand_ctx(c), cand, count);
+  KSDF_CUDA(c, cudaGetLastError());
+  return KSDF_OK;
+}
+
+static uint64_t bin_capacity(int64_t Q) {
+  uint64_t bcap = 1024;
+  while (bcap < 2 * (uint64_t)Q && bcap < (1ull << 25)) bcap <<= 1;
+  return bcap;
+}
+
+ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G) {
+  const uint64_t bcap = bin_capacity(Q);
+  const int K = c->p.K;
+  KSDF_CUDA(c, ensure(c->ws[WS_QKEY], sizeof(uint64_t) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_QBIN], sizeof(int32_t) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_QRANK], sizeof(int32_t) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_QSORT], sizeof(int32_t) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_QWIN], sizeof(int32_t) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_QU], sizeof(double) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_QFLAG], sizeof(uint32_t) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_QWSORT], sizeof(int32_t) * Q));
+  KSDF_CUDA(c, ensure(c->ws[WS_BHKEY], sizeof(uint64_t) * bcap));
+  // per-slot / per-bin arrays: slot ids, bin keys, counts, offsets, tile counts, tile offsets (+ totals)
+  KSDF_CUDA(c, ensure(c->ws[WS_BHVAL], sizeof(int64_t) * (bcap + 1)));
+  KSDF_CUDA(c, ensure(c->ws[WS_BIN], sizeof(int64_t) * (5 * bcap + 8)));
+  KSDF_CUDA(c, ensure(c->ws[WS_CAND], sizeof(int32_t) * (bcap * (K + 1))));
+  const int64_t max_tiles_a = Q / kTA + bcap + 1;
+  const int64_t max_tiles_b = Q / kTB64 + G + 1;
+  KSDF_CUDA(c, ensure(c->ws[WS_TILE], sizeof(int4) * (max_tiles_a + max_tiles_b)));
+  KSDF_CUDA(c, ensure(c->ws[WS_CELLQ], sizeof(int64_t) * (4 * G + 8)));
+  const int64_t nsc = (int64_t)bcap / 2048 + 2;
+  KSDF_CUDA(c, ensure(c->ws[WS_SCAN], sizeof(int64_t) * nsc));
+  return KSDF_OK;
+}
+
+ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const int8_t* sign, uint32_t mask, void* sdf,
+                      void* grad, void* var_sdf, void* var_f, int32_t* winner, uint32_t* flags) {
+  cudaStream_t st = c->stream;
+  const Params& p = c->p;
+  Model& m = c->m;
+  uint32_t* stw = ptr<uint32_t>(c->status_word);
+  const uint64_t bcap = bin_capacity(Q);
+  const int64_t G = m.G;
+  {
+    ksdf_status rs = query_reserve(c, Q, G);
+    if (rs) return rs;
+  }
+  const int64_t max_tiles_a = Q / kTA + bcap + 1;
+  const int TBq = f64 ? kTB64 : kTB;
+  uint64_t* qkey = ptr<uint64_t>(c->ws[WS_QKEY]);
+  int32_t* qbin = ptr<int32_t>(c->ws[WS_QBIN]);
+  int32_t* qrank = ptr<int32_t>(c->ws[WS_QRANK]);
+  int32_t* qsort = ptr<int32_t>(c->ws[WS_QSORT]);
+  int32_t* qwin = ptr<int32_t>(c->ws[WS_QWIN]);
+  float* qu = ptr<float>(c->ws[WS_QU]);
+  double* qu64 = ptr<double>(c->ws[WS_QU]);
+  uint32_t* qflag = ptr<uint32_t>(c->ws[WS_QFLAG]);
+  int32_t* qwsort = ptr<int32_t>(c->ws[WS_QWSORT]);
+  uint64_t* bhk = ptr<uint64_t>(c->ws[WS_BHKEY]);
+  int64_t* slot_id = ptr<int64_t>(c->ws[WS_BHVAL]);
+  int64_t* binbuf = ptr<int64_t>(c->ws[WS_BIN]);
+  uint64_t* bin_key = reinterpret_cast<uint64_t*>(binbuf);
+  int64_t* bin_cnt = binbuf + bcap;
+  int64_t* bin_off = binbuf + 2 * bcap;
+  int64_t* bin_nt = binbuf + 3 * bcap;
+  int64_t* bin_toff = binbuf + 4 * bcap;
+  int64_t* totals = binbuf + 5 * bcap;  // [0] n_bins, [1] n_queries grouped, [2] tiles A, [3] tiles B, [4..5] ctr
+  int32_t* cand = ptr<int32_t>(c->ws[WS_CAND]);
+  int32_t* ncand = cand + bcap * p.K;
+  int4* tiles_a = ptr<int4>(c->ws[WS_TILE]);
+  int4* tiles_b = tiles_a + max_tiles_a;
+  int64_t* cbuf = ptr<int64_t>(c->ws[WS_CELLQ]);
+  int64_t* wcnt = cbuf;
+  int64_t* woff = cbuf + G;
+  int64_t* wnt = cbuf + 2 * G;
+  int64_t* wtoff = cbuf + 3 * G;
+  int* counters = reinterpret_cast<int*>(totals + 6);
+
+  // Q1 (kEmptyKey is all ones)
+  KSDF_CUDA(c, cudaMemsetAsync(bhk, 0xFF, sizeof(uint64_t) * bcap, st));
+  KSDF_CUDA(c, cudaMemsetAsync(bin_cnt, 0, sizeof(int64_t) * bcap, st));
+  KSDF_CUDA(c, cudaMemsetAsync(totals, 0, sizeof(int64_t) * 8, st));
+  KSDF_CUDA(c, cudaMemsetAsync(wcnt, 0, sizeof(int64_t) * G, st));
+  if (f64)
+    k_q_bin<double><<<ceil_div(Q, 256), 256, 0, st>>>(static_cast<const double*>(xq), Q, p, qkey, bhk, bcap, stw);
+  else
+    k_q_bin<float><<<ceil_div(Q, 256), 256, 0, st>>>(static_cast<const float*>(xq), Q, p, qkey, bhk, bcap, stw);
+  // Q2
+  k_slot_flags<<<ceil_div(bcap, 256), 256, 0, st>>>(bhk, bcap, slot_id);
+  KSDF_CUDA(c, scan_i64(slot_id, slot_id, bcap, &totals[0], c->ws[WS_SCAN], st));
+  k_bin_table<<<ceil_div(bcap, 256), 256, 0, st>>>(bhk, bcap, slot_id, bin_key);
+  k_q_rank<<<ceil_div(Q, 256), 256, 0, st>>>(qkey, Q, bhk, slot_id, bcap, qbin, qrank, bin_cnt);
+  KSDF_CUDA(c, scan_i64(bin_cnt, bin_off, bcap, &totals[1], c->ws[WS_SCAN], st));
+  k_ntiles<<<ceil_div(bcap, 256), 256, 0, st>>>(bin_cnt, bcap, kTA, bin_nt);
+  KSDF_CUDA(c, scan_i64(bin_nt, bin_toff, bcap, &totals[2], c->ws[WS_SCAN], st));
+  k_scatter_grouped<<<ceil_div(Q, 256), 256, 0, st>>>(qbin, qrank, Q, bin_off, qsort);
+  k_make_tiles<<<ceil_div(bcap, 256), 256, 0, st>>>(bin_cnt, bin_off, bin_toff, bcap, kTA, tiles_a);
+  // Q3
+  {
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(bcap, kCandWarps), 8LL * c->num_sms);
+    k_candidates<<<grid, 32 * kCandWarps, 0, st>>>(bin_key, &totals[0], 0, cand_ctx(c), cand, ncand);
+  }
+  // Q4
+  PhaseAArgs pa;
+  pa.tiles = tiles_a;
+  pa.n_tiles = &totals[2];
+  pa.counter = &counters[0];
+  pa.sorted_q = qsort;
+  pa.bin_key = bin_key;
+  pa.cand = cand;
+  pa.ncand = ncand;
+  pa.ts_off = ptr<int64_t>(m.ts_off);
+  pa.cell_n = ptr<int32_t>(m.n);
+  pa.cell_key = ptr<uint64_t>(m.key);
+  pa.mf4 = ptr<float4>(m.mf4);
+  pa.md4 = ptr<D4>(m.md4);
+  pa.qwin = qwin;
+  pa.qu = qu;
+  pa.qu64 = qu64;
+  pa.qflag = qflag;
+  pa.st = stw;
+  const int maxn = std::max(m.max_n, 1);
+  if (f64) {
+    const size_t smem = sizeof(D4) * (size_t)p.K * maxn;
+    KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseA64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA64, kTA, smem));
+    k_phaseA64<<<std::max(1, occ) * c->num_sms, kTA, smem, st>>>(pa, static_cast<const double*>(xq), p);
+  } else {
+    const size_t smem = sizeof(float4) * (size_t)p.K * maxn;
+    KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA, kTA, smem));
+    k_phaseA<<<std::max(1, occ) * c->num_sms, kTA, smem, st>>>(pa, static_cast<const float*>(xq), p);
+  }
+  KSDF_CUDA(c, cudaGetLastError());
+  // Q5
+  int32_t* wrank = qrank;  // qrank no longer needed
+  if (f64)
+    k_w_rank<double><<<ceil_div(Q, 256), 256, 0, st>>>(qwin, qflag, qbin, Q, wrank, wcnt, mask, p.dim,
+                                                        static_cast<double*>(sdf), static_cast<double*>(grad),
+                                                        static_cast<double*>(var_sdf), static_cast<double*>(var_f),
+                                                        winner, flags);
+  else
+    k_w_rank<float><<<ceil_div(Q, 256), 256, 0, st>>>(qwin, qflag, qbin, Q, wrank, wcnt, mask, p.dim,
+                                                       static_cast<float*>(sdf), static_cast<float*>(grad),
+                                                       static_cast<float*>(var_sdf), static_cast<float*>(var_f),
+                                                       winner, flags);
+  KSDF_CUDA(c, scan_i64(wcnt, woff, G, nullptr, c->ws[WS_SCAN], st));
+  k_ntiles<<<ceil_div(G, 256), 256, 0, st>>>(wcnt, G, TBq, wnt);
+  KSDF_CUDA(c, scan_i64(wnt, wtoff, G, &totals[3], c->ws[WS_SCAN], st));
+  k_w_scatter<<<ceil_div(Q, 256), 256, 0, st>>>(qwin, qbin, wrank, Q, woff, qwsort);
+  k_make_tiles<<<ceil_div(G, 256), 256, 0, st>>>(wcnt, woff, wtoff, G, TBq, tiles_b);
+  // Q6
+  PhaseBArgs pb;
+  pb.tiles = tiles_b;
+  pb.n_tiles = &totals[3];
+  pb.counter = &counters[1];
+  pb.sorted_w = qwsort;
+  pb.ts_off = ptr<int64_t>(m.ts_off);
+  pb.cell_n = ptr<int32_t>(m.n);
+  pb.cell_key = ptr<uint64_t>(m.key);
+  pb.linv_off = ptr<int64_t>(m.linv_off);
+  pb.mf4 = ptr<float4>(m.mf4);
+  pb.md4 = ptr<D4>(m.md4);
+  pb.mvar = ptr<float>(m.mvar);
+  pb.mnrm = m.has_normals ? ptr<float4>(m.mnrm) : nullptr;
+  pb.linv32 = ptr<float>(m.linv32);
+  pb.linv32lo = ptr<float>(m.linv32lo);
+  pb.linv64 = ptr<double>(m.linv64);
+  pb.qu = qu;
+  pb.qu64 = qu64;
+  pb.qflag = qflag;
+  pb.sign = sign;
+  pb.has_normals = m.has_normals ? 1 : 0;
+  pb.mask = mask;
+  pb.st = stw;
+  if (f64) {
+    const size_t smem = sizeof(D4) * p.n_max + sizeof(double) * p.n_max * (1 + kTB64);
+    KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB64, kTB64, smem));
+    k_phaseB64<<<std::max(1, occ) * c->num_sms, kTB64, smem, st>>>(
+        pb, static_cast<const double*>(xq), p, static_cast<double*>(sdf), static_cast<double*>(grad),
+        static_cast<double*>(var_sdf), static_cast<double*>(var_f), winner, flags);
+  } else {
+    const size_t smem = sizeof(float4) * p.n_max + sizeof(float) * p.n_max * (1 + kTB);
+    KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB, kTB, smem));
+    k_phaseB<<<std::max(1, occ) * c->num_sms, kTB, smem, st>>>(
+        pb, static_cast<const float*>(xq), p, static_cast<float*>(sdf), static_cast<float*>(grad),
+        static_cast<float*>(var_sdf), static_cast<float*>(var_f), winner, flags);
+  }
+  KSDF_CUDA(c, cudaGetLastError());
+  return KSDF_OK;
+}
+
+}  // namespace ksdf

@@ -1,0 +1,69 @@
+"""The C ABI library (no GPU needed): it builds, loads, exports every entry point include/ksdf.h declares,
+and validates parameters before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_29227_gb300 import build, ksdf
+
+    build.build()
+    return ksdf.load()
+
+
+def declared():
+    hdr = open(os.path.join(ROOT, "include", "ksdf.h")).read()
+    return re.findall(r"^(?:ksdf_status|const char\*)\s+(ksdf_\w+)\(", hdr, re.M)
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2603_29227_gb300 import ksdf
+
+    names = declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(names) == sorted(ksdf.ABI_FUNCTIONS)
+
+
+def test_invalid_parameters_rejected_without_cuda(lib):
+    from paper_2603_29227_gb300 import ksdf
+
+    good = dict(dim=3, origin=(0, 0, 0), cell=0.5, margin=0.1, n_max=256, k_cand=8, softmin_alpha=0.0, sign_mode=0,
+                **{"lambda": 300.0})
+    bad = [dict(good, dim=4), dict(good, cell=0.0), dict(good, margin=-1.0), dict(good, n_max=0),
+           dict(good, n_max=513), dict(good, k_cand=0), dict(good, k_cand=33), dict(good, **{"lambda": -1.0}),
+           dict(good, sign_mode=2), dict(good, margin=10.0)]
+    for p in bad:
+        h = ctypes.c_void_p()
+        pr = ksdf.make_params(p)
+        assert lib.ksdf_create(ctypes.byref(pr), None, ctypes.byref(h)) == ksdf.KSDF_ERR_ARG, p
+        assert not h.value
+    # NULL handles are rejected everywhere
+    assert lib.ksdf_destroy(None) == ksdf.KSDF_ERR_ARG
+    assert lib.ksdf_sync_status(None) == ksdf.KSDF_ERR_ARG
+    assert lib.ksdf_fit(None, None, None, None, 1) == ksdf.KSDF_ERR_ARG
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2603_29227_gb300 import ksdf
+
+    saved = ksdf._lib
+    ksdf._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            ksdf.load(str(tmp_path / "missing.so"))
+    finally:
+        ksdf._lib = saved
+
+
+def test_graft_entry_build_importable():
+    import __graft_entry__
+
+    assert callable(__graft_entry__.build) and callable(__graft_entry__.smoke)
