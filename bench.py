@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the Kernel-SDF back-end hot path on GB300 (one JSON line on rank 0).
+
+One step = the whole path over one batch of the room workload (20 x 20 x 5 m room, 50 primitives,
+200,000 noisy surface samples, 1,000,000 uniform queries): fit of every local GP (binning, cell index,
+training sets, FP64 Cholesky / alpha / L^-1), query (candidates, min-fused SDF, gradient, softmin variance,
+GP variance) and the adjoint of sdf and grad with respect to the query points and the sample positions.
+value = queries per second of that step over all ranks (weak scaling: each rank fits the scene and
+answers its own 1M queries).  Inputs are resident on the device; L2 is flushed (256 MiB write) between
+timed steps.  The JSON line also carries the roofline of the dominant kernel (stage timing with CUDA
+events on the library's stream), the plain-FP64 query for comparison, a sampled parity check against the
+CPU FP64 oracle (which is also the timed CPU baseline), the end-to-end number through the C ABI with
+pinned host buffers, SM clocks sampled during the timed region, and the number of kernel launches.
+
+--impl reference times the CPU FP64 oracle itself (the reference arm; there is no other implementation of
+the paper's method to run) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 and FP32 rates from the profiling recipe's unit counts (nominal FP64 1.25 TFLOP/s; FP32: 128 FMA
+# lanes x 152 SMs x 2 flops at the 2.07 GHz maximum clock)
+NOMINAL_FP64_TFLOPS = 1.25
+NOMINAL_FP32_TFLOPS = 128 * 152 * 2 * 2.07e9 / 1e12
+METRIC = "SDF+grad+var queries/s at err<=1e-4 m vs FP64 oracle; % roofline; vs plain FP64"
+WORKLOAD = ("room3d: 20x20x5 m room with 50 spheres/boxes, 200,000 samples (sigma 0.01 m), 0.5 m cells, "
+            "n_max 256, K 8, lambda 300; 1,000,000 uniform queries; step = fit + query(sdf, grad, var_sdf, "
+            "var_f) + adjoint(d sdf, d grad -> d xq, d x)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--samples", type=int, default=200_000)
+    ap.add_argument("--queries", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg (cpu_baseline, parity)")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_workload(args, rank):
+    from paper_2603_29227_gb300 import scenes
+
+    w = scenes.workload("room3d", n_samples=args.samples, n_queries=args.queries)
+    if rank > 0:  # weak scaling: same scene, each rank its own query batch
+        rng = np.random.default_rng(1000 + rank)
+        xq = w.scene.room_lo + rng.random((args.queries, 3)) * (w.scene.room_hi - w.scene.room_lo)
+        w.xq = xq.astype(np.float32)
+        w.sign = w.scene.sign(w.xq.astype(np.float64))
+    return w
+
+
+# ----------------------------------------------------------------------------------------------------
+# oracle (CPU) legs
+
+
+def oracle_leg(w, n_sample, seed=0):
+    """Time the oracle on a bounded sample; returns (stats, per-query outputs on the sample)."""
+    import oracle
+
+    oracle.build()
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(len(w.xq), size=min(n_sample, len(w.xq)), replace=False))
+    t0 = time.perf_counter()
+    m = oracle.Model(w.params, w.x, w.var, w.normals)
+    t1 = time.perf_counter()
+    ref = m.query(w.xq[sel], w.sign[sel], with_cands=True)
+    t2 = time.perf_counter()
+    d_sdf = np.ones(len(sel))
+    d_grad = np.random.default_rng(7).standard_normal((len(sel), 3)) * 0.1
+    m.backward(w.xq[sel], d_sdf, d_grad, sign=w.sign[sel], winner=ref["winner"])
+    t3 = time.perf_counter()
+    Q = len(w.xq)
+    scale = Q / len(sel)
+    t_equiv = (t1 - t0) + (t3 - t1) * scale
+    stats = dict(value=Q / t_equiv, unit="queries/s", cores=threads, kind="oracle",
+                 sample="full FP64 fit of %d samples (%.2f s) + forward and adjoint of %d of the %d queries "
+                        "(%.2f s), query part scaled x%.1f" % (len(w.x), t1 - t0, len(sel), Q, t3 - t1, scale),
+                 fit_s=t1 - t0, query_backward_s=t3 - t1)
+    return stats, m, sel, ref
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    w = make_workload(args, 0)
+    oracle.build()
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    Q = len(w.xq)
+    qs = max(256, min(args.cpu_sample // 8, Q))
+    rng = np.random.default_rng(0)
+    times = []
+    for it in range(args.warmup + args.steps):
+        sel = rng.choice(Q, size=qs, replace=False)
+        t0 = time.perf_counter()
+        m = oracle.Model(w.params, w.x, w.var, w.normals)
+        t1 = time.perf_counter()
+        r = m.query(w.xq[sel], w.sign[sel])
+        m.backward(w.xq[sel], np.ones(qs), np.full((qs, 3), 0.1), sign=w.sign[sel], winner=r["winner"])
+        t2 = time.perf_counter()
+        if it >= args.warmup:
+            times.append((t1 - t0) + (t2 - t1) * Q / qs)
+        del m
+    t = float(np.mean(times))
+    value = Q / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "samples": len(w.x), "queries": Q},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                             "sample": "per step: full FP64 fit of %d samples + forward and adjoint of %d random "
+                                       "queries of %d, query part scaled x%.1f" % (len(w.x), qs, Q, Q / qs)},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------------------
+# clocks
+
+
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        rows = [ln.split(", ") for ln in self.lines if ln]
+        mine = [r for r in rows if self.uuid and r[0].strip() == self.uuid] or rows
+        if not mine:
+            return None
+        sm = [float(r[1]) for r in mine if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in mine if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in mine:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(mine)}
+
+
+# ----------------------------------------------------------------------------------------------------
+# algorithmic work per launch (roofline numerators)
+
+
+def fit_fp64_flops(n):
+    """FP64 flops of the fit of cells with training-set sizes n (exp evaluations not counted): kernel matrix
+    r^2 (8 flops per lower-triangle entry), Cholesky N^3/3, alpha 2N^2 (two triangular solves), L^-1 N^3/3."""
+    n = n.astype(np.float64)
+    return float(np.sum(8 * n * (n + 1) / 2 + n ** 3 / 3 + 2 * n ** 2 + n ** 3 / 3))
+
+
+def phase_a_pairs(w, h):
+    from paper_2603_29227_gb300 import ksdf
+
+    keys, status, off, mem = ksdf.ksdf_get_cells(h)
+    nsz = np.diff(off)
+    qk = np.empty(len(w.xq), np.uint64)
+    ksdf.ksdf_bin(h, np.ascontiguousarray(w.xq, dtype=np.float64), len(w.xq), qk)
+    ub, inv = np.unique(qk, return_inverse=True)
+    K = w.params["k_cand"]
+    cand = np.empty((len(ub), K), np.int32)
+    cnt = np.empty(len(ub), np.int32)
+    ksdf.ksdf_candidates(h, ub, len(ub), cand, cnt)
+    per_bin = np.where(cand >= 0, nsz[np.maximum(cand, 0)], 0).sum(axis=1)
+    return float(per_bin[inv].sum()), nsz
+
+
+# ----------------------------------------------------------------------------------------------------
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2603_29227_gb300 import ksdf
+
+    ksdf.load()
+    w = make_workload(args, rank)
+    Q, S = len(w.xq), len(w.x)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    x, var, nrm, xq, sign = t(w.x), t(w.var), t(w.normals), t(w.xq), t(w.sign)
+    gen = torch.Generator(device=dev).manual_seed(5 + rank)
+    d_sdf = torch.ones(Q, dtype=torch.float32, device=dev)
+    d_grad = torch.randn((Q, 3), generator=gen, device=dev, dtype=torch.float32) * 0.1
+    model = ksdf.KernelSDF(w.params)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        model.fit(x, var, nrm)
+        out = model.query(xq, sign)
+        dq, dx = model.backward(xq, out["winner"], d_sdf, d_grad, sign)
+        return out, dq, dx
+
+    for _ in range(max(args.warmup, 3)):
+        out, dq, dx = step()
+    torch.cuda.synchronize()
+    model.sync_status()
+    # timed region
+    ksdf.ksdf_profile(model.h, 1)
+    _, launches0 = ksdf.ksdf_profile_read(model.h)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # L2 flush between steps (outside the events)
+        ev[i][0].record()
+        out, dq, dx = step()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    stages, launches1 = ksdf.ksdf_profile_read(model.h)
+    ksdf.ksdf_profile(model.h, 0)
+    model.sync_status()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    total_s = float(step_ms.sum()) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = float(tt.item())
+    value = world * Q * args.steps / total_s
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel ----
+    peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
+    pairs, nsz = phase_a_pairs(w, model.h)
+    per = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
+    kernels = {k: per[k] for k in ("fit.cholesky", "fit.index", "fit.assemble", "query.group", "query.candidates",
+                                   "query.phaseA", "query.regroup", "query.phaseB", "backward.group",
+                                   "backward.query", "backward.cell") if k in per}
+    dom = max(kernels, key=kernels.get)
+    fl64 = fit_fp64_flops(nsz)
+    roof_all = {
+        "fit.cholesky": {"bound": "alu", "achieved": fl64 / (per["fit.cholesky"] * 1e-3) / 1e12,
+                         "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                         "what": "FP64 flops (kernel matrix, Cholesky, alpha, L^-1; exp not counted)"},
+        "query.phaseA": {"bound": "alu", "achieved": pairs * 12 / (per["query.phaseA"] * 1e-3) / 1e12,
+                         "peak": NOMINAL_FP32_TFLOPS, "unit": "TFLOP/s",
+                         "what": "12 FP32 flops per (query, candidate sample) pair + 1 ex2; %.3g pairs" % pairs},
+    }
+    for r in roof_all.values():
+        r["frac"] = r["achieved"] / r["peak"]
+        r["traffic"] = None
+    roof = dict(roof_all.get(dom, {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                                   "traffic": None}))
+    roof["kernel"] = dom
+    roof["peak_source"] = "recipe nominal (unit counts x clock); no FP64/FP32 figure in MEASURED_PEAKS.json"
+
+    # ---- plain FP64 query on the same inputs (outside the timed region) ----
+    xq64 = xq.double()
+    ksdf.ksdf_profile(model.h, 1)
+    for _ in range(2):
+        model.query(xq64, sign, f64=True)
+    st64, _ = ksdf.ksdf_profile_read(model.h)
+    ksdf.ksdf_profile(model.h, 0)
+    q64_ms = st64["query64"][0] / st64["query64"][1]
+    q32_ms = per.get("query", float("nan"))
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        hx, hv, hn, hq, hs = pin(w.x), pin(w.var), pin(w.normals), pin(w.xq), pin(w.sign)
+        hds, hdg = d_sdf.cpu().pin_memory(), d_grad.cpu().pin_memory()
+        outs = [torch.empty(Q, dtype=torch.float32).pin_memory(), torch.empty((Q, 3), dtype=torch.float32).pin_memory(),
+                torch.empty(Q, dtype=torch.float32).pin_memory(), torch.empty(Q, dtype=torch.float32).pin_memory(),
+                torch.empty(Q, dtype=torch.int32).pin_memory(), torch.empty(Q, dtype=torch.int32).pin_memory()]
+        hdq = torch.empty((Q, 3), dtype=torch.float32).pin_memory()
+        hdx = torch.zeros((S, 3), dtype=torch.float32).pin_memory()
+        h = model.h
+        ksdf.ksdf_set_stream(h, torch.cuda.current_stream().cuda_stream)
+
+        def e2e_step():
+            ksdf.ksdf_fit(h, hx, hv, hn, S)
+            ksdf.ksdf_query(h, hq, Q, hs, ksdf.OUT_ALL, *outs)
+            ksdf.ksdf_query_backward(h, hq, Q, hs, outs[4], hds, hdg, hdq, hdx)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        n_e2e = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h2d = sum(a.numel() * a.element_size() for a in (hx, hv, hn, hq, hs)) + \
+            sum(a.numel() * a.element_size() for a in (hq, hs, outs[4], hds, hdg, hdx))
+        d2h = sum(a.numel() * a.element_size() for a in outs) + hdq.numel() * 4 + hdx.numel() * 4
+        e2e = {"value": Q * n_e2e / (t1 - t0), "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
+               "how": "ksdf_fit/ksdf_query/ksdf_query_backward with pinned host arrays; the library copies "
+                      "in and out inside each call; host wall clock"}
+
+    # ---- CPU FP64 oracle: baseline timing and sampled parity of this run's outputs ----
+    cpu = None
+    parity = None
+    if not args.no_cpu:
+        cpu, om, sel, ref = oracle_leg(w, args.cpu_sample)
+        got = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+        sdf_err = np.abs(got["sdf"][sel].astype(np.float64) - ref["sdf"])
+        fin = np.isfinite(ref["sdf"])
+        same = got["winner"][sel] == ref["winner"]
+        gref = ref["grad"]
+        gg = got["grad"][sel].astype(np.float64)
+        ang = np.degrees(np.arccos(np.clip(np.sum(gg * gref, 1) / np.maximum(
+            np.linalg.norm(gg, axis=1) * np.linalg.norm(gref, axis=1), 1e-300), -1, 1)))
+        vf = np.abs(got["var_f"][sel] - ref["var_f"]) / np.maximum(ref["var_f"], 1e-3)
+        vs = np.abs(got["var_sdf"][sel] - ref["var_sdf"]) / np.maximum(np.abs(ref["var_sdf"]), 1e-30)
+        parity = {"sample": int(len(sel)), "sdf_max_err_m": float(sdf_err[fin].max()),
+                  "sdf_within_1e-4": bool(sdf_err[fin].max() <= 1e-4),
+                  "winner_agree": float(same.mean()),
+                  "grad_angle_p999_deg": float(np.quantile(ang[same & fin], 0.999)),
+                  "var_sdf_max_rel": float(vs[same & fin].max()), "var_f_max_scaled": float(vf[same & fin].max()),
+                  "note": "full per-query checks with medial/tie exclusions are in tests/test_gpu_full.py"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "samples": S, "queries": Q, "cells": int(len(nsz)),
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "precision": "FP64 fit (Cholesky, alpha, L^-1); FP32 query with compensated mean; FP32 adjoint "
+                                "with FP64 per-cell solves"},
+        "roofline": roof,
+        "rooflines": roof_all,
+        "stage_ms": {k: round(v, 4) for k, v in per.items()},
+        "plain_fp64": {"query_ms": q64_ms, "mixed_query_ms": q32_ms, "query_speedup": q64_ms / q32_ms},
+        "cpu_baseline": cpu,
+        "parity": parity,
+        "e2e": e2e,
+        "gpu_launches": int(launches1 - launches0),
+        "clocks": clk,
+        "wall_s": wall1 - wall0,
+        "step_ms_min_median_max": [float(step_ms.min()), float(np.median(step_ms)), float(step_ms.max())],
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

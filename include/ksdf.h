@@ -160,6 +160,22 @@ ksdf_status ksdf_get_fit(ksdf_ctx* ctx, double* alpha, double* linv);
 ksdf_status ksdf_bin(ksdf_ctx* ctx, const double* x, int64_t n, uint64_t* keys);
 ksdf_status ksdf_candidates(ksdf_ctx* ctx, const uint64_t* bin_keys, int64_t n, int32_t* cand, int32_t* count);
 
+/* ---- measurement (no counterpart in the paper: instrumentation of this library) ---- */
+
+/* Enable (1) or disable (0) per-stage timing: CUDA events are recorded on the context's stream around
+ * each pipeline stage ("fit.index", "fit.assemble", "fit.cholesky", "query.group", "query.candidates",
+ * "query.phaseA", "query.regroup", "query.phaseB", "backward.group", "backward.query", "backward.cell",
+ * and the totals "fit", "query", "backward"; the FP64 query uses the prefix "query64").  Synchronises the
+ * stream and clears the accumulated totals. */
+ksdf_status ksdf_profile(ksdf_ctx* ctx, int enable);
+/* Synchronise, fold the recorded events into per-stage totals and copy them out: names is a host buffer of
+ * max_stages x 32 chars (NUL-terminated names), total_ms[max_stages] and calls[max_stages] the summed
+ * device time and the number of timed calls per stage, *n_stages the number of stages known.  *launches
+ * gets the number of kernels this library has launched since it was loaded (all contexts).  Any output
+ * pointer may be NULL. */
+ksdf_status ksdf_profile_read(ksdf_ctx* ctx, int max_stages, char* names, double* total_ms, int64_t* calls,
+                              int* n_stages, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

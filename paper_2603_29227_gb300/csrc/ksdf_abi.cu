@@ -49,6 +49,53 @@ void release(DevBuf& b) {
   b.bytes = 0;
 }
 
+std::atomic<long long> g_launches{0};
+
+static cudaEvent_t pool_event(ksdf_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+cudaEvent_t prof_begin(ksdf_ctx* c) {
+  if (!c->prof) return nullptr;
+  cudaEvent_t e = pool_event(c);
+  if (e) cudaEventRecord(e, c->stream);
+  return e;
+}
+
+void prof_end(ksdf_ctx* c, cudaEvent_t a, const char* name) {
+  if (!c->prof || !a) return;
+  cudaEvent_t b = pool_event(c);
+  if (!b) return;
+  cudaEventRecord(b, c->stream);
+  c->pending.push_back({name, a, b});
+}
+
+static void prof_fold(ksdf_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) cudaGetLastError();
+    size_t i = 0;
+    while (i < c->stage_names.size() && c->stage_names[i] != p.name) ++i;
+    if (i == c->stage_names.size()) {
+      c->stage_names.push_back(p.name);
+      c->stage_ms.push_back(0.0);
+      c->stage_calls.push_back(0);
+    }
+    c->stage_ms[i] += ms;
+    c->stage_calls[i] += 1;
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
 namespace {
 
 bool on_device(const void* p) {
@@ -161,6 +208,11 @@ ksdf_status ksdf_destroy(ksdf_ctx* c) {
   for (DevBuf* b : bufs) release(*b);
   for (auto& b : c->ws) release(b);
   for (auto& b : c->stage) release(b);
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
   return KSDF_OK;
 }
@@ -198,6 +250,7 @@ static ksdf_status query_common(ksdf_ctx* c, const void* xq, bool f64, int64_t Q
   if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "query before a successful fit");
   if (Q < 0 || (Q > 0 && !xq)) return set_err(c, KSDF_ERR_ARG, "query: bad Q or NULL points");
   if (Q >= (1LL << 31)) return set_err(c, KSDF_ERR_CAPACITY, "query: Q must be < 2^31");
+  if (Q == 0) return KSDF_OK;  // empty arrays may carry NULL pointers
   mask &= KSDF_OUT_ALL;
   if (((mask & KSDF_OUT_SDF) && !sdf) || ((mask & KSDF_OUT_GRAD) && !grad) || ((mask & KSDF_OUT_VAR_SDF) && !var_sdf) ||
       ((mask & KSDF_OUT_VAR_F) && !var_f) || ((mask & KSDF_OUT_WINNER) && !winner) ||
@@ -273,6 +326,36 @@ ksdf_status ksdf_sync_status(ksdf_ctx* c) {
 }
 
 const char* ksdf_last_error(const ksdf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ksdf_status ksdf_profile(ksdf_ctx* c, int enable) {
+  if (!c) return KSDF_ERR_ARG;
+  KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  prof_fold(c);
+  c->stage_names.clear();
+  c->stage_ms.clear();
+  c->stage_calls.clear();
+  c->prof = enable != 0;
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_profile_read(ksdf_ctx* c, int max_stages, char* names, double* total_ms, int64_t* calls,
+                              int* n_stages, int64_t* launches) {
+  if (!c || max_stages < 0) return KSDF_ERR_ARG;
+  KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  prof_fold(c);
+  const int n = (int)c->stage_names.size();
+  if (n_stages) *n_stages = n;
+  for (int i = 0; i < n && i < max_stages; ++i) {
+    if (names) {
+      std::memset(names + 32 * i, 0, 32);
+      std::strncpy(names + 32 * i, c->stage_names[i].c_str(), 31);
+    }
+    if (total_ms) total_ms[i] = c->stage_ms[i];
+    if (calls) calls[i] = c->stage_calls[i];
+  }
+  if (launches) *launches = g_launches.load();
+  return KSDF_OK;
+}
 
 ksdf_status ksdf_model_size(ksdf_ctx* c, int64_t* n_cells, int64_t* n_members) {
   if (!c) return KSDF_ERR_ARG;

@@ -330,15 +330,17 @@ ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* 
   int* counter = reinterpret_cast<int*>(tot + 2);
   int4* tiles = ptr<int4>(c->ws[WS_TILE]);
   double* abar = ptr<double>(c->ws[WS_BW]);
+  cudaEvent_t e_b = prof_begin(c), e0 = prof_begin(c);
   KSDF_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int64_t) * G, st));
   KSDF_CUDA(c, cudaMemsetAsync(tot, 0, sizeof(int64_t) * 4, st));
   KSDF_CUDA(c, cudaMemsetAsync(abar, 0, sizeof(double) * (m.M + 1), st));
-  k_bw_count<<<ceil_div(Q, 256), 256, 0, st>>>(winner, Q, G, rank, cnt, d_xq, p.dim, stw);
+  launch(k_bw_count, ceil_div(Q, 256), 256, 0, st, winner, Q, G, rank, cnt, d_xq, p.dim, stw);
   KSDF_CUDA(c, scan_i64(cnt, off, G, nullptr, c->ws[WS_SCAN], st));
-  k_ntiles_w<<<ceil_div(G, 256), 256, 0, st>>>(cnt, G, nt);
+  launch(k_ntiles_w, ceil_div(G, 256), 256, 0, st, cnt, G, nt);
   KSDF_CUDA(c, scan_i64(nt, toff, G, &tot[0], c->ws[WS_SCAN], st));
-  k_bw_scatter<<<ceil_div(Q, 256), 256, 0, st>>>(winner, rank, Q, G, off, sorted);
-  k_bw_tiles<<<ceil_div(G, 256), 256, 0, st>>>(cnt, off, toff, G, tiles);
+  launch(k_bw_scatter, ceil_div(Q, 256), 256, 0, st, winner, rank, Q, G, off, sorted);
+  launch(k_bw_tiles, ceil_div(G, 256), 256, 0, st, cnt, off, toff, G, tiles);
+  prof_end(c, e0, "backward.group");
   BwArgs a;
   a.tiles = tiles;
   a.n_tiles = &tot[0];
@@ -361,15 +363,20 @@ ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* 
   KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bw_query, kTW, smem));
-  k_bw_query<<<std::max(1, occ) * c->num_sms, kTW, smem, st>>>(a, xq, p);
+  e0 = prof_begin(c);
+  launch(k_bw_query, std::max(1, occ) * c->num_sms, kTW, smem, st, a, xq, p);
+  prof_end(c, e0, "backward.query");
+  e0 = prof_begin(c);
   const size_t smem2 = sizeof(double) * 3 * p.n_max;
   KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
   const unsigned grid2 = (unsigned)std::min<int64_t>(G, 4LL * c->num_sms);
-  k_bw_cell<<<std::max(1u, grid2), 256, smem2, st>>>(cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
+  launch(k_bw_cell, std::max(1u, grid2), 256, smem2, st, cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
                                                      ptr<int64_t>(m.linv_off), ptr<double>(m.linv64),
                                                      ptr<D4>(m.md4), ptr<float4>(m.mf4), ptr<int32_t>(m.mgid),
                                                      abar, p, d_x);
   KSDF_CUDA(c, cudaGetLastError());
+  prof_end(c, e0, "backward.cell");
+  prof_end(c, e_b, "backward");
   return KSDF_OK;
 }
 

@@ -373,6 +373,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   if (S <= 0) return set_err(c, KSDF_ERR_ARG, "ksdf_fit: S must be positive");
   if (S >= (1LL << 31)) return set_err(c, KSDF_ERR_CAPACITY, "ksdf_fit: S must be < 2^31");
   uint32_t* stw = ptr<uint32_t>(c->status_word);
+  cudaEvent_t e_fit = prof_begin(c), e0 = prof_begin(c);
   // 1. bin
   KSDF_CUDA(c, ensure(c->ws[WS_A], sizeof(uint64_t) * S));
   KSDF_CUDA(c, ensure(c->ws[WS_B], sizeof(uint32_t) * S));
@@ -383,7 +384,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   int hb[8] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, INT32_MIN, 0, 0};
   KSDF_CUDA(c, cudaMemcpyAsync(bbox, hb, sizeof(hb), cudaMemcpyHostToDevice, st));
   KSDF_CUDA(c, cudaMemsetAsync(stw, 0, sizeof(uint32_t), st));
-  k_bin_samples<<<ceil_div(S, 256), 256, 0, st>>>(x, var, S, p, keys, vals, bbox, stw);
+  launch(k_bin_samples, ceil_div(S, 256), 256, 0, st, x, var, S, p, keys, vals, bbox, stw);
   uint32_t hst = 0;
   KSDF_CUDA(c, cudaMemcpyAsync(hb, bbox, sizeof(int) * 6, cudaMemcpyDeviceToHost, st));
   KSDF_CUDA(c, cudaMemcpyAsync(&hst, stw, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -395,11 +396,11 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   const int64_t nx = (int64_t)hb[3] - x0 + 1, ny = (int64_t)hb[4] - y0 + 1, nz = (int64_t)hb[5] - z0 + 1;
   const uint64_t vol = (uint64_t)nx * (uint64_t)ny * (uint64_t)nz;
   // 2. sort by linear cell index (ascending (cz, cy, cx)), stable in sample id
-  k_linear_keys<<<ceil_div(S, 256), 256, 0, st>>>(keys, S, x0, y0, z0, nx, ny);
+  launch(k_linear_keys, ceil_div(S, 256), 256, 0, st, keys, S, x0, y0, z0, nx, ny);
   KSDF_CUDA(c, radix_sort_u64(keys, vals, S, bits_for(vol - 1), c->ws[WS_SORT], st));
   KSDF_CUDA(c, ensure(c->ws[WS_D], sizeof(int64_t) * (S + 1)));
   int64_t* flag = ptr<int64_t>(c->ws[WS_D]);
-  k_flags<<<ceil_div(S, 256), 256, 0, st>>>(keys, S, flag);
+  launch(k_flags, ceil_div(S, 256), 256, 0, st, keys, S, flag);
   KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4));
   int64_t* dtot = ptr<int64_t>(c->ws[WS_E]);
   KSDF_CUDA(c, scan_i64(flag, flag, S, dtot, c->ws[WS_SCAN], st));
@@ -411,7 +412,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, ensure(m.key, sizeof(uint64_t) * G));
   KSDF_CUDA(c, ensure(c->ws[WS_F], sizeof(int64_t) * (G + 1)));
   int64_t* own_off = ptr<int64_t>(c->ws[WS_F]);
-  k_cells<<<ceil_div(S, 256), 256, 0, st>>>(keys, flag, S, x0, y0, z0, nx, ny, ptr<uint64_t>(m.key), own_off);
+  launch(k_cells, ceil_div(S, 256), 256, 0, st, keys, flag, S, x0, y0, z0, nx, ny, ptr<uint64_t>(m.key), own_off);
   KSDF_CUDA(c, cudaMemcpyAsync(own_off + G, &S, sizeof(int64_t), cudaMemcpyHostToDevice, st));
   // hash table key -> cell id
   uint64_t cap = 64;
@@ -419,9 +420,11 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   m.hcap = cap;
   KSDF_CUDA(c, ensure(m.hkeys, sizeof(uint64_t) * cap));
   KSDF_CUDA(c, ensure(m.hvals, sizeof(int32_t) * cap));
-  k_fill_u64<<<ceil_div(cap, 256), 256, 0, st>>>(ptr<uint64_t>(m.hkeys), cap, kEmptyKey);
-  k_hash_insert<<<ceil_div(G, 256), 256, 0, st>>>(ptr<uint64_t>(m.key), G, ptr<uint64_t>(m.hkeys),
+  launch(k_fill_u64, ceil_div(cap, 256), 256, 0, st, ptr<uint64_t>(m.hkeys), cap, kEmptyKey);
+  launch(k_hash_insert, ceil_div(G, 256), 256, 0, st, ptr<uint64_t>(m.key), G, ptr<uint64_t>(m.hkeys),
                                                    ptr<int32_t>(m.hvals), cap);
+  prof_end(c, e0, "fit.index");
+  e0 = prof_begin(c);
   // 3. training sets
   const int R = (int)floor(p.mu / p.h + 1e-6) + 1;
   KSDF_CUDA(c, ensure(m.mpad, sizeof(int32_t) * (size_t)G * p.n_max));
@@ -434,10 +437,10 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   int64_t* tri64 = n64 + (G + 1);
   int* dmax = bbox + 6;
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
-  k_assemble<<<(unsigned)G, 512, 0, st>>>(ptr<uint64_t>(m.key), G, own_off, vals, x, p, R, ptr<uint64_t>(m.hkeys),
+  launch(k_assemble, (unsigned)G, 512, 0, st, ptr<uint64_t>(m.key), G, own_off, vals, x, p, R, ptr<uint64_t>(m.hkeys),
                                           ptr<int32_t>(m.hvals), cap, ptr<int32_t>(m.mpad), n64,
                                           ptr<int32_t>(m.status), dmax, stw);
-  k_tri_sizes<<<ceil_div(G, 256), 256, 0, st>>>(n64, G, tri64, ptr<int32_t>(m.n));
+  launch(k_tri_sizes, ceil_div(G, 256), 256, 0, st, n64, G, tri64, ptr<int32_t>(m.n));
   KSDF_CUDA(c, scan_i64(n64, ptr<int64_t>(m.ts_off), G, dtot, c->ws[WS_SCAN], st));
   KSDF_CUDA(c, scan_i64(tri64, ptr<int64_t>(m.linv_off), G, dtot + 1, c->ws[WS_SCAN], st));
   int64_t tots[2];
@@ -453,6 +456,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   m.max_n = hmax[0];
   KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.ts_off) + G, &tots[0], sizeof(int64_t), cudaMemcpyHostToDevice, st));
   KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.linv_off) + G, &tots[1], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  prof_end(c, e0, "fit.assemble");
   // 4. member arrays
   const int64_t M = m.M;
   m.has_normals = nrm != nullptr;
@@ -464,7 +468,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, ensure(m.linv64, sizeof(double) * (m.linv_total + 1)));
   KSDF_CUDA(c, ensure(m.linv32, sizeof(float) * (m.linv_total + 1)));
   KSDF_CUDA(c, ensure(m.linv32lo, sizeof(float) * (m.linv_total + 1)));
-  k_gather_members<<<ceil_div(G * p.n_max, 256), 256, 0, st>>>(
+  launch(k_gather_members, ceil_div(G * p.n_max, 256), 256, 0, st, 
       ptr<uint64_t>(m.key), ptr<int32_t>(m.n), ptr<int64_t>(m.ts_off), ptr<int32_t>(m.mpad), G, p, x, var, nrm,
       ptr<int32_t>(m.mgid), ptr<D4>(m.md4), ptr<float4>(m.mf4), ptr<float>(m.mvar),
       nrm ? ptr<float4>(m.mnrm) : nullptr);
@@ -473,7 +477,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, ensure(m.cell_order, sizeof(uint32_t) * (G + 1)));
   uint64_t* okeys = ptr<uint64_t>(c->ws[WS_A]);
   uint32_t* order = ptr<uint32_t>(m.cell_order);
-  k_order_keys<<<ceil_div(G, 256), 256, 0, st>>>(ptr<int32_t>(m.n), G, p.n_max, okeys, order);
+  launch(k_order_keys, ceil_div(G, 256), 256, 0, st, ptr<int32_t>(m.n), G, p.n_max, okeys, order);
   KSDF_CUDA(c, radix_sort_u64(okeys, order, G, bits_for((uint64_t)p.n_max), c->ws[WS_SORT], st));
   const int nblk = (int)std::min<int64_t>(G, 2LL * c->num_sms);
   const int64_t stride = (m.max_n > kFitSmemN) ? tri(m.max_n) : 0;
@@ -481,18 +485,21 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   const size_t smem = sizeof(double) * (4 * (size_t)p.n_max + tri(kFitSmemN));
   KSDF_CUDA(c, cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
-  k_fit<<<nblk, kFitThreads, smem, st>>>(order, G, ptr<int32_t>(m.n), ptr<int64_t>(m.ts_off),
+  e0 = prof_begin(c);
+  launch(k_fit, nblk, kFitThreads, smem, st, order, G, ptr<int32_t>(m.n), ptr<int64_t>(m.ts_off),
                                          ptr<int64_t>(m.linv_off), p, ptr<D4>(m.md4), ptr<float4>(m.mf4),
                                          ptr<float>(m.mvar), ptr<double>(m.linv64), ptr<float>(m.linv32),
                                          ptr<float>(m.linv32lo), ptr<int32_t>(m.status),
                                          ptr<double>(c->ws[WS_FITSCR]), stride, dmax, dmax + 1, stw);
   KSDF_CUDA(c, cudaGetLastError());
+  prof_end(c, e0, "fit.cholesky");
   KSDF_CUDA(c, cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st));
   KSDF_CUDA(c, cudaStreamSynchronize(st));
   m.n_not_pd = hmax[1];
   // keep the sample positions for the adjoint's per-cell recomputation
   KSDF_CUDA(c, ensure(m.x, sizeof(double) * S * p.dim));
   KSDF_CUDA(c, cudaMemcpyAsync(m.x.p, x, sizeof(double) * S * p.dim, cudaMemcpyDeviceToDevice, st));
+  prof_end(c, e_fit, "fit");
   c->fitted = true;
   if (m.n_not_pd > 0)
     return set_err(c, KSDF_ERR_NOT_PD, "ksdf_fit: %d cell(s) not positive definite in FP64 (excluded)", m.n_not_pd);
@@ -513,7 +520,7 @@ __global__ void k_bin_keys(const double* x, int64_t n, Params p, uint64_t* keys,
 
 ksdf_status bin_points(ksdf_ctx* c, const double* x, int64_t n, uint64_t* keys) {
   if (n <= 0) return KSDF_OK;
-  k_bin_keys<<<ceil_div(n, 256), 256, 0, c->stream>>>(x, n, c->p, keys, ptr<uint32_t>(c->status_word));
+  launch(k_bin_keys, ceil_div(n, 256), 256, 0, c->stream, x, n, c->p, keys, ptr<uint32_t>(c->status_word));
   KSDF_CUDA(c, cudaGetLastError());
   return KSDF_OK;
 }

@@ -5,7 +5,10 @@
 
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/ksdf.h"
 
@@ -138,6 +141,17 @@ struct ksdf_ctx {
   ksdf::DevBuf stage[12];         // staging of host arrays
   int64_t reserved_q = 0, reserved_s = 0;
   int bb[6] = {0, 0, 0, 0, 0, 0};  // bounding box of the cells: min xyz, max xyz
+  // stage profiling (ksdf_profile): event pairs recorded on the stream, folded into totals when read
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<std::string> stage_names;
+  std::vector<double> stage_ms;
+  std::vector<long long> stage_calls;
 };
 
 namespace ksdf {
@@ -154,6 +168,10 @@ ksdf_status cuda_err(ksdf_ctx* c, cudaError_t e, const char* what);
 cudaError_t ensure(DevBuf& b, size_t bytes);
 void release(DevBuf& b);
 template <class T> inline T* ptr(DevBuf& b) { return static_cast<T*>(b.p); }
+
+// ---- stage profiling (ksdf_abi.cu): no-ops unless enabled ----
+cudaEvent_t prof_begin(ksdf_ctx* c);
+void prof_end(ksdf_ctx* c, cudaEvent_t a, const char* name);
 
 // ---- sorting and scanning (ksdf_sort.cu) ----
 // exclusive scan of n int64 values (in may equal out); total (optional) gets the sum on the device.
@@ -204,5 +222,13 @@ enum WsRole {
 };
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// every kernel launch of the library goes through launch(): it counts launches (ksdf_profile_read)
+extern std::atomic<long long> g_launches;
+template <class... KArgs, class... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+}
 
 }  // namespace ksdf

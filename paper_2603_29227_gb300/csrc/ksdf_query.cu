@@ -919,7 +919,7 @@ static CandCtx cand_ctx(ksdf_ctx* c) {
 ksdf_status candidates_for_keys(ksdf_ctx* c, const uint64_t* keys, int64_t n, int32_t* cand, int32_t* count) {
   if (n <= 0) return KSDF_OK;
   const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, kCandWarps), 8LL * c->num_sms);
-  k_candidates<<<grid, 32 * kCandWarps, 0, c->stream>>>(keys, nullptr, n, cand_ctx(c), cand, count);
+  launch(k_candidates, grid, 32 * kCandWarps, 0, c->stream, keys, nullptr, n, cand_ctx(c), cand, count);
   KSDF_CUDA(c, cudaGetLastError());
   return KSDF_OK;
 }
@@ -998,30 +998,35 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   int64_t* wtoff = cbuf + 3 * G;
   int* counters = reinterpret_cast<int*>(totals + 6);
 
+  cudaEvent_t e_q = prof_begin(c), e0 = prof_begin(c);
   // Q1 (kEmptyKey is all ones)
   KSDF_CUDA(c, cudaMemsetAsync(bhk, 0xFF, sizeof(uint64_t) * bcap, st));
   KSDF_CUDA(c, cudaMemsetAsync(bin_cnt, 0, sizeof(int64_t) * bcap, st));
   KSDF_CUDA(c, cudaMemsetAsync(totals, 0, sizeof(int64_t) * 8, st));
   KSDF_CUDA(c, cudaMemsetAsync(wcnt, 0, sizeof(int64_t) * G, st));
   if (f64)
-    k_q_bin<double><<<ceil_div(Q, 256), 256, 0, st>>>(static_cast<const double*>(xq), Q, p, qkey, bhk, bcap, stw);
+    launch(k_q_bin<double>, ceil_div(Q, 256), 256, 0, st, static_cast<const double*>(xq), Q, p, qkey, bhk, bcap, stw);
   else
-    k_q_bin<float><<<ceil_div(Q, 256), 256, 0, st>>>(static_cast<const float*>(xq), Q, p, qkey, bhk, bcap, stw);
+    launch(k_q_bin<float>, ceil_div(Q, 256), 256, 0, st, static_cast<const float*>(xq), Q, p, qkey, bhk, bcap, stw);
   // Q2
-  k_slot_flags<<<ceil_div(bcap, 256), 256, 0, st>>>(bhk, bcap, slot_id);
+  launch(k_slot_flags, ceil_div(bcap, 256), 256, 0, st, bhk, bcap, slot_id);
   KSDF_CUDA(c, scan_i64(slot_id, slot_id, bcap, &totals[0], c->ws[WS_SCAN], st));
-  k_bin_table<<<ceil_div(bcap, 256), 256, 0, st>>>(bhk, bcap, slot_id, bin_key);
-  k_q_rank<<<ceil_div(Q, 256), 256, 0, st>>>(qkey, Q, bhk, slot_id, bcap, qbin, qrank, bin_cnt);
+  launch(k_bin_table, ceil_div(bcap, 256), 256, 0, st, bhk, bcap, slot_id, bin_key);
+  launch(k_q_rank, ceil_div(Q, 256), 256, 0, st, qkey, Q, bhk, slot_id, bcap, qbin, qrank, bin_cnt);
   KSDF_CUDA(c, scan_i64(bin_cnt, bin_off, bcap, &totals[1], c->ws[WS_SCAN], st));
-  k_ntiles<<<ceil_div(bcap, 256), 256, 0, st>>>(bin_cnt, bcap, kTA, bin_nt);
+  launch(k_ntiles, ceil_div(bcap, 256), 256, 0, st, bin_cnt, bcap, kTA, bin_nt);
   KSDF_CUDA(c, scan_i64(bin_nt, bin_toff, bcap, &totals[2], c->ws[WS_SCAN], st));
-  k_scatter_grouped<<<ceil_div(Q, 256), 256, 0, st>>>(qbin, qrank, Q, bin_off, qsort);
-  k_make_tiles<<<ceil_div(bcap, 256), 256, 0, st>>>(bin_cnt, bin_off, bin_toff, bcap, kTA, tiles_a);
+  launch(k_scatter_grouped, ceil_div(Q, 256), 256, 0, st, qbin, qrank, Q, bin_off, qsort);
+  launch(k_make_tiles, ceil_div(bcap, 256), 256, 0, st, bin_cnt, bin_off, bin_toff, bcap, kTA, tiles_a);
+  prof_end(c, e0, "query.group");
+  e0 = prof_begin(c);
   // Q3
   {
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(bcap, kCandWarps), 8LL * c->num_sms);
-    k_candidates<<<grid, 32 * kCandWarps, 0, st>>>(bin_key, &totals[0], 0, cand_ctx(c), cand, ncand);
+    launch(k_candidates, grid, 32 * kCandWarps, 0, st, bin_key, &totals[0], 0, cand_ctx(c), cand, ncand);
   }
+  prof_end(c, e0, "query.candidates");
+  e0 = prof_begin(c);
   // Q4
   PhaseAArgs pa;
   pa.tiles = tiles_a;
@@ -1047,32 +1052,36 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseA64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA64, kTA, smem));
-    k_phaseA64<<<std::max(1, occ) * c->num_sms, kTA, smem, st>>>(pa, static_cast<const double*>(xq), p);
+    launch(k_phaseA64, std::max(1, occ) * c->num_sms, kTA, smem, st, pa, static_cast<const double*>(xq), p);
   } else {
     const size_t smem = sizeof(float4) * (size_t)p.K * maxn;
     KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA, kTA, smem));
-    k_phaseA<<<std::max(1, occ) * c->num_sms, kTA, smem, st>>>(pa, static_cast<const float*>(xq), p);
+    launch(k_phaseA, std::max(1, occ) * c->num_sms, kTA, smem, st, pa, static_cast<const float*>(xq), p);
   }
   KSDF_CUDA(c, cudaGetLastError());
+  prof_end(c, e0, f64 ? "query64.phaseA" : "query.phaseA");
+  e0 = prof_begin(c);
   // Q5
   int32_t* wrank = qrank;  // qrank no longer needed
   if (f64)
-    k_w_rank<double><<<ceil_div(Q, 256), 256, 0, st>>>(qwin, qflag, qbin, Q, wrank, wcnt, mask, p.dim,
+    launch(k_w_rank<double>, ceil_div(Q, 256), 256, 0, st, qwin, qflag, qbin, Q, wrank, wcnt, mask, p.dim,
                                                         static_cast<double*>(sdf), static_cast<double*>(grad),
                                                         static_cast<double*>(var_sdf), static_cast<double*>(var_f),
                                                         winner, flags);
   else
-    k_w_rank<float><<<ceil_div(Q, 256), 256, 0, st>>>(qwin, qflag, qbin, Q, wrank, wcnt, mask, p.dim,
+    launch(k_w_rank<float>, ceil_div(Q, 256), 256, 0, st, qwin, qflag, qbin, Q, wrank, wcnt, mask, p.dim,
                                                        static_cast<float*>(sdf), static_cast<float*>(grad),
                                                        static_cast<float*>(var_sdf), static_cast<float*>(var_f),
                                                        winner, flags);
   KSDF_CUDA(c, scan_i64(wcnt, woff, G, nullptr, c->ws[WS_SCAN], st));
-  k_ntiles<<<ceil_div(G, 256), 256, 0, st>>>(wcnt, G, TBq, wnt);
+  launch(k_ntiles, ceil_div(G, 256), 256, 0, st, wcnt, G, TBq, wnt);
   KSDF_CUDA(c, scan_i64(wnt, wtoff, G, &totals[3], c->ws[WS_SCAN], st));
-  k_w_scatter<<<ceil_div(Q, 256), 256, 0, st>>>(qwin, qbin, wrank, Q, woff, qwsort);
-  k_make_tiles<<<ceil_div(G, 256), 256, 0, st>>>(wcnt, woff, wtoff, G, TBq, tiles_b);
+  launch(k_w_scatter, ceil_div(Q, 256), 256, 0, st, qwin, qbin, wrank, Q, woff, qwsort);
+  launch(k_make_tiles, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, G, TBq, tiles_b);
+  prof_end(c, e0, "query.regroup");
+  e0 = prof_begin(c);
   // Q6
   PhaseBArgs pb;
   pb.tiles = tiles_b;
@@ -1102,7 +1111,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB64, kTB64, smem));
-    k_phaseB64<<<std::max(1, occ) * c->num_sms, kTB64, smem, st>>>(
+    launch(k_phaseB64, std::max(1, occ) * c->num_sms, kTB64, smem, st, 
         pb, static_cast<const double*>(xq), p, static_cast<double*>(sdf), static_cast<double*>(grad),
         static_cast<double*>(var_sdf), static_cast<double*>(var_f), winner, flags);
   } else {
@@ -1110,11 +1119,13 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB, kTB, smem));
-    k_phaseB<<<std::max(1, occ) * c->num_sms, kTB, smem, st>>>(
+    launch(k_phaseB, std::max(1, occ) * c->num_sms, kTB, smem, st, 
         pb, static_cast<const float*>(xq), p, static_cast<float*>(sdf), static_cast<float*>(grad),
         static_cast<float*>(var_sdf), static_cast<float*>(var_f), winner, flags);
   }
   KSDF_CUDA(c, cudaGetLastError());
+  prof_end(c, e0, f64 ? "query64.phaseB" : "query.phaseB");
+  prof_end(c, e_q, f64 ? "query64" : "query");
   return KSDF_OK;
 }
 

@@ -156,9 +156,9 @@ cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
   cudaError_t e = ensure(tmp, sizeof(int64_t) * (size_t)(nb + 1));
   if (e != cudaSuccess) return e;
   int64_t* sums = ptr<int64_t>(tmp);
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
-  k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb, total);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
+  launch(k_scan_reduce, (unsigned)nb, kScanThreads, 0, st, in, n, sums);
+  launch(k_scan_sums, 1, kScanThreads, 0, st, sums, nb, total);
+  launch(k_scan_apply, (unsigned)nb, kScanThreads, 0, st, in, out, n, sums);
   return cudaGetLastError();
 }
 
@@ -183,11 +183,11 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, 
   uint32_t *vi = vals, *vo = v2;
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
-    k_rs_hist<<<nblocks, kRsThreads, 0, st>>>(ki, n, shift, hist, nblocks);
-    k_scan_reduce<<<(unsigned)nb_scan, kScanThreads, 0, st>>>(hist, nh, sums);
-    k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb_scan, nullptr);
-    k_scan_apply<<<(unsigned)nb_scan, kScanThreads, 0, st>>>(hist, hist, nh, sums);
-    k_rs_scatter<<<nblocks, kRsThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, nblocks);
+    launch(k_rs_hist, nblocks, kRsThreads, 0, st, ki, n, shift, hist, nblocks);
+    launch(k_scan_reduce, (unsigned)nb_scan, kScanThreads, 0, st, hist, nh, sums);
+    launch(k_scan_sums, 1, kScanThreads, 0, st, sums, nb_scan, nullptr);
+    launch(k_scan_apply, (unsigned)nb_scan, kScanThreads, 0, st, hist, hist, nh, sums);
+    launch(k_rs_scatter, nblocks, kRsThreads, 0, st, ki, vi, ko, vo, n, shift, hist, nblocks);
     uint64_t* tk = ki; ki = ko; ko = tk;
     uint32_t* tv = vi; vi = vo; vo = tv;
   }

@@ -28,7 +28,7 @@ CELL_OK, CELL_EMPTY, CELL_NOT_PD = 0, 1, 2
 # every entry point declared in include/ksdf.h
 ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_query",
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
-                 "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates")
+                 "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read")
 
 
 class KsdfError(RuntimeError):
@@ -71,6 +71,8 @@ def load(path: str = LIB_PATH):
         "ksdf_get_fit": [P, P, P],
         "ksdf_bin": [P, P, I64, P],
         "ksdf_candidates": [P, P, I64, P, P],
+        "ksdf_profile": [P, ctypes.c_int],
+        "ksdf_profile_read": [P, ctypes.c_int, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(I64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +225,27 @@ def ksdf_bin(h, x, n, keys):
 def ksdf_candidates(h, keys, n, cand, count):
     _check(h, load().ksdf_candidates(h, _ptr(keys, np.uint64), int(n), _ptr(cand, np.int32), _ptr(count, np.int32)),
            "ksdf_candidates")
+
+
+def ksdf_profile(h, enable):
+    _check(h, load().ksdf_profile(h, int(bool(enable))), "ksdf_profile")
+
+
+def ksdf_profile_read(h, max_stages=64):
+    """{stage: (total_ms, calls)}, launches"""
+    names = ctypes.create_string_buffer(32 * max_stages)
+    ms = np.zeros(max_stages)
+    calls = np.zeros(max_stages, np.int64)
+    n = ctypes.c_int()
+    launches = ctypes.c_int64()
+    _check(h, load().ksdf_profile_read(h, max_stages, ctypes.addressof(names), _ptr(ms), _ptr(calls),
+                                       ctypes.byref(n), ctypes.byref(launches)), "ksdf_profile_read")
+    raw = names.raw
+    out = {}
+    for i in range(min(n.value, max_stages)):
+        name = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[name] = (float(ms[i]), int(calls[i]))
+    return out, launches.value
 
 
 # ---- convenience wrapper over one context (torch tensors) ----
