@@ -176,6 +176,35 @@ ksdf_status ksdf_profile(ksdf_ctx* ctx, int enable);
 ksdf_status ksdf_profile_read(ksdf_ctx* ctx, int max_stages, char* names, double* total_ms, int64_t* calls,
                               int* n_stages, int64_t* launches);
 
+/* ---- fit of one local GP without any device allocation (the paper has no counterpart: this serves
+ * callers that cannot allocate device memory) ----
+ *
+ * Who needs it: a real-time loop (a planner or controller that must not enter the CUDA allocator once it
+ * runs, because an allocation can block for an unbounded time and may synchronise the device), or a
+ * program whose device memory is all owned by another allocator.  Neither can create a context
+ * (ksdf_create allocates), so this call takes no context and allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ *
+ * What it computes: the FP64 fit of one training set, exactly as ksdf_fit does for one cell --
+ * A = K + diag(sigma^2) with K_ij = exp(-lambda |x_i - x_j|^2), A = L L^T, alpha = A^{-1} 1 (all labels 1),
+ * and L^{-1} -- with params->dim and params->lambda (the other fields are not used).
+ *   x       device, N x dim float64 positions (read)
+ *   var     device, N float32 sigma_i^2 >= 0 (read; NULL means 0)
+ *   alpha   device, N float64 (written; zeros if A is not positive definite)
+ *   linv    device, N (N+1) / 2 float64, L^{-1} as packed lower rows (written; unspecified if not PD)
+ *   status  device, one int32: KSDF_CELL_OK or KSDF_CELL_NOT_PD (written by the kernel)
+ *   stream  cudaStream_t the kernel is launched on (NULL = legacy default); the call is asynchronous
+ * Every array must be device (or managed) memory: host arrays give KSDF_ERR_ARG, because copying them
+ * would need an allocation.  N must be 1..512: larger N gives KSDF_ERR_CAPACITY.
+ * Scratch: a static 1,050,624-byte device array (the packed matrix for N = 512), which every GPU that
+ * loads the library holds until the process exits.  All calls on a device share it and it keeps the last
+ * call's contents (nothing in it needs to start at zero), so calls that overlap on the GPU -- on different
+ * streams, or from different host threads, without ordering between them -- race and give wrong results.
+ * The first call on each device resolves the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture. */
+ksdf_status ksdf_fit_gp_noalloc(const ksdf_params* params, const double* x, const float* var, int64_t N,
+                                double* alpha, double* linv, int32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

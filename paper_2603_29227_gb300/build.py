@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libksdf.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["ksdf_abi.cu", "ksdf_sort.cu", "ksdf_fit.cu", "ksdf_query.cu", "ksdf_backward.cu"]
+SOURCES = ["ksdf_abi.cu", "ksdf_sort.cu", "ksdf_fit.cu", "ksdf_query.cu", "ksdf_backward.cu", "ksdf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas",
          "-warn-spills"]

@@ -28,7 +28,8 @@ CELL_OK, CELL_EMPTY, CELL_NOT_PD = 0, 1, 2
 # every entry point declared in include/ksdf.h
 ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_query",
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
-                 "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read")
+                 "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
+                 "ksdf_fit_gp_noalloc")
 
 
 class KsdfError(RuntimeError):
@@ -73,6 +74,7 @@ def load(path: str = LIB_PATH):
         "ksdf_candidates": [P, P, I64, P, P],
         "ksdf_profile": [P, ctypes.c_int],
         "ksdf_profile_read": [P, ctypes.c_int, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(I64)],
+        "ksdf_fit_gp_noalloc": [ctypes.POINTER(ksdf_params), P, P, I64, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -246,6 +248,14 @@ def ksdf_profile_read(h, max_stages=64):
         name = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
         out[name] = (float(ms[i]), int(calls[i]))
     return out, launches.value
+
+
+def ksdf_fit_gp_noalloc(params: dict, x, var, N, alpha, linv, status, stream=None):
+    """Fit of one training set with no device allocation (device arrays only); asynchronous on `stream`."""
+    pr = make_params(params)
+    rc = load().ksdf_fit_gp_noalloc(ctypes.byref(pr), _ptr(x, np.float64), _ptr(var, np.float32), int(N),
+                                    _ptr(alpha, np.float64), _ptr(linv, np.float64), _ptr(status, np.int32), stream)
+    _check(None, rc, "ksdf_fit_gp_noalloc")
 
 
 # ---- convenience wrapper over one context (torch tensors) ----
