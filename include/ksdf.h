@@ -110,8 +110,10 @@ ksdf_status ksdf_set_stream(ksdf_ctx* ctx, void* stream);
 ksdf_status ksdf_reserve(ksdf_ctx* ctx, int64_t max_samples, int64_t max_queries);
 
 /* Fit (Sec. IV-B.1): bin the S samples x (S x dim, float64) into cells, assemble every cell's training
- * set from its collection box, build A = K + diag(sigma^2) (var: S float32 sigma_i^2 >= 0, NULL = 0),
- * factor A = L L^T in FP64, and store alpha = A^{-1} 1 and L^{-1} in FP64 and FP32.  normals (S x dim
+ * set from its collection box, build A = K + diag(sigma^2) (var: S float32 sigma_i^2 >= 0, NULL = 0) in
+ * FP64, factor A = L L^T in FP64 and solve alpha = A^{-1} 1 in FP64 (kept in FP64 and FP32); L is kept in
+ * FP64 for the plain query and the adjoint, and L^{-1} is formed in FP32 from L for the mixed query's
+ * variance contraction.  normals (S x dim
  * float32, may be NULL) feed the sign stand-in.  Replaces any previous model.  Synchronises the stream
  * (cell counts decide allocation sizes).  Returns KSDF_ERR_NONFINITE for NaN/Inf/out-of-grid samples
  * or a negative variance, KSDF_ERR_CAPACITY if a collection box holds more than 8192 samples before
@@ -119,8 +121,8 @@ ksdf_status ksdf_reserve(ksdf_ctx* ctx, int64_t max_samples, int64_t max_queries
 ksdf_status ksdf_fit(ksdf_ctx* ctx, const double* x, const float* var, const float* normals, int64_t S);
 
 /* Mixed-precision query: Q points xq (Q x dim float32); sign (Q int8, +1/-1, may be NULL).  FP32 SIMT
- * arithmetic in cell-local coordinates for the mean (compensated sum), gradient and softmin variance;
- * the GP variance contraction is computed from L^{-1} stored as FP32 hi + lo.  Outputs (selected by
+ * arithmetic in cell-local coordinates for the mean (compensated sum), gradient and softmin variance,
+ * and for the GP variance contraction with the FP32 L^{-1}.  Outputs (selected by
  * out_mask): sdf[Q], grad[Q x dim] (gradient of d = s grad u), var_sdf[Q] (V[u], Sec. IV-B.3),
  * var_f[Q] (V[f], Sec. IV-B.1), winner[Q] (cell id of the fused GP, -1 if none; keep it for the
  * backward), flags[Q] (KSDF_FLAG_*). */
@@ -152,9 +154,12 @@ ksdf_status ksdf_model_size(ksdf_ctx* ctx, int64_t* n_cells, int64_t* n_members)
 /* keys[G] (packed (cz,cy,cx) as three biased 21-bit fields, z most significant), status[G], ts_off[G+1],
  * members[n_members] (global sample ids, ascending within a cell).  Any pointer may be NULL. */
 ksdf_status ksdf_get_cells(ksdf_ctx* ctx, uint64_t* keys, int32_t* status, int64_t* ts_off, int64_t* members);
-/* alpha (n_members, float64) in training-set order; linv (sum N_g (N_g+1)/2, float64) packed row-major
- * lower triangle per cell, cells in id order.  Either may be NULL. */
-ksdf_status ksdf_get_fit(ksdf_ctx* ctx, double* alpha, double* linv);
+/* alpha (n_members, float64) in training-set order; chol (sum N_g (N_g+1)/2, float64) the Cholesky factor
+ * L of each cell as packed lower rows (row i at offset i (i+1)/2), cells in id order; linv (sum 32 nb (nb+1),
+ * nb = ceil(N_g / 8), float32) L^{-1} of each cell in 8-row blocks: block R holds, for every column
+ * j <= 8R+7, the eight values L^{-1}[8R+r][j], r = 0..7 (zero above the diagonal and past row N_g-1),
+ * block R starting at 32 R (R+1).  Any pointer may be NULL. */
+ksdf_status ksdf_get_fit(ksdf_ctx* ctx, double* alpha, double* chol, float* linv);
 /* Packed keys of points (n x dim float64) and the candidate lists (n x K int32, -1 padded; count[n]) of the
  * cells those keys name.  Device or host arrays. */
 ksdf_status ksdf_bin(ksdf_ctx* ctx, const double* x, int64_t n, uint64_t* keys);

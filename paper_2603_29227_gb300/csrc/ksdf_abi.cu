@@ -96,6 +96,28 @@ static void prof_fold(ksdf_ctx* c) {
   c->pending.clear();
 }
 
+cudaError_t fork_streams(ksdf_ctx* c) {
+  cudaError_t e = cudaSuccess;
+  if (!c->aux[0]) {
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaEventRecord(c->ev_fork, c->stream);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->aux[i], c->ev_fork, 0);
+  return e;
+}
+
+cudaError_t join_streams(ksdf_ctx* c) {
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(c->ev_join[i], c->aux[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join[i], 0);
+  }
+  return e;
+}
+
 namespace {
 
 bool on_device(const void* p) {
@@ -202,9 +224,9 @@ ksdf_status ksdf_destroy(ksdf_ctx* c) {
   if (!c) return KSDF_ERR_ARG;
   cudaStreamSynchronize(c->stream);
   Model& m = c->m;
-  DevBuf* bufs[] = {&m.key, &m.status, &m.n, &m.ts_off, &m.linv_off, &m.hkeys, &m.hvals, &m.cell_order, &m.mf4,
-                    &m.md4, &m.mvar, &m.mnrm, &m.mgid, &m.mpad, &m.linv64, &m.linv32, &m.linv32lo, &m.x,
-                    &c->status_word};
+  DevBuf* bufs[] = {&m.key,  &m.status, &m.n,    &m.ts_off, &m.chol_off, &m.linv_off, &m.hkeys,
+                    &m.hvals, &m.cell_order, &m.mf4, &m.md4, &m.mvar,   &m.mnrm,     &m.mgid,     &m.mpad,
+                    &m.chol64, &m.linv32, &m.x,   &c->status_word};
   for (DevBuf* b : bufs) release(*b);
   for (auto& b : c->ws) release(b);
   for (auto& b : c->stage) release(b);
@@ -213,6 +235,11 @@ ksdf_status ksdf_destroy(ksdf_ctx* c) {
     cudaEventDestroy(p.b);
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  for (int i = 0; i < 2; ++i) {
+    if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+    if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
   return KSDF_OK;
 }
@@ -383,7 +410,7 @@ ksdf_status ksdf_get_cells(ksdf_ctx* c, uint64_t* keys, int32_t* status, int64_t
   return KSDF_OK;
 }
 
-ksdf_status ksdf_get_fit(ksdf_ctx* c, double* alpha, double* linv) {
+ksdf_status ksdf_get_fit(ksdf_ctx* c, double* alpha, double* chol, float* linv) {
   if (!c) return KSDF_ERR_ARG;
   if (!c->fitted) return KSDF_ERR_NOT_FITTED;
   Model& m = c->m;
@@ -395,8 +422,10 @@ ksdf_status ksdf_get_fit(ksdf_ctx* c, double* alpha, double* linv) {
     for (int64_t i = 0; i < m.M; ++i) a[i] = tmp[i].w;
     KSDF_CUDA(c, cudaMemcpy(alpha, a.data(), sizeof(double) * m.M, cudaMemcpyDefault));
   }
+  if (chol && m.chol_total)
+    KSDF_CUDA(c, cudaMemcpy(chol, m.chol64.p, sizeof(double) * m.chol_total, cudaMemcpyDefault));
   if (linv && m.linv_total)
-    KSDF_CUDA(c, cudaMemcpy(linv, m.linv64.p, sizeof(double) * m.linv_total, cudaMemcpyDefault));
+    KSDF_CUDA(c, cudaMemcpy(linv, m.linv32.p, sizeof(float) * m.linv_total, cudaMemcpyDefault));
   return KSDF_OK;
 }
 

@@ -10,8 +10,8 @@
 // For the gradient output s G/|G| with cotangent gb: v = s (I - g g^T) gb / |G|, and
 //   x_bar += sum_i alpha_i k'_i (v - 2 lambda r_i (r_i . v)),  X_bar_i -= the i-th term,
 //   alpha_bar_i += k'_i (r_i . v).
-// Through alpha = A^{-1} 1 (A = K + Sigma): b = A^{-1} alpha_bar = L^{-T} L^{-1} alpha_bar (FP64, with the
-// stored L^{-1}), X_bar_i += sum_j 2 lambda K_ij (b_i alpha_j + b_j alpha_i)(x_i - x_j).
+// Through alpha = A^{-1} 1 (A = K + Sigma = L L^T): b = A^{-1} alpha_bar (FP32 L^{-1} products with one
+// FP64 refinement step against L), X_bar_i += sum_j 2 lambda K_ij (b_i alpha_j + b_j alpha_i)(x_i - x_j).
 // Kernel 1 recomputes k' per (query, winner) tile and reduces alpha_bar / X_bar in shared memory; kernel 2
 // runs once per touched cell.
 #include "ksdf_internal.cuh"
@@ -99,6 +99,7 @@ __device__ inline float warp_sum(float v) {
 __global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Params p) {
   extern __shared__ __align__(16) float4 s_x[];  // [n_max] samples, then [n_max][4] accumulators
   __shared__ int s_tile;
+  __shared__ float s_bh[3], s_bl[3];
   float* s_acc = reinterpret_cast<float*>(s_x + p.n_max);
   const int tid = threadIdx.x, lane = tid & 31;
   const float lam = (float)p.lambda;
@@ -117,15 +118,17 @@ __global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Par
       s_x[i] = a.mf4[m0 + i];
       s_acc[4 * i] = s_acc[4 * i + 1] = s_acc[4 * i + 2] = s_acc[4 * i + 3] = 0.f;
     }
-    int cc[3];
-    unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
+    if (tid == 0) {
+      int cc[3];
+      unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
+      for (int j = 0; j < 3; ++j) base_split(p.o[j], cc[j], p.h, s_bh[j], s_bl[j]);
+    }
     const bool live = tid < tile.z;
     const int q = live ? a.sorted[tile.y + tid] : 0;
+    __syncthreads();
     float ql[3] = {0.f, 0.f, 0.f};
     if (live)
-      for (int j = 0; j < p.dim; ++j)
-        ql[j] = (float)__dsub_rn((double)xq[(int64_t)q * p.dim + j], cell_base(p.o[j], cc[j], p.h));
-    __syncthreads();
+      for (int j = 0; j < p.dim; ++j) ql[j] = local32(xq[(int64_t)q * p.dim + j], s_bh[j], s_bl[j]);
     // forward recomputation
     float m = INFINITY;
     int nn = 0;
@@ -252,49 +255,94 @@ __global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Par
   }
 }
 
-// per touched cell: b = L^{-T} L^{-1} alpha_bar (FP64), then the alpha-path X_bar terms
+// L^{-1}[j][i] (i <= 8 floor(j/8) + 7) in the 8-row blocked FP32 layout
+__device__ __forceinline__ float linv_at(const float* Lb, int j, int i) {
+  const int R = j >> 3;
+  return Lb[linv_block_off(R) + (int64_t)i * 8 + (j & 7)];
+}
+
+// per touched cell: b = A^{-1} alpha_bar.  b0 = L^{-T} L^{-1} alpha_bar with the FP32 L^{-1}; one step of
+// iterative refinement against the FP64 factor, r = alpha_bar - L (L^T b0) (the only FP64 work, N^2
+// FMAs), b = b0 + L^{-T} L^{-1} r; then the alpha-path X_bar terms in FP32.
+__device__ void linv_solve32(const float* Lb, int n, const float* rhs, float* y, float* out, bool add) {
+  // y = L^{-1} rhs (rows over threads; 8 consecutive rows share a 32-byte sector per column)
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const float* row = Lb + linv_block_off(j >> 3) + (j & 7);
+    float acc = 0.f;
+    for (int i = 0; i <= j; ++i) acc = fmaf(row[(int64_t)i * 8], rhs[i], acc);
+    y[j] = acc;
+  }
+  __syncthreads();
+  // out (+)= L^{-T} y (columns over threads; the 8 rows of a block at one column are contiguous)
+  const int nb = (n + 7) >> 3;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float acc = 0.f;
+    for (int R = i >> 3; R < nb; ++R) {
+      const float4* v = reinterpret_cast<const float4*>(Lb + linv_block_off(R) + (int64_t)i * 8);
+      const float4 l0 = __ldg(v), l1 = __ldg(v + 1);
+      const float* yy = y + 8 * R;
+      const int rmax = min(8, n - 8 * R);
+      const float lr[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+      for (int r = 0; r < rmax; ++r) acc = fmaf(lr[r], yy[r], acc);
+    }
+    out[i] = add ? out[i] + acc : acc;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) k_bw_cell(const int64_t* qcnt, int64_t G, const int64_t* ts_off,
-                                                 const int32_t* cell_n, const int64_t* linv_off, const double* linv64,
-                                                 const D4* md4, const float4* mf4, const int32_t* mgid,
-                                                 const double* abar, Params p, float* d_x) {
-  extern __shared__ double sh[];  // [n] abar, [n] y, [n] b
+                                                 const int32_t* cell_n, const int64_t* chol_off, const double* chol64,
+                                                 const int64_t* linv_off, const float* linv32, const float4* mf4,
+                                                 const int32_t* mgid, const double* abar, Params p, float* d_x) {
+  extern __shared__ double sh[];  // [n] alpha_bar (double), [n] t (double), then floats: rhs, y, b
   for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
     if (qcnt[g] == 0) continue;
     const int n = cell_n[g];
     const int64_t m0 = ts_off[g];
-    const double* L = linv64 + linv_off[g];
+    const double* L = chol64 + chol_off[g];
+    const float* Lb = linv32 + linv_off[g];
     double* sa = sh;
-    double* sy = sh + n;
-    double* sb = sh + 2 * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sa[i] = abar[m0 + i];
-    __syncthreads();
-    // y = L^{-1} abar (row j of the packed lower triangle)
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const double* r = L + (int64_t)j * (j + 1) / 2;
-      double acc = 0.0;
-      for (int i = 0; i <= j; ++i) acc = fma(r[i], sa[i], acc);
-      sy[j] = acc;
-    }
-    __syncthreads();
-    // b = L^{-T} y: b_i = sum_{j >= i} Linv_ji y_j
+    double* st = sh + n;
+    float* srhs = reinterpret_cast<float*>(sh + 2 * n);
+    float* sy = srhs + n;
+    float* sb = sy + n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      double acc = 0.0;
-      for (int j = i; j < n; ++j) acc = fma(L[(int64_t)j * (j + 1) / 2 + i], sy[j], acc);
-      sb[i] = acc;
+      sa[i] = abar[m0 + i];
+      srhs[i] = (float)sa[i];
     }
     __syncthreads();
+    linv_solve32(Lb, n, srhs, sy, sb, false);  // b0
+    // t = L^T b0: rows in lockstep, threads over columns k (coalesced row reads)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) st[k] = 0.0;
+    for (int k0 = 0; k0 < n; k0 += blockDim.x) {
+      const int k = k0 + threadIdx.x;
+      double acc = 0.0;
+      for (int i = k0; i < n; ++i)
+        if (k < n && k <= i) acc = fma(L[(int64_t)i * (i + 1) / 2 + k], (double)sb[i], acc);
+      if (k < n) st[k] = acc;
+    }
+    __syncthreads();
+    // r = alpha_bar - L t (rows over threads)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double* Li = L + (int64_t)i * (i + 1) / 2;
+      double acc = sa[i];
+      for (int k = 0; k <= i; ++k) acc = fma(-Li[k], st[k], acc);
+      srhs[i] = (float)acc;
+    }
+    __syncthreads();
+    linv_solve32(Lb, n, srhs, sy, sb, true);  // b = b0 + L^{-T} L^{-1} r
     const float c1 = (float)p.lambda * kLog2e;
     const float tl = 2.f * (float)p.lambda;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const float4 xi = mf4[m0 + i];
-      const double bi = sb[i], ai = md4[m0 + i].w;
+      const float bi = sb[i], ai = xi.w;
       float X0 = 0.f, X1 = 0.f, X2 = 0.f;
       for (int j = 0; j < n; ++j) {
         if (j == i) continue;
         const float4 xj = mf4[m0 + j];
         const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
         const float kij = ex2(-c1 * fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        const float cf = tl * kij * (float)(bi * md4[m0 + j].w + sb[j] * ai);
+        const float cf = tl * kij * fmaf(bi, xj.w, sb[j] * ai);
         X0 = fmaf(cf, dx, X0);
         X1 = fmaf(cf, dy, X1);
         X2 = fmaf(cf, dz, X2);
@@ -367,13 +415,12 @@ ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* 
   launch(k_bw_query, std::max(1, occ) * c->num_sms, kTW, smem, st, a, xq, p);
   prof_end(c, e0, "backward.query");
   e0 = prof_begin(c);
-  const size_t smem2 = sizeof(double) * 3 * p.n_max;
+  const size_t smem2 = sizeof(double) * 2 * p.n_max + sizeof(float) * 3 * p.n_max;
   KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
   const unsigned grid2 = (unsigned)std::min<int64_t>(G, 4LL * c->num_sms);
   launch(k_bw_cell, std::max(1u, grid2), 256, smem2, st, cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
-                                                     ptr<int64_t>(m.linv_off), ptr<double>(m.linv64),
-                                                     ptr<D4>(m.md4), ptr<float4>(m.mf4), ptr<int32_t>(m.mgid),
-                                                     abar, p, d_x);
+         ptr<int64_t>(m.chol_off), ptr<double>(m.chol64), ptr<int64_t>(m.linv_off), ptr<float>(m.linv32),
+         ptr<float4>(m.mf4), ptr<int32_t>(m.mgid), abar, p, d_x);
   KSDF_CUDA(c, cudaGetLastError());
   prof_end(c, e0, "backward.cell");
   prof_end(c, e_b, "backward");

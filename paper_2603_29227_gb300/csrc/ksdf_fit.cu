@@ -6,10 +6,12 @@
 //   3. training sets: one CTA per cell gathers the samples of the neighbouring cells that fall in its
 //      collection box [o + c h - mu, o + (c+1) h + mu) (binary64 compares), sorts them by global id in
 //      shared memory and keeps ranks floor(j cnt / n_max) when there are more than n_max;
-//   4. the FP64 fit: A = K + diag(sigma^2) with K_ij = exp(-lambda |x_i - x_j|^2), A = L L^T, alpha =
-//      A^{-1} 1 (all labels are 1), and L^{-1} by forward substitution on I.  Persistent CTAs take the
-//      cells in descending size order; the packed matrix lives in shared memory up to N = 128 and in a
-//      per-CTA global scratch slot above that.
+//   4. the fit: A = K + diag(sigma^2) with K_ij = exp(-lambda |x_i - x_j|^2) in FP64, the FP64 Cholesky
+//      factor A = L L^T (blocked, right looking) and alpha = A^{-1} 1 by two FP64 triangular solves (all
+//      labels are 1); L^{-1} for the variance contraction in FP32, from L rounded to FP32.  Persistent
+//      CTAs take the cells in descending size order, in four size classes launched concurrently: the
+//      packed matrix lives in shared memory up to N = 218 and in a per-CTA global scratch slot above that.
+#include "ksdf_exp.cuh"
 #include "ksdf_internal.cuh"
 
 #include <cstdarg>
@@ -19,8 +21,11 @@ namespace ksdf {
 
 namespace {
 
-constexpr int kFitThreads = 256;
-constexpr int kFitSmemN = 128;  // packed matrix in shared memory up to this N
+constexpr int kPanel = 16;    // Cholesky panel width
+constexpr int kClassS = 96;   // size classes: the packed FP64 matrix in shared memory up to N = 218
+constexpr int kClassM = 160;
+constexpr int kClassL = 218;
+constexpr int kClassXL = kMaxNmax;
 
 __global__ void k_bin_samples(const double* x, const float* var, int64_t S, Params p, uint64_t* keys, uint32_t* vals,
                               int* bbox, uint32_t* status) {
@@ -192,10 +197,11 @@ __global__ void __launch_bounds__(512) k_assemble(const uint64_t* cell_key, int6
   }
 }
 
-__global__ void k_tri_sizes(const int64_t* n, int64_t G, int64_t* tri, int32_t* n32) {
+__global__ void k_sizes(const int64_t* n, int64_t G, int64_t* tri, int64_t* lb, int32_t* n32) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
-  tri[g] = n[g] * (n[g] + 1) / 2;
+  tri[g] = tri_sz(n[g]);
+  lb[g] = linv_blocked_size(n[g]);
   n32[g] = (int32_t)n[g];
 }
 
@@ -209,8 +215,7 @@ __global__ void k_order_keys(const int32_t* n32, int64_t G, int n_max, uint64_t*
 // members: global id, cell-local FP64/FP32 coordinates, variance, normal
 __global__ void k_gather_members(const uint64_t* cell_key, const int32_t* n32, const int64_t* ts_off,
                                  const int32_t* mpad, int64_t G, Params p, const double* x, const float* var,
-                                 const float* nrm, int32_t* mgid, D4* md4, float4* mf4, float* mvar,
-                                 float4* mnrm) {
+                                 const float* nrm, int32_t* mgid, D4* md4, float4* mf4, float* mvar, float4* mnrm) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t g = t / p.n_max;
   int j = (int)(t % p.n_max);
@@ -232,126 +237,252 @@ __global__ void k_gather_members(const uint64_t* cell_key, const int32_t* n32, c
   }
 }
 
-__host__ __device__ inline int64_t tri(int i) { return (int64_t)i * (i + 1) / 2; }
+struct FitArgs {
+  const uint32_t* order;  // cells by descending N; this launch takes order[first .. first + count)
+  int64_t first, count;
+  const int32_t* n32;
+  const int64_t* ts_off;
+  const int64_t* chol_off;
+  const int64_t* linv_off;
+  D4* md4;
+  float4* mf4;
+  const float* mvar;
+  double* chol64;
+  float* linv32;
+  int32_t* status;
+  double* gscr;     // per-CTA global slot (largest class): tri(np) doubles
+  int64_t gstride;  // doubles per slot
+  int np;           // largest N of this class
+  int smem_mat;     // 1: the matrix lives in shared memory
+  int* counter;
+  int* n_not_pd;
+};
 
-// FP64 fit of one cell per CTA iteration (persistent, dynamic work counter)
-__global__ void __launch_bounds__(kFitThreads) k_fit(const uint32_t* order, int64_t G, const int32_t* n32,
-                                                     const int64_t* ts_off, const int64_t* linv_off, Params p,
-                                                     D4* md4, float4* mf4, const float* mvar, double* linv64,
-                                                     float* linv32, float* linv32lo, int32_t* status,
-                                                     double* scratch, int64_t scratch_stride, int* counter,
-                                                     int* n_not_pd, uint32_t* st) {
-  extern __shared__ double sm[];
+__device__ __forceinline__ int64_t P(int i, int j) { return tri_sz(i) + j; }
+
+// row of the packed lower-triangle entry t (t = i (i+1)/2 + j, j <= i)
+__device__ __forceinline__ int tri_row(int64_t t) {
+  int i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while (tri_sz(i + 1) <= t) ++i;
+  while (tri_sz(i) > t) --i;
+  return i;
+}
+
+__device__ __forceinline__ double kernel_entry(const double* sx, int i, int j, double lam, const double* tab) {
+  const double dx = sx[3 * i] - sx[3 * j], dy = sx[3 * i + 1] - sx[3 * j + 1], dz = sx[3 * i + 2] - sx[3 * j + 2];
+  const double e = lam * (dx * dx + dy * dy + dz * dz);
+  return e > 50.0 ? 0.0 : exp_neg64(-e, tab);  // entries below e^-50 ~ 2e-22 are zero
+}
+
+constexpr int kInvRows = 2;  // rows per thread in the FP32 inversion (N <= 2 * blockDim.x)
+
+// One cell per iteration of a persistent CTA:
+//   A = K + diag(sigma^2) (FP64, packed lower), blocked Cholesky (FP64: 16-column panels factored by warp 0
+//   with rsqrt pivots, trailing updates in 2x2 register blocks by the whole CTA), alpha by two FP64
+//   triangular solves (warp 0) while the other warps copy L out; then L is converted in place to FP32 and
+//   inverted column by column (all threads), and L^{-1} is written in 8-row blocks.
+__global__ void __launch_bounds__(256) k_fit(FitArgs a, Params p) {
+  extern __shared__ __align__(16) double sm[];
   __shared__ int s_cell, s_fail;
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-  // shared layout: [xyz: 3 * n_max][b: n_max][A packed: tri(kFitSmemN) if used]
-  double* sx = sm;
-  double* sb = sx + 3 * p.n_max;
-  double* sA = sb + p.n_max;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  double* tab = sm;
+  double* dinv = tab + 32;
+  double* sx = dinv + a.np;
+  double* sb = sx + 3 * a.np;
+  double* A = a.smem_mat ? sb + a.np : a.gscr + (int64_t)blockIdx.x * a.gstride;
+  float* X = reinterpret_cast<float*>(A);  // L^{-1} in FP32 overwrites the FP64 factor at the end
+  for (int i = tid; i < 32; i += nthr) tab[i] = kExp2Frac32[i];
+  const double lam = p.lambda;
   for (;;) {
     if (tid == 0) {
-      int w = atomicAdd(counter, 1);
-      s_cell = w < G ? (int)order[w] : -1;
+      int w = atomicAdd(a.counter, 1);
+      s_cell = w < a.count ? (int)a.order[a.first + w] : -1;
       s_fail = 0;
     }
     __syncthreads();
     const int g = s_cell;
     if (g < 0) break;
-    const int N = n32[g];
+    const int N = a.n32[g];
     if (N == 0) {
       __syncthreads();
       continue;
     }
-    const int64_t m0 = ts_off[g];
-    double* A = N <= kFitSmemN ? sA : scratch + (int64_t)blockIdx.x * scratch_stride;
+    const int64_t m0 = a.ts_off[g];
+    const int64_t T = tri_sz(N);
     for (int i = tid; i < N; i += nthr) {
-      D4 v = md4[m0 + i];
+      const D4 v = a.md4[m0 + i];
       sx[3 * i] = v.x;
       sx[3 * i + 1] = v.y;
       sx[3 * i + 2] = v.z;
     }
     __syncthreads();
-    // A = K + diag(sigma^2), lower triangle, rows by warps
-    for (int i = warp; i < N; i += nwarp)
-      for (int j = lane; j <= i; j += 32) {
-        double dx = sx[3 * i] - sx[3 * j], dy = sx[3 * i + 1] - sx[3 * j + 1], dz = sx[3 * i + 2] - sx[3 * j + 2];
-        double r2 = dx * dx + dy * dy + dz * dz;
-        double a = exp(-p.lambda * r2);
-        if (i == j) a += (double)mvar[m0 + i];
-        A[tri(i) + j] = a;
-      }
+    // A = K + diag(sigma^2): two independent entries per thread and iteration
+    for (int64_t t0 = tid; t0 < T; t0 += 2 * nthr) {
+      const int64_t t1 = t0 + nthr;
+      const int i0 = tri_row(t0), j0 = (int)(t0 - tri_sz(i0));
+      const int i1 = t1 < T ? tri_row(t1) : i0, j1 = t1 < T ? (int)(t1 - tri_sz(i1)) : j0;
+      double v0 = kernel_entry(sx, i0, j0, lam, tab);
+      double v1 = kernel_entry(sx, i1, j1, lam, tab);
+      if (i0 == j0) v0 += (double)a.mvar[m0 + i0];
+      if (i1 == j1) v1 += (double)a.mvar[m0 + i1];
+      A[t0] = v0;
+      if (t1 < T) A[t1] = v1;
+    }
     __syncthreads();
-    // Cholesky, right looking: column k scaled by the pivot, then the trailing update
-    for (int k = 0; k < N; ++k) {
-      if (tid == 0) {
-        double piv = A[tri(k) + k];
-        if (!(piv > 0.0)) s_fail = 1;
-        else A[tri(k) + k] = sqrt(piv);
+    for (int kb = 0; kb < N; kb += kPanel) {
+      const int ke = min(kb + kPanel, N);
+      if (warp == 0) {
+        for (int k = kb; k < ke; ++k) {
+          int bad = 0;
+          double r = 0.0;
+          if (lane == 0) {
+            const double piv = A[P(k, k)];
+            if (!(piv > 0.0)) {
+              bad = 1;
+            } else {
+              r = rsqrt(piv);
+              A[P(k, k)] = piv * r;
+              dinv[k] = r;
+            }
+          }
+          bad = __shfl_sync(0xffffffffu, bad, 0);
+          r = __shfl_sync(0xffffffffu, r, 0);
+          if (bad) {
+            if (lane == 0) s_fail = 1;
+            break;
+          }
+          for (int i = k + 1 + lane; i < N; i += 32) A[P(i, k)] *= r;
+          __syncwarp();
+          for (int i = k + 1 + lane; i < N; i += 32) {
+            const double lik = A[P(i, k)];
+            const int cmax = min(i, ke - 1);
+            for (int c = k + 1; c <= cmax; ++c) A[P(i, c)] = fma(-lik, A[P(c, k)], A[P(i, c)]);
+          }
+          __syncwarp();
+        }
       }
       __syncthreads();
       if (s_fail) break;
-      const double dkk = A[tri(k) + k];
-      for (int i = k + 1 + tid; i < N; i += nthr) A[tri(i) + k] = A[tri(i) + k] / dkk;
-      __syncthreads();
-      for (int i = k + 1 + warp; i < N; i += nwarp) {
-        const double lik = A[tri(i) + k];
-        for (int j = k + 1 + lane; j <= i; j += 32) A[tri(i) + j] = fma(-lik, A[tri(j) + k], A[tri(i) + j]);
+      // trailing update A[i][j] -= sum_{k in panel} L[i][k] L[j][k] for ke <= j <= i, in 2x2 blocks
+      const int w = ke - kb, nbk = (N - ke + 1) >> 1;
+      const int64_t nblk = tri_sz(nbk);
+      for (int64_t t = tid; t < nblk; t += nthr) {
+        const int I = tri_row(t), J = (int)(t - tri_sz(I));
+        const int i0 = ke + 2 * I, j0 = ke + 2 * J, i1 = i0 + 1, j1 = j0 + 1;
+        const bool vi1 = i1 < N, v01 = j1 <= i0, vj1 = j1 < N;
+        const double* Li0 = A + P(i0, kb);
+        const double* Li1 = vi1 ? A + P(i1, kb) : Li0;
+        const double* Lj0 = A + P(j0, kb);
+        const double* Lj1 = vj1 ? A + P(j1, kb) : Lj0;
+        double a00 = A[P(i0, j0)];
+        double a01 = v01 ? A[P(i0, j1)] : 0.0;
+        double a10 = vi1 ? A[P(i1, j0)] : 0.0;
+        double a11 = vi1 ? A[P(i1, j1)] : 0.0;
+        for (int k = 0; k < w; ++k) {
+          const double li0 = Li0[k], li1 = Li1[k], lj0 = Lj0[k], lj1 = Lj1[k];
+          a00 = fma(-li0, lj0, a00);
+          a01 = fma(-li0, lj1, a01);
+          a10 = fma(-li1, lj0, a10);
+          a11 = fma(-li1, lj1, a11);
+        }
+        A[P(i0, j0)] = a00;
+        if (v01) A[P(i0, j1)] = a01;
+        if (vi1) {
+          A[P(i1, j0)] = a10;
+          A[P(i1, j1)] = a11;
+        }
       }
       __syncthreads();
     }
     if (s_fail) {
       if (tid == 0) {
-        status[g] = KSDF_CELL_NOT_PD;
-        atomicAdd(n_not_pd, 1);
+        a.status[g] = KSDF_CELL_NOT_PD;
+        atomicAdd(a.n_not_pd, 1);
       }
       for (int i = tid; i < N; i += nthr) {
-        md4[m0 + i].w = 0.0;
-        mf4[m0 + i].w = 0.f;
+        a.md4[m0 + i].w = 0.0;
+        a.mf4[m0 + i].w = 0.f;
       }
       __syncthreads();
       continue;
     }
-    // alpha: L y = 1, then L^T alpha = y
-    for (int i = tid; i < N; i += nthr) sb[i] = 1.0;
+    if (warp == 0) {
+      // alpha: L y = 1, then L^T alpha = y (FP64, reciprocal pivots)
+      for (int i = lane; i < N; i += 32) sb[i] = 1.0;
+      __syncwarp();
+      for (int k = 0; k < N; ++k) {
+        const double bk = sb[k] * dinv[k];
+        for (int i = k + 1 + lane; i < N; i += 32) sb[i] = fma(-A[P(i, k)], bk, sb[i]);
+        __syncwarp();
+        if (lane == 0) sb[k] = bk;
+        __syncwarp();
+      }
+      for (int k = N - 1; k >= 0; --k) {
+        const double bk = sb[k] * dinv[k];
+        for (int i = lane; i < k; i += 32) sb[i] = fma(-A[P(k, i)], bk, sb[i]);
+        __syncwarp();
+        if (lane == 0) sb[k] = bk;
+        __syncwarp();
+      }
+    } else {
+      double* Lout = a.chol64 + a.chol_off[g];
+      for (int64_t e = tid - 32; e < T; e += nthr - 32) Lout[e] = A[e];
+    }
     __syncthreads();
-    for (int k = 0; k < N; ++k) {
-      if (tid == 0) sb[k] = sb[k] / A[tri(k) + k];
-      __syncthreads();
-      const double bk = sb[k];
-      for (int i = k + 1 + tid; i < N; i += nthr) sb[i] = fma(-A[tri(i) + k], bk, sb[i]);
-      __syncthreads();
-    }
-    for (int k = N - 1; k >= 0; --k) {
-      if (tid == 0) sb[k] = sb[k] / A[tri(k) + k];
-      __syncthreads();
-      const double bk = sb[k];
-      for (int i = tid; i < k; i += nthr) sb[i] = fma(-A[tri(k) + i], bk, sb[i]);
-      __syncthreads();
-    }
     for (int i = tid; i < N; i += nthr) {
-      md4[m0 + i].w = sb[i];
-      mf4[m0 + i].w = (float)sb[i];
+      a.md4[m0 + i].w = sb[i];
+      a.mf4[m0 + i].w = (float)sb[i];
     }
-    // L^{-1}: X = I, row k divided by L_kk, then rows below updated (right looking); X lives in the output
-    double* X = linv64 + linv_off[g];
-    for (int i = warp; i < N; i += nwarp)
-      for (int j = lane; j <= i; j += 32) X[tri(i) + j] = (i == j) ? 1.0 : 0.0;
-    __syncthreads();
-    for (int k = 0; k < N; ++k) {
-      const double dkk = A[tri(k) + k];
-      for (int j = tid; j <= k; j += nthr) X[tri(k) + j] = X[tri(k) + j] / dkk;
+    // FP64 -> FP32 in place, in chunks: the writes of a chunk only touch FP64 entries already read
+    for (int64_t c0 = 0; c0 < T; c0 += 8 * (int64_t)nthr) {
+      float v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int64_t e = c0 + tid + (int64_t)r * nthr;
+        v[r] = e < T ? (float)A[e] : 0.f;
+      }
       __syncthreads();
-      for (int i = k + 1 + warp; i < N; i += nwarp) {
-        const double lik = A[tri(i) + k];
-        for (int j = lane; j <= k; j += 32) X[tri(i) + j] = fma(-lik, X[tri(k) + j], X[tri(i) + j]);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int64_t e = c0 + tid + (int64_t)r * nthr;
+        if (e < T) X[e] = v[r];
       }
       __syncthreads();
     }
-    for (int64_t e = tid; e < tri(N); e += nthr) {
-      double v = X[e];
-      float hi = (float)v;
-      linv32[linv_off[g] + e] = hi;
-      linv32lo[linv_off[g] + e] = (float)(v - (double)hi);
+    // X = L^{-1}: column j (from the last) becomes X[j][j] = 1/L_jj,
+    // X[i][j] = -X[j][j] sum_{k=j+1..i} X[i][k] L[k][j] (i > j), reading finished columns k > j of X and
+    // the untouched column j of L
+    for (int j = N - 1; j >= 0; --j) {
+      float tv[kInvRows];
+#pragma unroll
+      for (int r = 0; r < kInvRows; ++r) {
+        const int i = j + 1 + tid + r * nthr;
+        float acc = 0.f;
+        if (i < N) {
+          const float* Xi = X + P(i, 0);
+          for (int k = j + 1; k <= i; ++k) acc = fmaf(Xi[k], X[P(k, j)], acc);
+        }
+        tv[r] = acc;
+      }
+      __syncthreads();
+      const float xjj = (float)dinv[j];
+#pragma unroll
+      for (int r = 0; r < kInvRows; ++r) {
+        const int i = j + 1 + tid + r * nthr;
+        if (i < N) X[P(i, j)] = -xjj * tv[r];
+      }
+      if (tid == 0) X[P(j, j)] = xjj;
+      __syncthreads();
+    }
+    float* Iout = a.linv32 + a.linv_off[g];
+    const int64_t lsz = linv_blocked_size(N);
+    for (int64_t e = tid; e < lsz; e += nthr) {
+      int R = (int)((sqrtf(1.f + (float)e / 8.f) - 1.f) * 0.5f);
+      while (linv_block_off(R + 1) <= e) ++R;
+      while (linv_block_off(R) > e) --R;
+      const int64_t q = e - linv_block_off(R);
+      const int col = (int)(q >> 3), i = 8 * R + (int)(q & 7);
+      Iout[e] = (i < N && col <= i) ? X[P(i, col)] : 0.f;
     }
     __syncthreads();
   }
@@ -363,6 +494,12 @@ static int bits_for(uint64_t v) {
   int b = 0;
   while (b < 64 && (v >> b) != 0) ++b;
   return b;
+}
+
+static size_t fit_smem(int np, bool smem_mat) {
+  size_t d = 32 + 5 * (size_t)np;  // exp table, reciprocal pivots, coordinates, right-hand side
+  if (smem_mat) d += (size_t)tri_sz(np);
+  return d * sizeof(double);
 }
 
 ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const float* nrm, int64_t S) {
@@ -422,7 +559,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, ensure(m.hvals, sizeof(int32_t) * cap));
   launch(k_fill_u64, ceil_div(cap, 256), 256, 0, st, ptr<uint64_t>(m.hkeys), cap, kEmptyKey);
   launch(k_hash_insert, ceil_div(G, 256), 256, 0, st, ptr<uint64_t>(m.key), G, ptr<uint64_t>(m.hkeys),
-                                                   ptr<int32_t>(m.hvals), cap);
+         ptr<int32_t>(m.hvals), cap);
   prof_end(c, e0, "fit.index");
   e0 = prof_begin(c);
   // 3. training sets
@@ -431,19 +568,21 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, ensure(m.status, sizeof(int32_t) * G));
   KSDF_CUDA(c, ensure(m.n, sizeof(int32_t) * G));
   KSDF_CUDA(c, ensure(m.ts_off, sizeof(int64_t) * (G + 1)));
+  KSDF_CUDA(c, ensure(m.chol_off, sizeof(int64_t) * (G + 1)));
   KSDF_CUDA(c, ensure(m.linv_off, sizeof(int64_t) * (G + 1)));
-  KSDF_CUDA(c, ensure(c->ws[WS_D], sizeof(int64_t) * (2 * G + 2)));
+  KSDF_CUDA(c, ensure(c->ws[WS_D], sizeof(int64_t) * (3 * G + 3)));
   int64_t* n64 = ptr<int64_t>(c->ws[WS_D]);
   int64_t* tri64 = n64 + (G + 1);
+  int64_t* lb64 = tri64 + (G + 1);
   int* dmax = bbox + 6;
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
   launch(k_assemble, (unsigned)G, 512, 0, st, ptr<uint64_t>(m.key), G, own_off, vals, x, p, R, ptr<uint64_t>(m.hkeys),
-                                          ptr<int32_t>(m.hvals), cap, ptr<int32_t>(m.mpad), n64,
-                                          ptr<int32_t>(m.status), dmax, stw);
-  launch(k_tri_sizes, ceil_div(G, 256), 256, 0, st, n64, G, tri64, ptr<int32_t>(m.n));
+         ptr<int32_t>(m.hvals), cap, ptr<int32_t>(m.mpad), n64, ptr<int32_t>(m.status), dmax, stw);
+  launch(k_sizes, ceil_div(G, 256), 256, 0, st, n64, G, tri64, lb64, ptr<int32_t>(m.n));
   KSDF_CUDA(c, scan_i64(n64, ptr<int64_t>(m.ts_off), G, dtot, c->ws[WS_SCAN], st));
-  KSDF_CUDA(c, scan_i64(tri64, ptr<int64_t>(m.linv_off), G, dtot + 1, c->ws[WS_SCAN], st));
-  int64_t tots[2];
+  KSDF_CUDA(c, scan_i64(tri64, ptr<int64_t>(m.chol_off), G, dtot + 1, c->ws[WS_SCAN], st));
+  KSDF_CUDA(c, scan_i64(lb64, ptr<int64_t>(m.linv_off), G, dtot + 2, c->ws[WS_SCAN], st));
+  int64_t tots[3];
   int hmax[2];
   KSDF_CUDA(c, cudaMemcpyAsync(tots, dtot, sizeof(tots), cudaMemcpyDeviceToHost, st));
   KSDF_CUDA(c, cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st));
@@ -452,10 +591,12 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   if (hst & ST_CAPACITY)
     return set_err(c, KSDF_ERR_CAPACITY, "ksdf_fit: a collection box holds more than %d samples", kMaxPre);
   m.M = tots[0];
-  m.linv_total = tots[1];
+  m.chol_total = tots[1];
+  m.linv_total = tots[2];
   m.max_n = hmax[0];
   KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.ts_off) + G, &tots[0], sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.linv_off) + G, &tots[1], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.chol_off) + G, &tots[1], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.linv_off) + G, &tots[2], sizeof(int64_t), cudaMemcpyHostToDevice, st));
   prof_end(c, e0, "fit.assemble");
   // 4. member arrays
   const int64_t M = m.M;
@@ -465,33 +606,79 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, ensure(m.mf4, sizeof(float4) * (M + 1)));
   KSDF_CUDA(c, ensure(m.mvar, sizeof(float) * (M + 1)));
   if (nrm) KSDF_CUDA(c, ensure(m.mnrm, sizeof(float4) * (M + 1)));
-  KSDF_CUDA(c, ensure(m.linv64, sizeof(double) * (m.linv_total + 1)));
-  KSDF_CUDA(c, ensure(m.linv32, sizeof(float) * (m.linv_total + 1)));
-  KSDF_CUDA(c, ensure(m.linv32lo, sizeof(float) * (m.linv_total + 1)));
-  launch(k_gather_members, ceil_div(G * p.n_max, 256), 256, 0, st, 
-      ptr<uint64_t>(m.key), ptr<int32_t>(m.n), ptr<int64_t>(m.ts_off), ptr<int32_t>(m.mpad), G, p, x, var, nrm,
-      ptr<int32_t>(m.mgid), ptr<D4>(m.md4), ptr<float4>(m.mf4), ptr<float>(m.mvar),
-      nrm ? ptr<float4>(m.mnrm) : nullptr);
-  // 5. FP64 fit, largest cells first
+  KSDF_CUDA(c, ensure(m.chol64, sizeof(double) * (m.chol_total + 1)));
+  KSDF_CUDA(c, ensure(m.linv32, sizeof(float) * (m.linv_total + 4)));
+  launch(k_gather_members, ceil_div(G * p.n_max, 256), 256, 0, st, ptr<uint64_t>(m.key), ptr<int32_t>(m.n),
+         ptr<int64_t>(m.ts_off), ptr<int32_t>(m.mpad), G, p, x, var, nrm, ptr<int32_t>(m.mgid), ptr<D4>(m.md4),
+         ptr<float4>(m.mf4), ptr<float>(m.mvar), nrm ? ptr<float4>(m.mnrm) : nullptr);
+  // 5. the fit, largest cells first, three size classes on three streams
   KSDF_CUDA(c, ensure(c->ws[WS_A], sizeof(uint64_t) * (G + 1)));
   KSDF_CUDA(c, ensure(m.cell_order, sizeof(uint32_t) * (G + 1)));
   uint64_t* okeys = ptr<uint64_t>(c->ws[WS_A]);
   uint32_t* order = ptr<uint32_t>(m.cell_order);
   launch(k_order_keys, ceil_div(G, 256), 256, 0, st, ptr<int32_t>(m.n), G, p.n_max, okeys, order);
   KSDF_CUDA(c, radix_sort_u64(okeys, order, G, bits_for((uint64_t)p.n_max), c->ws[WS_SORT], st));
-  const int nblk = (int)std::min<int64_t>(G, 2LL * c->num_sms);
-  const int64_t stride = (m.max_n > kFitSmemN) ? tri(m.max_n) : 0;
-  KSDF_CUDA(c, ensure(c->ws[WS_FITSCR], sizeof(double) * (size_t)(stride * nblk + 1)));
-  const size_t smem = sizeof(double) * (4 * (size_t)p.n_max + tri(kFitSmemN));
-  KSDF_CUDA(c, cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // size classes (host histogram): N <= 96 (128 threads), <= 160, <= 218 (256 threads, matrix in shared
+  // memory), larger (256 threads, matrix in a per-CTA global slot); launched concurrently, largest first
+  std::vector<int32_t> hn((size_t)G);
+  KSDF_CUDA(c, cudaMemcpyAsync(hn.data(), m.n.p, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, st));
+  KSDF_CUDA(c, cudaStreamSynchronize(st));
+  const int lim[4] = {kClassXL, kClassL, kClassM, kClassS};  // upper bounds, descending
+  int64_t cnt[4] = {0, 0, 0, 0};
+  for (int32_t v : hn) {
+    if (v > kClassL) ++cnt[0];
+    else if (v > kClassM) ++cnt[1];
+    else if (v > kClassS) ++cnt[2];
+    else ++cnt[3];
+  }
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
+  KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 8));
+  int* ctr = reinterpret_cast<int*>(ptr<int64_t>(c->ws[WS_E]) + 4);
+  KSDF_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int) * 4, st));
+  FitArgs fa;
+  fa.order = order;
+  fa.n32 = ptr<int32_t>(m.n);
+  fa.ts_off = ptr<int64_t>(m.ts_off);
+  fa.chol_off = ptr<int64_t>(m.chol_off);
+  fa.linv_off = ptr<int64_t>(m.linv_off);
+  fa.md4 = ptr<D4>(m.md4);
+  fa.mf4 = ptr<float4>(m.mf4);
+  fa.mvar = ptr<float>(m.mvar);
+  fa.chol64 = ptr<double>(m.chol64);
+  fa.linv32 = ptr<float>(m.linv32);
+  fa.status = ptr<int32_t>(m.status);
+  fa.n_not_pd = dmax + 1;
+  fa.gscr = nullptr;
+  fa.gstride = 0;
+  KSDF_CUDA(c, cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem(kClassL, true)));
   e0 = prof_begin(c);
-  launch(k_fit, nblk, kFitThreads, smem, st, order, G, ptr<int32_t>(m.n), ptr<int64_t>(m.ts_off),
-                                         ptr<int64_t>(m.linv_off), p, ptr<D4>(m.md4), ptr<float4>(m.mf4),
-                                         ptr<float>(m.mvar), ptr<double>(m.linv64), ptr<float>(m.linv32),
-                                         ptr<float>(m.linv32lo), ptr<int32_t>(m.status),
-                                         ptr<double>(c->ws[WS_FITSCR]), stride, dmax, dmax + 1, stw);
+  KSDF_CUDA(c, fork_streams(c));
+  int64_t first = 0;
+  for (int cl = 0; cl < 4; ++cl) {
+    if (cnt[cl] == 0) continue;
+    FitArgs f = fa;
+    f.first = first;
+    f.count = cnt[cl];
+    f.counter = ctr + cl;
+    first += cnt[cl];
+    const int threads = cl == 3 ? 128 : 256;
+    f.smem_mat = cl > 0 ? 1 : 0;
+    f.np = cl > 0 ? lim[cl] : std::max(m.max_n, 1);
+    if (cl == 0) {
+      const int nblk = (int)std::min<int64_t>(cnt[cl], c->num_sms);
+      f.gstride = tri_sz(f.np);
+      KSDF_CUDA(c, ensure(c->ws[WS_FITSCR], sizeof(double) * (size_t)(f.gstride * nblk + 1)));
+      f.gscr = ptr<double>(c->ws[WS_FITSCR]);
+    }
+    const size_t smem = fit_smem(f.np, f.smem_mat != 0);
+    int occ = 0;
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fit, threads, smem));
+    const int nblk = (int)std::min<int64_t>(cnt[cl], (int64_t)std::max(1, occ) * c->num_sms);
+    cudaStream_t s = cl == 3 ? st : c->aux[cl & 1];
+    launch(k_fit, nblk, threads, smem, s, f, p);
+  }
   KSDF_CUDA(c, cudaGetLastError());
+  KSDF_CUDA(c, join_streams(c));
   prof_end(c, e0, "fit.cholesky");
   KSDF_CUDA(c, cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st));
   KSDF_CUDA(c, cudaStreamSynchronize(st));

@@ -48,6 +48,16 @@ __device__ inline bool bin_coord(double x, double o, double h, int& c) {
 // lower corner o + c h of a cell along one axis, IEEE binary64, no contraction
 __device__ inline double cell_base(double o, int c, double h) { return __dadd_rn(o, __dmul_rn((double)c, h)); }
 
+// the cell base o + c h as an FP32 head + tail (computed once per tile in binary64), and a point's
+// cell-local coordinate (x - head) - tail in FP32: within one FP32 rounding of fl32(x - (o + c h)),
+// without per-point FP64 work (the FP64 pipe is 1/64 of the FP32 rate on this part)
+__device__ inline void base_split(double o, int c, double h, float& hi, float& lo) {
+  const double b = cell_base(o, c, h);
+  hi = (float)b;
+  lo = (float)(b - (double)hi);
+}
+__device__ __forceinline__ float local32(float x, float hi, float lo) { return __fsub_rn(__fsub_rn(x, hi), lo); }
+
 // hash of a packed key (splitmix64 finaliser)
 __host__ __device__ inline uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
@@ -102,12 +112,13 @@ struct DevBuf {
 
 struct Model {
   int64_t S = 0, G = 0, M = 0;    // samples, cells, training-set members
-  int64_t linv_total = 0;         // sum N (N+1) / 2
+  int64_t chol_total = 0;         // sum N (N+1) / 2 (packed FP64 L)
+  int64_t linv_total = 0;         // sum 32 nb (nb+1), nb = ceil(N/8) (FP32 L^-1, 8-row interleaved)
   int max_n = 0;                  // largest training set
   bool has_normals = false;
   int n_not_pd = 0;
   // per cell
-  DevBuf key, status, n, ts_off, linv_off;     // uint64, int32, int32, int64 (G+1), int64 (G+1)
+  DevBuf key, status, n, ts_off, chol_off, linv_off;  // uint64, int32, int32, int64 (G+1) x 3
   DevBuf hkeys, hvals;                          // GP cell hash table
   uint64_t hcap = 0;
   DevBuf cell_order;                            // cells sorted by descending N (fit work order)
@@ -118,9 +129,10 @@ struct Model {
   DevBuf mnrm;     // float4 normal
   DevBuf mgid;     // int32 global sample id
   DevBuf mpad;     // int32 padded ids (G x n_max), assembly scratch
-  DevBuf linv64;   // double, packed lower rows
-  DevBuf linv32;   // float hi, packed lower rows
-  DevBuf linv32lo; // float lo = linv - hi
+  DevBuf chol64;   // double: Cholesky factor L, packed lower rows (row i at i (i+1) / 2)
+  DevBuf linv32;   // float: L^-1 in 8-row blocks: block R (rows 8R..8R+7) holds, for each column
+                   // j <= 8R+7, the 8 values L^-1[8R+r][j] (0 above the diagonal); block R starts at
+                   // 32 R (R+1); size per cell 32 nb (nb+1), nb = ceil(N/8)
   DevBuf x;        // sample positions (S x dim double), kept for the backward's scatter
 };
 
@@ -152,6 +164,9 @@ struct ksdf_ctx {
   std::vector<std::string> stage_names;
   std::vector<double> stage_ms;
   std::vector<long long> stage_calls;
+  // auxiliary streams for concurrent launches inside one call (fork/join through events)
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
 };
 
 namespace ksdf {
@@ -172,6 +187,10 @@ template <class T> inline T* ptr(DevBuf& b) { return static_cast<T*>(b.p); }
 // ---- stage profiling (ksdf_abi.cu): no-ops unless enabled ----
 cudaEvent_t prof_begin(ksdf_ctx* c);
 void prof_end(ksdf_ctx* c, cudaEvent_t a, const char* name);
+
+// ---- fork/join of the context stream with two auxiliary streams (ksdf_abi.cu) ----
+cudaError_t fork_streams(ksdf_ctx* c);
+cudaError_t join_streams(ksdf_ctx* c);
 
 // ---- sorting and scanning (ksdf_sort.cu) ----
 // exclusive scan of n int64 values (in may equal out); total (optional) gets the sum on the device.
@@ -222,6 +241,14 @@ enum WsRole {
 };
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+__host__ __device__ inline int64_t tri_sz(int64_t n) { return n * (n + 1) / 2; }
+// size and block offset of the 8-row interleaved L^-1 layout
+__host__ __device__ inline int64_t linv_blocked_size(int64_t n) {
+  const int64_t nb = (n + 7) / 8;
+  return 32 * nb * (nb + 1);
+}
+__host__ __device__ inline int64_t linv_block_off(int64_t R) { return 32 * R * (R + 1); }
 
 // every kernel launch of the library goes through launch(): it counts launches (ksdf_profile_read)
 extern std::atomic<long long> g_launches;

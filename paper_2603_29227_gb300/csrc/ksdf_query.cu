@@ -23,7 +23,6 @@ namespace ksdf {
 namespace {
 
 constexpr int kTA = 128;   // phase A threads (one query each)
-constexpr int kTB = 64;    // phase B threads, mixed path
 constexpr int kTB64 = 32;  // phase B threads, FP64 path
 constexpr int kRingMax = 16;
 constexpr float kLog2e = 1.4426950408889634f;
@@ -331,6 +330,7 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_tile, s_nc, s_c[kMaxK], s_n[kMaxK], s_base[kMaxK];
   __shared__ float s_off[kMaxK][3];
+  __shared__ float s_bh[3], s_bl[3];
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -372,20 +372,21 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
       for (int k = 0; k < nc; ++k)
         bulk_g2s(s_x + s_base[k], a.mf4 + a.ts_off[s_c[k]], (uint32_t)s_n[k] * 16u, &bar);
     }
-    // the query in the bin's frame: fl32(x - (o + b h)), binary64 subtraction
+    if (tid == 0)
+      for (int j = 0; j < 3; ++j) base_split(p.o[j], bc[j], p.h, s_bh[j], s_bl[j]);
     const bool live = tid < tile.z;
-    int q = 0;
-    float ql[3] = {0.f, 0.f, 0.f};
-    if (live) {
-      q = a.sorted_q[tile.y + tid];
-      for (int j = 0; j < p.dim; ++j)
-        ql[j] = (float)__dsub_rn((double)xq[(int64_t)q * p.dim + j], cell_base(p.o[j], bc[j], p.h));
-    }
+    const int q = live ? a.sorted_q[tile.y + tid] : 0;
+    float xg[3] = {0.f, 0.f, 0.f};
+    if (live)
+      for (int j = 0; j < p.dim; ++j) xg[j] = xq[(int64_t)q * p.dim + j];
     if (!mbar_wait_all(&bar, phase)) {
       if (tid == 0) atomicOr(a.st, ST_TIMEOUT);
       return;
     }
     phase ^= 1;
+    // the query in the bin's frame (FP32 two-term subtraction of the bin corner)
+    float ql[3] = {0.f, 0.f, 0.f};
+    for (int j = 0; j < p.dim; ++j) ql[j] = local32(xg[j], s_bh[j], s_bl[j]);
     const int nc = s_nc;
     float bu = INFINITY, su = INFINITY;
     int bk = -1;
@@ -602,7 +603,12 @@ __global__ void k_w_scatter(const int32_t* qwin, const int32_t* qbin, const int3
 }
 
 // ---------------------------------------------------------------------------------------------
-// Q6: phase B, mixed precision (tile of queries sharing the winner cell)
+// Q6: phase B, mixed precision.  A tile is up to 32 queries sharing the winner cell (lane = query); the
+// 4 warps of the CTA split the cell's samples for the minimum, k', the gradient and the softmin sums,
+// and split the 8-row blocks of L^{-1} for V[f] = 1 - e^{-2 lambda d^2} |L^{-1} k'|^2.
+
+constexpr int kBQ = 32;
+constexpr int kBW = 4;
 
 struct PhaseBArgs {
   const int4* tiles;
@@ -612,14 +618,14 @@ struct PhaseBArgs {
   const int64_t* ts_off;
   const int32_t* cell_n;
   const uint64_t* cell_key;
+  const int64_t* chol_off;
   const int64_t* linv_off;
   const float4* mf4;
   const D4* md4;
   const float* mvar;
   const float4* mnrm;
   const float* linv32;
-  const float* linv32lo;
-  const double* linv64;
+  const double* chol64;
   const float* qu;
   const double* qu64;
   const uint32_t* qflag;
@@ -629,12 +635,15 @@ struct PhaseBArgs {
   uint32_t* st;
 };
 
-__global__ void __launch_bounds__(kTB) k_phaseB(PhaseBArgs a, const float* xq, Params p, float* sdf, float* grad,
-                                                float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags) {
-  extern __shared__ __align__(128) float4 s_x[];  // [n_max] samples, then [n_max] var, then [n_max][kTB] k'
+__global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* xq, Params p, float* sdf, float* grad,
+                                                     float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags) {
+  extern __shared__ __align__(128) float4 s_x[];  // [n_max] samples | [n_max] var | [n_max][32] k'
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_tile;
-  const int tid = threadIdx.x;
+  __shared__ float s_red[kBW][9][kBQ];
+  __shared__ int s_nn[kBW][kBQ];
+  __shared__ float s_bh[3], s_bl[3];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   float* s_var = reinterpret_cast<float*>(s_x + p.n_max);
   float* s_k = s_var + p.n_max;
   if (tid == 0) {
@@ -662,24 +671,31 @@ __global__ void __launch_bounds__(kTB) k_phaseB(PhaseBArgs a, const float* xq, P
       bulk_g2s(s_x, a.mf4 + m0, (uint32_t)n * 16u, &bar);
     }
     for (int i = tid; i < n; i += blockDim.x) s_var[i] = a.mvar[m0 + i];  // not 16-byte aligned: plain loads
-    int cc[3];
-    unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
-    const bool live = tid < tile.z;
-    const int q = live ? a.sorted_w[tile.y + tid] : 0;
-    float ql[3] = {0.f, 0.f, 0.f};
+    if (tid == 0) {
+      int cc[3];
+      unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
+      for (int j = 0; j < 3; ++j) base_split(p.o[j], cc[j], p.h, s_bh[j], s_bl[j]);
+    }
+    const bool live = lane < tile.z;
+    const int q = live ? a.sorted_w[tile.y + lane] : 0;
+    float xg[3] = {0.f, 0.f, 0.f};
     if (live)
-      for (int j = 0; j < p.dim; ++j)
-        ql[j] = (float)__dsub_rn((double)xq[(int64_t)q * p.dim + j], cell_base(p.o[j], cc[j], p.h));
+      for (int j = 0; j < p.dim; ++j) xg[j] = xq[(int64_t)q * p.dim + j];
     if (!mbar_wait_all(&bar, phase)) {
       if (tid == 0) atomicOr(a.st, ST_TIMEOUT);
       return;
     }
     phase ^= 1;
-    if (live) {
-      // pass 1: nearest sample (first minimum: training sets are in ascending global id)
+    float ql[3] = {0.f, 0.f, 0.f};
+    for (int j = 0; j < p.dim; ++j) ql[j] = local32(xg[j], s_bh[j], s_bl[j]);
+    // this warp's share of the samples
+    const int per = (n + kBW - 1) / kBW;
+    const int i0 = w * per, i1 = min(n, i0 + per);
+    // pass 1: nearest sample (first minimum in id order)
+    {
       float m = INFINITY;
-      int nn = 0;
-      for (int i = 0; i < n; ++i) {
+      int nn = 0x7fffffff;
+      for (int i = i0; i < i1; ++i) {
         const float4 v = s_x[i];
         const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -688,78 +704,114 @@ __global__ void __launch_bounds__(kTB) k_phaseB(PhaseBArgs a, const float* xq, P
           nn = i;
         }
       }
-      const float zmin = sqrtf(m);
-      // pass 2: k'_i, grad f', softmin accumulators
+      s_red[w][0][lane] = m;
+      s_nn[w][lane] = nn;
+    }
+    __syncthreads();
+    float m = s_red[0][0][lane];
+    int nn = s_nn[0][lane];
+    for (int v = 1; v < kBW; ++v)
+      if (s_red[v][0][lane] < m) {
+        m = s_red[v][0][lane];
+        nn = s_nn[v][lane];
+      }
+    const float zmin = sqrtf(m);
+    __syncthreads();
+    // pass 2: k'_i (kept for V[f]), grad f', softmin sums
+    {
       float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
       const float cmn = c1 * m;
-      for (int i = 0; i < n; ++i) {
+      for (int i = i0; i < i1; ++i) {
         const float4 v = s_x[i];
         const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float kp = ex2(fmaf(-c1, r2, cmn));
-        s_k[i * kTB + tid] = kp;
+        s_k[i * kBQ + lane] = kp;
         const float ak = v.w * kp;
         G0 = fmaf(ak, dx, G0);
         G1 = fmaf(ak, dy, G1);
         G2 = fmaf(ak, dz, G2);
         const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
         const float y = fmaxf(z - zmin, 0.f);
-        const float w = ex2(-c2 * y);
-        W += w;
-        HY = fmaf(w, y, HY);
-        const float tw = w * w * s_var[i];
+        const float wt = ex2(-c2 * y);
+        W += wt;
+        HY = fmaf(wt, y, HY);
+        const float tw = wt * wt * s_var[i];
         T0 += tw;
         T1 = fmaf(tw, y, T1);
         T2 = fmaf(tw * y, y, T2);
       }
-      float vs = 0.f;
-      {
-        const float hy = HY / W;
-        const float B = fmaf(as, hy, 1.f);
-        vs = (B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W);
-        vs = fmaxf(vs, 0.f);
-      }
-      // GP variance: V = L^{-1} k' (rows of the packed lower triangle), FP32 hi + lo
-      float vf = 1.f;
-      if (a.mask & KSDF_OUT_VAR_F) {
-        const float* Lh = a.linv32 + a.linv_off[g];
-        const float* Ll = a.linv32lo + a.linv_off[g];
-        float acc = 0.f;
-        for (int j = 0; j < n; ++j) {
-          const float* rh = Lh + (int64_t)j * (j + 1) / 2;
-          const float* rl = Ll + (int64_t)j * (j + 1) / 2;
-          float v = 0.f, vl = 0.f;
-          for (int i = 0; i <= j; ++i) {
-            const float kk = s_k[i * kTB + tid];
-            v = fmaf(__ldg(rh + i), kk, v);
-            vl = fmaf(__ldg(rl + i), kk, vl);
-          }
-          v += vl;
-          acc = fmaf(v, v, acc);
+      s_red[w][1][lane] = G0;
+      s_red[w][2][lane] = G1;
+      s_red[w][3][lane] = G2;
+      s_red[w][4][lane] = W;
+      s_red[w][5][lane] = HY;
+      s_red[w][6][lane] = T0;
+      s_red[w][7][lane] = T1;
+      s_red[w][8][lane] = T2;
+    }
+    __syncthreads();
+    // V[f]: warp w takes the 8-row blocks R = w, w + 4, ...; rows of a block are read 8 at a time
+    float vsum = 0.f;
+    if (a.mask & KSDF_OUT_VAR_F) {
+      const float* Lb = a.linv32 + a.linv_off[g];
+      const int nb = (n + 7) / 8;
+      for (int R = w; R < nb; R += kBW) {
+        const float4* blk = reinterpret_cast<const float4*>(Lb + linv_block_off(R));
+        const int imax = min(8 * R + 8, n);
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int i = 0; i < imax; ++i) {
+          const float4 l0 = __ldg(blk + 2 * i), l1 = __ldg(blk + 2 * i + 1);
+          const float kk = s_k[i * kBQ + lane];
+          acc[0] = fmaf(l0.x, kk, acc[0]);
+          acc[1] = fmaf(l0.y, kk, acc[1]);
+          acc[2] = fmaf(l0.z, kk, acc[2]);
+          acc[3] = fmaf(l0.w, kk, acc[3]);
+          acc[4] = fmaf(l1.x, kk, acc[4]);
+          acc[5] = fmaf(l1.y, kk, acc[5]);
+          acc[6] = fmaf(l1.z, kk, acc[6]);
+          acc[7] = fmaf(l1.w, kk, acc[7]);
         }
-        vf = fmaxf(1.f - ex2(-2.f * c1 * m) * acc, 0.f);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) vsum = fmaf(acc[r], acc[r], vsum);
       }
-      // sign
+    }
+    __syncthreads();  // everyone has read s_red[.][1..8]
+    s_red[w][0][lane] = vsum;
+    __syncthreads();
+    if (w == 0 && live) {
+      float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f, VS = 0.f;
+      for (int v = 0; v < kBW; ++v) {
+        G0 += s_red[v][1][lane];
+        G1 += s_red[v][2][lane];
+        G2 += s_red[v][3][lane];
+        W += s_red[v][4][lane];
+        HY += s_red[v][5][lane];
+        T0 += s_red[v][6][lane];
+        T1 += s_red[v][7][lane];
+        T2 += s_red[v][8][lane];
+        VS += s_red[v][0][lane];
+      }
+      const float hy = HY / W;
+      const float B = fmaf(as, hy, 1.f);
+      const float vs = fmaxf((B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W), 0.f);
+      const float vf = fmaxf(1.f - ex2(-2.f * c1 * m) * VS, 0.f);
       float s = 1.f;
       if (a.sign) {
         s = a.sign[q] < 0 ? -1.f : 1.f;
       } else if (p.sign_mode == 1 && a.has_normals) {
         const float4 v = s_x[nn];
         const float4 nv = a.mnrm[m0 + nn];
-        const float dot = nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z);
-        s = dot >= 0.f ? 1.f : -1.f;
+        s = (nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z)) >= 0.f ? 1.f : -1.f;
       }
       uint32_t fl = a.qflag[q];
       const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
       if (a.mask & KSDF_OUT_SDF) sdf[q] = s * a.qu[q];
       if (a.mask & KSDF_OUT_GRAD) {
-        float gv[3] = {G0, G1, G2};
-        if (gn > 0.f) {
-          const float ig = s / gn;
-          for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gv[j] * ig;
-        } else {
-          for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = 0.f;
-        }
+        const float gv[3] = {G0, G1, G2};
+        const float ig = gn > 0.f ? s / gn : 0.f;
+        for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gv[j] * ig;
       }
       if (!(gn > 0.f)) fl |= KSDF_FLAG_ZERO_GRAD;
       if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
@@ -771,7 +823,8 @@ __global__ void __launch_bounds__(kTB) k_phaseB(PhaseBArgs a, const float* xq, P
   }
 }
 
-// Q6 (plain path): binary64 throughout
+// Q6 (plain path): binary64 throughout; V[f] by forward substitution with the stored Cholesky factor,
+// v = L^{-1} k' (in place over k'), V[f] = 1 - e^{-2 lambda d^2} |v|^2.
 __global__ void __launch_bounds__(kTB64) k_phaseB64(PhaseBArgs a, const double* xq, Params p, double* sdf,
                                                     double* grad, double* var_sdf, double* var_f, int32_t* winner,
                                                     uint32_t* flags) {
@@ -841,9 +894,9 @@ __global__ void __launch_bounds__(kTB64) k_phaseB64(PhaseBArgs a, const double* 
         G1 += ak * dy;
         G2 += ak * dz;
         const double z = sqrt(r2);
-        const double w = exp(-as * (z - zmin));
-        W += w;
-        HZ += w * z;
+        const double wt = exp(-as * (z - zmin));
+        W += wt;
+        HZ += wt * z;
       }
       const double h = HZ / W;
       double vs = 0.0;
@@ -857,12 +910,14 @@ __global__ void __launch_bounds__(kTB64) k_phaseB64(PhaseBArgs a, const double* 
       }
       double vf = 1.0;
       if (a.mask & KSDF_OUT_VAR_F) {
-        const double* L = a.linv64 + a.linv_off[g];
+        const double* L = a.chol64 + a.chol_off[g];
         double acc = 0.0;
-        for (int j = 0; j < n; ++j) {
-          const double* r = L + (int64_t)j * (j + 1) / 2;
-          double v = 0.0;
-          for (int i = 0; i <= j; ++i) v = fma(r[i], s_k[i * kTB64 + tid], v);
+        for (int i = 0; i < n; ++i) {
+          const double* Li = L + (int64_t)i * (i + 1) / 2;
+          double sm = s_k[i * kTB64 + tid];
+          for (int j = 0; j < i; ++j) sm = fma(-Li[j], s_k[j * kTB64 + tid], sm);
+          const double v = sm / Li[i];
+          s_k[i * kTB64 + tid] = v;
           acc = fma(v, v, acc);
         }
         vf = fmax(1.0 - exp(-2.0 * lam * m) * acc, 0.0);
@@ -947,7 +1002,7 @@ ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G) {
   KSDF_CUDA(c, ensure(c->ws[WS_BIN], sizeof(int64_t) * (5 * bcap + 8)));
   KSDF_CUDA(c, ensure(c->ws[WS_CAND], sizeof(int32_t) * (bcap * (K + 1))));
   const int64_t max_tiles_a = Q / kTA + bcap + 1;
-  const int64_t max_tiles_b = Q / kTB64 + G + 1;
+  const int64_t max_tiles_b = Q / kTB64 + G + 1;  // also covers the mixed path's 32-query tiles
   KSDF_CUDA(c, ensure(c->ws[WS_TILE], sizeof(int4) * (max_tiles_a + max_tiles_b)));
   KSDF_CUDA(c, ensure(c->ws[WS_CELLQ], sizeof(int64_t) * (4 * G + 8)));
   const int64_t nsc = (int64_t)bcap / 2048 + 2;
@@ -968,7 +1023,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     if (rs) return rs;
   }
   const int64_t max_tiles_a = Q / kTA + bcap + 1;
-  const int TBq = f64 ? kTB64 : kTB;
+  const int TBq = f64 ? kTB64 : kBQ;
   uint64_t* qkey = ptr<uint64_t>(c->ws[WS_QKEY]);
   int32_t* qbin = ptr<int32_t>(c->ws[WS_QBIN]);
   int32_t* qrank = ptr<int32_t>(c->ws[WS_QRANK]);
@@ -1092,13 +1147,13 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   pb.cell_n = ptr<int32_t>(m.n);
   pb.cell_key = ptr<uint64_t>(m.key);
   pb.linv_off = ptr<int64_t>(m.linv_off);
+  pb.chol_off = ptr<int64_t>(m.chol_off);
   pb.mf4 = ptr<float4>(m.mf4);
   pb.md4 = ptr<D4>(m.md4);
   pb.mvar = ptr<float>(m.mvar);
   pb.mnrm = m.has_normals ? ptr<float4>(m.mnrm) : nullptr;
   pb.linv32 = ptr<float>(m.linv32);
-  pb.linv32lo = ptr<float>(m.linv32lo);
-  pb.linv64 = ptr<double>(m.linv64);
+  pb.chol64 = ptr<double>(m.chol64);
   pb.qu = qu;
   pb.qu64 = qu64;
   pb.qflag = qflag;
@@ -1115,13 +1170,13 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
         pb, static_cast<const double*>(xq), p, static_cast<double*>(sdf), static_cast<double*>(grad),
         static_cast<double*>(var_sdf), static_cast<double*>(var_f), winner, flags);
   } else {
-    const size_t smem = sizeof(float4) * p.n_max + sizeof(float) * p.n_max * (1 + kTB);
+    const size_t smem = sizeof(float4) * p.n_max + sizeof(float) * p.n_max * (1 + kBQ);
     KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB, kTB, smem));
-    launch(k_phaseB, std::max(1, occ) * c->num_sms, kTB, smem, st, 
-        pb, static_cast<const float*>(xq), p, static_cast<float*>(sdf), static_cast<float*>(grad),
-        static_cast<float*>(var_sdf), static_cast<float*>(var_f), winner, flags);
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB, kBQ * kBW, smem));
+    launch(k_phaseB, std::max(1, occ) * c->num_sms, kBQ * kBW, smem, st, pb, static_cast<const float*>(xq), p,
+           static_cast<float*>(sdf), static_cast<float*>(grad), static_cast<float*>(var_sdf),
+           static_cast<float*>(var_f), winner, flags);
   }
   KSDF_CUDA(c, cudaGetLastError());
   prof_end(c, e0, f64 ? "query64.phaseB" : "query.phaseB");

@@ -69,7 +69,7 @@ def load(path: str = LIB_PATH):
         "ksdf_last_error": [P],
         "ksdf_model_size": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "ksdf_get_cells": [P, P, P, P, P],
-        "ksdf_get_fit": [P, P, P],
+        "ksdf_get_fit": [P, P, P, P],
         "ksdf_bin": [P, P, I64, P],
         "ksdf_candidates": [P, P, I64, P, P],
         "ksdf_profile": [P, ctypes.c_int],
@@ -211,13 +211,32 @@ def ksdf_get_cells(h):
 
 
 def ksdf_get_fit(h):
+    """(alpha float64 [M], chol float64 packed L per cell, linv float32 8-row-blocked L^-1 per cell)"""
     keys, status, off, mem = ksdf_get_cells(h)
     n = np.diff(off)
     alpha = np.empty(max(int(off[-1]), 1), np.float64)
     ntri = int(np.sum(n * (n + 1) // 2))
-    linv = np.empty(max(ntri, 1), np.float64)
-    _check(h, load().ksdf_get_fit(h, _ptr(alpha), _ptr(linv)), "ksdf_get_fit")
-    return alpha[: int(off[-1])], linv[:ntri]
+    nb = (n + 7) // 8
+    nlb = int(np.sum(32 * nb * (nb + 1)))
+    chol = np.empty(max(ntri, 1), np.float64)
+    linv = np.empty(max(nlb, 1), np.float32)
+    _check(h, load().ksdf_get_fit(h, _ptr(alpha), _ptr(chol), _ptr(linv)), "ksdf_get_fit")
+    return alpha[: int(off[-1])], chol[:ntri], linv[:nlb]
+
+
+def unpack_linv_blocked(linv_cell, n):
+    """Dense n x n L^-1 of one cell from its 8-row-blocked FP32 layout (host helper for tests)."""
+    out = np.zeros((n, n), np.float64)
+    nb = (n + 7) // 8
+    for R in range(nb):
+        base = 32 * R * (R + 1)
+        cols = 8 * R + 8
+        blk = np.asarray(linv_cell[base:base + cols * 8], np.float64).reshape(cols, 8)
+        for r in range(8):
+            i = 8 * R + r
+            if i < n:
+                out[i, : min(cols, n)] = blk[: min(cols, n), r]
+    return out
 
 
 def ksdf_bin(h, x, n, keys):

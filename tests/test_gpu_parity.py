@@ -69,25 +69,33 @@ def test_cells_and_training_sets_bit_exact(case):
     assert np.array_equal(m0, m1), name
 
 
-def test_fit_alpha_fp64(case):
+def test_fit_alpha_chol_linv(case):
+    """FP64 alpha and Cholesky factor against the oracle (1e-9); FP32 L^-1 is the inverse of L to FP32 level."""
     name, w, ref, gm = case
     keys, status, off, mem = ref.cells()
-    alpha_gpu, linv = gm.fit_arrays()
-    worst = 0.0
+    alpha_gpu, chol, linv = gm.fit_arrays()
+    n = np.diff(off)
+    tri_off = np.concatenate([[0], np.cumsum(n * (n + 1) // 2)])
+    nb = (n + 7) // 8
+    lb_off = np.concatenate([[0], np.cumsum(32 * nb * (nb + 1))])
+    worst_a = worst_l = worst_i = 0.0
+    rng = np.random.default_rng(0)
+    check_inv = set(rng.choice(len(keys), size=min(60, len(keys)), replace=False).tolist()) | {int(np.argmax(n))}
     for g in range(len(keys)):
         if status[g] != oracle.CELL_OK:
             continue
         a = ref.alpha(g)
-        b = alpha_gpu[off[g]:off[g + 1]]
-        worst = max(worst, float(np.max(np.abs(a - b)) / np.max(np.abs(a))))
-    assert worst <= 1e-9, (name, worst)
-    # L^{-1} of one cell against the oracle's Cholesky factor: L^{-1} L = I
-    g = int(np.argmax(np.diff(off)))
-    n = int(off[g + 1] - off[g])
-    tri0 = int(np.sum([(off[i + 1] - off[i]) * (off[i + 1] - off[i] + 1) // 2 for i in range(g)]))
-    Li = np.zeros((n, n))
-    Li[np.tril_indices(n)] = linv[tri0:tri0 + n * (n + 1) // 2]
-    assert np.max(np.abs(Li @ ref.chol(g) - np.eye(n))) <= 1e-9
+        worst_a = max(worst_a, float(np.max(np.abs(a - alpha_gpu[off[g]:off[g + 1]])) / np.max(np.abs(a))))
+        Lr = ref.chol(g)
+        Lg = np.zeros_like(Lr)
+        Lg[np.tril_indices(n[g])] = chol[tri_off[g]:tri_off[g + 1]]
+        worst_l = max(worst_l, float(np.max(np.abs(Lg - Lr)) / np.max(np.abs(Lr))))
+        if g in check_inv:
+            Li = ksdf.unpack_linv_blocked(linv[lb_off[g]:lb_off[g + 1]], int(n[g]))
+            worst_i = max(worst_i, float(np.max(np.abs(Li @ Lr - np.eye(n[g])))))
+    assert worst_a <= 1e-9, (name, worst_a)
+    assert worst_l <= 1e-9, (name, worst_l)
+    assert worst_i <= 1e-4, (name, worst_i)
 
 
 def test_candidate_lists_bit_exact(case):

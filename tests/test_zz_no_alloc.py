@@ -4,8 +4,9 @@ Callers such as real-time control loops, or programs whose device memory belongs
 cannot call cudaMalloc; for them the library offers a context-free fit of one training set whose only
 scratch is a static device array.  This test calls it twice in a row through the C ABI (the second call
 with a smaller training set, on top of the first call's scratch contents) and checks each result against
-the regular ksdf_fit of a one-cell model on the same samples, within the FP64 tolerance of the other GPU
-tests (1e-9 relative).  The file name makes pytest collect it last.
+the regular ksdf_fit of a one-cell model on the same samples (alpha, and L^-1 against the inverse of the
+regular fit's FP64 Cholesky factor), within the FP64 tolerance of the other GPU tests (1e-9 relative).
+The file name makes pytest collect it last.
 """
 import numpy as np
 import pytest
@@ -33,7 +34,7 @@ def _build():
 
 def regular_fit(x, var):
     """The existing path: ksdf_fit on a one-cell model (one 64 m cell at the origin holds every sample, in
-    id order, with no cap), read back with ksdf_get_fit."""
+    id order, with no cap), read back with ksdf_get_fit (alpha and the FP64 Cholesky factor)."""
     p = dict(PARAMS, cell=64.0, margin=0.0, n_max=512, k_cand=1)
     m = ksdf.KernelSDF(p)
     m.fit(torch.from_numpy(x).to(DEV), torch.from_numpy(var).to(DEV), None)
@@ -49,7 +50,10 @@ def test_noalloc_fit_matches_regular_fit_on_two_calls():
         rng = np.random.default_rng(seed)
         x = rng.uniform(0.2, 0.8, size=(n, 3))
         var = rng.uniform(2.5e-5, 4e-4, size=n).astype(np.float32)
-        alpha_ref, linv_ref = regular_fit(x, var)
+        alpha_ref, chol_ref, _ = regular_fit(x, var)
+        L = np.zeros((n, n))
+        L[np.tril_indices(n)] = chol_ref
+        linv_ref = np.linalg.inv(L)[np.tril_indices(n)]  # L^-1 of the regular fit's FP64 factor
         alpha = torch.empty(n, dtype=torch.float64, device=DEV)
         linv = torch.empty(n * (n + 1) // 2, dtype=torch.float64, device=DEV)
         status = torch.full((1,), -1, dtype=torch.int32, device=DEV)
