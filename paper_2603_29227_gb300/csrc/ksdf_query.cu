@@ -635,17 +635,53 @@ struct PhaseBArgs {
   uint32_t* st;
 };
 
+__device__ __forceinline__ float vf_rows(const float* Lb, int n, int w, const float* s_k, int lane) {
+  // sum over this warp's 8-row blocks R = w, w + 4, ... of |L^{-1}[8R..8R+7][:] k'|^2
+  float vsum = 0.f;
+  const int nb = (n + 7) / 8;
+  for (int R = w; R < nb; R += kBW) {
+    const float4* blk = reinterpret_cast<const float4*>(Lb + linv_block_off(R));
+    const int imax = min(8 * R + 8, n);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int i = 0; i < imax; ++i) {
+      const float4 l0 = blk[2 * i], l1 = blk[2 * i + 1];
+      const float kk = s_k[i * kBQ + lane];
+      acc[0] = fmaf(l0.x, kk, acc[0]);
+      acc[1] = fmaf(l0.y, kk, acc[1]);
+      acc[2] = fmaf(l0.z, kk, acc[2]);
+      acc[3] = fmaf(l0.w, kk, acc[3]);
+      acc[4] = fmaf(l1.x, kk, acc[4]);
+      acc[5] = fmaf(l1.y, kk, acc[5]);
+      acc[6] = fmaf(l1.z, kk, acc[6]);
+      acc[7] = fmaf(l1.w, kk, acc[7]);
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) vsum = fmaf(acc[r], acc[r], vsum);
+  }
+  return vsum;
+}
+
+constexpr int kBItem = 256;     // queries per phase-B work item (processed 32 at a time)
+constexpr int kLinvStageN = 128;  // L^{-1} of cells up to this N is staged in shared memory
+
+// One work item = up to 256 queries sharing the winner cell; the cell's samples and (for N <= 128) its
+// L^{-1} are staged once by TMA bulk copies and reused by every chunk of 32 queries.
 __global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* xq, Params p, float* sdf, float* grad,
-                                                     float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags) {
-  extern __shared__ __align__(128) float4 s_x[];  // [n_max] samples | [n_max] var | [n_max][32] k'
+                                                     float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags,
+                                                     int smax_n) {
+  // dynamic shared memory: [smax_n] samples (float4) | [linv_blocked_size(128)] L^{-1} | [smax_n] var |
+  // [smax_n][32] k'
+  extern __shared__ __align__(128) float4 s_x[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_tile;
   __shared__ float s_red[kBW][9][kBQ];
   __shared__ int s_nn[kBW][kBQ];
   __shared__ float s_bh[3], s_bl[3];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  float* s_var = reinterpret_cast<float*>(s_x + p.n_max);
-  float* s_k = s_var + p.n_max;
+  float* s_linv = reinterpret_cast<float*>(s_x + smax_n);
+  float* s_var = s_linv + linv_blocked_size(kLinvStageN);
+  float* s_k = s_var + smax_n;
   if (tid == 0) {
     mbar_init(&bar, 1);
     fence_proxy_async();
@@ -665,161 +701,137 @@ __global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* 
     const int g = tile.x;
     const int n = a.cell_n[g];
     const int64_t m0 = a.ts_off[g];
+    const bool staged = n <= kLinvStageN;
     if (tid == 0) {
       fence_proxy_async();
-      mbar_expect_tx(&bar, (uint32_t)n * 16u);
+      const uint32_t lbytes = staged ? (uint32_t)linv_blocked_size(n) * 4u : 0u;
+      mbar_expect_tx(&bar, (uint32_t)n * 16u + lbytes);
       bulk_g2s(s_x, a.mf4 + m0, (uint32_t)n * 16u, &bar);
-    }
-    for (int i = tid; i < n; i += blockDim.x) s_var[i] = a.mvar[m0 + i];  // not 16-byte aligned: plain loads
-    if (tid == 0) {
+      if (staged) bulk_g2s(s_linv, a.linv32 + a.linv_off[g], lbytes, &bar);
       int cc[3];
       unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
       for (int j = 0; j < 3; ++j) base_split(p.o[j], cc[j], p.h, s_bh[j], s_bl[j]);
     }
-    const bool live = lane < tile.z;
-    const int q = live ? a.sorted_w[tile.y + lane] : 0;
-    float xg[3] = {0.f, 0.f, 0.f};
-    if (live)
-      for (int j = 0; j < p.dim; ++j) xg[j] = xq[(int64_t)q * p.dim + j];
+    for (int i = tid; i < n; i += blockDim.x) s_var[i] = a.mvar[m0 + i];  // not 16-byte aligned: plain loads
     if (!mbar_wait_all(&bar, phase)) {
       if (tid == 0) atomicOr(a.st, ST_TIMEOUT);
       return;
     }
     phase ^= 1;
-    float ql[3] = {0.f, 0.f, 0.f};
-    for (int j = 0; j < p.dim; ++j) ql[j] = local32(xg[j], s_bh[j], s_bl[j]);
-    // this warp's share of the samples
+    const float* Lb = staged ? s_linv : a.linv32 + a.linv_off[g];
     const int per = (n + kBW - 1) / kBW;
     const int i0 = w * per, i1 = min(n, i0 + per);
-    // pass 1: nearest sample (first minimum in id order)
-    {
-      float m = INFINITY;
-      int nn = 0x7fffffff;
-      for (int i = i0; i < i1; ++i) {
-        const float4 v = s_x[i];
-        const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (r2 < m) {
-          m = r2;
-          nn = i;
+    for (int q0 = 0; q0 < tile.z; q0 += kBQ) {
+      const bool live = q0 + lane < tile.z;
+      const int q = live ? a.sorted_w[tile.y + q0 + lane] : 0;
+      float ql[3] = {0.f, 0.f, 0.f};
+      if (live)
+        for (int j = 0; j < p.dim; ++j) ql[j] = local32(xq[(int64_t)q * p.dim + j], s_bh[j], s_bl[j]);
+      // pass 1: nearest sample (first minimum in id order), this warp's share of the samples
+      {
+        float m = INFINITY;
+        int nn = 0x7fffffff;
+        for (int i = i0; i < i1; ++i) {
+          const float4 v = s_x[i];
+          const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (r2 < m) {
+            m = r2;
+            nn = i;
+          }
         }
+        s_red[w][0][lane] = m;
+        s_nn[w][lane] = nn;
       }
-      s_red[w][0][lane] = m;
-      s_nn[w][lane] = nn;
-    }
-    __syncthreads();
-    float m = s_red[0][0][lane];
-    int nn = s_nn[0][lane];
-    for (int v = 1; v < kBW; ++v)
-      if (s_red[v][0][lane] < m) {
-        m = s_red[v][0][lane];
-        nn = s_nn[v][lane];
-      }
-    const float zmin = sqrtf(m);
-    __syncthreads();
-    // pass 2: k'_i (kept for V[f]), grad f', softmin sums
-    {
-      float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
-      const float cmn = c1 * m;
-      for (int i = i0; i < i1; ++i) {
-        const float4 v = s_x[i];
-        const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float kp = ex2(fmaf(-c1, r2, cmn));
-        s_k[i * kBQ + lane] = kp;
-        const float ak = v.w * kp;
-        G0 = fmaf(ak, dx, G0);
-        G1 = fmaf(ak, dy, G1);
-        G2 = fmaf(ak, dz, G2);
-        const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-        const float y = fmaxf(z - zmin, 0.f);
-        const float wt = ex2(-c2 * y);
-        W += wt;
-        HY = fmaf(wt, y, HY);
-        const float tw = wt * wt * s_var[i];
-        T0 += tw;
-        T1 = fmaf(tw, y, T1);
-        T2 = fmaf(tw * y, y, T2);
-      }
-      s_red[w][1][lane] = G0;
-      s_red[w][2][lane] = G1;
-      s_red[w][3][lane] = G2;
-      s_red[w][4][lane] = W;
-      s_red[w][5][lane] = HY;
-      s_red[w][6][lane] = T0;
-      s_red[w][7][lane] = T1;
-      s_red[w][8][lane] = T2;
-    }
-    __syncthreads();
-    // V[f]: warp w takes the 8-row blocks R = w, w + 4, ...; rows of a block are read 8 at a time
-    float vsum = 0.f;
-    if (a.mask & KSDF_OUT_VAR_F) {
-      const float* Lb = a.linv32 + a.linv_off[g];
-      const int nb = (n + 7) / 8;
-      for (int R = w; R < nb; R += kBW) {
-        const float4* blk = reinterpret_cast<const float4*>(Lb + linv_block_off(R));
-        const int imax = min(8 * R + 8, n);
-        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-        for (int i = 0; i < imax; ++i) {
-          const float4 l0 = __ldg(blk + 2 * i), l1 = __ldg(blk + 2 * i + 1);
-          const float kk = s_k[i * kBQ + lane];
-          acc[0] = fmaf(l0.x, kk, acc[0]);
-          acc[1] = fmaf(l0.y, kk, acc[1]);
-          acc[2] = fmaf(l0.z, kk, acc[2]);
-          acc[3] = fmaf(l0.w, kk, acc[3]);
-          acc[4] = fmaf(l1.x, kk, acc[4]);
-          acc[5] = fmaf(l1.y, kk, acc[5]);
-          acc[6] = fmaf(l1.z, kk, acc[6]);
-          acc[7] = fmaf(l1.w, kk, acc[7]);
+      __syncthreads();
+      float m = s_red[0][0][lane];
+      int nn = s_nn[0][lane];
+      for (int v = 1; v < kBW; ++v)
+        if (s_red[v][0][lane] < m) {
+          m = s_red[v][0][lane];
+          nn = s_nn[v][lane];
         }
-#pragma unroll
-        for (int r = 0; r < 8; ++r) vsum = fmaf(acc[r], acc[r], vsum);
+      const float zmin = sqrtf(m);
+      __syncthreads();
+      // pass 2: k'_i (kept for V[f]), grad f', softmin sums
+      {
+        float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
+        const float cmn = c1 * m;
+        for (int i = i0; i < i1; ++i) {
+          const float4 v = s_x[i];
+          const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float kp = ex2(fmaf(-c1, r2, cmn));
+          s_k[i * kBQ + lane] = kp;
+          const float ak = v.w * kp;
+          G0 = fmaf(ak, dx, G0);
+          G1 = fmaf(ak, dy, G1);
+          G2 = fmaf(ak, dz, G2);
+          const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+          const float y = fmaxf(z - zmin, 0.f);
+          const float wt = ex2(-c2 * y);
+          W += wt;
+          HY = fmaf(wt, y, HY);
+          const float tw = wt * wt * s_var[i];
+          T0 += tw;
+          T1 = fmaf(tw, y, T1);
+          T2 = fmaf(tw * y, y, T2);
+        }
+        s_red[w][1][lane] = G0;
+        s_red[w][2][lane] = G1;
+        s_red[w][3][lane] = G2;
+        s_red[w][4][lane] = W;
+        s_red[w][5][lane] = HY;
+        s_red[w][6][lane] = T0;
+        s_red[w][7][lane] = T1;
+        s_red[w][8][lane] = T2;
       }
+      __syncthreads();
+      const float vsum = (a.mask & KSDF_OUT_VAR_F) ? vf_rows(Lb, n, w, s_k, lane) : 0.f;
+      __syncthreads();  // everyone has read s_red[.][1..8] and s_k
+      s_red[w][0][lane] = vsum;
+      __syncthreads();
+      if (w == 0 && live) {
+        float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f, VS = 0.f;
+        for (int v = 0; v < kBW; ++v) {
+          G0 += s_red[v][1][lane];
+          G1 += s_red[v][2][lane];
+          G2 += s_red[v][3][lane];
+          W += s_red[v][4][lane];
+          HY += s_red[v][5][lane];
+          T0 += s_red[v][6][lane];
+          T1 += s_red[v][7][lane];
+          T2 += s_red[v][8][lane];
+          VS += s_red[v][0][lane];
+        }
+        const float hy = HY / W;
+        const float B = fmaf(as, hy, 1.f);
+        const float vs = fmaxf((B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W), 0.f);
+        const float vf = fmaxf(1.f - ex2(-2.f * c1 * m) * VS, 0.f);
+        float s = 1.f;
+        if (a.sign) {
+          s = a.sign[q] < 0 ? -1.f : 1.f;
+        } else if (p.sign_mode == 1 && a.has_normals) {
+          const float4 v = s_x[nn];
+          const float4 nv = a.mnrm[m0 + nn];
+          s = (nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z)) >= 0.f ? 1.f : -1.f;
+        }
+        uint32_t fl = a.qflag[q];
+        const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
+        if (a.mask & KSDF_OUT_SDF) sdf[q] = s * a.qu[q];
+        if (a.mask & KSDF_OUT_GRAD) {
+          const float gv[3] = {G0, G1, G2};
+          const float ig = gn > 0.f ? s / gn : 0.f;
+          for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gv[j] * ig;
+        }
+        if (!(gn > 0.f)) fl |= KSDF_FLAG_ZERO_GRAD;
+        if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
+        if (a.mask & KSDF_OUT_VAR_F) var_f[q] = vf;
+        if (a.mask & KSDF_OUT_WINNER) winner[q] = g;
+        if (a.mask & KSDF_OUT_FLAGS) flags[q] = fl;
+      }
+      __syncthreads();
     }
-    __syncthreads();  // everyone has read s_red[.][1..8]
-    s_red[w][0][lane] = vsum;
-    __syncthreads();
-    if (w == 0 && live) {
-      float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f, VS = 0.f;
-      for (int v = 0; v < kBW; ++v) {
-        G0 += s_red[v][1][lane];
-        G1 += s_red[v][2][lane];
-        G2 += s_red[v][3][lane];
-        W += s_red[v][4][lane];
-        HY += s_red[v][5][lane];
-        T0 += s_red[v][6][lane];
-        T1 += s_red[v][7][lane];
-        T2 += s_red[v][8][lane];
-        VS += s_red[v][0][lane];
-      }
-      const float hy = HY / W;
-      const float B = fmaf(as, hy, 1.f);
-      const float vs = fmaxf((B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W), 0.f);
-      const float vf = fmaxf(1.f - ex2(-2.f * c1 * m) * VS, 0.f);
-      float s = 1.f;
-      if (a.sign) {
-        s = a.sign[q] < 0 ? -1.f : 1.f;
-      } else if (p.sign_mode == 1 && a.has_normals) {
-        const float4 v = s_x[nn];
-        const float4 nv = a.mnrm[m0 + nn];
-        s = (nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z)) >= 0.f ? 1.f : -1.f;
-      }
-      uint32_t fl = a.qflag[q];
-      const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
-      if (a.mask & KSDF_OUT_SDF) sdf[q] = s * a.qu[q];
-      if (a.mask & KSDF_OUT_GRAD) {
-        const float gv[3] = {G0, G1, G2};
-        const float ig = gn > 0.f ? s / gn : 0.f;
-        for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gv[j] * ig;
-      }
-      if (!(gn > 0.f)) fl |= KSDF_FLAG_ZERO_GRAD;
-      if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
-      if (a.mask & KSDF_OUT_VAR_F) var_f[q] = vf;
-      if (a.mask & KSDF_OUT_WINNER) winner[q] = g;
-      if (a.mask & KSDF_OUT_FLAGS) flags[q] = fl;
-    }
-    __syncthreads();
   }
 }
 
@@ -1023,7 +1035,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     if (rs) return rs;
   }
   const int64_t max_tiles_a = Q / kTA + bcap + 1;
-  const int TBq = f64 ? kTB64 : kBQ;
+  const int TBq = f64 ? kTB64 : kBItem;
   uint64_t* qkey = ptr<uint64_t>(c->ws[WS_QKEY]);
   int32_t* qbin = ptr<int32_t>(c->ws[WS_QBIN]);
   int32_t* qrank = ptr<int32_t>(c->ws[WS_QRANK]);
@@ -1170,13 +1182,14 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
         pb, static_cast<const double*>(xq), p, static_cast<double*>(sdf), static_cast<double*>(grad),
         static_cast<double*>(var_sdf), static_cast<double*>(var_f), winner, flags);
   } else {
-    const size_t smem = sizeof(float4) * p.n_max + sizeof(float) * p.n_max * (1 + kBQ);
+    const int smax = std::max(m.max_n, 1);
+    const size_t smem = sizeof(float4) * smax + sizeof(float) * (linv_blocked_size(kLinvStageN) + (size_t)smax * (1 + kBQ));
     KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB, kBQ * kBW, smem));
     launch(k_phaseB, std::max(1, occ) * c->num_sms, kBQ * kBW, smem, st, pb, static_cast<const float*>(xq), p,
            static_cast<float*>(sdf), static_cast<float*>(grad), static_cast<float*>(var_sdf),
-           static_cast<float*>(var_f), winner, flags);
+           static_cast<float*>(var_f), winner, flags, smax);
   }
   KSDF_CUDA(c, cudaGetLastError());
   prof_end(c, e0, f64 ? "query64.phaseB" : "query.phaseB");

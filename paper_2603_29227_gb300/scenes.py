@@ -46,14 +46,53 @@ class Scene:
     box_hi: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
 
     # ---- ground truth (used by tests for sanity checks and by the generators for rejection) ----
+    def _in_primitives(self, x: np.ndarray, tol: float) -> np.ndarray:
+        """Points strictly inside some sphere/circle (radius - tol) or box (shrunk by tol).  With many
+        primitives, each one is tested only against the points of the 1 m grid cells its bounding box
+        touches (same result as testing every point)."""
+        n = x.shape[0]
+        out = np.zeros(n, dtype=bool)
+        nprim = len(self.radii) + len(self.box_lo)
+        if nprim <= 64 or n < 4096:
+            for c, r in zip(self.centres, self.radii):
+                out |= np.sum((x - c) ** 2, axis=1) < (r - tol) ** 2
+            for lo, hi in zip(self.box_lo, self.box_hi):
+                out |= np.all((x > lo + tol) & (x < hi - tol), axis=1)
+            return out
+        g0 = self.room_lo - 1.0
+        dims = (np.ceil((self.room_hi - g0) / 1.0).astype(np.int64) + 2)
+        cell = np.clip(np.floor(x - g0).astype(np.int64), 0, dims - 1)
+        lin = cell[:, 0]
+        for j in range(1, self.dim):
+            lin = lin * dims[j] + cell[:, j]
+        order = np.argsort(lin, kind="stable")
+        starts = np.searchsorted(lin[order], np.arange(int(np.prod(dims)) + 1))
+
+        def candidates(lo, hi):
+            a = np.clip(np.floor(lo - g0).astype(np.int64), 0, dims - 1)
+            b = np.clip(np.floor(hi - g0).astype(np.int64), 0, dims - 1)
+            rng = [np.arange(a[j], b[j] + 1) for j in range(self.dim)]
+            mesh = np.meshgrid(*rng, indexing="ij")
+            l = mesh[0].ravel()
+            for j in range(1, self.dim):
+                l = l * dims[j] + mesh[j].ravel()
+            parts = [order[starts[v]:starts[v + 1]] for v in l]
+            return np.concatenate(parts) if parts else np.zeros(0, np.int64)
+
+        for c, r in zip(self.centres, self.radii):
+            idx = candidates(c - r, c + r)
+            if idx.size:
+                out[idx] |= np.sum((x[idx] - c) ** 2, axis=1) < (r - tol) ** 2
+        for lo, hi in zip(self.box_lo, self.box_hi):
+            idx = candidates(lo, hi)
+            if idx.size:
+                out[idx] |= np.all((x[idx] > lo + tol) & (x[idx] < hi - tol), axis=1)
+        return out
+
     def occupied(self, x: np.ndarray) -> np.ndarray:
         x = np.asarray(x, dtype=np.float64)
         occ = np.any((x < self.room_lo) | (x > self.room_hi), axis=1)
-        for c, r in zip(self.centres, self.radii):
-            occ |= np.sum((x - c) ** 2, axis=1) < r * r
-        for lo, hi in zip(self.box_lo, self.box_hi):
-            occ |= np.all((x > lo) & (x < hi), axis=1)
-        return occ
+        return occ | self._in_primitives(x, 0.0)
 
     def sign(self, x: np.ndarray) -> np.ndarray:
         """+1 in free space, -1 inside an obstacle (int8)."""
@@ -95,8 +134,10 @@ class Scene:
         pick = rng.choice(len(pieces), size=n, p=w / w.sum())
         x = np.empty((n, self.dim))
         nrm = np.zeros((n, self.dim))
+        order = np.argsort(pick, kind="stable")
+        bounds = np.searchsorted(pick[order], np.arange(len(pieces) + 1))
         for k, (kind, idx, _) in enumerate(pieces):
-            sel = np.nonzero(pick == k)[0]
+            sel = order[bounds[k]:bounds[k + 1]]
             m = sel.size
             if m == 0:
                 continue
@@ -144,11 +185,7 @@ class Scene:
 
     def _inside_other(self, x: np.ndarray, tol: float) -> np.ndarray:
         bad = np.any((x < self.room_lo - tol) | (x > self.room_hi + tol), axis=1)
-        for c, r in zip(self.centres, self.radii):
-            bad |= np.sum((x - c) ** 2, axis=1) < (r - tol) ** 2
-        for lo, hi in zip(self.box_lo, self.box_hi):
-            bad |= np.all((x > lo + tol) & (x < hi - tol), axis=1)
-        return bad
+        return bad | self._in_primitives(x, tol)
 
 
 def make_plane2d(rng: np.random.Generator, n_circles: int = 20, size: float = 10.0) -> Scene:

@@ -11,7 +11,10 @@ Exclusions, each counted and bounded:
     minimum, and gradient/variances are compared with the oracle evaluated on the GPU's winner;
   - medial-axis queries for the gradient angle: cancellation ratio
     |sum_i a_i k'_i (x - x_i)| / sum_i |a_i| k'_i |x - x_i| < 1e-2 on the winner (the direction of a
-    nearly cancelling sum is ill-conditioned), and zero-gradient flags.
+    nearly cancelling sum is ill-conditioned), and zero-gradient flags;
+  - gradients whose FP32 condition estimate kappa = (1 + lambda d^2) 2^-23 / ratio exceeds a tenth of the
+    tolerance (far queries in cancelling configurations, where the 0.1 deg bound is out of reach of any
+    FP32 evaluation); these are still required to stay within 20 kappa.
 """
 import numpy as np
 
@@ -43,6 +46,14 @@ def cancellation_ratio(model, xq, cells):
         den = np.sum(np.abs(al) * kp * np.sqrt(r2), axis=1)
         out[sel] = num / np.maximum(den, 1e-300)
     return out
+
+
+def fp32_direction_condition(lam, d, ratio):
+    """Expected error (radians) of the gradient direction from FP32 inputs: each term alpha_i k'_i r_i of
+    the gradient sum carries a relative error of about (1 + lambda d^2) 2^-23 (metre-scale differences
+    rounded to FP32, amplified by lambda in the kernel exponent), and the direction of a sum that cancels
+    to `ratio` of its absolute sum is that many times more sensitive."""
+    return (1.0 + lam * d * d) * 2.0 ** -23 / np.maximum(ratio, 1e-300)
 
 
 def _ang_deg(a, b):
@@ -77,15 +88,32 @@ def check_mixed(model, xq, sign, gpu, label=""):
         for key in ("grad", "var_sdf", "var_f"):
             ref[key][diff] = alt[key]
     ok = fin
-    # gradient angle with medial-axis and zero-gradient exclusions
+    # gradient angle with medial-axis, FP32-conditioning and zero-gradient exclusions
     ratio = cancellation_ratio(model, xq, np.where(ok, gw, -1))
     zero = ((gpu["flags"] | ref["flags"]) & 8) != 0
     med = ratio < MEDIAL_RATIO
-    gsel = ok & ~zero & ~med
+    lam = model.params["lambda"]
+    d = np.where(fin, np.abs(ref["sdf"]), 0.0)
+    kappa = fp32_direction_condition(lam, d, ratio)  # radians
+    illc = np.degrees(10.0 * kappa) > ANGLE_TOL_DEG
+    gsel = ok & ~zero & ~med & ~illc
     ang = _ang_deg(gpu["grad"].astype(np.float64)[gsel], ref["grad"][gsel])
     stats["angle_max_deg"] = float(ang.max()) if ang.size else 0.0
     stats["medial_excluded"] = int((ok & med).sum())
-    assert stats["angle_max_deg"] <= ANGLE_TOL_DEG, "%s: max angle %g deg" % (label, stats["angle_max_deg"])
+    stats["fp32_illcond_excluded"] = int((ok & ~med & illc).sum())
+    isel = ok & ~zero & ~med & illc
+    if isel.any():  # still bounded by their own FP32 conditioning
+        ai = _ang_deg(gpu["grad"].astype(np.float64)[isel], ref["grad"][isel])
+        assert np.all(ai <= np.degrees(20.0 * kappa[isel])), "%s: ill-conditioned gradient beyond 20 kappa" % label
+    if ang.size and stats["angle_max_deg"] > ANGLE_TOL_DEG:
+        keys, status, off, mem = model.cells()
+        idx = np.nonzero(gsel)[0]
+        worst = idx[np.argsort(-ang)[:5]]
+        diag = ["q=%d ang=%.3g ratio=%.3g sdf=%.3g N=%d" % (q, a, ratio[q], ref["sdf"][q], off[gw[q] + 1] - off[gw[q]])
+                for q, a in zip(worst, np.sort(ang)[::-1][:5])]
+        over = ang > ANGLE_TOL_DEG
+        diag.append("over=%d of %d; ratio of those: %s" % (over.sum(), ang.size, np.round(ratio[idx[over]], 4)[:12]))
+        raise AssertionError("%s: max angle %g deg; %s" % (label, stats["angle_max_deg"], "; ".join(diag)))
     rv = ref["var_sdf"][ok]
     ev = np.abs(gpu["var_sdf"][ok].astype(np.float64) - rv)
     stats["var_sdf_max_rel"] = float(np.max(ev / np.maximum(np.abs(rv), 1e-30))) if ev.size else 0.0
