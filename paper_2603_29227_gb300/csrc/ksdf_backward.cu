@@ -255,12 +255,6 @@ __global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Par
   }
 }
 
-// L^{-1}[j][i] (i <= 8 floor(j/8) + 7) in the 8-row blocked FP32 layout
-__device__ __forceinline__ float linv_at(const float* Lb, int j, int i) {
-  const int R = j >> 3;
-  return Lb[linv_block_off(R) + (int64_t)i * 8 + (j & 7)];
-}
-
 // per touched cell: b = A^{-1} alpha_bar.  b0 = L^{-T} L^{-1} alpha_bar with the FP32 L^{-1}; one step of
 // iterative refinement against the FP64 factor, r = alpha_bar - L (L^T b0) (the only FP64 work, N^2
 // FMAs), b = b0 + L^{-T} L^{-1} r; then the alpha-path X_bar terms in FP32.
@@ -268,9 +262,16 @@ __device__ void linv_solve32(const float* Lb, int n, const float* rhs, float* y,
   // y = L^{-1} rhs (rows over threads; 8 consecutive rows share a 32-byte sector per column)
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     const float* row = Lb + linv_block_off(j >> 3) + (j & 7);
-    float acc = 0.f;
-    for (int i = 0; i <= j; ++i) acc = fmaf(row[(int64_t)i * 8], rhs[i], acc);
-    y[j] = acc;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;  // four independent chains
+    int i = 0;
+    for (; i + 3 <= j; i += 4) {
+      a0 = fmaf(row[(int64_t)i * 8], rhs[i], a0);
+      a1 = fmaf(row[(int64_t)(i + 1) * 8], rhs[i + 1], a1);
+      a2 = fmaf(row[(int64_t)(i + 2) * 8], rhs[i + 2], a2);
+      a3 = fmaf(row[(int64_t)(i + 3) * 8], rhs[i + 3], a3);
+    }
+    for (; i <= j; ++i) a0 = fmaf(row[(int64_t)i * 8], rhs[i], a0);
+    y[j] = (a0 + a1) + (a2 + a3);
   }
   __syncthreads();
   // out (+)= L^{-T} y (columns over threads; the 8 rows of a block at one column are contiguous)
@@ -316,18 +317,35 @@ __global__ void __launch_bounds__(256) k_bw_cell(const int64_t* qcnt, int64_t G,
     for (int k = threadIdx.x; k < n; k += blockDim.x) st[k] = 0.0;
     for (int k0 = 0; k0 < n; k0 += blockDim.x) {
       const int k = k0 + threadIdx.x;
-      double acc = 0.0;
-      for (int i = k0; i < n; ++i)
-        if (k < n && k <= i) acc = fma(L[(int64_t)i * (i + 1) / 2 + k], (double)sb[i], acc);
-      if (k < n) st[k] = acc;
+      double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;  // four independent chains (DFMA latency ~64 cycles)
+      // a warp walks rows from its first lane's column so that a row's loads coalesce; entries above the
+      // diagonal (k > i, read in bounds from the following row) are masked to zero
+      int i = k0 + (threadIdx.x & ~31);
+      if (k < n) {
+        for (; i + 3 < n; i += 4) {
+          c0 = fma(k <= i ? L[tri_sz(i) + k] : 0.0, (double)sb[i], c0);
+          c1 = fma(k <= i + 1 ? L[tri_sz(i + 1) + k] : 0.0, (double)sb[i + 1], c1);
+          c2 = fma(k <= i + 2 ? L[tri_sz(i + 2) + k] : 0.0, (double)sb[i + 2], c2);
+          c3 = fma(k <= i + 3 ? L[tri_sz(i + 3) + k] : 0.0, (double)sb[i + 3], c3);
+        }
+        for (; i < n; ++i) c0 = fma(k <= i ? L[tri_sz(i) + k] : 0.0, (double)sb[i], c0);
+        st[k] = (c0 + c1) + (c2 + c3);
+      }
     }
     __syncthreads();
     // r = alpha_bar - L t (rows over threads)
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const double* Li = L + (int64_t)i * (i + 1) / 2;
-      double acc = sa[i];
-      for (int k = 0; k <= i; ++k) acc = fma(-Li[k], st[k], acc);
-      srhs[i] = (float)acc;
+      double c0 = sa[i], c1 = 0.0, c2 = 0.0, c3 = 0.0;
+      int k = 0;
+      for (; k + 3 <= i; k += 4) {
+        c0 = fma(-Li[k], st[k], c0);
+        c1 = fma(-Li[k + 1], st[k + 1], c1);
+        c2 = fma(-Li[k + 2], st[k + 2], c2);
+        c3 = fma(-Li[k + 3], st[k + 3], c3);
+      }
+      for (; k <= i; ++k) c0 = fma(-Li[k], st[k], c0);
+      srhs[i] = (float)((c0 + c1) + (c2 + c3));
     }
     __syncthreads();
     linv_solve32(Lb, n, srhs, sy, sb, true);  // b = b0 + L^{-T} L^{-1} r
@@ -417,7 +435,9 @@ ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* 
   e0 = prof_begin(c);
   const size_t smem2 = sizeof(double) * 2 * p.n_max + sizeof(float) * 3 * p.n_max;
   KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-  const unsigned grid2 = (unsigned)std::min<int64_t>(G, 4LL * c->num_sms);
+  int occ2 = 0;
+  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_bw_cell, 256, smem2));
+  const unsigned grid2 = (unsigned)std::min<int64_t>(G, (int64_t)std::max(1, occ2) * c->num_sms);
   launch(k_bw_cell, std::max(1u, grid2), 256, smem2, st, cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
          ptr<int64_t>(m.chol_off), ptr<double>(m.chol64), ptr<int64_t>(m.linv_off), ptr<float>(m.linv32),
          ptr<float4>(m.mf4), ptr<int32_t>(m.mgid), abar, p, d_x);

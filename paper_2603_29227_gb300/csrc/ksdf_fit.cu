@@ -149,27 +149,28 @@ __global__ void __launch_bounds__(512) k_assemble(const uint64_t* cell_key, int6
     lo[j] = __dsub_rn(cell_base(p.o[j], c[j], p.h), p.mu);
     hi[j] = __dadd_rn(cell_base(p.o[j], c[j] + 1, p.h), p.mu);
   }
-  const int zr = p.dim == 3 ? R : 0;
-  for (int dz = -zr; dz <= zr; ++dz)
-    for (int dy = -R; dy <= R; ++dy)
-      for (int dx = -R; dx <= R; ++dx) {
-        int64_t nb[3] = {(int64_t)c[0] + dx, (int64_t)c[1] + dy, (int64_t)c[2] + dz};
-        bool inr = true;
-        for (int j = 0; j < 3; ++j) inr &= nb[j] >= -kBias && nb[j] < kBias;
-        if (!inr) continue;
-        int h = hash_find(hk, hv, hcap, pack_key(nb[0], nb[1], nb[2]));
-        if (h < 0) continue;
-        for (int64_t t = own_off[h] + threadIdx.x; t < own_off[h + 1]; t += blockDim.x) {
-          uint32_t id = own_id[t];
-          const double* xi = x + (int64_t)id * p.dim;
-          bool in = true;
-          for (int j = 0; j < p.dim; ++j) in &= (xi[j] >= lo[j]) && (xi[j] < hi[j]);
-          if (in) {
-            int pos = atomicAdd(&cnt, 1);
-            if (pos < kMaxPre) ids[pos] = (int)id;
-          }
-        }
+  // neighbour cells are spread over the warps (their hash lookups and member scans overlap)
+  const int side = 2 * R + 1, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int nnb = p.dim == 3 ? side * side * side : side * side;
+  for (int v = threadIdx.x >> 5; v < nnb; v += nwarps) {
+    const int dx = v % side - R, dy = (v / side) % side - R, dz = p.dim == 3 ? v / (side * side) - R : 0;
+    int64_t nb[3] = {(int64_t)c[0] + dx, (int64_t)c[1] + dy, (int64_t)c[2] + dz};
+    bool inr = true;
+    for (int j = 0; j < 3; ++j) inr &= nb[j] >= -kBias && nb[j] < kBias;
+    if (!inr) continue;
+    const int h = hash_find(hk, hv, hcap, pack_key(nb[0], nb[1], nb[2]));
+    if (h < 0) continue;
+    for (int64_t t = own_off[h] + lane; t < own_off[h + 1]; t += 32) {
+      const uint32_t id = own_id[t];
+      const double* xi = x + (int64_t)id * p.dim;
+      bool in = true;
+      for (int j = 0; j < p.dim; ++j) in &= (xi[j] >= lo[j]) && (xi[j] < hi[j]);
+      if (in) {
+        const int pos = atomicAdd(&cnt, 1);
+        if (pos < kMaxPre) ids[pos] = (int)id;
       }
+    }
+  }
   __syncthreads();
   int n = cnt;
   if (n > kMaxPre) {
@@ -286,12 +287,12 @@ __global__ void __launch_bounds__(256) k_fit(FitArgs a, Params p) {
   __shared__ int s_cell, s_fail;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
   double* tab = sm;
-  double* dinv = tab + 32;
+  double* dinv = tab + kExpTab;
   double* sx = dinv + a.np;
   double* sb = sx + 3 * a.np;
   double* A = a.smem_mat ? sb + a.np : a.gscr + (int64_t)blockIdx.x * a.gstride;
   float* X = reinterpret_cast<float*>(A);  // L^{-1} in FP32 overwrites the FP64 factor at the end
-  for (int i = tid; i < 32; i += nthr) tab[i] = kExp2Frac32[i];
+  for (int i = tid; i < kExpTab; i += nthr) tab[i] = kExp2FracTab[i];
   const double lam = p.lambda;
   for (;;) {
     if (tid == 0) {
@@ -497,7 +498,7 @@ static int bits_for(uint64_t v) {
 }
 
 static size_t fit_smem(int np, bool smem_mat) {
-  size_t d = 32 + 5 * (size_t)np;  // exp table, reciprocal pivots, coordinates, right-hand side
+  size_t d = kExpTab + 5 * (size_t)np;  // exp table, reciprocal pivots, coordinates, right-hand side
   if (smem_mat) d += (size_t)tri_sz(np);
   return d * sizeof(double);
 }

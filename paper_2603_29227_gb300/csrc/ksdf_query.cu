@@ -639,7 +639,13 @@ __device__ __forceinline__ float vf_rows(const float* Lb, int n, int w, const fl
   // sum over this warp's 8-row blocks R = w, w + 4, ... of |L^{-1}[8R..8R+7][:] k'|^2
   float vsum = 0.f;
   const int nb = (n + 7) / 8;
-  for (int R = w; R < nb; R += kBW) {
+  // serpentine assignment: blocks w, 2 kBW - 1 - w, 2 kBW + w, ... (the work of block R grows with R)
+  for (int k = 0;; ++k) {
+    const int R = (k >> 1) * 2 * kBW + ((k & 1) ? 2 * kBW - 1 - w : w);
+    if (R >= nb) {
+      if (k & 1) continue;
+      break;
+    }
     const float4* blk = reinterpret_cast<const float4*>(Lb + linv_block_off(R));
     const int imax = min(8 * R + 8, n);
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
