@@ -1,12 +1,14 @@
 """Generate the constants of the binary64 exponential used by the fit (ksdf_exp.cuh).
 
-The method is the table-driven exponential of P. T. P. Tang ("Table-driven implementation of the
-exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
-    x = (32 m + j) ln2/32 + r,  |r| <= ln2/64,   exp(x) = 2^m * 2^(j/32) * exp(r).
-The library uses 256 table entries: x = (256 m + j) ln2/256 + r, |r| <= ln2/512.  This script computes,
-with 60-digit decimal arithmetic, ln 2 / 256 split into a head with its low 24 bits zero (so n * head is
-exact for |n| < 2^24) and a tail, 256 / ln 2, and 2^(j/256) for j < 256 rounded to binary64.  Run it to
-reproduce the literals in ksdf_exp.cuh.
+The fit needs exp(-lambda r^2) to binary64 accuracy.  Its argument is carried in units of ln2 / 2^16:
+e = (2^16 / ln2) lambda r^2, so that the value is 2^(-e / 2^16).  With n = round(e) = 2^16 m + 2^8 a + b
+(0 <= a, b < 256) and r = e - n (|r| <= 1/2),
+    2^(-e / 2^16) = 2^-m * T1[a] * T2[b] * exp(-C1 r),   T1[a] = 2^(-a/256),  T2[b] = 2^(-b/65536),
+and exp(-C1 r) = 1 - C1 r + C1^2 r^2 / 2 to within 3e-17 (C1 = ln2 / 2^16, |C1 r| <= 5.3e-6).  This is a
+two-level table method in the spirit of P. T. P. Tang ("Table-driven implementation of the exponential
+function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989) with a table fine enough for a
+second-degree polynomial.  This script computes the tables and constants with 60-digit decimal arithmetic
+and prints them; run it to reproduce the literals in ksdf_exp.cuh.
 """
 from decimal import Decimal, getcontext
 
@@ -26,32 +28,32 @@ def ln2():
     return s
 
 
+def exp_dec(x: Decimal) -> Decimal:
+    # Taylor series; |x| < 1 here
+    s, t, k = Decimal(1), Decimal(1), 1
+    while abs(t) > Decimal(10) ** -58:
+        t = t * x / k
+        s += t
+        k += 1
+    return s
+
+
 def to_double(d: Decimal) -> float:
     return float(d)  # correctly rounded (Python converts the decimal string exactly)
 
 
 def main():
-    T = 256
     L = ln2()
-    l32 = L / T
-    head = float(l32)
-    import struct
-
-    bits = struct.unpack("<Q", struct.pack("<d", head))[0] & ~((1 << 24) - 1)
-    head = struct.unpack("<d", struct.pack("<Q", bits))[0]
-    tail = to_double(l32 - Decimal(head))
-    inv = to_double(Decimal(T) / L)
-    print("// ln2/256 head, tail; 256/ln2")
-    print("constexpr double kLn2_TabHi = %s;  // %r" % (head.hex(), head))
-    print("constexpr double kLn2_TabLo = %s;  // %r" % (tail.hex(), tail))
-    print("constexpr double kInvLn2_Tab = %s;  // %r" % (inv.hex(), inv))
-    print("// 2^(j/256), j = 0..255")
-    vals = []
-    for j in range(T):
-        v = to_double((Decimal(2) ** (Decimal(j) / T)))
-        vals.append(v.hex())
-    for i in range(0, T, 4):
-        print("    " + ", ".join(vals[i:i + 4]) + ",")
+    c1 = L / 65536
+    print("// ln2 / 2^16, (ln2 / 2^16)^2 / 2, 2^16 / ln2")
+    print("constexpr double kExpC1 = %s;" % to_double(c1).hex())
+    print("constexpr double kExpC2 = %s;" % to_double(c1 * c1 / 2).hex())
+    print("constexpr double kExpQ16PerNat = %s;" % to_double(Decimal(65536) / L).hex())
+    for name, den in (("kExpT1", 256), ("kExpT2", 65536)):
+        print("// %s[j] = 2^(-j/%d), j = 0..255" % (name, den))
+        vals = [to_double(exp_dec(-Decimal(j) * L / den)).hex() for j in range(256)]
+        for i in range(0, 256, 4):
+            print("    " + ", ".join(vals[i:i + 4]) + ",")
 
 
 if __name__ == "__main__":

@@ -99,19 +99,19 @@ static void prof_fold(ksdf_ctx* c) {
 cudaError_t fork_streams(ksdf_ctx* c) {
   cudaError_t e = cudaSuccess;
   if (!c->aux[0]) {
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
+    for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
+    for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
   }
   e = cudaEventRecord(c->ev_fork, c->stream);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->aux[i], c->ev_fork, 0);
+  for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->aux[i], c->ev_fork, 0);
   return e;
 }
 
 cudaError_t join_streams(ksdf_ctx* c) {
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) {
     e = cudaEventRecord(c->ev_join[i], c->aux[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join[i], 0);
   }
@@ -235,7 +235,7 @@ ksdf_status ksdf_destroy(ksdf_ctx* c) {
     cudaEventDestroy(p.b);
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < ksdf_ctx::kNumAux; ++i) {
     if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
   }

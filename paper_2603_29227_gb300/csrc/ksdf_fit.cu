@@ -14,6 +14,7 @@
 #include "ksdf_exp.cuh"
 #include "ksdf_internal.cuh"
 
+#include <cmath>
 #include <cstdarg>
 #include <vector>
 
@@ -21,11 +22,6 @@ namespace ksdf {
 
 namespace {
 
-constexpr int kPanel = 16;    // Cholesky panel width
-constexpr int kClassS = 96;   // size classes: the packed FP64 matrix in shared memory up to N = 218
-constexpr int kClassM = 160;
-constexpr int kClassL = 218;
-constexpr int kClassXL = kMaxNmax;
 
 __global__ void k_bin_samples(const double* x, const float* var, int64_t S, Params p, uint64_t* keys, uint32_t* vals,
                               int* bbox, uint32_t* status) {
@@ -251,15 +247,14 @@ struct FitArgs {
   double* chol64;
   float* linv32;
   int32_t* status;
-  double* gscr;     // per-CTA global slot (largest class): tri(np) doubles
+  double* gscr;     // per-CTA global slot (largest class): tri(np + 1) doubles
   int64_t gstride;  // doubles per slot
   int np;           // largest N of this class
-  int smem_mat;     // 1: the matrix lives in shared memory
+  double sc;        // sqrt(lambda 2^16 / ln2): coordinates scaled so that |s_i - s_j|^2 is exp2_neg_q16's argument
+  float lamf;       // lambda in FP32 (the near/far screen)
   int* counter;
   int* n_not_pd;
 };
-
-__device__ __forceinline__ int64_t P(int i, int j) { return tri_sz(i) + j; }
 
 // row of the packed lower-triangle entry t (t = i (i+1)/2 + j, j <= i)
 __device__ __forceinline__ int tri_row(int64_t t) {
@@ -269,223 +264,294 @@ __device__ __forceinline__ int tri_row(int64_t t) {
   return i;
 }
 
-__device__ __forceinline__ double kernel_entry(const double* sx, int i, int j, double lam, const double* tab) {
-  const double dx = sx[3 * i] - sx[3 * j], dy = sx[3 * i + 1] - sx[3 * j + 1], dz = sx[3 * i + 2] - sx[3 * j + 2];
-  const double e = lam * (dx * dx + dy * dy + dz * dz);
-  return e > 50.0 ? 0.0 : exp_neg64(-e, tab);  // entries below e^-50 ~ 2e-22 are zero
+constexpr int kB = 8;        // Cholesky panel width
+constexpr float kNearE = 36.f;  // lambda r^2 below this: FP64 entry; above: FP32 (value < 2.4e-16)
+
+__device__ __forceinline__ bool pivot_ok(double d) {  // finite, positive and normal
+  const long long b = __double_as_longlong(d);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  return b > 0 && ex > 0 && ex < 2047;
 }
 
-constexpr int kInvRows = 2;  // rows per thread in the FP32 inversion (N <= 2 * blockDim.x)
+__device__ __forceinline__ void fit_sync(int team) {
+  if (team == 32) __syncwarp();
+  else __syncthreads();
+}
 
-// One cell per iteration of a persistent CTA:
-//   A = K + diag(sigma^2) (FP64, packed lower), blocked Cholesky (FP64: 16-column panels factored by warp 0
-//   with rsqrt pivots, trailing updates in 2x2 register blocks by the whole CTA), alpha by two FP64
-//   triangular solves (warp 0) while the other warps copy L out; then L is converted in place to FP32 and
-//   inverted column by column (all threads), and L^{-1} is written in 8-row blocks.
-__global__ void __launch_bounds__(256) k_fit(FitArgs a, Params p) {
+// Shared-memory layout of one cell's fit (doubles): scaled coordinates 3 np | two column buffers
+// 2 (np + 1) | reciprocal pivots np | FP32 coordinates 4 np floats | near-entry queues 64 ints per warp |
+// FP32 reciprocal pivots np floats | the augmented packed matrix tri(np + 1) (when it lives here).
+__host__ __device__ inline int64_t fit_smem_doubles(int np, int warps, bool smem_mat) {
+  return 3 * (int64_t)np + 2 * ((int64_t)np + 1) + np + 2 * (int64_t)np + 32 * (int64_t)warps + (np + 1) / 2 +
+         (smem_mat ? tri_sz(np + 1) : 0);
+}
+
+// The fit of one cell per iteration of a persistent team (TEAM threads; one warp for the small classes).
+// On GB300 the FP64 pipe retires about two lanes per clock per SM and a warp instruction costs the same
+// whether 1 or 32 lanes are active, so every step keeps its FP64 work in full warps:
+//   1. A = K + diag(sigma^2), augmented with a row of ones (the right-hand side of A alpha = 1).  Each
+//      off-diagonal entry is screened in FP32: lambda r^2 >= 36 gives a value below 2.4e-16 that FP32
+//      evaluates to far better than its absolute rounding; the others are queued per warp and evaluated
+//      32 at a time in FP64 (exp2_neg_q16 on coordinates pre-scaled by sqrt(lambda 2^16 / ln2)).
+//   2. Right-looking Cholesky of the augmented matrix in panels of kB columns: warp 0 factors a panel
+//      (pivots by rsqrt_pivot, column scaling, updates inside the panel, lanes along the rows), then the
+//      team updates the trailing triangle in 2 x 2 register blocks over the panel depth (about three
+//      instructions per DFMA).  The augmented row ends as y = L^{-1} 1.
+//   3. alpha = L^{-T} y by backward substitution (warp 0) while the other warps write L out.
+//   4. L rounded to FP32 in place and inverted column by column; L^{-1} written in 8-row blocks.
+template <int TEAM, int ROWS, bool GMAT>
+__global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitArgs a, Params p) {
+  constexpr int W = TEAM / 32;
   extern __shared__ __align__(16) double sm[];
   __shared__ int s_cell, s_fail;
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  double* tab = sm;
-  double* dinv = tab + kExpTab;
-  double* sx = dinv + a.np;
-  double* sb = sx + 3 * a.np;
-  double* A = a.smem_mat ? sb + a.np : a.gscr + (int64_t)blockIdx.x * a.gstride;
-  float* X = reinterpret_cast<float*>(A);  // L^{-1} in FP32 overwrites the FP64 factor at the end
-  for (int i = tid; i < kExpTab; i += nthr) tab[i] = kExp2FracTab[i];
-  const double lam = p.lambda;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int np = a.np;
+  double* s = sm;
+  double* cb = s + 3 * np;
+  double* dinv = cb + 2 * (np + 1);
+  float* xf = reinterpret_cast<float*>(dinv + np);
+  int* qw = reinterpret_cast<int*>(xf + 4 * np) + 64 * warp;
+  float* dinvf = reinterpret_cast<float*>(reinterpret_cast<int*>(xf + 4 * np) + 64 * W);
+  double* A = GMAT ? a.gscr + (int64_t)blockIdx.x * a.gstride
+                   : reinterpret_cast<double*>(sm + fit_smem_doubles(np, W, false));
+  float* X = reinterpret_cast<float*>(A);
+  const unsigned lt_mask = (1u << lane) - 1u;
   for (;;) {
     if (tid == 0) {
-      int w = atomicAdd(a.counter, 1);
+      const int w = atomicAdd(a.counter, 1);
       s_cell = w < a.count ? (int)a.order[a.first + w] : -1;
       s_fail = 0;
     }
-    __syncthreads();
+    fit_sync(TEAM);
     const int g = s_cell;
     if (g < 0) break;
     const int N = a.n32[g];
     if (N == 0) {
-      __syncthreads();
+      fit_sync(TEAM);
       continue;
     }
     const int64_t m0 = a.ts_off[g];
     const int64_t T = tri_sz(N);
-    for (int i = tid; i < N; i += nthr) {
+    for (int i = tid; i < N; i += TEAM) {
       const D4 v = a.md4[m0 + i];
-      sx[3 * i] = v.x;
-      sx[3 * i + 1] = v.y;
-      sx[3 * i + 2] = v.z;
+      s[3 * i] = a.sc * v.x;
+      s[3 * i + 1] = a.sc * v.y;
+      s[3 * i + 2] = a.sc * v.z;
+      const float4 f = a.mf4[m0 + i];
+      xf[4 * i] = f.x;
+      xf[4 * i + 1] = f.y;
+      xf[4 * i + 2] = f.z;
+      A[tri_sz(i) + i] = 1.0 + f2d_bits(a.mvar[m0 + i]);  // exp(0) + sigma_i^2
+      A[T + i] = 1.0;                                       // augmented row: the right-hand side
     }
-    __syncthreads();
-    // A = K + diag(sigma^2): two independent entries per thread and iteration
-    for (int64_t t0 = tid; t0 < T; t0 += 2 * nthr) {
-      const int64_t t1 = t0 + nthr;
-      const int i0 = tri_row(t0), j0 = (int)(t0 - tri_sz(i0));
-      const int i1 = t1 < T ? tri_row(t1) : i0, j1 = t1 < T ? (int)(t1 - tri_sz(i1)) : j0;
-      double v0 = kernel_entry(sx, i0, j0, lam, tab);
-      double v1 = kernel_entry(sx, i1, j1, lam, tab);
-      if (i0 == j0) v0 += (double)a.mvar[m0 + i0];
-      if (i1 == j1) v1 += (double)a.mvar[m0 + i1];
-      A[t0] = v0;
-      if (t1 < T) A[t1] = v1;
-    }
-    __syncthreads();
-    for (int kb = 0; kb < N; kb += kPanel) {
-      const int ke = min(kb + kPanel, N);
-      if (warp == 0) {
-        for (int k = kb; k < ke; ++k) {
-          int bad = 0;
-          double r = 0.0;
-          if (lane == 0) {
-            const double piv = A[P(k, k)];
-            if (!(piv > 0.0)) {
-              bad = 1;
-            } else {
-              r = rsqrt(piv);
-              A[P(k, k)] = piv * r;
-              dinv[k] = r;
-            }
+    if (tid == 0) A[T + N] = 0.0;  // never used; kept finite
+    fit_sync(TEAM);
+    // 1. off-diagonal kernel entries: rows round-robin over the warps, lanes along the row
+    {
+      int qn = 0;
+      for (int i = 1 + warp; i < N; i += W) {
+        const float xi = xf[4 * i], yi = xf[4 * i + 1], zi = xf[4 * i + 2];
+        double* Ai = A + tri_sz(i);
+        for (int j0 = 0; j0 < i; j0 += 32) {
+          const int j = j0 + lane;
+          bool near = false;
+          if (j < i) {
+            const float dx = xi - xf[4 * j], dy = yi - xf[4 * j + 1], dz = zi - xf[4 * j + 2];
+            const float ef = a.lamf * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (ef < kNearE) near = true;
+            else Ai[j] = f2d_bits(exp2f(-1.44269504f * ef));
           }
-          bad = __shfl_sync(0xffffffffu, bad, 0);
-          r = __shfl_sync(0xffffffffu, r, 0);
-          if (bad) {
+          const unsigned mask = __ballot_sync(0xffffffffu, near);
+          if (near) qw[qn + __popc(mask & lt_mask)] = (i << 16) | j;
+          qn += __popc(mask);
+          if (qn >= 32) {
+            __syncwarp();
+            {
+              const int ij = qw[lane], ii = ij >> 16, jj = ij & 0xffff;
+              const double ex = s[3 * ii] - s[3 * jj], ey = s[3 * ii + 1] - s[3 * jj + 1],
+                           ez = s[3 * ii + 2] - s[3 * jj + 2];
+              A[tri_sz(ii) + jj] = exp2_neg_q16(fma(ez, ez, fma(ey, ey, ex * ex)));
+            }
+            __syncwarp();
+            if (lane < qn - 32) qw[lane] = qw[32 + lane];
+            qn -= 32;
+            __syncwarp();
+          }
+        }
+      }
+      __syncwarp();
+      if (lane < qn) {
+        const int ij = qw[lane], ii = ij >> 16, jj = ij & 0xffff;
+        const double ex = s[3 * ii] - s[3 * jj], ey = s[3 * ii + 1] - s[3 * jj + 1], ez = s[3 * ii + 2] - s[3 * jj + 2];
+        A[tri_sz(ii) + jj] = exp2_neg_q16(fma(ez, ez, fma(ey, ey, ex * ex)));
+      }
+    }
+    fit_sync(TEAM);
+    // 2. Cholesky of the augmented matrix in panels of kB columns: warp 0 factors the panel (pivots,
+    //    column scaling, updates inside the panel), then the team updates the trailing triangle (rows and
+    //    columns ke..N, the augmented row included) in 2 x 2 register blocks over the panel depth.  The
+    //    diagonal keeps the pivot d_k until the end (L_kk = d_k / sqrt(d_k) is applied in bulk).
+    for (int kb = 0; kb < N; kb += kB) {
+      const int ke = min(kb + kB, N);
+      if (warp == 0) {
+        for (int c = kb; c < ke; ++c) {
+          const double d = A[tri_sz(c) + c];
+          if (!pivot_ok(d)) {
             if (lane == 0) s_fail = 1;
             break;
           }
-          for (int i = k + 1 + lane; i < N; i += 32) A[P(i, k)] *= r;
+          const double y = rsqrt_pivot(d);
+          if (lane == 0) dinv[c] = y;
+          for (int i = c + 1 + lane; i <= N; i += 32) A[tri_sz(i) + c] *= y;
           __syncwarp();
-          for (int i = k + 1 + lane; i < N; i += 32) {
-            const double lik = A[P(i, k)];
-            const int cmax = min(i, ke - 1);
-            for (int c = k + 1; c <= cmax; ++c) A[P(i, c)] = fma(-lik, A[P(c, k)], A[P(i, c)]);
+          const int nc = ke - 1 - c;
+          if (nc > 0) {
+            for (int i = c + 1 + lane; i <= N; i += 32) {
+              double* Ai = A + tri_sz(i);
+              const double lic = Ai[c];
+              const int ue = min(nc, i - c);
+              for (int u = 0; u < ue; ++u) {
+                const int j = c + 1 + u;
+                Ai[j] = fma(-lic, A[tri_sz(j) + c], Ai[j]);
+              }
+            }
+            __syncwarp();
           }
-          __syncwarp();
         }
       }
-      __syncthreads();
+      fit_sync(TEAM);
       if (s_fail) break;
-      // trailing update A[i][j] -= sum_{k in panel} L[i][k] L[j][k] for ke <= j <= i, in 2x2 blocks
-      const int w = ke - kb, nbk = (N - ke + 1) >> 1;
+      const int w = ke - kb;
+      const int nbk = (N + 2 - ke) >> 1;  // 2-row blocks over rows ke..N
       const int64_t nblk = tri_sz(nbk);
-      for (int64_t t = tid; t < nblk; t += nthr) {
+      for (int64_t t = tid; t < nblk; t += TEAM) {
         const int I = tri_row(t), J = (int)(t - tri_sz(I));
         const int i0 = ke + 2 * I, j0 = ke + 2 * J, i1 = i0 + 1, j1 = j0 + 1;
-        const bool vi1 = i1 < N, v01 = j1 <= i0, vj1 = j1 < N;
-        const double* Li0 = A + P(i0, kb);
-        const double* Li1 = vi1 ? A + P(i1, kb) : Li0;
-        const double* Lj0 = A + P(j0, kb);
-        const double* Lj1 = vj1 ? A + P(j1, kb) : Lj0;
-        double a00 = A[P(i0, j0)];
-        double a01 = v01 ? A[P(i0, j1)] : 0.0;
-        double a10 = vi1 ? A[P(i1, j0)] : 0.0;
-        double a11 = vi1 ? A[P(i1, j1)] : 0.0;
-        for (int k = 0; k < w; ++k) {
-          const double li0 = Li0[k], li1 = Li1[k], lj0 = Lj0[k], lj1 = Lj1[k];
-          a00 = fma(-li0, lj0, a00);
-          a01 = fma(-li0, lj1, a01);
-          a10 = fma(-li1, lj0, a10);
-          a11 = fma(-li1, lj1, a11);
+        const bool vi1 = i1 <= N, v01 = j1 <= i0, vj1 = j1 <= N;
+        double* Ai0 = A + tri_sz(i0);
+        double* Ai1 = vi1 ? A + tri_sz(i1) : Ai0;
+        const double* Lj0 = A + tri_sz(j0) + kb;
+        const double* Lj1 = vj1 ? A + tri_sz(j1) + kb : Lj0;
+        const double* Li0 = Ai0 + kb;
+        const double* Li1 = Ai1 + kb;
+        double a00 = Ai0[j0];
+        double a01 = v01 ? Ai0[j1] : 0.0;
+        double a10 = vi1 ? Ai1[j0] : 0.0;
+        double a11 = vi1 ? Ai1[j1] : 0.0;
+#pragma unroll
+        for (int k = 0; k < kB; ++k) {
+          if (k < w) {
+            const double li0 = Li0[k], li1 = Li1[k], lj0 = Lj0[k], lj1 = Lj1[k];
+            a00 = fma(-li0, lj0, a00);
+            a01 = fma(-li0, lj1, a01);
+            a10 = fma(-li1, lj0, a10);
+            a11 = fma(-li1, lj1, a11);
+          }
         }
-        A[P(i0, j0)] = a00;
-        if (v01) A[P(i0, j1)] = a01;
+        Ai0[j0] = a00;
+        if (v01) Ai0[j1] = a01;
         if (vi1) {
-          A[P(i1, j0)] = a10;
-          A[P(i1, j1)] = a11;
+          Ai1[j0] = a10;
+          Ai1[j1] = a11;
         }
       }
-      __syncthreads();
+      fit_sync(TEAM);
     }
     if (s_fail) {
       if (tid == 0) {
         a.status[g] = KSDF_CELL_NOT_PD;
         atomicAdd(a.n_not_pd, 1);
       }
-      for (int i = tid; i < N; i += nthr) {
+      for (int i = tid; i < N; i += TEAM) {
         a.md4[m0 + i].w = 0.0;
         a.mf4[m0 + i].w = 0.f;
       }
-      __syncthreads();
+      fit_sync(TEAM);
       continue;
     }
+    for (int k = tid; k < N; k += TEAM) A[tri_sz(k) + k] *= dinv[k];  // L_kk = d_k / sqrt(d_k)
+    fit_sync(TEAM);
+    // 3. alpha = L^{-T} y (warp 0); the other warps write L out meanwhile
+    double* yb = cb;
+    double* Lout = a.chol64 + a.chol_off[g];
     if (warp == 0) {
-      // alpha: L y = 1, then L^T alpha = y (FP64, reciprocal pivots)
-      for (int i = lane; i < N; i += 32) sb[i] = 1.0;
+      for (int i = lane; i < N; i += 32) yb[i] = A[T + i];
       __syncwarp();
-      for (int k = 0; k < N; ++k) {
-        const double bk = sb[k] * dinv[k];
-        for (int i = k + 1 + lane; i < N; i += 32) sb[i] = fma(-A[P(i, k)], bk, sb[i]);
-        __syncwarp();
-        if (lane == 0) sb[k] = bk;
-        __syncwarp();
-      }
       for (int k = N - 1; k >= 0; --k) {
-        const double bk = sb[k] * dinv[k];
-        for (int i = lane; i < k; i += 32) sb[i] = fma(-A[P(k, i)], bk, sb[i]);
+        const double ak = yb[k] * dinv[k];
+        const double* Lk = A + tri_sz(k);
+        for (int i = lane; i < k; i += 32) yb[i] = fma(-Lk[i], ak, yb[i]);
         __syncwarp();
-        if (lane == 0) sb[k] = bk;
-        __syncwarp();
+        if (lane == 0) yb[k] = ak;
       }
     } else {
-      double* Lout = a.chol64 + a.chol_off[g];
-      for (int64_t e = tid - 32; e < T; e += nthr - 32) Lout[e] = A[e];
+      for (int64_t e = tid - 32; e < T; e += TEAM - 32) Lout[e] = A[e];
     }
-    __syncthreads();
-    for (int i = tid; i < N; i += nthr) {
-      a.md4[m0 + i].w = sb[i];
-      a.mf4[m0 + i].w = (float)sb[i];
+    fit_sync(TEAM);
+    if (W == 1)
+      for (int64_t e = tid; e < T; e += TEAM) Lout[e] = A[e];
+    for (int i = tid; i < N; i += TEAM) {
+      a.md4[m0 + i].w = yb[i];
+      a.mf4[m0 + i].w = d2f_bits(yb[i]);
+      dinvf[i] = d2f_bits(dinv[i]);
     }
-    // FP64 -> FP32 in place, in chunks: the writes of a chunk only touch FP64 entries already read
-    for (int64_t c0 = 0; c0 < T; c0 += 8 * (int64_t)nthr) {
+    // 4. FP64 -> FP32 in place, in chunks: the writes of a chunk only touch FP64 entries already read
+    for (int64_t c0 = 0; c0 < T; c0 += 8 * (int64_t)TEAM) {
       float v[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const int64_t e = c0 + tid + (int64_t)r * nthr;
-        v[r] = e < T ? (float)A[e] : 0.f;
+        const int64_t e = c0 + tid + (int64_t)r * TEAM;
+        v[r] = e < T ? d2f_bits(A[e]) : 0.f;
       }
-      __syncthreads();
+      fit_sync(TEAM);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const int64_t e = c0 + tid + (int64_t)r * nthr;
+        const int64_t e = c0 + tid + (int64_t)r * TEAM;
         if (e < T) X[e] = v[r];
       }
-      __syncthreads();
+      fit_sync(TEAM);
     }
     // X = L^{-1}: column j (from the last) becomes X[j][j] = 1/L_jj,
     // X[i][j] = -X[j][j] sum_{k=j+1..i} X[i][k] L[k][j] (i > j), reading finished columns k > j of X and
     // the untouched column j of L
     for (int j = N - 1; j >= 0; --j) {
-      float tv[kInvRows];
+      float tv[ROWS];
 #pragma unroll
-      for (int r = 0; r < kInvRows; ++r) {
-        const int i = j + 1 + tid + r * nthr;
-        float acc = 0.f;
+      for (int r = 0; r < ROWS; ++r) {
+        const int i = j + 1 + tid + r * TEAM;
+        float acc0 = 0.f, acc1 = 0.f;
         if (i < N) {
-          const float* Xi = X + P(i, 0);
-          for (int k = j + 1; k <= i; ++k) acc = fmaf(Xi[k], X[P(k, j)], acc);
+          const float* Xi = X + tri_sz(i);
+          int k = j + 1;
+          for (; k + 1 <= i; k += 2) {
+            acc0 = fmaf(Xi[k], X[tri_sz(k) + j], acc0);
+            acc1 = fmaf(Xi[k + 1], X[tri_sz(k + 1) + j], acc1);
+          }
+          if (k <= i) acc0 = fmaf(Xi[k], X[tri_sz(k) + j], acc0);
         }
-        tv[r] = acc;
+        tv[r] = acc0 + acc1;
       }
-      __syncthreads();
-      const float xjj = (float)dinv[j];
+      fit_sync(TEAM);
+      const float xjj = dinvf[j];
 #pragma unroll
-      for (int r = 0; r < kInvRows; ++r) {
-        const int i = j + 1 + tid + r * nthr;
-        if (i < N) X[P(i, j)] = -xjj * tv[r];
+      for (int r = 0; r < ROWS; ++r) {
+        const int i = j + 1 + tid + r * TEAM;
+        if (i < N) X[tri_sz(i) + j] = -xjj * tv[r];
       }
-      if (tid == 0) X[P(j, j)] = xjj;
-      __syncthreads();
+      if (tid == 0) X[tri_sz(j) + j] = xjj;
+      fit_sync(TEAM);
     }
     float* Iout = a.linv32 + a.linv_off[g];
     const int64_t lsz = linv_blocked_size(N);
-    for (int64_t e = tid; e < lsz; e += nthr) {
+    for (int64_t e = tid; e < lsz; e += TEAM) {
       int R = (int)((sqrtf(1.f + (float)e / 8.f) - 1.f) * 0.5f);
       while (linv_block_off(R + 1) <= e) ++R;
       while (linv_block_off(R) > e) --R;
       const int64_t q = e - linv_block_off(R);
       const int col = (int)(q >> 3), i = 8 * R + (int)(q & 7);
-      Iout[e] = (i < N && col <= i) ? X[P(i, col)] : 0.f;
+      Iout[e] = (i < N && col <= i) ? X[tri_sz(i) + col] : 0.f;
     }
-    __syncthreads();
+    fit_sync(TEAM);
   }
 }
 
@@ -497,10 +563,19 @@ static int bits_for(uint64_t v) {
   return b;
 }
 
-static size_t fit_smem(int np, bool smem_mat) {
-  size_t d = kExpTab + 5 * (size_t)np;  // exp table, reciprocal pivots, coordinates, right-hand side
-  if (smem_mat) d += (size_t)tri_sz(np);
-  return d * sizeof(double);
+// persistent launch of one size class: as many teams as fit on the GPU (at most one per cell)
+template <int TEAM, int ROWS, bool GMAT>
+static cudaError_t launch_fit(ksdf_ctx* c, const FitArgs& f, const Params& p, size_t smem, cudaStream_t s) {
+  if (f.np > TEAM * ROWS) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_fit<TEAM, ROWS, GMAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fit<TEAM, ROWS, GMAT>, TEAM, smem);
+  if (e != cudaSuccess) return e;
+  int64_t nblk = std::min<int64_t>(f.count, (int64_t)std::max(1, occ) * c->num_sms);
+  if (GMAT) nblk = std::min<int64_t>(nblk, c->num_sms);  // one global slot per CTA
+  launch(k_fit<TEAM, ROWS, GMAT>, (unsigned)nblk, TEAM, smem, s, f, p);
+  return cudaSuccess;
 }
 
 ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const float* nrm, int64_t S) {
@@ -619,23 +694,28 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   uint32_t* order = ptr<uint32_t>(m.cell_order);
   launch(k_order_keys, ceil_div(G, 256), 256, 0, st, ptr<int32_t>(m.n), G, p.n_max, okeys, order);
   KSDF_CUDA(c, radix_sort_u64(okeys, order, G, bits_for((uint64_t)p.n_max), c->ws[WS_SORT], st));
-  // size classes (host histogram): N <= 96 (128 threads), <= 160, <= 218 (256 threads, matrix in shared
-  // memory), larger (256 threads, matrix in a per-CTA global slot); launched concurrently, largest first
+  // size classes (host histogram), launched concurrently, largest first; each class has its team size
+  // and the number of rows per thread of the FP32 inversion (np <= team * rows)
   std::vector<int32_t> hn((size_t)G);
   KSDF_CUDA(c, cudaMemcpyAsync(hn.data(), m.n.p, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, st));
   KSDF_CUDA(c, cudaStreamSynchronize(st));
-  const int lim[4] = {kClassXL, kClassL, kClassM, kClassS};  // upper bounds, descending
-  int64_t cnt[4] = {0, 0, 0, 0};
+  constexpr int kNumClass = 7;
+  struct FitClass {
+    int np, team;
+    bool gmat;
+  };
+  const FitClass cls[kNumClass] = {{kMaxNmax, 256, true}, {218, 256, false}, {156, 128, false}, {128, 128, false},
+                                   {96, 64, false},       {80, 32, false},   {64, 32, false}};
+  int64_t cnt[kNumClass] = {};
   for (int32_t v : hn) {
-    if (v > kClassL) ++cnt[0];
-    else if (v > kClassM) ++cnt[1];
-    else if (v > kClassS) ++cnt[2];
-    else ++cnt[3];
+    int cl = kNumClass - 1;
+    while (cl > 0 && v > cls[cl].np) --cl;
+    ++cnt[cl];
   }
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
-  KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 8));
+  KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 16));
   int* ctr = reinterpret_cast<int*>(ptr<int64_t>(c->ws[WS_E]) + 4);
-  KSDF_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int) * 4, st));
+  KSDF_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int) * kNumClass, st));
   FitArgs fa;
   fa.order = order;
   fa.n32 = ptr<int32_t>(m.n);
@@ -651,32 +731,42 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   fa.n_not_pd = dmax + 1;
   fa.gscr = nullptr;
   fa.gstride = 0;
-  KSDF_CUDA(c, cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem(kClassL, true)));
+  fa.sc = std::sqrt(p.lambda * kExpQ16PerNat);
+  fa.lamf = (float)p.lambda;
   e0 = prof_begin(c);
   KSDF_CUDA(c, fork_streams(c));
   int64_t first = 0;
-  for (int cl = 0; cl < 4; ++cl) {
+  int launched = 0;
+  for (int cl = 0; cl < kNumClass; ++cl) {
     if (cnt[cl] == 0) continue;
     FitArgs f = fa;
     f.first = first;
     f.count = cnt[cl];
     f.counter = ctr + cl;
     first += cnt[cl];
-    const int threads = cl == 3 ? 128 : 256;
-    f.smem_mat = cl > 0 ? 1 : 0;
-    f.np = cl > 0 ? lim[cl] : std::max(m.max_n, 1);
-    if (cl == 0) {
-      const int nblk = (int)std::min<int64_t>(cnt[cl], c->num_sms);
-      f.gstride = tri_sz(f.np);
-      KSDF_CUDA(c, ensure(c->ws[WS_FITSCR], sizeof(double) * (size_t)(f.gstride * nblk + 1)));
-      f.gscr = ptr<double>(c->ws[WS_FITSCR]);
+    const int team = cls[cl].team;
+    f.np = cls[cl].gmat ? std::max(m.max_n, 1) : cls[cl].np;
+    const size_t smem = sizeof(double) * (size_t)fit_smem_doubles(f.np, team / 32, !cls[cl].gmat);
+    cudaStream_t s = (launched % (ksdf_ctx::kNumAux + 1)) == ksdf_ctx::kNumAux
+                         ? st
+                         : c->aux[launched % (ksdf_ctx::kNumAux + 1)];
+    ++launched;
+    switch (cl) {
+      case 0: {
+        const int nblk = (int)std::min<int64_t>(cnt[cl], c->num_sms);
+        f.gstride = tri_sz(f.np + 1);
+        KSDF_CUDA(c, ensure(c->ws[WS_FITSCR], sizeof(double) * (size_t)(f.gstride * nblk + 1)));
+        f.gscr = ptr<double>(c->ws[WS_FITSCR]);
+        KSDF_CUDA(c, (launch_fit<256, 2, true>(c, f, p, smem, s)));
+        break;
+      }
+      case 1: KSDF_CUDA(c, (launch_fit<256, 1, false>(c, f, p, smem, s))); break;
+      case 2: KSDF_CUDA(c, (launch_fit<128, 2, false>(c, f, p, smem, s))); break;
+      case 3: KSDF_CUDA(c, (launch_fit<128, 1, false>(c, f, p, smem, s))); break;
+      case 4: KSDF_CUDA(c, (launch_fit<64, 2, false>(c, f, p, smem, s))); break;
+      case 5: KSDF_CUDA(c, (launch_fit<32, 3, false>(c, f, p, smem, s))); break;
+      default: KSDF_CUDA(c, (launch_fit<32, 2, false>(c, f, p, smem, s))); break;
     }
-    const size_t smem = fit_smem(f.np, f.smem_mat != 0);
-    int occ = 0;
-    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fit, threads, smem));
-    const int nblk = (int)std::min<int64_t>(cnt[cl], (int64_t)std::max(1, occ) * c->num_sms);
-    cudaStream_t s = cl == 3 ? st : c->aux[cl & 1];
-    launch(k_fit, nblk, threads, smem, s, f, p);
   }
   KSDF_CUDA(c, cudaGetLastError());
   KSDF_CUDA(c, join_streams(c));

@@ -165,8 +165,9 @@ struct ksdf_ctx {
   std::vector<double> stage_ms;
   std::vector<long long> stage_calls;
   // auxiliary streams for concurrent launches inside one call (fork/join through events)
-  cudaStream_t aux[2] = {nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  static constexpr int kNumAux = 4;
+  cudaStream_t aux[kNumAux] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kNumAux] = {};
 };
 
 namespace ksdf {
@@ -188,7 +189,7 @@ template <class T> inline T* ptr(DevBuf& b) { return static_cast<T*>(b.p); }
 cudaEvent_t prof_begin(ksdf_ctx* c);
 void prof_end(ksdf_ctx* c, cudaEvent_t a, const char* name);
 
-// ---- fork/join of the context stream with two auxiliary streams (ksdf_abi.cu) ----
+// ---- fork/join of the context stream with the auxiliary streams (ksdf_abi.cu) ----
 cudaError_t fork_streams(ksdf_ctx* c);
 cudaError_t join_streams(ksdf_ctx* c);
 
