@@ -313,7 +313,7 @@ def main():
     peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
     pairs, nsz = phase_a_pairs(w, model.h)
     per = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
-    kernels = {k: per[k] for k in ("fit.cholesky", "fit.index", "fit.assemble", "query.group", "query.candidates",
+    kernels = {k: per[k] for k in ("fit.cholesky", "fit.linv", "fit.index", "fit.assemble", "query.group", "query.candidates",
                                    "query.phaseA", "query.regroup", "query.phaseB", "backward.group",
                                    "backward.query", "backward.cell") if k in per}
     dom = max(kernels, key=kernels.get)

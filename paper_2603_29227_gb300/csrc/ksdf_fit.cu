@@ -280,9 +280,9 @@ __device__ __forceinline__ void fit_sync(int team) {
 
 // Shared-memory layout of one cell's fit (doubles): scaled coordinates 3 np | two column buffers
 // 2 (np + 1) | reciprocal pivots np | FP32 coordinates 4 np floats | near-entry queues 64 ints per warp |
-// FP32 reciprocal pivots np floats | the augmented packed matrix tri(np + 1) (when it lives here).
+// the augmented packed matrix tri(np + 1) (when it lives here).
 __host__ __device__ inline int64_t fit_smem_doubles(int np, int warps, bool smem_mat) {
-  return 3 * (int64_t)np + 2 * ((int64_t)np + 1) + np + 2 * (int64_t)np + 32 * (int64_t)warps + (np + 1) / 2 +
+  return 3 * (int64_t)np + 2 * ((int64_t)np + 1) + np + 2 * (int64_t)np + 32 * (int64_t)warps +
          (smem_mat ? tri_sz(np + 1) : 0);
 }
 
@@ -298,8 +298,8 @@ __host__ __device__ inline int64_t fit_smem_doubles(int np, int warps, bool smem
 //      team updates the trailing triangle in 2 x 2 register blocks over the panel depth (about three
 //      instructions per DFMA).  The augmented row ends as y = L^{-1} 1.
 //   3. alpha = L^{-T} y by backward substitution (warp 0) while the other warps write L out.
-//   4. L rounded to FP32 in place and inverted column by column; L^{-1} written in 8-row blocks.
-template <int TEAM, int ROWS, bool GMAT>
+// L^{-1} in FP32 follows in k_linv.
+template <int TEAM, bool GMAT>
 __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitArgs a, Params p) {
   constexpr int W = TEAM / 32;
   extern __shared__ __align__(16) double sm[];
@@ -311,10 +311,8 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
   double* dinv = cb + 2 * (np + 1);
   float* xf = reinterpret_cast<float*>(dinv + np);
   int* qw = reinterpret_cast<int*>(xf + 4 * np) + 64 * warp;
-  float* dinvf = reinterpret_cast<float*>(reinterpret_cast<int*>(xf + 4 * np) + 64 * W);
   double* A = GMAT ? a.gscr + (int64_t)blockIdx.x * a.gstride
                    : reinterpret_cast<double*>(sm + fit_smem_doubles(np, W, false));
-  float* X = reinterpret_cast<float*>(A);
   const unsigned lt_mask = (1u << lane) - 1u;
   for (;;) {
     if (tid == 0) {
@@ -493,63 +491,149 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
     for (int i = tid; i < N; i += TEAM) {
       a.md4[m0 + i].w = yb[i];
       a.mf4[m0 + i].w = d2f_bits(yb[i]);
-      dinvf[i] = d2f_bits(dinv[i]);
     }
-    // 4. FP64 -> FP32 in place, in chunks: the writes of a chunk only touch FP64 entries already read
-    for (int64_t c0 = 0; c0 < T; c0 += 8 * (int64_t)TEAM) {
-      float v[8];
+    fit_sync(TEAM);
+  }
+}
+
+// L^{-1} in FP32 for the variance contraction, one team per cell (persistent over cells order[first ..
+// first + count)).  L is rounded to FP32 (integer-bit conversion) into shared memory and each column of X =
+// L^{-1} is the forward substitution L x = e_j: X[j][j] = 1/L_jj and X[i][j] = -(sum_{k=j..i-1} L_ik X_kj) /
+// L_ii for i > j.  A lane owns a column and a warp a group of 32 consecutive columns, walking the rows
+// four at a time so that every X_kj load feeds four FFMAs; no synchronisation beyond the warp.
+//   INPLACE (one warp, small cells): the groups run in order and X overwrites L (a group only reads L in
+//     its own and later columns, and a row's L entries until that row is finished);
+//   otherwise one warp per group, all groups concurrently, each with its own buffer of (np - 32 g) rows.
+// The group's columns are then written in the 8-row blocked layout.  A separate kernel so that the fit's
+// warps keep the FP64 pipe busy; this one is FP32 only.
+struct LinvArgs {
+  const uint32_t* order;
+  int64_t first, count;
+  const int32_t* n32;
+  const int32_t* status;
+  const int64_t* chol_off;
+  const int64_t* linv_off;
+  const double* chol64;
+  float* linv32;
+  float* gscr;      // per-CTA global slot (largest class): linv_slot_floats(np, false)
+  int64_t gstride;
+  int np;
+  int* counter;
+};
+
+// float offset of group g's buffer (after the reciprocal diagonal and L) and the slot size
+__host__ __device__ inline int64_t linv_group_off(int np, int g) {
+  return (((int64_t)np + 3) & ~3LL) + tri_sz(np) + 32LL * ((int64_t)g * np - 32LL * tri_sz(g - 1));
+}
+__host__ __device__ inline int64_t linv_slot_floats(int np, bool inplace) {
+  return inplace ? (((int64_t)np + 3) & ~3LL) + tri_sz(np) : linv_group_off(np, (np + 31) / 32);
+}
+
+template <int TEAM, bool INPLACE, bool GMAT>
+__global__ void __launch_bounds__(TEAM) k_linv(LinvArgs a) {
+  extern __shared__ __align__(16) float smf[];
+  __shared__ int s_cell;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int np = a.np;
+  float* ws = GMAT ? a.gscr + (int64_t)blockIdx.x * a.gstride : smf;
+  float* dg = ws;
+  float* L = ws + ((np + 3) & ~3);
+  for (;;) {
+    if (tid == 0) {
+      const int w = atomicAdd(a.counter, 1);
+      s_cell = w < a.count ? (int)a.order[a.first + w] : -1;
+    }
+    fit_sync(TEAM);
+    const int g = s_cell;
+    if (g < 0) break;
+    const int N = a.n32[g];
+    if (N == 0 || a.status[g] != KSDF_CELL_OK) {
+      fit_sync(TEAM);
+      continue;
+    }
+    const int64_t T = tri_sz(N);
+    const double* Ld = a.chol64 + a.chol_off[g];
+    for (int64_t e0 = tid; e0 < T; e0 += 8 * (int64_t)TEAM) {  // eight loads in flight per thread
+      double v[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const int64_t e = c0 + tid + (int64_t)r * TEAM;
-        v[r] = e < T ? d2f_bits(A[e]) : 0.f;
+        const int64_t e = e0 + (int64_t)r * TEAM;
+        v[r] = e < T ? Ld[e] : 0.0;
       }
-      fit_sync(TEAM);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const int64_t e = c0 + tid + (int64_t)r * TEAM;
-        if (e < T) X[e] = v[r];
+        const int64_t e = e0 + (int64_t)r * TEAM;
+        if (e < T) L[e] = d2f_bits(v[r]);
       }
-      fit_sync(TEAM);
     }
-    // X = L^{-1}: column j (from the last) becomes X[j][j] = 1/L_jj,
-    // X[i][j] = -X[j][j] sum_{k=j+1..i} X[i][k] L[k][j] (i > j), reading finished columns k > j of X and
-    // the untouched column j of L
-    for (int j = N - 1; j >= 0; --j) {
-      float tv[ROWS];
-#pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        const int i = j + 1 + tid + r * TEAM;
-        float acc0 = 0.f, acc1 = 0.f;
-        if (i < N) {
-          const float* Xi = X + tri_sz(i);
-          int k = j + 1;
-          for (; k + 1 <= i; k += 2) {
-            acc0 = fmaf(Xi[k], X[tri_sz(k) + j], acc0);
-            acc1 = fmaf(Xi[k + 1], X[tri_sz(k + 1) + j], acc1);
-          }
-          if (k <= i) acc0 = fmaf(Xi[k], X[tri_sz(k) + j], acc0);
-        }
-        tv[r] = acc0 + acc1;
-      }
-      fit_sync(TEAM);
-      const float xjj = dinvf[j];
-#pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        const int i = j + 1 + tid + r * TEAM;
-        if (i < N) X[tri_sz(i) + j] = -xjj * tv[r];
-      }
-      if (tid == 0) X[tri_sz(j) + j] = xjj;
-      fit_sync(TEAM);
-    }
+    fit_sync(TEAM);
+    for (int j = tid; j < N; j += TEAM) dg[j] = 1.f / L[tri_sz(j) + j];
+    fit_sync(TEAM);
     float* Iout = a.linv32 + a.linv_off[g];
-    const int64_t lsz = linv_blocked_size(N);
-    for (int64_t e = tid; e < lsz; e += TEAM) {
-      int R = (int)((sqrtf(1.f + (float)e / 8.f) - 1.f) * 0.5f);
-      while (linv_block_off(R + 1) <= e) ++R;
-      while (linv_block_off(R) > e) --R;
-      const int64_t q = e - linv_block_off(R);
-      const int col = (int)(q >> 3), i = 8 * R + (int)(q & 7);
-      Iout[e] = (i < N && col <= i) ? X[tri_sz(i) + col] : 0.f;
+    const int nR = (N + 7) >> 3;
+    for (int gi = INPLACE ? 0 : warp; 32 * gi < N; gi += INPLACE ? 1 : TEAM / 32) {
+      const int base = 32 * gi, j = base + lane;
+      // X[k][j] lives at xs[k * ldx] (in place: L's packed row k; else the group's buffer)
+      float* xcol = INPLACE ? L + j : ws + linv_group_off(np, gi) - (int64_t)base * 32 + lane;
+      for (int i0 = base; i0 < N; i0 += 4) {
+        const float* L0 = L + tri_sz(i0);
+        const float* L1 = L + tri_sz(min(i0 + 1, N - 1));
+        const float* L2 = L + tri_sz(min(i0 + 2, N - 1));
+        const float* L3 = L + tri_sz(min(i0 + 3, N - 1));
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll 4
+        for (int k = base; k < i0; ++k) {
+          float x;
+          if (INPLACE) x = k >= j ? xcol[tri_sz(k)] : 0.f;  // X[k][j], zero above the diagonal
+          else x = xcol[(int64_t)k * 32];
+          c0 = fmaf(L0[k], x, c0);
+          c1 = fmaf(L1[k], x, c1);
+          c2 = fmaf(L2[k], x, c2);
+          c3 = fmaf(L3[k], x, c3);
+        }
+        float xv[4];
+        xv[0] = i0 > j ? -c0 * dg[i0] : (i0 == j ? dg[j] : 0.f);
+        if (i0 + 1 < N) {
+          c1 = fmaf(L1[i0], xv[0], c1);
+          xv[1] = i0 + 1 > j ? -c1 * dg[i0 + 1] : (i0 + 1 == j ? dg[j] : 0.f);
+          if (i0 + 2 < N) {
+            c2 = fmaf(L2[i0 + 1], xv[1], fmaf(L2[i0], xv[0], c2));
+            xv[2] = i0 + 2 > j ? -c2 * dg[i0 + 2] : (i0 + 2 == j ? dg[j] : 0.f);
+            if (i0 + 3 < N) {
+              c3 = fmaf(L3[i0 + 2], xv[2], fmaf(L3[i0 + 1], xv[1], fmaf(L3[i0], xv[0], c3)));
+              xv[3] = i0 + 3 > j ? -c3 * dg[i0 + 3] : (i0 + 3 == j ? dg[j] : 0.f);
+            }
+          }
+        }
+        // rows i0.. are finished: store (in place: only on or below the diagonal and inside the matrix)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int i = i0 + r;
+          if (i < N) {
+            if (INPLACE) {
+              if (j <= i) xcol[tri_sz(i)] = xv[r];
+            } else {
+              xcol[(int64_t)i * 32] = xv[r];
+            }
+          }
+        }
+        if (INPLACE) __syncwarp();  // rows of L read by other lanes' columns are overwritten in place
+      }
+      // blocked output of the group's columns (columns N .. 8 nR - 1 of the last block are zero)
+      if (j < 8 * nR) {
+        for (int R = j >> 3; R < nR; ++R) {
+          float v[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int i = 8 * R + r;
+            v[r] = (j < N && i < N && i >= j) ? (INPLACE ? xcol[tri_sz(i)] : xcol[(int64_t)i * 32]) : 0.f;
+          }
+          float4* dst = reinterpret_cast<float4*>(Iout + linv_block_off(R) + (int64_t)j * 8);
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+      }
+      if (INPLACE) __syncwarp();
     }
     fit_sync(TEAM);
   }
@@ -563,18 +647,18 @@ static int bits_for(uint64_t v) {
   return b;
 }
 
-// persistent launch of one size class: as many teams as fit on the GPU (at most one per cell)
-template <int TEAM, int ROWS, bool GMAT>
-static cudaError_t launch_fit(ksdf_ctx* c, const FitArgs& f, const Params& p, size_t smem, cudaStream_t s) {
-  if (f.np > TEAM * ROWS) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_fit<TEAM, ROWS, GMAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// persistent launches of one size class: as many teams as fit on the GPU (at most one per cell)
+template <class K, class Args, class... Extra>
+static cudaError_t launch_persistent(ksdf_ctx* c, K kern, int team, const Args& f, size_t smem, bool gslot,
+                                     cudaStream_t s, const Extra&... extra) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fit<TEAM, ROWS, GMAT>, TEAM, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, team, smem);
   if (e != cudaSuccess) return e;
   int64_t nblk = std::min<int64_t>(f.count, (int64_t)std::max(1, occ) * c->num_sms);
-  if (GMAT) nblk = std::min<int64_t>(nblk, c->num_sms);  // one global slot per CTA
-  launch(k_fit<TEAM, ROWS, GMAT>, (unsigned)nblk, TEAM, smem, s, f, p);
+  if (gslot) nblk = std::min<int64_t>(nblk, c->num_sms);  // one global slot per CTA
+  launch(kern, (unsigned)nblk, team, smem, s, f, extra...);
   return cudaSuccess;
 }
 
@@ -713,7 +797,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     ++cnt[cl];
   }
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
-  KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 16));
+  KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 16));  // counters: fit and L^-1 classes
   int* ctr = reinterpret_cast<int*>(ptr<int64_t>(c->ws[WS_E]) + 4);
   KSDF_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int) * kNumClass, st));
   FitArgs fa;
@@ -751,26 +835,86 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
                          ? st
                          : c->aux[launched % (ksdf_ctx::kNumAux + 1)];
     ++launched;
-    switch (cl) {
-      case 0: {
-        const int nblk = (int)std::min<int64_t>(cnt[cl], c->num_sms);
-        f.gstride = tri_sz(f.np + 1);
-        KSDF_CUDA(c, ensure(c->ws[WS_FITSCR], sizeof(double) * (size_t)(f.gstride * nblk + 1)));
-        f.gscr = ptr<double>(c->ws[WS_FITSCR]);
-        KSDF_CUDA(c, (launch_fit<256, 2, true>(c, f, p, smem, s)));
-        break;
-      }
-      case 1: KSDF_CUDA(c, (launch_fit<256, 1, false>(c, f, p, smem, s))); break;
-      case 2: KSDF_CUDA(c, (launch_fit<128, 2, false>(c, f, p, smem, s))); break;
-      case 3: KSDF_CUDA(c, (launch_fit<128, 1, false>(c, f, p, smem, s))); break;
-      case 4: KSDF_CUDA(c, (launch_fit<64, 2, false>(c, f, p, smem, s))); break;
-      case 5: KSDF_CUDA(c, (launch_fit<32, 3, false>(c, f, p, smem, s))); break;
-      default: KSDF_CUDA(c, (launch_fit<32, 2, false>(c, f, p, smem, s))); break;
+    if (cls[cl].gmat) {
+      f.gstride = tri_sz(f.np + 1);
+      const int64_t slots = std::min<int64_t>(cnt[cl], c->num_sms);
+      KSDF_CUDA(c, ensure(c->ws[WS_FITSCR], sizeof(double) * (size_t)(f.gstride * slots + 1)));
+      f.gscr = ptr<double>(c->ws[WS_FITSCR]);
     }
+    cudaError_t le = cudaSuccess;
+    switch (team) {
+      case 256: le = cls[cl].gmat ? launch_persistent(c, k_fit<256, true>, 256, f, smem, true, s, p)
+                                  : launch_persistent(c, k_fit<256, false>, 256, f, smem, false, s, p); break;
+      case 128: le = launch_persistent(c, k_fit<128, false>, 128, f, smem, false, s, p); break;
+      case 64: le = launch_persistent(c, k_fit<64, false>, 64, f, smem, false, s, p); break;
+      default: le = launch_persistent(c, k_fit<32, false>, 32, f, smem, false, s, p); break;
+    }
+    KSDF_CUDA(c, le);
   }
   KSDF_CUDA(c, cudaGetLastError());
   KSDF_CUDA(c, join_streams(c));
   prof_end(c, e0, "fit.cholesky");
+  // L^{-1} in FP32, by size class (np <= team * rows of the kernel's inversion loop)
+  e0 = prof_begin(c);
+  {
+    // small cells: one warp, in place; larger: one warp per 32-column group (team = 32 ceil(np / 32))
+    constexpr int kNumLinv = 5;
+    const FitClass lcls[kNumLinv] = {{kMaxNmax, 512, true}, {218, 224, false}, {156, 160, false}, {96, 32, false},
+                                     {64, 32, false}};
+    int64_t lcnt[kNumLinv] = {};
+    for (int32_t v : hn) {
+      int cl = kNumLinv - 1;
+      while (cl > 0 && v > lcls[cl].np) --cl;
+      ++lcnt[cl];
+    }
+    KSDF_CUDA(c, cudaMemsetAsync(ctr + kNumClass, 0, sizeof(int) * kNumLinv, st));
+    KSDF_CUDA(c, fork_streams(c));
+    LinvArgs la;
+    la.order = order;
+    la.n32 = ptr<int32_t>(m.n);
+    la.status = ptr<int32_t>(m.status);
+    la.chol_off = ptr<int64_t>(m.chol_off);
+    la.linv_off = ptr<int64_t>(m.linv_off);
+    la.chol64 = ptr<double>(m.chol64);
+    la.linv32 = ptr<float>(m.linv32);
+    la.gscr = nullptr;
+    la.gstride = 0;
+    int64_t lfirst = 0;
+    int nl = 0;
+    for (int cl = 0; cl < kNumLinv; ++cl) {
+      if (lcnt[cl] == 0) continue;
+      LinvArgs f = la;
+      f.first = lfirst;
+      f.count = lcnt[cl];
+      f.counter = ctr + kNumClass + cl;
+      lfirst += lcnt[cl];
+      f.np = lcls[cl].gmat ? std::max(m.max_n, 1) : lcls[cl].np;
+      const bool inplace = lcls[cl].team == 32;
+      const int64_t slot = linv_slot_floats(f.np, inplace);
+      size_t smem = 0;
+      if (lcls[cl].gmat) {
+        f.gstride = (slot + 3) & ~3LL;
+        const int64_t slots = std::min<int64_t>(lcnt[cl], c->num_sms);
+        KSDF_CUDA(c, ensure(c->ws[WS_LINVSCR], sizeof(float) * (size_t)(f.gstride * slots + 4)));
+        f.gscr = ptr<float>(c->ws[WS_LINVSCR]);
+      } else {
+        smem = sizeof(float) * (size_t)slot;
+      }
+      cudaStream_t s = (nl % (ksdf_ctx::kNumAux + 1)) == ksdf_ctx::kNumAux ? st : c->aux[nl % (ksdf_ctx::kNumAux + 1)];
+      ++nl;
+      cudaError_t le = cudaSuccess;
+      switch (cl) {
+        case 0: le = launch_persistent(c, k_linv<512, false, true>, 512, f, smem, true, s); break;
+        case 1: le = launch_persistent(c, k_linv<224, false, false>, 224, f, smem, false, s); break;
+        case 2: le = launch_persistent(c, k_linv<160, false, false>, 160, f, smem, false, s); break;
+        default: le = launch_persistent(c, k_linv<32, true, false>, 32, f, smem, false, s); break;
+      }
+      KSDF_CUDA(c, le);
+    }
+    KSDF_CUDA(c, cudaGetLastError());
+    KSDF_CUDA(c, join_streams(c));
+  }
+  prof_end(c, e0, "fit.linv");
   KSDF_CUDA(c, cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st));
   KSDF_CUDA(c, cudaStreamSynchronize(st));
   m.n_not_pd = hmax[1];

@@ -149,7 +149,7 @@ struct ksdf_ctx {
   ksdf::Model m;
   // workspaces
   ksdf::DevBuf status_word;       // uint32 device status
-  ksdf::DevBuf ws[24];            // general workspaces (grow only), indexed by role
+  ksdf::DevBuf ws[25];            // general workspaces (grow only), indexed by role
   ksdf::DevBuf stage[12];         // staging of host arrays
   int64_t reserved_q = 0, reserved_s = 0;
   int bb[6] = {0, 0, 0, 0, 0, 0};  // bounding box of the cells: min xyz, max xyz
@@ -238,7 +238,8 @@ enum WsRole {
   WS_CAND = 20,
   WS_CELLQ = 21,  // per cell query counts / offsets
   WS_FITSCR = 22, // FP64 fit scratch
-  WS_BW = 23      // backward accumulators
+  WS_BW = 23,     // backward accumulators
+  WS_LINVSCR = 24 // FP32 L^-1 scratch of the largest cells
 };
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
