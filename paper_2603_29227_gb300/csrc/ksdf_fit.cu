@@ -106,6 +106,13 @@ __global__ void k_hash_insert(const uint64_t* cell_key, int64_t G, uint64_t* hk,
   }
 }
 
+// integer key with the order of the binary64 values (non-NaN; -0 and +0 equal): x < y iff key(x) < key(y)
+__device__ __forceinline__ long long f64_order_key(double v) {
+  long long b = __double_as_longlong(v);
+  if (b == (long long)0x8000000000000000ull) b = 0;
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
 // bitonic sort of n (power of two) ints in shared memory, ascending
 __device__ void smem_bitonic(int* a, int n) {
   for (int k = 2; k <= n; k <<= 1) {
@@ -134,17 +141,21 @@ __global__ void __launch_bounds__(512) k_assemble(const uint64_t* cell_key, int6
                                                   uint32_t* st) {
   __shared__ int ids[kMaxPre];
   __shared__ int cnt;
+  __shared__ long long s_lo[3], s_hi[3];
   const int64_t g = blockIdx.x;
   if (g >= G) return;
-  if (threadIdx.x == 0) cnt = 0;
-  __syncthreads();
   int c[3];
   unpack_key(cell_key[g], c[0], c[1], c[2]);
-  double lo[3], hi[3];
-  for (int j = 0; j < 3; ++j) {
-    lo[j] = __dsub_rn(cell_base(p.o[j], c[j], p.h), p.mu);
-    hi[j] = __dadd_rn(cell_base(p.o[j], c[j] + 1, p.h), p.mu);
+  // the box [lo, hi) in binary64 (computed once), compared through order-preserving integer keys
+  if (threadIdx.x == 0) {
+    cnt = 0;
+    for (int j = 0; j < 3; ++j) {
+      s_lo[j] = f64_order_key(__dsub_rn(cell_base(p.o[j], c[j], p.h), p.mu));
+      s_hi[j] = f64_order_key(__dadd_rn(cell_base(p.o[j], c[j] + 1, p.h), p.mu));
+    }
   }
+  __syncthreads();
+  const long long lo[3] = {s_lo[0], s_lo[1], s_lo[2]}, hi[3] = {s_hi[0], s_hi[1], s_hi[2]};
   // neighbour cells are spread over the warps (their hash lookups and member scans overlap)
   const int side = 2 * R + 1, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int nnb = p.dim == 3 ? side * side * side : side * side;
@@ -160,7 +171,10 @@ __global__ void __launch_bounds__(512) k_assemble(const uint64_t* cell_key, int6
       const uint32_t id = own_id[t];
       const double* xi = x + (int64_t)id * p.dim;
       bool in = true;
-      for (int j = 0; j < p.dim; ++j) in &= (xi[j] >= lo[j]) && (xi[j] < hi[j]);
+      for (int j = 0; j < p.dim; ++j) {
+        const long long k = f64_order_key(xi[j]);
+        in &= (k >= lo[j]) && (k < hi[j]);
+      }
       if (in) {
         const int pos = atomicAdd(&cnt, 1);
         if (pos < kMaxPre) ids[pos] = (int)id;
