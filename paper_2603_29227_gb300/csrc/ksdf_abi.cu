@@ -226,7 +226,7 @@ ksdf_status ksdf_destroy(ksdf_ctx* c) {
   Model& m = c->m;
   DevBuf* bufs[] = {&m.key,  &m.status, &m.n,    &m.ts_off, &m.chol_off, &m.linv_off, &m.hkeys,
                     &m.hvals, &m.cell_order, &m.mf4, &m.md4, &m.mvar,   &m.mnrm,     &m.mgid,     &m.mpad,
-                    &m.chol64, &m.linv32, &m.x,   &c->status_word};
+                    &m.chol64, &m.linv32, &m.x,   &m.ltc_off,   &m.ltc,      &c->status_word};
   for (DevBuf* b : bufs) release(*b);
   for (auto& b : c->ws) release(b);
   for (auto& b : c->stage) release(b);

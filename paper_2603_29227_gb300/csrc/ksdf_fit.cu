@@ -208,11 +208,12 @@ __global__ void __launch_bounds__(512) k_assemble(const uint64_t* cell_key, int6
   }
 }
 
-__global__ void k_sizes(const int64_t* n, int64_t G, int64_t* tri, int64_t* lb, int32_t* n32) {
+__global__ void k_sizes(const int64_t* n, int64_t G, int64_t* tri, int64_t* lb, int64_t* tc, int32_t* n32) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
   tri[g] = tri_sz(n[g]);
   lb[g] = linv_blocked_size(n[g]);
+  tc[g] = ltc_size(n[g]);
   n32[g] = (int32_t)n[g];
 }
 
@@ -529,6 +530,8 @@ struct LinvArgs {
   const int64_t* linv_off;
   const double* chol64;
   float* linv32;
+  const int64_t* ltc_off;
+  float* ltc;
   float* gscr;      // per-CTA global slot (largest class): linv_slot_floats(np, false)
   int64_t gstride;
   int np;
@@ -647,6 +650,15 @@ __global__ void __launch_bounds__(TEAM) k_linv(LinvArgs a) {
           dst[1] = make_float4(v[4], v[5], v[6], v[7]);
         }
       }
+      // the tensor-core image (column j of L^-1 is K index j of the B operand): all Np rows, zero padded
+      if (N <= kTcMaxN && j < tc_kp(N)) {
+        const int np16 = tc_np(N);
+        float* col = a.ltc + a.ltc_off[g] + (int64_t)(j >> 2) * np16 * 4 + (j & 3);
+        for (int i = 0; i < np16; ++i) {
+          const float v = (j < N && i < N && i >= j) ? (INPLACE ? xcol[tri_sz(i)] : xcol[(int64_t)i * 32]) : 0.f;
+          col[(int64_t)i * 4] = v;
+        }
+      }
       if (INPLACE) __syncwarp();
     }
     fit_sync(TEAM);
@@ -744,19 +756,22 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, ensure(m.ts_off, sizeof(int64_t) * (G + 1)));
   KSDF_CUDA(c, ensure(m.chol_off, sizeof(int64_t) * (G + 1)));
   KSDF_CUDA(c, ensure(m.linv_off, sizeof(int64_t) * (G + 1)));
-  KSDF_CUDA(c, ensure(c->ws[WS_D], sizeof(int64_t) * (3 * G + 3)));
+  KSDF_CUDA(c, ensure(m.ltc_off, sizeof(int64_t) * (G + 1)));
+  KSDF_CUDA(c, ensure(c->ws[WS_D], sizeof(int64_t) * (4 * G + 4)));
   int64_t* n64 = ptr<int64_t>(c->ws[WS_D]);
   int64_t* tri64 = n64 + (G + 1);
   int64_t* lb64 = tri64 + (G + 1);
+  int64_t* tc64 = lb64 + (G + 1);
   int* dmax = bbox + 6;
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
   launch(k_assemble, (unsigned)G, 512, 0, st, ptr<uint64_t>(m.key), G, own_off, vals, x, p, R, ptr<uint64_t>(m.hkeys),
          ptr<int32_t>(m.hvals), cap, ptr<int32_t>(m.mpad), n64, ptr<int32_t>(m.status), dmax, stw);
-  launch(k_sizes, ceil_div(G, 256), 256, 0, st, n64, G, tri64, lb64, ptr<int32_t>(m.n));
+  launch(k_sizes, ceil_div(G, 256), 256, 0, st, n64, G, tri64, lb64, tc64, ptr<int32_t>(m.n));
   KSDF_CUDA(c, scan_i64(n64, ptr<int64_t>(m.ts_off), G, dtot, c->ws[WS_SCAN], st));
   KSDF_CUDA(c, scan_i64(tri64, ptr<int64_t>(m.chol_off), G, dtot + 1, c->ws[WS_SCAN], st));
   KSDF_CUDA(c, scan_i64(lb64, ptr<int64_t>(m.linv_off), G, dtot + 2, c->ws[WS_SCAN], st));
-  int64_t tots[3];
+  KSDF_CUDA(c, scan_i64(tc64, ptr<int64_t>(m.ltc_off), G, dtot + 3, c->ws[WS_SCAN], st));
+  int64_t tots[4];
   int hmax[2];
   KSDF_CUDA(c, cudaMemcpyAsync(tots, dtot, sizeof(tots), cudaMemcpyDeviceToHost, st));
   KSDF_CUDA(c, cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st));
@@ -767,10 +782,12 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   m.M = tots[0];
   m.chol_total = tots[1];
   m.linv_total = tots[2];
+  m.ltc_total = tots[3];
   m.max_n = hmax[0];
   KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.ts_off) + G, &tots[0], sizeof(int64_t), cudaMemcpyHostToDevice, st));
   KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.chol_off) + G, &tots[1], sizeof(int64_t), cudaMemcpyHostToDevice, st));
   KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.linv_off) + G, &tots[2], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  KSDF_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(m.ltc_off) + G, &tots[3], sizeof(int64_t), cudaMemcpyHostToDevice, st));
   prof_end(c, e0, "fit.assemble");
   // 4. member arrays
   const int64_t M = m.M;
@@ -782,6 +799,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   if (nrm) KSDF_CUDA(c, ensure(m.mnrm, sizeof(float4) * (M + 1)));
   KSDF_CUDA(c, ensure(m.chol64, sizeof(double) * (m.chol_total + 1)));
   KSDF_CUDA(c, ensure(m.linv32, sizeof(float) * (m.linv_total + 4)));
+  KSDF_CUDA(c, ensure(m.ltc, sizeof(float) * (m.ltc_total + 4)));
   launch(k_gather_members, ceil_div(G * p.n_max, 256), 256, 0, st, ptr<uint64_t>(m.key), ptr<int32_t>(m.n),
          ptr<int64_t>(m.ts_off), ptr<int32_t>(m.mpad), G, p, x, var, nrm, ptr<int32_t>(m.mgid), ptr<D4>(m.md4),
          ptr<float4>(m.mf4), ptr<float>(m.mvar), nrm ? ptr<float4>(m.mnrm) : nullptr);
@@ -891,6 +909,8 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     la.linv_off = ptr<int64_t>(m.linv_off);
     la.chol64 = ptr<double>(m.chol64);
     la.linv32 = ptr<float>(m.linv32);
+    la.ltc_off = ptr<int64_t>(m.ltc_off);
+    la.ltc = ptr<float>(m.ltc);
     la.gscr = nullptr;
     la.gstride = 0;
     int64_t lfirst = 0;

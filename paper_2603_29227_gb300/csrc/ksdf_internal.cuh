@@ -114,6 +114,7 @@ struct Model {
   int64_t S = 0, G = 0, M = 0;    // samples, cells, training-set members
   int64_t chol_total = 0;         // sum N (N+1) / 2 (packed FP64 L)
   int64_t linv_total = 0;         // sum 32 nb (nb+1), nb = ceil(N/8) (FP32 L^-1, 8-row interleaved)
+  int64_t ltc_total = 0;          // sum ltc_size(N) (FP32 L^-1 as the tensor-core B operand)
   int max_n = 0;                  // largest training set
   bool has_normals = false;
   int n_not_pd = 0;
@@ -134,6 +135,10 @@ struct Model {
                    // j <= 8R+7, the 8 values L^-1[8R+r][j] (0 above the diagonal); block R starts at
                    // 32 R (R+1); size per cell 32 nb (nb+1), nb = ceil(N/8)
   DevBuf x;        // sample positions (S x dim double), kept for the backward's scatter
+  DevBuf ltc_off;  // int64 (G+1): offsets into ltc
+  DevBuf ltc;      // float: for cells with N <= kTcMaxN, L^-1 as the K-major B operand of the variance
+                   // contraction, rows (N dim) padded to Np = 16 ceil(N/16), columns (K dim) to Kp = 8 ceil(N/8),
+                   // in K-quads: element (j, i) at (i / 4) Np 4 + j 4 + i % 4 (zero outside the lower triangle)
 };
 
 }  // namespace ksdf
@@ -245,6 +250,14 @@ enum WsRole {
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 __host__ __device__ inline int64_t tri_sz(int64_t n) { return n * (n + 1) / 2; }
+
+// cells up to this size run the variance contraction on the tensor cores (one MMA covers N <= 256)
+constexpr int kTcMaxN = 256;
+__host__ __device__ inline int tc_np(int n) { return (n + 15) & ~15; }
+__host__ __device__ inline int tc_kp(int n) { return (n + 7) & ~7; }
+__host__ __device__ inline int64_t ltc_size(int64_t n) {
+  return (n > 0 && n <= kTcMaxN) ? (int64_t)tc_np((int)n) * tc_kp((int)n) : 0;
+}
 // size and block offset of the 8-row interleaved L^-1 layout
 __host__ __device__ inline int64_t linv_blocked_size(int64_t n) {
   const int64_t nb = (n + 7) / 8;

@@ -841,6 +841,347 @@ __global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* 
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Q6 with the variance contraction on the tensor cores (cells of N <= kTcMaxN samples).  A tile is up to
+// 128 queries of one winner cell, one thread per query (= row m of the MMA and TMEM lane m).  The thread
+// computes the nearest sample, then walks the samples in steps of 8: k'_i, grad f', the softmin sums, and
+// the k' values of the step written as the A operand (TF32 hi = rna(k'), lo = rna(k' - hi)).  The B operand
+// of the step -- 8 columns of L^-1, i.e. rows j of L^-1 restricted to the step's K range -- arrives by a TMA
+// bulk copy from the cell's tensor-core image and is split into hi/lo in place.  One thread issues
+//   D[:, n0:Np] (+)= A_hi B_hi + A_hi B_lo + A_lo B_hi   (tcgen05.mma kind::tf32, M = 128, K = 8),
+// with n0 = 16 floor(8 c / 16) skipping the zero upper blocks of L^-1; D = K' L^-T lives in TMEM.  Three
+// stages of A/B buffers, a TMA issued one step ahead, per-stage mbarriers for copy and MMA completion.
+// Finally each thread reads its TMEM row, |V_row|^2, and V[f] = 1 - e^{-2 lambda d^2} |V_row|^2.
+
+constexpr int kTcM = 128;
+constexpr int kTcSmallN = 96;  // cells up to this size: 128 TMEM columns (four CTAs per SM)
+constexpr int kTcStages = 3;
+constexpr uint32_t kTcStageA = 8192;  // A hi + lo: 2 K-quads x 128 rows x 16 B, twice
+
+__device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor, K-major without swizzle: lbo = bytes between core matrices along K,
+// sbo = bytes between 8-row groups
+__device__ inline uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor: D FP32, A and B TF32, both K-major, N and M
+__device__ inline uint32_t umma_idesc_tf32(int n, int m) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ inline void umma_tf32(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ inline void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ inline float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+// bounded wait of one thread (no barrier)
+__device__ inline bool mbar_wait_one(uint64_t* bar, uint32_t parity) {
+  for (unsigned it = 0; it < (kWaitLimit >> 4); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// sum of squares of 16 consecutive TMEM columns of this thread's lane
+__device__ inline float tmem_sumsq16(uint32_t taddr) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) s = fmaf(__uint_as_float(r[k]), __uint_as_float(r[k]), s);
+  return s;
+}
+
+struct TcArgs {
+  const int4* tiles;
+  const int64_t* n_tiles;
+  int* counter;
+  const int64_t* ltc_off;
+  const float* ltc;
+};
+
+// shared memory of one CTA: [kcap] samples (float4) | [kcap] var | stages of A (hi, lo) and B (hi, lo)
+__host__ __device__ inline size_t tc_stage_bytes(int npm) { return kTcStageA + 64u * (size_t)npm; }
+__host__ __device__ inline size_t tc_head_bytes(int kcap) { return ((size_t)20 * kcap + 1023) & ~(size_t)1023; }
+__host__ __device__ inline size_t tc_smem_bytes(int kcap) {
+  return tc_head_bytes(kcap) + kTcStages * tc_stage_bytes(tc_np(kcap));
+}
+
+__global__ void __launch_bounds__(kTcM) k_phaseB_tc(PhaseBArgs a, TcArgs t, const float* xq, Params p, float* sdf,
+                                                    float* grad, float* var_sdf, float* var_f, int32_t* winner,
+                                                    uint32_t* flags, int kcap, uint32_t ncols) {
+  extern __shared__ __align__(1024) unsigned char smb[];
+  __shared__ __align__(8) uint64_t bar_x, bar_tma[kTcStages], bar_mma[kTcStages];
+  __shared__ uint32_t s_tmem;
+  __shared__ int4 s_tile;
+  __shared__ float s_bh[3], s_bl[3];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int npm = tc_np(kcap);
+  float4* s_x = reinterpret_cast<float4*>(smb);
+  float* s_var = reinterpret_cast<float*>(s_x + kcap);
+  unsigned char* stg = smb + tc_head_bytes(kcap);
+  const uint32_t stage_bytes = (uint32_t)tc_stage_bytes(npm);
+  if (tid == 0) {
+    mbar_init(&bar_x, 1);
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&bar_tma[s], 1);
+      mbar_init(&bar_mma[s], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const float c1 = (float)p.lambda * kLog2e;
+  const float as = (float)p.alpha_s;
+  const float c2 = as * kLog2e;
+  const int64_t ntiles = *t.n_tiles;
+  uint32_t gstep = 0, tile_iter = 0;  // global step counter (stage = gstep % 3, use = gstep / 3)
+  bool fail = false;
+  for (;;) {
+    if (tid == 0) {
+      const int ti = atomicAdd(t.counter, 1);
+      s_tile = ti < ntiles ? t.tiles[ti] : make_int4(-1, 0, 0, 0);
+      if (ti < ntiles) {
+        const int g = s_tile.x, n = a.cell_n[g];
+        fence_proxy_async();
+        mbar_expect_tx(&bar_x, (uint32_t)n * 16u);
+        bulk_g2s(s_x, a.mf4 + a.ts_off[g], (uint32_t)n * 16u, &bar_x);
+        int cc[3];
+        unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
+        for (int j = 0; j < 3; ++j) base_split(p.o[j], cc[j], p.h, s_bh[j], s_bl[j]);
+      }
+    }
+    __syncthreads();
+    const int4 tile = s_tile;
+    if (tile.x < 0) break;
+    const int g = tile.x;
+    const int n = a.cell_n[g];
+    const int64_t m0 = a.ts_off[g];
+    const int np16 = tc_np(n), nsteps = tc_kp(n) >> 3;
+    const float* img = t.ltc + t.ltc_off[g];
+    for (int i = tid; i < n; i += kTcM) s_var[i] = a.mvar[m0 + i];  // not 16-byte aligned: plain loads
+    const bool live = tid < tile.z;
+    const int q = a.sorted_w[tile.y + (live ? tid : 0)];
+    float ql[3] = {0.f, 0.f, 0.f};
+    for (int j = 0; j < p.dim; ++j) ql[j] = local32(xq[(int64_t)q * p.dim + j], s_bh[j], s_bl[j]);
+    // B chunk of step c into the stage of global step gs: the two K-quads, rows n0 .. np16 - 1
+    auto issue_b = [&](int c, uint32_t gs) {
+      const int s = (int)(gs % kTcStages);
+      if (gs >= (uint32_t)kTcStages && !mbar_wait_one(&bar_mma[s], ((gs / kTcStages) - 1) & 1)) fail = true;
+      const int n0 = (c >> 1) << 4;
+      const uint32_t bytes = (uint32_t)(np16 - n0) * 16u;
+      unsigned char* bb = stg + (size_t)s * stage_bytes + kTcStageA;
+      fence_proxy_async();
+      mbar_expect_tx(&bar_tma[s], 2u * bytes);
+      for (int qd = 0; qd < 2; ++qd)
+        bulk_g2s(bb + (size_t)qd * npm * 16 + (size_t)n0 * 16, img + ((int64_t)(2 * c + qd) * np16 + n0) * 4, bytes,
+                 &bar_tma[s]);
+    };
+    if (tid == 0) issue_b(0, gstep);
+    if (!mbar_wait_one(&bar_x, tile_iter & 1)) fail = true;
+    __syncthreads();  // samples and var are in shared memory
+    // pass 1: nearest sample (first minimum in id order)
+    float m = INFINITY;
+    int nn = 0;
+    for (int i = 0; i < n; ++i) {
+      const float4 v = s_x[i];
+      const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (r2 < m) {
+        m = r2;
+        nn = i;
+      }
+    }
+    const float zmin = sqrtf(m);
+    const float cmn = c1 * m;
+    float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
+    for (int c = 0; c < nsteps; ++c, ++gstep) {
+      const int s = (int)(gstep % kTcStages);
+      unsigned char* sa = stg + (size_t)s * stage_bytes;
+      unsigned char* sb = sa + kTcStageA;
+      if (tid == 0 && c + 1 < nsteps) issue_b(c + 1, gstep + 1);
+      // the stage's previous MMA has finished reading A
+      if (gstep >= (uint32_t)kTcStages && !mbar_wait_one(&bar_mma[s], ((gstep / kTcStages) - 1) & 1)) fail = true;
+      // k' of samples 8c .. 8c+7 for this thread's query, with the gradient and softmin sums
+      float kv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = 8 * c + u;
+        float kp = 0.f;
+        if (i < n) {
+          const float4 v = s_x[i];
+          const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          kp = ex2(fmaf(-c1, r2, cmn));
+          const float ak = v.w * kp;
+          G0 = fmaf(ak, dx, G0);
+          G1 = fmaf(ak, dy, G1);
+          G2 = fmaf(ak, dz, G2);
+          const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+          const float y = fmaxf(z - zmin, 0.f);
+          const float wt = ex2(-c2 * y);
+          W += wt;
+          HY = fmaf(wt, y, HY);
+          const float tw = wt * wt * s_var[i];
+          T0 += tw;
+          T1 = fmaf(tw, y, T1);
+          T2 = fmaf(tw * y, y, T2);
+        }
+        kv[u] = live ? kp : 0.f;
+      }
+      // A operand (row tid): K-quad q at q * 2048 + tid * 16; lo part 4096 bytes further
+#pragma unroll
+      for (int qd = 0; qd < 2; ++qd) {
+        float hv[4], lv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          hv[e] = tf32_rna(kv[4 * qd + e]);
+          lv[e] = tf32_rna(kv[4 * qd + e] - hv[e]);
+        }
+        *reinterpret_cast<float4*>(sa + qd * 2048 + tid * 16) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<float4*>(sa + 4096 + qd * 2048 + tid * 16) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      }
+      // B operand of the step: split rows n0 .. np16 - 1 of both K-quads into hi (in place) and lo
+      if (!mbar_wait_one(&bar_tma[s], (gstep / kTcStages) & 1)) fail = true;
+      const int n0 = (c >> 1) << 4, rows = np16 - n0;
+      for (int e = tid; e < 2 * rows; e += kTcM) {
+        const int qd = e / rows, j = n0 + e - qd * rows;
+        float4* hp = reinterpret_cast<float4*>(sb + (size_t)qd * npm * 16 + (size_t)j * 16);
+        float4* lp = reinterpret_cast<float4*>(sb + (size_t)npm * 32 + (size_t)qd * npm * 16 + (size_t)j * 16);
+        const float4 x = *hp;
+        const float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
+        *hp = h;
+        *lp = make_float4(tf32_rna(x.x - h.x), tf32_rna(x.y - h.y), tf32_rna(x.z - h.z), tf32_rna(x.w - h.w));
+      }
+      fence_proxy_async();
+      if (__syncthreads_or(fail)) break;
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t idesc = umma_idesc_tf32(rows, kTcM);
+        const uint32_t a_hi = smem_u32(sa), a_lo = a_hi + 4096;
+        const uint32_t b_hi = smem_u32(sb) + (uint32_t)n0 * 16, b_lo = b_hi + (uint32_t)npm * 32;
+        const uint32_t d = tmem + (uint32_t)n0;
+        const uint32_t lbo_b = (uint32_t)npm * 16;
+        umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, c > 0 ? 1u : 0u);
+        umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_lo, lbo_b, 128), idesc, 1u);
+        umma_tf32(d, umma_desc(a_lo, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, 1u);
+        umma_commit(&bar_mma[s]);
+      }
+    }
+    if (__syncthreads_or(fail)) {
+      fail = true;
+      break;
+    }
+    // all MMAs of the tile are done when the last commit has arrived
+    {
+      const uint32_t gl = gstep - 1;
+      if (!mbar_wait_one(&bar_mma[gl % kTcStages], (gl / kTcStages) & 1)) fail = true;
+    }
+    tc_fence_after();
+    float VS = 0.f;
+    if (!fail) {
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+      for (int c0 = 0; c0 < np16; c0 += 16) VS += tmem_sumsq16(ta + (uint32_t)c0);
+    }
+    if (live && !fail) {
+      const float hy = HY / W;
+      const float B = fmaf(as, hy, 1.f);
+      const float vs = fmaxf((B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W), 0.f);
+      const float vf = fmaxf(1.f - ex2(-2.f * c1 * m) * VS, 0.f);
+      float sg = 1.f;
+      if (a.sign) {
+        sg = a.sign[q] < 0 ? -1.f : 1.f;
+      } else if (p.sign_mode == 1 && a.has_normals) {
+        const float4 v = s_x[nn];
+        const float4 nv = a.mnrm[m0 + nn];
+        sg = (nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z)) >= 0.f ? 1.f : -1.f;
+      }
+      uint32_t fl = a.qflag[q];
+      const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
+      if (a.mask & KSDF_OUT_SDF) sdf[q] = sg * a.qu[q];
+      if (a.mask & KSDF_OUT_GRAD) {
+        const float gv[3] = {G0, G1, G2};
+        const float ig = gn > 0.f ? sg / gn : 0.f;
+        for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gv[j] * ig;
+      }
+      if (!(gn > 0.f)) fl |= KSDF_FLAG_ZERO_GRAD;
+      if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
+      if (a.mask & KSDF_OUT_VAR_F) var_f[q] = vf;
+      if (a.mask & KSDF_OUT_WINNER) winner[q] = g;
+      if (a.mask & KSDF_OUT_FLAGS) flags[q] = fl;
+    }
+    ++tile_iter;
+    tc_fence_before();
+    if (__syncthreads_or(fail)) {
+      fail = true;
+      break;
+    }
+  }
+  if (fail && tid == 0) atomicOr(a.st, ST_TIMEOUT);
+  // on a timeout, give the last committed MMAs a bounded chance to finish before the TMEM is released
+  if (fail && gstep > 0 && tid == 0) {
+    const uint32_t gl = gstep - 1;
+    mbar_wait_one(&bar_mma[gl % kTcStages], (gl / kTcStages) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// tile counts of the cells in three lists by cell size: (0, n1], (n1, n2] (tiles of T12 queries) and larger
+// (tiles of T3 queries)
+__global__ void k_ntiles3(const int64_t* cnt, const int32_t* cell_n, int64_t n, int n1, int n2, int T12, int T3,
+                          int64_t* nt0, int64_t* nt1, int64_t* nt2) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int cn = cell_n[i];
+  const int cl = cn <= n1 ? 0 : (cn <= n2 ? 1 : 2);
+  const int T = cl == 2 ? T3 : T12;
+  const int64_t t = (cnt[i] + T - 1) / T;
+  nt0[i] = cl == 0 ? t : 0;
+  nt1[i] = cl == 1 ? t : 0;
+  nt2[i] = cl == 2 ? t : 0;
+}
+
+__global__ void k_make_tiles3(const int64_t* cnt, const int64_t* off, const int64_t* toff0, const int64_t* toff1,
+                              const int64_t* toff2, const int32_t* cell_n, int n1, int n2, int64_t ngroups, int T12,
+                              int T3, int4* tiles0, int4* tiles1, int4* tiles2) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ngroups) return;
+  const int64_t c = cnt[i];
+  const int cn = cell_n[i];
+  const int cl = cn <= n1 ? 0 : (cn <= n2 ? 1 : 2);
+  const int T = cl == 2 ? T3 : T12;
+  int4* dst = cl == 0 ? tiles0 + toff0[i] : (cl == 1 ? tiles1 + toff1[i] : tiles2 + toff2[i]);
+  for (int64_t k = 0; k * T < c; ++k)
+    dst[k] = make_int4((int)i, (int)(off[i] + k * T), (int)(c - k * T < T ? c - k * T : T), 0);
+}
+
 // Q6 (plain path): binary64 throughout; V[f] by forward substitution with the stored Cholesky factor,
 // v = L^{-1} k' (in place over k'), V[f] = 1 - e^{-2 lambda d^2} |v|^2.
 __global__ void __launch_bounds__(kTB64) k_phaseB64(PhaseBArgs a, const double* xq, Params p, double* sdf,
@@ -1020,9 +1361,9 @@ ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G) {
   KSDF_CUDA(c, ensure(c->ws[WS_BIN], sizeof(int64_t) * (5 * bcap + 8)));
   KSDF_CUDA(c, ensure(c->ws[WS_CAND], sizeof(int32_t) * (bcap * (K + 1))));
   const int64_t max_tiles_a = Q / kTA + bcap + 1;
-  const int64_t max_tiles_b = Q / kTB64 + G + 1;  // also covers the mixed path's 32-query tiles
-  KSDF_CUDA(c, ensure(c->ws[WS_TILE], sizeof(int4) * (max_tiles_a + max_tiles_b)));
-  KSDF_CUDA(c, ensure(c->ws[WS_CELLQ], sizeof(int64_t) * (4 * G + 8)));
+  const int64_t max_tiles_b = Q / kTB64 + G + 1;  // also covers the mixed path's three tile lists (+ 2 G + 2)
+  KSDF_CUDA(c, ensure(c->ws[WS_TILE], sizeof(int4) * (max_tiles_a + max_tiles_b + 2 * G + 2)));
+  KSDF_CUDA(c, ensure(c->ws[WS_CELLQ], sizeof(int64_t) * (8 * G + 8)));
   const int64_t nsc = (int64_t)bcap / 2048 + 2;
   KSDF_CUDA(c, ensure(c->ws[WS_SCAN], sizeof(int64_t) * nsc));
   return KSDF_OK;
@@ -1149,10 +1490,28 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
                                                        static_cast<float*>(var_sdf), static_cast<float*>(var_f),
                                                        winner, flags);
   KSDF_CUDA(c, scan_i64(wcnt, woff, G, nullptr, c->ws[WS_SCAN], st));
-  launch(k_ntiles, ceil_div(G, 256), 256, 0, st, wcnt, G, TBq, wnt);
-  KSDF_CUDA(c, scan_i64(wnt, wtoff, G, &totals[3], c->ws[WS_SCAN], st));
+  // mixed path: three tile lists by winner-cell size -- tensor-core tiles of kTcM queries for cells of at most
+  // kTcSmallN and kTcMaxN samples, SIMT tiles of kBItem for larger cells
+  const int64_t tcap = Q / kTcM + G + 1;
+  int4* tiles_b1 = tiles_b + tcap;
+  int4* tiles_b2 = tiles_b1 + tcap;
+  int64_t *nt1 = cbuf + 4 * G, *nt2 = cbuf + 5 * G, *toff1 = cbuf + 6 * G, *toff2 = cbuf + 7 * G;
+  if (f64) {
+    launch(k_ntiles, ceil_div(G, 256), 256, 0, st, wcnt, G, TBq, wnt);
+    KSDF_CUDA(c, scan_i64(wnt, wtoff, G, &totals[3], c->ws[WS_SCAN], st));
+  } else {
+    launch(k_ntiles3, ceil_div(G, 256), 256, 0, st, wcnt, ptr<int32_t>(m.n), G, kTcSmallN, kTcMaxN, kTcM, kBItem, wnt,
+           nt1, nt2);
+    KSDF_CUDA(c, scan_i64(wnt, wtoff, G, &totals[3], c->ws[WS_SCAN], st));
+    KSDF_CUDA(c, scan_i64(nt1, toff1, G, &totals[4], c->ws[WS_SCAN], st));
+    KSDF_CUDA(c, scan_i64(nt2, toff2, G, &totals[5], c->ws[WS_SCAN], st));
+  }
   launch(k_w_scatter, ceil_div(Q, 256), 256, 0, st, qwin, qbin, wrank, Q, woff, qwsort);
-  launch(k_make_tiles, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, G, TBq, tiles_b);
+  if (f64)
+    launch(k_make_tiles, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, G, TBq, tiles_b);
+  else
+    launch(k_make_tiles3, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, toff1, toff2, ptr<int32_t>(m.n), kTcSmallN,
+           kTcMaxN, G, kTcM, kBItem, tiles_b, tiles_b1, tiles_b2);
   prof_end(c, e0, "query.regroup");
   e0 = prof_begin(c);
   // Q6
@@ -1188,14 +1547,48 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
         pb, static_cast<const double*>(xq), p, static_cast<double*>(sdf), static_cast<double*>(grad),
         static_cast<double*>(var_sdf), static_cast<double*>(var_f), winner, flags);
   } else {
-    const int smax = std::max(m.max_n, 1);
-    const size_t smem = sizeof(float4) * smax + sizeof(float) * (linv_blocked_size(kLinvStageN) + (size_t)smax * (1 + kBQ));
-    KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int occ = 0;
-    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB, kBQ * kBW, smem));
-    launch(k_phaseB, std::max(1, occ) * c->num_sms, kBQ * kBW, smem, st, pb, static_cast<const float*>(xq), p,
-           static_cast<float*>(sdf), static_cast<float*>(grad), static_cast<float*>(var_sdf),
-           static_cast<float*>(var_f), winner, flags, smax);
+    // tensor-core tiles: cells of at most kTcSmallN samples, then of at most kTcMaxN (one after the other, each
+    // with the whole GPU: the TMEM of an SM is 512 columns); cells beyond kTcMaxN on the SIMT kernel meanwhile
+    const int maxn = std::max(m.max_n, 1);
+    if (maxn > kTcMaxN) {
+      KSDF_CUDA(c, fork_streams(c));
+      const int smax = maxn;
+      const size_t smem = sizeof(float4) * smax + sizeof(float) * (linv_blocked_size(kLinvStageN) + (size_t)smax * (1 + kBQ));
+      KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int occ = 0;
+      KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB, kBQ * kBW, smem));
+      PhaseBArgs p2 = pb;
+      p2.tiles = tiles_b2;
+      p2.n_tiles = &totals[5];
+      p2.counter = &counters[3];
+      launch(k_phaseB, std::max(1, occ) * c->num_sms, kBQ * kBW, smem, c->aux[0], p2, static_cast<const float*>(xq), p,
+             static_cast<float*>(sdf), static_cast<float*>(grad), static_cast<float*>(var_sdf),
+             static_cast<float*>(var_f), winner, flags, smax);
+    }
+    for (int part = 0; part < 2; ++part) {
+      if (part == 1 && maxn <= kTcSmallN) break;
+      const int kcap = std::min(part == 0 ? kTcSmallN : kTcMaxN, maxn);
+      uint32_t ncols = 32;
+      while ((int)ncols < tc_np(kcap)) ncols <<= 1;
+      const size_t smem = tc_smem_bytes(kcap);
+      KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+      // CTAs per SM: bounded by the TMEM columns (512 per SM) and the shared memory (227 KB per SM usable,
+      // plus the static part and the 1 KB the driver reserves per CTA)
+      const int by_smem = (int)((size_t)(227 * 1024) / (smem + 2048));
+      const int occ = std::max(1, std::min(by_smem, (int)(512 / ncols)));
+      TcArgs ta;
+      ta.tiles = part == 0 ? tiles_b : tiles_b1;
+      ta.n_tiles = &totals[3 + part];
+      ta.counter = &counters[1 + part];
+      ta.ltc_off = ptr<int64_t>(m.ltc_off);
+      ta.ltc = ptr<float>(m.ltc);
+      launch(k_phaseB_tc, occ * c->num_sms, kTcM, smem, st, pb, ta, static_cast<const float*>(xq), p,
+             static_cast<float*>(sdf), static_cast<float*>(grad), static_cast<float*>(var_sdf),
+             static_cast<float*>(var_f), winner, flags, kcap, ncols);
+    }
+    if (maxn > kTcMaxN) KSDF_CUDA(c, join_streams(c));
   }
   KSDF_CUDA(c, cudaGetLastError());
   prof_end(c, e0, f64 ? "query64.phaseB" : "query.phaseB");
