@@ -531,12 +531,19 @@ struct LinvArgs {
   const double* chol64;
   float* linv32;
   const int64_t* ltc_off;
-  float* ltc;
+  float* ltc;       // hi image at ltc + ltc_off[g], lo image ltc_lo floats further
+  int64_t ltc_lo;
   float* gscr;      // per-CTA global slot (largest class): linv_slot_floats(np, false)
   int64_t gstride;
   int np;
   int* counter;
 };
+
+__device__ __forceinline__ float tf32_rna_fit(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 
 // float offset of group g's buffer (after the reciprocal diagonal and L) and the slot size
 __host__ __device__ inline int64_t linv_group_off(int np, int g) {
@@ -650,13 +657,16 @@ __global__ void __launch_bounds__(TEAM) k_linv(LinvArgs a) {
           dst[1] = make_float4(v[4], v[5], v[6], v[7]);
         }
       }
-      // the tensor-core image (column j of L^-1 is K index j of the B operand): all Np rows, zero padded
+      // the tensor-core images (column j of L^-1 is K index j of the B operand): all Np rows, zero padded,
+      // split into TF32 hi = rna(x) and lo = rna(x - hi)
       if (N <= kTcMaxN && j < tc_kp(N)) {
         const int np16 = tc_np(N);
         float* col = a.ltc + a.ltc_off[g] + (int64_t)(j >> 2) * np16 * 4 + (j & 3);
         for (int i = 0; i < np16; ++i) {
           const float v = (j < N && i < N && i >= j) ? (INPLACE ? xcol[tri_sz(i)] : xcol[(int64_t)i * 32]) : 0.f;
-          col[(int64_t)i * 4] = v;
+          const float hi = tf32_rna_fit(v);
+          col[(int64_t)i * 4] = hi;
+          col[a.ltc_lo + (int64_t)i * 4] = tf32_rna_fit(v - hi);
         }
       }
       if (INPLACE) __syncwarp();
@@ -799,7 +809,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   if (nrm) KSDF_CUDA(c, ensure(m.mnrm, sizeof(float4) * (M + 1)));
   KSDF_CUDA(c, ensure(m.chol64, sizeof(double) * (m.chol_total + 1)));
   KSDF_CUDA(c, ensure(m.linv32, sizeof(float) * (m.linv_total + 4)));
-  KSDF_CUDA(c, ensure(m.ltc, sizeof(float) * (m.ltc_total + 4)));
+  KSDF_CUDA(c, ensure(m.ltc, sizeof(float) * (2 * m.ltc_total + 4)));
   launch(k_gather_members, ceil_div(G * p.n_max, 256), 256, 0, st, ptr<uint64_t>(m.key), ptr<int32_t>(m.n),
          ptr<int64_t>(m.ts_off), ptr<int32_t>(m.mpad), G, p, x, var, nrm, ptr<int32_t>(m.mgid), ptr<D4>(m.md4),
          ptr<float4>(m.mf4), ptr<float>(m.mvar), nrm ? ptr<float4>(m.mnrm) : nullptr);
@@ -911,6 +921,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     la.linv32 = ptr<float>(m.linv32);
     la.ltc_off = ptr<int64_t>(m.ltc_off);
     la.ltc = ptr<float>(m.ltc);
+    la.ltc_lo = m.ltc_total;
     la.gscr = nullptr;
     la.gstride = 0;
     int64_t lfirst = 0;

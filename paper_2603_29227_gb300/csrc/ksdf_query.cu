@@ -913,7 +913,8 @@ struct TcArgs {
   const int64_t* n_tiles;
   int* counter;
   const int64_t* ltc_off;
-  const float* ltc;
+  const float* ltc;  // TF32 hi images; the lo images ltc_lo floats further
+  int64_t ltc_lo;
 };
 
 // shared memory of one CTA: [kcap] samples (float4) | [kcap] var | stages of A (hi, lo) and B (hi, lo)
@@ -923,15 +924,24 @@ __host__ __device__ inline size_t tc_smem_bytes(int kcap) {
   return tc_head_bytes(kcap) + kTcStages * tc_stage_bytes(tc_np(kcap));
 }
 
-__global__ void __launch_bounds__(kTcM) k_phaseB_tc(PhaseBArgs a, TcArgs t, const float* xq, Params p, float* sdf,
-                                                    float* grad, float* var_sdf, float* var_f, int32_t* winner,
-                                                    uint32_t* flags, int kcap, uint32_t ncols) {
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp roles: warps 0..3 hold the tile's 128 queries (one per thread, = row m of the MMA and TMEM lane m) and
+// write the A operand step by step, signalling bar_full; warp 4 (lane 0) is the producer: it streams the B
+// chunks by TMA and issues the MMAs once a step's A is written and its B has arrived.  The query threads wait
+// only to reuse a stage (its MMA done) and for the tile's last MMA.
+__global__ void __launch_bounds__(kTcM + 32) k_phaseB_tc(PhaseBArgs a, TcArgs t, const float* xq, Params p,
+                                                         float* sdf, float* grad, float* var_sdf, float* var_f,
+                                                         int32_t* winner, uint32_t* flags, int kcap, uint32_t ncols) {
   extern __shared__ __align__(1024) unsigned char smb[];
-  __shared__ __align__(8) uint64_t bar_x, bar_tma[kTcStages], bar_mma[kTcStages];
+  __shared__ __align__(8) uint64_t bar_x, bar_tma[kTcStages], bar_mma[kTcStages], bar_full[kTcStages];
   __shared__ uint32_t s_tmem;
   __shared__ int4 s_tile;
   __shared__ float s_bh[3], s_bl[3];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool producer = warp == kTcM / 32;
   const int npm = tc_np(kcap);
   float4* s_x = reinterpret_cast<float4*>(smb);
   float* s_var = reinterpret_cast<float*>(s_x + kcap);
@@ -942,6 +952,7 @@ __global__ void __launch_bounds__(kTcM) k_phaseB_tc(PhaseBArgs a, TcArgs t, cons
     for (int s = 0; s < kTcStages; ++s) {
       mbar_init(&bar_tma[s], 1);
       mbar_init(&bar_mma[s], 1);
+      mbar_init(&bar_full[s], kTcM);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -967,7 +978,6 @@ __global__ void __launch_bounds__(kTcM) k_phaseB_tc(PhaseBArgs a, TcArgs t, cons
       s_tile = ti < ntiles ? t.tiles[ti] : make_int4(-1, 0, 0, 0);
       if (ti < ntiles) {
         const int g = s_tile.x, n = a.cell_n[g];
-        fence_proxy_async();
         mbar_expect_tx(&bar_x, (uint32_t)n * 16u);
         bulk_g2s(s_x, a.mf4 + a.ts_off[g], (uint32_t)n * 16u, &bar_x);
         int cc[3];
@@ -982,158 +992,159 @@ __global__ void __launch_bounds__(kTcM) k_phaseB_tc(PhaseBArgs a, TcArgs t, cons
     const int n = a.cell_n[g];
     const int64_t m0 = a.ts_off[g];
     const int np16 = tc_np(n), nsteps = tc_kp(n) >> 3;
-    const float* img = t.ltc + t.ltc_off[g];
-    for (int i = tid; i < n; i += kTcM) s_var[i] = a.mvar[m0 + i];  // not 16-byte aligned: plain loads
-    const bool live = tid < tile.z;
-    const int q = a.sorted_w[tile.y + (live ? tid : 0)];
-    float ql[3] = {0.f, 0.f, 0.f};
-    for (int j = 0; j < p.dim; ++j) ql[j] = local32(xq[(int64_t)q * p.dim + j], s_bh[j], s_bl[j]);
-    // B chunk of step c into the stage of global step gs: the two K-quads, rows n0 .. np16 - 1
-    auto issue_b = [&](int c, uint32_t gs) {
-      const int s = (int)(gs % kTcStages);
-      if (gs >= (uint32_t)kTcStages && !mbar_wait_one(&bar_mma[s], ((gs / kTcStages) - 1) & 1)) fail = true;
-      const int n0 = (c >> 1) << 4;
-      const uint32_t bytes = (uint32_t)(np16 - n0) * 16u;
-      unsigned char* bb = stg + (size_t)s * stage_bytes + kTcStageA;
-      fence_proxy_async();
-      mbar_expect_tx(&bar_tma[s], 2u * bytes);
-      for (int qd = 0; qd < 2; ++qd)
-        bulk_g2s(bb + (size_t)qd * npm * 16 + (size_t)n0 * 16, img + ((int64_t)(2 * c + qd) * np16 + n0) * 4, bytes,
-                 &bar_tma[s]);
-    };
-    if (tid == 0) issue_b(0, gstep);
-    if (!mbar_wait_one(&bar_x, tile_iter & 1)) fail = true;
-    __syncthreads();  // samples and var are in shared memory
-    // pass 1: nearest sample (first minimum in id order)
-    float m = INFINITY;
-    int nn = 0;
-    for (int i = 0; i < n; ++i) {
-      const float4 v = s_x[i];
-      const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (r2 < m) {
-        m = r2;
-        nn = i;
-      }
-    }
-    const float zmin = sqrtf(m);
-    const float cmn = c1 * m;
-    float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
-    for (int c = 0; c < nsteps; ++c, ++gstep) {
-      const int s = (int)(gstep % kTcStages);
-      unsigned char* sa = stg + (size_t)s * stage_bytes;
-      unsigned char* sb = sa + kTcStageA;
-      if (tid == 0 && c + 1 < nsteps) issue_b(c + 1, gstep + 1);
-      // the stage's previous MMA has finished reading A
-      if (gstep >= (uint32_t)kTcStages && !mbar_wait_one(&bar_mma[s], ((gstep / kTcStages) - 1) & 1)) fail = true;
-      // k' of samples 8c .. 8c+7 for this thread's query, with the gradient and softmin sums
-      float kv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int i = 8 * c + u;
-        float kp = 0.f;
-        if (i < n) {
-          const float4 v = s_x[i];
-          const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          kp = ex2(fmaf(-c1, r2, cmn));
-          const float ak = v.w * kp;
-          G0 = fmaf(ak, dx, G0);
-          G1 = fmaf(ak, dy, G1);
-          G2 = fmaf(ak, dz, G2);
-          const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-          const float y = fmaxf(z - zmin, 0.f);
-          const float wt = ex2(-c2 * y);
-          W += wt;
-          HY = fmaf(wt, y, HY);
-          const float tw = wt * wt * s_var[i];
-          T0 += tw;
-          T1 = fmaf(tw, y, T1);
-          T2 = fmaf(tw * y, y, T2);
+    if (producer) {
+      if (lane == 0) {
+        const float* img = t.ltc + t.ltc_off[g];
+        // B chunk of step c (hi and lo images) into the stage of global step gs: both K-quads, rows n0 .. np16-1,
+        // once the stage's previous MMA has finished reading it
+        auto issue_b = [&](int c, uint32_t gs) {
+          const int s = (int)(gs % kTcStages);
+          if (gs >= (uint32_t)kTcStages && !mbar_wait_one(&bar_mma[s], ((gs / kTcStages) - 1) & 1)) fail = true;
+          const int n0 = (c >> 1) << 4;
+          const uint32_t bytes = (uint32_t)(np16 - n0) * 16u;
+          unsigned char* bb = stg + (size_t)s * stage_bytes + kTcStageA;
+          mbar_expect_tx(&bar_tma[s], 4u * bytes);
+          for (int part = 0; part < 2; ++part)
+            for (int qd = 0; qd < 2; ++qd)
+              bulk_g2s(bb + (size_t)part * npm * 32 + (size_t)qd * npm * 16 + (size_t)n0 * 16,
+                       img + (part ? t.ltc_lo : 0) + ((int64_t)(2 * c + qd) * np16 + n0) * 4, bytes, &bar_tma[s]);
+        };
+        for (int c = 0; c < nsteps && c < kTcStages; ++c) issue_b(c, gstep + c);
+        for (int c = 0; c < nsteps && !fail; ++c) {
+          const uint32_t gs = gstep + c;
+          const int s = (int)(gs % kTcStages);
+          const uint32_t ph = (gs / kTcStages) & 1;
+          if (!mbar_wait_one(&bar_full[s], ph) || !mbar_wait_one(&bar_tma[s], ph)) {
+            fail = true;
+            break;
+          }
+          tc_fence_after();
+          const int n0 = (c >> 1) << 4, rows = np16 - n0;
+          unsigned char* sa = stg + (size_t)s * stage_bytes;
+          const uint32_t idesc = umma_idesc_tf32(rows, kTcM);
+          const uint32_t a_hi = smem_u32(sa), a_lo = a_hi + 4096;
+          const uint32_t b_hi = smem_u32(sa + kTcStageA) + (uint32_t)n0 * 16, b_lo = b_hi + (uint32_t)npm * 32;
+          const uint32_t d = tmem + (uint32_t)n0;
+          const uint32_t lbo_b = (uint32_t)npm * 16;
+          umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, c > 0 ? 1u : 0u);
+          umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_lo, lbo_b, 128), idesc, 1u);
+          umma_tf32(d, umma_desc(a_lo, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, 1u);
+          umma_commit(&bar_mma[s]);
+          if (c + kTcStages < nsteps) issue_b(c + kTcStages, gs + kTcStages);
         }
-        kv[u] = live ? kp : 0.f;
       }
-      // A operand (row tid): K-quad q at q * 2048 + tid * 16; lo part 4096 bytes further
-#pragma unroll
-      for (int qd = 0; qd < 2; ++qd) {
-        float hv[4], lv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          hv[e] = tf32_rna(kv[4 * qd + e]);
-          lv[e] = tf32_rna(kv[4 * qd + e] - hv[e]);
+      __syncwarp();
+    } else {
+      for (int i = tid; i < n; i += kTcM) s_var[i] = a.mvar[m0 + i];  // not 16-byte aligned: plain loads
+      const bool live = tid < tile.z;
+      const int q = a.sorted_w[tile.y + (live ? tid : 0)];
+      float ql[3] = {0.f, 0.f, 0.f};
+      for (int j = 0; j < p.dim; ++j) ql[j] = local32(xq[(int64_t)q * p.dim + j], s_bh[j], s_bl[j]);
+      if (!mbar_wait_one(&bar_x, tile_iter & 1)) fail = true;
+      asm volatile("bar.sync 1, %0;" ::"r"(kTcM) : "memory");  // var staged by all query threads
+      // pass 1: nearest sample (first minimum in id order)
+      float m = INFINITY;
+      int nn = 0;
+      for (int i = 0; i < n; ++i) {
+        const float4 v = s_x[i];
+        const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (r2 < m) {
+          m = r2;
+          nn = i;
         }
-        *reinterpret_cast<float4*>(sa + qd * 2048 + tid * 16) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<float4*>(sa + 4096 + qd * 2048 + tid * 16) = make_float4(lv[0], lv[1], lv[2], lv[3]);
       }
-      // B operand of the step: split rows n0 .. np16 - 1 of both K-quads into hi (in place) and lo
-      if (!mbar_wait_one(&bar_tma[s], (gstep / kTcStages) & 1)) fail = true;
-      const int n0 = (c >> 1) << 4, rows = np16 - n0;
-      for (int e = tid; e < 2 * rows; e += kTcM) {
-        const int qd = e / rows, j = n0 + e - qd * rows;
-        float4* hp = reinterpret_cast<float4*>(sb + (size_t)qd * npm * 16 + (size_t)j * 16);
-        float4* lp = reinterpret_cast<float4*>(sb + (size_t)npm * 32 + (size_t)qd * npm * 16 + (size_t)j * 16);
-        const float4 x = *hp;
-        const float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
-        *hp = h;
-        *lp = make_float4(tf32_rna(x.x - h.x), tf32_rna(x.y - h.y), tf32_rna(x.z - h.z), tf32_rna(x.w - h.w));
+      const float zmin = sqrtf(m);
+      const float cmn = c1 * m;
+      float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
+      for (int c = 0; c < nsteps; ++c) {
+        const uint32_t gs = gstep + c;
+        const int s = (int)(gs % kTcStages);
+        unsigned char* sa = stg + (size_t)s * stage_bytes;
+        // the stage's previous MMA has finished reading A
+        if (gs >= (uint32_t)kTcStages && !mbar_wait_one(&bar_mma[s], ((gs / kTcStages) - 1) & 1)) fail = true;
+        // k' of samples 8c .. 8c+7 for this thread's query, with the gradient and softmin sums
+        float kv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = 8 * c + u;
+          float kp = 0.f;
+          if (i < n) {
+            const float4 v = s_x[i];
+            const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            kp = ex2(fmaf(-c1, r2, cmn));
+            const float ak = v.w * kp;
+            G0 = fmaf(ak, dx, G0);
+            G1 = fmaf(ak, dy, G1);
+            G2 = fmaf(ak, dz, G2);
+            const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+            const float y = fmaxf(z - zmin, 0.f);
+            const float wt = ex2(-c2 * y);
+            W += wt;
+            HY = fmaf(wt, y, HY);
+            const float tw = wt * wt * s_var[i];
+            T0 += tw;
+            T1 = fmaf(tw, y, T1);
+            T2 = fmaf(tw * y, y, T2);
+          }
+          kv[u] = live ? kp : 0.f;
+        }
+        // A operand (row tid): K-quad q at q * 2048 + tid * 16; lo part 4096 bytes further
+#pragma unroll
+        for (int qd = 0; qd < 2; ++qd) {
+          float hv[4], lv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            hv[e] = tf32_rna(kv[4 * qd + e]);
+            lv[e] = tf32_rna(kv[4 * qd + e] - hv[e]);
+          }
+          *reinterpret_cast<float4*>(sa + qd * 2048 + tid * 16) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+          *reinterpret_cast<float4*>(sa + 4096 + qd * 2048 + tid * 16) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        }
+        fence_proxy_async();
+        mbar_arrive(&bar_full[s]);
       }
-      fence_proxy_async();
-      if (__syncthreads_or(fail)) break;
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t idesc = umma_idesc_tf32(rows, kTcM);
-        const uint32_t a_hi = smem_u32(sa), a_lo = a_hi + 4096;
-        const uint32_t b_hi = smem_u32(sb) + (uint32_t)n0 * 16, b_lo = b_hi + (uint32_t)npm * 32;
-        const uint32_t d = tmem + (uint32_t)n0;
-        const uint32_t lbo_b = (uint32_t)npm * 16;
-        umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, c > 0 ? 1u : 0u);
-        umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_lo, lbo_b, 128), idesc, 1u);
-        umma_tf32(d, umma_desc(a_lo, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, 1u);
-        umma_commit(&bar_mma[s]);
+      // the tile's last MMA (and so all of them) has finished
+      {
+        const uint32_t gl = gstep + nsteps - 1;
+        if (!mbar_wait_one(&bar_mma[gl % kTcStages], (gl / kTcStages) & 1)) fail = true;
+      }
+      tc_fence_after();
+      float VS = 0.f;
+      {
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < np16; c0 += 16) VS += tmem_sumsq16(ta + (uint32_t)c0);
+      }
+      if (live && !fail) {
+        const float hy = HY / W;
+        const float B = fmaf(as, hy, 1.f);
+        const float vs = fmaxf((B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W), 0.f);
+        const float vf = fmaxf(1.f - ex2(-2.f * c1 * m) * VS, 0.f);
+        float sg = 1.f;
+        if (a.sign) {
+          sg = a.sign[q] < 0 ? -1.f : 1.f;
+        } else if (p.sign_mode == 1 && a.has_normals) {
+          const float4 v = s_x[nn];
+          const float4 nv = a.mnrm[m0 + nn];
+          sg = (nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z)) >= 0.f ? 1.f : -1.f;
+        }
+        uint32_t fl = a.qflag[q];
+        const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
+        if (a.mask & KSDF_OUT_SDF) sdf[q] = sg * a.qu[q];
+        if (a.mask & KSDF_OUT_GRAD) {
+          const float gv[3] = {G0, G1, G2};
+          const float ig = gn > 0.f ? sg / gn : 0.f;
+          for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gv[j] * ig;
+        }
+        if (!(gn > 0.f)) fl |= KSDF_FLAG_ZERO_GRAD;
+        if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
+        if (a.mask & KSDF_OUT_VAR_F) var_f[q] = vf;
+        if (a.mask & KSDF_OUT_WINNER) winner[q] = g;
+        if (a.mask & KSDF_OUT_FLAGS) flags[q] = fl;
       }
     }
-    if (__syncthreads_or(fail)) {
-      fail = true;
-      break;
-    }
-    // all MMAs of the tile are done when the last commit has arrived
-    {
-      const uint32_t gl = gstep - 1;
-      if (!mbar_wait_one(&bar_mma[gl % kTcStages], (gl / kTcStages) & 1)) fail = true;
-    }
-    tc_fence_after();
-    float VS = 0.f;
-    if (!fail) {
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
-      for (int c0 = 0; c0 < np16; c0 += 16) VS += tmem_sumsq16(ta + (uint32_t)c0);
-    }
-    if (live && !fail) {
-      const float hy = HY / W;
-      const float B = fmaf(as, hy, 1.f);
-      const float vs = fmaxf((B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W), 0.f);
-      const float vf = fmaxf(1.f - ex2(-2.f * c1 * m) * VS, 0.f);
-      float sg = 1.f;
-      if (a.sign) {
-        sg = a.sign[q] < 0 ? -1.f : 1.f;
-      } else if (p.sign_mode == 1 && a.has_normals) {
-        const float4 v = s_x[nn];
-        const float4 nv = a.mnrm[m0 + nn];
-        sg = (nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z)) >= 0.f ? 1.f : -1.f;
-      }
-      uint32_t fl = a.qflag[q];
-      const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
-      if (a.mask & KSDF_OUT_SDF) sdf[q] = sg * a.qu[q];
-      if (a.mask & KSDF_OUT_GRAD) {
-        const float gv[3] = {G0, G1, G2};
-        const float ig = gn > 0.f ? sg / gn : 0.f;
-        for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gv[j] * ig;
-      }
-      if (!(gn > 0.f)) fl |= KSDF_FLAG_ZERO_GRAD;
-      if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
-      if (a.mask & KSDF_OUT_VAR_F) var_f[q] = vf;
-      if (a.mask & KSDF_OUT_WINNER) winner[q] = g;
-      if (a.mask & KSDF_OUT_FLAGS) flags[q] = fl;
-    }
+    gstep += (uint32_t)nsteps;
     ++tile_iter;
     tc_fence_before();
     if (__syncthreads_or(fail)) {
@@ -1584,7 +1595,8 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
       ta.counter = &counters[1 + part];
       ta.ltc_off = ptr<int64_t>(m.ltc_off);
       ta.ltc = ptr<float>(m.ltc);
-      launch(k_phaseB_tc, occ * c->num_sms, kTcM, smem, st, pb, ta, static_cast<const float*>(xq), p,
+      ta.ltc_lo = m.ltc_total;
+      launch(k_phaseB_tc, occ * c->num_sms, kTcM + 32, smem, st, pb, ta, static_cast<const float*>(xq), p,
              static_cast<float*>(sdf), static_cast<float*>(grad), static_cast<float*>(var_sdf),
              static_cast<float*>(var_f), winner, flags, kcap, ncols);
     }
