@@ -198,6 +198,12 @@ class ClockSampler:
 # algorithmic work per launch (roofline numerators)
 
 
+# DRAM bytes (read + write) per stage from one ncu capture of the current kernels on this workload
+# (profiles/room3d_kernels_ncu.md: the six populated k_fit size classes of one fit; the two k_phaseB_tc
+# launches of one query); None once a kernel changes until it is captured again
+MEASURED_TRAFFIC = {"fit.cholesky": 114.1e6, "query.phaseB": 490.3e6}
+
+
 def fit_fp64_flops(n):
     """FP64 flops of the fit of cells with training-set sizes n (exp evaluations not counted): kernel matrix
     r^2 (8 flops per lower-triangle entry), Cholesky N^3/3, alpha 2N^2 (two triangular solves).  The FP32
@@ -326,9 +332,9 @@ def main():
                          "peak": NOMINAL_FP32_TFLOPS, "unit": "TFLOP/s",
                          "what": "12 FP32 flops per (query, candidate sample) pair + 1 ex2; %.3g pairs" % pairs},
     }
-    for r in roof_all.values():
+    for k, r in roof_all.items():
         r["frac"] = r["achieved"] / r["peak"]
-        r["traffic"] = None
+        r["traffic"] = MEASURED_TRAFFIC.get(k)
     roof = dict(roof_all.get(dom, {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
                                    "traffic": None}))
     roof["kernel"] = dom
