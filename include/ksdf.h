@@ -120,9 +120,21 @@ ksdf_status ksdf_reserve(ksdf_ctx* ctx, int64_t max_samples, int64_t max_queries
  * the cap, KSDF_ERR_NOT_PD if some cell failed the factorisation (the model is still usable). */
 ksdf_status ksdf_fit(ksdf_ctx* ctx, const double* x, const float* var, const float* normals, int64_t S);
 
+/* Streaming update (Sec. IV-C: new surface samples arrive frame by frame and only the local GPs they touch
+ * are retrained): append S_new samples (x_new S_new x dim float64, var_new S_new float32 or NULL = 0,
+ * normals_new S_new x dim float32, required exactly when the model has normals) after the model's S
+ * samples, which keep their ids, and refit.  The result is the model ksdf_fit would build from all
+ * S + S_new samples; cells whose training set (members and their order) is unchanged take their factor,
+ * L^{-1} and alpha from the previous model instead of being refitted.  *n_cells_refit (host, may be NULL)
+ * receives the number of cells fitted.  Synchronises the stream.  Errors as ksdf_fit; on an error the
+ * context has no model (KSDF_ERR_NOT_FITTED until the next ksdf_fit).  KSDF_ERR_NOT_FITTED without a model. */
+ksdf_status ksdf_update(ksdf_ctx* ctx, const double* x_new, const float* var_new, const float* normals_new,
+                        int64_t S_new, int64_t* n_cells_refit);
+
 /* Mixed-precision query: Q points xq (Q x dim float32); sign (Q int8, +1/-1, may be NULL).  FP32 SIMT
- * arithmetic in cell-local coordinates for the mean (compensated sum), gradient and softmin variance,
- * and for the GP variance contraction with the FP32 L^{-1}.  Outputs (selected by
+ * arithmetic in cell-local coordinates for the mean (compensated sum), gradient and softmin variance; the
+ * GP variance contraction K' L^{-T} on the tensor cores in TF32 split three ways (hi*hi + hi*lo + lo*hi,
+ * FP32 accumulation) for winner cells of up to 256 samples, in FP32 SIMT beyond.  Outputs (selected by
  * out_mask): sdf[Q], grad[Q x dim] (gradient of d = s grad u), var_sdf[Q] (V[u], Sec. IV-B.3),
  * var_f[Q] (V[f], Sec. IV-B.1), winner[Q] (cell id of the fused GP, -1 if none; keep it for the
  * backward), flags[Q] (KSDF_FLAG_*). */

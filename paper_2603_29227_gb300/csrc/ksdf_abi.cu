@@ -2,6 +2,7 @@
 // argument checks, staging of host arrays through device workspaces, and dispatch to the fit, query and
 // backward pipelines.
 #include <cstdarg>
+#include <utility>
 #include <vector>
 
 #include "ksdf_internal.cuh"
@@ -226,8 +227,14 @@ ksdf_status ksdf_destroy(ksdf_ctx* c) {
   Model& m = c->m;
   DevBuf* bufs[] = {&m.key,  &m.status, &m.n,    &m.ts_off, &m.chol_off, &m.linv_off, &m.hkeys,
                     &m.hvals, &m.cell_order, &m.mf4, &m.md4, &m.mvar,   &m.mnrm,     &m.mgid,     &m.mpad,
-                    &m.chol64, &m.linv32, &m.x,   &m.ltc_off,   &m.ltc,      &c->status_word};
+                    &m.chol64, &m.linv32, &m.x,   &m.ltc_off,   &m.ltc,      &m.var_all, &m.nrm_all,
+                    &c->status_word};
   for (DevBuf* b : bufs) release(*b);
+  Model& mp = c->m_prev;
+  DevBuf* pbufs[] = {&mp.key,  &mp.status, &mp.n,      &mp.ts_off, &mp.chol_off, &mp.linv_off, &mp.hkeys,
+                     &mp.hvals, &mp.cell_order, &mp.mf4, &mp.md4, &mp.mvar,   &mp.mnrm,     &mp.mgid,
+                     &mp.mpad,  &mp.chol64, &mp.linv32, &mp.x, &mp.ltc_off, &mp.ltc, &mp.var_all, &mp.nrm_all};
+  for (DevBuf* b : pbufs) release(*b);
   for (auto& b : c->ws) release(b);
   for (auto& b : c->stage) release(b);
   for (auto& p : c->pending) {
@@ -256,6 +263,52 @@ ksdf_status ksdf_reserve(ksdf_ctx* c, int64_t max_samples, int64_t max_queries) 
   c->reserved_q = max_queries;
   if (max_queries > 0) return query_reserve(c, max_queries, c->m.G > 0 ? c->m.G : 1);
   return KSDF_OK;
+}
+
+ksdf_status ksdf_update(ksdf_ctx* c, const double* x_new, const float* var_new, const float* normals_new,
+                        int64_t S_new, int64_t* n_cells_refit) {
+  if (!c) return KSDF_ERR_ARG;
+  if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "ksdf_update: no model to update (call ksdf_fit first)");
+  if (S_new < 0 || (S_new > 0 && !x_new)) return set_err(c, KSDF_ERR_ARG, "ksdf_update: need x_new for S_new > 0");
+  Model& m = c->m;
+  if (S_new == 0) {
+    if (n_cells_refit) *n_cells_refit = 0;
+    return KSDF_OK;
+  }
+  if ((normals_new != nullptr) != m.has_normals)
+    return set_err(c, KSDF_ERR_ARG, "ksdf_update: normals must be given exactly when the model has normals");
+  const int dim = c->p.dim;
+  const int64_t S0 = m.S, S = S0 + S_new;
+  if (S >= (1LL << 31)) return set_err(c, KSDF_ERR_CAPACITY, "ksdf_update: S must stay below 2^31");
+  const void *dx, *dv, *dn;
+  ksdf_status s;
+  if ((s = stage_in(c, 0, x_new, sizeof(double) * S_new * dim, &dx))) return s;
+  if ((s = stage_in(c, 1, var_new, sizeof(float) * S_new, &dv))) return s;
+  if ((s = stage_in(c, 2, normals_new, sizeof(float) * S_new * dim, &dn))) return s;
+  // the union: the model's samples first (their ids are kept), then the new ones
+  cudaStream_t st = c->stream;
+  KSDF_CUDA(c, ensure(c->ws[WS_UX], sizeof(double) * S * dim));
+  KSDF_CUDA(c, ensure(c->ws[WS_UV], sizeof(float) * S));
+  double* ux = ptr<double>(c->ws[WS_UX]);
+  float* uv = ptr<float>(c->ws[WS_UV]);
+  float* un = nullptr;
+  KSDF_CUDA(c, cudaMemcpyAsync(ux, m.x.p, sizeof(double) * S0 * dim, cudaMemcpyDeviceToDevice, st));
+  KSDF_CUDA(c, cudaMemcpyAsync(ux + S0 * dim, dx, sizeof(double) * S_new * dim, cudaMemcpyDeviceToDevice, st));
+  KSDF_CUDA(c, cudaMemcpyAsync(uv, m.var_all.p, sizeof(float) * S0, cudaMemcpyDeviceToDevice, st));
+  if (dv) KSDF_CUDA(c, cudaMemcpyAsync(uv + S0, dv, sizeof(float) * S_new, cudaMemcpyDeviceToDevice, st));
+  else KSDF_CUDA(c, cudaMemsetAsync(uv + S0, 0, sizeof(float) * S_new, st));
+  if (m.has_normals) {
+    KSDF_CUDA(c, ensure(c->ws[WS_UN], sizeof(float) * S * dim));
+    un = ptr<float>(c->ws[WS_UN]);
+    KSDF_CUDA(c, cudaMemcpyAsync(un, m.nrm_all.p, sizeof(float) * S0 * dim, cudaMemcpyDeviceToDevice, st));
+    KSDF_CUDA(c, cudaMemcpyAsync(un + S0 * dim, dn, sizeof(float) * S_new * dim, cudaMemcpyDeviceToDevice, st));
+  }
+  // the current model becomes the previous one; the new model reuses the buffers of the one before
+  std::swap(c->m, c->m_prev);
+  int64_t nref = 0;
+  s = fit_model(c, ux, uv, un, S, &c->m_prev, &nref);
+  if (n_cells_refit) *n_cells_refit = nref;
+  return s;
 }
 
 ksdf_status ksdf_fit(ksdf_ctx* c, const double* x, const float* var, const float* normals, int64_t S) {

@@ -217,11 +217,82 @@ __global__ void k_sizes(const int64_t* n, int64_t G, int64_t* tri, int64_t* lb, 
   n32[g] = (int32_t)n[g];
 }
 
-__global__ void k_order_keys(const int32_t* n32, int64_t G, int n_max, uint64_t* keys, uint32_t* vals) {
+// fit order: descending size; cells not to be fitted (touched == 0) sort after every other
+__global__ void k_order_keys(const int32_t* n32, const int32_t* touched, int64_t G, int n_max, uint64_t* keys,
+                             uint32_t* vals) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
-  keys[g] = (uint64_t)(n_max - n32[g]);  // descending size
+  keys[g] = (!touched || touched[g]) ? (uint64_t)(n_max - n32[g]) : (uint64_t)(n_max + 1);
   vals[g] = (uint32_t)g;
+}
+
+// update: touched[g] = 1 unless the previous model has a cell with the same key, an OK fit and the same
+// training set (member ids in the same order); oid[g] = that cell's id (or -1).  One warp per cell.
+__global__ void k_touched(const uint64_t* key, const int32_t* n32, const int64_t* ts_off, const int32_t* mgid,
+                          int64_t G, const uint64_t* ohk, const int32_t* ohv, uint64_t ohcap, const int32_t* on32,
+                          const int64_t* ots_off, const int32_t* omgid, const int32_t* ostatus, int32_t* touched,
+                          int32_t* oid) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= G) return;
+  const int o = hash_find(ohk, ohv, ohcap, key[g]);
+  const int n = n32[g];
+  bool same = o >= 0 && on32[o] == n && ostatus[o] == KSDF_CELL_OK && n > 0;
+  if (same) {
+    const int32_t* a = mgid + ts_off[g];
+    const int32_t* b = omgid + ots_off[o];
+    bool eq = true;
+    for (int i = lane; i < n; i += 32) eq &= a[i] == b[i];
+    same = __all_sync(0xffffffffu, eq);
+  }
+  if (lane == 0) {
+    touched[g] = same ? 0 : 1;
+    oid[g] = o;
+  }
+}
+
+// update: an unchanged cell takes the previous model's fit (factor, L^-1 in both layouts, alpha, status)
+struct CopyFitArgs {
+  const int32_t *touched, *oid, *n32;
+  int64_t G;
+  const int64_t *ts_off, *chol_off, *linv_off, *ltc_off;
+  const int64_t *ots_off, *ochol_off, *olinv_off, *oltc_off;
+  const double* ochol64;
+  const float *olinv32, *oltc;
+  int64_t oltc_lo;
+  const D4* omd4;
+  double* chol64;
+  float *linv32, *ltc;
+  int64_t ltc_lo;
+  D4* md4;
+  float4* mf4;
+  int32_t* status;
+};
+
+__global__ void k_copy_fit(CopyFitArgs a) {
+  for (int64_t g = blockIdx.x; g < a.G; g += gridDim.x) {
+    if (a.touched[g]) continue;
+    const int o = a.oid[g], n = a.n32[g];
+    const int64_t T = tri_sz(n), lb = linv_blocked_size(n), tc = ltc_size(n);
+    const double* sc = a.ochol64 + a.ochol_off[o];
+    double* dc = a.chol64 + a.chol_off[g];
+    for (int64_t e = threadIdx.x; e < T; e += blockDim.x) dc[e] = sc[e];
+    const float* sl = a.olinv32 + a.olinv_off[o];
+    float* dl = a.linv32 + a.linv_off[g];
+    for (int64_t e = threadIdx.x; e < lb; e += blockDim.x) dl[e] = sl[e];
+    const float* st = a.oltc + a.oltc_off[o];
+    float* dt = a.ltc + a.ltc_off[g];
+    for (int64_t e = threadIdx.x; e < tc; e += blockDim.x) {
+      dt[e] = st[e];
+      dt[a.ltc_lo + e] = st[a.oltc_lo + e];
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double al = a.omd4[a.ots_off[o] + i].w;
+      a.md4[a.ts_off[g] + i].w = al;
+      a.mf4[a.ts_off[g] + i].w = d2f_bits(al);  // as the fit writes it
+    }
+    if (threadIdx.x == 0) a.status[g] = KSDF_CELL_OK;
+  }
 }
 
 // members: global id, cell-local FP64/FP32 coordinates, variance, normal
@@ -698,7 +769,8 @@ static cudaError_t launch_persistent(ksdf_ctx* c, K kern, int team, const Args& 
   return cudaSuccess;
 }
 
-ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const float* nrm, int64_t S) {
+ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const float* nrm, int64_t S, const Model* prev,
+                      int64_t* n_refit) {
   cudaStream_t st = c->stream;
   const Params& p = c->p;
   Model& m = c->m;
@@ -818,13 +890,35 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, ensure(m.cell_order, sizeof(uint32_t) * (G + 1)));
   uint64_t* okeys = ptr<uint64_t>(c->ws[WS_A]);
   uint32_t* order = ptr<uint32_t>(m.cell_order);
-  launch(k_order_keys, ceil_div(G, 256), 256, 0, st, ptr<int32_t>(m.n), G, p.n_max, okeys, order);
-  KSDF_CUDA(c, radix_sort_u64(okeys, order, G, bits_for((uint64_t)p.n_max), c->ws[WS_SORT], st));
-  // size classes (host histogram), launched concurrently, largest first; each class has its team size
-  // and the number of rows per thread of the FP32 inversion (np <= team * rows)
-  std::vector<int32_t> hn((size_t)G);
+  // update: which cells need a fit (training set changed), the others copy the previous model's later
+  int32_t* touched = nullptr;
+  int32_t* oid = nullptr;
+  if (prev) {
+    KSDF_CUDA(c, ensure(c->ws[WS_TOUCH], sizeof(int32_t) * 2 * (G + 1)));
+    touched = ptr<int32_t>(c->ws[WS_TOUCH]);
+    oid = touched + (G + 1);
+    Model& o = const_cast<Model&>(*prev);
+    launch(k_touched, ceil_div(G * 32, 256), 256, 0, st, ptr<uint64_t>(m.key), ptr<int32_t>(m.n),
+           ptr<int64_t>(m.ts_off), ptr<int32_t>(m.mgid), G, ptr<uint64_t>(o.hkeys), ptr<int32_t>(o.hvals), o.hcap,
+           ptr<int32_t>(o.n), ptr<int64_t>(o.ts_off), ptr<int32_t>(o.mgid), ptr<int32_t>(o.status), touched, oid);
+  }
+  launch(k_order_keys, ceil_div(G, 256), 256, 0, st, ptr<int32_t>(m.n), touched, G, p.n_max, okeys, order);
+  KSDF_CUDA(c, radix_sort_u64(okeys, order, G, bits_for((uint64_t)p.n_max + 1), c->ws[WS_SORT], st));
+  // size classes (host histogram of the cells to fit), launched concurrently, largest first; each class has
+  // its team size
+  std::vector<int32_t> hn((size_t)G), ht;
   KSDF_CUDA(c, cudaMemcpyAsync(hn.data(), m.n.p, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, st));
+  if (prev) {
+    ht.resize((size_t)G);
+    KSDF_CUDA(c, cudaMemcpyAsync(ht.data(), touched, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, st));
+  }
   KSDF_CUDA(c, cudaStreamSynchronize(st));
+  int64_t nfit = 0;
+  for (int64_t g = 0; g < G; ++g) {
+    if (prev && !ht[(size_t)g]) hn[(size_t)g] = -1;  // not fitted: out of every class
+    else ++nfit;
+  }
+  if (n_refit) *n_refit = nfit;
   constexpr int kNumClass = 7;
   struct FitClass {
     int np, team;
@@ -834,6 +928,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
                                    {96, 64, false},       {80, 32, false},   {64, 32, false}};
   int64_t cnt[kNumClass] = {};
   for (int32_t v : hn) {
+    if (v < 0) continue;
     int cl = kNumClass - 1;
     while (cl > 0 && v > cls[cl].np) --cl;
     ++cnt[cl];
@@ -905,6 +1000,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
                                      {64, 32, false}};
     int64_t lcnt[kNumLinv] = {};
     for (int32_t v : hn) {
+      if (v < 0) continue;
       int cl = kNumLinv - 1;
       while (cl > 0 && v > lcls[cl].np) --cl;
       ++lcnt[cl];
@@ -960,12 +1056,49 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     KSDF_CUDA(c, join_streams(c));
   }
   prof_end(c, e0, "fit.linv");
+  if (prev && nfit < G) {
+    Model& o = const_cast<Model&>(*prev);
+    CopyFitArgs ca;
+    ca.touched = touched;
+    ca.oid = oid;
+    ca.n32 = ptr<int32_t>(m.n);
+    ca.G = G;
+    ca.ts_off = ptr<int64_t>(m.ts_off);
+    ca.chol_off = ptr<int64_t>(m.chol_off);
+    ca.linv_off = ptr<int64_t>(m.linv_off);
+    ca.ltc_off = ptr<int64_t>(m.ltc_off);
+    ca.ots_off = ptr<int64_t>(o.ts_off);
+    ca.ochol_off = ptr<int64_t>(o.chol_off);
+    ca.olinv_off = ptr<int64_t>(o.linv_off);
+    ca.oltc_off = ptr<int64_t>(o.ltc_off);
+    ca.ochol64 = ptr<double>(o.chol64);
+    ca.olinv32 = ptr<float>(o.linv32);
+    ca.oltc = ptr<float>(o.ltc);
+    ca.oltc_lo = o.ltc_total;
+    ca.omd4 = ptr<D4>(o.md4);
+    ca.chol64 = ptr<double>(m.chol64);
+    ca.linv32 = ptr<float>(m.linv32);
+    ca.ltc = ptr<float>(m.ltc);
+    ca.ltc_lo = m.ltc_total;
+    ca.md4 = ptr<D4>(m.md4);
+    ca.mf4 = ptr<float4>(m.mf4);
+    ca.status = ptr<int32_t>(m.status);
+    launch(k_copy_fit, (unsigned)std::min<int64_t>(G, 8 * c->num_sms), 256, 0, st, ca);
+  }
   KSDF_CUDA(c, cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st));
   KSDF_CUDA(c, cudaStreamSynchronize(st));
   m.n_not_pd = hmax[1];
-  // keep the sample positions for the adjoint's per-cell recomputation
+  // keep the samples: positions for the adjoint's per-cell recomputation; all three for later updates
+  m.S = S;
   KSDF_CUDA(c, ensure(m.x, sizeof(double) * S * p.dim));
   KSDF_CUDA(c, cudaMemcpyAsync(m.x.p, x, sizeof(double) * S * p.dim, cudaMemcpyDeviceToDevice, st));
+  KSDF_CUDA(c, ensure(m.var_all, sizeof(float) * S));
+  if (var) KSDF_CUDA(c, cudaMemcpyAsync(m.var_all.p, var, sizeof(float) * S, cudaMemcpyDeviceToDevice, st));
+  else KSDF_CUDA(c, cudaMemsetAsync(m.var_all.p, 0, sizeof(float) * S, st));
+  if (nrm) {
+    KSDF_CUDA(c, ensure(m.nrm_all, sizeof(float) * S * p.dim));
+    KSDF_CUDA(c, cudaMemcpyAsync(m.nrm_all.p, nrm, sizeof(float) * S * p.dim, cudaMemcpyDeviceToDevice, st));
+  }
   prof_end(c, e_fit, "fit");
   c->fitted = true;
   if (m.n_not_pd > 0)

@@ -135,6 +135,8 @@ struct Model {
                    // j <= 8R+7, the 8 values L^-1[8R+r][j] (0 above the diagonal); block R starts at
                    // 32 R (R+1); size per cell 32 nb (nb+1), nb = ceil(N/8)
   DevBuf x;        // sample positions (S x dim double), kept for the backward's scatter
+  DevBuf var_all;  // float: every sample's sigma^2 (S), kept for updates
+  DevBuf nrm_all;  // float: every sample's normal (S x dim), when the model has normals
   DevBuf ltc_off;  // int64 (G+1): offsets into ltc
   DevBuf ltc;      // float: for cells with N <= kTcMaxN, L^-1 as the K-major B operand of the variance
                    // contraction, rows (N dim) padded to Np = 16 ceil(N/16), columns (K dim) to Kp = 8 ceil(N/8),
@@ -153,9 +155,10 @@ struct ksdf_ctx {
   std::string err;
   bool fitted = false;
   ksdf::Model m;
+  ksdf::Model m_prev;  // the previous model during an update (its buffers are reused by the next one)
   // workspaces
   ksdf::DevBuf status_word;       // uint32 device status
-  ksdf::DevBuf ws[25];            // general workspaces (grow only), indexed by role
+  ksdf::DevBuf ws[29];            // general workspaces (grow only), indexed by role
   ksdf::DevBuf stage[12];         // staging of host arrays
   int64_t reserved_q = 0, reserved_s = 0;
   int bb[6] = {0, 0, 0, 0, 0, 0};  // bounding box of the cells: min xyz, max xyz
@@ -206,7 +209,10 @@ cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
 cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, DevBuf& tmp, cudaStream_t st);
 
 // ---- fit (ksdf_fit.cu) ----
-ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const float* nrm, int64_t S);
+// the fit; with `prev` (the model being updated, whose samples are x[0 .. prev->S)), cells whose training set
+// is unchanged copy prev's factors instead of being refitted, and *n_refit receives the number refitted
+ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const float* nrm, int64_t S,
+                      const Model* prev = nullptr, int64_t* n_refit = nullptr);
 ksdf_status bin_points(ksdf_ctx* c, const double* x, int64_t n, uint64_t* keys);
 
 // ---- query (ksdf_query.cu) ----
@@ -245,7 +251,11 @@ enum WsRole {
   WS_CELLQ = 21,  // per cell query counts / offsets
   WS_FITSCR = 22, // FP64 fit scratch
   WS_BW = 23,     // backward accumulators
-  WS_LINVSCR = 24 // FP32 L^-1 scratch of the largest cells
+  WS_LINVSCR = 24, // FP32 L^-1 scratch of the largest cells
+  WS_TOUCH = 25,  // update: per cell touched flag and previous id
+  WS_UX = 26,     // update: the union of old and new samples (positions, variances, normals)
+  WS_UV = 27,
+  WS_UN = 28
 };
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }

@@ -26,7 +26,7 @@ FLAG_FALLBACK, FLAG_NO_GP, FLAG_NEAR_TIE, FLAG_ZERO_GRAD, FLAG_CLAMPED, FLAG_INV
 CELL_OK, CELL_EMPTY, CELL_NOT_PD = 0, 1, 2
 
 # every entry point declared in include/ksdf.h
-ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_query",
+ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_update", "ksdf_query",
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
                  "ksdf_fit_gp_noalloc")
@@ -62,6 +62,7 @@ def load(path: str = LIB_PATH):
         "ksdf_set_stream": [P, P],
         "ksdf_reserve": [P, I64, I64],
         "ksdf_fit": [P, P, P, P, I64],
+        "ksdf_update": [P, P, P, P, I64, ctypes.POINTER(I64)],
         "ksdf_query": [P, P, I64, P, U32, P, P, P, P, P, P],
         "ksdf_query_f64": [P, P, I64, P, U32, P, P, P, P, P, P],
         "ksdf_query_backward": [P, P, I64, P, P, P, P, P, P],
@@ -163,6 +164,16 @@ def ksdf_fit(h, x, var, normals, S, allow_not_pd=True):
         return rc
     _check(h, rc, "ksdf_fit")
     return rc
+
+
+def ksdf_update(h, x_new, var_new, normals_new, S_new, allow_not_pd=True):
+    """Append S_new samples and refit the touched cells; returns (status, number of cells refitted)."""
+    n = ctypes.c_int64(0)
+    rc = load().ksdf_update(h, _ptr(x_new, np.float64), _ptr(var_new, np.float32), _ptr(normals_new, np.float32),
+                            int(S_new), ctypes.byref(n))
+    if not (rc == KSDF_ERR_NOT_PD and allow_not_pd):
+        _check(h, rc, "ksdf_update")
+    return rc, int(n.value)
 
 
 def ksdf_query(h, xq, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags):
@@ -312,6 +323,14 @@ class KernelSDF:
         self.S = int(x.shape[0])
         self.fit_status = ksdf_fit(self.h, x, var, normals, self.S)
         return self.fit_status
+
+    def update(self, x_new, var=None, normals=None):
+        """Append samples (their ids follow the model's) and refit the cells they touch; returns the number
+        of cells refitted."""
+        self._stream()
+        self.fit_status, n = ksdf_update(self.h, x_new, var, normals, int(x_new.shape[0]))
+        self.S += int(x_new.shape[0])
+        return n
 
     def query(self, xq, sign=None, mask=OUT_ALL, f64=False):
         torch = self._torch
