@@ -291,11 +291,13 @@ __device__ void linv_solve32(const float* Lb, int n, const float* rhs, float* y,
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_bw_cell(const int64_t* qcnt, int64_t G, const int64_t* ts_off,
+constexpr int kBwCellThreads = 64;  // two warps per cell: ~70-row cells keep most lanes busy, 32 cells per SM
+
+__global__ void __launch_bounds__(kBwCellThreads) k_bw_cell(const int64_t* qcnt, int64_t G, const int64_t* ts_off,
                                                  const int32_t* cell_n, const int64_t* chol_off, const double* chol64,
                                                  const int64_t* linv_off, const float* linv32, const float4* mf4,
                                                  const int32_t* mgid, const double* abar, Params p, float* d_x) {
-  extern __shared__ double sh[];  // [n] alpha_bar (double), [n] t (double), then floats: rhs, y, b
+  extern __shared__ double sh[];  // [n] alpha_bar, [n] t, [n] b0 (double), then floats: rhs, y, b
   for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
     if (qcnt[g] == 0) continue;
     const int n = cell_n[g];
@@ -304,7 +306,8 @@ __global__ void __launch_bounds__(256) k_bw_cell(const int64_t* qcnt, int64_t G,
     const float* Lb = linv32 + linv_off[g];
     double* sa = sh;
     double* st = sh + n;
-    float* srhs = reinterpret_cast<float*>(sh + 2 * n);
+    double* sbd = sh + 2 * n;
+    float* srhs = reinterpret_cast<float*>(sh + 3 * n);
     float* sy = srhs + n;
     float* sb = sy + n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -313,6 +316,8 @@ __global__ void __launch_bounds__(256) k_bw_cell(const int64_t* qcnt, int64_t G,
     }
     __syncthreads();
     linv_solve32(Lb, n, srhs, sy, sb, false);  // b0
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sbd[i] = (double)sb[i];  // converted once, not per FMA
+    __syncthreads();
     // t = L^T b0: rows in lockstep, threads over columns k (coalesced row reads)
     for (int k = threadIdx.x; k < n; k += blockDim.x) st[k] = 0.0;
     for (int k0 = 0; k0 < n; k0 += blockDim.x) {
@@ -323,12 +328,12 @@ __global__ void __launch_bounds__(256) k_bw_cell(const int64_t* qcnt, int64_t G,
       int i = k0 + (threadIdx.x & ~31);
       if (k < n) {
         for (; i + 3 < n; i += 4) {
-          c0 = fma(k <= i ? L[tri_sz(i) + k] : 0.0, (double)sb[i], c0);
-          c1 = fma(k <= i + 1 ? L[tri_sz(i + 1) + k] : 0.0, (double)sb[i + 1], c1);
-          c2 = fma(k <= i + 2 ? L[tri_sz(i + 2) + k] : 0.0, (double)sb[i + 2], c2);
-          c3 = fma(k <= i + 3 ? L[tri_sz(i + 3) + k] : 0.0, (double)sb[i + 3], c3);
+          c0 = fma(k <= i ? L[tri_sz(i) + k] : 0.0, sbd[i], c0);
+          c1 = fma(k <= i + 1 ? L[tri_sz(i + 1) + k] : 0.0, sbd[i + 1], c1);
+          c2 = fma(k <= i + 2 ? L[tri_sz(i + 2) + k] : 0.0, sbd[i + 2], c2);
+          c3 = fma(k <= i + 3 ? L[tri_sz(i + 3) + k] : 0.0, sbd[i + 3], c3);
         }
-        for (; i < n; ++i) c0 = fma(k <= i ? L[tri_sz(i) + k] : 0.0, (double)sb[i], c0);
+        for (; i < n; ++i) c0 = fma(k <= i ? L[tri_sz(i) + k] : 0.0, sbd[i], c0);
         st[k] = (c0 + c1) + (c2 + c3);
       }
     }
@@ -433,12 +438,12 @@ ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* 
   launch(k_bw_query, std::max(1, occ) * c->num_sms, kTW, smem, st, a, xq, p);
   prof_end(c, e0, "backward.query");
   e0 = prof_begin(c);
-  const size_t smem2 = sizeof(double) * 2 * p.n_max + sizeof(float) * 3 * p.n_max;
+  const size_t smem2 = sizeof(double) * 3 * p.n_max + sizeof(float) * 3 * p.n_max;
   KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
   int occ2 = 0;
-  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_bw_cell, 256, smem2));
+  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_bw_cell, kBwCellThreads, smem2));
   const unsigned grid2 = (unsigned)std::min<int64_t>(G, (int64_t)std::max(1, occ2) * c->num_sms);
-  launch(k_bw_cell, std::max(1u, grid2), 256, smem2, st, cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
+  launch(k_bw_cell, std::max(1u, grid2), kBwCellThreads, smem2, st, cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
          ptr<int64_t>(m.chol_off), ptr<double>(m.chol64), ptr<int64_t>(m.linv_off), ptr<float>(m.linv32),
          ptr<float4>(m.mf4), ptr<int32_t>(m.mgid), abar, p, d_x);
   KSDF_CUDA(c, cudaGetLastError());
