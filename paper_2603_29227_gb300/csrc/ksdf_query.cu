@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
         int cc[3];
         unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
         for (int j = 0; j < 3; ++j) s_off[k][j] = (float)((double)(bc[j] - cc[j]) * p.h);
-        base += n;
+        base += (n + 7) & ~7;  // each candidate padded to a multiple of 8 samples
         bytes += (uint32_t)n * 16u;
       }
       fence_proxy_async();
@@ -374,6 +374,12 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
     }
     if (tid == 0)
       for (int j = 0; j < 3; ++j) base_split(p.o[j], bc[j], p.h, s_bh[j], s_bl[j]);
+    __syncthreads();  // candidate list known
+    // padding samples: far away with zero weight, so that every chunk of 8 is full (no per-sample guards)
+    for (int e = tid; e < s_nc * 8; e += blockDim.x) {
+      const int k = e >> 3, i = s_n[k] + (e & 7);
+      if (i < ((s_n[k] + 7) & ~7)) s_x[s_base[k] + i] = make_float4(1e15f, 1e15f, 1e15f, 0.f);
+    }
     const bool live = tid < tile.z;
     const int q = live ? a.sorted_q[tile.y + tid] : 0;
     float xg[3] = {0.f, 0.f, 0.f};
@@ -401,15 +407,10 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
           float r2[8], al[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            if (i0 + j < n) {
-              const float4 v = xs[i0 + j];
-              const float dx = qx - v.x, dy = qy - v.y, dz = qz - v.z;
-              r2[j] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              al[j] = v.w;
-            } else {
-              r2[j] = INFINITY;
-              al[j] = 0.f;
-            }
+            const float4 v = xs[i0 + j];
+            const float dx = qx - v.x, dy = qy - v.y, dz = qz - v.z;
+            r2[j] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            al[j] = v.w;
           }
           float cm = fminf(fminf(fminf(r2[0], r2[1]), fminf(r2[2], r2[3])), fminf(fminf(r2[4], r2[5]), fminf(r2[6], r2[7])));
           const float mn = fminf(m, cm);
@@ -417,14 +418,15 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
           s *= sc;
           comp *= sc;
           const float cmn = c1 * mn;
+          float tj[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float tj = al[j] * ex2(fmaf(-c1, r2[j], cmn));
-            const float y = tj - comp;
-            const float tt = s + y;
-            comp = (tt - s) - y;
-            s = tt;
-          }
+          for (int j = 0; j < 8; ++j) tj[j] = al[j] * ex2(fmaf(-c1, r2[j], cmn));
+          // the chunk's terms summed as a tree, then added to the running sum with compensation
+          const float cs = ((tj[0] + tj[1]) + (tj[2] + tj[3])) + ((tj[4] + tj[5]) + (tj[6] + tj[7]));
+          const float y = cs - comp;
+          const float tt = s + y;
+          comp = (tt - s) - y;
+          s = tt;
           m = mn;
         }
         const float f = s - comp;
@@ -1479,7 +1481,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA64, kTA, smem));
     launch(k_phaseA64, std::max(1, occ) * c->num_sms, kTA, smem, st, pa, static_cast<const double*>(xq), p);
   } else {
-    const size_t smem = sizeof(float4) * (size_t)p.K * maxn;
+    const size_t smem = sizeof(float4) * (size_t)p.K * ((maxn + 7) & ~7);
     KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA, kTA, smem));
