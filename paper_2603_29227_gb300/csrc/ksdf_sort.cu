@@ -83,6 +83,46 @@ __global__ void k_scan_apply(const int64_t* in, int64_t* out, int64_t n, const i
   }
 }
 
+// small arrays: the whole exclusive scan in one 1024-thread block (one launch instead of three); each
+// thread owns a contiguous run of up to kScanSingleItems elements
+constexpr int kScanSingleThreads = 1024;
+constexpr int kScanSingleItems = 64;
+
+__global__ void __launch_bounds__(kScanSingleThreads) k_scan_single(const int64_t* in, int64_t* out, int64_t n,
+                                                                     int64_t* total) {
+  __shared__ int64_t sw[kScanSingleThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t per = (n + kScanSingleThreads - 1) / kScanSingleThreads;
+  const int64_t b = (int64_t)threadIdx.x * per, e = b + per < n ? b + per : n;
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += in[i];
+  int64_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sw[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = sw[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sw[lane] = w;  // inclusive prefix over the warps
+  }
+  __syncthreads();
+  int64_t run = (warp ? sw[warp - 1] : 0) + x - s;
+  for (int64_t i = b; i < e; ++i) {
+    const int64_t v = in[i];
+    out[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == kScanSingleThreads - 1 && total) *total = sw[31];
+}
+
 // ---- radix sort ----
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
@@ -152,6 +192,10 @@ cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
     if (total) return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
     return cudaSuccess;
   }
+  if (n <= (int64_t)kScanSingleThreads * kScanSingleItems) {
+    launch(k_scan_single, 1, kScanSingleThreads, 0, st, in, out, n, total);
+    return cudaGetLastError();
+  }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   cudaError_t e = ensure(tmp, sizeof(int64_t) * (size_t)(nb + 1));
   if (e != cudaSuccess) return e;
@@ -184,9 +228,13 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, 
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
     launch(k_rs_hist, nblocks, kRsThreads, 0, st, ki, n, shift, hist, nblocks);
-    launch(k_scan_reduce, (unsigned)nb_scan, kScanThreads, 0, st, hist, nh, sums);
-    launch(k_scan_sums, 1, kScanThreads, 0, st, sums, nb_scan, nullptr);
-    launch(k_scan_apply, (unsigned)nb_scan, kScanThreads, 0, st, hist, hist, nh, sums);
+    if (nh <= (int64_t)kScanSingleThreads * kScanSingleItems) {
+      launch(k_scan_single, 1, kScanSingleThreads, 0, st, hist, hist, nh, (int64_t*)nullptr);
+    } else {
+      launch(k_scan_reduce, (unsigned)nb_scan, kScanThreads, 0, st, hist, nh, sums);
+      launch(k_scan_sums, 1, kScanThreads, 0, st, sums, nb_scan, (int64_t*)nullptr);
+      launch(k_scan_apply, (unsigned)nb_scan, kScanThreads, 0, st, hist, hist, nh, sums);
+    }
     launch(k_rs_scatter, nblocks, kRsThreads, 0, st, ki, vi, ko, vo, n, shift, hist, nblocks);
     uint64_t* tk = ki; ki = ko; ko = tk;
     uint32_t* tv = vi; vi = vo; vo = tv;
