@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg (cpu_baseline, parity)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch query + adjoint eagerly instead of replaying a CUDA graph")
     return ap.parse_args()
 
 
@@ -273,6 +274,28 @@ def main():
         out, dq, dx = step()
     torch.cuda.synchronize()
     model.sync_status()
+    # the query and its adjoint allocate nothing after the warm-up (workspaces sized): capture them once in a
+    # CUDA graph and replay it per step after the (eager) fit, which sizes its launches on the host
+    graph_launches = 0
+    if not args.no_graph:
+        _, l0 = ksdf.ksdf_profile_read(model.h)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            out_g = model.query(xq, sign)
+            dq_g, dx_g = model.backward(xq, out_g["winner"], d_sdf, d_grad, sign)
+        _, l1 = ksdf.ksdf_profile_read(model.h)
+        graph_launches = int(l1 - l0)
+        eager_step = step
+
+        def step():
+            model.fit(x, var, nrm)
+            graph.replay()
+            return out_g, dq_g, dx_g
+
+        for _ in range(2):
+            out, dq, dx = step()
+        torch.cuda.synchronize()
+        model.sync_status()
     # timed region
     ksdf.ksdf_profile(model.h, 1)
     _, launches0 = ksdf.ksdf_profile_read(model.h)
@@ -299,8 +322,21 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     stages, launches1 = ksdf.ksdf_profile_read(model.h)
+    launches1 += graph_launches * args.steps  # kernels replayed from the graph
     ksdf.ksdf_profile(model.h, 0)
     model.sync_status()
+    if not args.no_graph:
+        # per-stage times of the query and the adjoint (inside the graph above) from two eager profiled steps
+        ksdf.ksdf_profile(model.h, 1)
+        ksdf.ksdf_profile_read(model.h)
+        for _ in range(2):
+            eager_step()
+        torch.cuda.synchronize()
+        st2, _ = ksdf.ksdf_profile_read(model.h)
+        ksdf.ksdf_profile(model.h, 0)
+        for k, v in st2.items():
+            if k.startswith("query") or k.startswith("backward"):
+                stages[k] = v
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     total_s = float(step_ms.sum()) / 1e3
     if world > 1:
@@ -413,6 +449,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "samples": S, "queries": Q, "cells": int(len(nsz)),
+                   "launch": ("fit launched from the host (it sizes its launches on the host); query + adjoint "
+                              "replayed from one CUDA graph captured after the warm-up" if not args.no_graph
+                              else "all launched from the host"),
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "precision": "FP64 kernel matrix, Cholesky and alpha; FP32 L^-1; FP32 query with compensated "
                                 "mean; FP32 adjoint with one FP64 refinement of each cell solve"},
