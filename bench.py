@@ -278,6 +278,9 @@ def main():
         dq, dx = model.backward(xq, out["winner"], d_sdf, d_grad, sign)
         return out, dq, dx
 
+    # the fit's tile shape (warps per cell, by cell size) picked by timing the candidates on this model
+    model.fit(x, var, nrm)
+    tune_idx, tune_ms = model.autotune()
     for _ in range(max(args.warmup, 3)):
         out, dq, dx = step()
     torch.cuda.synchronize()
@@ -460,6 +463,7 @@ def main():
                    "launch": ("fit launched from the host (it sizes its launches on the host); query + adjoint "
                               "replayed from one CUDA graph captured after the warm-up" if not args.no_graph
                               else "all launched from the host"),
+                   "fit_autotune": {"table": tune_idx, "fit_ms_per_table": [round(float(v), 3) for v in tune_ms]},
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "precision": "FP64 kernel matrix (entries above 2.4e-16; smaller ones in FP32), Cholesky and "
                                 "alpha; FP32 L^-1; FP32 query with compensated mean; V[f] contraction on tcgen05 in "

@@ -131,6 +131,15 @@ ksdf_status ksdf_fit(ksdf_ctx* ctx, const double* x, const float* var, const flo
 ksdf_status ksdf_update(ksdf_ctx* ctx, const double* x_new, const float* var_new, const float* normals_new,
                         int64_t S_new, int64_t* n_cells_refit);
 
+/* Autotuning of the batched fit's tile shape (the number of warps that factor one cell, per range of cell
+ * sizes): times every candidate size-class table (ksdf_autotune_tables() of them) on the fitted model's own
+ * cells -- each a full fit run twice, the second timed with CUDA events on the context's stream -- keeps the
+ * fastest for the context's later fits and updates, and refits with it.  The model's numbers do not depend
+ * on the table.  *table (may be NULL) receives the chosen index, fit_ms (may be NULL, ksdf_autotune_tables()
+ * doubles) the measured fit times.  Synchronises the stream.  KSDF_ERR_NOT_FITTED without a model. */
+ksdf_status ksdf_autotune(ksdf_ctx* ctx, int* table, double* fit_ms);
+int ksdf_autotune_tables(void);
+
 /* Mixed-precision query: Q points xq (Q x dim float32); sign (Q int8, +1/-1, may be NULL).  FP32 SIMT
  * arithmetic in cell-local coordinates for the mean (compensated sum), gradient and softmin variance; the
  * GP variance contraction K' L^{-T} on the tensor cores in TF32 split three ways (hi*hi + hi*lo + lo*hi,

@@ -311,6 +311,13 @@ ksdf_status ksdf_update(ksdf_ctx* c, const double* x_new, const float* var_new, 
   return s;
 }
 
+ksdf_status ksdf_autotune(ksdf_ctx* c, int* table, double* fit_ms) {
+  if (!c) return KSDF_ERR_ARG;
+  return autotune_fit(c, table, fit_ms);
+}
+
+int ksdf_autotune_tables(void) { return fit_table_count(); }
+
 ksdf_status ksdf_fit(ksdf_ctx* c, const double* x, const float* var, const float* normals, int64_t S) {
   if (!c) return KSDF_ERR_ARG;
   if (S <= 0 || !x) return set_err(c, KSDF_ERR_ARG, "ksdf_fit: need S > 0 samples");

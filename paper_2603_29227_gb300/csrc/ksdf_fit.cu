@@ -919,14 +919,10 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     else ++nfit;
   }
   if (n_refit) *n_refit = nfit;
-  constexpr int kNumClass = 7;
-  struct FitClass {
-    int np, team;
-    bool gmat;
-  };
-  const FitClass cls[kNumClass] = {{kMaxNmax, 256, true}, {218, 256, false}, {156, 128, false}, {128, 128, false},
-                                   {96, 64, false},       {80, 32, false},   {64, 32, false}};
-  int64_t cnt[kNumClass] = {};
+  using FitClass = FitClassCfg;
+  const std::vector<FitClassCfg>& cls = c->fit_cls.empty() ? fit_table(0) : c->fit_cls;
+  const int kNumClass = (int)cls.size();
+  std::vector<int64_t> cnt((size_t)kNumClass, 0);
   for (int32_t v : hn) {
     if (v < 0) continue;
     int cl = kNumClass - 1;
@@ -934,9 +930,9 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     ++cnt[cl];
   }
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
-  KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 16));  // counters: fit and L^-1 classes
+  KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 32));  // counters: fit and L^-1 classes
   int* ctr = reinterpret_cast<int*>(ptr<int64_t>(c->ws[WS_E]) + 4);
-  KSDF_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int) * kNumClass, st));
+  KSDF_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int) * 16, st));
   FitArgs fa;
   fa.order = order;
   fa.n32 = ptr<int32_t>(m.n);
@@ -1005,7 +1001,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
       while (cl > 0 && v > lcls[cl].np) --cl;
       ++lcnt[cl];
     }
-    KSDF_CUDA(c, cudaMemsetAsync(ctr + kNumClass, 0, sizeof(int) * kNumLinv, st));
+    KSDF_CUDA(c, cudaMemsetAsync(ctr + 16, 0, sizeof(int) * kNumLinv, st));
     KSDF_CUDA(c, fork_streams(c));
     LinvArgs la;
     la.order = order;
@@ -1027,7 +1023,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
       LinvArgs f = la;
       f.first = lfirst;
       f.count = lcnt[cl];
-      f.counter = ctr + kNumClass + cl;
+      f.counter = ctr + 16 + cl;
       lfirst += lcnt[cl];
       f.np = lcls[cl].gmat ? std::max(m.max_n, 1) : lcls[cl].np;
       const bool inplace = lcls[cl].team == 32;
@@ -1104,6 +1100,83 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   if (m.n_not_pd > 0)
     return set_err(c, KSDF_ERR_NOT_PD, "ksdf_fit: %d cell(s) not positive definite in FP64 (excluded)", m.n_not_pd);
   return KSDF_OK;
+}
+
+// candidate size-class tables of the fit (largest class first; the first entry keeps its matrices in a
+// global slot).  Table 0 is the default; ksdf_autotune times them all on the model's own cells.  The result
+// of a fit does not depend on the table (each cell's arithmetic is the same whatever the team size).
+static const std::vector<std::vector<FitClassCfg>> kFitTables = {
+    // one warp up to 80, two up to 96, four up to 156, eight up to 218
+    {{kMaxNmax, 256, true}, {218, 256, false}, {156, 128, false}, {128, 128, false}, {96, 64, false},
+     {80, 32, false}, {64, 32, false}},
+    // one warp up to 96, two up to 128
+    {{kMaxNmax, 256, true}, {218, 256, false}, {156, 128, false}, {128, 64, false}, {96, 32, false},
+     {80, 32, false}, {64, 32, false}},
+    // one warp up to 64, two up to 128
+    {{kMaxNmax, 256, true}, {218, 256, false}, {156, 128, false}, {128, 64, false}, {96, 64, false},
+     {80, 64, false}, {64, 32, false}, {48, 32, false}},
+    // one warp up to 80, two up to 128, four up to 218
+    {{kMaxNmax, 256, true}, {218, 128, false}, {156, 128, false}, {128, 64, false}, {96, 64, false},
+     {80, 32, false}, {64, 32, false}},
+};
+
+int fit_table_count() { return (int)kFitTables.size(); }
+const std::vector<FitClassCfg>& fit_table(int i) { return kFitTables[(size_t)i]; }
+
+// time every candidate table on the fitted model (each fit run twice, the second timed with CUDA events on
+// the context stream), keep the fastest in the context, and refit with it; the model is unchanged
+ksdf_status autotune_fit(ksdf_ctx* c, int* chosen, double* ms) {
+  if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "ksdf_autotune: no model (call ksdf_fit first)");
+  Model& m = c->m;
+  const int dim = c->p.dim;
+  const int64_t S = m.S;
+  cudaStream_t st = c->stream;
+  KSDF_CUDA(c, ensure(c->ws[WS_UX], sizeof(double) * S * dim));
+  KSDF_CUDA(c, ensure(c->ws[WS_UV], sizeof(float) * S));
+  double* ux = ptr<double>(c->ws[WS_UX]);
+  float* uv = ptr<float>(c->ws[WS_UV]);
+  float* un = nullptr;
+  KSDF_CUDA(c, cudaMemcpyAsync(ux, m.x.p, sizeof(double) * S * dim, cudaMemcpyDeviceToDevice, st));
+  KSDF_CUDA(c, cudaMemcpyAsync(uv, m.var_all.p, sizeof(float) * S, cudaMemcpyDeviceToDevice, st));
+  if (m.has_normals) {
+    KSDF_CUDA(c, ensure(c->ws[WS_UN], sizeof(float) * S * dim));
+    un = ptr<float>(c->ws[WS_UN]);
+    KSDF_CUDA(c, cudaMemcpyAsync(un, m.nrm_all.p, sizeof(float) * S * dim, cudaMemcpyDeviceToDevice, st));
+  }
+  const bool prof = c->prof;
+  c->prof = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KSDF_CUDA(c, cudaEventCreate(&e0));
+  KSDF_CUDA(c, cudaEventCreate(&e1));
+  int best = 0;
+  double best_ms = 1e300;
+  ksdf_status rs = KSDF_OK;
+  for (int t = 0; t < fit_table_count() && rs == KSDF_OK; ++t) {
+    c->fit_cls = fit_table(t);
+    float tms = 0.f;
+    for (int rep = 0; rep < 2 && rs == KSDF_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      rs = fit_model(c, ux, uv, un, S);
+      cudaEventRecord(e1, st);
+      if (rs == KSDF_ERR_NOT_PD) rs = KSDF_OK;
+    }
+    if (rs != KSDF_OK) break;
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&tms, e0, e1);
+    if (ms) ms[t] = tms;
+    if (tms < best_ms) {
+      best_ms = tms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->prof = prof;
+  if (rs != KSDF_OK) return rs;
+  c->fit_cls = fit_table(best);
+  if (chosen) *chosen = best;
+  rs = fit_model(c, ux, uv, un, S);
+  return rs == KSDF_ERR_NOT_PD ? KSDF_OK : rs;
 }
 
 namespace {

@@ -146,6 +146,15 @@ struct Model {
 
 }  // namespace ksdf
 
+namespace ksdf {
+// one size class of the batched fit: cells of N up to np are factored by teams of `team` threads; the
+// largest class keeps its matrices in a per-CTA global slot (gmat)
+struct FitClassCfg {
+  int np, team;
+  bool gmat;
+};
+}  // namespace ksdf
+
 struct ksdf_ctx {
   ksdf::Params p;
   ksdf_params abi;
@@ -156,6 +165,7 @@ struct ksdf_ctx {
   bool fitted = false;
   ksdf::Model m;
   ksdf::Model m_prev;  // the previous model during an update (its buffers are reused by the next one)
+  std::vector<ksdf::FitClassCfg> fit_cls;  // the fit's size classes (empty: the default table); ksdf_autotune
   // workspaces
   ksdf::DevBuf status_word;       // uint32 device status
   ksdf::DevBuf ws[29];            // general workspaces (grow only), indexed by role
@@ -197,6 +207,11 @@ template <class T> inline T* ptr(DevBuf& b) { return static_cast<T*>(b.p); }
 // ---- stage profiling (ksdf_abi.cu): no-ops unless enabled ----
 cudaEvent_t prof_begin(ksdf_ctx* c);
 void prof_end(ksdf_ctx* c, cudaEvent_t a, const char* name);
+
+// ---- autotuning of the fit's size classes (ksdf_fit.cu) ----
+int fit_table_count();
+const std::vector<FitClassCfg>& fit_table(int i);
+ksdf_status autotune_fit(ksdf_ctx* c, int* chosen, double* ms);
 
 // ---- fork/join of the context stream with the auxiliary streams (ksdf_abi.cu) ----
 cudaError_t fork_streams(ksdf_ctx* c);

@@ -29,7 +29,7 @@ CELL_OK, CELL_EMPTY, CELL_NOT_PD = 0, 1, 2
 ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_update", "ksdf_query",
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
-                 "ksdf_fit_gp_noalloc")
+                 "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables")
 
 
 class KsdfError(RuntimeError):
@@ -76,6 +76,8 @@ def load(path: str = LIB_PATH):
         "ksdf_profile": [P, ctypes.c_int],
         "ksdf_profile_read": [P, ctypes.c_int, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(I64)],
         "ksdf_fit_gp_noalloc": [ctypes.POINTER(ksdf_params), P, P, I64, P, P, P, P],
+        "ksdf_autotune": [P, ctypes.POINTER(ctypes.c_int), P],
+        "ksdf_autotune_tables": [],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -164,6 +166,15 @@ def ksdf_fit(h, x, var, normals, S, allow_not_pd=True):
         return rc
     _check(h, rc, "ksdf_fit")
     return rc
+
+
+def ksdf_autotune(h):
+    """Time the fit's candidate size-class tables on the fitted model; returns (chosen index, times in ms)."""
+    n = load().ksdf_autotune_tables()
+    ms = np.zeros(n)
+    t = ctypes.c_int(-1)
+    _check(h, load().ksdf_autotune(h, ctypes.byref(t), _ptr(ms)), "ksdf_autotune")
+    return int(t.value), ms
 
 
 def ksdf_update(h, x_new, var_new, normals_new, S_new, allow_not_pd=True):
@@ -323,6 +334,11 @@ class KernelSDF:
         self.S = int(x.shape[0])
         self.fit_status = ksdf_fit(self.h, x, var, normals, self.S)
         return self.fit_status
+
+    def autotune(self):
+        """Pick the fit's team-size table by timing the candidates on this model; returns (index, ms)."""
+        self._stream()
+        return ksdf_autotune(self.h)
 
     def update(self, x_new, var=None, normals=None):
         """Append samples (their ids follow the model's) and refit the cells they touch; returns the number

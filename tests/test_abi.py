@@ -19,7 +19,7 @@ def lib():
 
 def declared():
     hdr = open(os.path.join(ROOT, "include", "ksdf.h")).read()
-    return re.findall(r"^(?:ksdf_status|const char\*)\s+(ksdf_\w+)\(", hdr, re.M)
+    return re.findall(r"^(?:ksdf_status|const char\*|int)\s+(ksdf_\w+)\(", hdr, re.M)
 
 
 def test_exports_every_declared_symbol(lib):
