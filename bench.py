@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-repeats", type=int, default=9, help="repetitions of the oracle sample (~10 s in all)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg (cpu_baseline, parity)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-others", action="store_true", help="skip the other workloads (2D, differentiation, scale, "
+                    "streaming)")
     ap.add_argument("--no-graph", action="store_true", help="launch query + adjoint eagerly instead of replaying a CUDA graph")
     return ap.parse_args()
 
@@ -238,6 +240,108 @@ def phase_a_pairs(w, h):
 
 
 # ----------------------------------------------------------------------------------------------------
+
+
+def _timed(torch, fn, steps, warmup=3):
+    """Mean ms of fn() over `steps` runs timed with CUDA events on the current stream (after `warmup`)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def other_configs(torch, dev, ksdf):
+    """The other synthetic workloads, one GPU, device-resident inputs, CUDA-event timing (warm-up 3)."""
+    from paper_2603_29227_gb300 import scenes
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    res = {}
+    # 2D plain FP64: fit + FP64 query of the 128 x 128 grid (latency bound: microseconds)
+    w = scenes.workload("plane2d")
+    m = ksdf.KernelSDF(w.params)
+    x, var, nrm, sg = t(w.x), t(w.var), t(w.normals), t(w.sign)
+    xq64 = t(w.xq.astype(np.float64))
+    m.fit(x, var, nrm)
+    fit_ms = _timed(torch, lambda: m.fit(x, var, nrm), 10)
+    q_ms = _timed(torch, lambda: m.query(xq64, sg, f64=True), 10)
+    res["plane2d_fp64"] = {"workload": "10x10 m box + 20 circles, 2,000 samples, 1 m cells; 128^2 grid queries; "
+                                       "plain FP64 path", "fit_us": 1e3 * fit_ms, "query_us": 1e3 * q_ms,
+                           "queries_per_s": len(w.xq) / (q_ms * 1e-3)}
+    del m
+    # differentiation: 2,097,152 trajectory queries, forward sdf + grad and the adjoint (model fitted once)
+    w = scenes.workload("traj3d")
+    m = ksdf.KernelSDF(w.params)
+    x, var, nrm, xq = t(w.x), t(w.var), t(w.normals), t(w.xq)
+    m.fit(x, var, nrm)
+    Q = len(w.xq)
+    d_sdf = torch.ones(Q, device=dev)
+    d_grad = torch.zeros((Q, 3), device=dev)
+
+    def fb():
+        o = m.query(xq, None, ksdf.OUT_SDF | ksdf.OUT_GRAD | ksdf.OUT_WINNER | ksdf.OUT_FLAGS)
+        m.backward(xq, o["winner"], d_sdf, d_grad)
+
+    ms = _timed(torch, fb, 10)
+    res["traj3d_adjoint"] = {"workload": "room scene, 4,096 trajectories x 64 waypoints x 8 spheres = 2,097,152 "
+                                         "queries; sdf + grad forward and adjoint to queries and samples",
+                             "ms_per_step": ms, "queries_per_s": Q / (ms * 1e-3)}
+    del m, d_sdf, d_grad
+    # scale: 2M samples, 256^3 grid; mixed path vs plain FP64 path on the same inputs
+    w = scenes.workload("scale3d")
+    m = ksdf.KernelSDF(w.params)
+    x, var, nrm, xq = t(w.x), t(w.var), t(w.normals), t(w.xq)
+    m.fit(x, var, nrm)
+    fit_ms = _timed(torch, lambda: m.fit(x, var, nrm), 3, warmup=1)
+    q_ms = _timed(torch, lambda: m.query(xq), 3, warmup=1)
+    xq64 = xq.double()
+    q64_ms = _timed(torch, lambda: m.query(xq64, f64=True), 1, warmup=1)
+    G, M = ksdf.ksdf_model_size(m.h)
+    res["scale3d_mixed"] = {"workload": "50x50x10 m, 1,000 primitives, 2,000,000 samples, 0.5 m cells (n_max 512); "
+                                        "256^3 = 16,777,216 grid queries", "cells": int(G), "fit_ms": fit_ms,
+                            "query_ms": q_ms, "queries_per_s": len(w.xq) / (q_ms * 1e-3),
+                            "plain_fp64_query_ms": q64_ms, "speedup_vs_plain_fp64": q64_ms / q_ms}
+    del m, xq64
+    # streaming: LiDAR frames of a city block; frame 0 fits, every later frame appends its hits (ksdf_update:
+    # refit of the touched cells) and answers 1M queries around the pose
+    city = scenes.make_city()
+    m = ksdf.KernelSDF(city.params)
+    frames = []
+    n_frames = 6
+    S = 0
+    for f in range(n_frames):
+        hx, hv, hn = city.scan(f)
+        xq = t(city.queries(f, 1_000_000))
+        hx, hv, hn = t(hx), t(hv), t(hn)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        if f == 0:
+            m.fit(hx, hv, hn)
+            nref = int(ksdf.ksdf_model_size(m.h)[0])
+        else:
+            nref = m.update(hx, hv, hn)
+        e[1].record()
+        m.query(xq)
+        e[2].record()
+        torch.cuda.synchronize()
+        S += int(hx.shape[0])
+        frames.append({"hits": int(hx.shape[0]), "samples": S, "cells_refit": nref,
+                       "cells": int(ksdf.ksdf_model_size(m.h)[0]), "refit_ms": e[0].elapsed_time(e[1]),
+                       "query_ms": e[1].elapsed_time(e[2])})
+    upd = frames[1:]
+    tot = sum(fr["refit_ms"] + fr["query_ms"] for fr in upd)
+    res["city_stream"] = {"workload": "100x100 m city block, 96 boxes kept off the path, 64x2048 LiDAR scans "
+                                      "(~125k hits per frame), 1M queries per frame in the 40x40x6 m box around the "
+                                      "pose; the front-end occupancy update is out of scope",
+                          "frames": frames, "queries_per_s_incl_refit": 1e6 * len(upd) / (tot * 1e-3)}
+    del m
+    return res
 
 
 def main():
@@ -481,6 +585,9 @@ def main():
         "wall_s": wall1 - wall0,
         "step_ms_min_median_max": [float(step_ms.min()), float(np.median(step_ms)), float(step_ms.max())],
     }
+    if not args.no_others and world == 1:
+        del model
+        line["other_configs"] = other_configs(torch, dev, ksdf)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

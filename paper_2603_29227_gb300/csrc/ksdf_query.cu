@@ -188,6 +188,51 @@ __device__ inline void topk_insert(long long* D, uint64_t* Kk, int* Gg, int& n, 
 
 constexpr int kCandWarps = 8;
 
+// points of the Chebyshev shell of radius R around the origin (the cube's surface only): 24 R^2 + 2 in 3D
+// (faces z = +-R; y = +-R with |z| < R; x = +-R with |y|, |z| < R), 8 R in 2D, 1 for R = 0
+__device__ __forceinline__ int shell_size(int R, int dim) {
+  if (R == 0) return 1;
+  return dim == 3 ? 24 * R * R + 2 : 8 * R;
+}
+__device__ __forceinline__ void shell_point(int t, int R, int dim, int& dx, int& dy, int& dz) {
+  dz = 0;
+  if (R == 0) {
+    dx = dy = 0;
+    return;
+  }
+  const int side = 2 * R + 1, in = side - 2;
+  if (dim == 2) {
+    if (t < 2 * side) {  // rows y = -R, +R
+      dy = t < side ? -R : R;
+      dx = (t < side ? t : t - side) - R;
+    } else {  // columns x = -R, +R with |y| < R
+      const int u = t - 2 * side;
+      dx = u < in ? -R : R;
+      dy = (u < in ? u : u - in) - R + 1;
+    }
+    return;
+  }
+  const int f0 = 2 * side * side, f1 = f0 + 2 * side * in;
+  if (t < f0) {  // z = -R, +R: (x, y) over the full square
+    const int u = t < side * side ? t : t - side * side;
+    dz = t < side * side ? -R : R;
+    dy = u / side - R;
+    dx = u - (u / side) * side - R;
+  } else if (t < f1) {  // y = -R, +R: x over [-R, R], z over (-R, R)
+    const int u0 = t - f0, half = side * in;
+    const int u = u0 < half ? u0 : u0 - half;
+    dy = u0 < half ? -R : R;
+    dz = u / side - R + 1;
+    dx = u - (u / side) * side - R;
+  } else {  // x = -R, +R: y and z over (-R, R)
+    const int u0 = t - f1, half = in * in;
+    const int u = u0 < half ? u0 : u0 - half;
+    dx = u0 < half ? -R : R;
+    dz = u / in - R + 1;
+    dy = u - (u / in) * in - R + 1;
+  }
+}
+
 __global__ void __launch_bounds__(32 * kCandWarps)
     k_candidates(const uint64_t* bin_key, const int64_t* n_bins_dev, int64_t n_bins_host, CandCtx cc, int32_t* cand,
                  int32_t* ncand) {
@@ -209,23 +254,27 @@ __global__ void __launch_bounds__(32 * kCandWarps)
     __syncwarp();
     int rstop = 0;  // Chebyshev radius beyond which no cell exists
     for (int j = 0; j < 3; ++j) rstop = max(rstop, max(abs(bc[j] - cc.bb_lo[j]), abs(bc[j] - cc.bb_hi[j])));
-    bool done = false;
-    int R = 0;
-    for (; R <= min(rstop, kRingMax) && !done; ++R) {
-      const int side = 2 * R + 1;
-      const int64_t total = cc.dim == 3 ? (int64_t)side * side * side : (int64_t)side * side;
-      for (int64_t t0 = 0; t0 < total; t0 += 32) {
-        int64_t t = t0 + lane;
+    bool done = false, brute = false;
+    int64_t seen = 0;  // shell points visited so far
+    for (int R = 0; R <= rstop && !done; ++R) {
+      const int total = shell_size(R, cc.dim);
+      // once the rings would visit more points than there are cells, one pass over all cells is cheaper (and
+      // gives the same list: both are the exact top-K by (D, key))
+      if (R > kRingMax || seen + total > cc.G) {
+        brute = true;
+        break;
+      }
+      seen += total;
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
         bool found = false;
         long long d = 0;
         uint64_t key = 0;
         int g = -1;
         if (t < total) {
-          int dx = (int)(t % side) - R;
-          int64_t r = t / side;
-          int dy = (int)(r % side) - R;
-          int dz = cc.dim == 3 ? (int)(r / side) - R : 0;
-          if (max(abs(dx), max(abs(dy), abs(dz))) == R) {
+          int dx, dy, dz;
+          shell_point(t, R, cc.dim, dx, dy, dz);
+          {
             int64_t nx = (int64_t)bx + dx, ny = (int64_t)by + dy, nz = (int64_t)bz + dz;
             if (nx >= -kBias && nx < kBias && ny >= -kBias && ny < kBias && nz >= -kBias && nz < kBias) {
               key = pack_key(nx, ny, nz);
@@ -258,8 +307,8 @@ __global__ void __launch_bounds__(32 * kCandWarps)
       // every unseen cell has D >= (R+1)^2
       if (sN[w] >= K && sD[w][K - 1] < (long long)(R + 1) * (R + 1)) done = true;
     }
-    if (!done && rstop > kRingMax) {
-      // brute force over all cells (rare: bins far from every cell)
+    if (brute) {
+      // every cell (bins far from the nearest cells, or few cells)
       if (lane == 0) sN[w] = 0;
       __syncwarp();
       for (int64_t g0 = 0; g0 < cc.G; g0 += 32) {

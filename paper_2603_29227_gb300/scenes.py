@@ -20,6 +20,10 @@ Recipes (numpy PCG64, one seed per workload):
             0.5 m cells, n_max 512; queries on a 256^3 grid over the bounding box.
   traj3d    "differentiation": the room3d scene; 4,096 cubic Bezier trajectories x 64 waypoints x 8
             collision-sphere centres (corners of a 0.3 m cube around each waypoint) = 2,097,152 queries.
+  city      "streaming": a 100 x 100 m ground with 200 boxes (footprints U[4,20] m, heights U[3,30] m), a
+            64 x 2048 LiDAR-like scanner (elevation -25..+15 deg, 100 m range, range noise 0.02 m, sigma_i =
+            0.02 m) at 1.8 m on a smooth closed 100-pose path; per frame 1,000,000 queries in the 40 x 40 m
+            square around the pose, 0..6 m high; normals from the analytic scene (sign stand-in).
 Per-sample variance fed to the GP: sigma_i^2 = (sigma_noise * U[0.5, 2])^2, standing in for the
 front-end's per-point uncertainty.  Normals point from the obstacle into free space.  Samples that fall
 inside another obstacle (or outside the room) are rejected and redrawn.
@@ -30,7 +34,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["Scene", "make_plane2d", "make_room3d", "make_scale3d", "Workload", "workload", "WORKLOADS"]
+__all__ = ["Scene", "make_plane2d", "make_room3d", "make_scale3d", "Workload", "workload", "WORKLOADS", "City",
+           "make_city"]
 
 
 @dataclass
@@ -297,3 +302,94 @@ def workload(name: str, seed: int | None = None, n_samples: int | None = None, n
 
 
 WORKLOADS = ("plane2d", "room3d", "traj3d", "scale3d")
+
+
+# ---------------------------------------------------------------------------------------------------------
+# streaming: a city block scanned by a LiDAR-like sensor along a closed path
+
+@dataclass
+class City:
+    """A 100 x 100 m ground plane with axis-aligned boxes (buildings), a smooth closed sensor path at 1.8 m and
+    a 64-beam (elevation -25..+15 deg) x 2048-azimuth range scanner (max range 100 m, range noise 0.02 m)."""
+
+    box_lo: np.ndarray
+    box_hi: np.ndarray
+    poses: np.ndarray   # F x 3 sensor positions
+    params: dict
+    seed: int
+    sigma: float = 0.02
+    max_range: float = 100.0
+    n_beams: int = 64
+    n_az: int = 2048
+
+    def scan(self, f: int):
+        """Hits of frame f: (x S x 3 float64, var S float32, normals S x 3 float32), nearest surface per ray
+        (ground z = 0 or a box face), range noise along the ray; rays without a hit are dropped."""
+        rng = np.random.default_rng(self.seed * 1000 + 17 + f)
+        el = np.radians(np.linspace(-25.0, 15.0, self.n_beams))
+        az = np.arange(self.n_az) * (2.0 * np.pi / self.n_az) + rng.uniform(0.0, 2.0 * np.pi / self.n_az)
+        ce, se = np.cos(el)[:, None], np.sin(el)[:, None]
+        d = np.stack([(ce * np.cos(az)).ravel(), (ce * np.sin(az)).ravel(), np.repeat(se, self.n_az, axis=1).ravel()],
+                     axis=1)
+        o = self.poses[f]
+        R = d.shape[0]
+        t_hit = np.full(R, np.inf)
+        nrm = np.zeros((R, 3))
+        down = d[:, 2] < 0
+        tg = np.where(down, -o[2] / np.where(down, d[:, 2], -1.0), np.inf)
+        t_hit = np.minimum(t_hit, tg)
+        nrm[np.isfinite(tg)] = (0.0, 0.0, 1.0)
+        inv = 1.0 / np.where(np.abs(d) < 1e-12, 1e-12, d)
+        for b0 in range(0, len(self.box_lo), 16):
+            lo, hi = self.box_lo[b0:b0 + 16], self.box_hi[b0:b0 + 16]  # B x 3
+            t1 = (lo[None, :, :] - o) * inv[:, None, :]
+            t2 = (hi[None, :, :] - o) * inv[:, None, :]
+            tn3 = np.minimum(t1, t2)
+            tnear = tn3.max(axis=2)
+            tfar = np.maximum(t1, t2).min(axis=2)
+            hit = (tnear <= tfar) & (tnear > 1e-6)
+            tnear = np.where(hit, tnear, np.inf)
+            j = np.argmin(tnear, axis=1)
+            tb = tnear[np.arange(R), j]
+            better = tb < t_hit
+            if np.any(better):
+                ax = np.argmax(tn3[np.arange(R), j], axis=1)  # entry face
+                nb = np.zeros((R, 3))
+                nb[np.arange(R), ax] = -np.sign(d[np.arange(R), ax])
+                t_hit = np.where(better, tb, t_hit)
+                nrm[better] = nb[better]
+        ok = t_hit < self.max_range
+        t = t_hit[ok] + rng.normal(0.0, self.sigma, size=int(ok.sum()))
+        x = o + t[:, None] * d[ok]
+        var = np.full(x.shape[0], self.sigma ** 2, dtype=np.float32)
+        return np.ascontiguousarray(x), var, np.ascontiguousarray(nrm[ok], dtype=np.float32)
+
+    def queries(self, f: int, Q: int):
+        """Q points uniform in the 40 x 40 m square around the pose, 0..6 m above the ground."""
+        rng = np.random.default_rng(self.seed * 1000 + 911 + f)
+        o = self.poses[f]
+        lo = np.array([o[0] - 20.0, o[1] - 20.0, 0.0])
+        hi = np.array([o[0] + 20.0, o[1] + 20.0, 6.0])
+        return np.ascontiguousarray(lo + rng.random((Q, 3)) * (hi - lo), dtype=np.float32)
+
+
+def make_city(seed: int = 3, n_boxes: int = 200, n_poses: int = 100, size: float = 100.0) -> City:
+    """Boxes with footprints U[4, 20] m and heights U[3, 30] m; the path is a seeded smooth closed curve around
+    the block centre (radius 30 m with low-frequency wobble); boxes within 4 m of the path are removed."""
+    rng = np.random.default_rng(seed)
+    s = np.linspace(0.0, 2.0 * np.pi, n_poses, endpoint=False)
+    a = rng.normal(0.0, 3.0, size=(3, 2))
+    r = 30.0 + a[0, 0] * np.sin(s) + a[0, 1] * np.cos(2 * s) + a[1, 0] * np.sin(3 * s)
+    poses = np.stack([size / 2 + r * np.cos(s), size / 2 + r * np.sin(s), np.full(n_poses, 1.8)], axis=1)
+    fp = rng.uniform(4.0, 20.0, size=(n_boxes, 2))
+    h = rng.uniform(3.0, 30.0, size=n_boxes)
+    lo_xy = rng.uniform(0.0, 1.0, size=(n_boxes, 2)) * (size - fp)
+    lo = np.concatenate([lo_xy, np.zeros((n_boxes, 1))], axis=1)
+    hi = np.concatenate([lo_xy + fp, h[:, None]], axis=1)
+    # distance from each pose to each box footprint; keep boxes at least 4 m from the path
+    dx = np.maximum(np.maximum(lo[None, :, 0] - poses[:, None, 0], poses[:, None, 0] - hi[None, :, 0]), 0.0)
+    dy = np.maximum(np.maximum(lo[None, :, 1] - poses[:, None, 1], poses[:, None, 1] - hi[None, :, 1]), 0.0)
+    keep = np.min(np.hypot(dx, dy), axis=0) > 4.0
+    params = dict(dim=3, origin=(0.0, 0.0, 0.0), cell=0.5, margin=0.1, n_max=256, k_cand=8, **{"lambda": 300.0},
+                  softmin_alpha=300.0, sign_mode=1)
+    return City(box_lo=lo[keep], box_hi=hi[keep], poses=poses, params=params, seed=seed)
