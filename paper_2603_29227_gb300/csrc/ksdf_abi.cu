@@ -221,20 +221,20 @@ ksdf_status ksdf_create(const ksdf_params* params, void* stream, ksdf_ctx** out)
   return KSDF_OK;
 }
 
+static void release_model(Model& m) {
+  DevBuf* bufs[] = {&m.key,   &m.status, &m.n,      &m.ts_off, &m.chol_off, &m.linv_off, &m.hkeys,
+                    &m.hvals, &m.cell_order, &m.mf4, &m.md4,    &m.mvar,     &m.mnrm,     &m.mgid,
+                    &m.mpad,  &m.chol64, &m.linv32,  &m.x,      &m.ltc_off,  &m.ltc,      &m.var_all,
+                    &m.nrm_all, &m.bk_off, &m.bk_cells};
+  for (DevBuf* b : bufs) release(*b);
+}
+
 ksdf_status ksdf_destroy(ksdf_ctx* c) {
   if (!c) return KSDF_ERR_ARG;
   cudaStreamSynchronize(c->stream);
-  Model& m = c->m;
-  DevBuf* bufs[] = {&m.key,  &m.status, &m.n,    &m.ts_off, &m.chol_off, &m.linv_off, &m.hkeys,
-                    &m.hvals, &m.cell_order, &m.mf4, &m.md4, &m.mvar,   &m.mnrm,     &m.mgid,     &m.mpad,
-                    &m.chol64, &m.linv32, &m.x,   &m.ltc_off,   &m.ltc,      &m.var_all, &m.nrm_all,
-                    &c->status_word};
-  for (DevBuf* b : bufs) release(*b);
-  Model& mp = c->m_prev;
-  DevBuf* pbufs[] = {&mp.key,  &mp.status, &mp.n,      &mp.ts_off, &mp.chol_off, &mp.linv_off, &mp.hkeys,
-                     &mp.hvals, &mp.cell_order, &mp.mf4, &mp.md4, &mp.mvar,   &mp.mnrm,     &mp.mgid,
-                     &mp.mpad,  &mp.chol64, &mp.linv32, &mp.x, &mp.ltc_off, &mp.ltc, &mp.var_all, &mp.nrm_all};
-  for (DevBuf* b : pbufs) release(*b);
+  release_model(c->m);
+  release_model(c->m_prev);
+  release(c->status_word);
   for (auto& b : c->ws) release(b);
   for (auto& b : c->stage) release(b);
   for (auto& p : c->pending) {

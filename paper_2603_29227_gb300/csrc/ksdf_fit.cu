@@ -769,6 +769,33 @@ static cudaError_t launch_persistent(ksdf_ctx* c, K kern, int team, const Args& 
   return cudaSuccess;
 }
 
+// brick of an OK cell (index (bz nby + by) nbx + bx over the cell bounding box); -1 for other cells
+__device__ __forceinline__ int64_t cell_brick(uint64_t key, int lx, int ly, int lz, int nbx, int nby) {
+  int cx, cy, cz;
+  unpack_key(key, cx, cy, cz);
+  return ((int64_t)((cz - lz) >> kBrickShift) * nby + ((cy - ly) >> kBrickShift)) * nbx + ((cx - lx) >> kBrickShift);
+}
+
+// per-brick counts of OK cells, and each cell's rank within its brick
+__global__ void k_brick_count(const uint64_t* cell_key, const int32_t* status, int64_t G, int lx, int ly, int lz,
+                              int nbx, int nby, int64_t* bcnt, int32_t* rank) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  if (status[g] != KSDF_CELL_OK) {
+    rank[g] = -1;
+    return;
+  }
+  const int64_t b = cell_brick(cell_key[g], lx, ly, lz, nbx, nby);
+  rank[g] = (int32_t)atomicAdd((unsigned long long*)&bcnt[b], 1ull);
+}
+
+__global__ void k_brick_fill(const uint64_t* cell_key, const int32_t* rank, int64_t G, int lx, int ly, int lz,
+                             int nbx, int nby, const int64_t* boff, int32_t* cells) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G || rank[g] < 0) return;
+  cells[boff[cell_brick(cell_key[g], lx, ly, lz, nbx, nby)] + rank[g]] = (int32_t)g;
+}
+
 ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const float* nrm, int64_t S, const Model* prev,
                       int64_t* n_refit) {
   cudaStream_t st = c->stream;
@@ -1080,6 +1107,31 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     ca.mf4 = ptr<float4>(m.mf4);
     ca.status = ptr<int32_t>(m.status);
     launch(k_copy_fit, (unsigned)std::min<int64_t>(G, 8 * c->num_sms), 256, 0, st, ca);
+  }
+  // bricks over the cell bounding box for the candidate search (OK cells only; statuses are final here)
+  {
+    int64_t nbk[3];
+    for (int j = 0; j < 3; ++j) {
+      nbk[j] = (((int64_t)hb[3 + j] - hb[j]) >> kBrickShift) + 1;
+      m.bk_lo[j] = hb[j];
+    }
+    const int64_t nb = nbk[0] * nbk[1] * nbk[2];
+    m.nbricks = 0;
+    if (nb <= 4 * G + 4096) {
+      for (int j = 0; j < 3; ++j) m.bk_n[j] = (int)nbk[j];
+      m.nbricks = nb;
+      KSDF_CUDA(c, ensure(m.bk_off, sizeof(int64_t) * (nb + 1)));
+      KSDF_CUDA(c, ensure(m.bk_cells, sizeof(int32_t) * G));
+      KSDF_CUDA(c, ensure(c->ws[WS_BRICK], sizeof(int32_t) * G));
+      int64_t* boff = ptr<int64_t>(m.bk_off);
+      int32_t* rank = ptr<int32_t>(c->ws[WS_BRICK]);
+      KSDF_CUDA(c, cudaMemsetAsync(boff, 0, sizeof(int64_t) * (nb + 1), st));
+      launch(k_brick_count, ceil_div(G, 256), 256, 0, st, ptr<uint64_t>(m.key), ptr<int32_t>(m.status), G, hb[0],
+             hb[1], hb[2], m.bk_n[0], m.bk_n[1], boff, rank);
+      KSDF_CUDA(c, scan_i64(boff, boff, nb, boff + nb, c->ws[WS_SCAN], st));
+      launch(k_brick_fill, ceil_div(G, 256), 256, 0, st, ptr<uint64_t>(m.key), rank, G, hb[0], hb[1], hb[2],
+             m.bk_n[0], m.bk_n[1], boff, ptr<int32_t>(m.bk_cells));
+    }
   }
   KSDF_CUDA(c, cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st));
   KSDF_CUDA(c, cudaStreamSynchronize(st));

@@ -19,6 +19,7 @@ constexpr int kMaxPre = 8192;           // collection-box members before the cap
 constexpr int kMaxK = 32;               // candidate list length limit
 constexpr int kMaxNmax = 512;           // training-set cap limit
 constexpr uint64_t kEmptyKey = ~0ull;   // empty hash slot
+constexpr int kBrickShift = 3;          // bricks of 8 cells per axis
 constexpr unsigned kWaitLimit = 1u << 26;  // bounded spin on an mbarrier (~seconds)
 
 // device status word bits (ksdf_sync_status)
@@ -142,6 +143,13 @@ struct Model {
                    // contraction, rows (N dim) padded to Np = 16 ceil(N/16), columns (K dim) to Kp = 8 ceil(N/8),
                    // in K-quads: element (j, i) at (i / 4) Np 4 + j 4 + i % 4 (zero outside the lower triangle);
                    // TF32 hi = rna(x) at ltc_off, lo = rna(x - hi) ltc_total floats further
+  // bricks of 2^kBrickShift cells per axis over the cell bounding box, each listing its OK cells (the
+  // coarse level of the candidate search for query bins far from the nearest cells); nbricks = 0 when the
+  // box is too sparse for a dense brick grid
+  DevBuf bk_off;    // int64 (nbricks + 1), brick index (bz nby + by) nbx + bx
+  DevBuf bk_cells;  // int32 cell ids grouped by brick
+  int bk_lo[3] = {0, 0, 0}, bk_n[3] = {0, 0, 0};
+  int64_t nbricks = 0;
 };
 
 }  // namespace ksdf
@@ -168,7 +176,7 @@ struct ksdf_ctx {
   std::vector<ksdf::FitClassCfg> fit_cls;  // the fit's size classes (empty: the default table); ksdf_autotune
   // workspaces
   ksdf::DevBuf status_word;       // uint32 device status
-  ksdf::DevBuf ws[29];            // general workspaces (grow only), indexed by role
+  ksdf::DevBuf ws[30];            // general workspaces (grow only), indexed by role
   ksdf::DevBuf stage[12];         // staging of host arrays
   int64_t reserved_q = 0, reserved_s = 0;
   int bb[6] = {0, 0, 0, 0, 0, 0};  // bounding box of the cells: min xyz, max xyz
@@ -270,7 +278,8 @@ enum WsRole {
   WS_TOUCH = 25,  // update: per cell touched flag and previous id
   WS_UX = 26,     // update: the union of old and new samples (positions, variances, normals)
   WS_UV = 27,
-  WS_UN = 28
+  WS_UN = 28,
+  WS_BRICK = 29   // brick build: rank of each cell within its brick
 };
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }

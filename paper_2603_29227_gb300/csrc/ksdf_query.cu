@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kTA = 128;   // phase A threads (one query each)
 constexpr int kTB64 = 32;  // phase B threads, FP64 path
-constexpr int kRingMax = 16;
+constexpr int kRingCells = 4;  // cell shells of the candidate search before it moves to bricks
 constexpr float kLog2e = 1.4426950408889634f;
 
 // ---------------------------------------------------------------------------------------------
@@ -165,6 +165,10 @@ struct CandCtx {
   const uint64_t* cell_key;
   int64_t G;
   int bb_lo[3], bb_hi[3];  // bounding box of all cells
+  const int64_t* bk_off;   // bricks: CSR offsets (nbricks + 1) into bk_cells, 0 bricks when absent
+  const int32_t* bk_cells;
+  int bk_lo[3], bk_n[3];
+  int64_t nbricks;
   int K, dim;
 };
 
@@ -233,6 +237,54 @@ __device__ __forceinline__ void shell_point(int t, int R, int dim, int& dx, int&
   }
 }
 
+// each lane offers (d, key, g) when `found`; lane 0 merges the offers into the warp's sorted top-K list
+struct WarpTopK {
+  long long* D;
+  uint64_t* Kk;
+  int* Gg;
+  int* n;
+  long long* eD;
+  uint64_t* eK;
+  int* eG;
+  int K;
+  // whether (d, key) would enter the current list
+  __device__ __forceinline__ bool admits(long long d, uint64_t key) const {
+    const int c = *n;
+    return c < K || d < D[K - 1] || (d == D[K - 1] && key < Kk[K - 1]);
+  }
+  __device__ __forceinline__ void offer(bool found, long long d, uint64_t key, int g, int lane) const {
+    unsigned mask = __ballot_sync(0xffffffffu, found);
+    if (found) {
+      eD[lane] = d;
+      eK[lane] = key;
+      eG[lane] = g;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      int c = *n;
+      while (mask) {
+        const int l = __ffs(mask) - 1;
+        mask &= mask - 1;
+        topk_insert(D, Kk, Gg, c, K, eD[l], eK[l], eG[l]);
+      }
+      *n = c;
+    }
+    __syncwarp();
+  }
+  // every cell not offered yet has D >= lb2: the list is final
+  __device__ __forceinline__ bool final_below(long long lb2) const { return *n >= K && D[K - 1] < lb2; }
+};
+
+// The K valid cells nearest to a bin on the integer lattice, ordered by (squared distance D, key).  Three
+// exact searches, cheapest first for the bin at hand, all giving the same list:
+//   cell rings: Chebyshev shells R = 0, 1, ... of cells around the bin, looked up in the cell hash table,
+//     until the K-th distance is below (R+1)^2 (bins near the surface: a few shells);
+//   bricks: beyond kRingCells shells, Chebyshev shells of 8^3-cell bricks; the cells of a brick are
+//     offered unless the rings already visited them or the brick's box is farther than the K-th
+//     candidate; after brick shell Rb every unvisited cell is at least 8 Rb + 1 + (offset in the brick)
+//     away along some axis;
+//   all cells: one pass over every cell, when the shells would visit more lattice points than there are
+//     cells (or bricks).
 __global__ void __launch_bounds__(32 * kCandWarps)
     k_candidates(const uint64_t* bin_key, const int64_t* n_bins_dev, int64_t n_bins_host, CandCtx cc, int32_t* cand,
                  int32_t* ncand) {
@@ -246,6 +298,7 @@ __global__ void __launch_bounds__(32 * kCandWarps)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nb = n_bins_dev ? *n_bins_dev : n_bins_host;
   const int K = cc.K;
+  const WarpTopK top{sD[w], sK[w], sG[w], &sN[w], eD[w], eK[w], eG[w], K};
   for (int64_t b = (int64_t)blockIdx.x * kCandWarps + w; b < nb; b += (int64_t)gridDim.x * kCandWarps) {
     int bx, by, bz;
     unpack_key(bin_key[b], bx, by, bz);
@@ -254,14 +307,13 @@ __global__ void __launch_bounds__(32 * kCandWarps)
     __syncwarp();
     int rstop = 0;  // Chebyshev radius beyond which no cell exists
     for (int j = 0; j < 3; ++j) rstop = max(rstop, max(abs(bc[j] - cc.bb_lo[j]), abs(bc[j] - cc.bb_hi[j])));
-    bool done = false, brute = false;
-    int64_t seen = 0;  // shell points visited so far
-    for (int R = 0; R <= rstop && !done; ++R) {
+    bool done = false, far = false;
+    int Rdone = -1;    // cell shells 0..Rdone visited
+    int64_t seen = 0;  // lattice points visited so far
+    for (int R = 0; R <= rstop; ++R) {
       const int total = shell_size(R, cc.dim);
-      // once the rings would visit more points than there are cells, one pass over all cells is cheaper (and
-      // gives the same list: both are the exact top-K by (D, key))
-      if (R > kRingMax || seen + total > cc.G) {
-        brute = true;
+      if (R > kRingCells || seen + total > cc.G) {
+        far = true;
         break;
       }
       seen += total;
@@ -274,45 +326,105 @@ __global__ void __launch_bounds__(32 * kCandWarps)
         if (t < total) {
           int dx, dy, dz;
           shell_point(t, R, cc.dim, dx, dy, dz);
-          {
-            int64_t nx = (int64_t)bx + dx, ny = (int64_t)by + dy, nz = (int64_t)bz + dz;
-            if (nx >= -kBias && nx < kBias && ny >= -kBias && ny < kBias && nz >= -kBias && nz < kBias) {
-              key = pack_key(nx, ny, nz);
-              g = hash_find(cc.hk, cc.hv, cc.hcap, key);
-              if (g >= 0 && cc.status[g] == KSDF_CELL_OK) {
-                found = true;
-                d = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
-              }
+          const int64_t nx = (int64_t)bx + dx, ny = (int64_t)by + dy, nz = (int64_t)bz + dz;
+          if (nx >= -kBias && nx < kBias && ny >= -kBias && ny < kBias && nz >= -kBias && nz < kBias) {
+            key = pack_key(nx, ny, nz);
+            g = hash_find(cc.hk, cc.hv, cc.hcap, key);
+            if (g >= 0 && cc.status[g] == KSDF_CELL_OK) {
+              found = true;
+              d = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
             }
           }
         }
-        unsigned mask = __ballot_sync(0xffffffffu, found);
-        if (found) {
-          eD[w][lane] = d;
-          eK[w][lane] = key;
-          eG[w][lane] = g;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          int n = sN[w];
-          while (mask) {
-            int l = __ffs(mask) - 1;
-            mask &= mask - 1;
-            topk_insert(sD[w], sK[w], sG[w], n, K, eD[w][l], eK[w][l], eG[w][l]);
-          }
-          sN[w] = n;
-        }
-        __syncwarp();
+        top.offer(found, d, key, g, lane);
       }
-      // every unseen cell has D >= (R+1)^2
-      if (sN[w] >= K && sD[w][K - 1] < (long long)(R + 1) * (R + 1)) done = true;
+      Rdone = R;
+      if (top.final_below((long long)(R + 1) * (R + 1))) {
+        done = true;
+        break;
+      }
+    }
+    bool brute = far && !done;
+    if (brute && cc.nbricks > 0) {
+      brute = false;
+      int B[3], o[3], rbstop = 0;
+      for (int j = 0; j < 3; ++j) {
+        const int u = bc[j] - cc.bk_lo[j];
+        B[j] = u >> kBrickShift;  // floor (arithmetic shift)
+        o[j] = u - (B[j] << kBrickShift);
+        rbstop = max(rbstop, max(abs(B[j]), abs(B[j] - (cc.bk_n[j] - 1))));
+      }
+      int64_t seenb = 0;
+      for (int Rb = 0; Rb <= rbstop; ++Rb) {
+        const int total = shell_size(Rb, cc.dim);
+        if (seenb + total > cc.nbricks) {
+          brute = true;
+          break;
+        }
+        seenb += total;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+          const int t = t0 + lane;
+          int64_t boff = 0;
+          int bcnt = 0;
+          if (t < total) {
+            int d3[3];
+            shell_point(t, Rb, cc.dim, d3[0], d3[1], d3[2]);
+            const int q0 = B[0] + d3[0], q1 = B[1] + d3[1], q2 = B[2] + d3[2];
+            if (q0 >= 0 && q0 < cc.bk_n[0] && q1 >= 0 && q1 < cc.bk_n[1] && q2 >= 0 && q2 < cc.bk_n[2]) {
+              const int64_t bi = ((int64_t)q2 * cc.bk_n[1] + q1) * cc.bk_n[0] + q0;
+              boff = cc.bk_off[bi];
+              bcnt = (int)(cc.bk_off[bi + 1] - boff);
+              if (bcnt > 0) {
+                // squared lattice distance from the bin to the brick's box
+                const int q[3] = {q0, q1, q2};
+                long long dmin = 0;
+                for (int j = 0; j < 3; ++j) {
+                  const int lo = cc.bk_lo[j] + (q[j] << kBrickShift), hi = lo + (1 << kBrickShift) - 1;
+                  const long long gap = max(0, max(lo - bc[j], bc[j] - hi));
+                  dmin += gap * gap;
+                }
+                if (sN[w] >= K && dmin > sD[w][K - 1]) bcnt = 0;
+              }
+            }
+          }
+          unsigned bm = __ballot_sync(0xffffffffu, bcnt > 0);
+          while (bm) {
+            const int l = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const int64_t o0 = __shfl_sync(0xffffffffu, boff, l);
+            const int cl = __shfl_sync(0xffffffffu, bcnt, l);
+            for (int i0 = 0; i0 < cl; i0 += 32) {
+              const int i = i0 + lane;
+              bool found = false;
+              long long d = 0;
+              uint64_t key = 0;
+              int g = -1;
+              if (i < cl) {
+                g = cc.bk_cells[o0 + i];
+                key = cc.cell_key[g];
+                int cx, cy, cz;
+                unpack_key(key, cx, cy, cz);
+                const int dx = cx - bx, dy = cy - by, dz = cz - bz;
+                if (max(abs(dx), max(abs(dy), abs(dz))) > Rdone) {
+                  d = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+                  found = top.admits(d, key);
+                }
+              }
+              top.offer(found, d, key, g, lane);
+            }
+          }
+        }
+        int L = INT_MAX;
+        for (int j = 0; j < cc.dim; ++j)
+          L = min(L, min(o[j] + (Rb << kBrickShift) + 1, ((Rb + 1) << kBrickShift) - o[j]));
+        if (top.final_below((long long)L * L)) break;
+      }
     }
     if (brute) {
-      // every cell (bins far from the nearest cells, or few cells)
       if (lane == 0) sN[w] = 0;
       __syncwarp();
       for (int64_t g0 = 0; g0 < cc.G; g0 += 32) {
-        int64_t g = g0 + lane;
+        const int64_t g = g0 + lane;
         bool found = false;
         long long d = 0;
         uint64_t key = 0;
@@ -321,29 +433,11 @@ __global__ void __launch_bounds__(32 * kCandWarps)
           int cx, cy, cz;
           unpack_key(key, cx, cy, cz);
           d = (long long)(cx - bx) * (cx - bx) + (long long)(cy - by) * (cy - by) + (long long)(cz - bz) * (cz - bz);
-          int n = sN[w];
-          found = n < K || d < sD[w][K - 1] || (d == sD[w][K - 1] && key < sK[w][K - 1]);
+          found = top.admits(d, key);
         }
-        unsigned mask = __ballot_sync(0xffffffffu, found);
-        if (found) {
-          eD[w][lane] = d;
-          eK[w][lane] = key;
-          eG[w][lane] = (int)g;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          int n = sN[w];
-          while (mask) {
-            int l = __ffs(mask) - 1;
-            mask &= mask - 1;
-            topk_insert(sD[w], sK[w], sG[w], n, K, eD[w][l], eK[w][l], eG[w][l]);
-          }
-          sN[w] = n;
-        }
-        __syncwarp();
+        top.offer(found, d, key, (int)g, lane);
       }
     }
-    __syncwarp();
     const int n = sN[w];
     if (lane < K) cand[b * K + lane] = lane < n ? sG[w][lane] : -1;
     if (lane == 0) ncand[b] = n;
@@ -1386,7 +1480,12 @@ static CandCtx cand_ctx(ksdf_ctx* c) {
   for (int j = 0; j < 3; ++j) {
     cc.bb_lo[j] = c->bb[j];
     cc.bb_hi[j] = c->bb[3 + j];
+    cc.bk_lo[j] = m.bk_lo[j];
+    cc.bk_n[j] = m.bk_n[j];
   }
+  cc.bk_off = ptr<int64_t>(m.bk_off);
+  cc.bk_cells = ptr<int32_t>(m.bk_cells);
+  cc.nbricks = m.nbricks;
   cc.K = c->p.K;
   cc.dim = c->p.dim;
   return cc;

@@ -114,6 +114,27 @@ def test_candidate_lists_bit_exact(case):
     assert np.array_equal(keys, oracle.bin_keys(w.params, w.xq.astype(np.float64)))
 
 
+def test_candidate_lists_far_bins(case):
+    """Bins far from every cell: beyond the search's cell shells (its brick level), and far outside the
+    cells' box (its pass over all cells); bit-exact against the oracle's exhaustive search."""
+    name, w, ref, gm = case
+    p = w.params
+    dim, h = p["dim"], p["cell"]
+    lo, hi = w.x.min(0), w.x.max(0)
+    ext = hi - lo
+    rng = np.random.default_rng(7)
+    xq = np.concatenate([rng.uniform(lo - 0.5 * ext - 12 * h, hi + 0.5 * ext + 12 * h, size=(4000, dim)),
+                         rng.uniform(lo - 300 * h, hi + 300 * h, size=(500, dim))])
+    bins = np.unique(oracle.bin_keys(p, xq))
+    c0, n0 = ref.candidates(bins)
+    K = p["k_cand"]
+    c1 = np.empty((len(bins), K), np.int32)
+    n1 = np.empty(len(bins), np.int32)
+    ksdf.ksdf_candidates(gm.h, bins, len(bins), c1, n1)
+    assert np.array_equal(n0, n1), name
+    assert np.array_equal(c0, c1), name
+
+
 def test_query_mixed(case):
     name, w, ref, gm = case
     out = gpu_query(gm, w.xq, w.sign)
