@@ -140,6 +140,14 @@ ksdf_status ksdf_update(ksdf_ctx* ctx, const double* x_new, const float* var_new
 ksdf_status ksdf_autotune(ksdf_ctx* ctx, int* table, double* fit_ms);
 int ksdf_autotune_tables(void);
 
+/* Diagnostics: the scalar device routines of the fit (Sec. IV-B kernel matrix exp(-lambda r^2) and the
+ * Cholesky pivots), evaluated on n inputs x (float64, host or device) into y (float64, host or device) so
+ * that tests can hold them to their error bounds.  fn 0: 2^(-x / 2^16) from a binary64 argument; fn 1: the
+ * same from the 40-bit fixed-point argument floor(x 2^40) (both 0 <= x < 2^22); fn 2: 1 / sqrt(x) for a
+ * normal x > 0.  Inputs outside a routine's domain give NaN.  KSDF_ERR_ARG for an unknown fn or n < 0.
+ * Synchronises the stream. */
+ksdf_status ksdf_device_math(ksdf_ctx* ctx, int fn, const double* x, int64_t n, double* y);
+
 /* Mixed-precision query: Q points xq (Q x dim float32); sign (Q int8, +1/-1, may be NULL).  FP32 SIMT
  * arithmetic in cell-local coordinates for the mean (compensated sum), gradient and softmin variance; the
  * GP variance contraction K' L^{-T} on the tensor cores in TF32 split three ways (hi*hi + hi*lo + lo*hi,

@@ -318,6 +318,20 @@ ksdf_status ksdf_autotune(ksdf_ctx* c, int* table, double* fit_ms) {
 
 int ksdf_autotune_tables(void) { return fit_table_count(); }
 
+ksdf_status ksdf_device_math(ksdf_ctx* c, int fn, const double* x, int64_t n, double* y) {
+  if (!c || fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y))) return KSDF_ERR_ARG;
+  if (n == 0) return KSDF_OK;
+  const void* dx;
+  ksdf_status s;
+  if ((s = stage_in(c, 0, x, sizeof(double) * n, &dx))) return s;
+  OutStage o;
+  if ((s = stage_out(c, 1, y, sizeof(double) * n, false, &o))) return s;
+  if ((s = device_math(c, fn, static_cast<const double*>(dx), n, static_cast<double*>(o.dev)))) return s;
+  if ((s = finish_out(c, &o, 1))) return s;
+  KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return KSDF_OK;
+}
+
 ksdf_status ksdf_fit(ksdf_ctx* c, const double* x, const float* var, const float* normals, int64_t S) {
   if (!c) return KSDF_ERR_ARG;
   if (S <= 0 || !x) return set_err(c, KSDF_ERR_ARG, "ksdf_fit: need S > 0 samples");

@@ -162,6 +162,15 @@ __device__ __forceinline__ double fixed40_to_double(long long x) {
   return __longlong_as_double((long long)(neg | (ex << 52) | mant));
 }
 
+// 2^-m T1[a] T2[b] (1 + q) for n = 2^16 m + 2^8 a + b and the remainder r (|r| <= 1/2)
+__device__ __forceinline__ double exp2_neg_tail(unsigned long long n, double r) {
+  const double q = r * fma(r, kExpC2, -kExpC1);
+  const double t2 = __ldg(&kExpT2[n & 255]);
+  const double t1 = __ldg(&kExpT1[(n >> 8) & 255]);
+  const double v = t1 * fma(t2, q, t2);
+  return __longlong_as_double(__double_as_longlong(v) - (long long)((n >> 16) << 52));
+}
+
 // 2^(-e / 2^16) for 0 <= e < 2^22
 __device__ __forceinline__ double exp2_neg_q16(double e) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(e);
@@ -175,11 +184,21 @@ __device__ __forceinline__ double exp2_neg_q16(double e) {
     n = (F + (1ull << 39)) >> 40;
     r = fixed40_to_double((long long)(F - (n << 40)));
   }
-  const double q = r * fma(r, kExpC2, -kExpC1);
-  const double t2 = __ldg(&kExpT2[n & 255]);
-  const double t1 = __ldg(&kExpT1[(n >> 8) & 255]);
-  const double v = t1 * fma(t2, q, t2);
-  return __longlong_as_double(__double_as_longlong(v) - (long long)((n >> 16) << 52));
+  return exp2_neg_tail(n, r);
+}
+
+// the same for an argument given in fixed point, F = e 2^40 (0 <= e < 2^22): 4 FP64 operations in all
+__device__ __forceinline__ double exp2_neg_fixed40(unsigned long long F) {
+  const unsigned long long n = (F + (1ull << 39)) >> 40;
+  return exp2_neg_tail(n, fixed40_to_double((long long)(F - (n << 40))));
+}
+
+// floor((a - b)^2 / 2^40) for fixed-point values with |a - b| < 2^52, exactly, in integer arithmetic
+// (a 64 x 64 -> 128-bit square)
+__device__ __forceinline__ unsigned long long sqdiff40(long long a, long long b) {
+  const long long d = a - b;
+  const unsigned long long u = d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
+  return (__umul64hi(u, u) << 24) | ((u * u) >> 40);
 }
 
 // binary64 -> binary32, round to nearest even, values below FLT_MIN flushed to (signed) zero
@@ -206,17 +225,47 @@ __device__ __forceinline__ double f2d_bits(float v) {
                                           ((unsigned long long)(b & 0x7fffffu) << 29)));
 }
 
-// 1/sqrt(d) for finite d > 0 to about half an ulp: an FP32 seed on the mantissa scaled to [1, 4), then
-// one second-order correction y = y0 (1 + e/2 + 3 e^2 / 8), e = 1 - d y0^2 (5 FP64 operations; y0^2 is
-// exact in binary64, and the truncation 5 e^3 / 16 is below 2^-64)
+// 1/sqrt(d) for a normal d > 0 to about half an ulp, without FP64 instructions (each costs an SM as much
+// FP64 pipe time as 32 lanes of work, whatever the number of active lanes).  With d = 4^k d', d' in [1, 4):
+// an FP32 seed y0 = rsqrtf(d') (within 2 ulp, so |e| < 2^-21 below), then the second-order correction
+// y = y0 (1 + e/2 + 3 e^2 / 8), e = 1 - d' y0^2, whose truncation 5 e^3 / 16 is below 2^-64.  d' = D 2^-52
+// and y0 = Y 2^-25 are integers times powers of two, so e is formed exactly in 128-bit integer arithmetic
+// (e 2^76, truncated), the correction in fixed point, and the product is rounded to 53 bits.
 __device__ __forceinline__ double rsqrt_pivot(double d) {
-  const long long b = __double_as_longlong(d);
-  const int k = ((int)((b >> 52) & 0x7ff) - 1023) >> 1;  // d = 2^(2k) d', d' in [1, 4)
-  const double dp = __longlong_as_double(b - ((long long)(2 * k) << 52));
-  const float y0f = rsqrtf(d2f_bits(dp));
-  const double y0 = __longlong_as_double(__double_as_longlong(f2d_bits(y0f)) - ((long long)k << 52));
-  const double e = fma(-d, y0 * y0, 1.0);
-  return fma(y0, e * fma(e, 0.375, 0.5), y0);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int t = (int)((b >> 52) & 0x7ff) - 1023;
+  const int k = t >> 1, sh = t - 2 * k;  // d = 4^k d', d' = 2^sh 1.f
+  const unsigned long long frac = b & 0xFFFFFFFFFFFFFull;
+  const unsigned long long D = (frac | (1ull << 52)) << sh;
+  const double dp = __longlong_as_double((long long)(frac | ((unsigned long long)(1023 + sh) << 52)));
+  const unsigned yb = __float_as_uint(rsqrtf(d2f_bits(dp)));
+  const int ye = (int)((yb >> 23) & 0xffu) - 127;                                        // -2, -1 or 0
+  const unsigned long long Y = (unsigned long long)((yb & 0x7fffffu) | 0x800000u) << (ye + 2);  // y0 = Y 2^-25
+  const unsigned long long Y2 = Y * Y;
+  const unsigned long long plo = D * Y2, phi = __umul64hi(D, Y2);  // D Y^2 = d' y0^2 2^102
+  // e 2^102 = 2^102 - D Y^2 (128-bit), then E = e 2^76
+  const unsigned long long qlo = 0ull - plo, qhi = (1ull << 38) - phi - (plo != 0ull ? 1ull : 0ull);
+  const long long E = (long long)((qhi << 38) | (qlo >> 26));
+  const unsigned long long u = E < 0 ? (unsigned long long)(-E) : (unsigned long long)E;
+  const long long e2 = (long long)(__umul64hi(u, u) >> 12);  // e^2 2^76
+  const long long dl = (E >> 1) + ((3 * e2) >> 3);          // (e/2 + 3 e^2 / 8) 2^76
+  const unsigned long long w = dl < 0 ? (unsigned long long)(-dl) : (unsigned long long)dl;
+  unsigned long long zlo = Y * w, zhi = __umul64hi(Y, w);
+  if (dl < 0) {
+    zhi = ~zhi + (zlo == 0ull ? 1ull : 0ull);
+    zlo = 0ull - zlo;
+  }
+  zhi += Y << 12;  // Z = Y (2^76 + dl) = y 2^(101 + k), Z in (2^100, 2^102)
+  const int p = 63 - __clzll((long long)zhi) + 64;
+  const int s = p - 52;  // 48 or 49
+  unsigned long long mant = (zhi << (64 - s)) | (zlo >> s);
+  mant += (zlo >> (s - 1)) & 1ull;  // round half up
+  int ex = p - 101 - k;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++ex;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(ex + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 }  // namespace ksdf

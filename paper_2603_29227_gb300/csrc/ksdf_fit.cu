@@ -338,6 +338,7 @@ struct FitArgs {
   int np;           // largest N of this class
   double sc;        // sqrt(lambda 2^16 / ln2): coordinates scaled so that |s_i - s_j|^2 is exp2_neg_q16's argument
   float lamf;       // lambda in FP32 (the near/far screen)
+  bool fixed;       // scaled coordinates below 2^21: exact fixed-point squared distances (else binary64)
   int* counter;
   int* n_not_pd;
 };
@@ -352,6 +353,16 @@ __device__ __forceinline__ int tri_row(int64_t t) {
 
 constexpr int kB = 8;        // Cholesky panel width
 constexpr float kNearE = 36.f;  // lambda r^2 below this: FP64 entry; above: FP32 (value < 2.4e-16)
+
+// exp(-lambda r_ij^2) from the scaled coordinates: fixed point (exact squared distance) or binary64.  In
+// fixed-point mode the slots hold the same coordinates as 64-bit integers (s 2^40).
+__device__ __forceinline__ double near_entry(const double* s, const long long* sfix, bool fixed, int i, int j) {
+  if (fixed)
+    return exp2_neg_fixed40(sqdiff40(sfix[3 * i], sfix[3 * j]) + sqdiff40(sfix[3 * i + 1], sfix[3 * j + 1]) +
+                            sqdiff40(sfix[3 * i + 2], sfix[3 * j + 2]));
+  const double ex = s[3 * i] - s[3 * j], ey = s[3 * i + 1] - s[3 * j + 1], ez = s[3 * i + 2] - s[3 * j + 2];
+  return exp2_neg_q16(fma(ez, ez, fma(ey, ey, ex * ex)));
+}
 
 __device__ __forceinline__ bool pivot_ok(double d) {  // finite, positive and normal
   const long long b = __double_as_longlong(d);
@@ -378,7 +389,10 @@ __host__ __device__ inline int64_t fit_smem_doubles(int np, int warps, bool smem
 //   1. A = K + diag(sigma^2), augmented with a row of ones (the right-hand side of A alpha = 1).  Each
 //      off-diagonal entry is screened in FP32: lambda r^2 >= 36 gives a value below 2.4e-16 that FP32
 //      evaluates to far better than its absolute rounding; the others are queued per warp and evaluated
-//      32 at a time in FP64 (exp2_neg_q16 on coordinates pre-scaled by sqrt(lambda 2^16 / ln2)).
+//      32 at a time in FP64 (exp2_neg_q16 on coordinates pre-scaled by sqrt(lambda 2^16 / ln2)).  The
+//      scaled coordinates are held in fixed point with 40 fractional bits, so that the squared distance
+//      comes out of exact integer arithmetic as exp2_neg_fixed40's argument: 4 FP64 operations per entry
+//      instead of 10 (the rounding of s to 2^-41 moves an entry by below 1e-13 of its value).
 //   2. Right-looking Cholesky of the augmented matrix in panels of kB columns: warp 0 factors a panel
 //      (pivots by rsqrt_pivot, column scaling, updates inside the panel, lanes along the rows), then the
 //      team updates the trailing triangle in 2 x 2 register blocks over the panel depth (about three
@@ -393,6 +407,7 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = a.np;
   double* s = sm;
+  long long* sfix = reinterpret_cast<long long*>(s);  // the same slots, fixed point (a.fixed)
   double* cb = s + 3 * np;
   double* dinv = cb + 2 * (np + 1);
   float* xf = reinterpret_cast<float*>(dinv + np);
@@ -418,9 +433,11 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
     const int64_t T = tri_sz(N);
     for (int i = tid; i < N; i += TEAM) {
       const D4 v = a.md4[m0 + i];
-      s[3 * i] = a.sc * v.x;
-      s[3 * i + 1] = a.sc * v.y;
-      s[3 * i + 2] = a.sc * v.z;
+      const double sv[3] = {a.sc * v.x, a.sc * v.y, a.sc * v.z};
+      for (int d = 0; d < 3; ++d) {
+        if (a.fixed) sfix[3 * i + d] = __double2ll_rn(sv[d] * 0x1p40);
+        else s[3 * i + d] = sv[d];
+      }
       const float4 f = a.mf4[m0 + i];
       xf[4 * i] = f.x;
       xf[4 * i + 1] = f.y;
@@ -451,10 +468,8 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
           if (qn >= 32) {
             __syncwarp();
             {
-              const int ij = qw[lane], ii = ij >> 16, jj = ij & 0xffff;
-              const double ex = s[3 * ii] - s[3 * jj], ey = s[3 * ii + 1] - s[3 * jj + 1],
-                           ez = s[3 * ii + 2] - s[3 * jj + 2];
-              A[tri_sz(ii) + jj] = exp2_neg_q16(fma(ez, ez, fma(ey, ey, ex * ex)));
+              const int ij = qw[lane];
+              A[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
             }
             __syncwarp();
             if (lane < qn - 32) qw[lane] = qw[32 + lane];
@@ -465,9 +480,8 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
       }
       __syncwarp();
       if (lane < qn) {
-        const int ij = qw[lane], ii = ij >> 16, jj = ij & 0xffff;
-        const double ex = s[3 * ii] - s[3 * jj], ey = s[3 * ii + 1] - s[3 * jj + 1], ez = s[3 * ii + 2] - s[3 * jj + 2];
-        A[tri_sz(ii) + jj] = exp2_neg_q16(fma(ez, ez, fma(ey, ey, ex * ex)));
+        const int ij = qw[lane];
+        A[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
       }
     }
     fit_sync(TEAM);
@@ -490,13 +504,16 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
           __syncwarp();
           const int nc = ke - 1 - c;
           if (nc > 0) {
-            for (int i = c + 1 + lane; i <= N; i += 32) {
-              double* Ai = A + tri_sz(i);
-              const double lic = Ai[c];
-              const int ue = min(nc, i - c);
-              for (int u = 0; u < ue; ++u) {
-                const int j = c + 1 + u;
-                Ai[j] = fma(-lic, A[tri_sz(j) + c], Ai[j]);
+            // the (row, column) pairs of the update flattened over the lanes, so that each warp
+            // instruction carries 32 of them: t -> row c + 1 + t / nc, column c + 1 + t % nc
+            const unsigned mg = 0xFFFFFFFFu / (unsigned)nc + 1u;  // t / nc = umulhi(t, mg) for t < 2^29, nc > 1
+            const unsigned nt = (unsigned)(N - c) * (unsigned)nc;
+            for (unsigned t = lane; t < nt; t += 32) {
+              const unsigned q = nc == 1 ? t : __umulhi(t, mg);
+              const int i = c + 1 + (int)q, j = c + 1 + (int)(t - q * (unsigned)nc);
+              if (j <= i) {
+                double* Ai = A + tri_sz(i);
+                Ai[j] = fma(-Ai[c], A[tri_sz(j) + c], Ai[j]);
               }
             }
             __syncwarp();
@@ -769,6 +786,18 @@ static cudaError_t launch_persistent(ksdf_ctx* c, K kern, int team, const Args& 
   return cudaSuccess;
 }
 
+// the fit's scalar device routines on n inputs (diagnostics); NaN outside a routine's domain
+__global__ void k_device_math(int fn, const double* x, int64_t n, double* y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  double r = __longlong_as_double(0x7ff8000000000000ll);
+  if (fn == 0 && v >= 0.0 && v < 0x1p22) r = exp2_neg_q16(v);
+  if (fn == 1 && v >= 0.0 && v < 0x1p22) r = exp2_neg_fixed40((unsigned long long)(v * 0x1p40));
+  if (fn == 2 && pivot_ok(v)) r = rsqrt_pivot(v);
+  y[i] = r;
+}
+
 // brick of an OK cell (index (bz nby + by) nbx + bx over the cell bounding box); -1 for other cells
 __device__ __forceinline__ int64_t cell_brick(uint64_t key, int lx, int ly, int lz, int nbx, int nby) {
   int cx, cy, cz;
@@ -977,6 +1006,8 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   fa.gstride = 0;
   fa.sc = std::sqrt(p.lambda * kExpQ16PerNat);
   fa.lamf = (float)p.lambda;
+  // members lie within the margin of their cell: |local coordinate| <= h + mu
+  fa.fixed = fa.sc * (p.h + p.mu) < 0x1p21;
   e0 = prof_begin(c);
   KSDF_CUDA(c, fork_streams(c));
   int64_t first = 0;
@@ -1157,6 +1188,12 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
 // candidate size-class tables of the fit (largest class first; the first entry keeps its matrices in a
 // global slot).  Table 0 is the default; ksdf_autotune times them all on the model's own cells.  The result
 // of a fit does not depend on the table (each cell's arithmetic is the same whatever the team size).
+ksdf_status device_math(ksdf_ctx* c, int fn, const double* x, int64_t n, double* y) {
+  if (n > 0) launch(k_device_math, ceil_div(n, 256), 256, 0, c->stream, fn, x, n, y);
+  KSDF_CUDA(c, cudaGetLastError());
+  return KSDF_OK;
+}
+
 static const std::vector<std::vector<FitClassCfg>> kFitTables = {
     // one warp up to 80, two up to 96, four up to 156, eight up to 218
     {{kMaxNmax, 256, true}, {218, 256, false}, {156, 128, false}, {128, 128, false}, {96, 64, false},

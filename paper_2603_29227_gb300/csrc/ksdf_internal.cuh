@@ -192,7 +192,7 @@ struct ksdf_ctx {
   std::vector<double> stage_ms;
   std::vector<long long> stage_calls;
   // auxiliary streams for concurrent launches inside one call (fork/join through events)
-  static constexpr int kNumAux = 4;
+  static constexpr int kNumAux = 8;
   cudaStream_t aux[kNumAux] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kNumAux] = {};
 };
@@ -218,6 +218,7 @@ void prof_end(ksdf_ctx* c, cudaEvent_t a, const char* name);
 
 // ---- autotuning of the fit's size classes (ksdf_fit.cu) ----
 int fit_table_count();
+ksdf_status device_math(ksdf_ctx* c, int fn, const double* x, int64_t n, double* y);
 const std::vector<FitClassCfg>& fit_table(int i);
 ksdf_status autotune_fit(ksdf_ctx* c, int* chosen, double* ms);
 

@@ -29,7 +29,7 @@ CELL_OK, CELL_EMPTY, CELL_NOT_PD = 0, 1, 2
 ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_update", "ksdf_query",
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
-                 "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables")
+                 "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math")
 
 
 class KsdfError(RuntimeError):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
         "ksdf_fit_gp_noalloc": [ctypes.POINTER(ksdf_params), P, P, I64, P, P, P, P],
         "ksdf_autotune": [P, ctypes.POINTER(ctypes.c_int), P],
         "ksdf_autotune_tables": [],
+        "ksdf_device_math": [P, ctypes.c_int, P, I64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -175,6 +176,15 @@ def ksdf_autotune(h):
     t = ctypes.c_int(-1)
     _check(h, load().ksdf_autotune(h, ctypes.byref(t), _ptr(ms)), "ksdf_autotune")
     return int(t.value), ms
+
+
+def ksdf_device_math(h, fn, x):
+    """The fit's scalar device routines on float64 inputs x (fn 0: 2^(-x/2^16) from binary64, 1: the same from
+    floor(x 2^40) in fixed point, 2: 1/sqrt(x)); returns a float64 array."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    _check(h, load().ksdf_device_math(h, int(fn), _ptr(x), x.size, _ptr(y)), "ksdf_device_math")
+    return y
 
 
 def ksdf_update(h, x_new, var_new, normals_new, S_new, allow_not_pd=True):
