@@ -210,17 +210,17 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) per stage from one ncu capture of the current kernels on this workload
-# (profiles/room3d_kernels_ncu.md: the six populated k_fit size classes of one fit; the two k_phaseB_tc
-# launches of one query); None once a kernel changes until it is captured again
-MEASURED_TRAFFIC = {"fit.cholesky": 114.1e6, "query.phaseB": 490.3e6}
+# (profiles/room3d_fit_ncu.md: the six populated k_fit size classes of one fit; profiles/room3d_kernels_ncu.md:
+# the two k_phaseB_tc launches of one query); None once a kernel changes until it is captured again
+MEASURED_TRAFFIC = {"fit.cholesky": 288.0e6, "query.phaseB": 490.3e6}
 
 
 def fit_fp64_flops(n):
-    """FP64 flops of the fit of cells with training-set sizes n (exp evaluations not counted): kernel matrix
-    r^2 (8 flops per lower-triangle entry), Cholesky N^3/3, alpha 2N^2 (two triangular solves).  The FP32
-    inverse of the factor (N^3/3 FP32 flops) runs on another unit and is not counted."""
+    """FP64 flops of the factorisation stage (k_fit) for cells with training-set sizes n: Cholesky N^3/3 and
+    alpha 2N^2 (two triangular solves).  The kernel matrix (k_kmat, its own stage) and the FP32 inverse of
+    the factor (N^3/3 FP32 flops, another unit) are not counted."""
     n = n.astype(np.float64)
-    return float(np.sum(8 * n * (n + 1) / 2 + n ** 3 / 3 + 2 * n ** 2))
+    return float(np.sum(n ** 3 / 3 + 2 * n ** 2))
 
 
 def phase_a_pairs(w, h):
@@ -470,26 +470,33 @@ def main():
     peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
     pairs, nsz = phase_a_pairs(w, model.h)
     per = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
-    kernels = {k: per[k] for k in ("fit.cholesky", "fit.linv", "fit.index", "fit.assemble", "query.group", "query.candidates",
+    kernels = {k: per[k] for k in ("fit.cholesky", "fit.kmat", "fit.linv", "fit.index", "fit.assemble", "query.group",
+                                   "query.candidates",
                                    "query.phaseA", "query.regroup", "query.phaseB", "backward.group",
                                    "backward.query", "backward.cell") if k in per}
     dom = max(kernels, key=kernels.get)
     fl64 = fit_fp64_flops(nsz)
+    fp64_measured = ksdf.ksdf_fp64_rate(model.h)  # sustained DFMA rate of this GPU, outside the timed region
     roof_all = {
         "fit.cholesky": {"bound": "alu", "achieved": fl64 / (per["fit.cholesky"] * 1e-3) / 1e12,
                          "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                         "what": "FP64 flops (kernel matrix, Cholesky, alpha; exp and FP32 L^-1 not counted)"},
+                         "what": "FP64 flops of the factorisation: N^3/3 + 2 N^2 per cell (Cholesky and alpha)",
+                         "peak_measured": fp64_measured,
+                         "peak_measured_how": "ksdf_fp64_rate: dependent DFMA chains, 16 warps/SM, CUDA events"},
         "query.phaseA": {"bound": "alu", "achieved": pairs * 12 / (per["query.phaseA"] * 1e-3) / 1e12,
                          "peak": NOMINAL_FP32_TFLOPS, "unit": "TFLOP/s",
                          "what": "12 FP32 flops per (query, candidate sample) pair + 1 ex2; %.3g pairs" % pairs},
     }
     for k, r in roof_all.items():
         r["frac"] = r["achieved"] / r["peak"]
+        if r.get("peak_measured"):
+            r["frac_of_measured"] = r["achieved"] / r["peak_measured"]
         r["traffic"] = MEASURED_TRAFFIC.get(k)
     roof = dict(roof_all.get(dom, {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
                                    "traffic": None}))
     roof["kernel"] = dom
-    roof["peak_source"] = "recipe nominal (unit counts x clock); no FP64/FP32 figure in MEASURED_PEAKS.json"
+    roof["peak_source"] = ("recipe nominal (unit counts x clock); no FP64/FP32 figure in MEASURED_PEAKS.json; "
+                           "peak_measured: this GPU's sustained DFMA rate, measured live")
 
     # ---- plain FP64 query on the same inputs (outside the timed region) ----
     xq64 = xq.double()

@@ -148,6 +148,12 @@ int ksdf_autotune_tables(void);
  * Synchronises the stream. */
 ksdf_status ksdf_device_math(ksdf_ctx* ctx, int fn, const double* x, int64_t n, double* y);
 
+/* The device's sustained FP64 fused multiply-add rate, the ceiling of the FP64-bound factorisation: one
+ * 512-thread block per SM, four dependent chains of 4096 DFMAs per thread, timed with CUDA events on the
+ * context's stream after a warm-up launch (about 2 ms).  *tflops (host) receives 2 x FMAs / s / 1e12.
+ * Synchronises the stream.  KSDF_ERR_ARG for NULL arguments. */
+ksdf_status ksdf_fp64_rate(ksdf_ctx* ctx, double* tflops);
+
 /* Mixed-precision query: Q points xq (Q x dim float32); sign (Q int8, +1/-1, may be NULL).  FP32 SIMT
  * arithmetic in cell-local coordinates for the mean (compensated sum), gradient and softmin variance; the
  * GP variance contraction K' L^{-T} on the tensor cores in TF32 split three ways (hi*hi + hi*lo + lo*hi,

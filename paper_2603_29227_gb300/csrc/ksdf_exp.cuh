@@ -193,12 +193,15 @@ __device__ __forceinline__ double exp2_neg_fixed40(unsigned long long F) {
   return exp2_neg_tail(n, fixed40_to_double((long long)(F - (n << 40))));
 }
 
-// floor((a - b)^2 / 2^40) for fixed-point values with |a - b| < 2^52, exactly, in integer arithmetic
-// (a 64 x 64 -> 128-bit square)
+// (a - b)^2 / 2^40 for fixed-point values with |a - b| < 2^52, truncated (at most 2 units below the exact
+// quotient), in integer arithmetic: with |a - b| = h 2^32 + l, three 32 x 32 -> 64-bit products
 __device__ __forceinline__ unsigned long long sqdiff40(long long a, long long b) {
   const long long d = a - b;
   const unsigned long long u = d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
-  return (__umul64hi(u, u) << 24) | ((u * u) >> 40);
+  const unsigned h = (unsigned)(u >> 32), l = (unsigned)u;  // h < 2^20
+  const unsigned long long hh = (unsigned long long)h * h, hl = (unsigned long long)h * l,
+                           ll = (unsigned long long)l * l;
+  return (hh << 24) + (hl >> 7) + (ll >> 40);
 }
 
 // binary64 -> binary32, round to nearest even, values below FLT_MIN flushed to (signed) zero

@@ -336,11 +336,27 @@ struct FitArgs {
   double* gscr;     // per-CTA global slot (largest class): tri(np + 1) doubles
   int64_t gstride;  // doubles per slot
   int np;           // largest N of this class
-  double sc;        // sqrt(lambda 2^16 / ln2): coordinates scaled so that |s_i - s_j|^2 is exp2_neg_q16's argument
-  float lamf;       // lambda in FP32 (the near/far screen)
-  bool fixed;       // scaled coordinates below 2^21: exact fixed-point squared distances (else binary64)
   int* counter;
   int* n_not_pd;
+};
+
+// The kernel matrices of the cells order[0 .. count), each written (lower triangle with its diagonal) where
+// the cell's Cholesky factor will go: k_fit reads it back from there.
+struct KmatArgs {
+  const uint32_t* order;  // this launch takes order[first .. first + count)
+  int64_t first, count;
+  int* counter;
+  const int32_t* n32;
+  const int64_t* ts_off;
+  const int64_t* chol_off;
+  const D4* md4;
+  const float4* mf4;
+  const float* mvar;
+  double* chol64;
+  int np;      // largest N
+  double sc;   // sqrt(lambda 2^16 / ln2): coordinates scaled so that |s_i - s_j|^2 is exp2_neg_q16's argument
+  float lamf;  // lambda in FP32 (the near/far screen)
+  bool fixed;  // scaled coordinates below 2^21: exact fixed-point squared distances (else binary64)
 };
 
 // row of the packed lower-triangle entry t (t = i (i+1)/2 + j, j <= i)
@@ -375,28 +391,115 @@ __device__ __forceinline__ void fit_sync(int team) {
   else __syncthreads();
 }
 
-// Shared-memory layout of one cell's fit (doubles): scaled coordinates 3 np | two column buffers
-// 2 (np + 1) | reciprocal pivots np | FP32 coordinates 4 np floats | near-entry queues 64 ints per warp |
+constexpr int kKmatWarps = 4;
+
+// per-warp shared memory of k_kmat (doubles), with np rounded up to even so that every region starts on
+// 16 bytes (the FP32 coordinates are read as float4): scaled coordinates 3 np (binary64 or fixed point) |
+// FP32 coordinates 4 np floats | near-entry queue 64 ints
+__host__ __device__ inline int kmat_np_even(int np) { return (np + 1) & ~1; }
+__host__ __device__ inline int64_t kmat_warp_doubles(int np) { return 5 * (int64_t)kmat_np_even(np) + 32; }
+
+// The kernel matrix A = K + diag(sigma^2) of one cell per warp (persistent over the cells to fit).  Each
+// off-diagonal entry is screened in FP32: lambda r^2 >= 36 gives a value below 2.4e-16 that FP32 evaluates to
+// far better than its absolute rounding; the others are queued and evaluated 32 at a time in FP64
+// (exp2_neg_q16 on coordinates pre-scaled by sqrt(lambda 2^16 / ln2)).  The scaled coordinates are held in
+// fixed point with 40 fractional bits, so that the squared distance comes out of exact integer arithmetic as
+// exp2_neg_fixed40's argument: 4 FP64 operations per entry instead of 10 (the rounding of s to 2^-41 moves
+// an entry by below 1e-13 of its value).  A separate, high-occupancy kernel: the factorisation's warps then
+// spend their time in the FP64 factorisation alone.
+__global__ void __launch_bounds__(32 * kKmatWarps) k_kmat(KmatArgs a) {
+  extern __shared__ __align__(16) double smk[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int npe = kmat_np_even(a.np);
+  double* s = smk + warp * kmat_warp_doubles(a.np);
+  long long* sfix = reinterpret_cast<long long*>(s);  // the same slots, fixed point (a.fixed)
+  float* xf = reinterpret_cast<float*>(s + 3 * npe);
+  int* qw = reinterpret_cast<int*>(xf + 4 * npe);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(a.counter, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= a.count) break;
+    const int g = (int)a.order[a.first + w];
+    const int N = a.n32[g];
+    const int64_t m0 = a.ts_off[g];
+    double* Ag = a.chol64 + a.chol_off[g];
+    for (int i = lane; i < N; i += 32) {
+      const D4 v = a.md4[m0 + i];
+      const double sv[3] = {a.sc * v.x, a.sc * v.y, a.sc * v.z};
+      for (int d = 0; d < 3; ++d) {
+        if (a.fixed) sfix[3 * i + d] = __double2ll_rn(sv[d] * 0x1p40);
+        else s[3 * i + d] = sv[d];
+      }
+      const float4 f = a.mf4[m0 + i];
+      xf[4 * i] = f.x;
+      xf[4 * i + 1] = f.y;
+      xf[4 * i + 2] = f.z;
+      Ag[tri_sz(i) + i] = 1.0 + f2d_bits(a.mvar[m0 + i]);  // exp(0) + sigma_i^2
+    }
+    __syncwarp();
+    // the strictly lower pairs flattened, t = i (i - 1) / 2 + j, 32 consecutive pairs per step (full warps
+    // for every row length); a lane walks its (i, j) forward by 32 each step
+    const int64_t npair = (int64_t)N * (N - 1) / 2;
+    int i = 1, j = lane;
+    while (j >= i) {
+      j -= i;
+      ++i;
+    }
+    int qn = 0;
+    for (int64_t t0 = 0; t0 < npair; t0 += 32) {
+      bool near = false;
+      if (t0 + lane < npair) {
+        const float4 pi = reinterpret_cast<const float4*>(xf)[i];
+        const float4 pj = reinterpret_cast<const float4*>(xf)[j];
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float ef = a.lamf * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (ef < kNearE) near = true;
+        else Ag[tri_sz(i) + j] = f2d_bits(exp2f(-1.44269504f * ef));
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, near);
+      if (near) qw[qn + __popc(mask & lt_mask)] = (i << 16) | j;
+      qn += __popc(mask);
+      if (qn >= 32) {
+        __syncwarp();
+        const int ij = qw[lane];
+        Ag[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
+        __syncwarp();
+        if (lane < qn - 32) qw[lane] = qw[32 + lane];
+        qn -= 32;
+        __syncwarp();
+      }
+      j += 32;
+      while (j >= i) {
+        j -= i;
+        ++i;
+      }
+    }
+    __syncwarp();
+    if (lane < qn) {
+      const int ij = qw[lane];
+      Ag[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
+    }
+    __syncwarp();
+  }
+}
+
+// Shared-memory layout of one cell's fit (doubles): two column buffers 2 (np + 1) | reciprocal pivots np |
 // the augmented packed matrix tri(np + 1) (when it lives here).
-__host__ __device__ inline int64_t fit_smem_doubles(int np, int warps, bool smem_mat) {
-  return 3 * (int64_t)np + 2 * ((int64_t)np + 1) + np + 2 * (int64_t)np + 32 * (int64_t)warps +
-         (smem_mat ? tri_sz(np + 1) : 0);
+__host__ __device__ inline int64_t fit_smem_doubles(int np, bool smem_mat) {
+  return 2 * ((int64_t)np + 1) + np + (smem_mat ? tri_sz(np + 1) : 0);
 }
 
 // The fit of one cell per iteration of a persistent team (TEAM threads; one warp for the small classes).
-// On GB300 the FP64 pipe retires about two lanes per clock per SM and a warp instruction costs the same
-// whether 1 or 32 lanes are active, so every step keeps its FP64 work in full warps:
-//   1. A = K + diag(sigma^2), augmented with a row of ones (the right-hand side of A alpha = 1).  Each
-//      off-diagonal entry is screened in FP32: lambda r^2 >= 36 gives a value below 2.4e-16 that FP32
-//      evaluates to far better than its absolute rounding; the others are queued per warp and evaluated
-//      32 at a time in FP64 (exp2_neg_q16 on coordinates pre-scaled by sqrt(lambda 2^16 / ln2)).  The
-//      scaled coordinates are held in fixed point with 40 fractional bits, so that the squared distance
-//      comes out of exact integer arithmetic as exp2_neg_fixed40's argument: 4 FP64 operations per entry
-//      instead of 10 (the rounding of s to 2^-41 moves an entry by below 1e-13 of its value).
+// On GB300 an SM retires one FP64 warp instruction per ~20 cycles (one per ~68 per scheduler) whether 1 or
+// 32 lanes are active, so every step keeps its FP64 work in full warps:
+//   1. A = K + diag(sigma^2) (written by k_kmat where L goes) is read into the team's matrix and augmented
+//      with a row of ones (the right-hand side of A alpha = 1).
 //   2. Right-looking Cholesky of the augmented matrix in panels of kB columns: warp 0 factors a panel
-//      (pivots by rsqrt_pivot, column scaling, updates inside the panel, lanes along the rows), then the
-//      team updates the trailing triangle in 2 x 2 register blocks over the panel depth (about three
-//      instructions per DFMA).  The augmented row ends as y = L^{-1} 1.
+//      (pivots by rsqrt_pivot, column scaling, updates inside the panel flattened over the lanes), then the
+//      team updates the trailing triangle in 2 x 2 register blocks over the panel depth.  The augmented row
+//      ends as y = L^{-1} 1.
 //   3. alpha = L^{-T} y by backward substitution (warp 0) while the other warps write L out.
 // L^{-1} in FP32 follows in k_linv.
 template <int TEAM, bool GMAT>
@@ -406,15 +509,9 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
   __shared__ int s_cell, s_fail;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = a.np;
-  double* s = sm;
-  long long* sfix = reinterpret_cast<long long*>(s);  // the same slots, fixed point (a.fixed)
-  double* cb = s + 3 * np;
+  double* cb = sm;
   double* dinv = cb + 2 * (np + 1);
-  float* xf = reinterpret_cast<float*>(dinv + np);
-  int* qw = reinterpret_cast<int*>(xf + 4 * np) + 64 * warp;
-  double* A = GMAT ? a.gscr + (int64_t)blockIdx.x * a.gstride
-                   : reinterpret_cast<double*>(sm + fit_smem_doubles(np, W, false));
-  const unsigned lt_mask = (1u << lane) - 1u;
+  double* A = GMAT ? a.gscr + (int64_t)blockIdx.x * a.gstride : sm + fit_smem_doubles(np, false);
   for (;;) {
     if (tid == 0) {
       const int w = atomicAdd(a.counter, 1);
@@ -431,58 +528,24 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
     }
     const int64_t m0 = a.ts_off[g];
     const int64_t T = tri_sz(N);
-    for (int i = tid; i < N; i += TEAM) {
-      const D4 v = a.md4[m0 + i];
-      const double sv[3] = {a.sc * v.x, a.sc * v.y, a.sc * v.z};
-      for (int d = 0; d < 3; ++d) {
-        if (a.fixed) sfix[3 * i + d] = __double2ll_rn(sv[d] * 0x1p40);
-        else s[3 * i + d] = sv[d];
-      }
-      const float4 f = a.mf4[m0 + i];
-      xf[4 * i] = f.x;
-      xf[4 * i + 1] = f.y;
-      xf[4 * i + 2] = f.z;
-      A[tri_sz(i) + i] = 1.0 + f2d_bits(a.mvar[m0 + i]);  // exp(0) + sigma_i^2
-      A[T + i] = 1.0;                                       // augmented row: the right-hand side
-    }
-    if (tid == 0) A[T + N] = 0.0;  // never used; kept finite
-    fit_sync(TEAM);
-    // 1. off-diagonal kernel entries: rows round-robin over the warps, lanes along the row
+    // 1. the kernel matrix (eight loads in flight per thread) and the augmented row
     {
-      int qn = 0;
-      for (int i = 1 + warp; i < N; i += W) {
-        const float xi = xf[4 * i], yi = xf[4 * i + 1], zi = xf[4 * i + 2];
-        double* Ai = A + tri_sz(i);
-        for (int j0 = 0; j0 < i; j0 += 32) {
-          const int j = j0 + lane;
-          bool near = false;
-          if (j < i) {
-            const float dx = xi - xf[4 * j], dy = yi - xf[4 * j + 1], dz = zi - xf[4 * j + 2];
-            const float ef = a.lamf * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            if (ef < kNearE) near = true;
-            else Ai[j] = f2d_bits(exp2f(-1.44269504f * ef));
-          }
-          const unsigned mask = __ballot_sync(0xffffffffu, near);
-          if (near) qw[qn + __popc(mask & lt_mask)] = (i << 16) | j;
-          qn += __popc(mask);
-          if (qn >= 32) {
-            __syncwarp();
-            {
-              const int ij = qw[lane];
-              A[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
-            }
-            __syncwarp();
-            if (lane < qn - 32) qw[lane] = qw[32 + lane];
-            qn -= 32;
-            __syncwarp();
-          }
+      const double* Ag = a.chol64 + a.chol_off[g];
+      for (int64_t e0 = tid; e0 < T; e0 += 8 * (int64_t)TEAM) {
+        double v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int64_t e = e0 + (int64_t)r * TEAM;
+          v[r] = e < T ? Ag[e] : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int64_t e = e0 + (int64_t)r * TEAM;
+          if (e < T) A[e] = v[r];
         }
       }
-      __syncwarp();
-      if (lane < qn) {
-        const int ij = qw[lane];
-        A[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
-      }
+      for (int i = tid; i < N; i += TEAM) A[T + i] = 1.0;
+      if (tid == 0) A[T + N] = 0.0;  // never used; kept finite
     }
     fit_sync(TEAM);
     // 2. Cholesky of the augmented matrix in panels of kB columns: warp 0 factors the panel (pivots,
@@ -786,6 +849,19 @@ static cudaError_t launch_persistent(ksdf_ctx* c, K kern, int team, const Args& 
   return cudaSuccess;
 }
 
+// FP64 FMA throughput probe: four independent dependent chains per thread
+__global__ void k_fp64_rate(int iters, double* sink) {
+  double x0 = 1.0 + 1e-3 * threadIdx.x, x1 = x0 + 0.25, x2 = x0 + 0.5, x3 = x0 + 0.75;
+  const double a = 0.999999, b = 1e-7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b);
+    x1 = fma(x1, a, b);
+    x2 = fma(x2, a, b);
+    x3 = fma(x3, a, b);
+  }
+  if ((x0 + x1) + (x2 + x3) == 0.0) sink[0] = x0;  // never true; keeps the chains
+}
+
 // the fit's scalar device routines on n inputs (diagnostics); NaN outside a routine's domain
 __global__ void k_device_math(int fn, const double* x, int64_t n, double* y) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -988,7 +1064,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
   KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 32));  // counters: fit and L^-1 classes
   int* ctr = reinterpret_cast<int*>(ptr<int64_t>(c->ws[WS_E]) + 4);
-  KSDF_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int) * 16, st));
+  KSDF_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int) * 32, st));
   FitArgs fa;
   fa.order = order;
   fa.n32 = ptr<int32_t>(m.n);
@@ -1004,10 +1080,34 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   fa.n_not_pd = dmax + 1;
   fa.gscr = nullptr;
   fa.gstride = 0;
-  fa.sc = std::sqrt(p.lambda * kExpQ16PerNat);
-  fa.lamf = (float)p.lambda;
-  // members lie within the margin of their cell: |local coordinate| <= h + mu
-  fa.fixed = fa.sc * (p.h + p.mu) < 0x1p21;
+  // kernel matrices of the cells to fit (largest first), into the factor's place
+  e0 = prof_begin(c);
+  if (nfit > 0) {
+    KmatArgs ka;
+    ka.order = order;
+    ka.first = 0;
+    ka.count = nfit;
+    ka.counter = ctr + 24;
+    ka.n32 = ptr<int32_t>(m.n);
+    ka.ts_off = ptr<int64_t>(m.ts_off);
+    ka.chol_off = ptr<int64_t>(m.chol_off);
+    ka.md4 = ptr<D4>(m.md4);
+    ka.mf4 = ptr<float4>(m.mf4);
+    ka.mvar = ptr<float>(m.mvar);
+    ka.chol64 = ptr<double>(m.chol64);
+    ka.np = std::max(m.max_n, 1);
+    ka.sc = std::sqrt(p.lambda * kExpQ16PerNat);
+    ka.lamf = (float)p.lambda;
+    // members lie within the margin of their cell: |local coordinate| <= h + mu
+    ka.fixed = ka.sc * (p.h + p.mu) < 0x1p21;
+    const size_t ksm = sizeof(double) * (size_t)kmat_warp_doubles(ka.np) * kKmatWarps;
+    KSDF_CUDA(c, cudaFuncSetAttribute(k_kmat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksm));
+    int occ = 0;
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_kmat, 32 * kKmatWarps, ksm));
+    const int64_t nblk = std::min<int64_t>(ceil_div(nfit, kKmatWarps), (int64_t)std::max(1, occ) * c->num_sms);
+    launch(k_kmat, (unsigned)nblk, 32 * kKmatWarps, ksm, st, ka);
+  }
+  prof_end(c, e0, "fit.kmat");
   e0 = prof_begin(c);
   KSDF_CUDA(c, fork_streams(c));
   int64_t first = 0;
@@ -1021,7 +1121,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     first += cnt[cl];
     const int team = cls[cl].team;
     f.np = cls[cl].gmat ? std::max(m.max_n, 1) : cls[cl].np;
-    const size_t smem = sizeof(double) * (size_t)fit_smem_doubles(f.np, team / 32, !cls[cl].gmat);
+    const size_t smem = sizeof(double) * (size_t)fit_smem_doubles(f.np, !cls[cl].gmat);
     cudaStream_t s = (launched % (ksdf_ctx::kNumAux + 1)) == ksdf_ctx::kNumAux
                          ? st
                          : c->aux[launched % (ksdf_ctx::kNumAux + 1)];
@@ -1188,6 +1288,28 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
 // candidate size-class tables of the fit (largest class first; the first entry keeps its matrices in a
 // global slot).  Table 0 is the default; ksdf_autotune times them all on the model's own cells.  The result
 // of a fit does not depend on the table (each cell's arithmetic is the same whatever the team size).
+ksdf_status fp64_rate(ksdf_ctx* c, double* tflops) {
+  constexpr int kWarps = 16, kIters = 4096;
+  KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 32));
+  double* sink = ptr<double>(c->ws[WS_E]);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KSDF_CUDA(c, cudaEventCreate(&e0));
+  KSDF_CUDA(c, cudaEventCreate(&e1));
+  launch(k_fp64_rate, c->num_sms, 32 * kWarps, 0, c->stream, kIters, sink);  // warm-up
+  cudaEventRecord(e0, c->stream);
+  launch(k_fp64_rate, c->num_sms, 32 * kWarps, 0, c->stream, kIters, sink);
+  cudaEventRecord(e1, c->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  KSDF_CUDA(c, e);
+  const double fmas = (double)c->num_sms * kWarps * 32 * kIters * 4;
+  *tflops = 2.0 * fmas / (ms * 1e-3) / 1e12;
+  return KSDF_OK;
+}
+
 ksdf_status device_math(ksdf_ctx* c, int fn, const double* x, int64_t n, double* y) {
   if (n > 0) launch(k_device_math, ceil_div(n, 256), 256, 0, c->stream, fn, x, n, y);
   KSDF_CUDA(c, cudaGetLastError());

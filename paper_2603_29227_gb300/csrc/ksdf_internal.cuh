@@ -219,6 +219,7 @@ void prof_end(ksdf_ctx* c, cudaEvent_t a, const char* name);
 // ---- autotuning of the fit's size classes (ksdf_fit.cu) ----
 int fit_table_count();
 ksdf_status device_math(ksdf_ctx* c, int fn, const double* x, int64_t n, double* y);
+ksdf_status fp64_rate(ksdf_ctx* c, double* tflops);
 const std::vector<FitClassCfg>& fit_table(int i);
 ksdf_status autotune_fit(ksdf_ctx* c, int* chosen, double* ms);
 

@@ -29,7 +29,8 @@ CELL_OK, CELL_EMPTY, CELL_NOT_PD = 0, 1, 2
 ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_update", "ksdf_query",
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
-                 "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math")
+                 "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math",
+                 "ksdf_fp64_rate")
 
 
 class KsdfError(RuntimeError):
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH):
         "ksdf_autotune": [P, ctypes.POINTER(ctypes.c_int), P],
         "ksdf_autotune_tables": [],
         "ksdf_device_math": [P, ctypes.c_int, P, I64, P],
+        "ksdf_fp64_rate": [P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -185,6 +187,13 @@ def ksdf_device_math(h, fn, x):
     y = np.empty_like(x)
     _check(h, load().ksdf_device_math(h, int(fn), _ptr(x), x.size, _ptr(y)), "ksdf_device_math")
     return y
+
+
+def ksdf_fp64_rate(h):
+    """The device's sustained FP64 FMA rate in TFLOP/s (a short DFMA-chain probe on the context's stream)."""
+    t = ctypes.c_double(0.0)
+    _check(h, load().ksdf_fp64_rate(h, ctypes.byref(t)), "ksdf_fp64_rate")
+    return float(t.value)
 
 
 def ksdf_update(h, x_new, var_new, normals_new, S_new, allow_not_pd=True):
