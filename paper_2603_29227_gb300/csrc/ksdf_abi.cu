@@ -103,6 +103,7 @@ cudaError_t fork_streams(ksdf_ctx* c) {
     for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
+    for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_mid[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
   }
   e = cudaEventRecord(c->ev_fork, c->stream);
@@ -245,6 +246,7 @@ ksdf_status ksdf_destroy(ksdf_ctx* c) {
   for (int i = 0; i < ksdf_ctx::kNumAux; ++i) {
     if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+    if (c->ev_mid[i]) cudaEventDestroy(c->ev_mid[i]);
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;

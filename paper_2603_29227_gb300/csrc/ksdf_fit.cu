@@ -704,6 +704,154 @@ __host__ __device__ inline int64_t linv_slot_floats(int np, bool inplace) {
   return inplace ? (((int64_t)np + 3) & ~3LL) + tri_sz(np) : linv_group_off(np, (np + 31) / 32);
 }
 
+// L^{-1} of the cells with N <= 96, one warp per cell (persistent).  Shared memory holds L in FP32 with
+// every row padded to a multiple of four floats (row i at lrow_off(i)), the reciprocal diagonal, and the 32
+// columns of the current group of X = L^{-1}, one per lane, stored column-major (Xt[c xs + i] = X[i][base +
+// c], xs = 4 mod 32 so that the lanes' 16-byte loads are conflict-free).  A lane computes its column by
+// forward substitution four rows at a time, walking k four at a time with 16-byte loads: five loads feed
+// sixteen FFMAs (the L rows are broadcasts).  The group's columns are then written in the 8-row blocked
+// layout and as the tensor-core images (coalesced float4 stores along the rows).
+__host__ __device__ inline int lrow_off(int i) {
+  const int q = i >> 2, r = i & 3;
+  return 4 * (2 * q * (q + 1) + r * (q + 1));
+}
+__host__ __device__ inline int linv_small_stride(int np) { return 32 * ((np + 31) / 32) + 4; }
+__host__ __device__ inline int64_t linv_small_floats(int np) {
+  return lrow_off(np) + ((np + 3) & ~3) + 32LL * linv_small_stride(np);
+}
+
+__global__ void __launch_bounds__(32) k_linv_small(LinvArgs a) {
+  extern __shared__ __align__(16) float smf[];
+  const int lane = threadIdx.x;
+  const int np = a.np;
+  float* L = smf;
+  float* dg = smf + lrow_off(np);
+  const int xs = linv_small_stride(np);
+  float* Xt = dg + ((np + 3) & ~3);
+  float* xc = Xt + lane * xs;  // this lane's column of the current group
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(a.counter, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= a.count) break;
+    const int g = (int)a.order[a.first + w];
+    const int N = a.n32[g];
+    if (N == 0 || a.status[g] != KSDF_CELL_OK) continue;
+    // L: binary64 packed rows -> FP32 padded rows, eight loads in flight per lane; a lane walks its (row,
+    // column) forward by 32 entries per load
+    {
+      const int64_t T = tri_sz(N);
+      const double* Ld = a.chol64 + a.chol_off[g];
+      int ri = 0, rk = lane;
+      while (rk > ri) {
+        rk -= ri + 1;
+        ++ri;
+      }
+      for (int64_t e0 = lane; e0 < T; e0 += 256) {
+        double v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int64_t e = e0 + 32 * r;
+          v[r] = e < T ? Ld[e] : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if (e0 + 32 * r < T) L[lrow_off(ri) + rk] = d2f_bits(v[r]);
+          rk += 32;
+          while (rk > ri) {
+            rk -= ri + 1;
+            ++ri;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) dg[i] = 1.f / L[lrow_off(i) + i];
+    __syncwarp();
+    float* Iout = a.linv32 + a.linv_off[g];
+    const int nR = (N + 7) >> 3;
+    for (int base = 0; base < N; base += 32) {
+      const int j = base + lane;
+      for (int i0 = base; i0 < N; i0 += 4) {
+        const float* L0 = L + lrow_off(i0);
+        const float* L1 = L + lrow_off(min(i0 + 1, N - 1));
+        const float* L2 = L + lrow_off(min(i0 + 2, N - 1));
+        const float* L3 = L + lrow_off(min(i0 + 3, N - 1));
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll 2
+        for (int k0 = base; k0 < i0; k0 += 4) {
+          const float4 x = *reinterpret_cast<const float4*>(xc + k0);
+          const float4 l0 = *reinterpret_cast<const float4*>(L0 + k0);
+          const float4 l1 = *reinterpret_cast<const float4*>(L1 + k0);
+          const float4 l2 = *reinterpret_cast<const float4*>(L2 + k0);
+          const float4 l3 = *reinterpret_cast<const float4*>(L3 + k0);
+          c0 = fmaf(l0.w, x.w, fmaf(l0.z, x.z, fmaf(l0.y, x.y, fmaf(l0.x, x.x, c0))));
+          c1 = fmaf(l1.w, x.w, fmaf(l1.z, x.z, fmaf(l1.y, x.y, fmaf(l1.x, x.x, c1))));
+          c2 = fmaf(l2.w, x.w, fmaf(l2.z, x.z, fmaf(l2.y, x.y, fmaf(l2.x, x.x, c2))));
+          c3 = fmaf(l3.w, x.w, fmaf(l3.z, x.z, fmaf(l3.y, x.y, fmaf(l3.x, x.x, c3))));
+        }
+        // the 4 x 4 block on the diagonal, row by row
+        float xv[4] = {0.f, 0.f, 0.f, 0.f};
+        xv[0] = i0 > j ? -c0 * dg[i0] : (i0 == j ? dg[j] : 0.f);
+        if (i0 + 1 < N) {
+          c1 = fmaf(L1[i0], xv[0], c1);
+          xv[1] = i0 + 1 > j ? -c1 * dg[i0 + 1] : (i0 + 1 == j ? dg[j] : 0.f);
+          if (i0 + 2 < N) {
+            c2 = fmaf(L2[i0 + 1], xv[1], fmaf(L2[i0], xv[0], c2));
+            xv[2] = i0 + 2 > j ? -c2 * dg[i0 + 2] : (i0 + 2 == j ? dg[j] : 0.f);
+            if (i0 + 3 < N) {
+              c3 = fmaf(L3[i0 + 2], xv[2], fmaf(L3[i0 + 1], xv[1], fmaf(L3[i0], xv[0], c3)));
+              xv[3] = i0 + 3 > j ? -c3 * dg[i0 + 3] : (i0 + 3 == j ? dg[j] : 0.f);
+            }
+          }
+        }
+        *reinterpret_cast<float4*>(xc + i0) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+      }
+      __syncwarp();
+      // blocked output: column j, blocks R >= j / 8 (rows above the diagonal, beyond N, or above this group's
+      // first row read as zero)
+      if (j < 8 * nR) {
+        for (int R = j >> 3; R < nR; ++R) {
+          const float4 u0 = *reinterpret_cast<const float4*>(xc + 8 * R);
+          const float4 u1 = *reinterpret_cast<const float4*>(xc + 8 * R + 4);
+          const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+          float v[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int i = 8 * R + r;
+            v[r] = (j < N && i < N && i >= j) ? u[r] : 0.f;
+          }
+          float4* dst = reinterpret_cast<float4*>(Iout + linv_block_off(R) + (int64_t)j * 8);
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+      }
+      // tensor-core images: quads of this group's columns, all Np rows, TF32 hi = rna(x), lo = rna(x - hi)
+      if (N <= kTcMaxN) {
+        const int np16 = tc_np(N);
+        const int q1 = min(base + 32, tc_kp(N)) >> 2;
+        float* img = a.ltc + a.ltc_off[g];
+        for (int q = base >> 2; q < q1; ++q) {
+          for (int i = lane; i < np16; i += 32) {
+            float hi[4], lo[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int col = 4 * q + u;
+              const float v = (col <= i && i < N) ? Xt[(col - base) * xs + i] : 0.f;
+              hi[u] = tf32_rna_fit(v);
+              lo[u] = tf32_rna_fit(v - hi[u]);
+            }
+            const int64_t o = ((int64_t)q * np16 + i) * 4;
+            *reinterpret_cast<float4*>(img + o) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<float4*>(img + a.ltc_lo + o) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 template <int TEAM, bool INPLACE, bool GMAT>
 __global__ void __launch_bounds__(TEAM) k_linv(LinvArgs a) {
   extern __shared__ __align__(16) float smf[];
@@ -1122,9 +1270,8 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     const int team = cls[cl].team;
     f.np = cls[cl].gmat ? std::max(m.max_n, 1) : cls[cl].np;
     const size_t smem = sizeof(double) * (size_t)fit_smem_doubles(f.np, !cls[cl].gmat);
-    cudaStream_t s = (launched % (ksdf_ctx::kNumAux + 1)) == ksdf_ctx::kNumAux
-                         ? st
-                         : c->aux[launched % (ksdf_ctx::kNumAux + 1)];
+    const int si = launched % ksdf_ctx::kNumAux;  // auxiliary streams only: the main stream marks the stage end
+    cudaStream_t s = c->aux[si];
     ++launched;
     if (cls[cl].gmat) {
       f.gstride = tri_sz(f.np + 1);
@@ -1141,74 +1288,52 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
       default: le = launch_persistent(c, k_fit<32, false>, 32, f, smem, false, s, p); break;
     }
     KSDF_CUDA(c, le);
-  }
-  KSDF_CUDA(c, cudaGetLastError());
-  KSDF_CUDA(c, join_streams(c));
-  prof_end(c, e0, "fit.cholesky");
-  // L^{-1} in FP32, by size class (np <= team * rows of the kernel's inversion loop)
-  e0 = prof_begin(c);
-  {
-    // small cells: one warp, in place; larger: one warp per 32-column group (team = 32 ceil(np / 32))
-    constexpr int kNumLinv = 5;
-    const FitClass lcls[kNumLinv] = {{kMaxNmax, 512, true}, {218, 224, false}, {156, 160, false}, {96, 32, false},
-                                     {64, 32, false}};
-    int64_t lcnt[kNumLinv] = {};
-    for (int32_t v : hn) {
-      if (v < 0) continue;
-      int cl = kNumLinv - 1;
-      while (cl > 0 && v > lcls[cl].np) --cl;
-      ++lcnt[cl];
-    }
-    KSDF_CUDA(c, cudaMemsetAsync(ctr + 16, 0, sizeof(int) * kNumLinv, st));
-    KSDF_CUDA(c, fork_streams(c));
-    LinvArgs la;
-    la.order = order;
-    la.n32 = ptr<int32_t>(m.n);
-    la.status = ptr<int32_t>(m.status);
-    la.chol_off = ptr<int64_t>(m.chol_off);
-    la.linv_off = ptr<int64_t>(m.linv_off);
-    la.chol64 = ptr<double>(m.chol64);
-    la.linv32 = ptr<float>(m.linv32);
-    la.ltc_off = ptr<int64_t>(m.ltc_off);
-    la.ltc = ptr<float>(m.ltc);
-    la.ltc_lo = m.ltc_total;
-    la.gscr = nullptr;
-    la.gstride = 0;
-    int64_t lfirst = 0;
-    int nl = 0;
-    for (int cl = 0; cl < kNumLinv; ++cl) {
-      if (lcnt[cl] == 0) continue;
-      LinvArgs f = la;
-      f.first = lfirst;
-      f.count = lcnt[cl];
-      f.counter = ctr + 16 + cl;
-      lfirst += lcnt[cl];
-      f.np = lcls[cl].gmat ? std::max(m.max_n, 1) : lcls[cl].np;
-      const bool inplace = lcls[cl].team == 32;
-      const int64_t slot = linv_slot_floats(f.np, inplace);
-      size_t smem = 0;
-      if (lcls[cl].gmat) {
-        f.gstride = (slot + 3) & ~3LL;
-        const int64_t slots = std::min<int64_t>(lcnt[cl], c->num_sms);
-        KSDF_CUDA(c, ensure(c->ws[WS_LINVSCR], sizeof(float) * (size_t)(f.gstride * slots + 4)));
-        f.gscr = ptr<float>(c->ws[WS_LINVSCR]);
+    KSDF_CUDA(c, cudaEventRecord(c->ev_mid[si], s));
+    // L^{-1} in FP32 of the same cells, behind their factorisation on the same stream: its FP32 / integer
+    // work overlaps the FP64 factorisation of the other classes
+    {
+      LinvArgs la;
+      la.order = order;
+      la.first = f.first;
+      la.count = f.count;
+      la.counter = ctr + 16 + cl;
+      la.n32 = ptr<int32_t>(m.n);
+      la.status = ptr<int32_t>(m.status);
+      la.chol_off = ptr<int64_t>(m.chol_off);
+      la.linv_off = ptr<int64_t>(m.linv_off);
+      la.chol64 = ptr<double>(m.chol64);
+      la.linv32 = ptr<float>(m.linv32);
+      la.ltc_off = ptr<int64_t>(m.ltc_off);
+      la.ltc = ptr<float>(m.ltc);
+      la.ltc_lo = m.ltc_total;
+      la.gscr = nullptr;
+      la.gstride = 0;
+      la.np = f.np;
+      if (f.np <= 96) {
+        le = launch_persistent(c, k_linv_small, 32, la, sizeof(float) * (size_t)linv_small_floats(f.np), false, s);
+      } else if (f.np <= 160) {
+        le = launch_persistent(c, k_linv<160, false, false>, 160, la,
+                               sizeof(float) * (size_t)linv_slot_floats(f.np, false), false, s);
+      } else if (f.np <= 224 && !cls[cl].gmat) {
+        le = launch_persistent(c, k_linv<224, false, false>, 224, la,
+                               sizeof(float) * (size_t)linv_slot_floats(f.np, false), false, s);
       } else {
-        smem = sizeof(float) * (size_t)slot;
-      }
-      cudaStream_t s = (nl % (ksdf_ctx::kNumAux + 1)) == ksdf_ctx::kNumAux ? st : c->aux[nl % (ksdf_ctx::kNumAux + 1)];
-      ++nl;
-      cudaError_t le = cudaSuccess;
-      switch (cl) {
-        case 0: le = launch_persistent(c, k_linv<512, false, true>, 512, f, smem, true, s); break;
-        case 1: le = launch_persistent(c, k_linv<224, false, false>, 224, f, smem, false, s); break;
-        case 2: le = launch_persistent(c, k_linv<160, false, false>, 160, f, smem, false, s); break;
-        default: le = launch_persistent(c, k_linv<32, true, false>, 32, f, smem, false, s); break;
+        la.gstride = (linv_slot_floats(f.np, false) + 3) & ~3LL;
+        const int64_t slots = std::min<int64_t>(f.count, c->num_sms);
+        KSDF_CUDA(c, ensure(c->ws[WS_LINVSCR], sizeof(float) * (size_t)(la.gstride * slots + 4)));
+        la.gscr = ptr<float>(c->ws[WS_LINVSCR]);
+        le = launch_persistent(c, k_linv<512, false, true>, 512, la, 0, true, s);
       }
       KSDF_CUDA(c, le);
     }
-    KSDF_CUDA(c, cudaGetLastError());
-    KSDF_CUDA(c, join_streams(c));
   }
+  // the factorisations are done when every class stream has passed its k_fit
+  for (int i = 0; i < std::min(launched, ksdf_ctx::kNumAux); ++i) KSDF_CUDA(c, cudaStreamWaitEvent(st, c->ev_mid[i], 0));
+  KSDF_CUDA(c, cudaGetLastError());
+  prof_end(c, e0, "fit.cholesky");
+  // the rest of the L^{-1} kernels
+  e0 = prof_begin(c);
+  KSDF_CUDA(c, join_streams(c));
   prof_end(c, e0, "fit.linv");
   if (prev && nfit < G) {
     Model& o = const_cast<Model&>(*prev);

@@ -194,7 +194,7 @@ struct ksdf_ctx {
   // auxiliary streams for concurrent launches inside one call (fork/join through events)
   static constexpr int kNumAux = 8;
   cudaStream_t aux[kNumAux] = {};
-  cudaEvent_t ev_fork = nullptr, ev_join[kNumAux] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kNumAux] = {}, ev_mid[kNumAux] = {};  // ev_mid: a stage boundary inside a fork
 };
 
 namespace ksdf {
