@@ -512,6 +512,7 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
   double* cb = sm;
   double* dinv = cb + 2 * (np + 1);
   double* A = GMAT ? a.gscr + (int64_t)blockIdx.x * a.gstride : sm + fit_smem_doubles(np, false);
+  double* P = sm + fit_smem_doubles(np, false);  // GMAT: the current panel, (np + 1) x kB
   for (;;) {
     if (tid == 0) {
       const int w = atomicAdd(a.counter, 1);
@@ -554,16 +555,27 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
     //    diagonal keeps the pivot d_k until the end (L_kk = d_k / sqrt(d_k) is applied in bulk).
     for (int kb = 0; kb < N; kb += kB) {
       const int ke = min(kb + kB, N);
+      // the panel's element (row i >= kb, column kb <= c < ke): in the matrix itself, or (GMAT: the matrix
+      // in a global slot) in a shared-memory copy of the panel, so that the panel's factorisation and the
+      // trailing update read it from shared memory
+      auto PE = [&](int i, int c) -> double& { return GMAT ? P[(i - kb) * kB + (c - kb)] : A[tri_sz(i) + c]; };
+      if (GMAT) {
+        for (int t = tid; t < (N + 1 - kb) * kB; t += TEAM) {
+          const int i = kb + (t >> 3), col = kb + (t & 7);
+          P[t] = (col < ke && col <= i) ? A[tri_sz(i) + col] : 0.0;
+        }
+        fit_sync(TEAM);
+      }
       if (warp == 0) {
         for (int c = kb; c < ke; ++c) {
-          const double d = A[tri_sz(c) + c];
+          const double d = PE(c, c);
           if (!pivot_ok(d)) {
             if (lane == 0) s_fail = 1;
             break;
           }
           const double y = rsqrt_pivot(d);
           if (lane == 0) dinv[c] = y;
-          for (int i = c + 1 + lane; i <= N; i += 32) A[tri_sz(i) + c] *= y;
+          for (int i = c + 1 + lane; i <= N; i += 32) PE(i, c) *= y;
           __syncwarp();
           const int nc = ke - 1 - c;
           if (nc > 0) {
@@ -574,10 +586,7 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
             for (unsigned t = lane; t < nt; t += 32) {
               const unsigned q = nc == 1 ? t : __umulhi(t, mg);
               const int i = c + 1 + (int)q, j = c + 1 + (int)(t - q * (unsigned)nc);
-              if (j <= i) {
-                double* Ai = A + tri_sz(i);
-                Ai[j] = fma(-Ai[c], A[tri_sz(j) + c], Ai[j]);
-              }
+              if (j <= i) PE(i, j) = fma(-PE(i, c), PE(j, c), PE(i, j));
             }
             __syncwarp();
           }
@@ -585,6 +594,11 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
       }
       fit_sync(TEAM);
       if (s_fail) break;
+      if (GMAT)  // the factored panel back into the matrix (columns disjoint from the trailing update's)
+        for (int t = tid; t < (N + 1 - kb) * kB; t += TEAM) {
+          const int i = kb + (t >> 3), col = kb + (t & 7);
+          if (col < ke && col <= i) A[tri_sz(i) + col] = P[t];
+        }
       const int w = ke - kb;
       const int nbk = (N + 2 - ke) >> 1;  // 2-row blocks over rows ke..N
       const int64_t nblk = tri_sz(nbk);
@@ -594,10 +608,10 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
         const bool vi1 = i1 <= N, v01 = j1 <= i0, vj1 = j1 <= N;
         double* Ai0 = A + tri_sz(i0);
         double* Ai1 = vi1 ? A + tri_sz(i1) : Ai0;
-        const double* Lj0 = A + tri_sz(j0) + kb;
-        const double* Lj1 = vj1 ? A + tri_sz(j1) + kb : Lj0;
-        const double* Li0 = Ai0 + kb;
-        const double* Li1 = Ai1 + kb;
+        const double* Li0 = GMAT ? P + (i0 - kb) * kB : Ai0 + kb;
+        const double* Li1 = GMAT ? (vi1 ? P + (i1 - kb) * kB : Li0) : Ai1 + kb;
+        const double* Lj0 = GMAT ? P + (j0 - kb) * kB : A + tri_sz(j0) + kb;
+        const double* Lj1 = vj1 ? (GMAT ? P + (j1 - kb) * kB : A + tri_sz(j1) + kb) : Lj0;
         double a00 = Ai0[j0];
         double a01 = v01 ? Ai0[j1] : 0.0;
         double a10 = vi1 ? Ai1[j0] : 0.0;
@@ -704,60 +718,69 @@ __host__ __device__ inline int64_t linv_slot_floats(int np, bool inplace) {
   return inplace ? (((int64_t)np + 3) & ~3LL) + tri_sz(np) : linv_group_off(np, (np + 31) / 32);
 }
 
-// L^{-1} of the cells with N <= 96, one warp per cell (persistent).  Shared memory holds L in FP32 with
-// every row padded to a multiple of four floats (row i at lrow_off(i)), the reciprocal diagonal, and the 32
-// columns of the current group of X = L^{-1}, one per lane, stored column-major (Xt[c xs + i] = X[i][base +
-// c], xs = 4 mod 32 so that the lanes' 16-byte loads are conflict-free).  A lane computes its column by
-// forward substitution four rows at a time, walking k four at a time with 16-byte loads: five loads feed
-// sixteen FFMAs (the L rows are broadcasts).  The group's columns are then written in the 8-row blocked
-// layout and as the tensor-core images (coalesced float4 stores along the rows).
+// L^{-1} of the cells with N <= 256, a CTA of W warps per cell (persistent).  Shared memory holds L in FP32
+// with every row padded to a multiple of four floats (row i at lrow_off(i)), the reciprocal diagonal, and per
+// warp the 32 columns of its current group of X = L^{-1}, one per lane, stored column-major (Xt[c xs + i] =
+// X[i][base + c], xs = 4 mod 32 so that the lanes' 16-byte loads are conflict-free).  The 32-column groups
+// are independent (each reads only L): with two warps they are dealt out so that the warps' work, which
+// falls with the group's first row, balances (0, 3, 4, 7, ... and 1, 2, 5, 6, ...).  A lane computes its
+// column by forward substitution four rows at a time, walking k four at a time with 16-byte loads: five
+// loads feed sixteen FFMAs (the L rows are broadcasts).  The group's columns are then written in the 8-row
+// blocked layout and as the tensor-core images (coalesced float4 stores along the rows).
 __host__ __device__ inline int lrow_off(int i) {
   const int q = i >> 2, r = i & 3;
   return 4 * (2 * q * (q + 1) + r * (q + 1));
 }
 __host__ __device__ inline int linv_small_stride(int np) { return 32 * ((np + 31) / 32) + 4; }
-__host__ __device__ inline int64_t linv_small_floats(int np) {
-  return lrow_off(np) + ((np + 3) & ~3) + 32LL * linv_small_stride(np);
+__host__ __device__ inline int64_t linv_small_floats(int np, int warps) {
+  return lrow_off(np) + ((np + 3) & ~3) + 32LL * warps * linv_small_stride(np);
 }
 
-__global__ void __launch_bounds__(32) k_linv_small(LinvArgs a) {
+template <int W>
+__global__ void __launch_bounds__(32 * W) k_linv_small(LinvArgs a) {
   extern __shared__ __align__(16) float smf[];
-  const int lane = threadIdx.x;
+  __shared__ int s_cell;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = a.np;
   float* L = smf;
   float* dg = smf + lrow_off(np);
   const int xs = linv_small_stride(np);
-  float* Xt = dg + ((np + 3) & ~3);
+  float* Xt = dg + ((np + 3) & ~3) + (int64_t)warp * 32 * xs;  // this warp's group buffer
   float* xc = Xt + lane * xs;  // this lane's column of the current group
   for (;;) {
-    int w = 0;
-    if (lane == 0) w = atomicAdd(a.counter, 1);
-    w = __shfl_sync(0xffffffffu, w, 0);
-    if (w >= a.count) break;
-    const int g = (int)a.order[a.first + w];
+    if (tid == 0) {
+      const int w = atomicAdd(a.counter, 1);
+      s_cell = w < a.count ? (int)a.order[a.first + w] : -1;
+    }
+    __syncthreads();
+    const int g = s_cell;
+    if (g < 0) break;
     const int N = a.n32[g];
-    if (N == 0 || a.status[g] != KSDF_CELL_OK) continue;
+    if (N == 0 || a.status[g] != KSDF_CELL_OK) {
+      __syncthreads();
+      continue;
+    }
     // L: binary64 packed rows -> FP32 padded rows, eight loads in flight per lane; a lane walks its (row,
     // column) forward by 32 entries per load
     {
       const int64_t T = tri_sz(N);
       const double* Ld = a.chol64 + a.chol_off[g];
-      int ri = 0, rk = lane;
+      int ri = 0, rk = tid;
       while (rk > ri) {
         rk -= ri + 1;
         ++ri;
       }
-      for (int64_t e0 = lane; e0 < T; e0 += 256) {
+      for (int64_t e0 = tid; e0 < T; e0 += 8 * 32 * W) {
         double v[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-          const int64_t e = e0 + 32 * r;
+          const int64_t e = e0 + 32 * W * r;
           v[r] = e < T ? Ld[e] : 0.0;
         }
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-          if (e0 + 32 * r < T) L[lrow_off(ri) + rk] = d2f_bits(v[r]);
-          rk += 32;
+          if (e0 + 32 * W * r < T) L[lrow_off(ri) + rk] = d2f_bits(v[r]);
+          rk += 32 * W;
           while (rk > ri) {
             rk -= ri + 1;
             ++ri;
@@ -765,12 +788,14 @@ __global__ void __launch_bounds__(32) k_linv_small(LinvArgs a) {
         }
       }
     }
-    __syncwarp();
-    for (int i = lane; i < N; i += 32) dg[i] = 1.f / L[lrow_off(i) + i];
-    __syncwarp();
+    __syncthreads();
+    for (int i = tid; i < N; i += 32 * W) dg[i] = 1.f / L[lrow_off(i) + i];
+    __syncthreads();
     float* Iout = a.linv32 + a.linv_off[g];
     const int nR = (N + 7) >> 3;
     for (int base = 0; base < N; base += 32) {
+      const int grp = base >> 5;
+      if (W == 2 && (((grp >> 1) ^ grp) & 1) != warp) continue;  // the other warp's group
       const int j = base + lane;
       for (int i0 = base; i0 < N; i0 += 4) {
         const float* L0 = L + lrow_off(i0);
@@ -849,6 +874,7 @@ __global__ void __launch_bounds__(32) k_linv_small(LinvArgs a) {
       }
       __syncwarp();
     }
+    __syncthreads();  // L and dg are reused by the next cell
   }
 }
 
@@ -1269,7 +1295,8 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     first += cnt[cl];
     const int team = cls[cl].team;
     f.np = cls[cl].gmat ? std::max(m.max_n, 1) : cls[cl].np;
-    const size_t smem = sizeof(double) * (size_t)fit_smem_doubles(f.np, !cls[cl].gmat);
+    const size_t smem = sizeof(double) * (size_t)(fit_smem_doubles(f.np, !cls[cl].gmat) +
+                                                  (cls[cl].gmat ? (int64_t)(f.np + 1) * kB : 0));
     const int si = launched % ksdf_ctx::kNumAux;  // auxiliary streams only: the main stream marks the stage end
     cudaStream_t s = c->aux[si];
     ++launched;
@@ -1310,13 +1337,11 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
       la.gstride = 0;
       la.np = f.np;
       if (f.np <= 96) {
-        le = launch_persistent(c, k_linv_small, 32, la, sizeof(float) * (size_t)linv_small_floats(f.np), false, s);
-      } else if (f.np <= 160) {
-        le = launch_persistent(c, k_linv<160, false, false>, 160, la,
-                               sizeof(float) * (size_t)linv_slot_floats(f.np, false), false, s);
-      } else if (f.np <= 224 && !cls[cl].gmat) {
-        le = launch_persistent(c, k_linv<224, false, false>, 224, la,
-                               sizeof(float) * (size_t)linv_slot_floats(f.np, false), false, s);
+        le = launch_persistent(c, k_linv_small<1>, 32, la, sizeof(float) * (size_t)linv_small_floats(f.np, 1), false,
+                               s);
+      } else if (f.np <= kTcMaxN) {
+        le = launch_persistent(c, k_linv_small<2>, 64, la, sizeof(float) * (size_t)linv_small_floats(f.np, 2), false,
+                               s);
       } else {
         la.gstride = (linv_slot_floats(f.np, false) + 3) & ~3LL;
         const int64_t slots = std::min<int64_t>(f.count, c->num_sms);
