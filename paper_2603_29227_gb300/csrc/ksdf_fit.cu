@@ -602,7 +602,10 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
       const int w = ke - kb;
       const int nbk = (N + 2 - ke) >> 1;  // 2-row blocks over rows ke..N
       const int64_t nblk = tri_sz(nbk);
-      for (int64_t t = tid; t < nblk; t += TEAM) {
+      // full rounds of 2 x 2 blocks (every thread busy); the last, partial round is done as single entries
+      // below (a warp instruction costs the same FP64 pipe time however few lanes it has)
+      const int64_t nfull = (nblk / TEAM) * TEAM;
+      for (int64_t t = tid; t < nfull; t += TEAM) {
         const int I = tri_row(t), J = (int)(t - tri_sz(I));
         const int i0 = ke + 2 * I, j0 = ke + 2 * J, i1 = i0 + 1, j1 = j0 + 1;
         const bool vi1 = i1 <= N, v01 = j1 <= i0, vj1 = j1 <= N;
@@ -631,6 +634,21 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
         if (vi1) {
           Ai1[j0] = a10;
           Ai1[j1] = a11;
+        }
+      }
+      for (int64_t e = tid; e < 4 * (nblk - nfull); e += TEAM) {
+        const int64_t t = nfull + (e >> 2);
+        const int I = tri_row(t), J = (int)(t - tri_sz(I));
+        const int i = ke + 2 * I + (int)((e >> 1) & 1), j = ke + 2 * J + (int)(e & 1);
+        if (i <= N && j <= i) {
+          double* Aij = A + tri_sz(i) + j;
+          const double* Li = GMAT ? P + (i - kb) * kB : A + tri_sz(i) + kb;
+          const double* Lj = GMAT ? P + (j - kb) * kB : A + tri_sz(j) + kb;
+          double acc = *Aij;
+#pragma unroll
+          for (int k = 0; k < kB; ++k)
+            if (k < w) acc = fma(-Li[k], Lj[k], acc);
+          *Aij = acc;
         }
       }
       fit_sync(TEAM);
