@@ -133,8 +133,11 @@ __device__ void smem_bitonic(int* a, int n) {
   }
 }
 
-// training set of one cell per CTA: collection-box members, ascending global id, rank-selected cap
-__global__ void __launch_bounds__(512) k_assemble(const uint64_t* cell_key, int64_t G, const int64_t* own_off,
+// training set of one cell per CTA: collection-box members, ascending global id, rank-selected cap.  128
+// threads: the neighbour cells' scans spread over four warps, and a cell's candidates (tens to a few
+// hundred) sort with few idle threads at the bitonic network's barriers
+constexpr int kAssembleThreads = 128;
+__global__ void __launch_bounds__(kAssembleThreads) k_assemble(const uint64_t* cell_key, int64_t G, const int64_t* own_off,
                                                   const uint32_t* own_id, const double* x, Params p, int R,
                                                   const uint64_t* hk, const int32_t* hv, uint64_t hcap,
                                                   int32_t* mpad, int64_t* n_out, int32_t* status, int* max_n,
@@ -1170,7 +1173,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   int64_t* tc64 = lb64 + (G + 1);
   int* dmax = bbox + 6;
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
-  launch(k_assemble, (unsigned)G, 512, 0, st, ptr<uint64_t>(m.key), G, own_off, vals, x, p, R, ptr<uint64_t>(m.hkeys),
+  launch(k_assemble, (unsigned)G, kAssembleThreads, 0, st, ptr<uint64_t>(m.key), G, own_off, vals, x, p, R, ptr<uint64_t>(m.hkeys),
          ptr<int32_t>(m.hvals), cap, ptr<int32_t>(m.mpad), n64, ptr<int32_t>(m.status), dmax, stw);
   launch(k_sizes, ceil_div(G, 256), 256, 0, st, n64, G, tri64, lb64, tc64, ptr<int32_t>(m.n));
   KSDF_CUDA(c, scan_i64(n64, ptr<int64_t>(m.ts_off), G, dtot, c->ws[WS_SCAN], st));
