@@ -493,30 +493,44 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
     const int b = tile.x;
     int bc[3];
     unpack_key(a.bin_key[b], bc[0], bc[1], bc[2]);
-    if (tid == 0) {
+    if (tid < 32) {
+      // the first warp sets the tile up, a lane per candidate (their loads and FP64 offsets in parallel):
+      // offsets of the candidates' padded sample runs by a warp scan, then one bulk copy per lane
+      const int lane = tid;
       const int nc = a.ncand[b];
-      s_nc = nc;
-      uint32_t bytes = 0;
-      int base = 0;
-      for (int k = 0; k < nc; ++k) {
-        const int g = a.cand[(int64_t)b * p.K + k];
-        const int n = a.cell_n[g];
-        s_c[k] = g;
-        s_n[k] = n;
-        s_base[k] = base;
+      int g = -1, n = 0;
+      if (lane < nc) {
+        g = a.cand[(int64_t)b * p.K + lane];
+        n = a.cell_n[g];
+      }
+      const int pad = (n + 7) & ~7;  // each candidate padded to a multiple of 8 samples
+      int incl = pad;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int base = incl - pad;
+      int bytes = n * 16;
+      for (int o = 16; o; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+      if (lane < nc) {
+        s_c[lane] = g;
+        s_n[lane] = n;
+        s_base[lane] = base;
         int cc[3];
         unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
-        for (int j = 0; j < 3; ++j) s_off[k][j] = (float)((double)(bc[j] - cc[j]) * p.h);
-        base += (n + 7) & ~7;  // each candidate padded to a multiple of 8 samples
-        bytes += (uint32_t)n * 16u;
+        for (int j = 0; j < 3; ++j) s_off[lane][j] = (float)((double)(bc[j] - cc[j]) * p.h);
       }
-      fence_proxy_async();
-      mbar_expect_tx(&bar, bytes);
-      for (int k = 0; k < nc; ++k)
-        bulk_g2s(s_x + s_base[k], a.mf4 + a.ts_off[s_c[k]], (uint32_t)s_n[k] * 16u, &bar);
+      if (lane < 3) base_split(p.o[lane], bc[lane], p.h, s_bh[lane], s_bl[lane]);
+      if (lane == 0) {
+        s_nc = nc;
+        mbar_expect_tx(&bar, (uint32_t)bytes);
+      }
+      __syncwarp();
+      if (lane < nc && n > 0) {
+        fence_proxy_async();
+        bulk_g2s(s_x + base, a.mf4 + a.ts_off[g], (uint32_t)n * 16u, &bar);
+      }
     }
-    if (tid == 0)
-      for (int j = 0; j < 3; ++j) base_split(p.o[j], bc[j], p.h, s_bh[j], s_bl[j]);
     __syncthreads();  // candidate list known
     // padding samples: far away with zero weight, so that every chunk of 8 is full (no per-sample guards)
     for (int e = tid; e < s_nc * 8; e += blockDim.x) {
