@@ -74,6 +74,7 @@ def _load():
         lib.ko_query.argtypes = [P, P, i64, P, P, P, P, P, P, P, P, P]
         lib.ko_query_f64.argtypes = [P, P, i64, P, P, P, P, P, P, P]
         lib.ko_eval_cell.argtypes = [P, P, i64, P, P, P, P, P, P, P]
+        lib.ko_var_grad.argtypes = [P, P, i64, P, P]
         lib.ko_backward.argtypes = [P, P, i64, P, P, P, P, P, P]
         lib.ko_backward_f64.argtypes = [P, P, i64, P, P, P, P, P, P]
         _lib = lib
@@ -222,6 +223,16 @@ class Model:
                                   _ptr(out["var_sdf"]), _ptr(out["var_f"]), _ptr(out["winner"]), _ptr(out["flags"]))
         if rc:
             raise ValueError("ko_query_f64 failed (%d)" % rc)
+        return out
+
+    def var_grad(self, xq, cell):
+        """SDF-gradient variance (Sec. IV-B.3, App. C) of float32 points on the given cells: Q x dim float64."""
+        xq = np.ascontiguousarray(xq, dtype=np.float32).reshape(-1, self.dim)
+        cell = np.ascontiguousarray(cell, dtype=np.int32)
+        out = np.empty((xq.shape[0], self.dim))
+        rc = _load().ko_var_grad(self._h, _ptr(xq), xq.shape[0], _ptr(cell), _ptr(out))
+        if rc:
+            raise ValueError("ko_var_grad failed (%d)" % rc)
         return out
 
     def eval_cell(self, xq, cell, sign=None):

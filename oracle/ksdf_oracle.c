@@ -11,6 +11,7 @@
  *   adaptive scaling                      App. D (gamma from the distance d to the nearest sample)
  *   min-fusion of the K nearest GPs       Sec. IV-B.1
  *   softmin UDF variance                  Sec. IV-B.3
+ *   SDF-gradient variance                 Sec. IV-B.3 (gradient-variance approximation) and App. C
  *   SDF = sign * UDF                      Sec. IV-B.1 (d = s u), sign from the caller or a stand-in
  *
  * Readings where the paper is silent (each is also listed in the design notes):
@@ -22,7 +23,10 @@
  *   - d in the scaling is the distance to the GP's nearest training sample (so max k' = 1);
  *   - f' <= 0 gives u = d (flagged); a negative argument of the square root is clamped to 0;
  *   - the softmin alpha defaults to lambda (the kernel ablation treats them as the same scale);
- *   - winner ties go to the first candidate in list order; the nearest sample tie to the lowest id.
+ *   - winner ties go to the first candidate in list order; the nearest sample tie to the lowest id;
+ *   - in App. C the matrix printed for grad_{x_i} g has grad_{x_i} g_k as its k-th column (its first term
+ *     is v_i w^T: column k is w_k v_i, the derivative of g_k along x_i); V[grad_k u] sums the squared norms
+ *     of those columns; a query on a sample (z_i = 0, direction undefined) gets +inf.
  * Parity of every function here is pinned by tests/test_oracle_*.py (closed forms, brute force,
  * limits, invariants, finite differences).
  */
@@ -722,6 +726,90 @@ int ko_eval_cell(const ko_model* m, const float* xq, int64_t Q, const int32_t* c
   int rc = query_impl(m, x, Q, sign, cell, sdf, grad, var_sdf, var_f, NULL, flags, NULL, NULL);
   free(x);
   return rc;
+}
+
+/* SDF-gradient variance (Sec. IV-B.3, App. C) of the queries xq on the given cells: with z_i = |x - x_i|,
+ * v_i = (x - x_i) / z_i, softmin weights s_i = e^{-a z_i} / sum_j e^{-a z_j}, h = s^T z,
+ * l_i = s_i (a s^T z - a z_i + 1), V = [v_1 .. v_N], g = V (a s s^T z - a diag(s) z + s) (the gradient of h),
+ * the matrix of App. C
+ *     M_i = a v_i (l_i (v_i - V s) + s_i (v_i - g))^T + (l_i / z_i) (v_i v_i^T - I),
+ * whose k-th column is grad_{x_i} g_k, and V[grad_k u] = sum_i |M_i[:, k]|^2 sigma_i^2.  var_grad is Q x dim. */
+int ko_var_grad(const ko_model* m, const float* xq, int64_t Q, const int32_t* cell, double* var_grad) {
+  if (!m || Q < 0 || (Q > 0 && (!xq || !cell || !var_grad))) return KO_ERR_ARG;
+  const int dim = m->dim;
+  const double a = alpha_softmin(&m->p);
+  for (int64_t q = 0; q < Q; ++q)
+    if (cell[q] < 0 || cell[q] >= m->G || m->status[cell[q]] != KO_CELL_OK) return KO_ERR_ARG;
+  const int64_t NM = max_ts(m);
+  int fail = 0;
+#pragma omp parallel
+  {
+    double* z = (double*)malloc(sizeof(double) * (size_t)NM);
+    double* sw = (double*)malloc(sizeof(double) * (size_t)NM);
+    double* vv = (double*)malloc(sizeof(double) * (size_t)NM * 3);
+    if (!z || !sw || !vv) fail = 1;
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t q = 0; q < Q; ++q) {
+      if (fail) continue;
+      double x[3] = {0, 0, 0};
+      for (int j = 0; j < dim; ++j) x[j] = (double)xq[q * dim + j];
+      const int64_t g = cell[q];
+      const int64_t* ids = m->ts_id + m->ts_off[g];
+      const int64_t N = m->ts_off[g + 1] - m->ts_off[g];
+      double* out = var_grad + q * dim;
+      int on_sample = 0;
+      double zmin = INFINITY;
+      for (int64_t i = 0; i < N; ++i) {
+        const double* xi = m->x + ids[i] * dim;
+        z[i] = sqrt(sqdist(x, xi, dim));
+        if (z[i] == 0.0) on_sample = 1;
+        for (int j = 0; j < dim; ++j) vv[i * 3 + j] = z[i] > 0.0 ? (x[j] - xi[j]) / z[i] : 0.0;
+        if (z[i] < zmin) zmin = z[i];
+      }
+      if (on_sample) {
+        for (int j = 0; j < dim; ++j) out[j] = INFINITY;
+        continue;
+      }
+      /* softmin weights (the common factor e^{a zmin} cancels) and h = s^T z */
+      double W = 0.0;
+      for (int64_t i = 0; i < N; ++i) {
+        sw[i] = exp(-a * (z[i] - zmin));
+        W += sw[i];
+      }
+      double sz = 0.0;
+      for (int64_t i = 0; i < N; ++i) {
+        sw[i] /= W;
+        sz += sw[i] * z[i];
+      }
+      /* V s and g = V (a s s^T z - a diag(s) z + s) */
+      double Vs[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
+      for (int64_t i = 0; i < N; ++i) {
+        const double coef = a * sw[i] * sz - a * sw[i] * z[i] + sw[i];
+        for (int j = 0; j < dim; ++j) {
+          Vs[j] += vv[i * 3 + j] * sw[i];
+          gv[j] += vv[i * 3 + j] * coef;
+        }
+      }
+      for (int k = 0; k < dim; ++k) out[k] = 0.0;
+      for (int64_t i = 0; i < N; ++i) {
+        const double* v = vv + i * 3;
+        const double li = sw[i] * (a * sz - a * z[i] + 1.0);
+        double w[3];
+        for (int j = 0; j < dim; ++j) w[j] = li * (v[j] - Vs[j]) + sw[i] * (v[j] - gv[j]);
+        double M[3][3];
+        for (int r = 0; r < dim; ++r)
+          for (int c = 0; c < dim; ++c) M[r][c] = a * v[r] * w[c] + (li / z[i]) * (v[r] * v[c] - (r == c ? 1.0 : 0.0));
+        const double s2 = m->var[ids[i]];
+        for (int k = 0; k < dim; ++k) {
+          double col = 0.0;
+          for (int r = 0; r < dim; ++r) col += M[r][k] * M[r][k];
+          out[k] += col * s2;
+        }
+      }
+    }
+    free(z); free(sw); free(vv);
+  }
+  return fail ? KO_ERR_MEM : KO_OK;
 }
 
 /* ------------------------------------------------------------------------------------------------ */

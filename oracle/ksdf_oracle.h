@@ -86,6 +86,10 @@ int ko_query(const ko_model* m, const float* xq, int64_t Q, const int8_t* sign, 
              double* var_sdf, double* var_f, int32_t* winner, uint32_t* flags, double* cand_u, int32_t* cand_id);
 
 /* Same outputs, but evaluated with the given cell as the winner for each query (cell[q] >= 0). */
+/* SDF-gradient variance (Sec. IV-B.3, App. C) of queries xq (Q x dim float32) on the cells cell[Q] (each an
+ * OK cell): var_grad (Q x dim float64).  A query on a training sample gets +inf. */
+int ko_var_grad(const ko_model* m, const float* xq, int64_t Q, const int32_t* cell, double* var_grad);
+
 int ko_eval_cell(const ko_model* m, const float* xq, int64_t Q, const int32_t* cell, const int8_t* sign,
                  double* sdf, double* grad, double* var_sdf, double* var_f, uint32_t* flags);
 
