@@ -81,7 +81,8 @@ enum {
   KSDF_OUT_VAR_F = 8u,
   KSDF_OUT_WINNER = 16u,
   KSDF_OUT_FLAGS = 32u,
-  KSDF_OUT_ALL = 63u
+  KSDF_OUT_ALL = 63u,     /* the six outputs above */
+  KSDF_OUT_VAR_GRAD = 64u /* optional: the SDF-gradient variance (one more pass over the winner's samples) */
 };
 
 /* Per-query flag bits. */
@@ -159,14 +160,17 @@ ksdf_status ksdf_fp64_rate(ksdf_ctx* ctx, double* tflops);
  * GP variance contraction K' L^{-T} on the tensor cores in TF32 split three ways (hi*hi + hi*lo + lo*hi,
  * FP32 accumulation) for winner cells of up to 256 samples, in FP32 SIMT beyond.  Outputs (selected by
  * out_mask): sdf[Q], grad[Q x dim] (gradient of d = s grad u), var_sdf[Q] (V[u], Sec. IV-B.3),
- * var_f[Q] (V[f], Sec. IV-B.1), winner[Q] (cell id of the fused GP, -1 if none; keep it for the
- * backward), flags[Q] (KSDF_FLAG_*). */
+ * var_f[Q] (V[f], Sec. IV-B.1), var_grad[Q x dim] (only with KSDF_OUT_VAR_GRAD: V[grad_k u] of Sec. IV-B.3 /
+ * App. C, the surface-sample variances propagated through the softmin's gradient on the winner; +inf for a
+ * query on a sample, 0 without a GP), winner[Q] (cell id of the fused GP, -1 if none; keep it for the
+ * backward), flags[Q] (KSDF_FLAG_*).  Outputs not selected may be NULL. */
 ksdf_status ksdf_query(ksdf_ctx* ctx, const float* xq, int64_t Q, const int8_t* sign, uint32_t out_mask, float* sdf,
-                       float* grad, float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags);
+                       float* grad, float* var_sdf, float* var_f, float* var_grad, int32_t* winner, uint32_t* flags);
 
 /* The same query in FP64 end to end on the GPU (the plain path): xq and the outputs are float64. */
 ksdf_status ksdf_query_f64(ksdf_ctx* ctx, const double* xq, int64_t Q, const int8_t* sign, uint32_t out_mask,
-                           double* sdf, double* grad, double* var_sdf, double* var_f, int32_t* winner, uint32_t* flags);
+                           double* sdf, double* grad, double* var_sdf, double* var_f, double* var_grad,
+                           int32_t* winner, uint32_t* flags);
 
 /* Adjoint of the query (the spec differentiation path): given the cotangents d_sdf[Q] and
  * (optionally, may be NULL) d_grad[Q x dim] of the sdf and grad outputs, write d_xq[Q x dim] (overwritten)

@@ -352,17 +352,17 @@ ksdf_status ksdf_fit(ksdf_ctx* c, const double* x, const float* var, const float
 }
 
 static ksdf_status query_common(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const int8_t* sign,
-                                uint32_t mask, void* sdf, void* grad, void* var_sdf, void* var_f, int32_t* winner,
-                                uint32_t* flags) {
+                                uint32_t mask, void* sdf, void* grad, void* var_sdf, void* var_f, void* var_grad,
+                                int32_t* winner, uint32_t* flags) {
   if (!c) return KSDF_ERR_ARG;
   if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "query before a successful fit");
   if (Q < 0 || (Q > 0 && !xq)) return set_err(c, KSDF_ERR_ARG, "query: bad Q or NULL points");
   if (Q >= (1LL << 31)) return set_err(c, KSDF_ERR_CAPACITY, "query: Q must be < 2^31");
   if (Q == 0) return KSDF_OK;  // empty arrays may carry NULL pointers
-  mask &= KSDF_OUT_ALL;
+  mask &= KSDF_OUT_ALL | KSDF_OUT_VAR_GRAD;
   if (((mask & KSDF_OUT_SDF) && !sdf) || ((mask & KSDF_OUT_GRAD) && !grad) || ((mask & KSDF_OUT_VAR_SDF) && !var_sdf) ||
       ((mask & KSDF_OUT_VAR_F) && !var_f) || ((mask & KSDF_OUT_WINNER) && !winner) ||
-      ((mask & KSDF_OUT_FLAGS) && !flags))
+      ((mask & KSDF_OUT_FLAGS) && !flags) || ((mask & KSDF_OUT_VAR_GRAD) && !var_grad))
     return set_err(c, KSDF_ERR_ARG, "query: an output selected by out_mask is NULL");
   if (Q == 0) return KSDF_OK;
   const int dim = c->p.dim;
@@ -371,28 +371,29 @@ static ksdf_status query_common(ksdf_ctx* c, const void* xq, bool f64, int64_t Q
   ksdf_status s;
   if ((s = stage_in(c, 0, xq, fs * Q * dim, &dxq))) return s;
   if ((s = stage_in(c, 1, sign, sizeof(int8_t) * Q, &dsg))) return s;
-  OutStage o[6];
+  OutStage o[7];
   if ((s = stage_out(c, 2, (mask & KSDF_OUT_SDF) ? sdf : nullptr, fs * Q, false, &o[0]))) return s;
   if ((s = stage_out(c, 3, (mask & KSDF_OUT_GRAD) ? grad : nullptr, fs * Q * dim, false, &o[1]))) return s;
   if ((s = stage_out(c, 4, (mask & KSDF_OUT_VAR_SDF) ? var_sdf : nullptr, fs * Q, false, &o[2]))) return s;
   if ((s = stage_out(c, 5, (mask & KSDF_OUT_VAR_F) ? var_f : nullptr, fs * Q, false, &o[3]))) return s;
   if ((s = stage_out(c, 6, (mask & KSDF_OUT_WINNER) ? winner : nullptr, sizeof(int32_t) * Q, false, &o[4]))) return s;
   if ((s = stage_out(c, 7, (mask & KSDF_OUT_FLAGS) ? flags : nullptr, sizeof(uint32_t) * Q, false, &o[5]))) return s;
+  if ((s = stage_out(c, 8, (mask & KSDF_OUT_VAR_GRAD) ? var_grad : nullptr, fs * Q * dim, false, &o[6]))) return s;
   s = run_query(c, dxq, f64, Q, static_cast<const int8_t*>(dsg), mask, o[0].dev, o[1].dev, o[2].dev, o[3].dev,
-                static_cast<int32_t*>(o[4].dev), static_cast<uint32_t*>(o[5].dev));
+                o[6].dev, static_cast<int32_t*>(o[4].dev), static_cast<uint32_t*>(o[5].dev));
   if (s) return s;
-  return finish_out(c, o, 6);
+  return finish_out(c, o, 7);
 }
 
 ksdf_status ksdf_query(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, uint32_t out_mask, float* sdf,
-                       float* grad, float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags) {
-  return query_common(c, xq, false, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags);
+                       float* grad, float* var_sdf, float* var_f, float* var_grad, int32_t* winner, uint32_t* flags) {
+  return query_common(c, xq, false, Q, sign, out_mask, sdf, grad, var_sdf, var_f, var_grad, winner, flags);
 }
 
 ksdf_status ksdf_query_f64(ksdf_ctx* c, const double* xq, int64_t Q, const int8_t* sign, uint32_t out_mask,
-                           double* sdf, double* grad, double* var_sdf, double* var_f, int32_t* winner,
-                           uint32_t* flags) {
-  return query_common(c, xq, true, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags);
+                           double* sdf, double* grad, double* var_sdf, double* var_f, double* var_grad,
+                           int32_t* winner, uint32_t* flags) {
+  return query_common(c, xq, true, Q, sign, out_mask, sdf, grad, var_sdf, var_f, var_grad, winner, flags);
 }
 
 ksdf_status ksdf_query_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, const int32_t* winner,

@@ -242,7 +242,7 @@ ksdf_status bin_points(ksdf_ctx* c, const double* x, int64_t n, uint64_t* keys);
 
 // ---- query (ksdf_query.cu) ----
 ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const int8_t* sign, uint32_t mask, void* sdf,
-                      void* grad, void* var_sdf, void* var_f, int32_t* winner, uint32_t* flags);
+                      void* grad, void* var_sdf, void* var_f, void* var_grad, int32_t* winner, uint32_t* flags);
 ksdf_status candidates_for_keys(ksdf_ctx* c, const uint64_t* keys, int64_t n, int32_t* cand, int32_t* count);
 ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G);
 

@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(kTA) k_phaseA64(PhaseAArgs a, const double* xq
 template <class T>
 __global__ void k_w_rank(const int32_t* qwin, const uint32_t* qflag, const int32_t* qbin, int64_t Q, int32_t* wrank,
                          int64_t* wcnt, uint32_t mask, int dim, T* sdf, T* grad, T* var_sdf, T* var_f,
-                         int32_t* winner, uint32_t* flags) {
+                         T* var_grad, int32_t* winner, uint32_t* flags) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= Q) return;
   const int w = qbin[q] < 0 ? -1 : qwin[q];
@@ -748,6 +748,8 @@ __global__ void k_w_rank(const int32_t* qwin, const uint32_t* qflag, const int32
     for (int j = 0; j < dim; ++j) grad[q * dim + j] = invalid ? nan : (T)0;
   if (mask & KSDF_OUT_VAR_SDF) var_sdf[q] = invalid ? nan : (T)0;
   if (mask & KSDF_OUT_VAR_F) var_f[q] = invalid ? nan : (T)1;
+  if (mask & KSDF_OUT_VAR_GRAD)
+    for (int j = 0; j < dim; ++j) var_grad[q * dim + j] = invalid ? nan : (T)0;
   if (mask & KSDF_OUT_WINNER) winner[q] = -1;
   if (mask & KSDF_OUT_FLAGS) flags[q] = invalid ? KSDF_FLAG_INVALID : (qflag[q] | KSDF_FLAG_NO_GP);
 }
@@ -1480,6 +1482,147 @@ __global__ void __launch_bounds__(kTB64) k_phaseB64(PhaseBArgs a, const double* 
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
+// Q7 (optional output): SDF-gradient variance, Sec. IV-B.3 and App. C
+//
+// Per tile of queries of one winner cell, one thread per query over the cell's samples (staged in shared
+// memory with their variances), three passes:
+//   1. z_min;
+//   2. with y_i = z_i - z_min and e_i = e^{-a y_i} (the softmin's common factor e^{-a z_min} divided out):
+//      W = sum e_i, HY = sum e_i y_i, SV = sum e_i v_i, SYV = sum e_i y_i v_i; then s_i = e_i / W,
+//      B = a HY / W + 1 (so that l_i = s_i (a s^T z - a z_i + 1) = s_i (B - a y_i)), V s = SV / W and
+//      g = sum_i l_i v_i = (B SV - a SYV) / W;
+//   3. V[grad_k u] = sum_i sigma_i^2 |grad_{x_i} g_k|^2 with grad_{x_i} g_k = (a w_k + c_i v_k) v_i - c_i e_k,
+//      w = l_i (v_i - V s) + s_i (v_i - g), c_i = l_i / z_i; since |v_i| = 1 the squared norm is
+//      a^2 w_k^2 + c_i^2 (1 - v_k^2), and 1 - v_k^2 is formed as (r^2 - r_k^2) / r^2 (no cancellation).
+// A query on a sample (r^2 = 0) gets +inf.  FP32 (mixed path; ex2.approx for the weights) or FP64.
+constexpr int kVG = 128;
+
+struct VarGradArgs {
+  const int4* tiles;
+  const int64_t* n_tiles;
+  int* counter;
+  const int32_t* sorted_w;
+  const int64_t* ts_off;
+  const int32_t* cell_n;
+  const uint64_t* cell_key;
+  const float4* mf4;
+  const D4* md4;
+  const float* mvar;
+};
+
+template <class T>
+struct VgRec;
+template <>
+struct VgRec<float> {
+  typedef float4 R;
+};
+template <>
+struct VgRec<double> {
+  typedef D4 R;
+};
+
+template <class T>
+__device__ __forceinline__ T vg_exp(T x);  // e^x for x <= 0
+template <>
+__device__ __forceinline__ float vg_exp<float>(float x) { return ex2(x * kLog2e); }
+template <>
+__device__ __forceinline__ double vg_exp<double>(double x) { return exp(x); }
+
+template <class T>
+__global__ void __launch_bounds__(kVG) k_var_grad(VarGradArgs a, const T* xq, Params p, T* var_grad) {
+  typedef typename VgRec<T>::R R;
+  extern __shared__ __align__(32) unsigned char vg_sm[];
+  R* sx = reinterpret_cast<R*>(vg_sm);  // cell-local (x, y, z) and sigma^2
+  __shared__ int s_tile;
+  __shared__ int s_cc[3];
+  __shared__ float s_bh[3], s_bl[3];
+  const T al = (T)p.alpha_s;
+  const int dim = p.dim;
+  const int64_t ntiles = *a.n_tiles;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const int4 tile = a.tiles[t];
+    const int g = tile.x, n = a.cell_n[g];
+    const int64_t m0 = a.ts_off[g];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      R v;
+      if constexpr (sizeof(T) == 4) v = a.mf4[m0 + i];
+      else v = a.md4[m0 + i];
+      v.w = (T)a.mvar[m0 + i];
+      sx[i] = v;
+    }
+    if (threadIdx.x == 0) unpack_key(a.cell_key[g], s_cc[0], s_cc[1], s_cc[2]);
+    __syncthreads();
+    if (threadIdx.x < 3) base_split(p.o[threadIdx.x], s_cc[threadIdx.x], p.h, s_bh[threadIdx.x], s_bl[threadIdx.x]);
+    __syncthreads();
+    for (int qi = threadIdx.x; qi < tile.z; qi += blockDim.x) {
+      const int q = a.sorted_w[tile.y + qi];
+      T x[3] = {(T)0, (T)0, (T)0};
+      for (int j = 0; j < dim; ++j) {
+        if constexpr (sizeof(T) == 4) x[j] = local32(xq[(int64_t)q * dim + j], s_bh[j], s_bl[j]);
+        else x[j] = __dsub_rn(xq[(int64_t)q * dim + j], cell_base(p.o[j], s_cc[j], p.h));
+      }
+      T* out = var_grad + (int64_t)q * dim;
+      T r2min = (T)INFINITY;
+      for (int i = 0; i < n; ++i) {
+        const R v = sx[i];
+        const T rx = x[0] - (T)v.x, ry = x[1] - (T)v.y, rz = x[2] - (T)v.z;
+        r2min = fmin(r2min, rx * rx + ry * ry + rz * rz);
+      }
+      if (!(r2min > (T)0)) {
+        for (int j = 0; j < dim; ++j) out[j] = (T)INFINITY;
+        continue;
+      }
+      const T zmin = sqrt(r2min);
+      T W = 0, HY = 0, SV[3] = {0, 0, 0}, SYV[3] = {0, 0, 0};
+      for (int i = 0; i < n; ++i) {
+        const R v = sx[i];
+        const T r[3] = {x[0] - (T)v.x, x[1] - (T)v.y, x[2] - (T)v.z};
+        const T r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const T z = sqrt(r2);
+        const T y = z - zmin > (T)0 ? z - zmin : (T)0;
+        const T e = vg_exp<T>(-al * y);
+        const T ez = e / z;
+        W += e;
+        HY += e * y;
+        for (int k = 0; k < 3; ++k) {
+          SV[k] += ez * r[k];
+          SYV[k] += ez * y * r[k];
+        }
+      }
+      const T B = al * HY / W + (T)1;
+      T Vs[3], gg[3];
+      for (int k = 0; k < 3; ++k) {
+        Vs[k] = SV[k] / W;
+        gg[k] = (B * SV[k] - al * SYV[k]) / W;
+      }
+      T acc[3] = {0, 0, 0};
+      for (int i = 0; i < n; ++i) {
+        const R v = sx[i];
+        const T r[3] = {x[0] - (T)v.x, x[1] - (T)v.y, x[2] - (T)v.z};
+        const T r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const T z = sqrt(r2);
+        const T y = z - zmin > (T)0 ? z - zmin : (T)0;
+        const T si = vg_exp<T>(-al * y) / W;
+        const T li = si * (B - al * y);
+        const T ci = li / z;
+        const T s2 = (T)v.w;
+        for (int k = 0; k < dim; ++k) {
+          const T vk = r[k] / z;
+          const T wk = li * (vk - Vs[k]) + si * (vk - gg[k]);
+          acc[k] += s2 * (al * al * wk * wk + ci * ci * ((r2 - r[k] * r[k]) / r2));
+        }
+      }
+      for (int k = 0; k < dim; ++k) out[k] = acc[k];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // host orchestration
 
 static CandCtx cand_ctx(ksdf_ctx* c) {
@@ -1533,7 +1676,7 @@ ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G) {
   KSDF_CUDA(c, ensure(c->ws[WS_BHKEY], sizeof(uint64_t) * bcap));
   // per-slot / per-bin arrays: slot ids, bin keys, counts, offsets, tile counts, tile offsets (+ totals)
   KSDF_CUDA(c, ensure(c->ws[WS_BHVAL], sizeof(int64_t) * (bcap + 1)));
-  KSDF_CUDA(c, ensure(c->ws[WS_BIN], sizeof(int64_t) * (5 * bcap + 8)));
+  KSDF_CUDA(c, ensure(c->ws[WS_BIN], sizeof(int64_t) * (5 * bcap + 10)));
   KSDF_CUDA(c, ensure(c->ws[WS_CAND], sizeof(int32_t) * (bcap * (K + 1))));
   const int64_t max_tiles_a = Q / kTA + bcap + 1;
   const int64_t max_tiles_b = Q / kTB64 + G + 1;  // also covers the mixed path's three tile lists (+ 2 G + 2)
@@ -1545,7 +1688,7 @@ ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G) {
 }
 
 ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const int8_t* sign, uint32_t mask, void* sdf,
-                      void* grad, void* var_sdf, void* var_f, int32_t* winner, uint32_t* flags) {
+                      void* grad, void* var_sdf, void* var_f, void* var_grad, int32_t* winner, uint32_t* flags) {
   cudaStream_t st = c->stream;
   const Params& p = c->p;
   Model& m = c->m;
@@ -1591,7 +1734,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   // Q1 (kEmptyKey is all ones)
   KSDF_CUDA(c, cudaMemsetAsync(bhk, 0xFF, sizeof(uint64_t) * bcap, st));
   KSDF_CUDA(c, cudaMemsetAsync(bin_cnt, 0, sizeof(int64_t) * bcap, st));
-  KSDF_CUDA(c, cudaMemsetAsync(totals, 0, sizeof(int64_t) * 8, st));
+  KSDF_CUDA(c, cudaMemsetAsync(totals, 0, sizeof(int64_t) * 10, st));
   KSDF_CUDA(c, cudaMemsetAsync(wcnt, 0, sizeof(int64_t) * G, st));
   if (f64)
     launch(k_q_bin<double>, ceil_div(Q, 256), 256, 0, st, static_cast<const double*>(xq), Q, p, qkey, bhk, bcap, stw);
@@ -1658,12 +1801,12 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     launch(k_w_rank<double>, ceil_div(Q, 256), 256, 0, st, qwin, qflag, qbin, Q, wrank, wcnt, mask, p.dim,
                                                         static_cast<double*>(sdf), static_cast<double*>(grad),
                                                         static_cast<double*>(var_sdf), static_cast<double*>(var_f),
-                                                        winner, flags);
+                                                        static_cast<double*>(var_grad), winner, flags);
   else
     launch(k_w_rank<float>, ceil_div(Q, 256), 256, 0, st, qwin, qflag, qbin, Q, wrank, wcnt, mask, p.dim,
                                                        static_cast<float*>(sdf), static_cast<float*>(grad),
                                                        static_cast<float*>(var_sdf), static_cast<float*>(var_f),
-                                                       winner, flags);
+                                                       static_cast<float*>(var_grad), winner, flags);
   KSDF_CUDA(c, scan_i64(wcnt, woff, G, nullptr, c->ws[WS_SCAN], st));
   // mixed path: three tile lists by winner-cell size -- tensor-core tiles of kTcM queries for cells of at most
   // kTcSmallN and kTcMaxN samples, SIMT tiles of kBItem for larger cells
@@ -1768,6 +1911,44 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   }
   KSDF_CUDA(c, cudaGetLastError());
   prof_end(c, e0, f64 ? "query64.phaseB" : "query.phaseB");
+  if (mask & KSDF_OUT_VAR_GRAD) {
+    e0 = prof_begin(c);
+    VarGradArgs va;
+    va.sorted_w = qwsort;
+    va.ts_off = ptr<int64_t>(m.ts_off);
+    va.cell_n = ptr<int32_t>(m.n);
+    va.cell_key = ptr<uint64_t>(m.key);
+    va.mf4 = ptr<float4>(m.mf4);
+    va.md4 = ptr<D4>(m.md4);
+    va.mvar = ptr<float>(m.mvar);
+    const int nmax = std::max(m.max_n, 1);
+    // the winner tiles of phase B: one list on the plain path, three on the mixed path (by cell size)
+    const int nlists = f64 ? 1 : 3;
+    const int4* lists[3] = {tiles_b, tiles_b1, tiles_b2};
+    for (int l = 0; l < nlists; ++l) {
+      VarGradArgs v = va;
+      v.tiles = lists[l];
+      v.n_tiles = &totals[3 + l];
+      v.counter = &counters[4 + l];
+      if (f64) {
+        const size_t sm = sizeof(D4) * (size_t)nmax;
+        KSDF_CUDA(c, cudaFuncSetAttribute(k_var_grad<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int occ = 0;
+        KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_var_grad<double>, kVG, sm));
+        launch(k_var_grad<double>, std::max(1, occ) * c->num_sms, kVG, sm, st, v, static_cast<const double*>(xq), p,
+               static_cast<double*>(var_grad));
+      } else {
+        const size_t sm = sizeof(float4) * (size_t)nmax;
+        KSDF_CUDA(c, cudaFuncSetAttribute(k_var_grad<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int occ = 0;
+        KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_var_grad<float>, kVG, sm));
+        launch(k_var_grad<float>, std::max(1, occ) * c->num_sms, kVG, sm, st, v, static_cast<const float*>(xq), p,
+               static_cast<float*>(var_grad));
+      }
+    }
+    KSDF_CUDA(c, cudaGetLastError());
+    prof_end(c, e0, f64 ? "query64.var_grad" : "query.var_grad");
+  }
   prof_end(c, e_q, f64 ? "query64" : "query");
   return KSDF_OK;
 }

@@ -22,6 +22,7 @@ KSDF_OK, KSDF_ERR_ARG, KSDF_ERR_CUDA, KSDF_ERR_NOT_PD, KSDF_ERR_CAPACITY, KSDF_E
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_PD", 4: "ERR_CAPACITY", 5: "ERR_NOT_FITTED",
                 6: "ERR_NONFINITE", 7: "ERR_TIMEOUT"}
 OUT_SDF, OUT_GRAD, OUT_VAR_SDF, OUT_VAR_F, OUT_WINNER, OUT_FLAGS, OUT_ALL = 1, 2, 4, 8, 16, 32, 63
+OUT_VAR_GRAD = 64  # optional: the SDF-gradient variance (Q x dim)
 FLAG_FALLBACK, FLAG_NO_GP, FLAG_NEAR_TIE, FLAG_ZERO_GRAD, FLAG_CLAMPED, FLAG_INVALID = 1, 2, 4, 8, 16, 32
 CELL_OK, CELL_EMPTY, CELL_NOT_PD = 0, 1, 2
 
@@ -64,8 +65,8 @@ def load(path: str = LIB_PATH):
         "ksdf_reserve": [P, I64, I64],
         "ksdf_fit": [P, P, P, P, I64],
         "ksdf_update": [P, P, P, P, I64, ctypes.POINTER(I64)],
-        "ksdf_query": [P, P, I64, P, U32, P, P, P, P, P, P],
-        "ksdf_query_f64": [P, P, I64, P, U32, P, P, P, P, P, P],
+        "ksdf_query": [P, P, I64, P, U32, P, P, P, P, P, P, P],
+        "ksdf_query_f64": [P, P, I64, P, U32, P, P, P, P, P, P, P],
         "ksdf_query_backward": [P, P, I64, P, P, P, P, P, P],
         "ksdf_sync_status": [P],
         "ksdf_last_error": [P],
@@ -206,17 +207,18 @@ def ksdf_update(h, x_new, var_new, normals_new, S_new, allow_not_pd=True):
     return rc, int(n.value)
 
 
-def ksdf_query(h, xq, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags):
+def ksdf_query(h, xq, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags, var_grad=None):
     rc = load().ksdf_query(h, _ptr(xq, np.float32), int(Q), _ptr(sign, np.int8), int(out_mask), _ptr(sdf, np.float32),
                            _ptr(grad, np.float32), _ptr(var_sdf, np.float32), _ptr(var_f, np.float32),
-                           _ptr(winner, np.int32), _ptr(flags, np.uint32))
+                           _ptr(var_grad, np.float32), _ptr(winner, np.int32), _ptr(flags, np.uint32))
     _check(h, rc, "ksdf_query")
 
 
-def ksdf_query_f64(h, xq, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags):
+def ksdf_query_f64(h, xq, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags, var_grad=None):
     rc = load().ksdf_query_f64(h, _ptr(xq, np.float64), int(Q), _ptr(sign, np.int8), int(out_mask),
                                _ptr(sdf, np.float64), _ptr(grad, np.float64), _ptr(var_sdf, np.float64),
-                               _ptr(var_f, np.float64), _ptr(winner, np.int32), _ptr(flags, np.uint32))
+                               _ptr(var_f, np.float64), _ptr(var_grad, np.float64), _ptr(winner, np.int32),
+                               _ptr(flags, np.uint32))
     _check(h, rc, "ksdf_query_f64")
 
 
@@ -380,9 +382,10 @@ class KernelSDF:
         out["var_f"] = torch.empty(Q, dtype=dt, device=dev) if mask & OUT_VAR_F else None
         out["winner"] = torch.empty(Q, dtype=torch.int32, device=dev) if mask & OUT_WINNER else None
         out["flags"] = torch.empty(Q, dtype=torch.int32, device=dev) if mask & OUT_FLAGS else None
+        out["var_grad"] = torch.empty((Q, self.dim), dtype=dt, device=dev) if mask & OUT_VAR_GRAD else None
         fn = ksdf_query_f64 if f64 else ksdf_query
         fn(self.h, xq, Q, sign, mask, out["sdf"], out["grad"], out["var_sdf"], out["var_f"], out["winner"],
-           out["flags"])
+           out["flags"], out["var_grad"])
         return out
 
     def backward(self, xq, winner, d_sdf, d_grad=None, sign=None, d_x=None):
