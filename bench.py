@@ -593,8 +593,16 @@ def main():
         "step_ms_min_median_max": [float(step_ms.min()), float(np.median(step_ms)), float(step_ms.max())],
     }
     if not args.no_others and world == 1:
+        # the optional SDF-gradient variance on this workload: the same 1M-query forward with and without it
+        tq, ts = xq, sign
+        base_ms = _timed(torch, lambda: model.query(tq, ts), 5)
+        vg_ms = _timed(torch, lambda: model.query(tq, ts, mask=ksdf.OUT_ALL | ksdf.OUT_VAR_GRAD), 5)
+        vg = {"workload": "room3d, 1M queries: forward with the SDF-gradient variance output (Sec. IV-B.3, App. C)",
+              "query_ms": base_ms, "query_with_var_grad_ms": vg_ms, "var_grad_extra_ms": vg_ms - base_ms,
+              "queries_per_s_with_var_grad": Q / (vg_ms * 1e-3)}
         del model
         line["other_configs"] = other_configs(torch, dev, ksdf)
+        line["other_configs"]["room3d_var_grad"] = vg
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
