@@ -382,10 +382,12 @@ class KernelSDF:
         out["var_f"] = torch.empty(Q, dtype=dt, device=dev) if mask & OUT_VAR_F else None
         out["winner"] = torch.empty(Q, dtype=torch.int32, device=dev) if mask & OUT_WINNER else None
         out["flags"] = torch.empty(Q, dtype=torch.int32, device=dev) if mask & OUT_FLAGS else None
-        out["var_grad"] = torch.empty((Q, self.dim), dtype=dt, device=dev) if mask & OUT_VAR_GRAD else None
+        vg = torch.empty((Q, self.dim), dtype=dt, device=dev) if mask & OUT_VAR_GRAD else None
+        if vg is not None:  # the optional output appears in the dict only when requested
+            out["var_grad"] = vg
         fn = ksdf_query_f64 if f64 else ksdf_query
         fn(self.h, xq, Q, sign, mask, out["sdf"], out["grad"], out["var_sdf"], out["var_f"], out["winner"],
-           out["flags"], out["var_grad"])
+           out["flags"], vg)
         return out
 
     def backward(self, xq, winner, d_sdf, d_grad=None, sign=None, d_x=None):

@@ -88,4 +88,4 @@ def test_var_grad_fp64(case):
 def test_var_grad_not_requested_is_untouched(case):
     name, w, ref, gm = case
     out = gm.query(_t(w.xq[:1000]), _t(w.sign[:1000]))
-    assert out["var_grad"] is None
+    assert "var_grad" not in out
