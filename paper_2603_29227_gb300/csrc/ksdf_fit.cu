@@ -608,6 +608,24 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
       // full rounds of 2 x 2 blocks (every thread busy); the last, partial round is done as single entries
       // below (a warp instruction costs the same FP64 pipe time however few lanes it has)
       const int64_t nfull = (nblk / TEAM) * TEAM;
+      // (GMAT: the matrix is in a global slot; each thread loads its next block's four entries before this
+      // block's FMAs, so that the L2 latency overlaps the FP64 work)
+      double n00 = 0.0, n01 = 0.0, n10 = 0.0, n11 = 0.0;
+      auto load_block = [&](int64_t tt) {
+        const int I = tri_row(tt), J = (int)(tt - tri_sz(I));
+        const int i0 = ke + 2 * I, j0 = ke + 2 * J;
+        const double* Ai0 = A + tri_sz(i0);
+        n00 = Ai0[j0];
+        n01 = j0 + 1 <= i0 ? Ai0[j0 + 1] : 0.0;
+        if (i0 + 1 <= N) {
+          const double* Ai1 = A + tri_sz(i0 + 1);
+          n10 = Ai1[j0];
+          n11 = Ai1[j0 + 1];
+        } else {
+          n10 = n11 = 0.0;
+        }
+      };
+      if (GMAT && tid < nfull) load_block(tid);
       for (int64_t t = tid; t < nfull; t += TEAM) {
         const int I = tri_row(t), J = (int)(t - tri_sz(I));
         const int i0 = ke + 2 * I, j0 = ke + 2 * J, i1 = i0 + 1, j1 = j0 + 1;
@@ -618,10 +636,19 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
         const double* Li1 = GMAT ? (vi1 ? P + (i1 - kb) * kB : Li0) : Ai1 + kb;
         const double* Lj0 = GMAT ? P + (j0 - kb) * kB : A + tri_sz(j0) + kb;
         const double* Lj1 = vj1 ? (GMAT ? P + (j1 - kb) * kB : A + tri_sz(j1) + kb) : Lj0;
-        double a00 = Ai0[j0];
-        double a01 = v01 ? Ai0[j1] : 0.0;
-        double a10 = vi1 ? Ai1[j0] : 0.0;
-        double a11 = vi1 ? Ai1[j1] : 0.0;
+        double a00, a01, a10, a11;
+        if (GMAT) {
+          a00 = n00;
+          a01 = n01;
+          a10 = n10;
+          a11 = n11;
+          if (t + TEAM < nfull) load_block(t + TEAM);
+        } else {
+          a00 = Ai0[j0];
+          a01 = v01 ? Ai0[j1] : 0.0;
+          a10 = vi1 ? Ai1[j0] : 0.0;
+          a11 = vi1 ? Ai1[j1] : 0.0;
+        }
 #pragma unroll
         for (int k = 0; k < kB; ++k) {
           if (k < w) {
