@@ -132,6 +132,19 @@ ksdf_status ksdf_fit(ksdf_ctx* ctx, const double* x, const float* var, const flo
 ksdf_status ksdf_update(ksdf_ctx* ctx, const double* x_new, const float* var_new, const float* normals_new,
                         int64_t S_new, int64_t* n_cells_refit);
 
+/* Model serialisation (the serialised map of the paper's scalability experiment, whose size is set by the
+ * stored GP surface samples): ksdf_save writes the context's parameters and the S samples the model was
+ * fitted or updated from (positions float64, variances and normals float32, host byte order) to the file
+ * `path`; ksdf_load reads such a file into a context created with the same parameters and fits it.  The
+ * fit is deterministic, so the loaded model equals the saved one bit for bit.  File layout: the 8 bytes
+ * "KSDFMAP1", int32 version 1, int32 dim, int32 has_normals, int32 0, the 11 parameters (dim, n_max,
+ * k_cand, sign_mode as int32; origin[3], cell, margin, lambda, softmin_alpha as float64), int64 S, then
+ * x (S x dim), var (S), normals (S x dim, when present).  Synchronises the stream.  Errors:
+ * KSDF_ERR_NOT_FITTED (save without a model), KSDF_ERR_ARG (NULL path, a file that cannot be written or
+ * read, a bad header, parameters that differ from the context's), and the errors of ksdf_fit (load). */
+ksdf_status ksdf_save(ksdf_ctx* ctx, const char* path);
+ksdf_status ksdf_load(ksdf_ctx* ctx, const char* path);
+
 /* Autotuning of the batched fit's tile shape (the number of warps that factor one cell, per range of cell
  * sizes): times every candidate size-class table (ksdf_autotune_tables() of them) on the fitted model's own
  * cells -- each a full fit run twice, the second timed with CUDA events on the context's stream -- keeps the

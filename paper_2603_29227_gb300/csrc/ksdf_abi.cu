@@ -2,6 +2,8 @@
 // argument checks, staging of host arrays through device workspaces, and dispatch to the fit, query and
 // backward pipelines.
 #include <cstdarg>
+#include <cstdio>
+#include <cstring>
 #include <utility>
 #include <vector>
 
@@ -319,6 +321,90 @@ ksdf_status ksdf_autotune(ksdf_ctx* c, int* table, double* fit_ms) {
 }
 
 int ksdf_autotune_tables(void) { return fit_table_count(); }
+
+namespace {
+constexpr char kMapMagic[8] = {'K', 'S', 'D', 'F', 'M', 'A', 'P', '1'};
+struct MapParams {  // the parameters in a fixed layout (no padding): 4 int32 then 7 float64
+  int32_t dim, n_max, k_cand, sign_mode;
+  double origin[3], cell, margin, lambda, softmin_alpha;
+};
+MapParams map_params(const ksdf_params& a) {
+  MapParams m;
+  m.dim = a.dim;
+  m.n_max = a.n_max;
+  m.k_cand = a.k_cand;
+  m.sign_mode = a.sign_mode;
+  for (int j = 0; j < 3; ++j) m.origin[j] = a.origin[j];
+  m.cell = a.cell;
+  m.margin = a.margin;
+  m.lambda = a.lambda;
+  m.softmin_alpha = a.softmin_alpha;
+  return m;
+}
+static_assert(sizeof(MapParams) == 4 * 4 + 7 * 8, "the map header's parameter block has no padding");
+bool same_params(const MapParams& x, const MapParams& y) {
+  bool eq = x.dim == y.dim && x.n_max == y.n_max && x.k_cand == y.k_cand && x.sign_mode == y.sign_mode &&
+            x.cell == y.cell && x.margin == y.margin && x.lambda == y.lambda && x.softmin_alpha == y.softmin_alpha;
+  for (int j = 0; j < 3; ++j) eq = eq && x.origin[j] == y.origin[j];
+  return eq;
+}
+}  // namespace
+
+ksdf_status ksdf_save(ksdf_ctx* c, const char* path) {
+  if (!c || !path) return KSDF_ERR_ARG;
+  if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "ksdf_save: no model");
+  const Model& m = c->m;
+  const int dim = c->p.dim;
+  const int64_t S = m.S;
+  std::vector<double> hx((size_t)S * dim);
+  std::vector<float> hv((size_t)S), hn(m.has_normals ? (size_t)S * dim : 0);
+  KSDF_CUDA(c, cudaMemcpyAsync(hx.data(), m.x.p, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost, c->stream));
+  KSDF_CUDA(c, cudaMemcpyAsync(hv.data(), m.var_all.p, sizeof(float) * hv.size(), cudaMemcpyDeviceToHost, c->stream));
+  if (m.has_normals)
+    KSDF_CUDA(c, cudaMemcpyAsync(hn.data(), m.nrm_all.p, sizeof(float) * hn.size(), cudaMemcpyDeviceToHost, c->stream));
+  KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return set_err(c, KSDF_ERR_ARG, "ksdf_save: cannot open %s for writing", path);
+  const int32_t head[4] = {1, dim, m.has_normals ? 1 : 0, 0};
+  const MapParams mp = map_params(c->abi);
+  bool ok = std::fwrite(kMapMagic, 1, 8, f) == 8 && std::fwrite(head, sizeof(head), 1, f) == 1 &&
+            std::fwrite(&mp, sizeof(mp), 1, f) == 1 && std::fwrite(&S, sizeof(S), 1, f) == 1 &&
+            std::fwrite(hx.data(), sizeof(double), hx.size(), f) == hx.size() &&
+            std::fwrite(hv.data(), sizeof(float), hv.size(), f) == hv.size() &&
+            std::fwrite(hn.data(), sizeof(float), hn.size(), f) == hn.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return set_err(c, KSDF_ERR_ARG, "ksdf_save: write to %s failed", path);
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_load(ksdf_ctx* c, const char* path) {
+  if (!c || !path) return KSDF_ERR_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_err(c, KSDF_ERR_ARG, "ksdf_load: cannot open %s", path);
+  char magic[8];
+  int32_t head[4];
+  MapParams mp;
+  int64_t S = 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMapMagic, 8) == 0 &&
+            std::fread(head, sizeof(head), 1, f) == 1 && head[0] == 1 && std::fread(&mp, sizeof(mp), 1, f) == 1 &&
+            std::fread(&S, sizeof(S), 1, f) == 1;
+  const int dim = c->p.dim;
+  ok = ok && head[1] == dim && (head[2] == 0 || head[2] == 1) && S > 0 && S < (1LL << 31) &&
+       same_params(mp, map_params(c->abi));
+  std::vector<double> hx;
+  std::vector<float> hv, hn;
+  if (ok) {
+    hx.resize((size_t)S * dim);
+    hv.resize((size_t)S);
+    hn.resize(head[2] ? (size_t)S * dim : 0);
+    ok = std::fread(hx.data(), sizeof(double), hx.size(), f) == hx.size() &&
+         std::fread(hv.data(), sizeof(float), hv.size(), f) == hv.size() &&
+         std::fread(hn.data(), sizeof(float), hn.size(), f) == hn.size();
+  }
+  std::fclose(f);
+  if (!ok) return set_err(c, KSDF_ERR_ARG, "ksdf_load: %s is not a map of this context's parameters", path);
+  return ksdf_fit(c, hx.data(), hv.data(), head[2] ? hn.data() : nullptr, S);
+}
 
 ksdf_status ksdf_fp64_rate(ksdf_ctx* c, double* tflops) {
   if (!c || !tflops) return KSDF_ERR_ARG;

@@ -31,7 +31,7 @@ ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
                  "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math",
-                 "ksdf_fp64_rate")
+                 "ksdf_fp64_rate", "ksdf_save", "ksdf_load")
 
 
 class KsdfError(RuntimeError):
@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH):
         "ksdf_autotune_tables": [],
         "ksdf_device_math": [P, ctypes.c_int, P, I64, P],
         "ksdf_fp64_rate": [P, P],
+        "ksdf_save": [P, ctypes.c_char_p],
+        "ksdf_load": [P, ctypes.c_char_p],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -188,6 +190,21 @@ def ksdf_device_math(h, fn, x):
     y = np.empty_like(x)
     _check(h, load().ksdf_device_math(h, int(fn), _ptr(x), x.size, _ptr(y)), "ksdf_device_math")
     return y
+
+
+def ksdf_save(h, path):
+    """Write the model's parameters and samples to `path` (a map file; see include/ksdf.h)."""
+    _check(h, load().ksdf_save(h, os.fsencode(path)), "ksdf_save")
+
+
+def ksdf_load(h, path):
+    """Read a map file into the context (same parameters) and fit it; returns the number of samples."""
+    rc = load().ksdf_load(h, os.fsencode(path))
+    if rc != KSDF_ERR_NOT_PD:
+        _check(h, rc, "ksdf_load")
+    with open(path, "rb") as f:  # S sits after the magic, four int32 and the 72-byte parameter block
+        f.seek(8 + 16 + 72)
+        return int(np.frombuffer(f.read(8), dtype=np.int64)[0])
 
 
 def ksdf_fp64_rate(h):
@@ -355,6 +372,16 @@ class KernelSDF:
         self.S = int(x.shape[0])
         self.fit_status = ksdf_fit(self.h, x, var, normals, self.S)
         return self.fit_status
+
+    def save(self, path):
+        """Serialise the model (parameters and samples) to `path`."""
+        self._stream()
+        ksdf_save(self.h, path)
+
+    def load(self, path):
+        """Load a map saved with the same parameters and fit it (the model equals the saved one bit for bit)."""
+        self._stream()
+        self.S = ksdf_load(self.h, path)
 
     def autotune(self):
         """Pick the fit's team-size table by timing the candidates on this model; returns (index, ms)."""
