@@ -63,6 +63,19 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def whole_job_rate(total_s, world, queries_per_rank, steps, device=None):
+    """The slowest rank's timed seconds (all-reduce MAX over the ranks) and the whole job's queries/s: every
+    rank answers its own batch (weak scaling), so the job's rate is world x batch x steps over that time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        tt = torch.tensor([total_s], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = float(tt.item())
+    return total_s, world * queries_per_rank * steps / total_s
+
+
 def make_workload(args, rank):
     from paper_2603_29227_gb300 import scenes
 
@@ -453,14 +466,7 @@ def main():
             if k.startswith("query") or k.startswith("backward"):
                 stages[k] = v
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    total_s = float(step_ms.sum()) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
-    value = world * Q * args.steps / total_s
+    total_s, value = whole_job_rate(float(step_ms.sum()) / 1e3, world, Q, args.steps, dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
