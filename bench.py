@@ -225,7 +225,7 @@ class ClockSampler:
 # DRAM bytes (read + write) per stage from one ncu capture of the current kernels on this workload
 # (profiles/room3d_fit_ncu.md: the six populated k_fit size classes of one fit; profiles/room3d_kernels_ncu.md:
 # the two k_phaseB_tc launches of one query); None once a kernel changes until it is captured again
-MEASURED_TRAFFIC = {"fit.cholesky": 288.0e6, "query.phaseB": 490.3e6}
+MEASURED_TRAFFIC = {"fit.cholesky": None, "query.phaseB": 490.3e6}  # k_fit changed after its capture
 
 
 def fit_fp64_flops(n):
