@@ -11,6 +11,7 @@
  *   grad u  = -grad f' / |grad f'|                                                      (Sec. IV-B.1)
  *   V[u]    = sum_i s_i^2 (a (h - z_i) + 1)^2 sigma_i^2, softmin s, h = s^T z            (Sec. IV-B.3)
  *   V[f]    = 1 - k^T (K + Sigma)^{-1} k = 1 - e^{-2 lambda d^2} |L^{-1} k'|^2           (Sec. IV-B.1)
+ *   V[grad_k u] = sum_i |grad_{x_i} g_k|^2 sigma_i^2, g = grad h (optional)          (Sec. IV-B.3, App. C)
  *
  * where d is the distance to the GP's nearest training sample.  The library implements that path on one
  * GPU: integer binning of samples and queries into a hash grid of cells of edge h, training-set
