@@ -1,25 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the Kernel-SDF back-end hot path on GB300 (one JSON line on rank 0).
 
-One step = the whole path over one batch of the room workload (20 x 20 x 5 m room, 50 primitives,
-200,000 noisy surface samples, 1,000,000 uniform queries): fit of every local GP (binning, cell index,
-training sets, FP64 Cholesky / alpha / L^-1), query (candidates, min-fused SDF, gradient, softmin variance,
-GP variance) and the adjoint of sdf and grad with respect to the query points and the sample positions.
-value = queries per second of that step over all ranks (weak scaling: each rank fits the scene and
-answers its own 1M queries).  Inputs are resident on the device; L2 is flushed (256 MiB write) between
-timed steps.  The JSON line also carries the roofline of the dominant kernel (stage timing with CUDA
-events on the library's stream), the plain-FP64 query for comparison, a sampled parity check against the
-CPU FP64 oracle (which is also the timed CPU baseline), the end-to-end number through the C ABI with
-pinned host buffers, SM clocks sampled during the timed region, and the number of kernel launches.
+One step = the whole path over one batch of the scale workload (50 x 50 x 10 m scene with 1,000 spheres
+and boxes, 2,000,000 noisy surface samples, 0.5 m cells capped at 512 samples, a 256^3 grid of
+16,777,216 queries): the fit of every local GP (binning, cell index, training sets, FP64 Cholesky / alpha,
+FP32 L^-1), the query (candidates, min-fused SDF, gradient, softmin variance, GP variance) and the adjoint
+of sdf and grad with respect to the query points and the sample positions.  value = queries per second
+of that step over all ranks (weak scaling: each rank fits the scene and answers its own batch).  Inputs
+are resident on the device; L2 (129 MB) is flushed with a 256 MiB write between timed steps.
 
---impl reference times the CPU FP64 oracle itself (the reference arm; there is no other implementation of
-the paper's method to run) on a bounded sample of the same workload.
+The JSON line also carries: the roofline of the query and its adjoint (the binding unit among MUFU, FP32,
+tensor cores and HBM, from algorithmic counts of this run's model and queries, against peaks measured
+live by the probes of libksdf_peaks.so), the per-kernel rooflines and stage times, the plain FP64 GPU
+query of the same inputs, the end-to-end rate through the C ABI with pinned host buffers, the CPU FP64
+oracle on a bounded sample (cpu_baseline) with a parity check of this run's outputs on that sample, SM
+clocks sampled during the timed region, the number of kernel launches, and the other workloads.
+
+--impl reference times the CPU FP64 oracle itself (the reference arm; the paper ships no implementation
+to run) with the same per-step protocol as cpu_baseline.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -31,32 +36,34 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 and FP32 rates from the profiling recipe's unit counts (nominal FP64 1.25 TFLOP/s; FP32: 128 FMA
-# lanes x 152 SMs x 2 flops at the 2.07 GHz maximum clock)
-NOMINAL_FP64_TFLOPS = 1.25
-NOMINAL_FP32_TFLOPS = 128 * 152 * 2 * 2.07e9 / 1e12
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "scale3d_query_adjoint_dram.txt")
 METRIC = "SDF+grad+var queries/s at err<=1e-4 m vs FP64 oracle; % roofline; vs plain FP64"
-WORKLOAD = ("room3d: 20x20x5 m room with 50 spheres/boxes, 200,000 samples (sigma 0.01 m), 0.5 m cells, "
-            "n_max 256, K 8, lambda 300; 1,000,000 uniform queries; step = fit + query(sdf, grad, var_sdf, "
-            "var_f) + adjoint(d sdf, d grad -> d xq, d x)")
+WORKLOAD_TEXT = {
+    "scale3d": ("scale3d: 50x50x10 m scene with 1,000 spheres/boxes, 2,000,000 samples (sigma 0.01 m), 0.5 m cells, "
+                "n_max 512, K 8, lambda 300; 256^3 = 16,777,216 grid queries; step = fit + query(sdf, grad, var_sdf, "
+                "var_f) + adjoint(d sdf, d grad -> d xq, d x)"),
+    "room3d": ("room3d: 20x20x5 m room with 50 spheres/boxes, 200,000 samples (sigma 0.01 m), 0.5 m cells, n_max 256, "
+               "K 8, lambda 300; 1,000,000 uniform queries; step = fit + query(sdf, grad, var_sdf, var_f) + "
+               "adjoint(d sdf, d grad -> d xq, d x)"),
+}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--samples", type=int, default=200_000)
-    ap.add_argument("--queries", type=int, default=1_000_000)
-    ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="queries of the oracle's timed sample")
-    ap.add_argument("--cpu-repeats", type=int, default=9, help="repetitions of the oracle sample (~10 s in all)")
+    ap.add_argument("--workload", default="scale3d", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--samples", type=int, default=None, help="override the workload's sample count (tests)")
+    ap.add_argument("--queries", type=int, default=None, help="override the workload's query count (tests)")
+    ap.add_argument("--cpu-sample", type=int, default=65536, help="queries of the oracle's per-step sample")
+    ap.add_argument("--cpu-repeats", type=int, default=3, help="oracle steps of the cpu_baseline leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg (cpu_baseline, parity)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-others", action="store_true", help="skip the other workloads (2D, differentiation, scale, "
-                    "streaming)")
-    ap.add_argument("--no-graph", action="store_true", help="launch query + adjoint eagerly instead of replaying a CUDA graph")
-    return ap.parse_args()
+    ap.add_argument("--no-others", action="store_true", help="skip the other workloads")
+    ap.add_argument("--no-graph", action="store_true", help="launch query + adjoint eagerly instead of a CUDA graph")
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -77,53 +84,68 @@ def whole_job_rate(total_s, world, queries_per_rank, steps, device=None):
 
 
 def make_workload(args, rank):
+    """The benchmark workload; rank 0 answers the workload's own queries, every other rank the same number of
+    seeded uniform queries in the scene's box (its own batch of the same scene)."""
     from paper_2603_29227_gb300 import scenes
 
-    w = scenes.workload("room3d", n_samples=args.samples, n_queries=args.queries)
-    if rank > 0:  # weak scaling: same scene, each rank its own query batch
+    name = getattr(args, "workload", None) or "scale3d"
+    nq = getattr(args, "queries", None)
+    if name == "scale3d":
+        grid = None if nq is None else max(2, int(round(nq ** (1.0 / 3.0))))
+        w = scenes.workload("scale3d", n_samples=getattr(args, "samples", None), grid=grid)
+    else:
+        w = scenes.workload(name, n_samples=getattr(args, "samples", None), n_queries=nq)
+    if rank > 0:
         rng = np.random.default_rng(1000 + rank)
-        xq = w.scene.room_lo + rng.random((args.queries, 3)) * (w.scene.room_hi - w.scene.room_lo)
-        w.xq = xq.astype(np.float32)
+        lo, hi = w.scene.room_lo, w.scene.room_hi
+        w.xq = np.ascontiguousarray(lo + rng.random((len(w.xq), 3)) * (hi - lo), dtype=np.float32)
         w.sign = w.scene.sign(w.xq.astype(np.float64))
     return w
 
 
+def workload_config(w, args):
+    """The config block shared by both arms (same keys, same values)."""
+    return {"workload": WORKLOAD_TEXT[w.name], "samples": int(len(w.x)), "queries": int(len(w.xq)),
+            "l2": "inputs resident in HBM; L2 flushed between timed steps (256 MiB write outside the step events)"}
+
+
 # ----------------------------------------------------------------------------------------------------
-# oracle (CPU) legs
+# CPU FP64 oracle: the same per-step protocol for the reference arm and cpu_baseline
 
 
-def oracle_leg(w, n_sample, repeats=3, seed=0):
-    """Time the oracle on a bounded sample (the full fit plus the forward and adjoint of n_sample queries,
-    `repeats` times: ~10 s at the room workload); returns (stats, model, sample, outputs on the sample)."""
+def oracle_step(w, sel, d_sdf, d_grad):
+    """One oracle step: the full FP64 fit of every sample and the forward + adjoint of the queries `sel`.
+    Returns (fit seconds, query+adjoint seconds, forward outputs on sel)."""
     import oracle
 
-    oracle.build()
-    threads = oracle.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    m = oracle.Model(w.params, w.x, w.var, w.normals)
+    t1 = time.perf_counter()
+    ref = m.query(w.xq[sel], w.sign[sel], with_cands=True)
+    m.backward(w.xq[sel], d_sdf, d_grad, sign=w.sign[sel], winner=ref["winner"])
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, ref, m
+
+
+def oracle_sample(w, n_sample, seed=0):
     rng = np.random.default_rng(seed)
     sel = np.sort(rng.choice(len(w.xq), size=min(n_sample, len(w.xq)), replace=False))
     d_sdf = np.ones(len(sel))
-    d_grad = np.random.default_rng(7).standard_normal((len(sel), 3)) * 0.1
-    fit_s = qb_s = 0.0
-    for _ in range(max(1, repeats)):
-        t0 = time.perf_counter()
-        m = oracle.Model(w.params, w.x, w.var, w.normals)
-        t1 = time.perf_counter()
-        ref = m.query(w.xq[sel], w.sign[sel], with_cands=True)
-        m.backward(w.xq[sel], d_sdf, d_grad, sign=w.sign[sel], winner=ref["winner"])
-        t3 = time.perf_counter()
-        fit_s += t1 - t0
-        qb_s += t3 - t1
-    reps = max(1, repeats)
-    Q = len(w.xq)
-    scale = Q / len(sel)
-    t_equiv = (fit_s + qb_s * scale) / reps
-    stats = dict(value=Q / t_equiv, unit="queries/s", cores=threads, kind="oracle",
-                 sample="%d x (full FP64 fit of %d samples + forward and adjoint of %d of the %d queries): "
-                        "%.1f s of CPU time, fit %.2f s and queries %.2f s per repetition%s"
-                        % (reps, len(w.x), len(sel), Q, fit_s + qb_s, fit_s / reps, qb_s / reps,
-                           "" if scale == 1 else ", query part scaled x%.1f" % scale),
-                 fit_s=fit_s / reps, query_backward_s=qb_s / reps)
-    return stats, m, sel, ref
+    d_grad = np.random.default_rng(7).standard_normal((len(sel), w.params["dim"])) * 0.1
+    return sel, d_sdf, d_grad
+
+
+def oracle_stats(w, sel, fit_s, qb_s, threads):
+    """cpu_baseline block: value = the sample's queries per second of measured step time (fit included);
+    the whole-workload rate the same oracle would reach (one fit per full batch) is a separate field."""
+    q, Q = len(sel), len(w.xq)
+    fit_m, qb_m = float(np.mean(fit_s)), float(np.mean(qb_s))
+    return {"value": q / (fit_m + qb_m), "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": "per step: the full FP64 fit of all %d samples + forward and adjoint of %d seeded random queries "
+                      "of the %d (no scaling); %d steps" % (len(w.x), q, Q, len(fit_s)),
+            "ms_per_step": 1e3 * (fit_m + qb_m), "fit_s": fit_m, "query_adjoint_s": qb_m,
+            "extrapolated_full_workload_rate": Q / (fit_m + qb_m * Q / q),
+            "extrapolated_how": "one fit + the sample's per-query time x all queries of the workload"}
 
 
 def run_reference(args):
@@ -135,30 +157,20 @@ def run_reference(args):
     w = make_workload(args, 0)
     oracle.build()
     threads = oracle.set_threads(os.cpu_count() or 1)
-    Q = len(w.xq)
-    qs = max(256, min(args.cpu_sample // 8, Q))
-    rng = np.random.default_rng(0)
-    times = []
+    sel, d_sdf, d_grad = oracle_sample(w, args.cpu_sample)
+    fit_s, qb_s = [], []
     for it in range(args.warmup + args.steps):
-        sel = rng.choice(Q, size=qs, replace=False)
-        t0 = time.perf_counter()
-        m = oracle.Model(w.params, w.x, w.var, w.normals)
-        t1 = time.perf_counter()
-        r = m.query(w.xq[sel], w.sign[sel])
-        m.backward(w.xq[sel], np.ones(qs), np.full((qs, 3), 0.1), sign=w.sign[sel], winner=r["winner"])
-        t2 = time.perf_counter()
-        if it >= args.warmup:
-            times.append((t1 - t0) + (t2 - t1) * Q / qs)
+        tf, tq, _, m = oracle_step(w, sel, d_sdf, d_grad)
         del m
-    t = float(np.mean(times))
-    value = Q / t
+        if it >= args.warmup:
+            fit_s.append(tf)
+            qb_s.append(tq)
+    cpu = oracle_stats(w, sel, fit_s, qb_s, threads)
+    value = cpu["value"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": cpu["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "samples": len(w.x), "queries": Q},
-            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle",
-                             "sample": "per step: full FP64 fit of %d samples + forward and adjoint of %d random "
-                                       "queries of %d, query part scaled x%.1f" % (len(w.x), qs, Q, Q / qs)},
+            "config": workload_config(w, args), "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -219,28 +231,33 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------------------------------
-# algorithmic work per launch (roofline numerators)
-
-
-# DRAM bytes (read + write) per stage from one ncu capture of the current kernels on this workload
-# (profiles/room3d_fit_ncu.md: the six populated k_fit size classes of one fit; profiles/room3d_kernels_ncu.md:
-# the two k_phaseB_tc launches of one query); None once a kernel changes until it is captured again
-MEASURED_TRAFFIC = {"fit.cholesky": None, "query.phaseB": 490.3e6}  # k_fit changed after its capture
+# algorithmic work (roofline numerators)
 
 
 def fit_fp64_flops(n):
     """FP64 flops of the factorisation stage (k_fit) for cells with training-set sizes n: Cholesky N^3/3 and
-    alpha 2N^2 (two triangular solves).  The kernel matrix (k_kmat, its own stage) and the FP32 inverse of
-    the factor (N^3/3 FP32 flops, another unit) are not counted."""
+    alpha 2N^2 (two triangular solves)."""
     n = n.astype(np.float64)
     return float(np.sum(n ** 3 / 3 + 2 * n ** 2))
 
 
-def phase_a_pairs(w, h):
+def query_work(w, h, winner):
+    """Algorithmic counts of the query and of its adjoint on this model and batch.  Per query, C = sum of the
+    candidate cells' training-set sizes and N_w = the winner's:
+      forward   MUFU  C (phase A exp) + 3 N_w (k', z, softmin weight) + 3;   FP32 lane ops 8 C + 18 N_w;
+                V[f]: N_w (N_w + 1) / 2 MACs of K' L^-T, on the tensor cores (N_w <= 256) as TF32 split three
+                ways, 3 N_w (N_w + 1) flops, else N_w (N_w + 1) / 2 FP32 FMAs;
+                HBM  45 B per query (xq 12, sign 1; sdf, var_sdf, var_f, winner, flags 4 each, grad 12) + every
+                cell's members once (float4 position/alpha + sigma^2: 20 B) + the winners' FP32 L^-1 triangle;
+      adjoint   MUFU  N_w + per touched cell N_c (N_c - 1) (alpha-path kernel entries);
+                FP32 lane ops 25 N_w + per touched cell 10 N_c (N_c - 1) + 2 N_c^2 (two FP32 L^-1 products);
+                FP64 flops per touched cell 2 N_c^2 (one refinement residual);
+                HBM  45 B per query (xq, sign, winner, d_sdf, d_grad, d_xq) + 24 B per sample (d_x read and
+                written) + the touched cells' members, FP32 L^-1 and FP64 L triangles."""
     from paper_2603_29227_gb300 import ksdf
 
     keys, status, off, mem = ksdf.ksdf_get_cells(h)
-    nsz = np.diff(off)
+    nsz = np.diff(off).astype(np.float64)
     qk = np.empty(len(w.xq), np.uint64)
     ksdf.ksdf_bin(h, np.ascontiguousarray(w.xq, dtype=np.float64), len(w.xq), qk)
     ub, inv = np.unique(qk, return_inverse=True)
@@ -249,7 +266,66 @@ def phase_a_pairs(w, h):
     cnt = np.empty(len(ub), np.int32)
     ksdf.ksdf_candidates(h, ub, len(ub), cand, cnt)
     per_bin = np.where(cand >= 0, nsz[np.maximum(cand, 0)], 0).sum(axis=1)
-    return float(per_bin[inv].sum()), nsz
+    C = float(per_bin[inv].sum())
+    wn = np.asarray(winner)
+    ok = wn >= 0
+    nw = nsz[wn[ok]]
+    Q = len(w.xq)
+    tc_sel = nw <= 256
+    touched = np.unique(wn[ok])
+    nc = nsz[touched]
+    tri = lambda n: n * (n + 1) / 2  # noqa: E731
+    fwd = {"mufu": C + 3 * nw.sum() + 3 * Q,
+           "fp32": 8 * C + 18 * nw.sum() + tri(nw[~tc_sel]).sum(),
+           "tc": 6 * tri(nw[tc_sel]).sum(),
+           "hbm": 45.0 * Q + 20.0 * nsz.sum() + 4.0 * tri(nc).sum(), "fp64": 0.0}
+    bwd = {"mufu": nw.sum() + (nc * (nc - 1)).sum(),
+           "fp32": 25 * nw.sum() + (10 * nc * (nc - 1) + 2 * nc ** 2).sum(),
+           "tc": 0.0,
+           "hbm": 45.0 * Q + 24.0 * len(w.x) + (20.0 * nc + 12.0 * tri(nc)).sum(), "fp64": (2 * nc ** 2).sum()}
+    stats = {"C_per_query": C / Q, "Nw_mean": float(nw.mean()) if nw.size else 0.0,
+             "Nw_max": int(nw.max()) if nw.size else 0, "touched_cells": int(len(touched)), "cells": int(len(nsz))}
+    return fwd, bwd, stats, nsz
+
+
+def roofline_of(work, seconds, peaks):
+    """The binding unit of `work` (max over units of count / peak) and the achieved fraction of it in
+    `seconds`.  Peaks: units per second."""
+    t = {u: work[u] / peaks[u] for u in ("mufu", "fp32", "tc", "hbm", "fp64") if work.get(u) and peaks.get(u)}
+    unit = max(t, key=t.get)
+    names = {"mufu": ("alu", "Tops/s (MUFU ex2)"), "fp32": ("alu", "Tops/s (FP32 lane ops)"),
+             "tc": ("tensor", "TFLOP/s (TF32)"), "hbm": ("hbm", "GB/s"), "fp64": ("alu", "TFLOP/s (FP64)")}
+    scale = 1e9 if unit == "hbm" else 1e12
+    achieved = work[unit] / seconds / scale
+    peak = peaks[unit] / scale
+    return {"bound": names[unit][0], "binding_unit": unit, "achieved": achieved, "peak": peak,
+            "unit": names[unit][1], "frac": achieved / peak, "roofline_ms": 1e3 * t[unit], "measured_ms": 1e3 * seconds,
+            "unit_ms": {u: round(1e3 * v, 4) for u, v in t.items()}}
+
+
+def source_digest():
+    """Digest of the query and adjoint kernel sources: DRAM traffic recorded from ncu applies only to the
+    kernels it was captured from."""
+    import hashlib
+
+    hs = hashlib.sha256()
+    for f in ("ksdf_query.cu", "ksdf_backward.cu", "ksdf_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2603_29227_gb300", "csrc", f), "rb") as fh:
+            hs.update(fh.read())
+    return hs.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes (read + write) of one query + adjoint from the committed ncu summary, if it was captured
+    from the current kernel sources; else None."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    txt = open(TRAFFIC_FILE).read()
+    m = re.search(r"source_digest\s+(\w+)", txt)
+    t = re.search(r"query_adjoint_dram_bytes\s+([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != source_digest():
+        return None
+    return float(t.group(1))
 
 
 # ----------------------------------------------------------------------------------------------------
@@ -269,12 +345,48 @@ def _timed(torch, fn, steps, warmup=3):
     return e0.elapsed_time(e1) / steps
 
 
-def other_configs(torch, dev, ksdf):
+def full_step_bench(torch, dev, ksdf, w, steps=10):
+    """fit + query + adjoint of a workload, the query and adjoint replayed from a CUDA graph; ms per step."""
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    x, var, nrm, xq, sign = t(w.x), t(w.var), t(w.normals), t(w.xq), t(w.sign)
+    Q = len(w.xq)
+    d_sdf = torch.ones(Q, dtype=torch.float32, device=dev)
+    d_grad = torch.full((Q, 3), 0.1, dtype=torch.float32, device=dev)
+    m = ksdf.KernelSDF(w.params)
+    m.fit(x, var, nrm)
+    m.autotune()
+    for _ in range(3):
+        o = m.query(xq, sign)
+        m.backward(xq, o["winner"], d_sdf, d_grad, sign)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        o = m.query(xq, sign)
+        m.backward(xq, o["winner"], d_sdf, d_grad, sign)
+
+    def step():
+        m.fit(x, var, nrm)
+        g.replay()
+
+    ms = _timed(torch, step, steps)
+    qb = _timed(torch, g.replay, steps)
+    m.sync_status()
+    del m, g
+    return {"ms_per_step": ms, "queries_per_s": Q / (ms * 1e-3), "query_adjoint_ms": qb, "fit_ms": ms - qb}
+
+
+def other_configs(torch, dev, ksdf, main_name):
     """The other synthetic workloads, one GPU, device-resident inputs, CUDA-event timing (warm-up 3)."""
     from paper_2603_29227_gb300 import scenes
 
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     res = {}
+    # the other 3D workload's full step
+    other = "room3d" if main_name == "scale3d" else "scale3d"
+    w = scenes.workload(other)
+    r = full_step_bench(torch, dev, ksdf, w, steps=10 if other == "room3d" else 3)
+    r["workload"] = WORKLOAD_TEXT[other]
+    res[other + "_full_step"] = r
     # 2D plain FP64: fit + FP64 query of the 128 x 128 grid (latency bound: microseconds)
     w = scenes.workload("plane2d")
     m = ksdf.KernelSDF(w.params)
@@ -305,21 +417,6 @@ def other_configs(torch, dev, ksdf):
                                          "queries; sdf + grad forward and adjoint to queries and samples",
                              "ms_per_step": ms, "queries_per_s": Q / (ms * 1e-3)}
     del m, d_sdf, d_grad
-    # scale: 2M samples, 256^3 grid; mixed path vs plain FP64 path on the same inputs
-    w = scenes.workload("scale3d")
-    m = ksdf.KernelSDF(w.params)
-    x, var, nrm, xq = t(w.x), t(w.var), t(w.normals), t(w.xq)
-    m.fit(x, var, nrm)
-    fit_ms = _timed(torch, lambda: m.fit(x, var, nrm), 3, warmup=1)
-    q_ms = _timed(torch, lambda: m.query(xq), 3, warmup=1)
-    xq64 = xq.double()
-    q64_ms = _timed(torch, lambda: m.query(xq64, f64=True), 1, warmup=1)
-    G, M = ksdf.ksdf_model_size(m.h)
-    res["scale3d_mixed"] = {"workload": "50x50x10 m, 1,000 primitives, 2,000,000 samples, 0.5 m cells (n_max 512); "
-                                        "256^3 = 16,777,216 grid queries", "cells": int(G), "fit_ms": fit_ms,
-                            "query_ms": q_ms, "queries_per_s": len(w.xq) / (q_ms * 1e-3),
-                            "plain_fp64_query_ms": q64_ms, "speedup_vs_plain_fp64": q64_ms / q_ms}
-    del m, xq64
     # streaming: LiDAR frames of a city block; frame 0 fits, every later frame appends its hits (ksdf_update:
     # refit of the touched cells) and answers 1M queries around the pose
     city = scenes.make_city()
@@ -349,12 +446,58 @@ def other_configs(torch, dev, ksdf):
                        "query_ms": e[1].elapsed_time(e[2])})
     upd = frames[1:]
     tot = sum(fr["refit_ms"] + fr["query_ms"] for fr in upd)
-    res["city_stream"] = {"workload": "100x100 m city block, 96 boxes kept off the path, 64x2048 LiDAR scans "
-                                      "(~125k hits per frame), 1M queries per frame in the 40x40x6 m box around the "
-                                      "pose; the front-end occupancy update is out of scope",
-                          "frames": frames, "queries_per_s_incl_refit": 1e6 * len(upd) / (tot * 1e-3)}
+    res["city_stream"] = {"workload": "100x100 m city block, 64x2048 LiDAR scans (~125k hits per frame, range noise "
+                                      "0.02 m), 1M queries per frame in the 40x40x6 m box around the pose; the "
+                                      "front-end occupancy update is not built", "frames": frames,
+                          "queries_per_s_incl_refit": 1e6 * len(upd) / (tot * 1e-3)}
     del m
     return res
+
+
+def parity_block(w, sel, ref, om, got):
+    """This run's outputs on the oracle's sample: SDF for every query; where the GPU picked another winner
+    than the oracle (a near tie), the other outputs against the oracle evaluated on the GPU's winner;
+    gradient angle excluding only medial-axis queries (cancellation ratio < 1e-2) and zero gradients."""
+    gw = got["winner"][sel].astype(np.int64)
+    rw = ref["winner"].astype(np.int64)
+    fin = np.isfinite(ref["sdf"])
+    sdf_err = np.abs(got["sdf"][sel].astype(np.float64) - ref["sdf"])
+    diff = (gw != rw) & fin & (gw >= 0)
+    rg, rvs, rvf = ref["grad"].copy(), ref["var_sdf"].copy(), ref["var_f"].copy()
+    if diff.any():
+        alt = om.eval_cell(w.xq[sel][diff], gw[diff].astype(np.int32), w.sign[sel][diff])
+        rg[diff], rvs[diff], rvf[diff] = alt["grad"], alt["var_sdf"], alt["var_f"]
+    tie_flag = (got["flags"][sel].astype(np.int64) & 4) != 0
+    # medial-axis exclusion: cancellation ratio of the gradient sum on the GPU's winner (oracle side)
+    keys, status, off, mem = om.cells()
+    lam = w.params["lambda"]
+    ratio = np.ones(len(sel))
+    xs_q = w.xq[sel].astype(np.float64)
+    for g in np.unique(gw[fin & (gw >= 0)]):
+        s = np.nonzero((gw == g) & fin)[0]
+        xs = om.x[mem[off[g]:off[g + 1]]]
+        al = om.alpha(int(g))
+        r = xs_q[s][:, None, :] - xs[None, :, :]
+        r2 = np.sum(r * r, axis=2)
+        kp = np.exp(-lam * (r2 - r2.min(axis=1, keepdims=True)))
+        num = np.linalg.norm(np.sum((al * kp)[:, :, None] * r, axis=1), axis=1)
+        den = np.sum(np.abs(al) * kp * np.sqrt(r2), axis=1)
+        ratio[s] = num / np.maximum(den, 1e-300)
+    gg = got["grad"][sel].astype(np.float64)
+    cosang = np.sum(gg * rg, 1) / np.maximum(np.linalg.norm(gg, axis=1) * np.linalg.norm(rg, axis=1), 1e-300)
+    ang = np.degrees(np.arccos(np.clip(cosang, -1, 1)))
+    zero = ((got["flags"][sel].astype(np.int64) | ref["flags"].astype(np.int64)) & 8) != 0
+    gsel = fin & (ratio >= 1e-2) & ~zero
+    vs = np.abs(got["var_sdf"][sel] - rvs) / np.maximum(np.abs(rvs), 1e-30)
+    vf = np.abs(got["var_f"][sel] - rvf) / np.maximum(rvf, 1e-3)
+    return {"sample": int(len(sel)), "sdf_max_err_m": float(sdf_err[fin].max()),
+            "sdf_within_1e-4": bool(sdf_err[fin].max() <= 1e-4),
+            "winner_agree": float(np.mean(gw[fin] == rw[fin])),
+            "winner_disagree_flagged": float(np.mean(tie_flag[diff])) if diff.any() else 1.0,
+            "grad_angle_max_deg": float(ang[gsel].max()) if gsel.any() else 0.0,
+            "grad_medial_excluded": int(np.sum(fin & (ratio < 1e-2))),
+            "var_sdf_max_rel": float(vs[fin].max()), "var_f_max_scaled": float(vf[fin].max()),
+            "note": "per-query checks at every size are the GPU tests (tests/test_gpu_full.py)"}
 
 
 def main():
@@ -376,7 +519,7 @@ def main():
         __graft_entry__.build()
     if world > 1:
         torch.distributed.barrier()
-    from paper_2603_29227_gb300 import ksdf
+    from paper_2603_29227_gb300 import ksdf, peaks
 
     ksdf.load()
     w = make_workload(args, rank)
@@ -405,6 +548,7 @@ def main():
     # the query and its adjoint allocate nothing after the warm-up (workspaces sized): capture them once in a
     # CUDA graph and replay it per step after the (eager) fit, which sizes its launches on the host
     graph_launches = 0
+    graph = None
     if not args.no_graph:
         _, l0 = ksdf.ksdf_profile_read(model.h)
         graph = torch.cuda.CUDAGraph()
@@ -453,8 +597,25 @@ def main():
     launches1 += graph_launches * args.steps  # kernels replayed from the graph
     ksdf.ksdf_profile(model.h, 0)
     model.sync_status()
-    if not args.no_graph:
-        # per-stage times of the query and the adjoint (inside the graph above) from two eager profiled steps
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    total_s, value = whole_job_rate(float(step_ms.sum()) / 1e3, world, Q, args.steps, dev)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # ---- query + adjoint alone (the graph), L2 flushed before each replay, and per-stage times ----
+    qb_ms = None
+    if graph is not None:
+        e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a, b in e:
+            flush.fill_(1)
+            a.record()
+            graph.replay()
+            b.record()
+        torch.cuda.synchronize()
+        qb_ms = float(np.mean([a.elapsed_time(b) for a, b in e]))
+        # per-stage times of the query and the adjoint (inside the graph) from two eager profiled steps
         ksdf.ksdf_profile(model.h, 1)
         ksdf.ksdf_profile_read(model.h)
         for _ in range(2):
@@ -465,52 +626,49 @@ def main():
         for k, v in st2.items():
             if k.startswith("query") or k.startswith("backward"):
                 stages[k] = v
-    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    total_s, value = whole_job_rate(float(step_ms.sum()) / 1e3, world, Q, args.steps, dev)
-    if rank != 0:
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return 0
-
-    # ---- roofline of the dominant kernel ----
-    peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
-    pairs, nsz = phase_a_pairs(w, model.h)
     per = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
-    kernels = {k: per[k] for k in ("fit.cholesky", "fit.kmat", "fit.linv", "fit.index", "fit.assemble", "query.group",
-                                   "query.candidates",
-                                   "query.phaseA", "query.regroup", "query.phaseB", "backward.group",
-                                   "backward.query", "backward.cell") if k in per}
-    dom = max(kernels, key=kernels.get)
-    fl64 = fit_fp64_flops(nsz)
-    fp64_measured = ksdf.ksdf_fp64_rate(model.h)  # sustained DFMA rate of this GPU, outside the timed region
-    roof_all = {
-        "fit.cholesky": {"bound": "alu", "achieved": fl64 / (per["fit.cholesky"] * 1e-3) / 1e12,
-                         "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                         "what": "FP64 flops of the factorisation: N^3/3 + 2 N^2 per cell (Cholesky and alpha)",
-                         "peak_measured": fp64_measured,
-                         "peak_measured_how": "ksdf_fp64_rate: dependent DFMA chains, 16 warps/SM, CUDA events"},
-        "query.phaseA": {"bound": "alu", "achieved": pairs * 12 / (per["query.phaseA"] * 1e-3) / 1e12,
-                         "peak": NOMINAL_FP32_TFLOPS, "unit": "TFLOP/s",
-                         "what": "12 FP32 flops per (query, candidate sample) pair + 1 ex2; %.3g pairs" % pairs},
-    }
-    for k, r in roof_all.items():
-        r["frac"] = r["achieved"] / r["peak"]
-        if r.get("peak_measured"):
-            r["frac_of_measured"] = r["achieved"] / r["peak_measured"]
-        r["traffic"] = MEASURED_TRAFFIC.get(k)
-    roof = dict(roof_all.get(dom, {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-                                   "traffic": None}))
-    roof["kernel"] = dom
-    roof["peak_source"] = ("recipe nominal (unit counts x clock); no FP64/FP32 figure in MEASURED_PEAKS.json; "
-                           "peak_measured: this GPU's sustained DFMA rate, measured live")
+    if qb_ms is None:
+        qb_ms = per.get("query", 0.0) + per.get("backward", 0.0)
+
+    # ---- peaks of this GPU (probes, outside the timed region) ----
+    pk = peaks.measure_all()
+    mp = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
+    hbm_gbs = mp.get("hbm_gbs")
+    peak_src = "MEASURED_PEAKS.json hbm_gbs" if hbm_gbs else "recipe fallback 6800 GB/s"
+    hbm_gbs = hbm_gbs or 6800.0
+    P = {"mufu": pk.get("mufu_ex2_tops"), "fp32": pk.get("fp32_ffma_tops"), "tc": pk.get("tf32_tcgen05_tflops"),
+         "hbm": hbm_gbs * 1e-3, "fp64": pk.get("fp64_dfma_tflops")}
+    P = {u: v * 1e12 for u, v in P.items() if v}  # units per second
+
+    # ---- rooflines ----
+    win = out["winner"].cpu().numpy()
+    fwd, bwd, wstats, nsz = query_work(w, model.h, win)
+    both = {u: fwd[u] + bwd[u] for u in fwd}
+    roof = roofline_of(both, qb_ms * 1e-3, P)
+    roof["kernel"] = "query + adjoint (all their kernels, one CUDA graph)"
+    roof["traffic"] = recorded_traffic()
+    roof["algorithmic_bytes"] = both["hbm"]
+    roof["peak_source"] = ("probes of libksdf_peaks.so on this GPU (MUFU ex2, FP32 FFMA lane ops, tcgen05 TF32, "
+                           "FP64 DFMA), measured live; HBM: " + peak_src + " (of measured)")
+    rooflines = {"query": roofline_of(fwd, per.get("query", qb_ms) * 1e-3, P),
+                 "adjoint": roofline_of(bwd, per.get("backward", qb_ms) * 1e-3, P)}
+    if "fit.cholesky" in per and "fp64" in P:
+        fl64 = fit_fp64_flops(nsz)
+        rooflines["fit.cholesky"] = {"bound": "alu", "unit": "TFLOP/s (FP64)",
+                                     "achieved": fl64 / (per["fit.cholesky"] * 1e-3) / 1e12, "peak": P["fp64"] / 1e12,
+                                     "nominal_peak": 1.25,
+                                     "what": "FP64 flops of the factorisation: N^3/3 + 2 N^2 per cell"}
+        rooflines["fit.cholesky"]["frac"] = rooflines["fit.cholesky"]["achieved"] / rooflines["fit.cholesky"]["peak"]
 
     # ---- plain FP64 query on the same inputs (outside the timed region) ----
     xq64 = xq.double()
+    model.query(xq64, sign, f64=True)
+    torch.cuda.synchronize()
     ksdf.ksdf_profile(model.h, 1)
-    for _ in range(2):
-        model.query(xq64, sign, f64=True)
+    model.query(xq64, sign, f64=True)
     st64, _ = ksdf.ksdf_profile_read(model.h)
     ksdf.ksdf_profile(model.h, 0)
+    del xq64
     q64_ms = st64["query64"][0] / st64["query64"][1]
     q32_ms = per.get("query", float("nan"))
 
@@ -536,7 +694,7 @@ def main():
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
-        n_e2e = max(3, min(args.steps, 10))
+        n_e2e = max(3, min(args.steps, 5))
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             e2e_step()
@@ -549,46 +707,47 @@ def main():
                "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
                "how": "ksdf_fit/ksdf_query/ksdf_query_backward with pinned host arrays; the library copies "
                       "in and out inside each call; host wall clock"}
+        del hx, hv, hn, hq, hs, hds, hdg, outs, hdq, hdx
 
-    # ---- CPU FP64 oracle: baseline timing and sampled parity of this run's outputs ----
+    # ---- CPU FP64 oracle: baseline timing and the parity of this run's outputs on its sample ----
     cpu = None
     parity = None
     if not args.no_cpu:
-        cpu, om, sel, ref = oracle_leg(w, args.cpu_sample, args.cpu_repeats)
-        got = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
-        sdf_err = np.abs(got["sdf"][sel].astype(np.float64) - ref["sdf"])
-        fin = np.isfinite(ref["sdf"])
-        same = got["winner"][sel] == ref["winner"]
-        gref = ref["grad"]
-        gg = got["grad"][sel].astype(np.float64)
-        ang = np.degrees(np.arccos(np.clip(np.sum(gg * gref, 1) / np.maximum(
-            np.linalg.norm(gg, axis=1) * np.linalg.norm(gref, axis=1), 1e-300), -1, 1)))
-        vf = np.abs(got["var_f"][sel] - ref["var_f"]) / np.maximum(ref["var_f"], 1e-3)
-        vs = np.abs(got["var_sdf"][sel] - ref["var_sdf"]) / np.maximum(np.abs(ref["var_sdf"]), 1e-30)
-        parity = {"sample": int(len(sel)), "sdf_max_err_m": float(sdf_err[fin].max()),
-                  "sdf_within_1e-4": bool(sdf_err[fin].max() <= 1e-4),
-                  "winner_agree": float(same.mean()),
-                  "grad_angle_p999_deg": float(np.quantile(ang[same & fin], 0.999)),
-                  "var_sdf_max_rel": float(vs[same & fin].max()), "var_f_max_scaled": float(vf[same & fin].max()),
-                  "note": "full per-query checks with medial/tie exclusions are in tests/test_gpu_full.py"}
+        import oracle
 
+        oracle.build()
+        threads = oracle.set_threads(os.cpu_count() or 1)
+        sel, cd_sdf, cd_grad = oracle_sample(w, args.cpu_sample)
+        fit_s, qb_s = [], []
+        for _ in range(max(1, args.cpu_repeats)):
+            tf, tq, ref, om = oracle_step(w, sel, cd_sdf, cd_grad)
+            fit_s.append(tf)
+            qb_s.append(tq)
+        cpu = oracle_stats(w, sel, fit_s, qb_s, threads)
+        got = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+        parity = parity_block(w, sel, ref, om, got)
+        del om
+
+    cfg = workload_config(w, args)  # the same block as the reference arm's
+    run = {"cells": int(len(nsz)), "work": wstats,
+                "launch": ("fit launched from the host (it sizes its launches on the host); query + adjoint replayed "
+                           "from one CUDA graph captured after the warm-up" if not args.no_graph
+                           else "all launched from the host"),
+                "fit_autotune": {"table": tune_idx, "fit_ms_per_table": [round(float(v), 3) for v in tune_ms]},
+                "precision": "FP64 kernel matrix (entries above 2.4e-16; smaller ones in FP32), Cholesky and alpha; "
+                             "FP32 L^-1; FP32 query with compensated mean; V[f] contraction on tcgen05 in TF32 split "
+                             "three ways with FP32 accumulation; FP32 adjoint with one FP64 refinement of each cell "
+                             "solve"}
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "samples": S, "queries": Q, "cells": int(len(nsz)),
-                   "launch": ("fit launched from the host (it sizes its launches on the host); query + adjoint "
-                              "replayed from one CUDA graph captured after the warm-up" if not args.no_graph
-                              else "all launched from the host"),
-                   "fit_autotune": {"table": tune_idx, "fit_ms_per_table": [round(float(v), 3) for v in tune_ms]},
-                   "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "precision": "FP64 kernel matrix (entries above 2.4e-16; smaller ones in FP32), Cholesky and "
-                                "alpha; FP32 L^-1; FP32 query with compensated mean; V[f] contraction on tcgen05 in "
-                                "TF32 split three ways with FP32 accumulation; FP32 adjoint with one FP64 "
-                                "refinement of each cell solve"},
+        "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic", "config": cfg,
+        "run": run,
         "roofline": roof,
-        "rooflines": roof_all,
+        "rooflines": rooflines,
+        "peaks_measured": pk,
         "stage_ms": {k: round(v, 4) for k, v in per.items()},
+        "query_adjoint_ms": qb_ms,
         "plain_fp64": {"query_ms": q64_ms, "mixed_query_ms": q32_ms, "query_speedup": q64_ms / q32_ms},
         "cpu_baseline": cpu,
         "parity": parity,
@@ -599,16 +758,16 @@ def main():
         "step_ms_min_median_max": [float(step_ms.min()), float(np.median(step_ms)), float(step_ms.max())],
     }
     if not args.no_others and world == 1:
-        # the optional SDF-gradient variance on this workload: the same 1M-query forward with and without it
-        tq, ts = xq, sign
-        base_ms = _timed(torch, lambda: model.query(tq, ts), 5)
-        vg_ms = _timed(torch, lambda: model.query(tq, ts, mask=ksdf.OUT_ALL | ksdf.OUT_VAR_GRAD), 5)
-        vg = {"workload": "room3d, 1M queries: forward with the SDF-gradient variance output (Sec. IV-B.3, App. C)",
+        # the optional SDF-gradient variance on this workload: the same forward with and without it
+        base_ms = _timed(torch, lambda: model.query(xq, sign), 3)
+        vg_ms = _timed(torch, lambda: model.query(xq, sign, mask=ksdf.OUT_ALL | ksdf.OUT_VAR_GRAD), 3)
+        vg = {"workload": w.name + ": forward with the SDF-gradient variance output (Sec. IV-B.3, App. C)",
               "query_ms": base_ms, "query_with_var_grad_ms": vg_ms, "var_grad_extra_ms": vg_ms - base_ms,
               "queries_per_s_with_var_grad": Q / (vg_ms * 1e-3)}
-        del model
-        line["other_configs"] = other_configs(torch, dev, ksdf)
-        line["other_configs"]["room3d_var_grad"] = vg
+        del model, graph
+        torch.cuda.empty_cache()
+        line["other_configs"] = other_configs(torch, dev, ksdf, w.name)
+        line["other_configs"][w.name + "_var_grad"] = vg
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -90,7 +90,10 @@ enum {
 enum {
   KSDF_FLAG_FALLBACK = 1u,   /* winner's f' <= 0: u is the distance to its nearest sample */
   KSDF_FLAG_NO_GP = 2u,      /* no valid GP cell exists: sdf = +inf, grad 0, var_sdf 0, var_f 1 */
-  KSDF_FLAG_NEAR_TIE = 4u,   /* the second-best candidate's u is within 1e-5 m of the winner's */
+  KSDF_FLAG_NEAR_TIE = 4u,   /* another candidate's u is within 1e-5 m of the winner's, or (mixed path) may
+                                lie below it given the error bounds of the two FP32 evaluations: the binary64
+                                path could pick that candidate (overlapping GPs of the same surface often agree
+                                to far less than the FP32 error, so the flag is common) */
   KSDF_FLAG_ZERO_GRAD = 8u,  /* grad f' vanished: grad output 0 */
   KSDF_FLAG_CLAMPED = 16u,   /* -log f'/lambda + d^2 < 0 was clamped: u = 0 */
   KSDF_FLAG_INVALID = 32u    /* the query point was NaN/Inf or outside the grid: outputs NaN */
@@ -162,12 +165,6 @@ int ksdf_autotune_tables(void);
  * normal x > 0.  Inputs outside a routine's domain give NaN.  KSDF_ERR_ARG for an unknown fn or n < 0.
  * Synchronises the stream. */
 ksdf_status ksdf_device_math(ksdf_ctx* ctx, int fn, const double* x, int64_t n, double* y);
-
-/* The device's sustained FP64 fused multiply-add rate, the ceiling of the FP64-bound factorisation: one
- * 512-thread block per SM, four dependent chains of 4096 DFMAs per thread, timed with CUDA events on the
- * context's stream after a warm-up launch (about 2 ms).  *tflops (host) receives 2 x FMAs / s / 1e12.
- * Synchronises the stream.  KSDF_ERR_ARG for NULL arguments. */
-ksdf_status ksdf_fp64_rate(ksdf_ctx* ctx, double* tflops);
 
 /* Mixed-precision query: Q points xq (Q x dim float32); sign (Q int8, +1/-1, may be NULL).  FP32 SIMT
  * arithmetic in cell-local coordinates for the mean (compensated sum), gradient and softmin variance; the
@@ -243,23 +240,27 @@ ksdf_status ksdf_profile_read(ksdf_ctx* ctx, int max_stages, char* names, double
  * (ksdf_create allocates), so this call takes no context and allocates nothing: no cudaMalloc, no
  * cudaFree, no allocating library routine.
  *
- * What it computes: the FP64 fit of one training set, exactly as ksdf_fit does for one cell --
- * A = K + diag(sigma^2) with K_ij = exp(-lambda |x_i - x_j|^2), A = L L^T, alpha = A^{-1} 1 (all labels 1),
- * and L^{-1} -- with params->dim and params->lambda (the other fields are not used).
+ * What it computes: the same FP64 fit as ksdf_fit performs for one cell, within 1e-9 relative (ksdf_fit
+ * evaluates kernel entries below 2.4e-16 in FP32 and uses its own exponential, so the two are not bit for bit
+ * equal) -- A = K + diag(sigma^2) with K_ij = exp(-lambda |x_i - x_j|^2), A = L L^T, alpha = A^{-1} 1 (all
+ * labels 1), and L^{-1} -- with params->dim and params->lambda (the other fields are not used).
  *   x       device, N x dim float64 positions (read)
  *   var     device, N float32 sigma_i^2 >= 0 (read; NULL means 0)
  *   alpha   device, N float64 (written; zeros if A is not positive definite)
  *   linv    device, N (N+1) / 2 float64, L^{-1} as packed lower rows (written; unspecified if not PD)
- *   status  device, one int32: KSDF_CELL_OK or KSDF_CELL_NOT_PD (written by the kernel)
+ *   status  device, one int32: KSDF_CELL_OK, or KSDF_CELL_NOT_PD when a pivot is not finite, positive and
+ *           normal, or when an input is NaN/Inf or a variance is negative (written by the kernel)
  *   stream  cudaStream_t the kernel is launched on (NULL = legacy default); the call is asynchronous
- * Every array must be device (or managed) memory: host arrays give KSDF_ERR_ARG, because copying them
- * would need an allocation.  N must be 1..512: larger N gives KSDF_ERR_CAPACITY.
+ * Every array must be device memory of the current device, or managed memory: host arrays and arrays of
+ * another GPU give KSDF_ERR_ARG (copying them would need an allocation).  N must be 1..512: larger N gives
+ * KSDF_ERR_CAPACITY.  KSDF_ERR_CUDA if the launch itself fails.
  * Scratch: a static 1,050,624-byte device array (the packed matrix for N = 512), which every GPU that
  * loads the library holds until the process exits.  All calls on a device share it and it keeps the last
  * call's contents (nothing in it needs to start at zero), so calls that overlap on the GPU -- on different
  * streams, or from different host threads, without ordering between them -- race and give wrong results.
- * The first call on each device resolves the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture. */
+ * The first call on each device resolves the array's device address (cudaGetSymbolAddress) and keeps it for
+ * the life of the process; make that first call before any stream capture.  A cudaDeviceReset of that device
+ * invalidates the kept address: do not use this entry point on a device after resetting it. */
 ksdf_status ksdf_fit_gp_noalloc(const ksdf_params* params, const double* x, const float* var, int64_t N,
                                 double* alpha, double* linv, int32_t* status, void* stream);
 

@@ -406,11 +406,6 @@ ksdf_status ksdf_load(ksdf_ctx* c, const char* path) {
   return ksdf_fit(c, hx.data(), hv.data(), head[2] ? hn.data() : nullptr, S);
 }
 
-ksdf_status ksdf_fp64_rate(ksdf_ctx* c, double* tflops) {
-  if (!c || !tflops) return KSDF_ERR_ARG;
-  return fp64_rate(c, tflops);
-}
-
 ksdf_status ksdf_device_math(ksdf_ctx* c, int fn, const double* x, int64_t n, double* y) {
   if (!c || fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y))) return KSDF_ERR_ARG;
   if (n == 0) return KSDF_OK;

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Par
     float m = INFINITY;
     int nn = 0;
     float f = 0.f, comp = 0.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
+    float wx = 0.f, wy = 0.f, wz = 0.f;
     if (live) {
       for (int i = 0; i < n; ++i) {
         const float4 v = s_x[i];
@@ -143,11 +144,15 @@ __global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Par
           nn = i;
         }
       }
-      const float cmn = c1 * m;
+      // exponents relative to the nearest sample (excess_sq)
+      const float4 xn = s_x[nn];
+      wx = 2.f * (ql[0] - xn.x);
+      wy = 2.f * (ql[1] - xn.y);
+      wz = 2.f * (ql[2] - xn.z);
       for (int i = 0; i < n; ++i) {
         const float4 v = s_x[i];
         const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-        const float kp = ex2(fmaf(-c1, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), cmn));
+        const float kp = ex2(-c1 * excess_sq(v.x, v.y, v.z, xn.x, xn.y, xn.z, wx, wy, wz));
         const float ak = v.w * kp;
         const float y = ak - comp;
         const float tt = f + y;
@@ -203,13 +208,13 @@ __global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Par
       xb2 += ub * (ql[2] - v.z) / d;
     }
     // per-sample contributions, reduced over the warp then into shared memory
-    const float cmn = c1 * m;
+    const float4 xnn = s_x[nn];
     for (int i = 0; i < n; ++i) {
       float ab = 0.f, X0 = 0.f, X1 = 0.f, X2 = 0.f;
       if (live) {
         const float4 v = s_x[i];
         const float r0 = ql[0] - v.x, r1 = ql[1] - v.y, r2v = ql[2] - v.z;
-        const float kp = ex2(fmaf(-c1, fmaf(r0, r0, fmaf(r1, r1, r2v * r2v)), cmn));
+        const float kp = ex2(-c1 * excess_sq(v.x, v.y, v.z, xnn.x, xnn.y, xnn.z, wx, wy, wz));
         const float ak = v.w * kp;
         const float rv = r0 * v0 + r1 * v1 + r2v * v2;
         ab = fb * kp + kp * rv;

@@ -1071,20 +1071,6 @@ static cudaError_t launch_persistent(ksdf_ctx* c, K kern, int team, const Args& 
   return cudaSuccess;
 }
 
-// FP64 FMA throughput probe: four independent dependent chains per thread
-__global__ void k_fp64_rate(int iters, double* sink) {
-  double x0 = 1.0 + 1e-3 * threadIdx.x, x1 = x0 + 0.25, x2 = x0 + 0.5, x3 = x0 + 0.75;
-  const double a = 0.999999, b = 1e-7;
-  for (int i = 0; i < iters; ++i) {
-    x0 = fma(x0, a, b);
-    x1 = fma(x1, a, b);
-    x2 = fma(x2, a, b);
-    x3 = fma(x3, a, b);
-  }
-  if ((x0 + x1) + (x2 + x3) == 0.0) sink[0] = x0;  // never true; keeps the chains
-}
-
-// the fit's scalar device routines on n inputs (diagnostics); NaN outside a routine's domain
 __global__ void k_device_math(int fn, const double* x, int64_t n, double* y) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -1486,28 +1472,6 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
 // candidate size-class tables of the fit (largest class first; the first entry keeps its matrices in a
 // global slot).  Table 0 is the default; ksdf_autotune times them all on the model's own cells.  The result
 // of a fit does not depend on the table (each cell's arithmetic is the same whatever the team size).
-ksdf_status fp64_rate(ksdf_ctx* c, double* tflops) {
-  constexpr int kWarps = 16, kIters = 4096;
-  KSDF_CUDA(c, ensure(c->ws[WS_E], sizeof(int64_t) * 4 + sizeof(int) * 32));
-  double* sink = ptr<double>(c->ws[WS_E]);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  KSDF_CUDA(c, cudaEventCreate(&e0));
-  KSDF_CUDA(c, cudaEventCreate(&e1));
-  launch(k_fp64_rate, c->num_sms, 32 * kWarps, 0, c->stream, kIters, sink);  // warm-up
-  cudaEventRecord(e0, c->stream);
-  launch(k_fp64_rate, c->num_sms, 32 * kWarps, 0, c->stream, kIters, sink);
-  cudaEventRecord(e1, c->stream);
-  cudaError_t e = cudaEventSynchronize(e1);
-  float ms = 0.f;
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  KSDF_CUDA(c, e);
-  const double fmas = (double)c->num_sms * kWarps * 32 * kIters * 4;
-  *tflops = 2.0 * fmas / (ms * 1e-3) / 1e12;
-  return KSDF_OK;
-}
-
 ksdf_status device_math(ksdf_ctx* c, int fn, const double* x, int64_t n, double* y) {
   if (n > 0) launch(k_device_math, ceil_div(n, 256), 256, 0, c->stream, fn, x, n, y);
   KSDF_CUDA(c, cudaGetLastError());

@@ -59,6 +59,20 @@ __device__ inline void base_split(double o, int c, double h, float& hi, float& l
 }
 __device__ __forceinline__ float local32(float x, float hi, float lo) { return __fsub_rn(__fsub_rn(x, hi), lo); }
 
+// The kernel exponent of the scaled posterior mean, lambda (r_i^2 - d^2) with r_i = |q - x_i| and d = |q - x_n|
+// for the GP's nearest sample x_n (App. D scaling), in FP32 cell-local coordinates.  Subtracting the two
+// squares r_i^2 - d^2 (each about d^2) would leave an absolute error of a few 2^-24 d^2, which lambda turns
+// into a relative error of every k'_i of order lambda d^2 2^-23.  The identity
+//   r_i^2 - d^2 = (x_i - x_n) . ((x_i - x_n) - 2 (q - x_n))
+// forms it from the sample-to-sample difference a = x_i - x_n (one rounding of a small number) and the
+// query's offset from x_n, so the error scales with |a| d instead of d^2.  w = 2 (q - x_n) is computed once
+// per query.
+__device__ __forceinline__ float excess_sq(float vx, float vy, float vz, float nx, float ny, float nz, float wx,
+                                           float wy, float wz) {
+  const float ax = vx - nx, ay = vy - ny, az = vz - nz;
+  return fmaf(ax, ax - wx, fmaf(ay, ay - wy, az * (az - wz)));
+}
+
 // hash of a packed key (splitmix64 finaliser)
 __host__ __device__ inline uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
@@ -219,7 +233,6 @@ void prof_end(ksdf_ctx* c, cudaEvent_t a, const char* name);
 // ---- autotuning of the fit's size classes (ksdf_fit.cu) ----
 int fit_table_count();
 ksdf_status device_math(ksdf_ctx* c, int fn, const double* x, int64_t n, double* y);
-ksdf_status fp64_rate(ksdf_ctx* c, double* tflops);
 const std::vector<FitClassCfg>& fit_table(int i);
 ksdf_status autotune_fit(ksdf_ctx* c, int* chosen, double* ms);
 

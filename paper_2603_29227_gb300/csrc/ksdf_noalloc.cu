@@ -29,6 +29,13 @@ std::mutex g_scratch_mu;
 
 __device__ inline int64_t tri_na(int i) { return (int64_t)i * (i + 1) / 2; }
 
+// a usable Cholesky pivot: finite, positive and normal (the regular fit's rule)
+__device__ inline bool pivot_usable(double d) {
+  const long long b = __double_as_longlong(d);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  return b > 0 && ex > 0 && ex < 2047;
+}
+
 // One CTA fits one training set: A, right-looking Cholesky in the scratch, alpha = A^{-1} 1 by two
 // triangular solves, and L^{-1} (packed rows) written straight into the caller's output.
 __global__ void __launch_bounds__(256) k_fit_gp_noalloc(const double* x, const float* var, int N, int dim,
@@ -40,9 +47,24 @@ __global__ void __launch_bounds__(256) k_fit_gp_noalloc(const double* x, const f
   double* sb = sm + 3 * N;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
   if (tid == 0) s_fail = 0;
-  for (int i = tid; i < N; i += nthr)
-    for (int j = 0; j < 3; ++j) sx[3 * i + j] = j < dim ? x[(int64_t)i * dim + j] : 0.0;
   __syncthreads();
+  // inputs: finite coordinates, finite non-negative variances (else the cell is reported not PD untouched)
+  for (int i = tid; i < N; i += nthr) {
+    bool ok = true;
+    for (int j = 0; j < 3; ++j) {
+      const double v = j < dim ? x[(int64_t)i * dim + j] : 0.0;
+      ok &= isfinite(v);
+      sx[3 * i + j] = v;
+    }
+    if (var) ok &= isfinite(var[i]) && var[i] >= 0.f;
+    if (!ok) s_fail = 1;
+  }
+  __syncthreads();
+  if (s_fail) {
+    for (int i = tid; i < N; i += nthr) alpha[i] = 0.0;
+    if (tid == 0) *status = KSDF_CELL_NOT_PD;
+    return;
+  }
   for (int i = warp; i < N; i += nwarp)
     for (int j = lane; j <= i; j += 32) {
       double dx = sx[3 * i] - sx[3 * j], dy = sx[3 * i + 1] - sx[3 * j + 1], dz = sx[3 * i + 2] - sx[3 * j + 2];
@@ -54,7 +76,7 @@ __global__ void __launch_bounds__(256) k_fit_gp_noalloc(const double* x, const f
   for (int k = 0; k < N; ++k) {
     if (tid == 0) {
       double piv = A[tri_na(k) + k];
-      if (!(piv > 0.0)) s_fail = 1;
+      if (!pivot_usable(piv)) s_fail = 1;
       else A[tri_na(k) + k] = sqrt(piv);
     }
     __syncthreads();
@@ -107,13 +129,15 @@ __global__ void __launch_bounds__(256) k_fit_gp_noalloc(const double* x, const f
   if (tid == 0) *status = KSDF_CELL_OK;
 }
 
-bool device_or_managed(const void* p) {
+// memory the kernel may use on device `dev`: device memory of that device, or managed memory
+bool usable_on(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
+    cudaGetLastError();  // the failed query's own error, raised just above
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -126,13 +150,14 @@ extern "C" ksdf_status ksdf_fit_gp_noalloc(const ksdf_params* params, const doub
   if ((params->dim != 2 && params->dim != 3) || !(params->lambda > 0) || !(params->lambda < 1e12))
     return KSDF_ERR_ARG;
   if (N < 1 || N > kNoAllocMaxN) return KSDF_ERR_CAPACITY;
-  // device arrays only: staging host arrays would need an allocation
-  if (!device_or_managed(x) || (var && !device_or_managed(var)) || !device_or_managed(alpha) ||
-      !device_or_managed(linv) || !device_or_managed(status))
-    return KSDF_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return KSDF_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return KSDF_ERR_CAPACITY;
+  // arrays of the current device (or managed) only: staging host arrays, or arrays of another GPU, would need
+  // an allocation or peer access
+  if (!usable_on(x, dev) || (var && !usable_on(var, dev)) || !usable_on(alpha, dev) || !usable_on(linv, dev) ||
+      !usable_on(status, dev))
+    return KSDF_ERR_ARG;
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -147,8 +172,14 @@ extern "C" ksdf_status ksdf_fit_gp_noalloc(const ksdf_params* params, const doub
     scratch = g_scratch_addr[dev];
   }
   const size_t smem = sizeof(double) * 4 * (size_t)N;
-  launch(k_fit_gp_noalloc, 1, 256, smem, static_cast<cudaStream_t>(stream), x, var, (int)N, params->dim,
-         params->lambda, scratch, alpha, linv, status);
-  if (cudaGetLastError() != cudaSuccess) return KSDF_ERR_CUDA;
+  // launched through cudaLaunchKernel so that the status is this launch's own (an earlier, unrelated
+  // asynchronous error is neither reported as this call's nor cleared)
+  int n32 = (int)N, dim = params->dim;
+  double lambda = params->lambda;
+  void* args[] = {(void*)&x, (void*)&var, &n32, &dim, &lambda, &scratch, &alpha, &linv, &status};
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (cudaLaunchKernel((const void*)k_fit_gp_noalloc, dim3(1), dim3(256), args, smem,
+                       static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return KSDF_ERR_CUDA;
   return KSDF_OK;
 }

@@ -448,6 +448,28 @@ __global__ void __launch_bounds__(32 * kCandWarps)
 // ---------------------------------------------------------------------------------------------
 // Q4: phase A, mixed precision
 
+// Upper bound (with a factor 2 of margin) on |u - u_exact| for one candidate GP evaluated in FP32 by k_phaseA,
+// u_exact being the binary64 value on the binary64 data.  Inputs: f = the compensated sum f', sa = the sum of
+// |alpha_i k'_i| on the same scale, m = d^2 (FP32), u, nres = the number of rescalings of the running sum,
+// qa = the largest |coordinate| of the query in the candidate's frame, dxs = the rounding bound of a stored
+// FP32 sample coordinate.  Each term alpha_i k'_i carries a relative error eps from its exponent
+// lambda (r_i^2 - d^2): the FP32 squares (a few 2^-24 r^2), the positions of the sample (dxs) and of the query
+// (2^-23 qa) moving r_i^2 and d^2 by 2 r |delta| -- taken at r^2 = d^2 + 40 / lambda, beyond which the terms
+// are below e^-40 of the largest -- plus ex2.approx and the FP32 alpha; the sums and rescalings add 2^-21
+// and 2^-22 per rescale of sa.  Then d(ln f') = df'/f', d(u^2) = d(ln f')/lambda + the rounding of m and of
+// the final fma, and du = d(u^2) / (u + sqrt(d(u^2))).  f' within its own error of zero gives +inf.
+__device__ __forceinline__ float u_error_bound(float f, float sa, float m, float u, int nres, float qa, float lam,
+                                               float dxs) {
+  const float R = m + 40.f / lam;
+  const float dpos = 1.7320508f * (dxs + qa * 0x1p-23f);
+  const float dr2 = 2.f * sqrtf(R) * dpos + 3.f * 0x1p-24f * R;
+  const float eps = lam * 2.f * dr2 + 1e-6f + (float)nres * 0x1p-22f;
+  const float df = sa * (eps + 0x1p-21f);
+  if (!(f > 2.f * df)) return INFINITY;
+  const float du2 = df / (f * lam) + 0x1p-22f * (fabsf(__logf(f)) / lam + m) + dr2;
+  return 2.f * du2 / (u + sqrtf(du2));
+}
+
 struct PhaseAArgs {
   const int4* tiles;           // (bin, start, count)
   const int64_t* n_tiles;      // device count
@@ -482,6 +504,8 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
   __syncthreads();
   const float c1 = (float)p.lambda * kLog2e;
   const float inv_lam = (float)(1.0 / p.lambda);
+  const float lam = (float)p.lambda;
+  const float dxs = (float)((p.h + p.mu) * 0x1p-24);  // rounding of a stored cell-local FP32 coordinate
   uint32_t phase = 0;
   const int64_t ntiles = *a.n_tiles;
   for (;;) {
@@ -551,7 +575,7 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
     float ql[3] = {0.f, 0.f, 0.f};
     for (int j = 0; j < p.dim; ++j) ql[j] = local32(xg[j], s_bh[j], s_bl[j]);
     const int nc = s_nc;
-    float bu = INFINITY, su = INFINITY;
+    float bu = INFINITY, su = INFINITY, bdu = 0.f, olo = INFINITY;
     int bk = -1;
     uint32_t bflag = 0;
     if (live) {
@@ -559,7 +583,8 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
         const float qx = ql[0] + s_off[k][0], qy = ql[1] + s_off[k][1], qz = ql[2] + s_off[k][2];
         const float4* xs = s_x + s_base[k];
         const int n = s_n[k];
-        float m = INFINITY, s = 0.f, comp = 0.f;
+        float m = INFINITY, s = 0.f, comp = 0.f, sa = 0.f;
+        int nres = 0;
         for (int i0 = 0; i0 < n; i0 += 8) {
           float r2[8], al[8];
 #pragma unroll
@@ -571,15 +596,20 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
           }
           float cm = fminf(fminf(fminf(r2[0], r2[1]), fminf(r2[2], r2[3])), fminf(fminf(r2[4], r2[5]), fminf(r2[6], r2[7])));
           const float mn = fminf(m, cm);
+          nres += mn < m ? 1 : 0;
           const float sc = ex2(c1 * (mn - m));
           s *= sc;
           comp *= sc;
+          sa *= sc;
           const float cmn = c1 * mn;
           float tj[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) tj[j] = al[j] * ex2(fmaf(-c1, r2[j], cmn));
-          // the chunk's terms summed as a tree, then added to the running sum with compensation
+          // the chunk's terms summed as a tree, then added to the running sum with compensation; the sum of
+          // their magnitudes feeds the error bound of u
           const float cs = ((tj[0] + tj[1]) + (tj[2] + tj[3])) + ((tj[4] + tj[5]) + (tj[6] + tj[7]));
+          sa += ((fabsf(tj[0]) + fabsf(tj[1])) + (fabsf(tj[2]) + fabsf(tj[3]))) +
+                ((fabsf(tj[4]) + fabsf(tj[5])) + (fabsf(tj[6]) + fabsf(tj[7])));
           const float y = cs - comp;
           const float tt = s + y;
           comp = (tt - s) - y;
@@ -600,17 +630,23 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
           u = sqrtf(m);
           fl |= KSDF_FLAG_FALLBACK;
         }
+        const float du = u_error_bound(f, sa, m, u, nres, fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))), lam, dxs);
         if (u < bu) {
           su = bu;
+          olo = fminf(olo, bu - bdu);
           bu = u;
+          bdu = du;
           bk = k;
           bflag = fl;
-        } else if (u < su) {
-          su = u;
+        } else {
+          su = fminf(su, u);
+          olo = fminf(olo, u - du);
         }
       }
       uint32_t fl = bflag;
-      if (nc >= 2 && su - bu <= 1e-5f) fl |= KSDF_FLAG_NEAR_TIE;
+      // near tie: another candidate within 1e-5 m, or one whose u may lie below the winner's given the error
+      // bounds of the two FP32 evaluations
+      if (nc >= 2 && (su - bu <= 1e-5f || olo <= bu + bdu)) fl |= KSDF_FLAG_NEAR_TIE;
       if (nc == 0) fl |= KSDF_FLAG_NO_GP;
       a.qwin[q] = bk >= 0 ? s_c[bk] : -1;
       a.qu[q] = bu;
@@ -920,15 +956,17 @@ __global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* 
         }
       const float zmin = sqrtf(m);
       __syncthreads();
-      // pass 2: k'_i (kept for V[f]), grad f', softmin sums
+      // pass 2: k'_i (kept for V[f]), grad f', softmin sums; exponents relative to the nearest sample
       {
         float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
-        const float cmn = c1 * m;
+        const float4 xn = s_x[nn];
+        const float wx = 2.f * (ql[0] - xn.x), wy = 2.f * (ql[1] - xn.y), wz = 2.f * (ql[2] - xn.z);
         for (int i = i0; i < i1; ++i) {
           const float4 v = s_x[i];
           const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float kp = ex2(fmaf(-c1, r2, cmn));
+          const float e = excess_sq(v.x, v.y, v.z, xn.x, xn.y, xn.z, wx, wy, wz);
+          const float r2 = m + e;
+          const float kp = ex2(-c1 * e);
           s_k[i * kBQ + lane] = kp;
           const float ak = v.w * kp;
           G0 = fmaf(ak, dx, G0);
@@ -1216,7 +1254,9 @@ __global__ void __launch_bounds__(kTcM + 32) k_phaseB_tc(PhaseBArgs a, TcArgs t,
         }
       }
       const float zmin = sqrtf(m);
-      const float cmn = c1 * m;
+      // exponents relative to the nearest sample (excess_sq)
+      const float4 xn = s_x[nn];
+      const float wx = 2.f * (ql[0] - xn.x), wy = 2.f * (ql[1] - xn.y), wz = 2.f * (ql[2] - xn.z);
       float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
       for (int c = 0; c < nsteps; ++c) {
         const uint32_t gs = gstep + c;
@@ -1233,8 +1273,9 @@ __global__ void __launch_bounds__(kTcM + 32) k_phaseB_tc(PhaseBArgs a, TcArgs t,
           if (i < n) {
             const float4 v = s_x[i];
             const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            kp = ex2(fmaf(-c1, r2, cmn));
+            const float e = excess_sq(v.x, v.y, v.z, xn.x, xn.y, xn.z, wx, wy, wz);
+            const float r2 = m + e;
+            kp = ex2(-c1 * e);
             const float ak = v.w * kp;
             G0 = fmaf(ak, dx, G0);
             G1 = fmaf(ak, dy, G1);

@@ -31,7 +31,7 @@ ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
                  "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math",
-                 "ksdf_fp64_rate", "ksdf_save", "ksdf_load")
+                 "ksdf_save", "ksdf_load")
 
 
 class KsdfError(RuntimeError):
@@ -81,7 +81,6 @@ def load(path: str = LIB_PATH):
         "ksdf_autotune": [P, ctypes.POINTER(ctypes.c_int), P],
         "ksdf_autotune_tables": [],
         "ksdf_device_math": [P, ctypes.c_int, P, I64, P],
-        "ksdf_fp64_rate": [P, P],
         "ksdf_save": [P, ctypes.c_char_p],
         "ksdf_load": [P, ctypes.c_char_p],
     }
@@ -205,13 +204,6 @@ def ksdf_load(h, path):
     with open(path, "rb") as f:  # S sits after the magic, four int32 and the 72-byte parameter block
         f.seek(8 + 16 + 72)
         return int(np.frombuffer(f.read(8), dtype=np.int64)[0])
-
-
-def ksdf_fp64_rate(h):
-    """The device's sustained FP64 FMA rate in TFLOP/s (a short DFMA-chain probe on the context's stream)."""
-    t = ctypes.c_double(0.0)
-    _check(h, load().ksdf_fp64_rate(h, ctypes.byref(t)), "ksdf_fp64_rate")
-    return float(t.value)
 
 
 def ksdf_update(h, x_new, var_new, normals_new, S_new, allow_not_pd=True):

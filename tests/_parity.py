@@ -5,16 +5,14 @@ Tolerances (the targets of the mixed-precision and plain FP64 paths):
           var_f |err| <= 1e-3 * max(var_f, 1e-3) (var_f is cancellation-bound near the surface).
   fp64    relative <= 1e-9 with floor scale max(|ref|, 1e-3) for sdf, var_f; gradient components
           absolute <= 1e-9 (unit vector); var_sdf relative <= 1e-9.
-Exclusions, each counted and bounded:
-  - near-tie winners (flag bit 2): two candidate GPs within 1e-5 m; the GPU may pick the other one.  The
-    GPU's winner must then be an oracle candidate whose u is within the SDF tolerance of the oracle's
-    minimum, and gradient/variances are compared with the oracle evaluated on the GPU's winner;
-  - medial-axis queries for the gradient angle: cancellation ratio
-    |sum_i a_i k'_i (x - x_i)| / sum_i |a_i| k'_i |x - x_i| < 1e-2 on the winner (the direction of a
-    nearly cancelling sum is ill-conditioned), and zero-gradient flags;
-  - gradients whose FP32 condition estimate kappa = (1 + lambda d^2) 2^-23 / ratio exceeds a tenth of the
-    tolerance (far queries in cancelling configurations, where the 0.1 deg bound is out of reach of any
-    FP32 evaluation); these are still required to stay within 20 kappa.
+Winner choice: where the GPU's winner differs from the oracle's, the query must carry the near-tie flag
+(bit 2) on the GPU or in the oracle -- the mixed path sets it when another candidate's u lies within the
+error bounds of the two FP32 evaluations -- and the GPU's winner must be an oracle candidate whose u is
+within the SDF tolerance of the oracle's minimum; gradient and variances are then compared with the
+oracle evaluated on the GPU's winner.
+Exclusions (each counted): for the gradient angle only, medial-axis queries -- cancellation ratio
+|sum_i a_i k'_i (x - x_i)| / sum_i |a_i| k'_i |x - x_i| < 1e-2 on the winner (the direction of a nearly
+cancelling sum is ill-conditioned) -- and zero-gradient flags.
 """
 import numpy as np
 
@@ -24,6 +22,12 @@ VAR_SDF_REL = 1e-3
 VAR_F_REL, VAR_F_FLOOR = 1e-3, 1e-3
 F64_REL = 1e-9
 MEDIAL_RATIO = 1e-2
+# the FP32 adjoint: relative error of each query's d xq vector, and of the sample gradient d x (max over
+# samples of the error, over the largest entry).  For a cotangent on sdf alone d xq is d sdf times the SDF's
+# gradient: its direction is the forward gradient's (held to 0.1 deg = 1.75e-3 rad) and its magnitude
+# |grad f'| / (lambda u f') carries the same FP32 conditioning (the cancellation in the sums over the winner's
+# samples); the bound takes the direction tolerance for each of the two parts: 2 tan(0.1 deg) = 3.5e-3.
+ADJ_REL = 3.5e-3
 
 
 def cancellation_ratio(model, xq, cells):
@@ -48,14 +52,6 @@ def cancellation_ratio(model, xq, cells):
     return out
 
 
-def fp32_direction_condition(lam, d, ratio):
-    """Expected error (radians) of the gradient direction from FP32 inputs: each term alpha_i k'_i r_i of
-    the gradient sum carries a relative error of about (1 + lambda d^2) 2^-23 (metre-scale differences
-    rounded to FP32, amplified by lambda in the kernel exponent), and the direction of a sum that cancels
-    to `ratio` of its absolute sum is that many times more sensitive."""
-    return (1.0 + lam * d * d) * 2.0 ** -23 / np.maximum(ratio, 1e-300)
-
-
 def _ang_deg(a, b):
     na = np.linalg.norm(a, axis=1)
     nb = np.linalg.norm(b, axis=1)
@@ -78,6 +74,12 @@ def check_mixed(model, xq, sign, gpu, label=""):
     assert stats["sdf_max_err"] <= SDF_TOL, "%s: max |sdf err| %g" % (label, stats["sdf_max_err"])
     diff = gw != rw
     stats["winner_diff"] = int(diff.sum())
+    tie = ((gpu["flags"] | ref["flags"]) & 4) != 0
+    stats["near_tie_flagged"] = int(tie.sum())
+    unflagged = np.nonzero(diff & ~tie)[0]
+    assert unflagged.size == 0, "%s: %d winner disagreements without the near-tie flag, e.g. query %d: gpu %d " \
+        "oracle %d, oracle u of the two %s" % (label, unflagged.size, unflagged[0], gw[unflagged[0]], rw[unflagged[0]],
+                                              ref["cand_u"][unflagged[0]]) if unflagged.size else ""
     if diff.any():
         # the GPU's winner must be an oracle candidate with u within tolerance of the oracle minimum
         for q in np.nonzero(diff)[0]:
@@ -88,23 +90,14 @@ def check_mixed(model, xq, sign, gpu, label=""):
         for key in ("grad", "var_sdf", "var_f"):
             ref[key][diff] = alt[key]
     ok = fin
-    # gradient angle with medial-axis, FP32-conditioning and zero-gradient exclusions
+    # gradient angle with the medial-axis and zero-gradient exclusions only
     ratio = cancellation_ratio(model, xq, np.where(ok, gw, -1))
     zero = ((gpu["flags"] | ref["flags"]) & 8) != 0
     med = ratio < MEDIAL_RATIO
-    lam = model.params["lambda"]
-    d = np.where(fin, np.abs(ref["sdf"]), 0.0)
-    kappa = fp32_direction_condition(lam, d, ratio)  # radians
-    illc = np.degrees(10.0 * kappa) > ANGLE_TOL_DEG
-    gsel = ok & ~zero & ~med & ~illc
+    gsel = ok & ~zero & ~med
     ang = _ang_deg(gpu["grad"].astype(np.float64)[gsel], ref["grad"][gsel])
     stats["angle_max_deg"] = float(ang.max()) if ang.size else 0.0
     stats["medial_excluded"] = int((ok & med).sum())
-    stats["fp32_illcond_excluded"] = int((ok & ~med & illc).sum())
-    isel = ok & ~zero & ~med & illc
-    if isel.any():  # still bounded by their own FP32 conditioning
-        ai = _ang_deg(gpu["grad"].astype(np.float64)[isel], ref["grad"][isel])
-        assert np.all(ai <= np.degrees(20.0 * kappa[isel])), "%s: ill-conditioned gradient beyond 20 kappa" % label
     if ang.size and stats["angle_max_deg"] > ANGLE_TOL_DEG:
         keys, status, off, mem = model.cells()
         idx = np.nonzero(gsel)[0]

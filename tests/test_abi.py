@@ -67,3 +67,23 @@ def test_graft_entry_build_importable():
     import __graft_entry__
 
     assert callable(__graft_entry__.build) and callable(__graft_entry__.smoke)
+
+
+def test_peaks_library_exports_its_header():
+    """The benchmark's probe library (include/ksdf_peaks.h) builds beside libksdf.so and exports what its
+    header declares; libksdf.so itself does not carry the probes."""
+    import ctypes as ct
+
+    from paper_2603_29227_gb300 import build, ksdf, peaks
+
+    build.build()
+    hdr = open(os.path.join(ROOT, "include", "ksdf_peaks.h")).read()
+    names = re.findall(r"^(?:int|const char\*)\s+(ksdf_peaks_\w+)\(", hdr, re.M)
+    assert sorted(names) == ["ksdf_peaks_last_error", "ksdf_peaks_measure"]
+    lib = peaks.load()
+    for n in names:
+        assert hasattr(lib, n), n
+    main = ct.CDLL(ksdf.LIB_PATH)
+    assert not hasattr(main, "ksdf_peaks_measure")
+    # a NULL output pointer is rejected before any CUDA call
+    assert lib.ksdf_peaks_measure(0, None, None) == 1

@@ -14,11 +14,10 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import oracle  # noqa: E402
-from _parity import MEDIAL_RATIO, cancellation_ratio  # noqa: E402
+from _parity import ADJ_REL, MEDIAL_RATIO, cancellation_ratio  # noqa: E402
 from paper_2603_29227_gb300 import ksdf, scenes  # noqa: E402
 
 DEV = torch.device("cuda:0")
-ADJ_REL = 2e-3  # relative error of the FP32 adjoint (per query vector, and over the sample gradient)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -66,13 +65,14 @@ def test_backward_matches_oracle(setup):
         gq = d_xq.cpu().numpy().astype(np.float64)
         gx = d_x.cpu().numpy().astype(np.float64)
         eq = np.linalg.norm(gq - rq, axis=1) / np.maximum(np.linalg.norm(rq, axis=1), 1e-12)
-        assert np.quantile(eq, 0.999) <= ADJ_REL and eq.max() <= 10 * ADJ_REL, (with_grad, eq.max())
+        assert eq.max() <= ADJ_REL, (with_grad, eq.max(), sel[np.argmax(eq)])
         ex = np.max(np.abs(gx - rx)) / np.max(np.abs(rx))
         assert ex <= ADJ_REL, (with_grad, ex)
 
 
 def test_backward_finite_differences(setup):
-    """Central differences of the GPU's own FP32 forward at h = 1e-4 m against the adjoint (d sdf / d xq)."""
+    """Central differences at h = 1e-4 m of the oracle's FP64 forward (at the FP32 points x +- h) against the
+    GPU adjoint d sdf / d xq, for every query whose winner stays the same at both points."""
     w, ref, gm, o, sel = setup
     sel = sel[:400]
     xq = w.xq[sel].astype(np.float32)
@@ -84,17 +84,16 @@ def test_backward_finite_differences(setup):
     for j in range(3):
         e = np.zeros_like(xq)
         e[:, j] = h
-        sp = gm.query(_t(xq + e), _t(sg), mask=ksdf.OUT_SDF | ksdf.OUT_WINNER)
-        sm = gm.query(_t(xq - e), _t(sg), mask=ksdf.OUT_SDF | ksdf.OUT_WINNER)
-        same = (sp["winner"].cpu().numpy() == o["winner"][sel]) & (sm["winner"].cpu().numpy() == o["winner"][sel])
+        sp = ref.query(xq + e, sg)
+        sm = ref.query(xq - e, sg)
+        same = (sp["winner"] == o["winner"][sel]) & (sm["winner"] == o["winner"][sel])
         xp = (xq + e).astype(np.float64)[:, j]
         xm = (xq - e).astype(np.float64)[:, j]
-        fd[:, j] = (sp["sdf"].cpu().numpy().astype(np.float64) - sm["sdf"].cpu().numpy().astype(np.float64)) / (xp - xm)
+        fd[:, j] = (sp["sdf"] - sm["sdf"]) / (xp - xm)
         fd[~same, j] = np.nan
     ok = np.all(np.isfinite(fd), axis=1)
-    err = np.linalg.norm(g[ok] - fd[ok], axis=1)
-    # FP32 forward: |error of the difference| <~ 2 * 6e-8 * |sdf| / (2h); with |sdf| < 1.5 m that is < 1e-3
-    assert ok.sum() > 300 and np.quantile(err, 0.99) <= 5e-3, (ok.sum(), np.quantile(err, 0.99))
+    err = np.linalg.norm(g[ok] - fd[ok], axis=1) / np.linalg.norm(fd[ok], axis=1)
+    assert ok.sum() > 300 and err.max() <= ADJ_REL, (ok.sum(), err.max())
     # eikonal: the exact derivative of the SDF has unit norm off the surface (Sec. III)
     assert np.median(np.abs(np.linalg.norm(g, axis=1) - 1.0)) < 0.02
 
