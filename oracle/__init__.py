@@ -30,6 +30,8 @@ FLAG_NEAR_TIE = 4
 FLAG_ZERO_GRAD = 8
 FLAG_CLAMPED = 16
 CELL_OK, CELL_EMPTY, CELL_NOT_PD = 0, 1, 2
+KERNEL_RBF, KERNEL_MATERN32 = 0, 1
+KERNELS = {"rbf": KERNEL_RBF, "matern32": KERNEL_MATERN32}
 
 
 def build(force: bool = False) -> str:
@@ -49,7 +51,8 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("origin", ctypes.c_double * 3), ("cell", ctypes.c_double),
                 ("margin", ctypes.c_double), ("n_max", ctypes.c_int), ("k_cand", ctypes.c_int),
-                ("lambda_", ctypes.c_double), ("softmin_alpha", ctypes.c_double), ("sign_mode", ctypes.c_int)]
+                ("lambda_", ctypes.c_double), ("softmin_alpha", ctypes.c_double), ("sign_mode", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
 
 def _load():
@@ -106,6 +109,7 @@ def make_params(p: dict) -> _Params:
     q.lambda_ = float(p["lambda"])
     q.softmin_alpha = float(p.get("softmin_alpha", 0.0))
     q.sign_mode = int(p.get("sign_mode", 0))
+    q.kernel = KERNELS[p.get("kernel", "rbf")] if isinstance(p.get("kernel", 0), str) else int(p.get("kernel", 0))
     return q
 
 

@@ -6,7 +6,8 @@
  * is the textbook form of the definition it cites, in the paper's order and notation.
  *
  *   grid / cells / collection boxes      Sec. IV-B.1 (local GPs on overlapping collection boxes)
- *   kernel and inverse transform          Sec. IV-B.2 kernel table (RBF), lambda = 1/(2 l^2) (App. I)
+ *   kernel and inverse transform          Sec. IV-B.2 kernel table: RBF (lambda = 1/(2 l^2), App. I) and
+ *                                         Matern 3/2 (lambda = sqrt(3)/l, the kernel scale of Sec. IV-B.1)
  *   posterior mean, gradient, variance    Sec. IV-B.1 posterior equation
  *   adaptive scaling                      App. D (gamma from the distance d to the nearest sample)
  *   min-fusion of the K nearest GPs       Sec. IV-B.1
@@ -88,6 +89,42 @@ int ko_get_threads(void) {
 /* grid                                                                                             */
 
 static double alpha_softmin(const ko_params* p) { return p->softmin_alpha > 0 ? p->softmin_alpha : p->lambda; }
+
+/* kernel table (Sec. IV-B.2) as a function of the squared distance r2 */
+static double kernel_k(const ko_params* p, double r2) {
+  if (p->kernel == KO_KERNEL_MATERN32) {
+    const double r = sqrt(r2);
+    return (1.0 + p->lambda * r) * exp(-p->lambda * r);
+  }
+  return exp(-p->lambda * r2);
+}
+
+/* The scaled kernel k' = gamma k (App. D) of a sample at squared distance r2 from a query whose nearest
+ * sample is at squared distance d2, and the factor w of its gradient: grad_x k' = -c w (x - x_i) with c from
+ * kernel_grad_c (RBF: w = k', c = 2 lambda; Matern 3/2: w = e^{-lambda (r - d)}, c = lambda^2). */
+static double kernel_scaled(const ko_params* p, double r2, double d2, double* w) {
+  if (p->kernel == KO_KERNEL_MATERN32) {
+    const double r = sqrt(r2), e = exp(-p->lambda * (r - sqrt(d2)));
+    if (w) *w = e;
+    return (1.0 + p->lambda * r) * e;
+  }
+  const double k = exp(-p->lambda * (r2 - d2));
+  if (w) *w = k;
+  return k;
+}
+static double kernel_grad_c(const ko_params* p) {
+  return p->kernel == KO_KERNEL_MATERN32 ? p->lambda * p->lambda : 2.0 * p->lambda;
+}
+/* grad_x k(|x - x_j|) of the unscaled kernel, as -c w (x - x_j): w = k (RBF) or e^{-lambda r} (Matern) */
+static double kernel_grad_w(const ko_params* p, double r2) {
+  if (p->kernel == KO_KERNEL_MATERN32) return exp(-p->lambda * sqrt(r2));
+  return exp(-p->lambda * r2);
+}
+/* 1/gamma^2 = k(d)^2 / k'(d)^2 factor of the GP variance: e^{-2 lambda d^2} (RBF) or e^{-2 lambda d} (Matern) */
+static double kernel_unscale2(const ko_params* p, double d2) {
+  if (p->kernel == KO_KERNEL_MATERN32) return exp(-2.0 * p->lambda * sqrt(d2));
+  return exp(-2.0 * p->lambda * d2);
+}
 
 /* c_j = floor((x_j - o_j) / h) for j < dim, 0 otherwise.  Returns 0 on success. */
 static int bin_point(const ko_params* p, const double* x, int64_t c[3]) {
@@ -220,7 +257,8 @@ void ko_free(ko_model* m) {
 int ko_fit(const ko_params* p, const double* x, const double* var, const double* normals, int64_t S,
            ko_model** out) {
   if (!p || !out || S < 0 || (p->dim != 2 && p->dim != 3) || !(p->cell > 0) || !(p->margin >= 0) ||
-      p->n_max < 1 || p->k_cand < 1 || !(p->lambda > 0))
+      p->n_max < 1 || p->k_cand < 1 || !(p->lambda > 0) ||
+      (p->kernel != KO_KERNEL_RBF && p->kernel != KO_KERNEL_MATERN32))
     return KO_ERR_ARG;
   if (S > 0 && !x) return KO_ERR_ARG;
   const int dim = p->dim;
@@ -354,7 +392,7 @@ int ko_fit(const ko_params* p, const double* x, const double* var, const double*
   free(ts_tmp);
   free(ts_cnt);
 
-  /* 4. fit every cell: A = K + diag(sigma^2), K_ij = exp(-lambda |x_i - x_j|^2); A = L L^T;
+  /* 4. fit every cell: A = K + diag(sigma^2), K_ij = k(|x_i - x_j|) (kernel table); A = L L^T;
    *    alpha = A^{-1} 1 (all labels are f(x_i) = exp(-lambda * 0) = 1, Sec. IV-B.1). */
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t g = 0; g < G; ++g) {
@@ -370,7 +408,7 @@ int ko_fit(const ko_params* p, const double* x, const double* var, const double*
     for (int64_t i = 0; i < N; ++i)
       for (int64_t j = 0; j < N; ++j) {
         double r2 = sqdist(m->x + ids[i] * dim, m->x + ids[j] * dim, dim);
-        A[i * N + j] = exp(-p->lambda * r2) + (i == j ? m->var[ids[i]] : 0.0);
+        A[i * N + j] = kernel_k(p, r2) + (i == j ? m->var[ids[i]] : 0.0);
       }
     if (cholesky(A, L, N)) {
       m->status[g] = KO_CELL_NOT_PD;
@@ -470,8 +508,9 @@ typedef struct {
   uint32_t flags;
 } gp_val;
 
-/* f' = sum_i alpha_i exp(-lambda (r_i^2 - d^2)), d = nearest-sample distance (App. D scaling);
- * u = sqrt(-log f' / lambda + d^2) (scaled RBF inverse of the kernel table). */
+/* f' = sum_i alpha_i k'_i, d = nearest-sample distance (App. D scaling): RBF k'_i = exp(-lambda (r_i^2 - d^2)),
+ * u = sqrt(-log f' / lambda + d^2); Matern 3/2 k'_i = (1 + lambda r_i) exp(-lambda (r_i - d)),
+ * u = -log f' / lambda + d (the scaled inverses of the kernel table). */
 static gp_val gp_value(const ko_model* m, int64_t g, const double* x) {
   const int dim = m->dim;
   const int64_t* ids = m->ts_id + m->ts_off[g];
@@ -485,10 +524,14 @@ static gp_val gp_value(const ko_model* m, int64_t g, const double* x) {
   double fp = 0.0;
   for (int64_t i = 0; i < N; ++i) {
     double r2 = sqdist(x, m->x + ids[i] * dim, dim);
-    fp += m->alpha[g][i] * exp(-lam * (r2 - r.d2));
+    fp += m->alpha[g][i] * kernel_scaled(&m->p, r2, r.d2, NULL);
   }
   r.fp = fp;
-  if (fp > 0.0) {
+  if (fp > 0.0 && m->p.kernel == KO_KERNEL_MATERN32) {
+    double u = -log(fp) / lam + sqrt(r.d2);
+    if (u < 0.0) { r.flags |= KO_FLAG_CLAMPED; u = 0.0; }
+    r.u = u;
+  } else if (fp > 0.0) {
     double u2 = -log(fp) / lam + r.d2;
     if (u2 < 0.0) { r.flags |= KO_FLAG_CLAMPED; u2 = 0.0; }
     r.u = sqrt(u2);
@@ -508,18 +551,20 @@ static void gp_full(const ko_model* m, int64_t g, const double* x, int has_sign,
   const int dim = m->dim;
   const int64_t* ids = m->ts_id + m->ts_off[g];
   const int64_t N = m->ts_off[g + 1] - m->ts_off[g];
-  const double lam = m->p.lambda, as = alpha_softmin(&m->p);
+  const double as = alpha_softmin(&m->p);
   const double* al = m->alpha[g];
   gp_val val = gp_value(m, g, x);
   *flags |= val.flags;
 
-  /* gradient: grad f' = -2 lambda sum_i alpha_i k'_i (x - x_i); grad u = -grad f' / |grad f'| */
+  /* gradient: grad f' = -c sum_i alpha_i w_i (x - x_i) (kernel_scaled); grad u = -grad f' / |grad f'|, the
+   * direction of G = sum_i alpha_i w_i (x - x_i) */
   double Gv[3] = {0, 0, 0};
   for (int64_t i = 0; i < N; ++i) {
     const double* xi = m->x + ids[i] * dim;
+    double w;
     r2[i] = sqdist(x, xi, dim);
-    kp[i] = exp(-lam * (r2[i] - val.d2));
-    for (int j = 0; j < dim; ++j) Gv[j] += al[i] * kp[i] * (x[j] - xi[j]);
+    kp[i] = kernel_scaled(&m->p, r2[i], val.d2, &w);
+    for (int j = 0; j < dim; ++j) Gv[j] += al[i] * w * (x[j] - xi[j]);
   }
   double gn = 0.0;
   for (int j = 0; j < dim; ++j) gn += Gv[j] * Gv[j];
@@ -569,12 +614,12 @@ static void gp_full(const ko_model* m, int64_t g, const double* x, int has_sign,
     *var_sdf = acc;
   }
 
-  /* GP variance: V[f] = k(x,x) - k^T (K+Sigma)^{-1} k = 1 - |L^{-1} k|^2, with k = e^{-lambda d^2} k' */
+  /* GP variance: V[f] = k(x,x) - k^T (K+Sigma)^{-1} k = 1 - |L^{-1} k|^2, with k = k' / gamma */
   if (var_f) {
     forward_subst(m->L[g], N, kp, v);
     double q = 0.0;
     for (int64_t i = 0; i < N; ++i) q += v[i] * v[i];
-    double vf = 1.0 - exp(-2.0 * lam * val.d2) * q;
+    double vf = 1.0 - kernel_unscale2(&m->p, val.d2) * q;
     *var_f = vf > 0.0 ? vf : 0.0;
   }
 }
@@ -815,19 +860,23 @@ int ko_var_grad(const ko_model* m, const float* xq, int64_t Q, const int32_t* ce
 /* ------------------------------------------------------------------------------------------------ */
 /* adjoint                                                                                          */
 
-/* Reverse mode through the forward definitions above, for queries grouped by winner cell g:
- *   u^2 = -log f'/lambda + d^2 with d held constant (u does not depend on the scale gamma, so this is
- *   exact): dL/df' = -s dsdf / (2 lambda u f');  f' = sum_i alpha_i k'_i,  k'_i = e^{-lambda(|x-x_i|^2 - d^2)}.
- *   grad output s G/|G| with G = sum_i alpha_i k'_i (x - x_i): cotangent on G is
- *   v = s (I - g g^T) dgrad / |G|, and dG/dx = sum_i alpha_i k'_i (I - 2 lambda r_i r_i^T).
- *   alpha = A^{-1} 1 with A_ij = exp(-lambda |x_i - x_j|^2) + delta_ij sigma_i^2:
- *   with b = A^{-1} alpha_bar, dL/dx_m += sum_j 2 lambda A_mj (b_m alpha_j + b_j alpha_m)(x_m - x_j).
+/* Reverse mode through the forward definitions above, for queries grouped by winner cell g, with d held
+ * constant (u does not depend on the scale gamma, so this is exact):
+ *   RBF        u^2 = -log f'/lambda + d^2:  dL/df' = -s dsdf / (2 lambda u f');
+ *   Matern 3/2 u = -log f'/lambda + d:      dL/df' = -s dsdf / (lambda f');
+ *   f' = sum_i alpha_i k'_i and grad_x k'_i = -c w_i r_i (kernel_scaled, r_i = x - x_i).
+ *   grad output s G/|G| with G = sum_i alpha_i w_i r_i: cotangent on G is v = s (I - g g^T) dgrad / |G|, and
+ *   dG/dx = sum_i alpha_i w_i (I - beta_i r_i r_i^T), beta_i = 2 lambda (RBF: grad w = -2 lambda w r) or
+ *   lambda / |r_i| (Matern: grad w = -lambda w r / |r|).
+ *   alpha = A^{-1} 1 with A_ij = k(|x_i - x_j|) + delta_ij sigma_i^2, grad_{x_m} A_mj = -c w_mj (x_m - x_j)
+ *   (kernel_grad_w): with b = A^{-1} alpha_bar, dL/dx_m += sum_j c w_mj (b_m alpha_j + b_j alpha_m)(x_m - x_j).
  * The sign, sigma^2 and the winner choice are constants. */
 static int backward_impl(const ko_model* m, const double* xq, int64_t Q, const int8_t* sign, const int32_t* winner_in,
                          const double* d_sdf, const double* d_grad, double* d_xq, double* d_x) {
   if (!m || Q < 0 || (Q > 0 && (!xq || !d_xq || !d_x || (!d_sdf && !d_grad)))) return KO_ERR_ARG;
   const int dim = m->dim;
-  const double lam = m->p.lambda;
+  const double lam = m->p.lambda, cg = kernel_grad_c(&m->p);
+  const int matern = m->p.kernel == KO_KERNEL_MATERN32;
   const int64_t G = m->G;
   int32_t* win = (int32_t*)malloc(sizeof(int32_t) * (size_t)(Q + 1));
   if (!win) return KO_ERR_MEM;
@@ -867,10 +916,13 @@ static int backward_impl(const ko_model* m, const double* xq, int64_t Q, const i
     double* xb = (double*)calloc((size_t)(N * dim), sizeof(double));
     double* ab = (double*)calloc((size_t)N, sizeof(double));
     double* kp = (double*)malloc(sizeof(double) * (size_t)N);
+    double* wv = (double*)malloc(sizeof(double) * (size_t)N);
     double* r = (double*)malloc(sizeof(double) * (size_t)(N * dim));
     double* y = (double*)malloc(sizeof(double) * (size_t)N);
     double* b = (double*)malloc(sizeof(double) * (size_t)N);
-    if (!xb || !ab || !kp || !r || !y || !b) { fail = 1; free(xb); free(ab); free(kp); free(r); free(y); free(b); continue; }
+    if (!xb || !ab || !kp || !wv || !r || !y || !b) {
+      fail = 1; free(xb); free(ab); free(kp); free(wv); free(r); free(y); free(b); continue;
+    }
     for (int64_t t = qoff[g]; t < qoff[g + 1]; ++t) {
       const int64_t q = qlist[t];
       const double* x = xq + q * dim;
@@ -888,9 +940,9 @@ static int backward_impl(const ko_model* m, const double* xq, int64_t Q, const i
       for (int64_t i = 1; i < N; ++i) if (kp[i] < kp[nn]) nn = i;
       double fp = 0.0, Gv[3] = {0, 0, 0};
       for (int64_t i = 0; i < N; ++i) {
-        kp[i] = exp(-lam * (kp[i] - d2));
+        kp[i] = kernel_scaled(&m->p, kp[i], d2, &wv[i]);
         fp += al[i] * kp[i];
-        for (int j = 0; j < dim; ++j) Gv[j] += al[i] * kp[i] * r[i * dim + j];
+        for (int j = 0; j < dim; ++j) Gv[j] += al[i] * wv[i] * r[i * dim + j];
       }
       /* sign, as in the forward pass */
       int s = 1;
@@ -904,11 +956,17 @@ static int backward_impl(const ko_model* m, const double* xq, int64_t Q, const i
       double xqb[3] = {0, 0, 0};
       const double ub = d_sdf ? s * d_sdf[q] : 0.0;
       if (fp > 0.0) {
-        double u2 = -log(fp) / lam + d2;
-        double fb = u2 > 0.0 ? -ub / (2.0 * lam * sqrt(u2) * fp) : 0.0;
-        for (int j = 0; j < dim; ++j) xqb[j] += fb * (-2.0 * lam * Gv[j]);
+        double fb;
+        if (matern) {
+          double u = -log(fp) / lam + sqrt(d2);
+          fb = u > 0.0 ? -ub / (lam * fp) : 0.0;
+        } else {
+          double u2 = -log(fp) / lam + d2;
+          fb = u2 > 0.0 ? -ub / (2.0 * lam * sqrt(u2) * fp) : 0.0;
+        }
+        for (int j = 0; j < dim; ++j) xqb[j] += fb * (-cg * Gv[j]);
         for (int64_t i = 0; i < N; ++i) {
-          for (int j = 0; j < dim; ++j) xb[i * dim + j] += fb * 2.0 * lam * al[i] * kp[i] * r[i * dim + j];
+          for (int j = 0; j < dim; ++j) xb[i * dim + j] += fb * cg * al[i] * wv[i] * r[i * dim + j];
           ab[i] += fb * kp[i];
         }
       } else if (d2 > 0.0) { /* u = |x - x_nn| */
@@ -928,14 +986,16 @@ static int backward_impl(const ko_model* m, const double* xq, int64_t Q, const i
           for (int j = 0; j < dim; ++j) v[j] = s * (gb[j] - gh[j] * dot) / gn;
           for (int64_t i = 0; i < N; ++i) {
             const double* ri = r + i * dim;
-            double rv = 0.0;
-            for (int j = 0; j < dim; ++j) rv += ri[j] * v[j];
+            double rv = 0.0, rn = 0.0;
+            for (int j = 0; j < dim; ++j) { rv += ri[j] * v[j]; rn += ri[j] * ri[j]; }
+            double beta = 2.0 * lam;
+            if (matern) beta = rn > 0.0 ? lam / sqrt(rn) : 0.0;
             for (int j = 0; j < dim; ++j) {
-              double mv = al[i] * kp[i] * (v[j] - 2.0 * lam * ri[j] * rv); /* M_i v */
+              double mv = al[i] * wv[i] * (v[j] - beta * ri[j] * rv); /* (dG/dx)_i v */
               xqb[j] += mv;
               xb[i * dim + j] -= mv;
             }
-            ab[i] += kp[i] * rv;
+            ab[i] += wv[i] * rv;
           }
         }
       }
@@ -949,13 +1009,12 @@ static int backward_impl(const ko_model* m, const double* xq, int64_t Q, const i
       for (int64_t jj = 0; jj < N; ++jj) {
         if (jj == i) continue;
         const double* xj = m->x + ids[jj] * dim;
-        double kij = exp(-lam * sqdist(xi, xj, dim));
-        double c = 2.0 * lam * kij * (b[i] * al[jj] + b[jj] * al[i]);
+        double c = cg * kernel_grad_w(&m->p, sqdist(xi, xj, dim)) * (b[i] * al[jj] + b[jj] * al[i]);
         for (int j = 0; j < dim; ++j) xb[i * dim + j] += c * (xi[j] - xj[j]);
       }
     }
     xbar[g] = xb;
-    free(ab); free(kp); free(r); free(y); free(b);
+    free(ab); free(kp); free(wv); free(r); free(y); free(b);
   }
   if (!fail) {
     for (int64_t g = 0; g < G; ++g) {

@@ -12,12 +12,14 @@
  * Paper references (Kernel-SDF, arXiv 2603.29227):
  *   Sec. III       SDF definition and eikonal property.
  *   Sec. IV-B.1    log-GP posterior mean, gradient and variance; min-fusion of the K nearest local GPs.
- *   Sec. IV-B.2    kernel table (RBF k(r)=exp(-r^2/2l^2), inverse r(f)=sqrt(-2l^2 log f)); scaled inverse.
+ *   Sec. IV-B.2    kernel table (RBF k(r)=exp(-r^2/2l^2), inverse r(f)=sqrt(-2l^2 log f); Matern 3/2
+ *                  k(r)=(1+sqrt3 r/l)exp(-sqrt3 r/l), inverse r(f)=-l log f/sqrt3); scaled inverses.
  *   Sec. IV-B.3    softmin variance of the UDF.
- *   App. D         adaptive scaling (gamma = exp(d^2/2l^2), d = distance to the nearest sample).
+ *   App. D         adaptive scaling (gamma = exp(d^2/2l^2) or exp(sqrt3 d/l), d = distance to the nearest sample).
  *   App. E         softmin limits (used by the tests as pins).
  *   App. F         min-fusion consistency (used by the tests as a magnitude pin).
- * lambda = 1/(2 l^2) as in App. I, so k(r) = exp(-lambda r^2) and u = sqrt(-log f / lambda).
+ * RBF: lambda = 1/(2 l^2) as in App. I, so k(r) = exp(-lambda r^2) and u = sqrt(-log f / lambda).
+ * Matern 3/2: lambda = sqrt3/l, so k(r) = (1 + lambda r) exp(-lambda r) and u = -log f / lambda.
  */
 #ifndef KSDF_ORACLE_H
 #define KSDF_ORACLE_H
@@ -37,7 +39,16 @@ typedef struct {
   double lambda;      /* RBF scale lambda = 1/(2 l^2) */
   double softmin_alpha; /* softmin temperature alpha of Sec. IV-B.3; <= 0 means "equal to lambda" */
   int sign_mode;      /* 0: sign from the caller (or +1 if none); 1: nearest-sample-normal stand-in */
+  int kernel;         /* KO_KERNEL_RBF or KO_KERNEL_MATERN32 (kernel table of Sec. IV-B.2) */
 } ko_params;
+
+/* Kernels of the kernel table (Sec. IV-B.2) with lambda the scale of the exponent f = exp(-lambda u):
+ *   RBF         k(r) = exp(-lambda r^2), lambda = 1/(2 l^2),  u(f) = sqrt(-log f / lambda);
+ *   Matern 3/2  k(r) = (1 + lambda r) exp(-lambda r), lambda = sqrt(3)/l (the kernel scale sqrt(3)/lambda of
+ *               Sec. IV-B.1), u(f) = -log f / lambda.
+ * Scaled (App. D) with gamma = e^{lambda d^2} (RBF) or e^{lambda d} (Matern), d the nearest-sample distance:
+ *   u = sqrt(-log f'/lambda + d^2) (RBF),  u = -log f'/lambda + d (Matern). */
+enum { KO_KERNEL_RBF = 0, KO_KERNEL_MATERN32 = 1 };
 
 typedef struct ko_model ko_model;
 
