@@ -158,6 +158,14 @@ ksdf_status ksdf_load(ksdf_ctx* ctx, const char* path);
 ksdf_status ksdf_autotune(ksdf_ctx* ctx, int* table, double* fit_ms);
 int ksdf_autotune_tables(void);
 
+/* Diagnostic of failure detection (no counterpart in the paper): launches, on the context's stream, one CTA
+ * that allocates tensor memory like the tensor-core query kernel and then waits on an mbarrier that nothing
+ * completes (no copy or MMA is issued, so nothing is in flight), polling it at most `spins` times (1..2^24;
+ * KSDF_ERR_ARG otherwise).  The wait gives up the way a production wait does: the device status word gets the
+ * timeout bit, the tensor memory is released and the kernel returns, so the next ksdf_sync_status() returns
+ * KSDF_ERR_TIMEOUT and the context stays usable.  Asynchronous; returns KSDF_OK once launched. */
+ksdf_status ksdf_wait_diagnostic(ksdf_ctx* ctx, uint32_t spins);
+
 /* Diagnostics: the scalar device routines of the fit (Sec. IV-B kernel matrix exp(-lambda r^2) and the
  * Cholesky pivots), evaluated on n inputs x (float64, host or device) into y (float64, host or device) so
  * that tests can hold them to their error bounds.  fn 0: 2^(-x / 2^16) from a binary64 argument; fn 1: the

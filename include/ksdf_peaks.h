@@ -12,6 +12,8 @@
  *   KSDF_PEAK_FP32_FFMA     FP32 FFMA instructions per second per lane / 1e12 (lane operations, one per FMA;
  *                           the unit the kernels' FP32 operation counts use): eight chains per thread,
  *                           2 x 1024 threads per SM
+ *   KSDF_PEAK_FP32X2_FFMA   FP32 lane FMAs per second / 1e12 issued as packed fma.rn.f32x2 (two per
+ *                           instruction): eight chains per thread, 2 x 1024 threads per SM
  *   KSDF_PEAK_MUFU_EX2      ex2.approx operations per second / 1e12: eight chains per thread, 2 x 1024
  *                           threads per SM
  *   KSDF_PEAK_TF32_TCGEN05  dense TF32 tensor FLOP/s / 1e12 of tcgen05.mma kind::tf32 (M = 128, N = 256,
@@ -27,7 +29,13 @@
 extern "C" {
 #endif
 
-enum { KSDF_PEAK_FP64_DFMA = 0, KSDF_PEAK_FP32_FFMA = 1, KSDF_PEAK_MUFU_EX2 = 2, KSDF_PEAK_TF32_TCGEN05 = 3 };
+enum {
+  KSDF_PEAK_FP64_DFMA = 0,
+  KSDF_PEAK_FP32_FFMA = 1,
+  KSDF_PEAK_MUFU_EX2 = 2,
+  KSDF_PEAK_TF32_TCGEN05 = 3,
+  KSDF_PEAK_FP32X2_FFMA = 4
+};
 
 int ksdf_peaks_measure(int unit, void* stream, double* rate);
 const char* ksdf_peaks_last_error(void);

@@ -406,6 +406,12 @@ ksdf_status ksdf_load(ksdf_ctx* c, const char* path) {
   return ksdf_fit(c, hx.data(), hv.data(), head[2] ? hn.data() : nullptr, S);
 }
 
+ksdf_status ksdf_wait_diagnostic(ksdf_ctx* c, uint32_t spins) {
+  if (!c) return KSDF_ERR_ARG;
+  if (spins == 0 || spins > (1u << 24)) return set_err(c, KSDF_ERR_ARG, "ksdf_wait_diagnostic: spins must be 1..2^24");
+  return wait_diagnostic(c, spins);
+}
+
 ksdf_status ksdf_device_math(ksdf_ctx* c, int fn, const double* x, int64_t n, double* y) {
   if (!c || fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y))) return KSDF_ERR_ARG;
   if (n == 0) return KSDF_OK;

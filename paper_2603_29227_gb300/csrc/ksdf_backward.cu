@@ -12,8 +12,8 @@
 //   alpha_bar_i += k'_i (r_i . v).
 // Through alpha = A^{-1} 1 (A = K + Sigma = L L^T): b = A^{-1} alpha_bar (FP32 L^{-1} products with one
 // FP64 refinement step against L), X_bar_i += sum_j 2 lambda K_ij (b_i alpha_j + b_j alpha_i)(x_i - x_j).
-// Kernel 1 recomputes k' per (query, winner) tile and reduces alpha_bar / X_bar in shared memory; kernel 2
-// runs once per touched cell.
+// Kernel 1 recomputes k' per (query, winner) tile and accumulates alpha_bar / X_bar per sample; kernel 2 runs
+// once per touched cell.
 #include "ksdf_internal.cuh"
 
 #include <algorithm>
@@ -22,7 +22,7 @@ namespace ksdf {
 
 namespace {
 
-constexpr int kTW = 64;
+constexpr int kTW = 128;  // queries per backward tile
 constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ inline float ex2(float x) {
@@ -89,21 +89,37 @@ struct BwArgs {
   double* abar;  // per member
 };
 
-__device__ inline float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+// Per (winner, tile of up to kTW queries), two passes.
+//  Pass 1, a thread per query: the forward recomputation around the nearest sample x_n -- with p = x - x_n and
+//  delta_i = x_n - x_i (so r_i = x - x_i = p + delta_i) and the exponent relative to x_n (excess_sq):
+//    f' = sum_i alpha_i k'_i (compensated),  D = sum_i alpha_i k'_i delta_i,  M = sum_i alpha_i k'_i delta_i delta_i^T,
+//  hence G = sum_i alpha_i k'_i r_i = f' p + D and, for any v, H v = sum_i alpha_i k'_i r_i (r_i . v) =
+//  f' (p.v) p + (p.v) D + p (D.v) + M v.  (Sums of r_i r_i^T would hold d^2 p p^T-sized entries whose product
+//  with v -- orthogonal to the gradient -- cancels; the offsets delta_i are small.)  Then the cotangent scalars
+//  fb = dL/df', v (from d grad) and
+//    x_bar = -2 lambda (fb G + H v) + f' v
+//  (the sum over samples of alpha_i k'_i (v - 2 lambda r_i (r_i . v)) folded into f' and H v), written out; the
+//  query's fb, v, x_n and 2 p go to shared memory.
+//  Pass 2, a thread per sample (and per group of queries when the cell is small): over the tile's queries,
+//    alpha_bar_i += k'_i c,   X_bar_i += alpha_i k'_i (2 lambda c r_i - v),   c = fb + r_i . v,
+//  accumulated in registers, then added once per sample to the global accumulators.
+// A query whose f' <= 0 (the distance fallback) has fb = 0 and its term on the nearest sample added directly.
+constexpr int kTQ = 128;  // backward tile: queries (pass 1) and threads
 
-// per (winner, tile of queries): x_bar per query; alpha_bar and X_bar reduced over the tile
-__global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Params p) {
-  extern __shared__ __align__(16) float4 s_x[];  // [n_max] samples, then [n_max][4] accumulators
+__global__ void __launch_bounds__(kTQ) k_bw_query(BwArgs a, const float* xq, Params p) {
+  extern __shared__ __align__(16) float4 s_x[];  // [n_max] samples | per query: (x, fb) (w, -) (x_n, -) (v, -) |
+                                                 // [kTQ][4] group partial sums
   __shared__ int s_tile;
   __shared__ float s_bh[3], s_bl[3];
-  float* s_acc = reinterpret_cast<float*>(s_x + p.n_max);
-  const int tid = threadIdx.x, lane = tid & 31;
+  float4* QA = s_x + p.n_max;
+  float4* QW = QA + kTQ;
+  float4* QN = QW + kTQ;
+  float4* QV = QN + kTQ;
+  float4* RED = QV + kTQ;
+  const int tid = threadIdx.x;
   const float lam = (float)p.lambda;
   const float c1 = lam * kLog2e;
+  const float tl = 2.f * lam;
   const int64_t ntiles = *a.n_tiles;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(a.counter, 1);
@@ -114,27 +130,20 @@ __global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Par
     const int g = tile.x;
     const int n = a.cell_n[g];
     const int64_t m0 = a.ts_off[g];
-    for (int i = tid; i < n; i += blockDim.x) {
-      s_x[i] = a.mf4[m0 + i];
-      s_acc[4 * i] = s_acc[4 * i + 1] = s_acc[4 * i + 2] = s_acc[4 * i + 3] = 0.f;
-    }
+    for (int i = tid; i < n; i += kTQ) s_x[i] = __ldg(a.mf4 + m0 + i);
     if (tid == 0) {
       int cc[3];
       unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
       for (int j = 0; j < 3; ++j) base_split(p.o[j], cc[j], p.h, s_bh[j], s_bl[j]);
     }
-    const bool live = tid < tile.z;
-    const int q = live ? a.sorted[tile.y + tid] : 0;
     __syncthreads();
-    float ql[3] = {0.f, 0.f, 0.f};
-    if (live)
+    // ---- pass 1: a thread per query ----
+    if (tid < tile.z) {
+      const int q = a.sorted[tile.y + tid];
+      float ql[3] = {0.f, 0.f, 0.f};
       for (int j = 0; j < p.dim; ++j) ql[j] = local32(xq[(int64_t)q * p.dim + j], s_bh[j], s_bl[j]);
-    // forward recomputation
-    float m = INFINITY;
-    int nn = 0;
-    float f = 0.f, comp = 0.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
-    float wx = 0.f, wy = 0.f, wz = 0.f;
-    if (live) {
+      float m = INFINITY;
+      int nn = 0;
       for (int i = 0; i < n; ++i) {
         const float4 v = s_x[i];
         const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
@@ -144,117 +153,132 @@ __global__ void __launch_bounds__(kTW) k_bw_query(BwArgs a, const float* xq, Par
           nn = i;
         }
       }
-      // exponents relative to the nearest sample (excess_sq)
       const float4 xn = s_x[nn];
-      wx = 2.f * (ql[0] - xn.x);
-      wy = 2.f * (ql[1] - xn.y);
-      wz = 2.f * (ql[2] - xn.z);
+      const float px = ql[0] - xn.x, py = ql[1] - xn.y, pz = ql[2] - xn.z;
+      const float wx = 2.f * px, wy = 2.f * py, wz = 2.f * pz;
+      float f = 0.f, comp = 0.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
+      float M00 = 0.f, M01 = 0.f, M02 = 0.f, M11 = 0.f, M12 = 0.f, M22 = 0.f;
       for (int i = 0; i < n; ++i) {
         const float4 v = s_x[i];
-        const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-        const float kp = ex2(-c1 * excess_sq(v.x, v.y, v.z, xn.x, xn.y, xn.z, wx, wy, wz));
-        const float ak = v.w * kp;
+        const float ax = v.x - xn.x, ay = v.y - xn.y, az = v.z - xn.z;  // -delta_i
+        const float e = fmaf(ax, ax - wx, fmaf(ay, ay - wy, az * (az - wz)));
+        const float ak = v.w * ex2(-c1 * e);
         const float y = ak - comp;
         const float tt = f + y;
         comp = (tt - f) - y;
         f = tt;
-        G0 = fmaf(ak, dx, G0);
-        G1 = fmaf(ak, dy, G1);
-        G2 = fmaf(ak, dz, G2);
+        const float bx = ak * ax, by = ak * ay, bz = ak * az;
+        D0 -= bx;
+        D1 -= by;
+        D2 -= bz;
+        M00 = fmaf(bx, ax, M00);
+        M01 = fmaf(bx, ay, M01);
+        M02 = fmaf(bx, az, M02);
+        M11 = fmaf(by, ay, M11);
+        M12 = fmaf(by, az, M12);
+        M22 = fmaf(bz, az, M22);
       }
       f -= comp;
-    }
-    float s = 1.f;
-    if (live) {
+      const float G0 = fmaf(f, px, D0), G1 = fmaf(f, py, D1), G2 = fmaf(f, pz, D2);
+      float s = 1.f;
       if (a.sign) {
         s = a.sign[q] < 0 ? -1.f : 1.f;
       } else if (p.sign_mode == 1 && a.has_normals) {
-        const float4 v = s_x[nn];
         const float4 nv = a.mnrm[m0 + nn];
-        s = (nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z)) >= 0.f ? 1.f : -1.f;
+        s = (nv.x * (ql[0] - xn.x) + nv.y * (ql[1] - xn.y) + nv.z * (ql[2] - xn.z)) >= 0.f ? 1.f : -1.f;
       }
-    }
-    const float ub = live ? s * a.d_sdf[q] : 0.f;
-    float fb = 0.f;
-    bool fallback = false;
-    if (live) {
-      if (f > 0.f) {
+      const float ub = s * a.d_sdf[q];
+      float fb = 0.f;
+      const bool fallback = !(f > 0.f);
+      if (!fallback) {
         const float u2 = fmaf(-logf(f), 1.f / lam, m);
         fb = u2 > 0.f ? -ub / (2.f * lam * sqrtf(u2) * f) : 0.f;
-      } else {
-        fallback = true;
       }
-    }
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-    if (live && a.d_grad) {
-      const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
-      if (gn > 0.f) {
-        const float g0 = G0 / gn, g1 = G1 / gn, g2 = G2 / gn;
-        const float b0 = a.d_grad[(int64_t)q * p.dim + 0], b1 = a.d_grad[(int64_t)q * p.dim + 1];
-        const float b2 = p.dim == 3 ? a.d_grad[(int64_t)q * p.dim + 2] : 0.f;
-        const float dot = g0 * b0 + g1 * b1 + g2 * b2;
-        const float sc = s / gn;
-        v0 = sc * (b0 - g0 * dot);
-        v1 = sc * (b1 - g1 * dot);
-        v2 = sc * (b2 - g2 * dot);
-      }
-    }
-    float xb0 = fb * (-2.f * lam * G0), xb1 = fb * (-2.f * lam * G1), xb2 = fb * (-2.f * lam * G2);
-    if (live && fallback && m > 0.f) {
-      const float4 v = s_x[nn];
-      const float d = sqrtf(m);
-      xb0 += ub * (ql[0] - v.x) / d;
-      xb1 += ub * (ql[1] - v.y) / d;
-      xb2 += ub * (ql[2] - v.z) / d;
-    }
-    // per-sample contributions, reduced over the warp then into shared memory
-    const float4 xnn = s_x[nn];
-    for (int i = 0; i < n; ++i) {
-      float ab = 0.f, X0 = 0.f, X1 = 0.f, X2 = 0.f;
-      if (live) {
-        const float4 v = s_x[i];
-        const float r0 = ql[0] - v.x, r1 = ql[1] - v.y, r2v = ql[2] - v.z;
-        const float kp = ex2(-c1 * excess_sq(v.x, v.y, v.z, xnn.x, xnn.y, xnn.z, wx, wy, wz));
-        const float ak = v.w * kp;
-        const float rv = r0 * v0 + r1 * v1 + r2v * v2;
-        ab = fb * kp + kp * rv;
-        const float tl = 2.f * lam * rv;
-        const float mv0 = ak * (v0 - tl * r0), mv1 = ak * (v1 - tl * r1), mv2 = ak * (v2 - tl * r2v);
-        xb0 += mv0;
-        xb1 += mv1;
-        xb2 += mv2;
-        const float dir = fb * 2.f * lam * ak;
-        X0 = dir * r0 - mv0;
-        X1 = dir * r1 - mv1;
-        X2 = dir * r2v - mv2;
-        if (fallback && i == nn && m > 0.f) {
-          const float d = sqrtf(m);
-          X0 -= ub * r0 / d;
-          X1 -= ub * r1 / d;
-          X2 -= ub * r2v / d;
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      if (a.d_grad) {
+        const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
+        if (gn > 0.f) {
+          const float g0 = G0 / gn, g1 = G1 / gn, g2 = G2 / gn;
+          const float b0 = a.d_grad[(int64_t)q * p.dim + 0], b1 = a.d_grad[(int64_t)q * p.dim + 1];
+          const float b2 = p.dim == 3 ? a.d_grad[(int64_t)q * p.dim + 2] : 0.f;
+          const float dot = g0 * b0 + g1 * b1 + g2 * b2;
+          const float sc = s / gn;
+          v0 = sc * (b0 - g0 * dot);
+          v1 = sc * (b1 - g1 * dot);
+          v2 = sc * (b2 - g2 * dot);
         }
       }
-      ab = warp_sum(ab);
-      X0 = warp_sum(X0);
-      X1 = warp_sum(X1);
-      X2 = warp_sum(X2);
-      if (lane == 0) {
-        atomicAdd(&s_acc[4 * i], ab);
-        atomicAdd(&s_acc[4 * i + 1], X0);
-        atomicAdd(&s_acc[4 * i + 2], X1);
-        atomicAdd(&s_acc[4 * i + 3], X2);
+      // x_bar = -2 lambda (fb G + H v) + f' v,  H v = f' (p.v) p + (p.v) D + p (D.v) + M v
+      const float pv = fmaf(px, v0, fmaf(py, v1, pz * v2)), dv = fmaf(D0, v0, fmaf(D1, v1, D2 * v2));
+      const float fpv = f * pv;
+      const float hv0 = fmaf(fpv, px, fmaf(pv, D0, fmaf(px, dv, fmaf(M00, v0, fmaf(M01, v1, M02 * v2)))));
+      const float hv1 = fmaf(fpv, py, fmaf(pv, D1, fmaf(py, dv, fmaf(M01, v0, fmaf(M11, v1, M12 * v2)))));
+      const float hv2 = fmaf(fpv, pz, fmaf(pv, D2, fmaf(pz, dv, fmaf(M02, v0, fmaf(M12, v1, M22 * v2)))));
+      float xb0 = fmaf(-tl, fmaf(fb, G0, hv0), f * v0);
+      float xb1 = fmaf(-tl, fmaf(fb, G1, hv1), f * v1);
+      float xb2 = fmaf(-tl, fmaf(fb, G2, hv2), f * v2);
+      if (fallback && m > 0.f) {
+        // u = distance to the nearest sample: its own derivative, on the query and on that sample
+        const float d = sqrtf(m);
+        const float e0 = ub * (ql[0] - xn.x) / d, e1 = ub * (ql[1] - xn.y) / d, e2 = ub * (ql[2] - xn.z) / d;
+        xb0 += e0;
+        xb1 += e1;
+        xb2 += e2;
+        const int gid = a.mgid[m0 + nn];
+        atomicAdd(&a.d_x[(int64_t)gid * p.dim + 0], -e0);
+        atomicAdd(&a.d_x[(int64_t)gid * p.dim + 1], -e1);
+        if (p.dim == 3) atomicAdd(&a.d_x[(int64_t)gid * p.dim + 2], -e2);
       }
-    }
-    if (live) {
       a.d_xq[(int64_t)q * p.dim + 0] = xb0;
       a.d_xq[(int64_t)q * p.dim + 1] = xb1;
       if (p.dim == 3) a.d_xq[(int64_t)q * p.dim + 2] = xb2;
+      QA[tid] = make_float4(ql[0], ql[1], ql[2], fb);
+      QW[tid] = make_float4(wx, wy, wz, 0.f);
+      QN[tid] = make_float4(xn.x, xn.y, xn.z, 0.f);
+      QV[tid] = make_float4(v0, v1, v2, 0.f);
     }
     __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x) {
-      atomicAdd(&a.abar[m0 + i], (double)s_acc[4 * i]);
-      const int gid = a.mgid[m0 + i];
-      for (int j = 0; j < p.dim; ++j) atomicAdd(&a.d_x[(int64_t)gid * p.dim + j], s_acc[4 * i + 1 + j]);
+    // ---- pass 2: a thread per (sample, group of queries) ----
+    const int nrep = n < kTQ ? kTQ / n : 1;  // query groups when the cell is small
+    const int grp = tid / (n < kTQ ? n : kTQ);
+    const int nq = tile.z;
+    for (int i0 = 0; i0 < n; i0 += kTQ) {
+      const int i = i0 + (n < kTQ ? tid - grp * n : tid);
+      const bool act = grp < nrep && i < n;
+      float ab = 0.f, X0 = 0.f, X1 = 0.f, X2 = 0.f;
+      if (act) {
+        const float4 xi = s_x[i];
+        for (int qq = grp; qq < nq; qq += nrep) {
+          const float4 A = QA[qq], W = QW[qq], Nn = QN[qq], V = QV[qq];
+          const float r0 = A.x - xi.x, r1 = A.y - xi.y, r2 = A.z - xi.z;
+          const float kp = ex2(-c1 * excess_sq(xi.x, xi.y, xi.z, Nn.x, Nn.y, Nn.z, W.x, W.y, W.z));
+          const float c = fmaf(r0, V.x, fmaf(r1, V.y, fmaf(r2, V.z, A.w)));
+          ab = fmaf(kp, c, ab);
+          const float ak = xi.w * kp, t2 = tl * c;
+          X0 = fmaf(ak, fmaf(t2, r0, -V.x), X0);
+          X1 = fmaf(ak, fmaf(t2, r1, -V.y), X1);
+          X2 = fmaf(ak, fmaf(t2, r2, -V.z), X2);
+        }
+      }
+      if (nrep > 1) {  // combine the query groups of each sample
+        RED[tid] = make_float4(ab, X0, X1, X2);
+        __syncthreads();
+        if (grp == 0 && act)
+          for (int r = 1; r < nrep; ++r) {
+            const float4 o = RED[r * n + tid];
+            ab += o.x;
+            X0 += o.y;
+            X1 += o.z;
+            X2 += o.w;
+          }
+      }
+      if (grp == 0 && act) {
+        atomicAdd(&a.abar[m0 + i], (double)ab);
+        const int gid = a.mgid[m0 + i];
+        atomicAdd(&a.d_x[(int64_t)gid * p.dim + 0], X0);
+        atomicAdd(&a.d_x[(int64_t)gid * p.dim + 1], X1);
+        if (p.dim == 3) atomicAdd(&a.d_x[(int64_t)gid * p.dim + 2], X2);
+      }
     }
     __syncthreads();
   }
@@ -435,12 +459,12 @@ ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* 
   a.d_xq = d_xq;
   a.d_x = d_x;
   a.abar = abar;
-  const size_t smem = sizeof(float4) * p.n_max + sizeof(float) * 4 * p.n_max;
+  const size_t smem = sizeof(float4) * (p.n_max + 5 * kTQ);
   KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bw_query, kTW, smem));
+  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bw_query, kTQ, smem));
   e0 = prof_begin(c);
-  launch(k_bw_query, std::max(1, occ) * c->num_sms, kTW, smem, st, a, xq, p);
+  launch(k_bw_query, std::max(1, occ) * c->num_sms, kTQ, smem, st, a, xq, p);
   prof_end(c, e0, "backward.query");
   e0 = prof_begin(c);
   const size_t smem2 = sizeof(double) * 3 * p.n_max + sizeof(float) * 3 * p.n_max;

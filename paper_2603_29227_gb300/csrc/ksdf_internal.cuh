@@ -258,6 +258,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
                       void* grad, void* var_sdf, void* var_f, void* var_grad, int32_t* winner, uint32_t* flags);
 ksdf_status candidates_for_keys(ksdf_ctx* c, const uint64_t* keys, int64_t n, int32_t* cand, int32_t* count);
 ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G);
+ksdf_status wait_diagnostic(ksdf_ctx* c, uint32_t spins);
 
 // ---- backward (ksdf_backward.cu) ----
 ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, const int32_t* winner,

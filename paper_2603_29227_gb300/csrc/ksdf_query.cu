@@ -490,23 +490,73 @@ struct PhaseAArgs {
   uint32_t* st;
 };
 
+// packed FP32x2 arithmetic (two lanes of one thread per instruction): a u64 holds (lo, hi) floats
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f2unpack(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Phase A shared memory, per tile: candidates' samples as chunks of 8 in SoA form -- one chunk is 40 floats,
+// x[8] y[8] z[8] alpha[8] |alpha|[8] -- each candidate padded to whole chunks with far zero-weight samples, at
+// most kChunkBudget chunks at a time (a tile whose candidates hold more is done in rounds of whole candidates);
+// then the per-(candidate, query) results u, du and flag bits.
+constexpr int kChunkF = 40;
+constexpr int kChunkBudget = 128;  // 20 KB of samples
+__host__ __device__ inline int phase_a_chunks(int n_max) { return max(kChunkBudget, (n_max + 7) / 8); }
+__host__ __device__ inline size_t phase_a_smem(int K, int n_max) {
+  return sizeof(float) * (size_t)kChunkF * phase_a_chunks(n_max) + (size_t)K * kTA * (2 * sizeof(float) + 1);
+}
+
+// One CTA per tile of up to kTA queries of one bin.  The candidates' samples are read into shared memory (SoA
+// chunks); the warps then pull tasks (candidate k, block of 32 queries) and for a task each lane evaluates one
+// query on candidate k over its samples, eight per step with packed FP32x2 arithmetic:
+//   r_i^2 = |q - x_i|^2, the running minimum m = d^2 (App. D), rescaled sums
+//   f' = sum_i alpha_i 2^{c1 (m - r_i^2)} (Kahan-compensated across steps) and sum_i |alpha_i| 2^{c1 (m - r_i^2)},
+//   u = sqrt(-log f' / lambda + m) (kernel table) with its error bound (u_error_bound).
+// Finally a thread per query takes the minimum over the candidates in list order (min-fusion, Sec. IV-B.1), the
+// first on equal u, and sets the near-tie flag from the error bounds.
 __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, Params p) {
-  extern __shared__ __align__(128) float4 s_x[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ int s_tile, s_nc, s_c[kMaxK], s_n[kMaxK], s_base[kMaxK];
+  extern __shared__ __align__(16) float sA[];
+  __shared__ int s_tile, s_nc, s_task, s_k1, s_c[kMaxK], s_n[kMaxK], s_ch[kMaxK];
   __shared__ float s_off[kMaxK][3];
+  __shared__ float s_ql[kTA][3];
   __shared__ float s_bh[3], s_bl[3];
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    fence_proxy_async();
-  }
-  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int K = p.K;
   const float c1 = (float)p.lambda * kLog2e;
   const float inv_lam = (float)(1.0 / p.lambda);
   const float lam = (float)p.lambda;
   const float dxs = (float)((p.h + p.mu) * 0x1p-24);  // rounding of a stored cell-local FP32 coordinate
-  uint32_t phase = 0;
+  const int budget = phase_a_chunks(p.n_max);
+  float* s_u = sA + (size_t)kChunkF * budget;
+  float* s_du = s_u + K * kTA;
+  uint8_t* s_fl = reinterpret_cast<uint8_t*>(s_du + K * kTA);
   const int64_t ntiles = *a.n_tiles;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(a.counter, 1);
@@ -517,106 +567,130 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
     const int b = tile.x;
     int bc[3];
     unpack_key(a.bin_key[b], bc[0], bc[1], bc[2]);
-    if (tid < 32) {
-      // the first warp sets the tile up, a lane per candidate (their loads and FP64 offsets in parallel):
-      // offsets of the candidates' padded sample runs by a warp scan, then one bulk copy per lane
-      const int lane = tid;
+    if (tid < 32) {  // the candidate list and the candidates' frame offsets, a lane per candidate
       const int nc = a.ncand[b];
-      int g = -1, n = 0;
       if (lane < nc) {
-        g = a.cand[(int64_t)b * p.K + lane];
-        n = a.cell_n[g];
-      }
-      const int pad = (n + 7) & ~7;  // each candidate padded to a multiple of 8 samples
-      int incl = pad;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const int base = incl - pad;
-      int bytes = n * 16;
-      for (int o = 16; o; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
-      if (lane < nc) {
+        const int g = a.cand[(int64_t)b * K + lane];
         s_c[lane] = g;
-        s_n[lane] = n;
-        s_base[lane] = base;
+        s_n[lane] = a.cell_n[g];
         int cc[3];
         unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
         for (int j = 0; j < 3; ++j) s_off[lane][j] = (float)((double)(bc[j] - cc[j]) * p.h);
       }
-      if (lane < 3) base_split(p.o[lane], bc[lane], p.h, s_bh[lane], s_bl[lane]);
-      if (lane == 0) {
-        s_nc = nc;
-        mbar_expect_tx(&bar, (uint32_t)bytes);
-      }
-      __syncwarp();
-      if (lane < nc && n > 0) {
-        fence_proxy_async();
-        bulk_g2s(s_x + base, a.mf4 + a.ts_off[g], (uint32_t)n * 16u, &bar);
-      }
+      if (lane == 0) s_nc = nc;
+      if (lane < 3) base_split(p.o[lane], bc[lane], p.h, s_bh[lane], s_bl[lane]);  // the bin corner, binary64 once
     }
-    __syncthreads();  // candidate list known
-    // padding samples: far away with zero weight, so that every chunk of 8 is full (no per-sample guards)
-    for (int e = tid; e < s_nc * 8; e += blockDim.x) {
-      const int k = e >> 3, i = s_n[k] + (e & 7);
-      if (i < ((s_n[k] + 7) & ~7)) s_x[s_base[k] + i] = make_float4(1e15f, 1e15f, 1e15f, 0.f);
+    __syncthreads();
+    // the tile's queries in the bin's frame (FP32 two-term subtraction of the bin corner)
+    {
+      const bool live = tid < tile.z;
+      const int q = live ? a.sorted_q[tile.y + tid] : 0;
+      for (int j = 0; j < 3; ++j)
+        s_ql[tid][j] = (live && j < p.dim) ? local32(xq[(int64_t)q * p.dim + j], s_bh[j], s_bl[j]) : 0.f;
     }
-    const bool live = tid < tile.z;
-    const int q = live ? a.sorted_q[tile.y + tid] : 0;
-    float xg[3] = {0.f, 0.f, 0.f};
-    if (live)
-      for (int j = 0; j < p.dim; ++j) xg[j] = xq[(int64_t)q * p.dim + j];
-    if (!mbar_wait_all(&bar, phase)) {
-      if (tid == 0) atomicOr(a.st, ST_TIMEOUT);
-      return;
-    }
-    phase ^= 1;
-    // the query in the bin's frame (FP32 two-term subtraction of the bin corner)
-    float ql[3] = {0.f, 0.f, 0.f};
-    for (int j = 0; j < p.dim; ++j) ql[j] = local32(xg[j], s_bh[j], s_bl[j]);
+    __syncthreads();
     const int nc = s_nc;
-    float bu = INFINITY, su = INFINITY, bdu = 0.f, olo = INFINITY;
-    int bk = -1;
-    uint32_t bflag = 0;
-    if (live) {
-      for (int k = 0; k < nc; ++k) {
-        const float qx = ql[0] + s_off[k][0], qy = ql[1] + s_off[k][1], qz = ql[2] + s_off[k][2];
-        const float4* xs = s_x + s_base[k];
-        const int n = s_n[k];
-        float m = INFINITY, s = 0.f, comp = 0.f, sa = 0.f;
+    const int nqb = (tile.z + 31) >> 5;
+    for (int k0 = 0; k0 < nc;) {
+      // a round: candidates k0 .. k1-1 whose chunks fit the budget (at least one)
+      if (tid == 0) {
+        int k1 = k0, tot = 0;
+        while (k1 < nc && (k1 == k0 || tot + ((s_n[k1] + 7) >> 3) <= budget)) {
+          s_ch[k1] = tot;
+          tot += (s_n[k1] + 7) >> 3;
+          ++k1;
+        }
+        s_k1 = k1;
+        s_task = 0;
+      }
+      __syncthreads();
+      const int k1 = s_k1;
+      // samples into SoA chunks: thread e takes sample slot e of the round's flattened (candidate, slot) space
+      {
+        const int tot = 8 * (s_ch[k1 - 1] + ((s_n[k1 - 1] + 7) >> 3));
+        int k = k0;
+        for (int e = tid; e < tot; e += kTA) {
+          while (k + 1 < k1 && e >= 8 * s_ch[k + 1]) ++k;
+          const int i = e - 8 * s_ch[k];
+          float4 v = make_float4(1e15f, 1e15f, 1e15f, 0.f);  // padding: far away, zero weight
+          if (i < s_n[k]) v = __ldg(a.mf4 + a.ts_off[s_c[k]] + i);
+          float* ch = sA + (size_t)kChunkF * (s_ch[k] + (i >> 3)) + (i & 7);
+          ch[0] = v.x;
+          ch[8] = v.y;
+          ch[16] = v.z;
+          ch[24] = v.w;
+          ch[32] = fabsf(v.w);
+        }
+      }
+      __syncthreads();
+      const int ntask = (k1 - k0) * nqb;
+      for (;;) {
+        int task = 0;
+        if (lane == 0) task = atomicAdd(&s_task, 1);
+        task = __shfl_sync(0xffffffffu, task, 0);
+        if (task >= ntask) break;
+        const int k = k0 + task / nqb;
+        const int qi = (task % nqb) * 32 + lane;
+        const int qs = qi < tile.z ? qi : 0;
+        const float qx = s_ql[qs][0] + s_off[k][0], qy = s_ql[qs][1] + s_off[k][1], qz = s_ql[qs][2] + s_off[k][2];
+        const unsigned long long QX = f2pack(qx, qx), QY = f2pack(qy, qy), QZ = f2pack(qz, qz);
+        const unsigned long long NC1 = f2pack(-c1, -c1);
+        const float* ch = sA + (size_t)kChunkF * s_ch[k];
+        const int nch = (s_n[k] + 7) >> 3;
+        float m = INFINITY, s = 0.f, comp = 0.f;
+        unsigned long long SA = f2pack(0.f, 0.f);
         int nres = 0;
-        for (int i0 = 0; i0 < n; i0 += 8) {
-          float r2[8], al[8];
+        for (int c = 0; c < nch; ++c, ch += kChunkF) {
+          const float4* c4 = reinterpret_cast<const float4*>(ch);
+          unsigned long long r2[4];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 v = xs[i0 + j];
-            const float dx = qx - v.x, dy = qy - v.y, dz = qz - v.z;
-            r2[j] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            al[j] = v.w;
+          for (int h = 0; h < 2; ++h) {
+            const float4 x4 = c4[h], y4 = c4[2 + h], z4 = c4[4 + h];
+            const unsigned long long dx0 = f2sub(QX, f2pack(x4.x, x4.y)), dx1 = f2sub(QX, f2pack(x4.z, x4.w));
+            const unsigned long long dy0 = f2sub(QY, f2pack(y4.x, y4.y)), dy1 = f2sub(QY, f2pack(y4.z, y4.w));
+            const unsigned long long dz0 = f2sub(QZ, f2pack(z4.x, z4.y)), dz1 = f2sub(QZ, f2pack(z4.z, z4.w));
+            r2[2 * h] = f2fma(dx0, dx0, f2fma(dy0, dy0, f2mul(dz0, dz0)));
+            r2[2 * h + 1] = f2fma(dx1, dx1, f2fma(dy1, dy1, f2mul(dz1, dz1)));
           }
-          float cm = fminf(fminf(fminf(r2[0], r2[1]), fminf(r2[2], r2[3])), fminf(fminf(r2[4], r2[5]), fminf(r2[6], r2[7])));
+          float rv[8];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float2 u = f2unpack(r2[h]);
+            rv[2 * h] = u.x;
+            rv[2 * h + 1] = u.y;
+          }
+          const float cm = fminf(fminf(fminf(rv[0], rv[1]), fminf(rv[2], rv[3])),
+                                 fminf(fminf(rv[4], rv[5]), fminf(rv[6], rv[7])));
           const float mn = fminf(m, cm);
           nres += mn < m ? 1 : 0;
           const float sc = ex2(c1 * (mn - m));
           s *= sc;
           comp *= sc;
-          sa *= sc;
-          const float cmn = c1 * mn;
-          float tj[8];
+          SA = f2mul(SA, f2pack(sc, sc));
+          m = mn;
+          const unsigned long long CMN = f2pack(c1 * mn, c1 * mn);
+          unsigned long long T[4];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) tj[j] = al[j] * ex2(fmaf(-c1, r2[j], cmn));
-          // the chunk's terms summed as a tree, then added to the running sum with compensation; the sum of
-          // their magnitudes feeds the error bound of u
-          const float cs = ((tj[0] + tj[1]) + (tj[2] + tj[3])) + ((tj[4] + tj[5]) + (tj[6] + tj[7]));
-          sa += ((fabsf(tj[0]) + fabsf(tj[1])) + (fabsf(tj[2]) + fabsf(tj[3]))) +
-                ((fabsf(tj[4]) + fabsf(tj[5])) + (fabsf(tj[6]) + fabsf(tj[7])));
+          for (int h = 0; h < 4; ++h) {
+            const float2 ev = f2unpack(f2fma(NC1, r2[h], CMN));
+            const unsigned long long kk = f2pack(ex2(ev.x), ex2(ev.y));
+            const float4 al4 = c4[6 + (h >> 1)], ab4 = c4[8 + (h >> 1)];
+            const unsigned long long AL = (h & 1) ? f2pack(al4.z, al4.w) : f2pack(al4.x, al4.y);
+            const unsigned long long AB = (h & 1) ? f2pack(ab4.z, ab4.w) : f2pack(ab4.x, ab4.y);
+            T[h] = f2mul(AL, kk);
+            SA = f2fma(AB, kk, SA);
+          }
+          // the step's eight terms summed as a tree, then added to the running sum with compensation
+          const float2 cs2 = f2unpack(f2add(f2add(T[0], T[1]), f2add(T[2], T[3])));
+          const float cs = cs2.x + cs2.y;
           const float y = cs - comp;
           const float tt = s + y;
           comp = (tt - s) - y;
           s = tt;
-          m = mn;
         }
         const float f = s - comp;
+        const float2 sa2 = f2unpack(SA);
+        const float sa = sa2.x + sa2.y;
         float u;
         uint32_t fl = 0;
         if (f > 0.f) {
@@ -631,13 +705,29 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
           fl |= KSDF_FLAG_FALLBACK;
         }
         const float du = u_error_bound(f, sa, m, u, nres, fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))), lam, dxs);
+        if (qi < tile.z) {
+          s_u[k * kTA + qi] = u;
+          s_du[k * kTA + qi] = du;
+          s_fl[k * kTA + qi] = (uint8_t)fl;
+        }
+      }
+      __syncthreads();
+      k0 = k1;
+    }
+    // min-fusion over the candidates in list order, thread per query
+    if (tid < tile.z) {
+      float bu = INFINITY, su = INFINITY, bdu = 0.f, olo = INFINITY;
+      int bk = -1;
+      uint32_t bflag = 0;
+      for (int k = 0; k < nc; ++k) {
+        const float u = s_u[k * kTA + tid], du = s_du[k * kTA + tid];
         if (u < bu) {
           su = bu;
           olo = fminf(olo, bu - bdu);
           bu = u;
           bdu = du;
           bk = k;
-          bflag = fl;
+          bflag = s_fl[k * kTA + tid];
         } else {
           su = fminf(su, u);
           olo = fminf(olo, u - du);
@@ -648,6 +738,7 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
       // bounds of the two FP32 evaluations
       if (nc >= 2 && (su - bu <= 1e-5f || olo <= bu + bdu)) fl |= KSDF_FLAG_NEAR_TIE;
       if (nc == 0) fl |= KSDF_FLAG_NO_GP;
+      const int q = a.sorted_q[tile.y + tid];
       a.qwin[q] = bk >= 0 ? s_c[bk] : -1;
       a.qu[q] = bu;
       a.qflag[q] = fl;
@@ -1366,6 +1457,37 @@ __global__ void __launch_bounds__(kTcM + 32) k_phaseB_tc(PhaseBArgs a, TcArgs t,
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+// Diagnostic of the bounded waits (ksdf_wait_diagnostic): one CTA shaped like the tensor-core phase B (TMEM
+// allocated by warp 0, an mbarrier initialised by thread 0) waits on an mbarrier that nothing will complete --
+// no bulk copy or MMA is issued, so nothing is in flight -- for at most `spins` polls, then leaves the way a
+// production wait that gives up does: ST_TIMEOUT in the status word, the TMEM released, the kernel returned.
+__global__ void __launch_bounds__(64) k_wait_diag(uint32_t spins, uint32_t* st) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(32u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  bool done = false;
+  for (uint32_t it = 0; it < spins && !done; ++it) done = mbar_try_wait(&bar, 0);
+  if (__syncthreads_or(!done) && tid == 0) atomicOr(st, ST_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32u) : "memory");
+}
+
 // tile counts of the cells in three lists by cell size: (0, n1], (n1, n2] (tiles of T12 queries) and larger
 // (tiles of T3 queries)
 __global__ void k_ntiles3(const int64_t* cnt, const int32_t* cell_n, int64_t n, int n1, int n2, int T12, int T3,
@@ -1689,6 +1811,12 @@ static CandCtx cand_ctx(ksdf_ctx* c) {
   return cc;
 }
 
+ksdf_status wait_diagnostic(ksdf_ctx* c, uint32_t spins) {
+  launch(k_wait_diag, 1, 64, 0, c->stream, spins, ptr<uint32_t>(c->status_word));
+  KSDF_CUDA(c, cudaGetLastError());
+  return KSDF_OK;
+}
+
 ksdf_status candidates_for_keys(ksdf_ctx* c, const uint64_t* keys, int64_t n, int32_t* cand, int32_t* count) {
   if (n <= 0) return KSDF_OK;
   const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, kCandWarps), 8LL * c->num_sms);
@@ -1827,7 +1955,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA64, kTA, smem));
     launch(k_phaseA64, std::max(1, occ) * c->num_sms, kTA, smem, st, pa, static_cast<const double*>(xq), p);
   } else {
-    const size_t smem = sizeof(float4) * (size_t)p.K * ((maxn + 7) & ~7);
+    const size_t smem = phase_a_smem(p.K, p.n_max);
     KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA, kTA, smem));

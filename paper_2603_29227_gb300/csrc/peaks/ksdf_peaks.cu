@@ -48,6 +48,31 @@ __global__ void k_ffma(int iters, float* sink) {
   if (s == 0.f) sink[0] = s;
 }
 
+// packed FP32x2: eight independent fma.rn.f32x2 chains per thread (two FMAs per instruction)
+__global__ void k_ffma2(int iters, float* sink) {
+  unsigned long long x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float lo = 1.f + 1e-3f * threadIdx.x + 0.1f * k, hi = lo + 0.05f;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x[k]) : "f"(lo), "f"(hi));
+  }
+  unsigned long long a, b;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(a) : "f"(0.9999f));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(b) : "f"(1e-6f));
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[k]) : "l"(a), "l"(b));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[k]));
+    s += lo + hi;
+  }
+  if (s == 0.f) sink[0] = s;
+}
+
 // MUFU: eight independent ex2.approx chains per thread, x <- 2^-x (stays in (0.5, 1))
 __device__ __forceinline__ float ex2n(float x) {
   float y;
@@ -189,6 +214,12 @@ int ksdf_peaks_measure(int unit, void* stream, double* rate) {
       constexpr int kThreads = 1024, kIters = 8192;
       rc = time_launch(st, [&] { k_ffma<<<2 * sms, kThreads, 0, st>>>(kIters, (float*)sink); }, &ms);
       if (!rc) *rate = 2.0 * sms * kThreads * (double)kIters * 8 / (ms * 1e-3) / 1e12;  // two CTAs per SM
+      break;
+    }
+    case KSDF_PEAK_FP32X2_FFMA: {
+      constexpr int kThreads = 1024, kIters = 4096;
+      rc = time_launch(st, [&] { k_ffma2<<<2 * sms, kThreads, 0, st>>>(kIters, (float*)sink); }, &ms);
+      if (!rc) *rate = 2.0 * sms * kThreads * (double)kIters * 16 / (ms * 1e-3) / 1e12;  // two CTAs per SM
       break;
     }
     case KSDF_PEAK_MUFU_EX2: {

@@ -31,7 +31,7 @@ ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
                  "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math",
-                 "ksdf_save", "ksdf_load")
+                 "ksdf_save", "ksdf_load", "ksdf_wait_diagnostic")
 
 
 class KsdfError(RuntimeError):
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "ksdf_autotune_tables": [],
         "ksdf_device_math": [P, ctypes.c_int, P, I64, P],
         "ksdf_save": [P, ctypes.c_char_p],
+        "ksdf_wait_diagnostic": [P, U32],
         "ksdf_load": [P, ctypes.c_char_p],
     }
     for name, args in sig.items():
@@ -189,6 +190,12 @@ def ksdf_device_math(h, fn, x):
     y = np.empty_like(x)
     _check(h, load().ksdf_device_math(h, int(fn), _ptr(x), x.size, _ptr(y)), "ksdf_device_math")
     return y
+
+
+def ksdf_wait_diagnostic(h, spins):
+    """Launch the bounded-wait diagnostic (a wait that nothing completes gives up after `spins` polls); the next
+    ksdf_sync_status reports KSDF_ERR_TIMEOUT."""
+    _check(h, load().ksdf_wait_diagnostic(h, int(spins)), "ksdf_wait_diagnostic")
 
 
 def ksdf_save(h, path):

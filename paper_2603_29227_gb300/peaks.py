@@ -8,7 +8,8 @@ import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libksdf_peaks.so")
-UNITS = {"fp64_dfma_tflops": 0, "fp32_ffma_tops": 1, "mufu_ex2_tops": 2, "tf32_tcgen05_tflops": 3}
+UNITS = {"fp64_dfma_tflops": 0, "fp32_ffma_tops": 1, "mufu_ex2_tops": 2, "tf32_tcgen05_tflops": 3,
+         "fp32x2_ffma_tops": 4}
 _lib = None
 
 

@@ -92,10 +92,15 @@ def test_traj3d_full_forward_and_adjoint():
     ratio = cancellation_ratio(ref, w.xq, np.where(fin, gw, -1))
     kept = fin & (np.abs(sdf) > 0.02) & ~zero & (ratio >= MEDIAL_RATIO)
     assert kept.mean() > 0.8, kept.mean()
+    # the gradient output's cotangent also skips queries whose f' <= 0 (u is then the nearest-sample distance
+    # and the GP gradient, whose second derivatives this path takes, no longer describes it; there the oracle's
+    # own d grad adjoint moves by percents under 1e-7 m shifts of the query) and clamped ones
+    kept_g = kept & ((res["flags"] & (ksdf.FLAG_FALLBACK | ksdf.FLAG_CLAMPED)) == 0)
     d_sdf = np.where(kept, -1.0 / (1.0 + np.exp(-(0.15 + 0.1 - sdf))), 0.0).astype(np.float32)
-    d_grad = (0.1 * np.random.default_rng(21).standard_normal((Q, 3)) * kept[:, None]).astype(np.float32)
+    d_grad = (0.1 * np.random.default_rng(21).standard_normal((Q, 3)) * kept_g[:, None]).astype(np.float32)
     for with_grad in (False, True):
         dg = d_grad if with_grad else None
+        kept_w = kept_g if with_grad else kept
         d_xq, d_x = m.backward(_t(w.xq), _t(gw), _t(d_sdf), None if dg is None else _t(dg), _t(w.sign))
         torch.cuda.synchronize()
         m.sync_status()
@@ -105,13 +110,13 @@ def test_traj3d_full_forward_and_adjoint():
         rq, rx = ref.backward(w.xq, d_sdf.astype(np.float64), None if dg is None else dg.astype(np.float64),
                               sign=w.sign, winner=gw)
         nq = np.linalg.norm(rq, axis=1)
-        e = np.linalg.norm(gq - rq, axis=1)[kept] / np.maximum(nq[kept], 1e-12)
-        assert e.max() <= ADJ_REL, (with_grad, e.max(), np.nonzero(kept)[0][np.argmax(e)])
+        e = np.linalg.norm(gq - rq, axis=1)[kept_w] / np.maximum(nq[kept_w], 1e-12)
+        assert e.max() <= ADJ_REL, (with_grad, e.max(), np.nonzero(kept_w)[0][np.argmax(e)])
         assert np.all(gq[~kept] == 0.0)
         ex = np.max(np.abs(gx - rx)) / np.max(np.abs(rx))
         assert ex <= ADJ_REL, (with_grad, ex)
         print("traj3d adjoint (d grad %s): d xq max rel %.3g over %d kept queries, d x %.3g" % (
-            with_grad, e.max(), kept.sum(), ex))
+            with_grad, e.max(), kept_w.sum(), ex))
 
 
 def test_scale3d_full_mixed():
