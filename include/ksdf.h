@@ -71,7 +71,15 @@ typedef struct {
                            1: when the caller passes no sign array, use a stand-in that is NOT the
                            paper's BHM sign: s = +1 iff n_nn . (x - x_nn) >= 0 for the winner GP's
                            nearest training sample x_nn and its normal n_nn (needs normals at fit) */
+  int kernel;           /* KSDF_KERNEL_RBF (0) or KSDF_KERNEL_MATERN32 (1), the kernel table of Sec. IV-B.2 */
 } ksdf_params;
+
+/* Kernels (kernel table of Sec. IV-B.2), with `lambda` the scale of f = exp(-lambda u):
+ *   KSDF_KERNEL_RBF       k(r) = exp(-lambda r^2) (lambda = 1/(2 l^2)), u = sqrt(-log f'/lambda + d^2);
+ *   KSDF_KERNEL_MATERN32  k(r) = (1 + lambda r) exp(-lambda r) (lambda = sqrt(3)/l, the kernel scale sqrt(3)/lambda
+ *                         of Sec. IV-B.1), u = -log f'/lambda + d;
+ * f' is the posterior mean with the kernel vector scaled by gamma = e^{lambda d^2} or e^{lambda d} (App. D). */
+enum { KSDF_KERNEL_RBF = 0, KSDF_KERNEL_MATERN32 = 1 };
 
 /* out_mask bits for ksdf_query / ksdf_query_f64 (outputs whose bit is clear are not written and may be
  * NULL). */
@@ -141,7 +149,7 @@ ksdf_status ksdf_update(ksdf_ctx* ctx, const double* x_new, const float* var_new
  * fitted or updated from (positions float64, variances and normals float32, host byte order) to the file
  * `path`; ksdf_load reads such a file into a context created with the same parameters and fits it.  The
  * fit is deterministic, so the loaded model equals the saved one bit for bit.  File layout: the 8 bytes
- * "KSDFMAP1", int32 version 1, int32 dim, int32 has_normals, int32 0, the 11 parameters (dim, n_max,
+ * "KSDFMAP1", int32 version 1, int32 dim, int32 has_normals, int32 kernel, the 11 parameters (dim, n_max,
  * k_cand, sign_mode as int32; origin[3], cell, margin, lambda, softmin_alpha as float64), int64 S, then
  * x (S x dim), var (S), normals (S x dim, when present).  Synchronises the stream.  Errors:
  * KSDF_ERR_NOT_FITTED (save without a model), KSDF_ERR_ARG (NULL path, a file that cannot be written or
@@ -251,7 +259,8 @@ ksdf_status ksdf_profile_read(ksdf_ctx* ctx, int max_stages, char* names, double
  * What it computes: the same FP64 fit as ksdf_fit performs for one cell, within 1e-9 relative (ksdf_fit
  * evaluates kernel entries below 2.4e-16 in FP32 and uses its own exponential, so the two are not bit for bit
  * equal) -- A = K + diag(sigma^2) with K_ij = exp(-lambda |x_i - x_j|^2), A = L L^T, alpha = A^{-1} 1 (all
- * labels 1), and L^{-1} -- with params->dim and params->lambda (the other fields are not used).
+ * labels 1), and L^{-1} -- with params->dim and params->lambda; params->kernel must be KSDF_KERNEL_RBF (else
+ * KSDF_ERR_ARG); the other fields are not used.
  *   x       device, N x dim float64 positions (read)
  *   var     device, N float32 sigma_i^2 >= 0 (read; NULL means 0)
  *   alpha   device, N float64 (written; zeros if A is not positive definite)

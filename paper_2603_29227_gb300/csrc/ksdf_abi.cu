@@ -186,6 +186,7 @@ ksdf_status check_params(const ksdf_params* a) {
   for (int j = 0; j < 3; ++j)
     if (!(a->origin[j] == a->origin[j]) || a->origin[j] > 1e300 || a->origin[j] < -1e300) return KSDF_ERR_ARG;
   if (a->sign_mode != 0 && a->sign_mode != 1) return KSDF_ERR_ARG;
+  if (a->kernel != KSDF_KERNEL_RBF && a->kernel != KSDF_KERNEL_MATERN32) return KSDF_ERR_ARG;
   return KSDF_OK;
 }
 
@@ -211,6 +212,7 @@ ksdf_status ksdf_create(const ksdf_params* params, void* stream, ksdf_ctx** out)
   c->p.lambda = params->lambda;
   c->p.alpha_s = params->softmin_alpha > 0 ? params->softmin_alpha : params->lambda;
   c->p.sign_mode = params->sign_mode;
+  c->p.kernel = params->kernel;
   c->stream = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -365,7 +367,7 @@ ksdf_status ksdf_save(ksdf_ctx* c, const char* path) {
   KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
   FILE* f = std::fopen(path, "wb");
   if (!f) return set_err(c, KSDF_ERR_ARG, "ksdf_save: cannot open %s for writing", path);
-  const int32_t head[4] = {1, dim, m.has_normals ? 1 : 0, 0};
+  const int32_t head[4] = {1, dim, m.has_normals ? 1 : 0, c->abi.kernel};
   const MapParams mp = map_params(c->abi);
   bool ok = std::fwrite(kMapMagic, 1, 8, f) == 8 && std::fwrite(head, sizeof(head), 1, f) == 1 &&
             std::fwrite(&mp, sizeof(mp), 1, f) == 1 && std::fwrite(&S, sizeof(S), 1, f) == 1 &&
@@ -389,8 +391,8 @@ ksdf_status ksdf_load(ksdf_ctx* c, const char* path) {
             std::fread(head, sizeof(head), 1, f) == 1 && head[0] == 1 && std::fread(&mp, sizeof(mp), 1, f) == 1 &&
             std::fread(&S, sizeof(S), 1, f) == 1;
   const int dim = c->p.dim;
-  ok = ok && head[1] == dim && (head[2] == 0 || head[2] == 1) && S > 0 && S < (1LL << 31) &&
-       same_params(mp, map_params(c->abi));
+  ok = ok && head[1] == dim && (head[2] == 0 || head[2] == 1) && head[3] == c->abi.kernel && S > 0 &&
+       S < (1LL << 31) && same_params(mp, map_params(c->abi));
   std::vector<double> hx;
   std::vector<float> hv, hn;
   if (ok) {

@@ -30,6 +30,11 @@ __device__ inline float ex2(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 __global__ void k_bw_count(const int32_t* winner, int64_t Q, int64_t G, int32_t* rank, int64_t* cnt, float* d_xq,
                            int dim, uint32_t* st) {
@@ -104,8 +109,14 @@ struct BwArgs {
 //    alpha_bar_i += k'_i c,   X_bar_i += alpha_i k'_i (2 lambda c r_i - v),   c = fb + r_i . v,
 //  accumulated in registers, then added once per sample to the global accumulators.
 // A query whose f' <= 0 (the distance fallback) has fb = 0 and its term on the nearest sample added directly.
+// With the Matern 3/2 kernel (u = -log f'/lambda + d, k'_i = (1 + lambda r_i) w_i, w_i = e^{-lambda (r_i - d)},
+// grad k'_i = -lambda^2 w_i r_i): fb = -s d_sdf / (lambda f'), G = sum_i alpha_i w_i r_i, the gradient output's
+// Jacobian sum_i alpha_i w_i (I - (lambda / |r_i|) r_i r_i^T), so that
+//   x_bar = -lambda^2 fb G + f_w v - lambda H' v  (f_w = sum alpha_i w_i, H' = sum (alpha_i w_i / |r_i|) r_i r_i^T),
+//   alpha_bar_i += fb k'_i + w_i (r_i . v),  X_bar_i += alpha_i w_i ((lambda^2 fb + lambda (r_i . v) / |r_i|) r_i - v).
 constexpr int kTQ = 128;  // backward tile: queries (pass 1) and threads
 
+template <bool MATERN>
 __global__ void __launch_bounds__(kTQ) k_bw_query(BwArgs a, const float* xq, Params p) {
   extern __shared__ __align__(16) float4 s_x[];  // [n_max] samples | per query: (x, fb) (w, -) (x_n, -) (v, -) |
                                                  // [kTQ][4] group partial sums
@@ -156,21 +167,44 @@ __global__ void __launch_bounds__(kTQ) k_bw_query(BwArgs a, const float* xq, Par
       const float4 xn = s_x[nn];
       const float px = ql[0] - xn.x, py = ql[1] - xn.y, pz = ql[2] - xn.z;
       const float wx = 2.f * px, wy = 2.f * py, wz = 2.f * pz;
-      float f = 0.f, comp = 0.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
+      const float zmin = sqrtf(m);
+      // f' (compensated); the gradient weights' sums fw, D (G = fw p + D); the Jacobian weights' sums fc, Dc, M
+      // (RBF: the same weights; Matern: alpha_i w_i / |r_i|)
+      float f = 0.f, comp = 0.f, fw = 0.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
+      float fc = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
       float M00 = 0.f, M01 = 0.f, M02 = 0.f, M11 = 0.f, M12 = 0.f, M22 = 0.f;
       for (int i = 0; i < n; ++i) {
         const float4 v = s_x[i];
         const float ax = v.x - xn.x, ay = v.y - xn.y, az = v.z - xn.z;  // -delta_i
         const float e = fmaf(ax, ax - wx, fmaf(ay, ay - wy, az * (az - wz)));
-        const float ak = v.w * ex2(-c1 * e);
+        float ak, aw, ac;
+        if (MATERN) {
+          const float r2 = m + e, z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+          const float den = z + zmin;
+          const float y = den > 0.f ? fmaxf(e, 0.f) * __frcp_rn(den) : 0.f;
+          aw = v.w * ex2(-c1 * y);
+          ak = aw * fmaf(lam, z, 1.f);
+          ac = z > 0.f ? aw * __frcp_rn(z) : 0.f;
+        } else {
+          ak = v.w * ex2(-c1 * e);
+          aw = ak;
+          ac = ak;
+        }
         const float y = ak - comp;
         const float tt = f + y;
         comp = (tt - f) - y;
         f = tt;
-        const float bx = ak * ax, by = ak * ay, bz = ak * az;
-        D0 -= bx;
-        D1 -= by;
-        D2 -= bz;
+        fw += aw;
+        D0 -= aw * ax;
+        D1 -= aw * ay;
+        D2 -= aw * az;
+        const float bx = ac * ax, by = ac * ay, bz = ac * az;
+        if (MATERN) {
+          fc += ac;
+          C0 -= bx;
+          C1 -= by;
+          C2 -= bz;
+        }
         M00 = fmaf(bx, ax, M00);
         M01 = fmaf(bx, ay, M01);
         M02 = fmaf(bx, az, M02);
@@ -179,7 +213,14 @@ __global__ void __launch_bounds__(kTQ) k_bw_query(BwArgs a, const float* xq, Par
         M22 = fmaf(bz, az, M22);
       }
       f -= comp;
-      const float G0 = fmaf(f, px, D0), G1 = fmaf(f, py, D1), G2 = fmaf(f, pz, D2);
+      if (!MATERN) {
+        fw = f;  // the compensated sum
+        fc = f;
+        C0 = D0;
+        C1 = D1;
+        C2 = D2;
+      }
+      const float G0 = fmaf(fw, px, D0), G1 = fmaf(fw, py, D1), G2 = fmaf(fw, pz, D2);
       float s = 1.f;
       if (a.sign) {
         s = a.sign[q] < 0 ? -1.f : 1.f;
@@ -191,8 +232,12 @@ __global__ void __launch_bounds__(kTQ) k_bw_query(BwArgs a, const float* xq, Par
       float fb = 0.f;
       const bool fallback = !(f > 0.f);
       if (!fallback) {
-        const float u2 = fmaf(-logf(f), 1.f / lam, m);
-        fb = u2 > 0.f ? -ub / (2.f * lam * sqrtf(u2) * f) : 0.f;
+        if (MATERN) {
+          fb = fmaf(-logf(f), 1.f / lam, zmin) > 0.f ? -ub / (lam * f) : 0.f;
+        } else {
+          const float u2 = fmaf(-logf(f), 1.f / lam, m);
+          fb = u2 > 0.f ? -ub / (2.f * lam * sqrtf(u2) * f) : 0.f;
+        }
       }
       float v0 = 0.f, v1 = 0.f, v2 = 0.f;
       if (a.d_grad) {
@@ -208,15 +253,17 @@ __global__ void __launch_bounds__(kTQ) k_bw_query(BwArgs a, const float* xq, Par
           v2 = sc * (b2 - g2 * dot);
         }
       }
-      // x_bar = -2 lambda (fb G + H v) + f' v,  H v = f' (p.v) p + (p.v) D + p (D.v) + M v
-      const float pv = fmaf(px, v0, fmaf(py, v1, pz * v2)), dv = fmaf(D0, v0, fmaf(D1, v1, D2 * v2));
-      const float fpv = f * pv;
-      const float hv0 = fmaf(fpv, px, fmaf(pv, D0, fmaf(px, dv, fmaf(M00, v0, fmaf(M01, v1, M02 * v2)))));
-      const float hv1 = fmaf(fpv, py, fmaf(pv, D1, fmaf(py, dv, fmaf(M01, v0, fmaf(M11, v1, M12 * v2)))));
-      const float hv2 = fmaf(fpv, pz, fmaf(pv, D2, fmaf(pz, dv, fmaf(M02, v0, fmaf(M12, v1, M22 * v2)))));
-      float xb0 = fmaf(-tl, fmaf(fb, G0, hv0), f * v0);
-      float xb1 = fmaf(-tl, fmaf(fb, G1, hv1), f * v1);
-      float xb2 = fmaf(-tl, fmaf(fb, G2, hv2), f * v2);
+      // x_bar = -cg fb G + fw v - beta H v with H v = fc (p.v) p + (p.v) C + p (C.v) + M v; RBF cg = beta = 2 lambda,
+      // Matern cg = lambda^2, beta = lambda (the 1/|r_i| is inside the weights of fc, C, M)
+      const float pv = fmaf(px, v0, fmaf(py, v1, pz * v2)), cv = fmaf(C0, v0, fmaf(C1, v1, C2 * v2));
+      const float fpv = fc * pv;
+      const float hv0 = fmaf(fpv, px, fmaf(pv, C0, fmaf(px, cv, fmaf(M00, v0, fmaf(M01, v1, M02 * v2)))));
+      const float hv1 = fmaf(fpv, py, fmaf(pv, C1, fmaf(py, cv, fmaf(M01, v0, fmaf(M11, v1, M12 * v2)))));
+      const float hv2 = fmaf(fpv, pz, fmaf(pv, C2, fmaf(pz, cv, fmaf(M02, v0, fmaf(M12, v1, M22 * v2)))));
+      const float cg = MATERN ? lam * lam : tl, beta = MATERN ? lam : tl;
+      float xb0 = fmaf(-cg * fb, G0, fmaf(-beta, hv0, fw * v0));
+      float xb1 = fmaf(-cg * fb, G1, fmaf(-beta, hv1, fw * v1));
+      float xb2 = fmaf(-cg * fb, G2, fmaf(-beta, hv2, fw * v2));
       if (fallback && m > 0.f) {
         // u = distance to the nearest sample: its own derivative, on the query and on that sample
         const float d = sqrtf(m);
@@ -234,7 +281,7 @@ __global__ void __launch_bounds__(kTQ) k_bw_query(BwArgs a, const float* xq, Par
       if (p.dim == 3) a.d_xq[(int64_t)q * p.dim + 2] = xb2;
       QA[tid] = make_float4(ql[0], ql[1], ql[2], fb);
       QW[tid] = make_float4(wx, wy, wz, 0.f);
-      QN[tid] = make_float4(xn.x, xn.y, xn.z, 0.f);
+      QN[tid] = make_float4(xn.x, xn.y, xn.z, m);
       QV[tid] = make_float4(v0, v1, v2, 0.f);
     }
     __syncthreads();
@@ -251,13 +298,27 @@ __global__ void __launch_bounds__(kTQ) k_bw_query(BwArgs a, const float* xq, Par
         for (int qq = grp; qq < nq; qq += nrep) {
           const float4 A = QA[qq], W = QW[qq], Nn = QN[qq], V = QV[qq];
           const float r0 = A.x - xi.x, r1 = A.y - xi.y, r2 = A.z - xi.z;
-          const float kp = ex2(-c1 * excess_sq(xi.x, xi.y, xi.z, Nn.x, Nn.y, Nn.z, W.x, W.y, W.z));
-          const float c = fmaf(r0, V.x, fmaf(r1, V.y, fmaf(r2, V.z, A.w)));
-          ab = fmaf(kp, c, ab);
-          const float ak = xi.w * kp, t2 = tl * c;
-          X0 = fmaf(ak, fmaf(t2, r0, -V.x), X0);
-          X1 = fmaf(ak, fmaf(t2, r1, -V.y), X1);
-          X2 = fmaf(ak, fmaf(t2, r2, -V.z), X2);
+          const float e = excess_sq(xi.x, xi.y, xi.z, Nn.x, Nn.y, Nn.z, W.x, W.y, W.z);
+          const float rv = fmaf(r0, V.x, fmaf(r1, V.y, r2 * V.z));
+          float t2, aw;
+          if (MATERN) {
+            const float rr = Nn.w + e, z = rr > 0.f ? rr * rsqrtf(rr) : 0.f, zm = sqrtf(Nn.w);
+            const float den = z + zm;
+            const float y = den > 0.f ? fmaxf(e, 0.f) * __frcp_rn(den) : 0.f;
+            const float wg = ex2(-c1 * y);
+            ab = fmaf(A.w * fmaf(lam, z, 1.f), wg, fmaf(wg, rv, ab));
+            aw = xi.w * wg;
+            t2 = fmaf(lam * lam, A.w, z > 0.f ? lam * rv * __frcp_rn(z) : 0.f);
+          } else {
+            const float kp = ex2(-c1 * e);
+            const float c = rv + A.w;
+            ab = fmaf(kp, c, ab);
+            aw = xi.w * kp;
+            t2 = tl * c;
+          }
+          X0 = fmaf(aw, fmaf(t2, r0, -V.x), X0);
+          X1 = fmaf(aw, fmaf(t2, r1, -V.y), X1);
+          X2 = fmaf(aw, fmaf(t2, r2, -V.z), X2);
         }
       }
       if (nrep > 1) {  // combine the query groups of each sample
@@ -322,6 +383,7 @@ __device__ void linv_solve32(const float* Lb, int n, const float* rhs, float* y,
 
 constexpr int kBwCellThreads = 64;  // two warps per cell: ~70-row cells keep most lanes busy, 32 cells per SM
 
+template <bool MATERN>
 __global__ void __launch_bounds__(kBwCellThreads) k_bw_cell(const int64_t* qcnt, int64_t G, const int64_t* ts_off,
                                                  const int32_t* cell_n, const int64_t* chol_off, const double* chol64,
                                                  const int64_t* linv_off, const float* linv32, const float4* mf4,
@@ -384,7 +446,7 @@ __global__ void __launch_bounds__(kBwCellThreads) k_bw_cell(const int64_t* qcnt,
     __syncthreads();
     linv_solve32(Lb, n, srhs, sy, sb, true);  // b = b0 + L^{-T} L^{-1} r
     const float c1 = (float)p.lambda * kLog2e;
-    const float tl = 2.f * (float)p.lambda;
+    const float tl = 2.f * (float)p.lambda, cm = (float)(p.lambda * p.lambda);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const float4 xi = mf4[m0 + i];
       const float bi = sb[i], ai = xi.w;
@@ -393,8 +455,10 @@ __global__ void __launch_bounds__(kBwCellThreads) k_bw_cell(const int64_t* qcnt,
         if (j == i) continue;
         const float4 xj = mf4[m0 + j];
         const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-        const float kij = ex2(-c1 * fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        const float cf = tl * kij * fmaf(bi, xj.w, sb[j] * ai);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        // grad_{x_i} A_ij = -cg w_ij (x_i - x_j): RBF cg w = 2 lambda K_ij, Matern lambda^2 e^{-lambda r_ij}
+        const float cw = MATERN ? cm * ex2(-c1 * sqrt_approx(r2)) : tl * ex2(-c1 * r2);
+        const float cf = cw * fmaf(bi, xj.w, sb[j] * ai);
         X0 = fmaf(cf, dx, X0);
         X1 = fmaf(cf, dy, X1);
         X2 = fmaf(cf, dz, X2);
@@ -460,19 +524,22 @@ ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* 
   a.d_x = d_x;
   a.abar = abar;
   const size_t smem = sizeof(float4) * (p.n_max + 5 * kTQ);
-  KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const bool matern = p.kernel == KSDF_KERNEL_MATERN32;
+  auto kq = matern ? k_bw_query<true> : k_bw_query<false>;
+  KSDF_CUDA(c, cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bw_query, kTQ, smem));
+  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kq, kTQ, smem));
   e0 = prof_begin(c);
-  launch(k_bw_query, std::max(1, occ) * c->num_sms, kTQ, smem, st, a, xq, p);
+  launch(kq, std::max(1, occ) * c->num_sms, kTQ, smem, st, a, xq, p);
   prof_end(c, e0, "backward.query");
   e0 = prof_begin(c);
   const size_t smem2 = sizeof(double) * 3 * p.n_max + sizeof(float) * 3 * p.n_max;
-  KSDF_CUDA(c, cudaFuncSetAttribute(k_bw_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+  auto kc = matern ? k_bw_cell<true> : k_bw_cell<false>;
+  KSDF_CUDA(c, cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
   int occ2 = 0;
-  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_bw_cell, kBwCellThreads, smem2));
+  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kc, kBwCellThreads, smem2));
   const unsigned grid2 = (unsigned)std::min<int64_t>(G, (int64_t)std::max(1, occ2) * c->num_sms);
-  launch(k_bw_cell, std::max(1u, grid2), kBwCellThreads, smem2, st, cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
+  launch(kc, std::max(1u, grid2), kBwCellThreads, smem2, st, cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
          ptr<int64_t>(m.chol_off), ptr<double>(m.chol64), ptr<int64_t>(m.linv_off), ptr<float>(m.linv32),
          ptr<float4>(m.mf4), ptr<int32_t>(m.mgid), abar, p, d_x);
   KSDF_CUDA(c, cudaGetLastError());

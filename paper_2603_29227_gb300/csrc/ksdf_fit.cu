@@ -371,11 +371,20 @@ __device__ __forceinline__ int tri_row(int64_t t) {
 }
 
 constexpr int kB = 8;        // Cholesky panel width
-constexpr float kNearE = 36.f;  // lambda r^2 below this: FP64 entry; above: FP32 (value < 2.4e-16)
+constexpr float kNearE = 36.f;  // RBF: lambda r^2 below this: FP64 entry; above: FP32 (value < 2.4e-16)
+constexpr float kNearM = 42.f;  // Matern 3/2: lambda r below this: FP64 entry; above: FP32 (value < 2.5e-17)
 
-// exp(-lambda r_ij^2) from the scaled coordinates: fixed point (exact squared distance) or binary64.  In
-// fixed-point mode the slots hold the same coordinates as 64-bit integers (s 2^40).
+// The kernel entry from the scaled coordinates.  RBF: exp(-lambda r_ij^2), coordinates scaled by
+// sqrt(lambda 2^16 / ln2), in fixed point (exact squared distance; the slots hold the coordinates as 64-bit
+// integers s 2^40) or binary64.  Matern 3/2: (1 + lambda r) exp(-lambda r), coordinates scaled by
+// lambda 2^16 / ln2 so that the scaled distance is exp2_neg_q16's argument (binary64, correctly rounded sqrt).
+template <bool MATERN>
 __device__ __forceinline__ double near_entry(const double* s, const long long* sfix, bool fixed, int i, int j) {
+  if (MATERN) {
+    const double ex = s[3 * i] - s[3 * j], ey = s[3 * i + 1] - s[3 * j + 1], ez = s[3 * i + 2] - s[3 * j + 2];
+    const double e = sqrt(fma(ez, ez, fma(ey, ey, ex * ex)));
+    return fma(e, 1.0 / kExpQ16PerNat, 1.0) * exp2_neg_q16(e);
+  }
   if (fixed)
     return exp2_neg_fixed40(sqdiff40(sfix[3 * i], sfix[3 * j]) + sqdiff40(sfix[3 * i + 1], sfix[3 * j + 1]) +
                             sqdiff40(sfix[3 * i + 2], sfix[3 * j + 2]));
@@ -410,6 +419,7 @@ __host__ __device__ inline int64_t kmat_warp_doubles(int np) { return 5 * (int64
 // exp2_neg_fixed40's argument: 4 FP64 operations per entry instead of 10 (the rounding of s to 2^-41 moves
 // an entry by below 1e-13 of its value).  A separate, high-occupancy kernel: the factorisation's warps then
 // spend their time in the FP64 factorisation alone.
+template <bool MATERN>
 __global__ void __launch_bounds__(32 * kKmatWarps) k_kmat(KmatArgs a) {
   extern __shared__ __align__(16) double smk[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -457,9 +467,15 @@ __global__ void __launch_bounds__(32 * kKmatWarps) k_kmat(KmatArgs a) {
         const float4 pi = reinterpret_cast<const float4*>(xf)[i];
         const float4 pj = reinterpret_cast<const float4*>(xf)[j];
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        const float ef = a.lamf * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        if (ef < kNearE) near = true;
-        else Ag[tri_sz(i) + j] = f2d_bits(exp2f(-1.44269504f * ef));
+        if (MATERN) {
+          const float ef = a.lamf * sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+          if (ef < kNearM) near = true;
+          else Ag[tri_sz(i) + j] = f2d_bits((1.f + ef) * exp2f(-1.44269504f * ef));
+        } else {
+          const float ef = a.lamf * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          if (ef < kNearE) near = true;
+          else Ag[tri_sz(i) + j] = f2d_bits(exp2f(-1.44269504f * ef));
+        }
       }
       const unsigned mask = __ballot_sync(0xffffffffu, near);
       if (near) qw[qn + __popc(mask & lt_mask)] = (i << 16) | j;
@@ -467,7 +483,7 @@ __global__ void __launch_bounds__(32 * kKmatWarps) k_kmat(KmatArgs a) {
       if (qn >= 32) {
         __syncwarp();
         const int ij = qw[lane];
-        Ag[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
+        Ag[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry<MATERN>(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
         __syncwarp();
         if (lane < qn - 32) qw[lane] = qw[32 + lane];
         qn -= 32;
@@ -482,7 +498,7 @@ __global__ void __launch_bounds__(32 * kKmatWarps) k_kmat(KmatArgs a) {
     __syncwarp();
     if (lane < qn) {
       const int ij = qw[lane];
-      Ag[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
+      Ag[tri_sz(ij >> 16) + (ij & 0xffff)] = near_entry<MATERN>(s, sfix, a.fixed, ij >> 16, ij & 0xffff);
     }
     __syncwarp();
   }
@@ -1304,16 +1320,18 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     ka.mvar = ptr<float>(m.mvar);
     ka.chol64 = ptr<double>(m.chol64);
     ka.np = std::max(m.max_n, 1);
-    ka.sc = std::sqrt(p.lambda * kExpQ16PerNat);
+    const bool matern = p.kernel == KSDF_KERNEL_MATERN32;
+    ka.sc = matern ? p.lambda * kExpQ16PerNat : std::sqrt(p.lambda * kExpQ16PerNat);
     ka.lamf = (float)p.lambda;
     // members lie within the margin of their cell: |local coordinate| <= h + mu
-    ka.fixed = ka.sc * (p.h + p.mu) < 0x1p21;
+    ka.fixed = !matern && ka.sc * (p.h + p.mu) < 0x1p21;
     const size_t ksm = sizeof(double) * (size_t)kmat_warp_doubles(ka.np) * kKmatWarps;
-    KSDF_CUDA(c, cudaFuncSetAttribute(k_kmat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksm));
+    auto kern = matern ? k_kmat<true> : k_kmat<false>;
+    KSDF_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksm));
     int occ = 0;
-    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_kmat, 32 * kKmatWarps, ksm));
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * kKmatWarps, ksm));
     const int64_t nblk = std::min<int64_t>(ceil_div(nfit, kKmatWarps), (int64_t)std::max(1, occ) * c->num_sms);
-    launch(k_kmat, (unsigned)nblk, 32 * kKmatWarps, ksm, st, ka);
+    launch(kern, (unsigned)nblk, 32 * kKmatWarps, ksm, st, ka);
   }
   prof_end(c, e0, "fit.kmat");
   e0 = prof_begin(c);

@@ -115,6 +115,7 @@ struct Params {
   double lambda;
   double alpha_s;  // softmin temperature
   int sign_mode;
+  int kernel;      // KSDF_KERNEL_RBF or KSDF_KERNEL_MATERN32
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -241,8 +242,10 @@ cudaError_t fork_streams(ksdf_ctx* c);
 cudaError_t join_streams(ksdf_ctx* c);
 
 // ---- sorting and scanning (ksdf_sort.cu) ----
-// exclusive scan of n int64 values (in may equal out); total (optional) gets the sum on the device.
-cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, DevBuf& tmp, cudaStream_t st);
+// exclusive scan of n int64 values (in may equal out); total (optional) gets the sum on the device.  With
+// n_dev (optional, a device count) only the first min(n, *n_dev) elements are scanned.
+cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, DevBuf& tmp, cudaStream_t st,
+                     const int64_t* n_dev = nullptr);
 // stable LSD radix sort by the low `bits` bits of 64-bit keys, with 32-bit values.  Result in keys/vals.
 cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, DevBuf& tmp, cudaStream_t st);
 

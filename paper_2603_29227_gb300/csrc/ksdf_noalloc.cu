@@ -147,7 +147,8 @@ extern "C" ksdf_status ksdf_fit_gp_noalloc(const ksdf_params* params, const doub
                                            double* alpha, double* linv, int32_t* status, void* stream) {
   using namespace ksdf;
   if (!params || !x || !alpha || !linv || !status) return KSDF_ERR_ARG;
-  if ((params->dim != 2 && params->dim != 3) || !(params->lambda > 0) || !(params->lambda < 1e12))
+  if ((params->dim != 2 && params->dim != 3) || !(params->lambda > 0) || !(params->lambda < 1e12) ||
+      params->kernel != KSDF_KERNEL_RBF)
     return KSDF_ERR_ARG;
   if (N < 1 || N > kNoAllocMaxN) return KSDF_ERR_CAPACITY;
   int dev = 0;

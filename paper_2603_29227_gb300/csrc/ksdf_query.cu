@@ -107,9 +107,14 @@ __global__ void k_slot_flags(const uint64_t* bhk, uint64_t bcap, int64_t* flag) 
   if (s < (int64_t)bcap) flag[s] = bhk[s] != kEmptyKey ? 1 : 0;
 }
 
-__global__ void k_bin_table(const uint64_t* bhk, uint64_t bcap, const int64_t* slot_id, uint64_t* bin_key) {
+// the occupied slots numbered in slot order: bin b's key, and its query count cleared
+__global__ void k_bin_table(const uint64_t* bhk, uint64_t bcap, const int64_t* slot_id, uint64_t* bin_key,
+                            int64_t* bin_cnt) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < (int64_t)bcap && bhk[s] != kEmptyKey) bin_key[slot_id[s]] = bhk[s];
+  if (s < (int64_t)bcap && bhk[s] != kEmptyKey) {
+    bin_key[slot_id[s]] = bhk[s];
+    bin_cnt[slot_id[s]] = 0;
+  }
 }
 
 __global__ void k_q_rank(const uint64_t* qkey, int64_t Q, const uint64_t* bhk, const int64_t* slot_id, uint64_t bcap,
@@ -131,8 +136,9 @@ __global__ void k_q_rank(const uint64_t* qkey, int64_t Q, const uint64_t* bhk, c
   qrank[q] = (int32_t)atomicAdd((unsigned long long*)&bin_cnt[b], 1ull);
 }
 
-__global__ void k_ntiles(const int64_t* cnt, int64_t n, int T, int64_t* ntiles) {
+__global__ void k_ntiles(const int64_t* cnt, int64_t n, int T, int64_t* ntiles, const int64_t* n_dev) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n_dev && *n_dev < n) n = *n_dev;
   if (i < n) ntiles[i] = (cnt[i] + T - 1) / T;
 }
 
@@ -146,8 +152,9 @@ __global__ void k_scatter_grouped(const int32_t* grp, const int32_t* rank, int64
 
 // tiles: for group i with cnt items starting at off[i]: tiles at tile_off[i] ...
 __global__ void k_make_tiles(const int64_t* cnt, const int64_t* off, const int64_t* tile_off, int64_t ngroups, int T,
-                             int4* tiles) {
+                             int4* tiles, const int64_t* n_dev) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n_dev && *n_dev < ngroups) ngroups = *n_dev;
   if (i >= ngroups) return;
   int64_t c = cnt[i];
   for (int64_t t = 0; t * T < c; ++t)
@@ -490,6 +497,25 @@ struct PhaseAArgs {
   uint32_t* st;
 };
 
+// The same bound for the Matern 3/2 kernel, where u = -log f' / lambda + d is linear in log f' and d (m is d):
+// each term's exponent lambda (r_i - d) carries the errors of r_i = sqrt.approx(r_i^2) (2^-22 relative) and of
+// the positions (dxs, 2^-23 qa); the factor (1 + lambda r_i) carries a smaller relative error.
+__device__ __forceinline__ float u_error_bound_matern(float f, float sa, float d, int nres, float qa, float lam,
+                                                      float dxs) {
+  const float R = d + 40.f / lam;
+  const float dr = 0x1p-22f * R + 1.7320508f * (dxs + qa * 0x1p-23f);
+  const float eps = lam * 2.f * dr + 1e-6f + (float)nres * 0x1p-22f;
+  const float df = sa * (eps + 0x1p-21f);
+  if (!(f > 2.f * df)) return INFINITY;
+  return 2.f * (df / (f * lam) + 0x1p-22f * (fabsf(__logf(f)) / lam + d) + dr);
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // packed FP32x2 arithmetic (two lanes of one thread per instruction): a u64 holds (lo, hi) floats
 __device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
   unsigned long long r;
@@ -539,8 +565,11 @@ __host__ __device__ inline size_t phase_a_smem(int K, int n_max) {
 //   r_i^2 = |q - x_i|^2, the running minimum m = d^2 (App. D), rescaled sums
 //   f' = sum_i alpha_i 2^{c1 (m - r_i^2)} (Kahan-compensated across steps) and sum_i |alpha_i| 2^{c1 (m - r_i^2)},
 //   u = sqrt(-log f' / lambda + m) (kernel table) with its error bound (u_error_bound).
+// With the Matern 3/2 kernel the running minimum is over r_i = sqrt(r_i^2) (d itself), the terms are
+// alpha_i (1 + lambda r_i) 2^{c1 (d - r_i)} and u = -log f' / lambda + d.
 // Finally a thread per query takes the minimum over the candidates in list order (min-fusion, Sec. IV-B.1), the
 // first on equal u, and sets the near-tie flag from the error bounds.
+template <bool MATERN>
 __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, Params p) {
   extern __shared__ __align__(16) float sA[];
   __shared__ int s_tile, s_nc, s_task, s_k1, s_c[kMaxK], s_n[kMaxK], s_ch[kMaxK];
@@ -635,6 +664,7 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
         const float qx = s_ql[qs][0] + s_off[k][0], qy = s_ql[qs][1] + s_off[k][1], qz = s_ql[qs][2] + s_off[k][2];
         const unsigned long long QX = f2pack(qx, qx), QY = f2pack(qy, qy), QZ = f2pack(qz, qz);
         const unsigned long long NC1 = f2pack(-c1, -c1);
+        const unsigned long long LAM2 = f2pack(lam, lam), ONE2 = f2pack(1.f, 1.f);
         const float* ch = sA + (size_t)kChunkF * s_ch[k];
         const int nch = (s_n[k] + 7) >> 3;
         float m = INFINITY, s = 0.f, comp = 0.f;
@@ -659,6 +689,14 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
             rv[2 * h] = u.x;
             rv[2 * h + 1] = u.y;
           }
+          if (MATERN) {  // distances, and the exponents below act on them
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              rv[2 * h] = sqrt_approx(rv[2 * h]);
+              rv[2 * h + 1] = sqrt_approx(rv[2 * h + 1]);
+              r2[h] = f2pack(rv[2 * h], rv[2 * h + 1]);
+            }
+          }
           const float cm = fminf(fminf(fminf(rv[0], rv[1]), fminf(rv[2], rv[3])),
                                  fminf(fminf(rv[4], rv[5]), fminf(rv[6], rv[7])));
           const float mn = fminf(m, cm);
@@ -673,7 +711,8 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
             const float2 ev = f2unpack(f2fma(NC1, r2[h], CMN));
-            const unsigned long long kk = f2pack(ex2(ev.x), ex2(ev.y));
+            unsigned long long kk = f2pack(ex2(ev.x), ex2(ev.y));
+            if (MATERN) kk = f2mul(kk, f2fma(LAM2, r2[h], ONE2));  // (1 + lambda r) 2^{c1 (d - r)}
             const float4 al4 = c4[6 + (h >> 1)], ab4 = c4[8 + (h >> 1)];
             const unsigned long long AL = (h & 1) ? f2pack(al4.z, al4.w) : f2pack(al4.x, al4.y);
             const unsigned long long AB = (h & 1) ? f2pack(ab4.z, ab4.w) : f2pack(ab4.x, ab4.y);
@@ -694,17 +733,23 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
         float u;
         uint32_t fl = 0;
         if (f > 0.f) {
-          float u2 = fmaf(-logf(f), inv_lam, m);
-          if (u2 < 0.f) {
-            u2 = 0.f;
+          if (MATERN) {
+            u = fmaf(-logf(f), inv_lam, m);
+          } else {
+            u = fmaf(-logf(f), inv_lam, m);
+            u = u < 0.f ? u : sqrtf(u);
+          }
+          if (u < 0.f) {
+            u = 0.f;
             fl |= KSDF_FLAG_CLAMPED;
           }
-          u = sqrtf(u2);
         } else {
-          u = sqrtf(m);
+          u = MATERN ? m : sqrtf(m);
           fl |= KSDF_FLAG_FALLBACK;
         }
-        const float du = u_error_bound(f, sa, m, u, nres, fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))), lam, dxs);
+        const float qa = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+        const float du = MATERN ? u_error_bound_matern(f, sa, m, nres, qa, lam, dxs)
+                                : u_error_bound(f, sa, m, u, nres, qa, lam, dxs);
         if (qi < tile.z) {
           s_u[k * kTA + qi] = u;
           s_du[k * kTA + qi] = du;
@@ -750,6 +795,7 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
 // ---------------------------------------------------------------------------------------------
 // Q4 (plain path): phase A in binary64, two passes per candidate
 
+template <bool MATERN>
 __global__ void __launch_bounds__(kTA) k_phaseA64(PhaseAArgs a, const double* xq, Params p) {
   extern __shared__ __align__(128) D4 s_d[];
   __shared__ __align__(8) uint64_t bar;
@@ -816,22 +862,30 @@ __global__ void __launch_bounds__(kTA) k_phaseA64(PhaseAArgs a, const double* xq
           m = fmin(m, dx * dx + dy * dy + dz * dz);
         }
         double f = 0.0;
+        const double dm = sqrt(m);
         for (int i = 0; i < n; ++i) {
           const D4 v = xs[i];
           const double dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-          f += v.w * exp(-p.lambda * ((dx * dx + dy * dy + dz * dz) - m));
+          const double r2 = dx * dx + dy * dy + dz * dz;
+          if (MATERN) {
+            const double r = sqrt(r2);
+            f += v.w * (1.0 + p.lambda * r) * exp(-p.lambda * (r - dm));
+          } else {
+            f += v.w * exp(-p.lambda * (r2 - m));
+          }
         }
         double u;
         uint32_t fl = 0;
         if (f > 0.0) {
-          double u2 = -log(f) / p.lambda + m;
-          if (u2 < 0.0) {
-            u2 = 0.0;
+          u = MATERN ? -log(f) / p.lambda + dm : -log(f) / p.lambda + m;
+          if (u < 0.0) {
+            u = 0.0;
             fl |= KSDF_FLAG_CLAMPED;
+          } else if (!MATERN) {
+            u = sqrt(u);
           }
-          u = sqrt(u2);
         } else {
-          u = sqrt(m);
+          u = dm;
           fl |= KSDF_FLAG_FALLBACK;
         }
         if (u < bu) {
@@ -898,6 +952,25 @@ __global__ void k_w_scatter(const int32_t* qwin, const int32_t* qbin, const int3
 constexpr int kBQ = 32;
 constexpr int kBW = 4;
 
+// The per-sample kernel terms of phase B from e = r_i^2 - d^2 (excess_sq) and z = r_i: the scaled kernel value
+// k' (the A operand of V[f]), the factor wg of its gradient (grad k' = -c wg (x - x_i)) and y = z - d for the
+// softmin weights.  RBF: k' = wg = 2^{-c1 e}, y = z - d.  Matern 3/2: y = e / (z + d) (z - d without the
+// cancellation of two metre-scale numbers), wg = 2^{-c1 y}, k' = (1 + lambda z) wg.
+template <bool MATERN>
+__device__ __forceinline__ void kernel_terms(float e, float z, float zmin, float c1, float lam, float& kp, float& wg,
+                                             float& y) {
+  if (MATERN) {
+    const float den = z + zmin;
+    y = den > 0.f ? fmaxf(e, 0.f) * __frcp_rn(den) : 0.f;
+    wg = ex2(-c1 * y);
+    kp = fmaf(lam, z, 1.f) * wg;
+  } else {
+    kp = ex2(-c1 * e);
+    wg = kp;
+    y = fmaxf(z - zmin, 0.f);
+  }
+}
+
 struct PhaseBArgs {
   const int4* tiles;
   const int64_t* n_tiles;
@@ -961,6 +1034,7 @@ constexpr int kLinvStageN = 128;  // L^{-1} of cells up to this N is staged in s
 
 // One work item = up to 256 queries sharing the winner cell; the cell's samples and (for N <= 128) its
 // L^{-1} are staged once by TMA bulk copies and reused by every chunk of 32 queries.
+template <bool MATERN>
 __global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* xq, Params p, float* sdf, float* grad,
                                                      float* var_sdf, float* var_f, int32_t* winner, uint32_t* flags,
                                                      int smax_n) {
@@ -1057,14 +1131,14 @@ __global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* 
           const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
           const float e = excess_sq(v.x, v.y, v.z, xn.x, xn.y, xn.z, wx, wy, wz);
           const float r2 = m + e;
-          const float kp = ex2(-c1 * e);
+          const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+          float kp, wg, y;
+          kernel_terms<MATERN>(e, z, zmin, c1, (float)p.lambda, kp, wg, y);
           s_k[i * kBQ + lane] = kp;
-          const float ak = v.w * kp;
+          const float ak = v.w * wg;
           G0 = fmaf(ak, dx, G0);
           G1 = fmaf(ak, dy, G1);
           G2 = fmaf(ak, dz, G2);
-          const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-          const float y = fmaxf(z - zmin, 0.f);
           const float wt = ex2(-c2 * y);
           W += wt;
           HY = fmaf(wt, y, HY);
@@ -1103,7 +1177,7 @@ __global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* 
         const float hy = HY / W;
         const float B = fmaf(as, hy, 1.f);
         const float vs = fmaxf((B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W), 0.f);
-        const float vf = fmaxf(1.f - ex2(-2.f * c1 * m) * VS, 0.f);
+        const float vf = fmaxf(1.f - ex2(-2.f * c1 * (MATERN ? sqrtf(m) : m)) * VS, 0.f);
         float s = 1.f;
         if (a.sign) {
           s = a.sign[q] < 0 ? -1.f : 1.f;
@@ -1222,6 +1296,7 @@ __device__ inline void mbar_arrive(uint64_t* bar) {
 // write the A operand step by step, signalling bar_full; warp 4 (lane 0) is the producer: it streams the B
 // chunks by TMA and issues the MMAs once a step's A is written and its B has arrived.  The query threads wait
 // only to reuse a stage (its MMA done) and for the tile's last MMA.
+template <bool MATERN>
 __global__ void __launch_bounds__(kTcM + 32) k_phaseB_tc(PhaseBArgs a, TcArgs t, const float* xq, Params p,
                                                          float* sdf, float* grad, float* var_sdf, float* var_f,
                                                          int32_t* winner, uint32_t* flags, int kcap, uint32_t ncols) {
@@ -1366,13 +1441,13 @@ __global__ void __launch_bounds__(kTcM + 32) k_phaseB_tc(PhaseBArgs a, TcArgs t,
             const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
             const float e = excess_sq(v.x, v.y, v.z, xn.x, xn.y, xn.z, wx, wy, wz);
             const float r2 = m + e;
-            kp = ex2(-c1 * e);
-            const float ak = v.w * kp;
+            const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+            float wg, y;
+            kernel_terms<MATERN>(e, z, zmin, c1, (float)p.lambda, kp, wg, y);
+            const float ak = v.w * wg;
             G0 = fmaf(ak, dx, G0);
             G1 = fmaf(ak, dy, G1);
             G2 = fmaf(ak, dz, G2);
-            const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-            const float y = fmaxf(z - zmin, 0.f);
             const float wt = ex2(-c2 * y);
             W += wt;
             HY = fmaf(wt, y, HY);
@@ -1413,7 +1488,7 @@ __global__ void __launch_bounds__(kTcM + 32) k_phaseB_tc(PhaseBArgs a, TcArgs t,
         const float hy = HY / W;
         const float B = fmaf(as, hy, 1.f);
         const float vs = fmaxf((B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W), 0.f);
-        const float vf = fmaxf(1.f - ex2(-2.f * c1 * m) * VS, 0.f);
+        const float vf = fmaxf(1.f - ex2(-2.f * c1 * (MATERN ? zmin : m)) * VS, 0.f);
         float sg = 1.f;
         if (a.sign) {
           sg = a.sign[q] < 0 ? -1.f : 1.f;
@@ -1519,6 +1594,7 @@ __global__ void k_make_tiles3(const int64_t* cnt, const int64_t* off, const int6
 
 // Q6 (plain path): binary64 throughout; V[f] by forward substitution with the stored Cholesky factor,
 // v = L^{-1} k' (in place over k'), V[f] = 1 - e^{-2 lambda d^2} |v|^2.
+template <bool MATERN>
 __global__ void __launch_bounds__(kTB64) k_phaseB64(PhaseBArgs a, const double* xq, Params p, double* sdf,
                                                     double* grad, double* var_sdf, double* var_f, int32_t* winner,
                                                     uint32_t* flags) {
@@ -1581,9 +1657,18 @@ __global__ void __launch_bounds__(kTB64) k_phaseB64(PhaseBArgs a, const double* 
         const D4 v = s_d[i];
         const double dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
         const double r2 = dx * dx + dy * dy + dz * dz;
-        const double kp = exp(-lam * (r2 - m));
+        // k' and the factor w of its gradient (grad k' = -c w (x - x_i)): RBF w = k'; Matern w = e^{-lambda (r - d)}
+        double kp, wg;
+        if (MATERN) {
+          const double r = sqrt(r2);
+          wg = exp(-lam * (r - zmin));
+          kp = (1.0 + lam * r) * wg;
+        } else {
+          kp = exp(-lam * (r2 - m));
+          wg = kp;
+        }
         s_k[i * kTB64 + tid] = kp;
-        const double ak = v.w * kp;
+        const double ak = v.w * wg;
         G0 += ak * dx;
         G1 += ak * dy;
         G2 += ak * dz;
@@ -1614,7 +1699,7 @@ __global__ void __launch_bounds__(kTB64) k_phaseB64(PhaseBArgs a, const double* 
           s_k[i * kTB64 + tid] = v;
           acc = fma(v, v, acc);
         }
-        vf = fmax(1.0 - exp(-2.0 * lam * m) * acc, 0.0);
+        vf = fmax(1.0 - exp(-2.0 * lam * (MATERN ? zmin : m)) * acc, 0.0);
       }
       double s = 1.0;
       if (a.sign) {
@@ -1902,7 +1987,6 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   cudaEvent_t e_q = prof_begin(c), e0 = prof_begin(c);
   // Q1 (kEmptyKey is all ones)
   KSDF_CUDA(c, cudaMemsetAsync(bhk, 0xFF, sizeof(uint64_t) * bcap, st));
-  KSDF_CUDA(c, cudaMemsetAsync(bin_cnt, 0, sizeof(int64_t) * bcap, st));
   KSDF_CUDA(c, cudaMemsetAsync(totals, 0, sizeof(int64_t) * 10, st));
   KSDF_CUDA(c, cudaMemsetAsync(wcnt, 0, sizeof(int64_t) * G, st));
   if (f64)
@@ -1912,13 +1996,15 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   // Q2
   launch(k_slot_flags, ceil_div(bcap, 256), 256, 0, st, bhk, bcap, slot_id);
   KSDF_CUDA(c, scan_i64(slot_id, slot_id, bcap, &totals[0], c->ws[WS_SCAN], st));
-  launch(k_bin_table, ceil_div(bcap, 256), 256, 0, st, bhk, bcap, slot_id, bin_key);
+  launch(k_bin_table, ceil_div(bcap, 256), 256, 0, st, bhk, bcap, slot_id, bin_key, bin_cnt);
   launch(k_q_rank, ceil_div(Q, 256), 256, 0, st, qkey, Q, bhk, slot_id, bcap, qbin, qrank, bin_cnt);
-  KSDF_CUDA(c, scan_i64(bin_cnt, bin_off, bcap, &totals[1], c->ws[WS_SCAN], st));
-  launch(k_ntiles, ceil_div(bcap, 256), 256, 0, st, bin_cnt, bcap, kTA, bin_nt);
-  KSDF_CUDA(c, scan_i64(bin_nt, bin_toff, bcap, &totals[2], c->ws[WS_SCAN], st));
+  // the per-bin passes cover the occupied bins only (their count is on the device, totals[0])
+  const int64_t* nbins = &totals[0];
+  KSDF_CUDA(c, scan_i64(bin_cnt, bin_off, bcap, &totals[1], c->ws[WS_SCAN], st, nbins));
+  launch(k_ntiles, ceil_div(bcap, 256), 256, 0, st, bin_cnt, bcap, kTA, bin_nt, nbins);
+  KSDF_CUDA(c, scan_i64(bin_nt, bin_toff, bcap, &totals[2], c->ws[WS_SCAN], st, nbins));
   launch(k_scatter_grouped, ceil_div(Q, 256), 256, 0, st, qbin, qrank, Q, bin_off, qsort);
-  launch(k_make_tiles, ceil_div(bcap, 256), 256, 0, st, bin_cnt, bin_off, bin_toff, bcap, kTA, tiles_a);
+  launch(k_make_tiles, ceil_div(bcap, 256), 256, 0, st, bin_cnt, bin_off, bin_toff, bcap, kTA, tiles_a, nbins);
   prof_end(c, e0, "query.group");
   e0 = prof_begin(c);
   // Q3
@@ -1950,16 +2036,18 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   const int maxn = std::max(m.max_n, 1);
   if (f64) {
     const size_t smem = sizeof(D4) * (size_t)p.K * maxn;
-    KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseA64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = p.kernel == KSDF_KERNEL_MATERN32 ? k_phaseA64<true> : k_phaseA64<false>;
+    KSDF_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA64, kTA, smem));
-    launch(k_phaseA64, std::max(1, occ) * c->num_sms, kTA, smem, st, pa, static_cast<const double*>(xq), p);
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTA, smem));
+    launch(kern, std::max(1, occ) * c->num_sms, kTA, smem, st, pa, static_cast<const double*>(xq), p);
   } else {
     const size_t smem = phase_a_smem(p.K, p.n_max);
-    KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = p.kernel == KSDF_KERNEL_MATERN32 ? k_phaseA<true> : k_phaseA<false>;
+    KSDF_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseA, kTA, smem));
-    launch(k_phaseA, std::max(1, occ) * c->num_sms, kTA, smem, st, pa, static_cast<const float*>(xq), p);
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTA, smem));
+    launch(kern, std::max(1, occ) * c->num_sms, kTA, smem, st, pa, static_cast<const float*>(xq), p);
   }
   KSDF_CUDA(c, cudaGetLastError());
   prof_end(c, e0, f64 ? "query64.phaseA" : "query.phaseA");
@@ -1984,7 +2072,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   int4* tiles_b2 = tiles_b1 + tcap;
   int64_t *nt1 = cbuf + 4 * G, *nt2 = cbuf + 5 * G, *toff1 = cbuf + 6 * G, *toff2 = cbuf + 7 * G;
   if (f64) {
-    launch(k_ntiles, ceil_div(G, 256), 256, 0, st, wcnt, G, TBq, wnt);
+    launch(k_ntiles, ceil_div(G, 256), 256, 0, st, wcnt, G, TBq, wnt, (const int64_t*)nullptr);
     KSDF_CUDA(c, scan_i64(wnt, wtoff, G, &totals[3], c->ws[WS_SCAN], st));
   } else {
     launch(k_ntiles3, ceil_div(G, 256), 256, 0, st, wcnt, ptr<int32_t>(m.n), G, kTcSmallN, kTcMaxN, kTcM, kBItem, wnt,
@@ -1995,7 +2083,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   }
   launch(k_w_scatter, ceil_div(Q, 256), 256, 0, st, qwin, qbin, wrank, Q, woff, qwsort);
   if (f64)
-    launch(k_make_tiles, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, G, TBq, tiles_b);
+    launch(k_make_tiles, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, G, TBq, tiles_b, (const int64_t*)nullptr);
   else
     launch(k_make_tiles3, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, toff1, toff2, ptr<int32_t>(m.n), kTcSmallN,
            kTcMaxN, G, kTcM, kBItem, tiles_b, tiles_b1, tiles_b2);
@@ -2027,10 +2115,11 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   pb.st = stw;
   if (f64) {
     const size_t smem = sizeof(D4) * p.n_max + sizeof(double) * p.n_max * (1 + kTB64);
-    KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = p.kernel == KSDF_KERNEL_MATERN32 ? k_phaseB64<true> : k_phaseB64<false>;
+    KSDF_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB64, kTB64, smem));
-    launch(k_phaseB64, std::max(1, occ) * c->num_sms, kTB64, smem, st, 
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTB64, smem));
+    launch(kern, std::max(1, occ) * c->num_sms, kTB64, smem, st, 
         pb, static_cast<const double*>(xq), p, static_cast<double*>(sdf), static_cast<double*>(grad),
         static_cast<double*>(var_sdf), static_cast<double*>(var_f), winner, flags);
   } else {
@@ -2041,14 +2130,15 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
       KSDF_CUDA(c, fork_streams(c));
       const int smax = maxn;
       const size_t smem = sizeof(float4) * smax + sizeof(float) * (linv_blocked_size(kLinvStageN) + (size_t)smax * (1 + kBQ));
-      KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      auto kb = p.kernel == KSDF_KERNEL_MATERN32 ? k_phaseB<true> : k_phaseB<false>;
+      KSDF_CUDA(c, cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int occ = 0;
-      KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phaseB, kBQ * kBW, smem));
+      KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb, kBQ * kBW, smem));
       PhaseBArgs p2 = pb;
       p2.tiles = tiles_b2;
       p2.n_tiles = &totals[5];
       p2.counter = &counters[3];
-      launch(k_phaseB, std::max(1, occ) * c->num_sms, kBQ * kBW, smem, c->aux[0], p2, static_cast<const float*>(xq), p,
+      launch(kb, std::max(1, occ) * c->num_sms, kBQ * kBW, smem, c->aux[0], p2, static_cast<const float*>(xq), p,
              static_cast<float*>(sdf), static_cast<float*>(grad), static_cast<float*>(var_sdf),
              static_cast<float*>(var_f), winner, flags, smax);
     }
@@ -2058,8 +2148,9 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
       uint32_t ncols = 32;
       while ((int)ncols < tc_np(kcap)) ncols <<= 1;
       const size_t smem = tc_smem_bytes(kcap);
-      KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      KSDF_CUDA(c, cudaFuncSetAttribute(k_phaseB_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+      auto ktc = p.kernel == KSDF_KERNEL_MATERN32 ? k_phaseB_tc<true> : k_phaseB_tc<false>;
+      KSDF_CUDA(c, cudaFuncSetAttribute(ktc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      KSDF_CUDA(c, cudaFuncSetAttribute(ktc, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         (int)cudaSharedmemCarveoutMaxShared));
       // CTAs per SM: bounded by the TMEM columns (512 per SM) and the shared memory (227 KB per SM usable,
       // plus the static part and the 1 KB the driver reserves per CTA)
@@ -2072,7 +2163,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
       ta.ltc_off = ptr<int64_t>(m.ltc_off);
       ta.ltc = ptr<float>(m.ltc);
       ta.ltc_lo = m.ltc_total;
-      launch(k_phaseB_tc, occ * c->num_sms, kTcM + 32, smem, st, pb, ta, static_cast<const float*>(xq), p,
+      launch(ktc, occ * c->num_sms, kTcM + 32, smem, st, pb, ta, static_cast<const float*>(xq), p,
              static_cast<float*>(sdf), static_cast<float*>(grad), static_cast<float*>(var_sdf),
              static_cast<float*>(var_f), winner, flags, kcap, ncols);
     }

@@ -38,8 +38,14 @@ __device__ inline int64_t block_exscan(int64_t v, int64_t* smem_warp, int64_t* t
   return warp_base + x - v;
 }
 
-__global__ void k_scan_reduce(const int64_t* in, int64_t n, int64_t* sums) {
+// n_dev (may be NULL): the scan covers min(n, *n_dev) elements, a count known only on the device
+__device__ __forceinline__ int64_t scan_len(int64_t n, const int64_t* n_dev) {
+  return n_dev ? (*n_dev < n ? *n_dev : n) : n;
+}
+
+__global__ void k_scan_reduce(const int64_t* in, int64_t n, const int64_t* n_dev, int64_t* sums) {
   __shared__ int64_t sw[kScanThreads / 32];
+  n = scan_len(n, n_dev);
   int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int64_t s = 0;
 #pragma unroll
@@ -64,8 +70,10 @@ __global__ void k_scan_sums(int64_t* sums, int64_t nb, int64_t* total) {
   if (threadIdx.x == 0 && total) *total = carry;
 }
 
-__global__ void k_scan_apply(const int64_t* in, int64_t* out, int64_t n, const int64_t* sums) {
+__global__ void k_scan_apply(const int64_t* in, int64_t* out, int64_t n, const int64_t* n_dev, const int64_t* sums) {
   __shared__ int64_t sw[kScanThreads / 32];
+  n = scan_len(n, n_dev);
+  if ((int64_t)blockIdx.x * kScanTile >= n) return;  // the whole block is past the end (uniform)
   int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int64_t v[kScanItems];
   int64_t s = 0;
@@ -89,8 +97,9 @@ constexpr int kScanSingleThreads = 1024;
 constexpr int kScanSingleItems = 64;
 
 __global__ void __launch_bounds__(kScanSingleThreads) k_scan_single(const int64_t* in, int64_t* out, int64_t n,
-                                                                     int64_t* total) {
+                                                                     const int64_t* n_dev, int64_t* total) {
   __shared__ int64_t sw[kScanSingleThreads / 32];
+  n = scan_len(n, n_dev);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t per = (n + kScanSingleThreads - 1) / kScanSingleThreads;
   const int64_t b = (int64_t)threadIdx.x * per, e = b + per < n ? b + per : n;
@@ -187,22 +196,23 @@ __global__ void k_rs_scatter(const uint64_t* keys, const uint32_t* vals, uint64_
 
 }  // namespace
 
-cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, DevBuf& tmp, cudaStream_t st) {
+cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, DevBuf& tmp, cudaStream_t st,
+                     const int64_t* n_dev) {
   if (n <= 0) {
     if (total) return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
     return cudaSuccess;
   }
   if (n <= (int64_t)kScanSingleThreads * kScanSingleItems) {
-    launch(k_scan_single, 1, kScanSingleThreads, 0, st, in, out, n, total);
+    launch(k_scan_single, 1, kScanSingleThreads, 0, st, in, out, n, n_dev, total);
     return cudaGetLastError();
   }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   cudaError_t e = ensure(tmp, sizeof(int64_t) * (size_t)(nb + 1));
   if (e != cudaSuccess) return e;
   int64_t* sums = ptr<int64_t>(tmp);
-  launch(k_scan_reduce, (unsigned)nb, kScanThreads, 0, st, in, n, sums);
+  launch(k_scan_reduce, (unsigned)nb, kScanThreads, 0, st, in, n, n_dev, sums);
   launch(k_scan_sums, 1, kScanThreads, 0, st, sums, nb, total);
-  launch(k_scan_apply, (unsigned)nb, kScanThreads, 0, st, in, out, n, sums);
+  launch(k_scan_apply, (unsigned)nb, kScanThreads, 0, st, in, out, n, n_dev, sums);
   return cudaGetLastError();
 }
 
@@ -229,11 +239,11 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, 
     int shift = 8 * p;
     launch(k_rs_hist, nblocks, kRsThreads, 0, st, ki, n, shift, hist, nblocks);
     if (nh <= (int64_t)kScanSingleThreads * kScanSingleItems) {
-      launch(k_scan_single, 1, kScanSingleThreads, 0, st, hist, hist, nh, (int64_t*)nullptr);
+      launch(k_scan_single, 1, kScanSingleThreads, 0, st, hist, hist, nh, (const int64_t*)nullptr, (int64_t*)nullptr);
     } else {
-      launch(k_scan_reduce, (unsigned)nb_scan, kScanThreads, 0, st, hist, nh, sums);
+      launch(k_scan_reduce, (unsigned)nb_scan, kScanThreads, 0, st, hist, nh, (const int64_t*)nullptr, sums);
       launch(k_scan_sums, 1, kScanThreads, 0, st, sums, nb_scan, (int64_t*)nullptr);
-      launch(k_scan_apply, (unsigned)nb_scan, kScanThreads, 0, st, hist, hist, nh, sums);
+      launch(k_scan_apply, (unsigned)nb_scan, kScanThreads, 0, st, hist, hist, nh, (const int64_t*)nullptr, sums);
     }
     launch(k_rs_scatter, nblocks, kRsThreads, 0, st, ki, vi, ko, vo, n, shift, hist, nblocks);
     uint64_t* tk = ki; ki = ko; ko = tk;

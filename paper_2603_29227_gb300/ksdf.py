@@ -25,6 +25,8 @@ OUT_SDF, OUT_GRAD, OUT_VAR_SDF, OUT_VAR_F, OUT_WINNER, OUT_FLAGS, OUT_ALL = 1, 2
 OUT_VAR_GRAD = 64  # optional: the SDF-gradient variance (Q x dim)
 FLAG_FALLBACK, FLAG_NO_GP, FLAG_NEAR_TIE, FLAG_ZERO_GRAD, FLAG_CLAMPED, FLAG_INVALID = 1, 2, 4, 8, 16, 32
 CELL_OK, CELL_EMPTY, CELL_NOT_PD = 0, 1, 2
+KERNEL_RBF, KERNEL_MATERN32 = 0, 1  # kernel table of Sec. IV-B.2
+KERNELS = {"rbf": KERNEL_RBF, "matern32": KERNEL_MATERN32}
 
 # every entry point declared in include/ksdf.h
 ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_update", "ksdf_query",
@@ -43,7 +45,8 @@ class KsdfError(RuntimeError):
 class ksdf_params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("origin", ctypes.c_double * 3), ("cell", ctypes.c_double),
                 ("margin", ctypes.c_double), ("n_max", ctypes.c_int), ("k_cand", ctypes.c_int),
-                ("lambda_", ctypes.c_double), ("softmin_alpha", ctypes.c_double), ("sign_mode", ctypes.c_int)]
+                ("lambda_", ctypes.c_double), ("softmin_alpha", ctypes.c_double), ("sign_mode", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
 
 _lib = None
@@ -142,6 +145,8 @@ def make_params(p: dict) -> ksdf_params:
     q.lambda_ = float(p["lambda"])
     q.softmin_alpha = float(p.get("softmin_alpha", 0.0))
     q.sign_mode = int(p.get("sign_mode", 0))
+    k = p.get("kernel", KERNEL_RBF)
+    q.kernel = KERNELS[k] if isinstance(k, str) else int(k)
     return q
 
 

@@ -31,7 +31,8 @@ ADJ_REL = 3.5e-3
 
 
 def cancellation_ratio(model, xq, cells):
-    """Oracle-side conditioning of the gradient sum for each query on the given winner cell."""
+    """Oracle-side conditioning of the gradient sum sum_i alpha_i w_i (x - x_i) for each query on the given winner
+    cell (w_i the factor of grad k'_i: k'_i itself for the RBF kernel, e^{-lambda (r_i - d)} for Matern 3/2)."""
     keys, status, off, mem = model.cells()
     xq = np.asarray(xq, dtype=np.float64)
     out = np.ones(len(xq))
@@ -45,7 +46,11 @@ def cancellation_ratio(model, xq, cells):
         al = model.alpha(int(g))
         r = xq[sel][:, None, :] - xs[None, :, :]
         r2 = np.sum(r * r, axis=2)
-        kp = np.exp(-lam * (r2 - r2.min(axis=1, keepdims=True)))
+        if model.params.get("kernel", 0) in (1, "matern32"):  # gradient weights e^{-lambda (r_i - d)}
+            rr = np.sqrt(r2)
+            kp = np.exp(-lam * (rr - rr.min(axis=1, keepdims=True)))
+        else:  # k'_i = e^{-lambda (r_i^2 - d^2)}
+            kp = np.exp(-lam * (r2 - r2.min(axis=1, keepdims=True)))
         num = np.linalg.norm(np.sum((al * kp)[:, :, None] * r, axis=1), axis=1)
         den = np.sum(np.abs(al) * kp * np.sqrt(r2), axis=1)
         out[sel] = num / np.maximum(den, 1e-300)

@@ -39,7 +39,7 @@ def test_invalid_parameters_rejected_without_cuda(lib):
                 **{"lambda": 300.0})
     bad = [dict(good, dim=4), dict(good, cell=0.0), dict(good, margin=-1.0), dict(good, n_max=0),
            dict(good, n_max=513), dict(good, k_cand=0), dict(good, k_cand=33), dict(good, **{"lambda": -1.0}),
-           dict(good, sign_mode=2), dict(good, margin=10.0)]
+           dict(good, sign_mode=2), dict(good, margin=10.0), dict(good, kernel=2), dict(good, kernel=-1)]
     for p in bad:
         h = ctypes.c_void_p()
         pr = ksdf.make_params(p)
