@@ -139,10 +139,27 @@ ksdf_status ksdf_fit(ksdf_ctx* ctx, const double* x, const float* var, const flo
  * samples, which keep their ids, and refit.  The result is the model ksdf_fit would build from all
  * S + S_new samples; cells whose training set (members and their order) is unchanged take their factor,
  * L^{-1} and alpha from the previous model instead of being refitted.  *n_cells_refit (host, may be NULL)
- * receives the number of cells fitted.  Synchronises the stream.  Errors as ksdf_fit; on an error the
- * context has no model (KSDF_ERR_NOT_FITTED until the next ksdf_fit).  KSDF_ERR_NOT_FITTED without a model. */
+ * receives the number of cells fitted.  With a refit budget (ksdf_set_schedule) the changed cells beyond it are
+ * deferred and the model is no longer a fresh fit of all samples until they are fitted.  Synchronises the stream.
+ * Errors as ksdf_fit; on an error the context has no model (KSDF_ERR_NOT_FITTED until the next ksdf_fit).
+ * KSDF_ERR_NOT_FITTED without a model. */
 ksdf_status ksdf_update(ksdf_ctx* ctx, const double* x_new, const float* var_new, const float* normals_new,
                         int64_t S_new, int64_t* n_cells_refit);
+
+/* Refit scheduling of ksdf_update (the training queue of Sec. IV-C / App. G).  Every cell carries a query counter
+ * c0 -- each query that fuses the cell (the cell is one of its bin's K candidates) adds one, capped at 10000 --
+ * and training marks c2 -- each update in which the cell's training set changed adds one.  With max_refit > 0 an
+ * update fits at most max_refit cells: first every cell that must be fitted (new, or not fitted before), then the
+ * changed cells by descending score c2 (1 + eta c0) (FP32, ties in cell order); the other changed cells are
+ * deferred and keep the training set, factor and alpha of their last fit.  A fitted cell resets c2 to 0 and halves
+ * c0.  With max_refit > 0, ksdf_update with S_new = 0 runs one more round over the deferred cells.  max_refit = 0
+ * (the default) fits every changed cell, so that the model equals a fresh fit of all samples.  eta >= 0 (default
+ * 1e-3).  KSDF_ERR_ARG for a negative max_refit or a non-finite or negative eta. */
+ksdf_status ksdf_set_schedule(ksdf_ctx* ctx, int64_t max_refit, double eta);
+/* The scheduling state of the model's G cells (host or device int32 arrays, any may be NULL): c0, c2, and refit
+ * (1 if the last ksdf_fit / ksdf_update fitted the cell).  Synchronises the stream.  KSDF_ERR_NOT_FITTED without a
+ * model. */
+ksdf_status ksdf_get_schedule(ksdf_ctx* ctx, int32_t* c0, int32_t* c2, int32_t* refit);
 
 /* Model serialisation (the serialised map of the paper's scalability experiment, whose size is set by the
  * stored GP surface samples): ksdf_save writes the context's parameters and the S samples the model was

@@ -230,7 +230,7 @@ static void release_model(Model& m) {
   DevBuf* bufs[] = {&m.key,   &m.status, &m.n,      &m.ts_off, &m.chol_off, &m.linv_off, &m.hkeys,
                     &m.hvals, &m.cell_order, &m.mf4, &m.md4,    &m.mvar,     &m.mnrm,     &m.mgid,
                     &m.mpad,  &m.chol64, &m.linv32,  &m.x,      &m.ltc_off,  &m.ltc,      &m.var_all,
-                    &m.nrm_all, &m.bk_off, &m.bk_cells};
+                    &m.nrm_all, &m.bk_off, &m.bk_cells, &m.qc0,     &m.qc2,      &m.refit};
   for (DevBuf* b : bufs) release(*b);
 }
 
@@ -277,11 +277,11 @@ ksdf_status ksdf_update(ksdf_ctx* c, const double* x_new, const float* var_new, 
   if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "ksdf_update: no model to update (call ksdf_fit first)");
   if (S_new < 0 || (S_new > 0 && !x_new)) return set_err(c, KSDF_ERR_ARG, "ksdf_update: need x_new for S_new > 0");
   Model& m = c->m;
-  if (S_new == 0) {
+  if (S_new == 0 && c->sched_max <= 0) {  // nothing new, and no deferred cells without a budget
     if (n_cells_refit) *n_cells_refit = 0;
     return KSDF_OK;
   }
-  if ((normals_new != nullptr) != m.has_normals)
+  if (S_new > 0 && (normals_new != nullptr) != m.has_normals)
     return set_err(c, KSDF_ERR_ARG, "ksdf_update: normals must be given exactly when the model has normals");
   const int dim = c->p.dim;
   const int64_t S0 = m.S, S = S0 + S_new;
@@ -299,15 +299,17 @@ ksdf_status ksdf_update(ksdf_ctx* c, const double* x_new, const float* var_new, 
   float* uv = ptr<float>(c->ws[WS_UV]);
   float* un = nullptr;
   KSDF_CUDA(c, cudaMemcpyAsync(ux, m.x.p, sizeof(double) * S0 * dim, cudaMemcpyDeviceToDevice, st));
-  KSDF_CUDA(c, cudaMemcpyAsync(ux + S0 * dim, dx, sizeof(double) * S_new * dim, cudaMemcpyDeviceToDevice, st));
+  if (S_new > 0)
+    KSDF_CUDA(c, cudaMemcpyAsync(ux + S0 * dim, dx, sizeof(double) * S_new * dim, cudaMemcpyDeviceToDevice, st));
   KSDF_CUDA(c, cudaMemcpyAsync(uv, m.var_all.p, sizeof(float) * S0, cudaMemcpyDeviceToDevice, st));
   if (dv) KSDF_CUDA(c, cudaMemcpyAsync(uv + S0, dv, sizeof(float) * S_new, cudaMemcpyDeviceToDevice, st));
-  else KSDF_CUDA(c, cudaMemsetAsync(uv + S0, 0, sizeof(float) * S_new, st));
+  else if (S_new > 0) KSDF_CUDA(c, cudaMemsetAsync(uv + S0, 0, sizeof(float) * S_new, st));
   if (m.has_normals) {
     KSDF_CUDA(c, ensure(c->ws[WS_UN], sizeof(float) * S * dim));
     un = ptr<float>(c->ws[WS_UN]);
     KSDF_CUDA(c, cudaMemcpyAsync(un, m.nrm_all.p, sizeof(float) * S0 * dim, cudaMemcpyDeviceToDevice, st));
-    KSDF_CUDA(c, cudaMemcpyAsync(un + S0 * dim, dn, sizeof(float) * S_new * dim, cudaMemcpyDeviceToDevice, st));
+    if (S_new > 0)
+      KSDF_CUDA(c, cudaMemcpyAsync(un + S0 * dim, dn, sizeof(float) * S_new * dim, cudaMemcpyDeviceToDevice, st));
   }
   // the current model becomes the previous one; the new model reuses the buffers of the one before
   std::swap(c->m, c->m_prev);
@@ -315,6 +317,27 @@ ksdf_status ksdf_update(ksdf_ctx* c, const double* x_new, const float* var_new, 
   s = fit_model(c, ux, uv, un, S, &c->m_prev, &nref);
   if (n_cells_refit) *n_cells_refit = nref;
   return s;
+}
+
+ksdf_status ksdf_set_schedule(ksdf_ctx* c, int64_t max_refit, double eta) {
+  if (!c) return KSDF_ERR_ARG;
+  if (max_refit < 0 || !(eta >= 0) || !(eta < 1e30))
+    return set_err(c, KSDF_ERR_ARG, "ksdf_set_schedule: need max_refit >= 0 and a finite eta >= 0");
+  c->sched_max = max_refit;
+  c->sched_eta = (float)eta;
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_get_schedule(ksdf_ctx* c, int32_t* c0, int32_t* c2, int32_t* refit) {
+  if (!c) return KSDF_ERR_ARG;
+  if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "ksdf_get_schedule: no model");
+  const int64_t G = c->m.G;
+  int32_t* outs[3] = {c0, c2, refit};
+  DevBuf* srcs[3] = {&c->m.qc0, &c->m.qc2, &c->m.refit};
+  for (int k = 0; k < 3; ++k)
+    if (outs[k]) KSDF_CUDA(c, cudaMemcpyAsync(outs[k], srcs[k]->p, sizeof(int32_t) * G, cudaMemcpyDefault, c->stream));
+  KSDF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return KSDF_OK;
 }
 
 ksdf_status ksdf_autotune(ksdf_ctx* c, int* table, double* fit_ms) {

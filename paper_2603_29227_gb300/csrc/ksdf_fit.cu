@@ -221,6 +221,86 @@ __global__ void k_sizes(const int64_t* n, int64_t G, int64_t* tri, int64_t* lb, 
 }
 
 // fit order: descending size; cells not to be fitted (touched == 0) sort after every other
+// ---- refit scheduling (Sec. IV-C, App. G) ----
+// Per cell g of the new model (a warp each): its previous cell (by key), whether its freshly assembled training
+// set (mpad, n64) differs from the one the previous model was fitted on, the carried counters (c2 + 1 when it
+// changed) and the priority key of the training queue: 0 for a cell that must be fitted (new, or previously not
+// fitted), 1 + (2^32 - 1 - bits(s)) for a changed cell with score s = c2 (1 + eta c0) (FP32, rounded step by step,
+// so larger scores come first), 2^40 for an unchanged cell.  Ties keep cell order (ascending key).
+__global__ void k_sched_score(const uint64_t* key, const int64_t* n64, const int32_t* mpad, int64_t G, int n_max,
+                              const uint64_t* ohk, const int32_t* ohv, uint64_t ohcap, const int32_t* on32,
+                              const int64_t* ots_off, const int32_t* omgid, const int32_t* ostatus,
+                              const int32_t* oc0, const int32_t* oc2, float eta, int32_t* c0, int32_t* c2,
+                              int32_t* oid, int32_t* chg, uint64_t* skey, uint32_t* sval) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= G) return;
+  const int o = hash_find(ohk, ohv, ohcap, key[g]);
+  const int n = (int)n64[g];
+  const bool fitted_before = o >= 0 && ostatus[o] == KSDF_CELL_OK;
+  bool same = fitted_before && on32[o] == n && n > 0;
+  if (same) {
+    const int32_t* a = mpad + g * n_max;
+    const int32_t* b = omgid + ots_off[o];
+    bool eq = true;
+    for (int i = lane; i < n; i += 32) eq &= a[i] == b[i];
+    same = __all_sync(0xffffffffu, eq);
+  }
+  if (lane == 0) {
+    const int q0 = o >= 0 ? oc0[o] : 0, q2 = (o >= 0 ? oc2[o] : 0) + (same ? 0 : 1);
+    c0[g] = q0;
+    c2[g] = q2;
+    oid[g] = o;
+    chg[g] = same ? 0 : 1;
+    uint64_t k = 1ull << 40;
+    if (!fitted_before) {
+      k = 0;
+    } else if (!same) {
+      const float sc = __fmul_rn((float)q2, __fadd_rn(1.f, __fmul_rn(eta, (float)q0)));
+      k = 1ull + (0xFFFFFFFFull - (uint64_t)__float_as_uint(sc));
+    }
+    skey[g] = k;
+    sval[g] = (uint32_t)g;
+  }
+}
+
+// the first `budget` cells in priority order are fitted (cells that must be fitted always are); the other changed
+// cells are deferred
+__global__ void k_sched_select(const uint64_t* skey, const uint32_t* sval, int64_t G, int64_t budget, int32_t* sel) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G) return;
+  const uint64_t k = skey[r];
+  sel[sval[r]] = (k == 0 || (k < (1ull << 40) && r < budget)) ? 1 : 0;
+}
+
+// a deferred cell keeps the training set its previous fit was made on (a warp per cell)
+__global__ void k_sched_defer(const int32_t* chg, const int32_t* sel, const int32_t* oid, int64_t G, int n_max,
+                              const int32_t* on32, const int64_t* ots_off, const int32_t* omgid, int32_t* mpad,
+                              int64_t* n64, int* max_n) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= G || !chg[g] || sel[g]) return;
+  const int o = oid[g], n = on32[o];
+  for (int i = lane; i < n; i += 32) mpad[g * n_max + i] = omgid[ots_off[o] + i];
+  if (lane == 0) {
+    n64[g] = n;
+    atomicMax(max_n, n);
+  }
+}
+
+// after the fit: the cells fitted now (all of them on a fresh fit) reset their training marks and halve their
+// query counters
+__global__ void k_sched_after(const int32_t* touched, int64_t G, int32_t* c0, int32_t* c2, int32_t* refit) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int r = touched ? touched[g] : 1;
+  refit[g] = r;
+  if (r) {
+    c2[g] = 0;
+    c0[g] >>= 1;
+  }
+}
+
 __global__ void k_order_keys(const int32_t* n32, const int32_t* touched, int64_t G, int n_max, uint64_t* keys,
                              uint32_t* vals) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1204,6 +1284,33 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   KSDF_CUDA(c, cudaMemsetAsync(dmax, 0, sizeof(int) * 2, st));
   launch(k_assemble, (unsigned)G, kAssembleThreads, 0, st, ptr<uint64_t>(m.key), G, own_off, vals, x, p, R, ptr<uint64_t>(m.hkeys),
          ptr<int32_t>(m.hvals), cap, ptr<int32_t>(m.mpad), n64, ptr<int32_t>(m.status), dmax, stw);
+  // refit scheduling: carried counters; with a budget, the changed cells beyond it keep their previous training
+  // set (and, below, their previous fit)
+  KSDF_CUDA(c, ensure(m.qc0, sizeof(int32_t) * (G + 1)));
+  KSDF_CUDA(c, ensure(m.qc2, sizeof(int32_t) * (G + 1)));
+  KSDF_CUDA(c, ensure(m.refit, sizeof(int32_t) * (G + 1)));
+  if (!prev) {
+    KSDF_CUDA(c, cudaMemsetAsync(m.qc0.p, 0, sizeof(int32_t) * G, st));
+    KSDF_CUDA(c, cudaMemsetAsync(m.qc2.p, 0, sizeof(int32_t) * G, st));
+  } else {
+    Model& o = const_cast<Model&>(*prev);
+    KSDF_CUDA(c, ensure(c->ws[WS_SCHED], (sizeof(uint64_t) + 4 * sizeof(int32_t)) * (size_t)(G + 1)));
+    uint64_t* skey = ptr<uint64_t>(c->ws[WS_SCHED]);
+    uint32_t* sval = reinterpret_cast<uint32_t*>(skey + (G + 1));
+    int32_t* chg = reinterpret_cast<int32_t*>(sval + (G + 1));
+    int32_t* soid = chg + (G + 1);
+    int32_t* sel = soid + (G + 1);
+    launch(k_sched_score, ceil_div(G * 32, 256), 256, 0, st, ptr<uint64_t>(m.key), n64, ptr<int32_t>(m.mpad), G,
+           p.n_max, ptr<uint64_t>(o.hkeys), ptr<int32_t>(o.hvals), o.hcap, ptr<int32_t>(o.n), ptr<int64_t>(o.ts_off),
+           ptr<int32_t>(o.mgid), ptr<int32_t>(o.status), ptr<int32_t>(o.qc0), ptr<int32_t>(o.qc2), c->sched_eta,
+           ptr<int32_t>(m.qc0), ptr<int32_t>(m.qc2), soid, chg, skey, sval);
+    if (c->sched_max > 0) {
+      KSDF_CUDA(c, radix_sort_u64(skey, sval, G, 41, c->ws[WS_SORT], st));
+      launch(k_sched_select, ceil_div(G, 256), 256, 0, st, skey, sval, G, c->sched_max, sel);
+      launch(k_sched_defer, ceil_div(G * 32, 256), 256, 0, st, chg, sel, soid, G, p.n_max, ptr<int32_t>(o.n),
+             ptr<int64_t>(o.ts_off), ptr<int32_t>(o.mgid), ptr<int32_t>(m.mpad), n64, dmax);
+    }
+  }
   launch(k_sizes, ceil_div(G, 256), 256, 0, st, n64, G, tri64, lb64, tc64, ptr<int32_t>(m.n));
   KSDF_CUDA(c, scan_i64(n64, ptr<int64_t>(m.ts_off), G, dtot, c->ws[WS_SCAN], st));
   KSDF_CUDA(c, scan_i64(tri64, ptr<int64_t>(m.chol_off), G, dtot + 1, c->ws[WS_SCAN], st));
@@ -1441,6 +1548,8 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     ca.status = ptr<int32_t>(m.status);
     launch(k_copy_fit, (unsigned)std::min<int64_t>(G, 8 * c->num_sms), 256, 0, st, ca);
   }
+  launch(k_sched_after, ceil_div(G, 256), 256, 0, st, (const int32_t*)touched, G, ptr<int32_t>(m.qc0),
+         ptr<int32_t>(m.qc2), ptr<int32_t>(m.refit));
   // bricks over the cell bounding box for the candidate search (OK cells only; statuses are final here)
   {
     int64_t nbk[3];

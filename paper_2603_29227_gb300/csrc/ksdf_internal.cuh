@@ -165,6 +165,10 @@ struct Model {
   DevBuf bk_cells;  // int32 cell ids grouped by brick
   int bk_lo[3] = {0, 0, 0}, bk_n[3] = {0, 0, 0};
   int64_t nbricks = 0;
+  // refit scheduling (Sec. IV-C, App. G), per cell (int32): the query counter c0 (requests as a fused candidate,
+  // capped, halved when the cell is fitted), the training marks c2 (updates that changed the cell's training set
+  // since its last fit), and whether the last fit or update fitted the cell
+  DevBuf qc0, qc2, refit;
 };
 
 }  // namespace ksdf
@@ -191,7 +195,9 @@ struct ksdf_ctx {
   std::vector<ksdf::FitClassCfg> fit_cls;  // the fit's size classes (empty: the default table); ksdf_autotune
   // workspaces
   ksdf::DevBuf status_word;       // uint32 device status
-  ksdf::DevBuf ws[30];            // general workspaces (grow only), indexed by role
+  ksdf::DevBuf ws[31];            // general workspaces (grow only), indexed by role
+  int64_t sched_max = 0;          // refit budget of ksdf_update (cells per update; 0 = every changed cell)
+  float sched_eta = 1e-3f;        // weight of the query counter in the training priority
   ksdf::DevBuf stage[12];         // staging of host arrays
   int64_t reserved_q = 0, reserved_s = 0;
   int bb[6] = {0, 0, 0, 0, 0, 0};  // bounding box of the cells: min xyz, max xyz
@@ -298,8 +304,10 @@ enum WsRole {
   WS_UX = 26,     // update: the union of old and new samples (positions, variances, normals)
   WS_UV = 27,
   WS_UN = 28,
-  WS_BRICK = 29   // brick build: rank of each cell within its brick
+  WS_BRICK = 29,  // brick build: rank of each cell within its brick
+  WS_SCHED = 30   // refit scheduling: priority keys, cell ids, changed flags, previous ids
 };
+constexpr int kQueryCounterCap = 10000;  // cap of the per-cell query counter (App. G)
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 

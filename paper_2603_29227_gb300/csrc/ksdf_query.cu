@@ -102,6 +102,20 @@ __global__ void k_q_bin(const T* xq, int64_t Q, Params p, uint64_t* qkey, uint64
   atomicOr(st, ST_CAPACITY);
 }
 
+// query counters of the refit scheduling (App. G): every cell fused for a query (a candidate of its bin) counts
+// one request; counters are capped
+__global__ void k_count_requests(const int64_t* bin_cnt, const int32_t* cand, const int32_t* ncand,
+                                 const int64_t* n_bins, int K, int32_t* qc0) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= *n_bins) return;
+  const int n = ncand[b];
+  const int add = (int)(bin_cnt[b] < kQueryCounterCap ? bin_cnt[b] : (int64_t)kQueryCounterCap);
+  for (int k = 0; k < n; ++k) {
+    const int g = cand[b * K + k];
+    if (atomicAdd(&qc0[g], add) + add > kQueryCounterCap) atomicMin(&qc0[g], kQueryCounterCap);
+  }
+}
+
 __global__ void k_slot_flags(const uint64_t* bhk, uint64_t bcap, int64_t* flag) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s < (int64_t)bcap) flag[s] = bhk[s] != kEmptyKey ? 1 : 0;
@@ -2011,6 +2025,8 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   {
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(bcap, kCandWarps), 8LL * c->num_sms);
     launch(k_candidates, grid, 32 * kCandWarps, 0, st, bin_key, &totals[0], 0, cand_ctx(c), cand, ncand);
+    launch(k_count_requests, ceil_div(bcap, 256), 256, 0, st, bin_cnt, cand, ncand, &totals[0], p.K,
+           ptr<int32_t>(m.qc0));
   }
   prof_end(c, e0, "query.candidates");
   e0 = prof_begin(c);

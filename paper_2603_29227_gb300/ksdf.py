@@ -33,7 +33,7 @@ ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
                  "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math",
-                 "ksdf_save", "ksdf_load", "ksdf_wait_diagnostic")
+                 "ksdf_save", "ksdf_load", "ksdf_wait_diagnostic", "ksdf_set_schedule", "ksdf_get_schedule")
 
 
 class KsdfError(RuntimeError):
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
         "ksdf_device_math": [P, ctypes.c_int, P, I64, P],
         "ksdf_save": [P, ctypes.c_char_p],
         "ksdf_wait_diagnostic": [P, U32],
+        "ksdf_set_schedule": [P, I64, ctypes.c_double],
+        "ksdf_get_schedule": [P, P, P, P],
         "ksdf_load": [P, ctypes.c_char_p],
     }
     for name, args in sig.items():
@@ -201,6 +203,19 @@ def ksdf_wait_diagnostic(h, spins):
     """Launch the bounded-wait diagnostic (a wait that nothing completes gives up after `spins` polls); the next
     ksdf_sync_status reports KSDF_ERR_TIMEOUT."""
     _check(h, load().ksdf_wait_diagnostic(h, int(spins)), "ksdf_wait_diagnostic")
+
+
+def ksdf_set_schedule(h, max_refit, eta=1e-3):
+    """Refit budget of ksdf_update (cells per update, 0 = all changed cells) and the query-counter weight."""
+    _check(h, load().ksdf_set_schedule(h, int(max_refit), float(eta)), "ksdf_set_schedule")
+
+
+def ksdf_get_schedule(h):
+    """(c0, c2, refit) int32 arrays of the model's cells: query counters, training marks, fitted-last flags."""
+    G, _ = ksdf_model_size(h)
+    out = [np.empty(G, dtype=np.int32) for _ in range(3)]
+    _check(h, load().ksdf_get_schedule(h, *[_ptr(a) for a in out]), "ksdf_get_schedule")
+    return tuple(out)
 
 
 def ksdf_save(h, path):
@@ -392,12 +407,14 @@ class KernelSDF:
         self._stream()
         return ksdf_autotune(self.h)
 
-    def update(self, x_new, var=None, normals=None):
-        """Append samples (their ids follow the model's) and refit the cells they touch; returns the number
-        of cells refitted."""
+    def update(self, x_new, var=None, normals=None, S_new=None):
+        """Append samples (their ids follow the model's) and refit the cells they touch (within the refit budget
+        of ksdf_set_schedule); returns the number of cells refitted.  x_new None with S_new = 0 runs a round over
+        the deferred cells."""
         self._stream()
-        self.fit_status, n = ksdf_update(self.h, x_new, var, normals, int(x_new.shape[0]))
-        self.S += int(x_new.shape[0])
+        n_new = int(x_new.shape[0]) if x_new is not None else int(S_new or 0)
+        self.fit_status, n = ksdf_update(self.h, x_new, var, normals, n_new)
+        self.S += n_new
         return n
 
     def query(self, xq, sign=None, mask=OUT_ALL, f64=False):
