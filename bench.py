@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "scale3d_query_adjoint_dram.txt")
 METRIC = "SDF+grad+var queries/s at err<=1e-4 m vs FP64 oracle; % roofline; vs plain FP64"
+CITY_REFIT_BUDGET = 2000  # cells refitted per frame in the scheduled city stream
 WORKLOAD_TEXT = {
     "scale3d": ("scale3d: 50x50x10 m scene with 1,000 spheres/boxes, 2,000,000 samples (sigma 0.01 m), 0.5 m cells, "
                 "n_max 512, K 8, lambda 300; 256^3 = 16,777,216 grid queries; step = fit + query(sdf, grad, var_sdf, "
@@ -355,6 +356,7 @@ def full_step_bench(torch, dev, ksdf, w, steps=10):
     m = ksdf.KernelSDF(w.params)
     m.fit(x, var, nrm)
     m.autotune()
+    m.autotune_query(xq, sign)
     for _ in range(3):
         o = m.query(xq, sign)
         m.backward(xq, o["winner"], d_sdf, d_grad, sign)
@@ -417,40 +419,54 @@ def other_configs(torch, dev, ksdf, main_name):
                                          "queries; sdf + grad forward and adjoint to queries and samples",
                              "ms_per_step": ms, "queries_per_s": Q / (ms * 1e-3)}
     del m, d_sdf, d_grad
-    # streaming: LiDAR frames of a city block; frame 0 fits, every later frame appends its hits (ksdf_update:
-    # refit of the touched cells) and answers 1M queries around the pose
+    # streaming: LiDAR frames of a city block (scans made on the host by a process pool); frame 0 fits, every later
+    # frame appends its hits (ksdf_update) and answers 1M queries around the pose; once refitting every changed
+    # cell (the model stays a fresh fit of all samples), once with a refit budget per frame (the training queue)
     city = scenes.make_city()
-    m = ksdf.KernelSDF(city.params)
-    frames = []
-    n_frames = 6
-    S = 0
-    for f in range(n_frames):
-        hx, hv, hn = city.scan(f)
-        xq = t(city.queries(f, 1_000_000))
-        hx, hv, hn = t(hx), t(hv), t(hn)
-        torch.cuda.synchronize()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record()
-        if f == 0:
-            m.fit(hx, hv, hn)
-            nref = int(ksdf.ksdf_model_size(m.h)[0])
-        else:
-            nref = m.update(hx, hv, hn)
-        e[1].record()
-        m.query(xq)
-        e[2].record()
-        torch.cuda.synchronize()
-        S += int(hx.shape[0])
-        frames.append({"hits": int(hx.shape[0]), "samples": S, "cells_refit": nref,
-                       "cells": int(ksdf.ksdf_model_size(m.h)[0]), "refit_ms": e[0].elapsed_time(e[1]),
-                       "query_ms": e[1].elapsed_time(e[2])})
-    upd = frames[1:]
-    tot = sum(fr["refit_ms"] + fr["query_ms"] for fr in upd)
-    res["city_stream"] = {"workload": "100x100 m city block, 64x2048 LiDAR scans (~125k hits per frame, range noise "
-                                      "0.02 m), 1M queries per frame in the 40x40x6 m box around the pose; the "
-                                      "front-end occupancy update is not built", "frames": frames,
-                          "queries_per_s_incl_refit": 1e6 * len(upd) / (tot * 1e-3)}
-    del m
+    n_frames = len(city.poses)
+    import multiprocessing as mpc
+
+    with mpc.get_context("spawn").Pool(processes=min(16, os.cpu_count() or 1)) as pool:
+        scans = pool.map(city.scan, range(n_frames))
+    streams = {}
+    for mode, budget in (("exact", 0), ("scheduled", CITY_REFIT_BUDGET)):
+        m = ksdf.KernelSDF(city.params)
+        ksdf.ksdf_set_schedule(m.h, budget, 1e-3)
+        rec = {"refit_ms": [], "query_ms": [], "cells_refit": [], "cells": [], "samples": []}
+        S = 0
+        for f in range(n_frames):
+            hx, hv, hn = (t(a) for a in scans[f])
+            xq = t(city.queries(f, 1_000_000))
+            torch.cuda.synchronize()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            if f == 0:
+                m.fit(hx, hv, hn)
+                nref = int(ksdf.ksdf_model_size(m.h)[0])
+            else:
+                nref = m.update(hx, hv, hn)
+            e[1].record()
+            m.query(xq)
+            e[2].record()
+            torch.cuda.synchronize()
+            S += int(hx.shape[0])
+            rec["refit_ms"].append(round(e[0].elapsed_time(e[1]), 3))
+            rec["query_ms"].append(round(e[1].elapsed_time(e[2]), 3))
+            rec["cells_refit"].append(nref)
+            rec["cells"].append(int(ksdf.ksdf_model_size(m.h)[0]))
+            rec["samples"].append(S)
+        upd = slice(1, None)
+        tot = sum(rec["refit_ms"][upd]) + sum(rec["query_ms"][upd])
+        rec["queries_per_s_incl_refit"] = 1e6 * (n_frames - 1) / (tot * 1e-3)
+        rec["refit_ms_mean"] = float(np.mean(rec["refit_ms"][upd]))
+        rec["query_ms_mean"] = float(np.mean(rec["query_ms"][upd]))
+        rec["refit_budget"] = budget
+        streams[mode] = rec
+        del m
+    res["city_stream"] = {"workload": "100x100 m city block, %d frames of a 64x2048 LiDAR scan (~125k hits each, range "
+                                      "noise 0.02 m) on a closed path, 1M queries per frame in the 40x40x6 m box "
+                                      "around the pose; the front-end occupancy update is not built" % n_frames,
+                          "exact": streams["exact"], "scheduled": streams["scheduled"]}
     return res
 
 
@@ -538,9 +554,11 @@ def main():
         dq, dx = model.backward(xq, out["winner"], d_sdf, d_grad, sign)
         return out, dq, dx
 
-    # the fit's tile shape (warps per cell, by cell size) picked by timing the candidates on this model
+    # the fit's tile shape (warps per cell, by cell size) and the query's tile shapes picked by timing the
+    # candidates on this model and batch
     model.fit(x, var, nrm)
     tune_idx, tune_ms = model.autotune()
+    qtune_idx, qtune_ms = model.autotune_query(xq, sign)
     for _ in range(max(args.warmup, 3)):
         out, dq, dx = step()
     torch.cuda.synchronize()
@@ -734,6 +752,9 @@ def main():
                            "from one CUDA graph captured after the warm-up" if not args.no_graph
                            else "all launched from the host"),
                 "fit_autotune": {"table": tune_idx, "fit_ms_per_table": [round(float(v), 3) for v in tune_ms]},
+                "query_autotune": {"choice": qtune_idx, "query_ms_per_pair": [round(float(v), 3) for v in qtune_ms],
+                                   "pairs": "3 x phase A budget (64, 128, 256 chunks) + phase B class split (64, "
+                                            "96, 128 samples)"},
                 "precision": "FP64 kernel matrix (entries above 2.4e-16; smaller ones in FP32), Cholesky and alpha; "
                              "FP32 L^-1; FP32 query with compensated mean; V[f] contraction on tcgen05 in TF32 split "
                              "three ways with FP32 accumulation; FP32 adjoint with one FP64 refinement of each cell "

@@ -183,6 +183,19 @@ ksdf_status ksdf_load(ksdf_ctx* ctx, const char* path);
 ksdf_status ksdf_autotune(ksdf_ctx* ctx, int* table, double* fit_ms);
 int ksdf_autotune_tables(void);
 
+/* Autotuning of the query's tile shapes on the caller's own batch (Q points xq, Q x dim float32, sign Q int8 or
+ * NULL; host or device): phase A's shared-memory budget for the candidates' samples (64, 128 or 256 chunks of 8
+ * samples; a tile whose candidates hold more is processed in rounds) and the largest cell of phase B's 128-column
+ * tensor-memory class (64, 96 or 128 samples; larger cells up to 256 take 256 columns).  Every pair
+ * (ksdf_autotune_query_configs() of them, index = 3 x budget index + class index) runs the full query twice, the
+ * second timed with CUDA events on the context's stream; the fastest is kept for the context's later queries.
+ * The outputs do not depend on the choice.  *choice (may be NULL) gets the index, query_ms (may be NULL,
+ * ksdf_autotune_query_configs() doubles) the times.  Synchronises the stream.  KSDF_ERR_NOT_FITTED without a
+ * model, KSDF_ERR_ARG for Q <= 0. */
+ksdf_status ksdf_autotune_query(ksdf_ctx* ctx, const float* xq, int64_t Q, const int8_t* sign, int* choice,
+                                double* query_ms);
+int ksdf_autotune_query_configs(void);
+
 /* Diagnostic of failure detection (no counterpart in the paper): launches, on the context's stream, one CTA
  * that allocates tensor memory like the tensor-core query kernel and then waits on an mbarrier that nothing
  * completes (no copy or MMA is issued, so nothing is in flight), polling it at most `spins` times (1..2^24;

@@ -347,6 +347,23 @@ ksdf_status ksdf_autotune(ksdf_ctx* c, int* table, double* fit_ms) {
 
 int ksdf_autotune_tables(void) { return fit_table_count(); }
 
+int ksdf_autotune_query_configs(void) { return query_tune_count(); }
+
+ksdf_status ksdf_autotune_query(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, int* choice,
+                                double* query_ms) {
+  if (!c) return KSDF_ERR_ARG;
+  if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "ksdf_autotune_query: no model");
+  if (Q <= 0 || !xq) return set_err(c, KSDF_ERR_ARG, "ksdf_autotune_query: need Q > 0 queries");
+  const void *dq, *ds;
+  ksdf_status s;
+  if ((s = stage_in(c, 3, xq, sizeof(float) * Q * c->p.dim, &dq))) return s;
+  if ((s = stage_in(c, 4, sign, sizeof(int8_t) * Q, &ds))) return s;
+  std::vector<double> ms((size_t)query_tune_count(), 0.0);
+  s = autotune_query(c, static_cast<const float*>(dq), Q, static_cast<const int8_t*>(ds), choice, ms.data());
+  if (query_ms) std::memcpy(query_ms, ms.data(), sizeof(double) * ms.size());
+  return s;
+}
+
 namespace {
 constexpr char kMapMagic[8] = {'K', 'S', 'D', 'F', 'M', 'A', 'P', '1'};
 struct MapParams {  // the parameters in a fixed layout (no padding): 4 int32 then 7 float64

@@ -196,6 +196,8 @@ struct ksdf_ctx {
   // workspaces
   ksdf::DevBuf status_word;       // uint32 device status
   ksdf::DevBuf ws[31];            // general workspaces (grow only), indexed by role
+  int qt_chunks = 128;            // query tile shapes (ksdf_autotune_query): phase A's shared-memory budget in
+  int qt_tc_small = 96;           // chunks of 8 samples, and the largest cell of phase B's 128-column TMEM class
   int64_t sched_max = 0;          // refit budget of ksdf_update (cells per update; 0 = every changed cell)
   float sched_eta = 1e-3f;        // weight of the query counter in the training priority
   ksdf::DevBuf stage[12];         // staging of host arrays
@@ -268,6 +270,8 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
 ksdf_status candidates_for_keys(ksdf_ctx* c, const uint64_t* keys, int64_t n, int32_t* cand, int32_t* count);
 ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G);
 ksdf_status wait_diagnostic(ksdf_ctx* c, uint32_t spins);
+int query_tune_count();
+ksdf_status autotune_query(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, int* choice, double* ms);
 
 // ---- backward (ksdf_backward.cu) ----
 ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, const int32_t* winner,

@@ -509,6 +509,7 @@ struct PhaseAArgs {
   double* qu64;
   uint32_t* qflag;
   uint32_t* st;
+  int chunks;  // phase A's shared-memory budget in chunks of 8 samples
 };
 
 // The same bound for the Matern 3/2 kernel, where u = -log f' / lambda + d is linear in log f' and d (m is d):
@@ -564,13 +565,13 @@ __device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsign
 
 // Phase A shared memory, per tile: candidates' samples as chunks of 8 in SoA form -- one chunk is 40 floats,
 // x[8] y[8] z[8] alpha[8] |alpha|[8] -- each candidate padded to whole chunks with far zero-weight samples, at
-// most kChunkBudget chunks at a time (a tile whose candidates hold more is done in rounds of whole candidates);
+// most the budget's chunks at a time (a tile whose candidates hold more is done in rounds of whole candidates);
 // then the per-(candidate, query) results u, du and flag bits.
 constexpr int kChunkF = 40;
-constexpr int kChunkBudget = 128;  // 20 KB of samples
-__host__ __device__ inline int phase_a_chunks(int n_max) { return max(kChunkBudget, (n_max + 7) / 8); }
-__host__ __device__ inline size_t phase_a_smem(int K, int n_max) {
-  return sizeof(float) * (size_t)kChunkF * phase_a_chunks(n_max) + (size_t)K * kTA * (2 * sizeof(float) + 1);
+// the budget: the context's tile shape (ksdf_autotune_query), at least one whole largest candidate
+__host__ __device__ inline int phase_a_chunks(int tuned, int n_max) { return max(tuned, (n_max + 7) / 8); }
+__host__ __device__ inline size_t phase_a_smem(int K, int chunks) {
+  return sizeof(float) * (size_t)kChunkF * chunks + (size_t)K * kTA * (2 * sizeof(float) + 1);
 }
 
 // One CTA per tile of up to kTA queries of one bin.  The candidates' samples are read into shared memory (SoA
@@ -596,7 +597,7 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
   const float inv_lam = (float)(1.0 / p.lambda);
   const float lam = (float)p.lambda;
   const float dxs = (float)((p.h + p.mu) * 0x1p-24);  // rounding of a stored cell-local FP32 coordinate
-  const int budget = phase_a_chunks(p.n_max);
+  const int budget = a.chunks;
   float* s_u = sA + (size_t)kChunkF * budget;
   float* s_du = s_u + K * kTA;
   uint8_t* s_fl = reinterpret_cast<uint8_t*>(s_du + K * kTA);
@@ -1232,7 +1233,8 @@ __global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* 
 // Finally each thread reads its TMEM row, |V_row|^2, and V[f] = 1 - e^{-2 lambda d^2} |V_row|^2.
 
 constexpr int kTcM = 128;
-constexpr int kTcSmallN = 96;  // cells up to this size: 128 TMEM columns (four CTAs per SM)
+// cells up to the context's qt_tc_small (96 by default; a multiple of 16, at most 128) take 128 TMEM columns
+// (four CTAs per SM), the larger ones up to kTcMaxN 256
 constexpr int kTcStages = 3;
 constexpr uint32_t kTcStageA = 8192;  // A hi + lo: 2 K-quads x 128 rows x 16 B, twice
 
@@ -1910,6 +1912,63 @@ static CandCtx cand_ctx(ksdf_ctx* c) {
   return cc;
 }
 
+// ---- autotuning of the query tile shapes ----
+namespace {
+constexpr int kTuneChunks[3] = {64, 128, 256};
+constexpr int kTuneTcSmall[3] = {64, 96, 128};
+}  // namespace
+
+int query_tune_count() { return 9; }
+
+// Times every (phase A budget, phase B class split) pair on the caller's query batch -- each a full query of all
+// outputs run twice, the second timed with CUDA events on the context stream -- and keeps the fastest.
+ksdf_status autotune_query(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* sign, int* choice, double* ms) {
+  const int dim = c->p.dim;
+  KSDF_CUDA(c, ensure(c->ws[WS_A], sizeof(float) * (size_t)Q * (4 + dim) + sizeof(int32_t) * 2 * (size_t)Q + 64));
+  float* o = ptr<float>(c->ws[WS_A]);
+  float *sdf = o, *grad = o + Q, *vs = grad + (size_t)Q * dim, *vf = vs + Q;
+  int32_t* win = reinterpret_cast<int32_t*>(vf + Q);
+  uint32_t* fl = reinterpret_cast<uint32_t*>(win + Q);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KSDF_CUDA(c, cudaEventCreate(&e0));
+  KSDF_CUDA(c, cudaEventCreate(&e1));
+  const bool prof = c->prof;
+  c->prof = false;
+  int best = -1;
+  double best_ms = 0.0;
+  ksdf_status s = KSDF_OK;
+  for (int t = 0; t < query_tune_count() && s == KSDF_OK; ++t) {
+    c->qt_chunks = kTuneChunks[t / 3];
+    c->qt_tc_small = kTuneTcSmall[t % 3];
+    float tms = 0.f;
+    for (int rep = 0; rep < 2 && s == KSDF_OK; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, c->stream);
+      s = run_query(c, xq, false, Q, sign, KSDF_OUT_ALL, sdf, grad, vs, vf, nullptr, win, fl);
+      if (rep == 1) cudaEventRecord(e1, c->stream);
+    }
+    if (s != KSDF_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&tms, e0, e1);
+    if (e != cudaSuccess) {
+      s = cuda_err(c, e, "autotune_query timing");
+      break;
+    }
+    if (ms) ms[t] = tms;
+    if (best < 0 || tms < best_ms) {
+      best = t;
+      best_ms = tms;
+    }
+  }
+  c->prof = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) best = 4;  // the defaults
+  c->qt_chunks = kTuneChunks[best / 3];
+  c->qt_tc_small = kTuneTcSmall[best % 3];
+  if (choice) *choice = best;
+  return s;
+}
+
 ksdf_status wait_diagnostic(ksdf_ctx* c, uint32_t spins) {
   launch(k_wait_diag, 1, 64, 0, c->stream, spins, ptr<uint32_t>(c->status_word));
   KSDF_CUDA(c, cudaGetLastError());
@@ -1969,6 +2028,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   }
   const int64_t max_tiles_a = Q / kTA + bcap + 1;
   const int TBq = f64 ? kTB64 : kBItem;
+  const int tc_small = c->qt_tc_small;
   uint64_t* qkey = ptr<uint64_t>(c->ws[WS_QKEY]);
   int32_t* qbin = ptr<int32_t>(c->ws[WS_QBIN]);
   int32_t* qrank = ptr<int32_t>(c->ws[WS_QRANK]);
@@ -2058,7 +2118,8 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTA, smem));
     launch(kern, std::max(1, occ) * c->num_sms, kTA, smem, st, pa, static_cast<const double*>(xq), p);
   } else {
-    const size_t smem = phase_a_smem(p.K, p.n_max);
+    pa.chunks = phase_a_chunks(c->qt_chunks, p.n_max);
+    const size_t smem = phase_a_smem(p.K, pa.chunks);
     auto kern = p.kernel == KSDF_KERNEL_MATERN32 ? k_phaseA<true> : k_phaseA<false>;
     KSDF_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -2082,7 +2143,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
                                                        static_cast<float*>(var_grad), winner, flags);
   KSDF_CUDA(c, scan_i64(wcnt, woff, G, nullptr, c->ws[WS_SCAN], st));
   // mixed path: three tile lists by winner-cell size -- tensor-core tiles of kTcM queries for cells of at most
-  // kTcSmallN and kTcMaxN samples, SIMT tiles of kBItem for larger cells
+  // tc_small and kTcMaxN samples, SIMT tiles of kBItem for larger cells
   const int64_t tcap = Q / kTcM + G + 1;
   int4* tiles_b1 = tiles_b + tcap;
   int4* tiles_b2 = tiles_b1 + tcap;
@@ -2091,7 +2152,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     launch(k_ntiles, ceil_div(G, 256), 256, 0, st, wcnt, G, TBq, wnt, (const int64_t*)nullptr);
     KSDF_CUDA(c, scan_i64(wnt, wtoff, G, &totals[3], c->ws[WS_SCAN], st));
   } else {
-    launch(k_ntiles3, ceil_div(G, 256), 256, 0, st, wcnt, ptr<int32_t>(m.n), G, kTcSmallN, kTcMaxN, kTcM, kBItem, wnt,
+    launch(k_ntiles3, ceil_div(G, 256), 256, 0, st, wcnt, ptr<int32_t>(m.n), G, tc_small, kTcMaxN, kTcM, kBItem, wnt,
            nt1, nt2);
     KSDF_CUDA(c, scan_i64(wnt, wtoff, G, &totals[3], c->ws[WS_SCAN], st));
     KSDF_CUDA(c, scan_i64(nt1, toff1, G, &totals[4], c->ws[WS_SCAN], st));
@@ -2101,7 +2162,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   if (f64)
     launch(k_make_tiles, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, G, TBq, tiles_b, (const int64_t*)nullptr);
   else
-    launch(k_make_tiles3, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, toff1, toff2, ptr<int32_t>(m.n), kTcSmallN,
+    launch(k_make_tiles3, ceil_div(G, 256), 256, 0, st, wcnt, woff, wtoff, toff1, toff2, ptr<int32_t>(m.n), tc_small,
            kTcMaxN, G, kTcM, kBItem, tiles_b, tiles_b1, tiles_b2);
   prof_end(c, e0, "query.regroup");
   e0 = prof_begin(c);
@@ -2139,7 +2200,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
         pb, static_cast<const double*>(xq), p, static_cast<double*>(sdf), static_cast<double*>(grad),
         static_cast<double*>(var_sdf), static_cast<double*>(var_f), winner, flags);
   } else {
-    // tensor-core tiles: cells of at most kTcSmallN samples, then of at most kTcMaxN (one after the other, each
+    // tensor-core tiles: cells of at most tc_small samples, then of at most kTcMaxN (one after the other, each
     // with the whole GPU: the TMEM of an SM is 512 columns); cells beyond kTcMaxN on the SIMT kernel meanwhile
     const int maxn = std::max(m.max_n, 1);
     if (maxn > kTcMaxN) {
@@ -2159,8 +2220,8 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
              static_cast<float*>(var_f), winner, flags, smax);
     }
     for (int part = 0; part < 2; ++part) {
-      if (part == 1 && maxn <= kTcSmallN) break;
-      const int kcap = std::min(part == 0 ? kTcSmallN : kTcMaxN, maxn);
+      if (part == 1 && maxn <= tc_small) break;
+      const int kcap = std::min(part == 0 ? tc_small : kTcMaxN, maxn);
       uint32_t ncols = 32;
       while ((int)ncols < tc_np(kcap)) ncols <<= 1;
       const size_t smem = tc_smem_bytes(kcap);

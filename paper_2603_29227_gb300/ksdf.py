@@ -33,7 +33,8 @@ ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
                  "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math",
-                 "ksdf_save", "ksdf_load", "ksdf_wait_diagnostic", "ksdf_set_schedule", "ksdf_get_schedule")
+                 "ksdf_save", "ksdf_load", "ksdf_wait_diagnostic", "ksdf_set_schedule", "ksdf_get_schedule",
+                 "ksdf_autotune_query", "ksdf_autotune_query_configs")
 
 
 class KsdfError(RuntimeError):
@@ -87,6 +88,8 @@ def load(path: str = LIB_PATH):
         "ksdf_save": [P, ctypes.c_char_p],
         "ksdf_wait_diagnostic": [P, U32],
         "ksdf_set_schedule": [P, I64, ctypes.c_double],
+        "ksdf_autotune_query": [P, P, I64, P, ctypes.POINTER(ctypes.c_int), P],
+        "ksdf_autotune_query_configs": [],
         "ksdf_get_schedule": [P, P, P, P],
         "ksdf_load": [P, ctypes.c_char_p],
     }
@@ -187,6 +190,16 @@ def ksdf_autotune(h):
     ms = np.zeros(n)
     t = ctypes.c_int(-1)
     _check(h, load().ksdf_autotune(h, ctypes.byref(t), _ptr(ms)), "ksdf_autotune")
+    return int(t.value), ms
+
+
+def ksdf_autotune_query(h, xq, Q, sign=None):
+    """Time the query tile-shape pairs on this batch; returns (chosen index, times in ms)."""
+    n = load().ksdf_autotune_query_configs()
+    ms = np.zeros(n)
+    t = ctypes.c_int(-1)
+    _check(h, load().ksdf_autotune_query(h, _ptr(xq, np.float32), int(Q), _ptr(sign, np.int8), ctypes.byref(t),
+                                         _ptr(ms)), "ksdf_autotune_query")
     return int(t.value), ms
 
 
@@ -406,6 +419,11 @@ class KernelSDF:
         """Pick the fit's team-size table by timing the candidates on this model; returns (index, ms)."""
         self._stream()
         return ksdf_autotune(self.h)
+
+    def autotune_query(self, xq, sign=None):
+        """Pick the query's tile shapes by timing the candidates on this batch; returns (index, ms)."""
+        self._stream()
+        return ksdf_autotune_query(self.h, xq, int(xq.shape[0]), sign)
 
     def update(self, x_new, var=None, normals=None, S_new=None):
         """Append samples (their ids follow the model's) and refit the cells they touch (within the refit budget

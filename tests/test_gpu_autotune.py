@@ -47,3 +47,21 @@ def test_autotune_keeps_the_model():
     m.fit(_t(w.x), _t(w.var), _t(w.normals))
     for a, b in zip(before, m.fit_arrays()):
         assert np.array_equal(a, b)
+
+
+def test_query_autotune_keeps_the_outputs():
+    """The chosen query tile-shape pair gives the same outputs as the default one bit for bit (the per-query
+    arithmetic does not depend on the tiling), and the fastest is kept."""
+    w = scenes.workload("scale3d", n_samples=200000, grid=48)
+    m = ksdf.KernelSDF(w.params)
+    m.fit(_t(w.x), _t(w.var), _t(w.normals))
+    xq, sg = _t(w.xq), _t(w.sign)
+    with pytest.raises(ksdf.KsdfError):
+        ksdf.ksdf_autotune_query(m.h, xq, 0)
+    q0 = {k: v.cpu().numpy() for k, v in m.query(xq, sg).items() if v is not None}
+    best, ms = m.autotune_query(xq, sg)
+    n = ksdf.load().ksdf_autotune_query_configs()
+    assert 0 <= best < n and len(ms) == n and np.all(ms > 0) and ms[best] == ms.min()
+    q1 = {k: v.cpu().numpy() for k, v in m.query(xq, sg).items() if v is not None}
+    for k in q0:
+        assert np.array_equal(q0[k], q1[k]), k
