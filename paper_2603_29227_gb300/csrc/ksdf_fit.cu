@@ -342,11 +342,9 @@ struct CopyFitArgs {
   const int64_t *ots_off, *ochol_off, *olinv_off, *oltc_off;
   const double* ochol64;
   const float *olinv32, *oltc;
-  int64_t oltc_lo;
   const D4* omd4;
   double* chol64;
   float *linv32, *ltc;
-  int64_t ltc_lo;
   D4* md4;
   float4* mf4;
   int32_t* status;
@@ -365,10 +363,7 @@ __global__ void k_copy_fit(CopyFitArgs a) {
     for (int64_t e = threadIdx.x; e < lb; e += blockDim.x) dl[e] = sl[e];
     const float* st = a.oltc + a.oltc_off[o];
     float* dt = a.ltc + a.ltc_off[g];
-    for (int64_t e = threadIdx.x; e < tc; e += blockDim.x) {
-      dt[e] = st[e];
-      dt[a.ltc_lo + e] = st[a.oltc_lo + e];
-    }
+    for (int64_t e = threadIdx.x; e < tc; e += blockDim.x) dt[e] = st[e];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const double al = a.omd4[a.ots_off[o] + i].w;
       a.md4[a.ts_off[g] + i].w = al;
@@ -590,6 +585,118 @@ __host__ __device__ inline int64_t fit_smem_doubles(int np, bool smem_mat) {
   return 2 * ((int64_t)np + 1) + np + (smem_mat ? tri_sz(np + 1) : 0);
 }
 
+// Panel kb..ke-1 of the packed augmented matrix A (rows up to N) by one warp: per column the pivot (its
+// reciprocal square root kept in dinv; the diagonal keeps d_k), the column scaled, and the updates inside the
+// panel flattened over (row, column) pairs so that each warp instruction carries 32 of them.  Sets *fail on an
+// unusable pivot.
+__device__ __forceinline__ void fit_factor_panel(double* A, double* dinv, int N, int kb, int ke, int* fail) {
+  const int lane = threadIdx.x & 31;
+  for (int c = kb; c < ke; ++c) {
+    const double d = A[tri_sz(c) + c];
+    if (!pivot_ok(d)) {
+      if (lane == 0) *fail = 1;
+      break;
+    }
+    const double y = rsqrt_pivot(d);
+    if (lane == 0) dinv[c] = y;
+    for (int i = c + 1 + lane; i <= N; i += 32) A[tri_sz(i) + c] *= y;
+    __syncwarp();
+    const int nc = ke - 1 - c;
+    if (nc > 0) {
+      const unsigned mg = 0xFFFFFFFFu / (unsigned)nc + 1u;  // t / nc = umulhi(t, mg) for t < 2^29, nc > 1
+      const unsigned nt = (unsigned)(N - c) * (unsigned)nc;
+      for (unsigned t = lane; t < nt; t += 32) {
+        const unsigned q = nc == 1 ? t : __umulhi(t, mg);
+        const int i = c + 1 + (int)q, j = c + 1 + (int)(t - q * (unsigned)nc);
+        if (j <= i) A[tri_sz(i) + j] = fma(-A[tri_sz(i) + c], A[tri_sz(j) + c], A[tri_sz(i) + j]);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// The update of the 2 x 2 block of entries (i0, j0), (i0, j0+1), (i0+1, j0), (i0+1, j0+1) -- those with
+// j <= i, i <= N and j < cmax -- by the w factored columns kb .. kb+w-1: a_ij -= sum_k L_ik L_jk, k in order.
+__device__ __forceinline__ void fit_update_block(double* A, int N, int kb, int w, int i0, int j0, int cmax) {
+  const int i1 = i0 + 1, j1 = j0 + 1;
+  const bool vi1 = i1 <= N, vj1 = j1 < cmax, v01 = vj1 && j1 <= i0;
+  double* Ai0 = A + tri_sz(i0);
+  double* Ai1 = vi1 ? A + tri_sz(i1) : Ai0;
+  const double* Li0 = Ai0 + kb;
+  const double* Li1 = Ai1 + kb;
+  const double* Lj0 = A + tri_sz(j0) + kb;
+  const double* Lj1 = vj1 ? A + tri_sz(j1) + kb : Lj0;
+  double a00 = Ai0[j0];
+  double a01 = v01 ? Ai0[j1] : 0.0;
+  double a10 = vi1 ? Ai1[j0] : 0.0;
+  double a11 = (vi1 && vj1) ? Ai1[j1] : 0.0;
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    if (k < w) {
+      const double li0 = Li0[k], li1 = Li1[k], lj0 = Lj0[k], lj1 = Lj1[k];
+      a00 = fma(-li0, lj0, a00);
+      a01 = fma(-li0, lj1, a01);
+      a10 = fma(-li1, lj0, a10);
+      a11 = fma(-li1, lj1, a11);
+    }
+  }
+  Ai0[j0] = a00;
+  if (v01) Ai0[j1] = a01;
+  if (vi1) {
+    Ai1[j0] = a10;
+    if (vj1) Ai1[j1] = a11;
+  }
+}
+
+// Right-looking Cholesky of the augmented matrix in shared memory with a one-panel look-ahead (teams of
+// TEAM >= 64 threads).  Per panel kb..ke-1, once it is factored:
+//   1. the whole team updates the next panel's columns ke..ken-1 (rows ke..N) by it;
+//   2. warp 0 factors the next panel while the team updates the rest of the trailing triangle (rows and
+//      columns ken..N) by the current one, in chunks of 32 2 x 2 blocks taken from a shared counter, so that
+//      warp 0 joins in when its panel is done.
+template <int TEAM>
+__device__ void fit_lookahead(double* A, double* dinv, int N, int& s_fail, int& s_next) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int kb = 0, ke = min(kB, N);
+  if (warp == 0) fit_factor_panel(A, dinv, N, kb, ke, &s_fail);
+  __syncthreads();
+  while (!s_fail && ke < N) {
+    const int w = ke - kb;
+    const int ken = min(ke + kB, N);
+    // 1. the next panel's columns: 2 x 2 blocks (ke + 2I, ke + 2J), J < 4, J <= I
+    {
+      const int nI = (N + 2 - ke) >> 1;
+      for (int t = tid; t < 4 * nI; t += TEAM) {
+        const int I = t >> 2, J = t & 3;
+        const int i0 = ke + 2 * I, j0 = ke + 2 * J;
+        if (J <= I && j0 < ken) fit_update_block(A, N, kb, w, i0, j0, ken);
+      }
+    }
+    if (tid == 0) s_next = 0;
+    __syncthreads();
+    // 2. warp 0: the next panel; everyone: the trailing triangle beyond it
+    if (warp == 0) fit_factor_panel(A, dinv, N, ke, ken, &s_fail);
+    {
+      const int nbk = (N + 2 - ken) >> 1;  // 2-row blocks over rows ken..N
+      const int64_t nblk = tri_sz(nbk);
+      for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&s_next, 32);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if ((int64_t)base >= nblk) break;
+        const int64_t t = base + lane;
+        if (t < nblk) {
+          const int I = tri_row(t), J = (int)(t - tri_sz(I));
+          fit_update_block(A, N, kb, w, ken + 2 * I, ken + 2 * J, N + 1);
+        }
+      }
+    }
+    __syncthreads();
+    kb = ke;
+    ke = ken;
+  }
+}
+
 // The fit of one cell per iteration of a persistent team (TEAM threads; one warp for the small classes).
 // On GB300 an SM retires one FP64 warp instruction per ~20 cycles (one per ~68 per scheduler) whether 1 or
 // 32 lanes are active, so every step keeps its FP64 work in full warps:
@@ -605,7 +712,7 @@ template <int TEAM, bool GMAT>
 __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitArgs a, Params p) {
   constexpr int W = TEAM / 32;
   extern __shared__ __align__(16) double sm[];
-  __shared__ int s_cell, s_fail;
+  __shared__ int s_cell, s_fail, s_next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = a.np;
   double* cb = sm;
@@ -652,6 +759,13 @@ __global__ void __launch_bounds__(TEAM, TEAM == 32 ? 12 : 256 / TEAM) k_fit(FitA
     //    column scaling, updates inside the panel), then the team updates the trailing triangle (rows and
     //    columns ke..N, the augmented row included) in 2 x 2 register blocks over the panel depth.  The
     //    diagonal keeps the pivot d_k until the end (L_kk = d_k / sqrt(d_k) is applied in bulk).
+    //    Teams of two or more warps with the matrix in shared memory look one panel ahead: once a panel is
+    //    factored, the team first brings the next panel's columns up to date, then warp 0 factors that
+    //    panel while the other warps (and warp 0, when it is done) take the rest of the trailing update in
+    //    chunks of 32 blocks.  Every entry receives the same FMAs in the same order either way.
+    if (W > 1 && !GMAT) {
+      fit_lookahead<TEAM>(A, dinv, N, s_fail, s_next);
+    } else
     for (int kb = 0; kb < N; kb += kB) {
       const int ke = min(kb + kB, N);
       // the panel's element (row i >= kb, column kb <= c < ke): in the matrix itself, or (GMAT: the matrix
@@ -840,19 +954,12 @@ struct LinvArgs {
   const double* chol64;
   float* linv32;
   const int64_t* ltc_off;
-  float* ltc;       // hi image at ltc + ltc_off[g], lo image ltc_lo floats further
-  int64_t ltc_lo;
+  float* ltc;       // the cell's image at ltc + ltc_off[g]
   float* gscr;      // per-CTA global slot (largest class): linv_slot_floats(np, false)
   int64_t gstride;
   int np;
   int* counter;
 };
-
-__device__ __forceinline__ float tf32_rna_fit(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
 
 // float offset of group g's buffer (after the reciprocal diagonal and L) and the slot size
 __host__ __device__ inline int64_t linv_group_off(int np, int g) {
@@ -995,24 +1102,22 @@ __global__ void __launch_bounds__(32 * W) k_linv_small(LinvArgs a) {
           dst[1] = make_float4(v[4], v[5], v[6], v[7]);
         }
       }
-      // tensor-core images: quads of this group's columns, all Np rows, TF32 hi = rna(x), lo = rna(x - hi)
+      // tensor-core image: quads of this group's columns, all Np rows (FP32; the query splits it into TF32
+      // hi and lo parts in shared memory)
       if (N <= kTcMaxN) {
         const int np16 = tc_np(N);
         const int q1 = min(base + 32, tc_kp(N)) >> 2;
         float* img = a.ltc + a.ltc_off[g];
         for (int q = base >> 2; q < q1; ++q) {
           for (int i = lane; i < np16; i += 32) {
-            float hi[4], lo[4];
+            float v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int col = 4 * q + u;
-              const float v = (col <= i && i < N) ? Xt[(col - base) * xs + i] : 0.f;
-              hi[u] = tf32_rna_fit(v);
-              lo[u] = tf32_rna_fit(v - hi[u]);
+              v[u] = (col <= i && i < N) ? Xt[(col - base) * xs + i] : 0.f;
             }
             const int64_t o = ((int64_t)q * np16 + i) * 4;
-            *reinterpret_cast<float4*>(img + o) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<float4*>(img + a.ltc_lo + o) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<float4*>(img + o) = make_float4(v[0], v[1], v[2], v[3]);
           }
         }
       }
@@ -1126,17 +1231,13 @@ __global__ void __launch_bounds__(TEAM) k_linv(LinvArgs a) {
           dst[1] = make_float4(v[4], v[5], v[6], v[7]);
         }
       }
-      // the tensor-core images (column j of L^-1 is K index j of the B operand): all Np rows, zero padded,
-      // split into TF32 hi = rna(x) and lo = rna(x - hi)
+      // the tensor-core image (column j of L^-1 is K index j of the B operand): all Np rows, zero padded, FP32
       if (N <= kTcMaxN && j < tc_kp(N)) {
         const int np16 = tc_np(N);
         float* col = a.ltc + a.ltc_off[g] + (int64_t)(j >> 2) * np16 * 4 + (j & 3);
-        for (int i = 0; i < np16; ++i) {
-          const float v = (j < N && i < N && i >= j) ? (INPLACE ? xcol[tri_sz(i)] : xcol[(int64_t)i * 32]) : 0.f;
-          const float hi = tf32_rna_fit(v);
-          col[(int64_t)i * 4] = hi;
-          col[a.ltc_lo + (int64_t)i * 4] = tf32_rna_fit(v - hi);
-        }
+        for (int i = 0; i < np16; ++i)
+          col[(int64_t)i * 4] =
+              (j < N && i < N && i >= j) ? (INPLACE ? xcol[tri_sz(i)] : xcol[(int64_t)i * 32]) : 0.f;
       }
       if (INPLACE) __syncwarp();
     }
@@ -1344,7 +1445,7 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
   if (nrm) KSDF_CUDA(c, ensure(m.mnrm, sizeof(float4) * (M + 1)));
   KSDF_CUDA(c, ensure(m.chol64, sizeof(double) * (m.chol_total + 1)));
   KSDF_CUDA(c, ensure(m.linv32, sizeof(float) * (m.linv_total + 4)));
-  KSDF_CUDA(c, ensure(m.ltc, sizeof(float) * (2 * m.ltc_total + 4)));
+  KSDF_CUDA(c, ensure(m.ltc, sizeof(float) * (m.ltc_total + 4)));
   launch(k_gather_members, ceil_div(G * p.n_max, 256), 256, 0, st, ptr<uint64_t>(m.key), ptr<int32_t>(m.n),
          ptr<int64_t>(m.ts_off), ptr<int32_t>(m.mpad), G, p, x, var, nrm, ptr<int32_t>(m.mgid), ptr<D4>(m.md4),
          ptr<float4>(m.mf4), ptr<float>(m.mvar), nrm ? ptr<float4>(m.mnrm) : nullptr);
@@ -1491,7 +1592,6 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
       la.linv32 = ptr<float>(m.linv32);
       la.ltc_off = ptr<int64_t>(m.ltc_off);
       la.ltc = ptr<float>(m.ltc);
-      la.ltc_lo = m.ltc_total;
       la.gscr = nullptr;
       la.gstride = 0;
       la.np = f.np;
@@ -1537,12 +1637,10 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     ca.ochol64 = ptr<double>(o.chol64);
     ca.olinv32 = ptr<float>(o.linv32);
     ca.oltc = ptr<float>(o.ltc);
-    ca.oltc_lo = o.ltc_total;
     ca.omd4 = ptr<D4>(o.md4);
     ca.chol64 = ptr<double>(m.chol64);
     ca.linv32 = ptr<float>(m.linv32);
     ca.ltc = ptr<float>(m.ltc);
-    ca.ltc_lo = m.ltc_total;
     ca.md4 = ptr<D4>(m.md4);
     ca.mf4 = ptr<float4>(m.mf4);
     ca.status = ptr<int32_t>(m.status);

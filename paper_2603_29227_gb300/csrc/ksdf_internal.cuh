@@ -156,8 +156,8 @@ struct Model {
   DevBuf ltc_off;  // int64 (G+1): offsets into ltc
   DevBuf ltc;      // float: for cells with N <= kTcMaxN, L^-1 as the K-major B operand of the variance
                    // contraction, rows (N dim) padded to Np = 16 ceil(N/16), columns (K dim) to Kp = 8 ceil(N/8),
-                   // in K-quads: element (j, i) at (i / 4) Np 4 + j 4 + i % 4 (zero outside the lower triangle);
-                   // TF32 hi = rna(x) at ltc_off, lo = rna(x - hi) ltc_total floats further
+                   // in K-quads: element (j, i) at (i / 4) Np 4 + j 4 + i % 4 (zero outside the lower triangle),
+                   // FP32 (split into TF32 hi and lo parts in shared memory by the query)
   // bricks of 2^kBrickShift cells per axis over the cell bounding box, each listing its OK cells (the
   // coarse level of the candidate search for query bins far from the nearest cells); nbricks = 0 when the
   // box is too sparse for a dense brick grid

@@ -54,15 +54,15 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// bounded wait of one thread (no barrier)
+__device__ inline bool mbar_wait_one(uint64_t* bar, uint32_t parity) {
+  for (unsigned it = 0; it < (kWaitLimit >> 4); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
 // bounded wait; returns false (for every thread of the CTA) if any thread gave up
 __device__ inline bool mbar_wait_all(uint64_t* bar, uint32_t parity) {
-  bool done = false;
-  for (unsigned it = 0; it < (kWaitLimit >> 4); ++it)
-    if (mbar_try_wait(bar, parity)) {
-      done = true;
-      break;
-    }
-  return !__syncthreads_or(!done);
+  return !__syncthreads_or(!mbar_wait_one(bar, parity));
 }
 
 __device__ inline float ex2(float x) {
@@ -1223,19 +1223,27 @@ __global__ void __launch_bounds__(kBQ* kBW) k_phaseB(PhaseBArgs a, const float* 
 // ---------------------------------------------------------------------------------------------
 // Q6 with the variance contraction on the tensor cores (cells of N <= kTcMaxN samples).  A tile is up to
 // 128 queries of one winner cell, one thread per query (= row m of the MMA and TMEM lane m).  The thread
-// computes the nearest sample, then walks the samples in steps of 8: k'_i, grad f', the softmin sums, and
-// the k' values of the step written as the A operand (TF32 hi = rna(k'), lo = rna(k' - hi)).  The B operand
-// of the step -- 8 columns of L^-1, i.e. rows j of L^-1 restricted to the step's K range -- arrives by a TMA
-// bulk copy from the cell's tensor-core image and is split into hi/lo in place.  One thread issues
+// finds the nearest sample, then walks the samples in steps of 8 -- k'_i, grad f', the softmin sums, two
+// samples per packed FP32x2 instruction -- and writes the step's k' values as the A operand (TF32 hi = rna(k'),
+// lo = rna(k' - hi)).  The B operand of the step -- 8 columns of L^-1, i.e. rows j of L^-1 restricted to the
+// step's K range -- arrives by a TMA bulk copy from the cell's FP32 tensor-core image, and the producer warp
+// splits it in place (hi = rna(x), lo = rna(x - hi) beside it).  One thread issues
 //   D[:, n0:Np] (+)= A_hi B_hi + A_hi B_lo + A_lo B_hi   (tcgen05.mma kind::tf32, M = 128, K = 8),
-// with n0 = 16 floor(8 c / 16) skipping the zero upper blocks of L^-1; D = K' L^-T lives in TMEM.  Three
-// stages of A/B buffers, a TMA issued one step ahead, per-stage mbarriers for copy and MMA completion.
-// Finally each thread reads its TMEM row, |V_row|^2, and V[f] = 1 - e^{-2 lambda d^2} |V_row|^2.
+// with n0 = 16 floor(8 c / 16) skipping the zero upper blocks of L^-1; D = K' L^-T lives in TMEM.  A ring of
+// three A stages and a ring of three B stages (the copy for step c + 2 is issued with the MMA of step c), each
+// with its mbarriers.  Finally each thread reads its TMEM row, |V_row|^2, and
+// V[f] = 1 - e^{-2 lambda d^2} |V_row|^2.  While the query warps finish a tile, the producer warp fetches the
+// next one into the other of two tile buffers: its samples by TMA, their variances, the padding, and each
+// query's index, cell-local position, flags and u.  A warp whose 32 rows hold no query of the tile zeroes its
+// A rows once and sits the tile out.
 
 constexpr int kTcM = 128;
+constexpr int kTcThreads = kTcM + 32;  // a query thread per row, one producer warp
+constexpr float kTcPad = 1e7f;        // cell-local coordinate of the padding samples (n .. Kp): far from every query
 // cells up to the context's qt_tc_small (96 by default; a multiple of 16, at most 128) take 128 TMEM columns
 // (four CTAs per SM), the larger ones up to kTcMaxN 256
-constexpr int kTcStages = 3;
+constexpr int kTcStages = 3;   // A operand ring
+constexpr int kTcBStages = 3;  // B operand ring: a step's B copy is issued two steps ahead
 constexpr uint32_t kTcStageA = 8192;  // A hi + lo: 2 K-quads x 128 rows x 16 B, twice
 
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -1267,12 +1275,6 @@ __device__ inline float tf32_rna(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
-// bounded wait of one thread (no barrier)
-__device__ inline bool mbar_wait_one(uint64_t* bar, uint32_t parity) {
-  for (unsigned it = 0; it < (kWaitLimit >> 4); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 // sum of squares of 16 consecutive TMEM columns of this thread's lane
 __device__ inline float tmem_sumsq16(uint32_t taddr) {
   uint32_t r[16];
@@ -1293,45 +1295,59 @@ struct TcArgs {
   const int64_t* n_tiles;
   int* counter;
   const int64_t* ltc_off;
-  const float* ltc;  // TF32 hi images; the lo images ltc_lo floats further
-  int64_t ltc_lo;
+  const float* ltc;  // FP32 images of L^-1 (K-major B operand)
 };
 
-// shared memory of one CTA: [kcap] samples (float4) | [kcap] var | stages of A (hi, lo) and B (hi, lo)
-__host__ __device__ inline size_t tc_stage_bytes(int npm) { return kTcStageA + 64u * (size_t)npm; }
-__host__ __device__ inline size_t tc_head_bytes(int kcap) { return ((size_t)20 * kcap + 1023) & ~(size_t)1023; }
+// shared memory of one CTA: two tile buffers, each [kcap] samples (float4), [kcap] var, [kTcM] query records
+// (cell-local position and u as a float4, index and flags as a uint2) | A ring (hi, lo) | B ring (hi, lo)
+__host__ __device__ inline size_t tc_bstage_bytes(int npm) { return 64u * (size_t)npm; }
+__host__ __device__ inline size_t tc_head_bytes(int kcap) {
+  return ((size_t)40 * kcap + (size_t)2 * kTcM * 24 + 1023) & ~(size_t)1023;
+}
 __host__ __device__ inline size_t tc_smem_bytes(int kcap) {
-  return tc_head_bytes(kcap) + kTcStages * tc_stage_bytes(tc_np(kcap));
+  return tc_head_bytes(kcap) + kTcStages * (size_t)kTcStageA + kTcBStages * tc_bstage_bytes(tc_np(kcap));
 }
 
 __device__ inline void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+__device__ inline void mbar_arrive_n(uint64_t* bar, uint32_t n) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(n) : "memory");
+}
 
 // Warp roles: warps 0..3 hold the tile's 128 queries (one per thread, = row m of the MMA and TMEM lane m) and
-// write the A operand step by step, signalling bar_full; warp 4 (lane 0) is the producer: it streams the B
-// chunks by TMA and issues the MMAs once a step's A is written and its B has arrived.  The query threads wait
-// only to reuse a stage (its MMA done) and for the tile's last MMA.
+// write the A operand step by step, signalling bar_full; warp 4 is the producer: it fetches tiles, streams the B
+// chunks by TMA, splits them, and (lane 0) issues the MMAs once a step's A is written.  The query threads wait
+// only to reuse an A stage (its MMA done) and for the tile's last MMA.
 template <bool MATERN>
-__global__ void __launch_bounds__(kTcM + 32) k_phaseB_tc(PhaseBArgs a, TcArgs t, const float* xq, Params p,
-                                                         float* sdf, float* grad, float* var_sdf, float* var_f,
-                                                         int32_t* winner, uint32_t* flags, int kcap, uint32_t ncols) {
+__global__ void __launch_bounds__(kTcThreads, 4) k_phaseB_tc(PhaseBArgs a, TcArgs t, const float* xq, Params p,
+                                                             float* sdf, float* grad, float* var_sdf, float* var_f,
+                                                             int32_t* winner, uint32_t* flags, int kcap,
+                                                             uint32_t ncols) {
   extern __shared__ __align__(1024) unsigned char smb[];
-  __shared__ __align__(8) uint64_t bar_x, bar_tma[kTcStages], bar_mma[kTcStages], bar_full[kTcStages];
+  // bar_x: a sample buffer's copy; bar_full / bar_mma: A ring (operands written, MMA done); bar_tma / bar_bfree:
+  // B ring (copy landed, MMA done)
+  __shared__ __align__(8) uint64_t bar_x[2], bar_full[kTcStages], bar_mma[kTcStages], bar_tma[kTcBStages],
+      bar_bfree[kTcBStages];
   __shared__ uint32_t s_tmem;
-  __shared__ int4 s_tile;
-  __shared__ float s_bh[3], s_bl[3];
+  __shared__ int4 s_tile[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool producer = warp == kTcM / 32;
   const int npm = tc_np(kcap);
-  float4* s_x = reinterpret_cast<float4*>(smb);
-  float* s_var = reinterpret_cast<float*>(s_x + kcap);
+  float4* s_xb = reinterpret_cast<float4*>(smb);             // [2][kcap]
+  float4* s_qpb = s_xb + 2 * kcap;                           // [2][kTcM]: cell-local query position, u
+  uint2* s_qib = reinterpret_cast<uint2*>(s_qpb + 2 * kTcM);  // [2][kTcM]: query index, flags
+  float* s_varb = reinterpret_cast<float*>(s_qib + 2 * kTcM);  // [2][kcap]
   unsigned char* stg = smb + tc_head_bytes(kcap);
-  const uint32_t stage_bytes = (uint32_t)tc_stage_bytes(npm);
+  unsigned char* ringb = stg + kTcStages * kTcStageA;
+  const uint32_t bstage_bytes = (uint32_t)tc_bstage_bytes(npm);
   if (tid == 0) {
-    mbar_init(&bar_x, 1);
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int b = 0; b < 2; ++b) mbar_init(&bar_x[b], 1);
+    for (int s = 0; s < kTcBStages; ++s) {
       mbar_init(&bar_tma[s], 1);
+      mbar_init(&bar_bfree[s], 1);
+    }
+    for (int s = 0; s < kTcStages; ++s) {
       mbar_init(&bar_mma[s], 1);
       mbar_init(&bar_full[s], kTcM);
     }
@@ -1350,186 +1366,338 @@ __global__ void __launch_bounds__(kTcM + 32) k_phaseB_tc(PhaseBArgs a, TcArgs t,
   const float c1 = (float)p.lambda * kLog2e;
   const float as = (float)p.alpha_s;
   const float c2 = as * kLog2e;
+  const float lam = (float)p.lambda;
   const int64_t ntiles = *t.n_tiles;
-  uint32_t gstep = 0, tile_iter = 0;  // global step counter (stage = gstep % 3, use = gstep / 3)
-  bool fail = false;
-  for (;;) {
-    if (tid == 0) {
+  // The producer warp takes the next tile and stages it into tile buffer b in three parts, so that the latency of
+  // its loads overlaps the current tile's steps: begin -- the tile index, the samples by TMA (lane 0), the
+  // variances and the padding samples n .. Kp - 1 (far away, zero weight and variance, so that every step takes
+  // 8 whole samples), the query indices into registers; middle -- the loads that depend on the query indices;
+  // end -- the query records into shared memory.
+  constexpr int kRK = kTcM / 32;
+  int4 f_tl = make_int4(-1, 0, 0, 0);
+  float f_x[kRK][3], f_u[kRK];
+  int f_q[kRK];
+  uint32_t f_fl[kRK];
+  auto fetch_begin = [&](int b) {
+    if (lane == 0) {
       const int ti = atomicAdd(t.counter, 1);
-      s_tile = ti < ntiles ? t.tiles[ti] : make_int4(-1, 0, 0, 0);
+      f_tl = make_int4(-1, 0, 0, 0);
       if (ti < ntiles) {
-        const int g = s_tile.x, n = a.cell_n[g];
-        mbar_expect_tx(&bar_x, (uint32_t)n * 16u);
-        bulk_g2s(s_x, a.mf4 + a.ts_off[g], (uint32_t)n * 16u, &bar_x);
-        int cc[3];
-        unpack_key(a.cell_key[g], cc[0], cc[1], cc[2]);
-        for (int j = 0; j < 3; ++j) base_split(p.o[j], cc[j], p.h, s_bh[j], s_bl[j]);
+        f_tl = t.tiles[ti];
+        const int n = a.cell_n[f_tl.x];
+        mbar_expect_tx(&bar_x[b], (uint32_t)n * 16u);
+        bulk_g2s(s_xb + b * kcap, a.mf4 + a.ts_off[f_tl.x], (uint32_t)n * 16u, &bar_x[b]);
+      }
+      s_tile[b] = f_tl;
+    }
+    f_tl.x = __shfl_sync(0xFFFFFFFFu, f_tl.x, 0);
+    f_tl.y = __shfl_sync(0xFFFFFFFFu, f_tl.y, 0);
+    f_tl.z = __shfl_sync(0xFFFFFFFFu, f_tl.z, 0);
+    if (f_tl.x >= 0) {
+      const int n = a.cell_n[f_tl.x];
+      const int64_t m0 = a.ts_off[f_tl.x];
+#pragma unroll
+      for (int k = 0; k < kRK; ++k) f_q[k] = lane + 32 * k < f_tl.z ? a.sorted_w[f_tl.y + lane + 32 * k] : 0;
+      float* sv = s_varb + b * kcap;
+      for (int i = lane; i < n; i += 32) sv[i] = a.mvar[m0 + i];  // not 16-byte aligned in HBM: plain loads
+      for (int i = n + lane; i < tc_kp(n); i += 32) {
+        s_xb[b * kcap + i] = make_float4(kTcPad, kTcPad, kTcPad, 0.f);
+        sv[i] = 0.f;
       }
     }
-    __syncthreads();
-    const int4 tile = s_tile;
+  };
+  auto fetch_mid = [&]() {
+    if (f_tl.x < 0) return;
+#pragma unroll
+    for (int k = 0; k < kRK; ++k) {
+      f_x[k][0] = f_x[k][1] = f_x[k][2] = 0.f;
+      f_u[k] = 0.f;
+      f_fl[k] = 0;
+      if (lane + 32 * k < f_tl.z) {
+        const int q = f_q[k];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          if (j < p.dim) f_x[k][j] = xq[(int64_t)q * p.dim + j];
+        f_u[k] = a.qu[q];
+        f_fl[k] = a.qflag[q];
+      }
+    }
+  };
+  auto fetch_end = [&](int b) {
+    if (f_tl.x < 0) return;
+    float bh[3], bl[3];
+    int cc[3];
+    unpack_key(a.cell_key[f_tl.x], cc[0], cc[1], cc[2]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) base_split(p.o[j], cc[j], p.h, bh[j], bl[j]);
+#pragma unroll
+    for (int k = 0; k < kRK; ++k) {
+      const int r = lane + 32 * k;
+      if (r < f_tl.z) {
+        float ql[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          if (j < p.dim) ql[j] = local32(f_x[k][j], bh[j], bl[j]);
+        s_qpb[b * kTcM + r] = make_float4(ql[0], ql[1], ql[2], f_u[k]);
+        s_qib[b * kTcM + r] = make_uint2((uint32_t)f_q[k], f_fl[k]);
+      }
+    }
+  };
+  if (producer) {
+    fetch_begin(0);
+    fetch_mid();
+    fetch_end(0);
+  }
+  __syncthreads();
+  uint32_t gstep = 0;  // global step counter: A stage gstep % 3, B stage gstep % 4
+  bool fail = false;
+  for (int it = 0;; ++it) {
+    const int buf = it & 1;
+    const int4 tile = s_tile[buf];
     if (tile.x < 0) break;
+    const float4* s_x = s_xb + buf * kcap;
+    const float* s_var = s_varb + buf * kcap;
     const int g = tile.x;
     const int n = a.cell_n[g];
     const int64_t m0 = a.ts_off[g];
     const int np16 = tc_np(n), nsteps = tc_kp(n) >> 3;
     if (producer) {
-      if (lane == 0) {
-        const float* img = t.ltc + t.ltc_off[g];
-        // B chunk of step c (hi and lo images) into the stage of global step gs: both K-quads, rows n0 .. np16-1,
-        // once the stage's previous MMA has finished reading it
-        auto issue_b = [&](int c, uint32_t gs) {
-          const int s = (int)(gs % kTcStages);
-          if (gs >= (uint32_t)kTcStages && !mbar_wait_one(&bar_mma[s], ((gs / kTcStages) - 1) & 1)) fail = true;
-          const int n0 = (c >> 1) << 4;
-          const uint32_t bytes = (uint32_t)(np16 - n0) * 16u;
-          unsigned char* bb = stg + (size_t)s * stage_bytes + kTcStageA;
-          mbar_expect_tx(&bar_tma[s], 4u * bytes);
-          for (int part = 0; part < 2; ++part)
-            for (int qd = 0; qd < 2; ++qd)
-              bulk_g2s(bb + (size_t)part * npm * 32 + (size_t)qd * npm * 16 + (size_t)n0 * 16,
-                       img + (part ? t.ltc_lo : 0) + ((int64_t)(2 * c + qd) * np16 + n0) * 4, bytes, &bar_tma[s]);
-        };
-        for (int c = 0; c < nsteps && c < kTcStages; ++c) issue_b(c, gstep + c);
-        for (int c = 0; c < nsteps && !fail; ++c) {
-          const uint32_t gs = gstep + c;
-          const int s = (int)(gs % kTcStages);
-          const uint32_t ph = (gs / kTcStages) & 1;
-          if (!mbar_wait_one(&bar_full[s], ph) || !mbar_wait_one(&bar_tma[s], ph)) {
-            fail = true;
-            break;
-          }
-          tc_fence_after();
-          const int n0 = (c >> 1) << 4, rows = np16 - n0;
-          unsigned char* sa = stg + (size_t)s * stage_bytes;
-          const uint32_t idesc = umma_idesc_tf32(rows, kTcM);
-          const uint32_t a_hi = smem_u32(sa), a_lo = a_hi + 4096;
-          const uint32_t b_hi = smem_u32(sa + kTcStageA) + (uint32_t)n0 * 16, b_lo = b_hi + (uint32_t)npm * 32;
-          const uint32_t d = tmem + (uint32_t)n0;
-          const uint32_t lbo_b = (uint32_t)npm * 16;
-          umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, c > 0 ? 1u : 0u);
-          umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_lo, lbo_b, 128), idesc, 1u);
-          umma_tf32(d, umma_desc(a_lo, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, 1u);
-          umma_commit(&bar_mma[s]);
-          if (c + kTcStages < nsteps) issue_b(c + kTcStages, gs + kTcStages);
-        }
-      }
-      __syncwarp();
-    } else {
-      for (int i = tid; i < n; i += kTcM) s_var[i] = a.mvar[m0 + i];  // not 16-byte aligned: plain loads
-      const bool live = tid < tile.z;
-      const int q = a.sorted_w[tile.y + (live ? tid : 0)];
-      float ql[3] = {0.f, 0.f, 0.f};
-      for (int j = 0; j < p.dim; ++j) ql[j] = local32(xq[(int64_t)q * p.dim + j], s_bh[j], s_bl[j]);
-      if (!mbar_wait_one(&bar_x, tile_iter & 1)) fail = true;
-      asm volatile("bar.sync 1, %0;" ::"r"(kTcM) : "memory");  // var staged by all query threads
-      // pass 1: nearest sample (first minimum in id order)
-      float m = INFINITY;
-      int nn = 0;
-      for (int i = 0; i < n; ++i) {
-        const float4 v = s_x[i];
-        const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (r2 < m) {
-          m = r2;
-          nn = i;
-        }
-      }
-      const float zmin = sqrtf(m);
-      // exponents relative to the nearest sample (excess_sq)
-      const float4 xn = s_x[nn];
-      const float wx = 2.f * (ql[0] - xn.x), wy = 2.f * (ql[1] - xn.y), wz = 2.f * (ql[2] - xn.z);
-      float G0 = 0.f, G1 = 0.f, G2 = 0.f, W = 0.f, HY = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
-      for (int c = 0; c < nsteps; ++c) {
+      const float* img = t.ltc + t.ltc_off[g];
+      // (lane 0) B chunk of step c (FP32) into the B slot of global step gs: both K-quads, rows n0 .. np16-1, once
+      // the slot's previous MMA (global step gs - kTcBStages) has finished reading it
+      auto issue_b = [&](int c, uint32_t gs) {
+        const int s = (int)(gs % kTcBStages);
+        if (gs >= (uint32_t)kTcBStages && !mbar_wait_one(&bar_bfree[s], ((gs / kTcBStages) - 1) & 1)) fail = true;
+        const int n0 = (c >> 1) << 4;
+        const uint32_t bytes = (uint32_t)(np16 - n0) * 16u;
+        unsigned char* bb = ringb + (size_t)s * bstage_bytes;
+        mbar_expect_tx(&bar_tma[s], 2u * bytes);
+        for (int qd = 0; qd < 2; ++qd)
+          bulk_g2s(bb + (size_t)qd * npm * 16 + (size_t)n0 * 16, img + ((int64_t)(2 * c + qd) * np16 + n0) * 4,
+                   bytes, &bar_tma[s]);
+      };
+      if (lane == 0)
+        for (int c = 0; c < nsteps && c < kTcBStages - 1; ++c) issue_b(c, gstep + c);
+      fetch_begin(buf ^ 1);  // the next tile, into the other buffer (its last readers finished before the
+                             // previous barrier)
+      for (int c = 0; c < nsteps && !fail; ++c) {
         const uint32_t gs = gstep + c;
-        const int s = (int)(gs % kTcStages);
-        unsigned char* sa = stg + (size_t)s * stage_bytes;
-        // the stage's previous MMA has finished reading A
-        if (gs >= (uint32_t)kTcStages && !mbar_wait_one(&bar_mma[s], ((gs / kTcStages) - 1) & 1)) fail = true;
-        // k' of samples 8c .. 8c+7 for this thread's query, with the gradient and softmin sums
-        float kv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = 8 * c + u;
-          float kp = 0.f;
-          if (i < n) {
-            const float4 v = s_x[i];
-            const float dx = ql[0] - v.x, dy = ql[1] - v.y, dz = ql[2] - v.z;
-            const float e = excess_sq(v.x, v.y, v.z, xn.x, xn.y, xn.z, wx, wy, wz);
-            const float r2 = m + e;
-            const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-            float wg, y;
-            kernel_terms<MATERN>(e, z, zmin, c1, (float)p.lambda, kp, wg, y);
-            const float ak = v.w * wg;
-            G0 = fmaf(ak, dx, G0);
-            G1 = fmaf(ak, dy, G1);
-            G2 = fmaf(ak, dz, G2);
-            const float wt = ex2(-c2 * y);
-            W += wt;
-            HY = fmaf(wt, y, HY);
-            const float tw = wt * wt * s_var[i];
-            T0 += tw;
-            T1 = fmaf(tw, y, T1);
-            T2 = fmaf(tw * y, y, T2);
+        const int s = (int)(gs % kTcStages), sb = (int)(gs % kTcBStages);
+        const int n0 = (c >> 1) << 4, rows = np16 - n0;
+        // the step's B has landed: split it in place, TF32 hi = rna(x), lo = rna(x - hi) npm * 32 bytes further
+        if (!mbar_wait_one(&bar_tma[sb], (gs / kTcBStages) & 1)) fail = true;
+        {
+          unsigned char* bb = ringb + (size_t)sb * bstage_bytes + (size_t)n0 * 16;
+          for (int u = lane; u < 2 * rows; u += 32) {
+            const int qd = u >= rows ? 1 : 0;
+            float4* hp = reinterpret_cast<float4*>(bb + (size_t)qd * npm * 16 + (size_t)(u - qd * rows) * 16);
+            const float4 v = *hp;
+            const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+            *hp = h;
+            *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(hp) + (size_t)npm * 32) =
+                make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
           }
-          kv[u] = live ? kp : 0.f;
-        }
-        // A operand (row tid): K-quad q at q * 2048 + tid * 16; lo part 4096 bytes further
-#pragma unroll
-        for (int qd = 0; qd < 2; ++qd) {
-          float hv[4], lv[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            hv[e] = tf32_rna(kv[4 * qd + e]);
-            lv[e] = tf32_rna(kv[4 * qd + e] - hv[e]);
-          }
-          *reinterpret_cast<float4*>(sa + qd * 2048 + tid * 16) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-          *reinterpret_cast<float4*>(sa + 4096 + qd * 2048 + tid * 16) = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
         fence_proxy_async();
-        mbar_arrive(&bar_full[s]);
-      }
-      // the tile's last MMA (and so all of them) has finished
-      {
-        const uint32_t gl = gstep + nsteps - 1;
-        if (!mbar_wait_one(&bar_mma[gl % kTcStages], (gl / kTcStages) & 1)) fail = true;
-      }
-      tc_fence_after();
-      float VS = 0.f;
-      {
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < np16; c0 += 16) VS += tmem_sumsq16(ta + (uint32_t)c0);
-      }
-      if (live && !fail) {
-        const float hy = HY / W;
-        const float B = fmaf(as, hy, 1.f);
-        const float vs = fmaxf((B * B * T0 - 2.f * B * as * T1 + as * as * T2) / (W * W), 0.f);
-        const float vf = fmaxf(1.f - ex2(-2.f * c1 * (MATERN ? zmin : m)) * VS, 0.f);
-        float sg = 1.f;
-        if (a.sign) {
-          sg = a.sign[q] < 0 ? -1.f : 1.f;
-        } else if (p.sign_mode == 1 && a.has_normals) {
-          const float4 v = s_x[nn];
-          const float4 nv = a.mnrm[m0 + nn];
-          sg = (nv.x * (ql[0] - v.x) + nv.y * (ql[1] - v.y) + nv.z * (ql[2] - v.z)) >= 0.f ? 1.f : -1.f;
+        __syncwarp();
+        if (lane == 0) {
+          // A written by the query threads
+          if (!mbar_wait_one(&bar_full[s], (gs / kTcStages) & 1)) fail = true;
+          if (!fail) {
+            tc_fence_after();
+            unsigned char* sa = stg + (size_t)s * kTcStageA;
+            const uint32_t idesc = umma_idesc_tf32(rows, kTcM);
+            const uint32_t a_hi = smem_u32(sa), a_lo = a_hi + 4096;
+            const uint32_t b_hi = smem_u32(ringb + (size_t)sb * bstage_bytes) + (uint32_t)n0 * 16;
+            const uint32_t b_lo = b_hi + (uint32_t)npm * 32;
+            const uint32_t d = tmem + (uint32_t)n0;
+            const uint32_t lbo_b = (uint32_t)npm * 16;
+            umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, c > 0 ? 1u : 0u);
+            umma_tf32(d, umma_desc(a_hi, 2048, 128), umma_desc(b_lo, lbo_b, 128), idesc, 1u);
+            umma_tf32(d, umma_desc(a_lo, 2048, 128), umma_desc(b_hi, lbo_b, 128), idesc, 1u);
+            umma_commit(&bar_mma[s]);
+            umma_commit(&bar_bfree[sb]);
+            if (c + kTcBStages - 1 < nsteps) issue_b(c + kTcBStages - 1, gs + kTcBStages - 1);
+          }
         }
-        uint32_t fl = a.qflag[q];
-        const float gn = sqrtf(G0 * G0 + G1 * G1 + G2 * G2);
-        if (a.mask & KSDF_OUT_SDF) sdf[q] = sg * a.qu[q];
-        if (a.mask & KSDF_OUT_GRAD) {
-          const float gv[3] = {G0, G1, G2};
-          const float ig = gn > 0.f ? sg / gn : 0.f;
-          for (int j = 0; j < p.dim; ++j) grad[(int64_t)q * p.dim + j] = gv[j] * ig;
+        fail = __any_sync(0xFFFFFFFFu, fail);
+        if (c == 0) fetch_mid();
+      }
+      if (!fail) fetch_end(buf ^ 1);
+    } else {
+      const bool live = tid < tile.z;
+      const bool wlive = warp * 32 < tile.z;  // the warp holds at least one query (uniform over the warp)
+      const int nlw = (tile.z + 31) >> 5;     // live warps: 0 .. nlw - 1
+      const int r = live ? tid : 0;           // a dead row of a live warp computes row 0's query, unused
+      const float4 qp = s_qpb[buf * kTcM + r];
+      const uint2 qi = s_qib[buf * kTcM + r];
+      const int q = (int)qi.x;
+      const float ql[3] = {qp.x, qp.y, qp.z};
+      const float qu = qp.w;
+      uint32_t fl = qi.y;
+      float m = INFINITY;
+      int nn = 0;
+      if (wlive) {
+        if (!mbar_wait_one(&bar_x[buf], (it >> 1) & 1)) fail = true;
+        // pass 1: nearest sample (first minimum in id order), two samples per packed instruction (sample n, when
+        // n is odd, is a far padding sample)
+        const unsigned long long QX = f2pack(ql[0], ql[0]), QY = f2pack(ql[1], ql[1]), QZ = f2pack(ql[2], ql[2]);
+        for (int i = 0; i < n; i += 2) {
+          const float4 v0 = s_x[i], v1 = s_x[i + 1];
+          const unsigned long long dx = f2sub(QX, f2pack(v0.x, v1.x)), dy = f2sub(QY, f2pack(v0.y, v1.y));
+          const unsigned long long dz = f2sub(QZ, f2pack(v0.z, v1.z));
+          const float2 r2 = f2unpack(f2fma(dx, dx, f2fma(dy, dy, f2mul(dz, dz))));
+          if (r2.x < m) {
+            m = r2.x;
+            nn = i;
+          }
+          if (r2.y < m) {
+            m = r2.y;
+            nn = i + 1;
+          }
         }
-        if (!(gn > 0.f)) fl |= KSDF_FLAG_ZERO_GRAD;
-        if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
-        if (a.mask & KSDF_OUT_VAR_F) var_f[q] = vf;
-        if (a.mask & KSDF_OUT_WINNER) winner[q] = g;
-        if (a.mask & KSDF_OUT_FLAGS) flags[q] = fl;
+      } else {
+        // no query in these rows: zero A (hi and lo) in every stage once -- no MMA of the previous tile reads
+        // them any more (every thread waited for its last MMA), and none of this tile's is issued before the
+        // live warps arrive, after the barrier below -- then sit the tile out
+        for (int s = 0; s < kTcStages; ++s) {
+          unsigned char* sa = stg + (size_t)s * kTcStageA;
+#pragma unroll
+          for (int qd = 0; qd < 2; ++qd) {
+            *reinterpret_cast<float4*>(sa + qd * 2048 + tid * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(sa + 4096 + qd * 2048 + tid * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+        fence_proxy_async();
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(kTcM) : "memory");  // the dead warps' zero rows written
+      if (wlive) {
+        const float zmin = sqrtf(m);
+        // exponents relative to the nearest sample (excess_sq); the per-query constants of the packed loop
+        const float4 xn = s_x[nn];
+        const float wx = 2.f * (ql[0] - xn.x), wy = 2.f * (ql[1] - xn.y), wz = 2.f * (ql[2] - xn.z);
+        const unsigned long long QX = f2pack(ql[0], ql[0]), QY = f2pack(ql[1], ql[1]), QZ = f2pack(ql[2], ql[2]);
+        const unsigned long long NX = f2pack(xn.x, xn.x), NY = f2pack(xn.y, xn.y), NZ = f2pack(xn.z, xn.z);
+        const unsigned long long WX = f2pack(wx, wx), WY = f2pack(wy, wy), WZ = f2pack(wz, wz);
+        const unsigned long long M2 = f2pack(m, m), ZM = f2pack(zmin, zmin);
+        const unsigned long long NC1 = f2pack(-c1, -c1), NC2 = f2pack(-c2, -c2), LAM = f2pack(lam, lam);
+        const unsigned long long ONE = f2pack(1.f, 1.f);
+        unsigned long long G0 = 0ull, G1 = 0ull, G2 = 0ull, W = 0ull, HY = 0ull, T0 = 0ull, T1 = 0ull, T2 = 0ull;
+        for (int c = 0; c < nsteps; ++c) {
+          const uint32_t gs = gstep + c;
+          const int s = (int)(gs % kTcStages);
+          unsigned char* sa = stg + (size_t)s * kTcStageA;
+          // the stage's previous MMA has finished reading A
+          if (gs >= (uint32_t)kTcStages && !mbar_wait_one(&bar_mma[s], ((gs / kTcStages) - 1) & 1)) fail = true;
+          float kv[8];
+          // samples 8c .. 8c+7 in pairs: k'_i, grad f', the softmin sums
+#pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            const int i = 8 * c + u;
+            const float4 v0 = s_x[i], v1 = s_x[i + 1];
+            const float2 vr = *reinterpret_cast<const float2*>(s_var + i);
+            const unsigned long long X = f2pack(v0.x, v1.x), Y = f2pack(v0.y, v1.y), Z = f2pack(v0.z, v1.z);
+            const unsigned long long dx = f2sub(QX, X), dy = f2sub(QY, Y), dz = f2sub(QZ, Z);
+            // excess_sq, both samples
+            const unsigned long long ax = f2sub(X, NX), ay = f2sub(Y, NY), az = f2sub(Z, NZ);
+            const unsigned long long e = f2fma(ax, f2sub(ax, WX), f2fma(ay, f2sub(ay, WY), f2mul(az, f2sub(az, WZ))));
+            const unsigned long long r2 = f2add(M2, e);
+            const float2 r2s = f2unpack(r2);
+            const unsigned long long z =
+                f2mul(r2, f2pack(rsqrtf(fmaxf(r2s.x, 1e-30f)), rsqrtf(fmaxf(r2s.y, 1e-30f))));
+            unsigned long long kp, wg, y;
+            if (MATERN) {
+              // y = max(e, 0) / (z + zmin), wg = 2^{-c1 y}, k' = (1 + lambda z) wg
+              const float2 es = f2unpack(e), den = f2unpack(f2add(z, ZM));
+              y = f2pack(den.x > 0.f ? fmaxf(es.x, 0.f) * __frcp_rn(den.x) : 0.f,
+                         den.y > 0.f ? fmaxf(es.y, 0.f) * __frcp_rn(den.y) : 0.f);
+              const float2 ey = f2unpack(f2mul(NC1, y));
+              wg = f2pack(ex2(ey.x), ex2(ey.y));
+              kp = f2mul(f2fma(LAM, z, ONE), wg);
+            } else {
+              const float2 ee = f2unpack(f2mul(NC1, e));
+              kp = f2pack(ex2(ee.x), ex2(ee.y));
+              wg = kp;
+              const float2 ys = f2unpack(f2sub(z, ZM));
+              y = f2pack(fmaxf(ys.x, 0.f), fmaxf(ys.y, 0.f));
+            }
+            const unsigned long long ak = f2mul(f2pack(v0.w, v1.w), wg);
+            G0 = f2fma(ak, dx, G0);
+            G1 = f2fma(ak, dy, G1);
+            G2 = f2fma(ak, dz, G2);
+            const float2 cy = f2unpack(f2mul(NC2, y));
+            // softmin weights of the padding samples masked
+            const unsigned long long wt = f2pack(i < n ? ex2(cy.x) : 0.f, i + 1 < n ? ex2(cy.y) : 0.f);
+            const float2 k2 = f2unpack(kp);
+            W = f2add(W, wt);
+            HY = f2fma(wt, y, HY);
+            const unsigned long long tw = f2mul(f2mul(wt, wt), f2pack(vr.x, vr.y));
+            T0 = f2add(T0, tw);
+            T1 = f2fma(tw, y, T1);
+            T2 = f2fma(f2mul(tw, y), y, T2);
+            kv[u] = live ? k2.x : 0.f;
+            kv[u + 1] = live ? k2.y : 0.f;
+          }
+          // A operand (row tid): K-quad q at q * 2048 + tid * 16; lo part 4096 bytes further
+#pragma unroll
+          for (int qd = 0; qd < 2; ++qd) {
+            float hv[4], lv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              hv[e] = tf32_rna(kv[4 * qd + e]);
+              lv[e] = tf32_rna(kv[4 * qd + e] - hv[e]);
+            }
+            *reinterpret_cast<float4*>(sa + qd * 2048 + tid * 16) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+            *reinterpret_cast<float4*>(sa + 4096 + qd * 2048 + tid * 16) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+          }
+          fence_proxy_async();
+          mbar_arrive(&bar_full[s]);
+          if (tid == 0 && nlw < kTcM / 32) mbar_arrive_n(&bar_full[s], 32u * (kTcM / 32 - nlw));  // the dead warps'
+        }
+        // the tile's last MMA (and so all of them) has finished
+        {
+          const uint32_t gl = gstep + nsteps - 1;
+          if (!mbar_wait_one(&bar_mma[gl % kTcStages], (gl / kTcStages) & 1)) fail = true;
+        }
+        tc_fence_after();
+        float VS = 0.f;
+        {
+          const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+          for (int c0 = 0; c0 < np16; c0 += 16) VS += tmem_sumsq16(ta + (uint32_t)c0);
+        }
+        const float2 g0 = f2unpack(G0), g1 = f2unpack(G1), g2 = f2unpack(G2), w2 = f2unpack(W), hy2 = f2unpack(HY);
+        const float2 t0 = f2unpack(T0), t1 = f2unpack(T1), t2 = f2unpack(T2);
+        const float gx = g0.x + g0.y, gy = g1.x + g1.y, gz = g2.x + g2.y, Ws = w2.x + w2.y;
+        const float T0s = t0.x + t0.y, T1s = t1.x + t1.y, T2s = t2.x + t2.y;
+        if (live && !fail) {
+          const float hy = (hy2.x + hy2.y) / Ws;
+          const float B = fmaf(as, hy, 1.f);
+          const float vs = fmaxf((B * B * T0s - 2.f * B * as * T1s + as * as * T2s) / (Ws * Ws), 0.f);
+          const float vf = fmaxf(1.f - ex2(-2.f * c1 * (MATERN ? zmin : m)) * VS, 0.f);
+          float sg = 1.f;
+          if (a.sign) {
+            sg = a.sign[q] < 0 ? -1.f : 1.f;
+          } else if (p.sign_mode == 1 && a.has_normals) {
+            const float4 nv = a.mnrm[m0 + nn];
+            sg = (nv.x * (ql[0] - xn.x) + nv.y * (ql[1] - xn.y) + nv.z * (ql[2] - xn.z)) >= 0.f ? 1.f : -1.f;
+          }
+          const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
+          if (a.mask & KSDF_OUT_SDF) sdf[q] = sg * qu;
+          if (a.mask & KSDF_OUT_GRAD) {
+            const float ig = gn > 0.f ? sg / gn : 0.f;
+            grad[(int64_t)q * p.dim + 0] = gx * ig;
+            grad[(int64_t)q * p.dim + 1] = gy * ig;
+            if (p.dim == 3) grad[(int64_t)q * p.dim + 2] = gz * ig;
+          }
+          if (!(gn > 0.f)) fl |= KSDF_FLAG_ZERO_GRAD;
+          if (a.mask & KSDF_OUT_VAR_SDF) var_sdf[q] = vs;
+          if (a.mask & KSDF_OUT_VAR_F) var_f[q] = vf;
+          if (a.mask & KSDF_OUT_WINNER) winner[q] = g;
+          if (a.mask & KSDF_OUT_FLAGS) flags[q] = fl;
+        }
       }
     }
     gstep += (uint32_t)nsteps;
-    ++tile_iter;
     tc_fence_before();
     if (__syncthreads_or(fail)) {
       fail = true;
@@ -2221,7 +2389,8 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
     }
     for (int part = 0; part < 2; ++part) {
       if (part == 1 && maxn <= tc_small) break;
-      const int kcap = std::min(part == 0 ? tc_small : kTcMaxN, maxn);
+      // whole steps of 8 samples are staged (padding samples up to Kp)
+      const int kcap = tc_kp(std::min(part == 0 ? tc_small : kTcMaxN, maxn));
       uint32_t ncols = 32;
       while ((int)ncols < tc_np(kcap)) ncols <<= 1;
       const size_t smem = tc_smem_bytes(kcap);
@@ -2239,8 +2408,7 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
       ta.counter = &counters[1 + part];
       ta.ltc_off = ptr<int64_t>(m.ltc_off);
       ta.ltc = ptr<float>(m.ltc);
-      ta.ltc_lo = m.ltc_total;
-      launch(ktc, occ * c->num_sms, kTcM + 32, smem, st, pb, ta, static_cast<const float*>(xq), p,
+      launch(ktc, occ * c->num_sms, kTcThreads, smem, st, pb, ta, static_cast<const float*>(xq), p,
              static_cast<float*>(sdf), static_cast<float*>(grad), static_cast<float*>(var_sdf),
              static_cast<float*>(var_f), winner, flags, kcap, ncols);
     }
