@@ -322,8 +322,8 @@ def recorded_traffic():
     if not os.path.exists(TRAFFIC_FILE):
         return None
     txt = open(TRAFFIC_FILE).read()
-    m = re.search(r"source_digest\s+(\w+)", txt)
-    t = re.search(r"query_adjoint_dram_bytes\s+([0-9.eE+]+)", txt)
+    m = re.search(r"^source_digest\s+([0-9a-f]+)\s*$", txt, re.M)
+    t = re.search(r"^query_adjoint_dram_bytes\s+([0-9.eE+]+)\s*$", txt, re.M)
     if not m or not t or m.group(1) != source_digest():
         return None
     return float(t.group(1))

@@ -2,6 +2,12 @@
 for an external profiler:
 
     python -m paper_2603_29227_gb300.profile_step <workload> [steps] [--autotune]
+    python -m paper_2603_29227_gb300.profile_step --summarize <ncu launch list .csv>
+
+The second form turns an ncu CSV launch list of such a run (gpu__time_duration.sum, optionally
+dram__bytes_read.sum and dram__bytes_write.sum) into a per-kernel table of its last step, each kernel assigned to
+the stage that launched it (fit, query, adjoint), with the DRAM bytes of the query and adjoint kernels and a digest
+of their sources.
 
 The library must have been built (``__graft_entry__.build()``).  Each step runs ksdf_fit, ksdf_query and
 ksdf_query_backward once, eagerly, on the library's stream; the first step doubles as the warm-up.  The script
@@ -57,5 +63,73 @@ def main(argv):
     print("ok", name, Q)
 
 
+def source_digest():
+    """Digest of the query and adjoint kernel sources (the same one bench.py checks before it reports traffic)."""
+    import hashlib
+    import os
+
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    hs = hashlib.sha256()
+    for f in ("ksdf_query.cu", "ksdf_backward.cu", "ksdf_internal.cuh"):
+        with open(os.path.join(here, f), "rb") as fh:
+            hs.update(fh.read())
+    return hs.hexdigest()[:16]
+
+
+def summarize(path):
+    import csv
+    from collections import OrderedDict
+
+    rows, hdr = [], None
+    with open(path) as fh:
+        for r in csv.reader(fh):
+            if r and r[0] == "ID":
+                hdr = r
+                continue
+            if hdr and len(r) == len(hdr):
+                rows.append(dict(zip(hdr, r)))
+    launches = OrderedDict()
+    for r in rows:
+        d = launches.setdefault(int(r["ID"]), {"name": r["Kernel Name"].split("(")[0].replace("void ", "")})
+        d[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+    seq = [launches[i] for i in sorted(launches)]
+    for d in seq:
+        d["name"] = d["name"].replace("ksdf::<unnamed>::", "").replace("ksdf::", "")
+    starts = [k for k, d in enumerate(seq) if d["name"] == "k_bin_samples"]
+    if not starts:
+        raise SystemExit("no fit launch (k_bin_samples) in %s" % path)
+    step = seq[starts[-1]:]
+    stage, per = "fit", OrderedDict()
+    for d in step:
+        n = d["name"]
+        if n.startswith("k_q_bin"):
+            stage = "query"
+        elif n.startswith("k_bw_count"):
+            stage = "adjoint"
+        st = stage if n.startswith("k_") else "other (PyTorch)"
+        a = per.setdefault((st, n), {"n": 0, "ns": 0.0, "rd": 0.0, "wr": 0.0})
+        a["n"] += 1
+        a["ns"] += d.get("gpu__time_duration.sum", 0.0)
+        a["rd"] += d.get("dram__bytes_read.sum", 0.0)
+        a["wr"] += d.get("dram__bytes_write.sum", 0.0)
+    tot = sum(a["ns"] for a in per.values())
+    print("| stage | kernel | launches | ms (serialised) | share | DRAM read GB | DRAM write GB |")
+    print("|---|---|---|---|---|---|---|")
+    for (st, n), a in sorted(per.items(), key=lambda kv: -kv[1]["ns"]):
+        print("| %s | %s | %d | %.3f | %.1f%% | %.3f | %.3f |" % (st, n, a["n"], a["ns"] / 1e6, 100 * a["ns"] / tot,
+                                                            a["rd"] / 1e9, a["wr"] / 1e9))
+    for st in ("fit", "query", "adjoint"):
+        sel = [a for (s2, _), a in per.items() if s2 == st]
+        print("\n%s: %d launches, %.3f ms, DRAM %.3f GB" % (st, sum(a["n"] for a in sel), sum(a["ns"] for a in sel) / 1e6,
+                                                          sum(a["rd"] + a["wr"] for a in sel) / 1e9))
+    qa = sum(a["rd"] + a["wr"] for (s2, _), a in per.items() if s2 in ("query", "adjoint"))
+    print("\nstep total %.3f ms over %d launches" % (tot / 1e6, sum(a["n"] for a in per.values())))
+    print("source_digest %s" % source_digest())
+    print("query_adjoint_dram_bytes %d" % int(qa))
+
+
 if __name__ == "__main__":
-    main(sys.argv[1:])
+    if len(sys.argv) > 2 and sys.argv[1] == "--summarize":
+        summarize(sys.argv[2])
+    else:
+        main(sys.argv[1:])
