@@ -1,6 +1,7 @@
 // ksdf_abi.cu -- the extern "C" entry points of libksdf.so (declared and documented in include/ksdf.h):
 // argument checks, staging of host arrays through device workspaces, and dispatch to the fit, query and
 // backward pipelines.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -206,6 +207,10 @@ ksdf_status ksdf_create(const ksdf_params* params, void* stream, ksdf_ctx** out)
   c->p.dim = params->dim;
   for (int j = 0; j < 3; ++j) c->p.o[j] = j < params->dim ? params->origin[j] : 0.0;
   c->p.h = params->cell;
+  {
+    int e = 0;
+    c->p.rh = std::frexp(params->cell, &e) == 0.5 ? std::ldexp(1.0, 1 - e) : 0.0;  // cell = 2^(e-1)
+  }
   c->p.mu = params->margin;
   c->p.n_max = params->n_max;
   c->p.K = params->k_cand;

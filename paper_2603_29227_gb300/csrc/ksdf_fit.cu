@@ -29,7 +29,7 @@ __global__ void k_bin_samples(const double* x, const float* var, int64_t S, Para
   int c[3] = {0, 0, 0};
   bool ok = true, live = i < S;
   if (live) {
-    for (int j = 0; j < p.dim; ++j) ok &= bin_coord(x[i * p.dim + j], p.o[j], p.h, c[j]);
+    for (int j = 0; j < p.dim; ++j) ok &= bin_coord(x[i * p.dim + j], p.o[j], p.h, p.rh, c[j]);
     if (var) {
       float v = var[i];
       ok &= (v >= 0.f) && isfinite(v);
@@ -1783,7 +1783,7 @@ __global__ void k_bin_keys(const double* x, int64_t n, Params p, uint64_t* keys,
   if (i >= n) return;
   int c[3] = {0, 0, 0};
   bool ok = true;
-  for (int j = 0; j < p.dim; ++j) ok &= bin_coord(x[i * p.dim + j], p.o[j], p.h, c[j]);
+  for (int j = 0; j < p.dim; ++j) ok &= bin_coord(x[i * p.dim + j], p.o[j], p.h, p.rh, c[j]);
   if (!ok) atomicOr(st, ST_NONFINITE);
   keys[i] = ok ? pack_key(c[0], c[1], c[2]) : kEmptyKey;
 }

@@ -37,9 +37,12 @@ __host__ __device__ inline void unpack_key(uint64_t k, int& cx, int& cy, int& cz
   cz = (int)((int64_t)((k >> 42) & 0x1FFFFF) - kBias);
 }
 
-// bin of one coordinate: floor((x - o) / h) in IEEE binary64 with no contraction; false if out of range
-__device__ inline bool bin_coord(double x, double o, double h, int& c) {
-  double t = __ddiv_rn(__dsub_rn(x, o), h);
+// bin of one coordinate: floor((x - o) / h) in IEEE binary64 with no contraction; false if out of range.
+// rh = 1/h when h is a power of two, else 0: then (x - o) / h and (x - o) * rh are the same real number, so
+// their correctly rounded results agree bit for bit and the multiplication stands in for the division.
+__device__ inline bool bin_coord(double x, double o, double h, double rh, int& c) {
+  const double d = __dsub_rn(x, o);
+  double t = rh != 0.0 ? __dmul_rn(d, rh) : __ddiv_rn(d, h);
   double f = floor(t);
   if (!(f >= -(double)kBias && f < (double)kBias)) return false;
   c = (int)f;
@@ -58,6 +61,38 @@ __device__ inline void base_split(double o, int c, double h, float& hi, float& l
   lo = (float)(b - (double)hi);
 }
 __device__ __forceinline__ float local32(float x, float hi, float lo) { return __fsub_rn(__fsub_rn(x, hi), lo); }
+
+// packed FP32x2 arithmetic (two lanes of one thread per instruction): a u64 holds (lo, hi) floats
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f2unpack(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
 
 // The kernel exponent of the scaled posterior mean, lambda (r_i^2 - d^2) with r_i = |q - x_i| and d = |q - x_n|
 // for the GP's nearest sample x_n (App. D scaling), in FP32 cell-local coordinates.  Subtracting the two
@@ -109,6 +144,7 @@ struct Params {
   int dim;
   double o[3];
   double h;
+  double rh;  // 1 / h when h is a power of two (exact), else 0
   double mu;
   int n_max;
   int K;

@@ -80,7 +80,7 @@ __global__ void k_q_bin(const T* xq, int64_t Q, Params p, uint64_t* qkey, uint64
   if (q >= Q) return;
   int c[3] = {0, 0, 0};
   bool ok = true;
-  for (int j = 0; j < p.dim; ++j) ok &= bin_coord((double)xq[q * p.dim + j], p.o[j], p.h, c[j]);
+  for (int j = 0; j < p.dim; ++j) ok &= bin_coord((double)xq[q * p.dim + j], p.o[j], p.h, p.rh, c[j]);
   if (!ok) {
     atomicOr(st, ST_NONFINITE);
     qkey[q] = kEmptyKey;
@@ -529,38 +529,6 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-// packed FP32x2 arithmetic (two lanes of one thread per instruction): a u64 holds (lo, hi) floats
-__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 f2unpack(unsigned long long v) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
 }
 
 // Phase A shared memory, per tile: candidates' samples as chunks of 8 in SoA form -- one chunk is 40 floats,

@@ -48,12 +48,20 @@ def gpu_query(m, xq, sign, f64=False):
 WORKLOADS = {
     "plane2d": dict(name="plane2d"),
     "room3d_small": dict(name="room3d", n_samples=20000, n_queries=30011),
+    # a cell edge that is not a power of two and an origin off the grid: binning by division (a power-of-two
+    # edge bins by the equivalent exact multiplication)
+    "room3d_cell03": dict(name="room3d", n_samples=20000, n_queries=20011,
+                          params=dict(cell=0.3, origin=(-0.1, 0.05, -0.02))),
 }
 
 
 @pytest.fixture(scope="module", params=list(WORKLOADS))
 def case(request):
-    w = scenes.workload(**WORKLOADS[request.param])
+    spec = dict(WORKLOADS[request.param])
+    over = spec.pop("params", None)
+    w = scenes.workload(**spec)
+    if over:
+        w.params = dict(w.params, **over)
     ref = oracle.Model(w.params, w.x, w.var, w.normals)
     gm = gpu_model(w)
     return request.param, w, ref, gm
