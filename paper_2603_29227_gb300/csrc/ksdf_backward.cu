@@ -382,16 +382,19 @@ __device__ void linv_solve32(const float* Lb, int n, const float* rhs, float* y,
 }
 
 constexpr int kBwCellThreads = 64;  // two warps per cell: ~70-row cells keep most lanes busy, 32 cells per SM
+constexpr int kBwCellSmallN = 128;  // the small-cell launch: shared memory for at most this many samples
 
 template <bool MATERN>
 __global__ void __launch_bounds__(kBwCellThreads) k_bw_cell(const int64_t* qcnt, int64_t G, const int64_t* ts_off,
                                                  const int32_t* cell_n, const int64_t* chol_off, const double* chol64,
                                                  const int64_t* linv_off, const float* linv32, const float4* mf4,
-                                                 const int32_t* mgid, const double* abar, Params p, float* d_x) {
+                                                 const int32_t* mgid, const double* abar, Params p, float* d_x,
+                                                 int nlo, int nhi) {
   extern __shared__ double sh[];  // [n] alpha_bar, [n] t, [n] b0 (double), then floats: rhs, y, b
   for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
     if (qcnt[g] == 0) continue;
     const int n = cell_n[g];
+    if (n < nlo || n > nhi) continue;  // another launch's size class
     const int64_t m0 = ts_off[g];
     const double* L = chol64 + chol_off[g];
     const float* Lb = linv32 + linv_off[g];
@@ -533,15 +536,25 @@ ksdf_status run_backward(ksdf_ctx* c, const float* xq, int64_t Q, const int8_t* 
   launch(kq, std::max(1, occ) * c->num_sms, kTQ, smem, st, a, xq, p);
   prof_end(c, e0, "backward.query");
   e0 = prof_begin(c);
-  const size_t smem2 = sizeof(double) * 3 * p.n_max + sizeof(float) * 3 * p.n_max;
+  // two size classes, so that the many small cells run with shared memory for their own size (more CTAs per SM
+  // to hide the factors' load latency); the larger cells beside them on an auxiliary stream
   auto kc = matern ? k_bw_cell<true> : k_bw_cell<false>;
-  KSDF_CUDA(c, cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-  int occ2 = 0;
-  KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kc, kBwCellThreads, smem2));
-  const unsigned grid2 = (unsigned)std::min<int64_t>(G, (int64_t)std::max(1, occ2) * c->num_sms);
-  launch(kc, std::max(1u, grid2), kBwCellThreads, smem2, st, cnt, G, ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n),
-         ptr<int64_t>(m.chol_off), ptr<double>(m.chol64), ptr<int64_t>(m.linv_off), ptr<float>(m.linv32),
-         ptr<float4>(m.mf4), ptr<int32_t>(m.mgid), abar, p, d_x);
+  const int maxn = std::max(m.max_n, 1), nsplit = std::min(maxn, kBwCellSmallN);
+  const bool two = maxn > nsplit;
+  if (two) KSDF_CUDA(c, fork_streams(c));
+  for (int part = 0; part < (two ? 2 : 1); ++part) {
+    const int nlo = part == 0 ? 0 : nsplit + 1, nhi = part == 0 ? nsplit : maxn;
+    const size_t smem2 = (sizeof(double) + sizeof(float)) * 3 * (size_t)nhi;
+    KSDF_CUDA(c, cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    int occ2 = 0;
+    KSDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kc, kBwCellThreads, smem2));
+    const unsigned grid2 = (unsigned)std::min<int64_t>(G, (int64_t)std::max(1, occ2) * c->num_sms);
+    launch(kc, std::max(1u, grid2), kBwCellThreads, smem2, part == 0 ? st : c->aux[0], cnt, G,
+           ptr<int64_t>(m.ts_off), ptr<int32_t>(m.n), ptr<int64_t>(m.chol_off), ptr<double>(m.chol64),
+           ptr<int64_t>(m.linv_off), ptr<float>(m.linv32), ptr<float4>(m.mf4), ptr<int32_t>(m.mgid), abar, p, d_x,
+           nlo, nhi);
+  }
+  if (two) KSDF_CUDA(c, join_streams(c));
   KSDF_CUDA(c, cudaGetLastError());
   prof_end(c, e0, "backward.cell");
   prof_end(c, e_b, "backward");
