@@ -543,8 +543,9 @@ __host__ __device__ inline size_t phase_a_smem(int K, int chunks) {
 }
 
 // One CTA per tile of up to kTA queries of one bin.  The candidates' samples are read into shared memory (SoA
-// chunks); the warps then pull tasks (candidate k, block of 32 queries) and for a task each lane evaluates one
-// query on candidate k over its samples, eight per step with packed FP32x2 arithmetic:
+// chunks); the warps then pull tasks (candidate k, block of 16 queries), two at a time (one per half-warp), and
+// for a task each lane evaluates one query on candidate k over its samples, eight per step with packed FP32x2
+// arithmetic:
 //   r_i^2 = |q - x_i|^2, the running minimum m = d^2 (App. D), rescaled sums
 //   f' = sum_i alpha_i 2^{c1 (m - r_i^2)} (Kahan-compensated across steps) and sum_i |alpha_i| 2^{c1 (m - r_i^2)},
 //   u = sqrt(-log f' / lambda + m) (kernel table) with its error bound (u_error_bound).
@@ -602,7 +603,7 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
     }
     __syncthreads();
     const int nc = s_nc;
-    const int nqb = (tile.z + 31) >> 5;
+    const int nqb = (tile.z + 15) >> 4;  // blocks of 16 queries: a warp takes two tasks, one per half
     for (int k0 = 0; k0 < nc;) {
       // a round: candidates k0 .. k1-1 whose chunks fit the budget (at least one)
       if (tid == 0) {
@@ -638,11 +639,15 @@ __global__ void __launch_bounds__(kTA) k_phaseA(PhaseAArgs a, const float* xq, P
       const int ntask = (k1 - k0) * nqb;
       for (;;) {
         int task = 0;
-        if (lane == 0) task = atomicAdd(&s_task, 1);
+        if (lane == 0) task = atomicAdd(&s_task, 2);
         task = __shfl_sync(0xffffffffu, task, 0);
         if (task >= ntask) break;
-        const int k = k0 + task / nqb;
-        const int qi = (task % nqb) * 32 + lane;
+        // the second half of the warp takes the next task (when there is none it repeats the first with no
+        // query: its results are not stored)
+        const bool hv = task + (lane >> 4) < ntask;
+        const int tk = hv ? task + (lane >> 4) : task;
+        const int k = k0 + tk / nqb;
+        const int qi = hv ? (tk % nqb) * 16 + (lane & 15) : tile.z;
         const int qs = qi < tile.z ? qi : 0;
         const float qx = s_ql[qs][0] + s_off[k][0], qy = s_ql[qs][1] + s_off[k][1], qz = s_ql[qs][2] + s_off[k][2];
         const unsigned long long QX = f2pack(qx, qx), QY = f2pack(qy, qy), QZ = f2pack(qz, qz);
