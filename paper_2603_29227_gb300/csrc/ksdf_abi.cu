@@ -107,10 +107,17 @@ cudaError_t fork_streams(ksdf_ctx* c) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
     for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_mid[i], cudaEventDisableTiming);
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i)
+      e = cudaStreamCreateWithPriority(&c->aux_hi[i], cudaStreamNonBlocking, greatest);
+    for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&c->ev_join_hi[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
   }
   e = cudaEventRecord(c->ev_fork, c->stream);
   for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->aux[i], c->ev_fork, 0);
+  for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->aux_hi[i], c->ev_fork, 0);
   return e;
 }
 
@@ -119,6 +126,8 @@ cudaError_t join_streams(ksdf_ctx* c) {
   for (int i = 0; i < ksdf_ctx::kNumAux && e == cudaSuccess; ++i) {
     e = cudaEventRecord(c->ev_join[i], c->aux[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join[i], 0);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join_hi[i], c->aux_hi[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join_hi[i], 0);
   }
   return e;
 }
@@ -256,6 +265,8 @@ ksdf_status ksdf_destroy(ksdf_ctx* c) {
     if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
     if (c->ev_mid[i]) cudaEventDestroy(c->ev_mid[i]);
+    if (c->aux_hi[i]) cudaStreamDestroy(c->aux_hi[i]);
+    if (c->ev_join_hi[i]) cudaEventDestroy(c->ev_join_hi[i]);
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;

@@ -1576,9 +1576,12 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
     }
     KSDF_CUDA(c, le);
     KSDF_CUDA(c, cudaEventRecord(c->ev_mid[si], s));
-    // L^{-1} in FP32 of the same cells, behind their factorisation on the same stream: its FP32 / integer
-    // work overlaps the FP64 factorisation of the other classes
+    // L^{-1} in FP32 of the same cells, behind their factorisation, on a high-priority stream: its blocks take
+    // the SM resources this class's factorisation frees ahead of the pending blocks of the other classes'
+    // factorisations, so that its FP32 work overlaps their FP64 work instead of trailing it
     {
+      const cudaStream_t sh = c->aux_hi[si];
+      KSDF_CUDA(c, cudaStreamWaitEvent(sh, c->ev_mid[si], 0));
       LinvArgs la;
       la.order = order;
       la.first = f.first;
@@ -1597,16 +1600,16 @@ ksdf_status fit_model(ksdf_ctx* c, const double* x, const float* var, const floa
       la.np = f.np;
       if (f.np <= 96) {
         le = launch_persistent(c, k_linv_small<1>, 32, la, sizeof(float) * (size_t)linv_small_floats(f.np, 1), false,
-                               s);
+                               sh);
       } else if (f.np <= kTcMaxN) {
         le = launch_persistent(c, k_linv_small<2>, 64, la, sizeof(float) * (size_t)linv_small_floats(f.np, 2), false,
-                               s);
+                               sh);
       } else {
         la.gstride = (linv_slot_floats(f.np, false) + 3) & ~3LL;
         const int64_t slots = std::min<int64_t>(f.count, c->num_sms);
         KSDF_CUDA(c, ensure(c->ws[WS_LINVSCR], sizeof(float) * (size_t)(la.gstride * slots + 4)));
         la.gscr = ptr<float>(c->ws[WS_LINVSCR]);
-        le = launch_persistent(c, k_linv<512, false, true>, 512, la, 0, true, s);
+        le = launch_persistent(c, k_linv<512, false, true>, 512, la, 0, true, sh);
       }
       KSDF_CUDA(c, le);
     }

@@ -254,6 +254,10 @@ struct ksdf_ctx {
   static constexpr int kNumAux = 8;
   cudaStream_t aux[kNumAux] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kNumAux] = {}, ev_mid[kNumAux] = {};  // ev_mid: a stage boundary inside a fork
+  // high-priority auxiliary streams: work queued there is dispatched ahead of the pending blocks of kernels on
+  // the other streams as soon as SM resources free up
+  cudaStream_t aux_hi[kNumAux] = {};
+  cudaEvent_t ev_join_hi[kNumAux] = {};
 };
 
 namespace ksdf {
