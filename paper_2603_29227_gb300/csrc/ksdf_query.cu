@@ -175,6 +175,42 @@ __global__ void k_make_tiles(const int64_t* cnt, const int64_t* off, const int64
     tiles[tile_off[i] + t] = make_int4((int)i, (int)(off[i] + t * T), (int)(c - t * T < T ? c - t * T : T), 0);
 }
 
+// Phase A's tiles in a coarse spatial order of their bins, so that the bins processed at the same time share
+// candidate cells (their samples then come from L2): a counting sort of the occupied bins by a 16-bit key of
+// their 4 x 4 x 4-bin block ((cz/4) mod 16, (cy/4) mod 64, (cx/4) mod 64, lexicographic; wrap-around only
+// coarsens the order), bins of one block in any order.
+constexpr int kCoarseBuckets = 1 << 16;
+__device__ inline uint32_t bin_coarse_key(uint64_t k) {
+  const uint32_t x = (uint32_t)(k & 0x1FFFFF) >> 2, y = (uint32_t)((k >> 21) & 0x1FFFFF) >> 2;
+  const uint32_t z = (uint32_t)((k >> 42) & 0x1FFFFF) >> 2;
+  return ((z & 15u) << 12) | ((y & 63u) << 6) | (x & 63u);
+}
+__global__ void k_bin_coarse(const uint64_t* bin_key, const int64_t* n_dev, int32_t* coarse, int32_t* rank,
+                             int64_t* hist) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= *n_dev) return;
+  const uint32_t c = bin_coarse_key(bin_key[b]);
+  coarse[b] = (int32_t)c;
+  rank[b] = (int32_t)atomicAdd((unsigned long long*)&hist[c], 1ull);
+}
+__global__ void k_bin_order(const int32_t* coarse, const int32_t* rank, const int64_t* hoff, const int64_t* n_dev,
+                            const int64_t* bin_nt, int32_t* order, int64_t* nt_ord) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= *n_dev) return;
+  const int64_t pos = hoff[coarse[b]] + rank[b];
+  order[pos] = (int32_t)b;
+  nt_ord[pos] = bin_nt[b];
+}
+__global__ void k_make_tiles_ordered(const int32_t* order, const int64_t* cnt, const int64_t* off,
+                                     const int64_t* tile_off, const int64_t* n_dev, int T, int4* tiles) {
+  const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= *n_dev) return;
+  const int b = order[pos];
+  const int64_t c = cnt[b];
+  for (int64_t t = 0; t * T < c; ++t)
+    tiles[tile_off[pos] + t] = make_int4(b, (int)(off[b] + t * T), (int)(c - t * T < T ? c - t * T : T), 0);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Q3: candidate lists (warp per bin)
 
@@ -2150,7 +2186,10 @@ ksdf_status query_reserve(ksdf_ctx* c, int64_t Q, int64_t G) {
   const int64_t max_tiles_b = Q / kTB64 + G + 1;  // also covers the mixed path's three tile lists (+ 2 G + 2)
   KSDF_CUDA(c, ensure(c->ws[WS_TILE], sizeof(int4) * (max_tiles_a + max_tiles_b + 2 * G + 2)));
   KSDF_CUDA(c, ensure(c->ws[WS_CELLQ], sizeof(int64_t) * (8 * G + 8)));
-  const int64_t nsc = (int64_t)bcap / 2048 + 2;
+  // coarse order of the bins: three int32 arrays over at most min(bcap, Q) bins, then the bucket counts
+  const int64_t nb_max = std::min<int64_t>((int64_t)bcap, Q);
+  KSDF_CUDA(c, ensure(c->ws[WS_BORD], sizeof(int32_t) * (3 * nb_max + 2) + sizeof(int64_t) * kCoarseBuckets));
+  const int64_t nsc = std::max<int64_t>((int64_t)bcap, kCoarseBuckets) / 2048 + 2;
   KSDF_CUDA(c, ensure(c->ws[WS_SCAN], sizeof(int64_t) * nsc));
   return KSDF_OK;
 }
@@ -2217,9 +2256,24 @@ ksdf_status run_query(ksdf_ctx* c, const void* xq, bool f64, int64_t Q, const in
   const int64_t* nbins = &totals[0];
   KSDF_CUDA(c, scan_i64(bin_cnt, bin_off, bcap, &totals[1], c->ws[WS_SCAN], st, nbins));
   launch(k_ntiles, ceil_div(bcap, 256), 256, 0, st, bin_cnt, bcap, kTA, bin_nt, nbins);
-  KSDF_CUDA(c, scan_i64(bin_nt, bin_toff, bcap, &totals[2], c->ws[WS_SCAN], st, nbins));
   launch(k_scatter_grouped, ceil_div(Q, 256), 256, 0, st, qbin, qrank, Q, bin_off, qsort);
-  launch(k_make_tiles, ceil_div(bcap, 256), 256, 0, st, bin_cnt, bin_off, bin_toff, bcap, kTA, tiles_a, nbins);
+  // phase A's tiles in the bins' coarse spatial order (bin_toff holds the tile counts in that order, then their
+  // offsets)
+  {
+    const int64_t nb_max = std::min<int64_t>((int64_t)bcap, Q);
+    int32_t* coarse = ptr<int32_t>(c->ws[WS_BORD]);
+    int32_t* brank = coarse + nb_max;
+    int32_t* border = brank + nb_max;
+    // the bucket counts after the three int32 arrays, at an int32 offset rounded up to even (8-byte aligned)
+    int64_t* hist = reinterpret_cast<int64_t*>(coarse + ((3 * nb_max + 1) & ~(int64_t)1));
+    const unsigned gb = ceil_div(nb_max, 256);
+    KSDF_CUDA(c, cudaMemsetAsync(hist, 0, sizeof(int64_t) * kCoarseBuckets, st));
+    launch(k_bin_coarse, gb, 256, 0, st, bin_key, nbins, coarse, brank, hist);
+    KSDF_CUDA(c, scan_i64(hist, hist, kCoarseBuckets, nullptr, c->ws[WS_SCAN], st));
+    launch(k_bin_order, gb, 256, 0, st, coarse, brank, hist, nbins, bin_nt, border, bin_toff);
+    KSDF_CUDA(c, scan_i64(bin_toff, bin_toff, nb_max, &totals[2], c->ws[WS_SCAN], st, nbins));
+    launch(k_make_tiles_ordered, gb, 256, 0, st, border, bin_cnt, bin_off, bin_toff, nbins, kTA, tiles_a);
+  }
   prof_end(c, e0, "query.group");
   e0 = prof_begin(c);
   // Q3
