@@ -1719,6 +1719,12 @@ static const std::vector<std::vector<FitClassCfg>> kFitTables = {
     // one warp up to 80, two up to 128, four up to 218
     {{kMaxNmax, 256, true}, {218, 128, false}, {156, 128, false}, {128, 64, false}, {96, 64, false},
      {80, 32, false}, {64, 32, false}},
+    // one warp up to 64, two up to 112, four up to 180, finer classes
+    {{kMaxNmax, 256, true}, {218, 256, false}, {180, 128, false}, {140, 128, false}, {112, 64, false},
+     {96, 64, false}, {80, 64, false}, {64, 32, false}},
+    // one warp up to 72, two up to 156, four up to 218
+    {{kMaxNmax, 256, true}, {218, 128, false}, {156, 64, false}, {128, 64, false}, {96, 64, false},
+     {72, 32, false}, {56, 32, false}, {40, 32, false}},
 };
 
 int fit_table_count() { return (int)kFitTables.size(); }
