@@ -6,6 +6,7 @@ computes one by one:
   traj3d   the room scene, 2,097,152 trajectory queries: forward, and the adjoint of all of them in one call
            (d sdf and d grad cotangents) against the oracle's FP64 adjoint: d xq per query, d x per sample
   scale3d  2,000,000 samples, a 256^3 grid (16,777,216 queries): mixed path
+  room3d with the Matern 3/2 kernel (lambda 100): mixed path and the adjoint of all 1M queries
 """
 import numpy as np
 import pytest
@@ -127,3 +128,43 @@ def test_scale3d_full_mixed():
     m, res = _run(w)
     st = check_mixed(ref, w.xq[sel], w.sign[sel], _sub(res, sel), "scale3d full mixed")
     print(st)
+
+
+def test_room3d_full_matern_mixed_and_adjoint():
+    """The Matern 3/2 kernel (kernel table of Sec. IV-B.2, scaling of App. D) at the full room size: every
+    size class of the fit, both phase B kernels (cells up to and beyond the tensor-core class split) and both
+    adjoint cell launches run; the same bars as the RBF path."""
+    w = scenes.workload("room3d")
+    w.params = dict(w.params, kernel="matern32", softmin_alpha=100.0, **{"lambda": 100.0})
+    ref = oracle.Model(w.params, w.x, w.var, w.normals)
+    sel = _sample(len(w.xq), 14)
+    m, res = _run(w)
+    st = check_mixed(ref, w.xq[sel], w.sign[sel], _sub(res, sel), "room3d full matern mixed")
+    print(st)
+    # adjoint of every query (d sdf), compared on the sample; the same conditioning exclusions as traj3d
+    Q = len(w.xq)
+    gw = res["winner"]
+    sdf = res["sdf"].astype(np.float64)
+    fin = np.isfinite(sdf) & (gw >= 0)
+    zero = (res["flags"] & ksdf.FLAG_ZERO_GRAD) != 0
+    kept = fin & (np.abs(sdf) > 0.02) & ~zero
+    kept[np.setdiff1d(np.arange(Q), sel)] = False  # cotangents only on the sample: the oracle adjoint's cost
+    ratio = np.ones(Q)
+    ratio[sel] = cancellation_ratio(ref, w.xq[sel], np.where(fin[sel], gw[sel], -1))
+    kept &= ratio >= MEDIAL_RATIO
+    assert kept.sum() > 0.8 * len(sel), kept.sum()
+    d_sdf = np.where(kept, 1.0, 0.0).astype(np.float32)
+    d_xq, d_x = m.backward(_t(w.xq), _t(gw), _t(d_sdf), None, _t(w.sign))
+    torch.cuda.synchronize()
+    m.sync_status()
+    gq = d_xq.cpu().numpy().astype(np.float64)
+    gx = d_x.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(gq)) and np.all(np.isfinite(gx))
+    rq, rx = ref.backward(w.xq[sel], d_sdf[sel].astype(np.float64), None, sign=w.sign[sel], winner=gw[sel])
+    k = kept[sel]
+    nq = np.linalg.norm(rq, axis=1)
+    e = np.linalg.norm(gq[sel] - rq, axis=1)[k] / np.maximum(nq[k], 1e-12)
+    assert e.max() <= ADJ_REL, (e.max(), sel[k][np.argmax(e)])
+    ex = np.max(np.abs(gx - rx)) / np.max(np.abs(rx))
+    assert ex <= ADJ_REL, ex
+    print("room3d matern adjoint: d xq max rel %.3g over %d kept queries, d x %.3g" % (e.max(), k.sum(), ex))
