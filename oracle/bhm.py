@@ -147,6 +147,7 @@ class BHMOracle:
     active: list = field(default_factory=list)     # slot -> bool
     mu: list = field(default_factory=list)         # slot -> float64[n_h^3 + 1] (last = bias)
     prec: list = field(default_factory=list)       # slot -> float64[n_h^3 + 1]
+    mag: list = field(default_factory=list)        # slot -> float64[n_h^3 + 1], see update()
     tau: float = 0.0
     marked: set = field(default_factory=set)       # marked cells of the last update
     last_samples: int = 0
@@ -176,6 +177,7 @@ class BHMOracle:
             self.active.append(False)
             self.mu.append(np.zeros(self.nw))
             self.prec.append(np.full(self.nw, 1.0 / self.P.prior_var))
+            self.mag.append(np.zeros(self.nw))
         return self.slot[key]
 
     def weight_of_hinge(self, g):
@@ -298,9 +300,15 @@ class BHMOracle:
         P0 = np.concatenate(self.prec) if self.prec else np.zeros(0)
         if rows:
             mu, Pn, _ = em_diag(rows, t, mu0, P0, P.xi_init, P.em_iters)
+            # magnitude of the mean's numerator over the precision, (P0 |mu0| + sum |t - 1/2| phi) / P: a scale
+            # for comparing a lower-precision evaluation with this one (not used by the method)
+            absB = np.zeros_like(mu0)
+            np.add.at(absB, np.concatenate([r[0] for r in rows]), 0.5 * np.concatenate([r[1] for r in rows]))
+            mag = (P0 * np.abs(mu0) + absB) / Pn
             for s in range(len(self.keys)):
                 self.mu[s] = mu[s * nw:(s + 1) * nw].copy()
                 self.prec[s] = Pn[s * nw:(s + 1) * nw].copy()
+                self.mag[s] = mag[s * nw:(s + 1) * nw].copy()
         # 4. threshold
         if len(hits):
             lsum = sum(self.eval_u(self.lattice(xh), tuple(xh))[0] for xh in hits)

@@ -19,7 +19,8 @@ OUT = os.path.join(HERE, "libksdf.so")
 PEAKS_OUT = os.path.join(HERE, "libksdf_peaks.so")
 PEAKS_SRC = os.path.join(CSRC, "peaks", "ksdf_peaks.cu")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["ksdf_abi.cu", "ksdf_sort.cu", "ksdf_fit.cu", "ksdf_query.cu", "ksdf_backward.cu", "ksdf_noalloc.cu"]
+SOURCES = ["ksdf_abi.cu", "ksdf_sort.cu", "ksdf_fit.cu", "ksdf_query.cu", "ksdf_backward.cu", "ksdf_noalloc.cu",
+           "ksdf_bhm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas",
          "-warn-spills"]
@@ -37,7 +38,7 @@ def _stale() -> bool:
         return True
     t = min(os.path.getmtime(OUT), os.path.getmtime(PEAKS_OUT))
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [PEAKS_SRC, __file__]
-    deps += [os.path.join(HERE, "..", "include", h) for h in ("ksdf.h", "ksdf_peaks.h")]
+    deps += [os.path.join(HERE, "..", "include", h) for h in ("ksdf.h", "ksdf_bhm.h", "ksdf_peaks.h")]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

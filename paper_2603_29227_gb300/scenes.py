@@ -393,3 +393,28 @@ def make_city(seed: int = 3, n_boxes: int = 200, n_poses: int = 100, size: float
     params = dict(dim=3, origin=(0.0, 0.0, 0.0), cell=0.5, margin=0.1, n_max=256, k_cand=8, **{"lambda": 300.0},
                   softmin_alpha=300.0, sign_mode=1)
     return City(box_lo=lo[keep], box_hi=hi[keep], poses=poses, params=params, seed=seed)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# front-end (BHM) inputs from the same city scans
+
+# BHM parameters of the city stream, read from App. I's outdoor LiDAR setting (0.7 m octree voxels, local BHM boxes
+# of two voxels with 9 hinges per axis, so a hinge spacing of 0.175 m and 8 owned hinges per block axis; kernel
+# scale l = 0.11 m, gamma = 1 / (2 l^2)).  Free samples one hinge spacing apart, none within 0.1 m of the hit;
+# marching cells of half a hinge spacing.
+CITY_BHM = dict(origin=(0.0, 0.0, 0.0), hinge_spacing=0.175, block_hinges=8, gamma=1.0 / (2.0 * 0.11 ** 2),
+                phi_min=1e-3, prior_var=1.0, em_iters=2, xi_init=0.0, free_step=0.175, free_gap=0.1, tau_alpha=0.1,
+                tau_init=0.0, beta=1.0, march_sub=2)
+
+
+def city_bhm_frame(city: City, f: int, radius: float | None = None, max_hits: int | None = None, seed: int = 0):
+    """Sensor position and hits (R x 3 float64) of frame f: every hit, or those within `radius` of the sensor,
+    subsampled (seeded, order kept) to at most max_hits."""
+    x, _, _ = city.scan(f)
+    p = city.poses[f]
+    if radius is not None:
+        x = x[np.linalg.norm(x - p, axis=1) <= radius]
+    if max_hits is not None and len(x) > max_hits:
+        rng = np.random.default_rng(seed * 7919 + f)
+        x = x[np.sort(rng.choice(len(x), size=max_hits, replace=False))]
+    return np.asarray(p, dtype=np.float64), np.ascontiguousarray(x, dtype=np.float64)

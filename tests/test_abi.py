@@ -17,8 +17,8 @@ def lib():
     return ksdf.load()
 
 
-def declared():
-    hdr = open(os.path.join(ROOT, "include", "ksdf.h")).read()
+def declared(header="ksdf.h"):
+    hdr = open(os.path.join(ROOT, "include", header)).read()
     return re.findall(r"^(?:ksdf_status|const char\*|int)\s+(ksdf_\w+)\(", hdr, re.M)
 
 
@@ -30,6 +30,41 @@ def test_exports_every_declared_symbol(lib):
     for n in names:
         assert hasattr(lib, n), n
     assert sorted(names) == sorted(ksdf.ABI_FUNCTIONS)
+
+
+def test_exports_every_front_end_symbol(lib):
+    """include/ksdf_bhm.h (the BHM front-end) is part of the same library and of its binding."""
+    from paper_2603_29227_gb300 import bhm
+
+    names = declared("ksdf_bhm.h")
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(names) == sorted(bhm.BHM_ABI_FUNCTIONS)
+
+
+def test_front_end_parameters_rejected_without_cuda(lib):
+    from paper_2603_29227_gb300 import bhm, ksdf
+
+    bhm.load()
+    good = dict(bhm.DEFAULTS)
+    bad = [dict(good, hinge_spacing=0.0), dict(good, block_hinges=3), dict(good, block_hinges=17),
+           dict(good, gamma=-1.0), dict(good, phi_min=0.0), dict(good, phi_min=1.0), dict(good, prior_var=0.0),
+           dict(good, em_iters=0), dict(good, em_iters=5), dict(good, xi_init=-1.0), dict(good, free_step=0.0),
+           dict(good, free_gap=-0.1), dict(good, tau_alpha=0.0), dict(good, tau_alpha=1.5), dict(good, beta=0.0),
+           dict(good, march_sub=3), dict(good, gamma=1.0),  # window wider than two hinges
+           dict(good, block_hinges=4)]  # 2 r + 1 > n_h
+    for p in bad:
+        h = ctypes.c_void_p()
+        pr = bhm.make_params(p)
+        assert lib.ksdf_bhm_create(ctypes.byref(pr), 100, 0, None, ctypes.byref(h)) == ksdf.KSDF_ERR_ARG, p
+        assert not h.value
+    pr = bhm.make_params(good)
+    h = ctypes.c_void_p()
+    assert lib.ksdf_bhm_create(ctypes.byref(pr), 0, 0, None, ctypes.byref(h)) == ksdf.KSDF_ERR_ARG
+    assert lib.ksdf_bhm_destroy(None) == ksdf.KSDF_OK
+    assert lib.ksdf_bhm_sync_status(None) == ksdf.KSDF_ERR_ARG
+    assert lib.ksdf_bhm_update(None, None, None, 0) == ksdf.KSDF_ERR_ARG
 
 
 def test_invalid_parameters_rejected_without_cuda(lib):

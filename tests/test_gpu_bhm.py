@@ -1,0 +1,319 @@
+"""GPU parity of the BHM front-end (include/ksdf_bhm.h) with the binary64 oracle (oracle/bhm.py) on frames of the
+city scan: blocks, active flags and the sample count exactly; weights, threshold, log-odds, gradient and occupancy
+within the binary32 bound below; the sign and the marched edge set exactly wherever the oracle's values are
+farther from tau than that bound; the surface points within the bound propagated through the interpolation.
+
+Tolerance.  The GPU forms each feature as a product of three binary32 exponentials of binary32 arguments
+(relative error a few 2^-24 each) and sums and accumulates in binary32 (sums of up to ~10^3 terms, atomics in
+no fixed order).  A quantity that is a sum of terms t_i is therefore within c * sum |t_i| of the binary64 value
+with c of order 10^3 2^-24 ~ 6e-5 at worst; the tests use c = 2e-4 on the magnitude sums the oracle reports."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+C_REL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_29227_gb300 import build
+
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _oracle(params):
+    from oracle import bhm as ob
+
+    return ob.BHMOracle(ob.BHMParams(**params))
+
+
+def _unpack_block(k):
+    k = int(k)
+    b = 1 << 20
+    return ((k & 0x1FFFFF) - b, ((k >> 21) & 0x1FFFFF) - b, ((k >> 42) & 0x1FFFFF) - b)
+
+
+def _mags(o, x):
+    """(sum |mu phi| + |bias|, 2 gamma sum |mu phi| |x - x~|) of the oracle at point x: magnitude sums that bound
+    the binary32 error of l and grad l."""
+    P = o.P
+    f = o.features_u(o.lattice(x), tuple(x))
+    sl, sg = 0.0, 0.0
+    for (s, i), phi, g in f:
+        t = abs(o.mu[s][i] * phi)
+        sl += t
+        if g is not None:
+            d = math.sqrt(sum((x[a] - (P.origin[a] + g[a] * P.hinge_spacing)) ** 2 for a in range(3)))
+            sg += 2.0 * P.gamma * t * d
+    return sl, sg
+
+
+def _compare_maps(o, m):
+    keys, act, mu, prec = m.weights()
+    blocks = {_unpack_block(k): s for s, k in enumerate(keys)}
+    assert set(blocks) == set(o.slot), "allocated block sets differ"
+    for b, s in blocks.items():
+        so = o.slot[b]
+        assert bool(act[s]) == o.active[so], b
+        Po, mo = o.prec[so], o.mu[so]
+        assert np.all(np.abs(prec[s] - Po) <= C_REL * Po), b
+        # mu = (P0 mu0 + B) / P: bounded by the magnitude of its numerator over P, and by mu's own rounding
+        tol = C_REL * (o.mag[so] + np.abs(mo)) + 1e-7
+        assert np.all(np.abs(mu[s] - mo) <= tol), (b, np.max(np.abs(mu[s] - mo) - tol))
+
+
+def _frame(n_hits, f=0, radius=10.0, seed=0):
+    from paper_2603_29227_gb300 import scenes
+
+    city = scenes.make_city()
+    return scenes.city_bhm_frame(city, f, radius=radius, max_hits=n_hits, seed=seed)
+
+
+def _params(**kw):
+    from paper_2603_29227_gb300 import scenes
+
+    return dict(scenes.CITY_BHM, **kw)
+
+
+@pytest.fixture(scope="module")
+def two_frames(dev):
+    """Two frames (poses 0 and 1) through the oracle and the GPU map, with snapshots after each."""
+    import torch
+    from paper_2603_29227_gb300 import bhm
+
+    P = _params()
+    o = _oracle(P)
+    m = bhm.BHMap(P, max_blocks=20000)
+    snaps = []
+    for f in (0, 1):
+        p, hits = _frame(1200, f=f)
+        o.update(p, hits)
+        m.update(p, torch.from_numpy(hits).to(dev))
+        m.sync_status()
+        snaps.append((p, hits, m.size()[1], o.last_samples, m.tau, o.tau))
+        if f == 0:
+            _compare_maps(o, m)  # after the first frame
+    return o, m, snaps
+
+
+def test_update_blocks_samples_weights_tau(two_frames):
+    o, m, snaps = two_frames
+    sl_max = 0.0
+    for p, hits, ns_gpu, ns_oracle, tau_gpu, tau_oracle in snaps:
+        assert ns_gpu == ns_oracle
+        # tau is a moving average of hit log-odds: within the largest of their bounds
+        sl_max = max(sl_max, max(_mags(o, h)[0] for h in hits[::5]))
+        assert abs(tau_gpu - tau_oracle) <= 2 * C_REL * sl_max + 1e-7, (tau_gpu, tau_oracle)
+    _compare_maps(o, m)
+
+
+def test_query_logodds_sign_grad_prob(two_frames, dev):
+    import torch
+
+    o, m, snaps = two_frames
+    p, hits, *_ = snaps[-1]
+    rng = np.random.default_rng(3)
+    xq = np.concatenate([hits[::7] + rng.normal(0, 0.15, (len(hits[::7]), 3)),
+                         p + rng.uniform(-8, 8, (200, 3)) * np.array([1, 1, 0.2])]).astype(np.float32)
+    out = m.query(torch.from_numpy(xq).to(dev))
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    L, S, G, Pr = o.query(xq.astype(np.float64))
+    tau = o.tau
+    dtau = abs(m.tau - tau)
+    n_sign = 0
+    for k in range(len(xq)):
+        sl, sg = _mags(o, xq[k].astype(np.float64))
+        tl = C_REL * sl + 1e-6
+        assert abs(got["logodds"][k] - L[k]) <= tl, (k, got["logodds"][k], L[k])
+        assert np.max(np.abs(got["grad"][k] - G[k])) <= C_REL * sg + 1e-5, (k, got["grad"][k], G[k])
+        assert abs(got["prob"][k] - Pr[k]) <= (tl + C_REL * abs(L[k])) / 4 + 1e-6, (k, got["prob"][k], Pr[k])
+        if abs(L[k] - tau) > tl + dtau:
+            assert got["sign"][k] == S[k], k
+            n_sign += 1
+        else:
+            assert got["sign"][k] == (1 if got["logodds"][k] < m.tau else -1)
+    assert n_sign > 0.95 * len(xq)
+
+
+@pytest.mark.parametrize("march_sub", [2, 4])
+def test_march_parity(dev, march_sub):
+    import torch
+    from paper_2603_29227_gb300 import bhm
+
+    P = _params(march_sub=march_sub)
+    p, hits = _frame(300 if march_sub == 2 else 120, f=2, radius=9.0, seed=1)
+    o = _oracle(P)
+    o.update(p, hits)
+    m = bhm.BHMap(P, max_blocks=20000)
+    m.update(p, torch.from_numpy(hits).to(dev))
+    x, var, nrm, keys = m.march(device=dev)
+    m.sync_status()
+    x, var, nrm = x.cpu().numpy(), var.cpu().numpy(), nrm.cpu().numpy()
+    keys = keys.cpu().numpy().view(np.uint64)
+    assert np.all(np.diff(keys.astype(np.float64)) > 0) or len(keys) < 2  # ascending, unique
+    X, V, N, K = o.march()
+    B = 1 << 19
+    ko = np.array([((k[0] + B) << 42) | ((k[1] + B) << 22) | ((k[2] + B) << 2) | k[3] for k in K], dtype=np.uint64)
+    gi = {int(k): i for i, k in enumerate(keys)}
+    oi = {int(k): i for i, k in enumerate(ko)}
+    tau = o.tau
+    dtau = abs(m.tau - tau)
+    m_ = o.P.march_sub
+    h = o.P.hinge_spacing
+    decided, matched = 0, 0
+    for nu, a in o.marked_edges():
+        nv = list(nu)
+        nv[a] += 1
+        ua, ub = o.node_u(nu), o.node_u(tuple(nv))
+        la, lb = o.eval_u(ua)[0], o.eval_u(ub)[0]
+        xa = tuple(o.P.origin[i] + ua[i] * h for i in range(3))
+        xb = tuple(o.P.origin[i] + ub[i] * h for i in range(3))
+        ta = C_REL * _mags(o, np.array(xa))[0] + 1e-6 + dtau
+        tb = C_REL * _mags(o, np.array(xb))[0] + 1e-6 + dtau
+        key = int(((nu[2] + B) << 42) | ((nu[1] + B) << 22) | ((nu[0] + B) << 2) | a)
+        if abs(la - tau) <= ta or abs(lb - tau) <= tb:
+            continue  # the binary32 side may decide this edge either way
+        decided += 1
+        assert (key in gi) == (key in oi), (nu, a, la, lb, tau)
+        if key not in oi:
+            continue
+        i, j = oi[key], gi[key]
+        matched += 1
+        # position along the edge: t = (tau - la) / (lb - la), each l within its bound
+        dt = (ta + tb) / abs(lb - la) * (1.0 + 1e-3)
+        assert np.max(np.abs(x[j] - X[i])) <= dt * h / m_ + 1e-9, (key, x[j], X[i])
+        sl, sg = _mags(o, X[i])
+        l, g, _ = o.eval_u(o.lattice(X[i]), tuple(X[i]))
+        gnorm = float(np.linalg.norm(g))
+        # the gradient moves with the point (second derivatives ~ 2 gamma |grad l|) and by its own rounding
+        dxp = dt * h / m_
+        tg = C_REL * sg + 1e-5 + 2.0 * o.P.gamma * (sl + gnorm) * dxp
+        dl = C_REL * sl + 1e-6 + gnorm * dxp + tg * dxp
+        sig_o = math.sqrt(V[i])
+        sig_g = math.sqrt(float(var[j]))
+        bound = (dl + abs(tau - l) * tg / gnorm) / max(gnorm - tg, 1e-3 * gnorm) * math.sqrt(o.P.beta) + 1e-7
+        assert abs(sig_g - sig_o) <= bound, (key, sig_g, sig_o, bound)
+        assert np.max(np.abs(nrm[j] - N[i])) <= 2.0 * tg / gnorm + 1e-6, (key, nrm[j], N[i])
+    assert decided > 100 and matched > 50
+    assert abs(len(keys) - len(ko)) <= max(5, 0.02 * len(ko))
+
+
+def test_edge_cases(dev):
+    """R = 0, NaN hits, a capacity overflow, queries far from every block, and EM rounds 1 and 3 with xi_0 = 1."""
+    import torch
+    from paper_2603_29227_gb300 import bhm, ksdf
+
+    P = _params()
+    m = bhm.BHMap(P, max_blocks=20000)
+    p, hits = _frame(200, f=3, radius=8.0)
+    # no hits: nothing happens, tau unchanged
+    m.update(p, torch.zeros((0, 3), dtype=torch.float64, device=dev))
+    m.sync_status()
+    assert m.size() == (0, 0) and m.tau == P["tau_init"]
+    x, _, _, _ = m.march()
+    assert len(x) == 0
+    # a NaN hit is reported and skipped; the rest matches an oracle run without it
+    bad = hits.copy()
+    bad[5] = np.nan
+    m.update(p, torch.from_numpy(bad).to(dev))
+    with pytest.raises(ksdf.KsdfError) as e:
+        m.sync_status()
+    assert e.value.status == ksdf.KSDF_ERR_NONFINITE
+    o = _oracle(P)
+    o.update(p, np.delete(hits, 5, axis=0))
+    keys, act, _, _ = m.weights()
+    assert {_unpack_block(k) for k in keys} == set(o.slot)
+    # far from any block: log-odds 0, probability 1/2, gradient 0
+    q = m.query(torch.tensor([[p[0] + 500.0, p[1], 0.5]], dtype=torch.float32, device=dev))
+    assert float(q["logodds"][0]) == 0.0 and abs(float(q["prob"][0]) - 0.5) < 1e-7
+    assert torch.all(q["grad"] == 0)
+    # capacity: too few blocks
+    small = bhm.BHMap(P, max_blocks=10)
+    small.update(p, torch.from_numpy(hits).to(dev))
+    with pytest.raises(ksdf.KsdfError) as e:
+        small.sync_status()
+    assert e.value.status == ksdf.KSDF_ERR_CAPACITY
+    assert small.size()[0] == 10
+    # other EM schedules against the oracle
+    for iters, xi0 in ((1, 0.0), (3, 1.0)):
+        Pq = _params(em_iters=iters, xi_init=xi0)
+        o = _oracle(Pq)
+        o.update(p, hits)
+        mm = bhm.BHMap(Pq, max_blocks=20000)
+        mm.update(p, torch.from_numpy(hits).to(dev))
+        mm.sync_status()
+        _compare_maps(o, mm)
+        assert abs(mm.tau - o.tau) <= C_REL * (1.0 + abs(o.tau)) * 10
+
+
+def test_invalid_query_point(dev):
+    import torch
+    from paper_2603_29227_gb300 import bhm, ksdf
+
+    m = bhm.BHMap(_params(), max_blocks=100)
+    q = m.query(torch.tensor([[float("nan"), 0.0, 0.0], [1e9, 0.0, 0.0]], dtype=torch.float32, device=dev))
+    assert torch.all(torch.isnan(q["logodds"])) and torch.all(q["sign"] == 1)
+    with pytest.raises(ksdf.KsdfError) as e:
+        m.sync_status()
+    assert e.value.status == ksdf.KSDF_ERR_NONFINITE
+
+
+def test_front_end_feeds_the_back_end(dev):
+    """The paper's pipeline on three city frames: BHM update, surface points with their variance, the GP fit on
+    those points, and the SDF query signed by the BHM; away from the surface the sign agrees with the scene."""
+    import torch
+    from paper_2603_29227_gb300 import bhm, ksdf, scenes
+
+    city = scenes.make_city()
+    P = _params()
+    m = bhm.BHMap(P, max_blocks=200000)
+    pts, vs = [], []
+    for f in range(3):
+        p, hits = scenes.city_bhm_frame(city, f, radius=15.0)
+        m.update(p, torch.from_numpy(hits).to(dev))
+        x, var, _, _ = m.march(device=dev)
+        pts.append(x)
+        vs.append(var)
+    m.sync_status()
+    x = torch.cat(pts)
+    var = torch.cat(vs)
+    assert len(x) > 10000
+    gp = ksdf.KernelSDF(dict(city.params, sign_mode=0))
+    gp.fit(x, var, None)
+    # queries near what the scans saw: marched points moved by up to a metre or so
+    rng = np.random.default_rng(4)
+    idx = torch.from_numpy(rng.choice(len(x), size=20000, replace=False)).to(dev)
+    xq = (x[idx] + torch.from_numpy(rng.normal(0, 0.6, (20000, 3))).to(dev)).float().contiguous()
+    xn = xq.double().cpu().numpy()
+    truth_free = ~city_occupied(city, xn)
+    d_true = city_free_distance(city, xn)
+    sgn = m.query(xq, bhm.BHM_SIGN)["sign"]
+    o = gp.query(xq, sgn)
+    sdf = o["sdf"].cpu().numpy()
+    sel = ((d_true > 0.3) | ~truth_free) & np.isfinite(sdf) & (xn[:, 2] > -1.0)
+    assert sel.sum() > 5000
+    agree = np.mean((sdf[sel] > 0) == truth_free[sel])
+    assert agree > 0.97, agree
+
+
+def city_occupied(city, x):
+    inside = x[:, 2] < 0.0
+    for lo, hi in zip(city.box_lo, city.box_hi):
+        inside |= np.all((x >= lo) & (x <= hi), axis=1)
+    return inside
+
+
+def city_free_distance(city, x):
+    d = np.maximum(x[:, 2], 0.0)
+    for lo, hi in zip(city.box_lo, city.box_hi):
+        q = np.maximum(np.maximum(lo - x, x - hi), 0.0)
+        d = np.minimum(d, np.linalg.norm(q, axis=1))
+    return d
