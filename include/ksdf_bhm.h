@@ -77,6 +77,7 @@ typedef struct {
   double tau_init;      /* initial tau */
   double beta;          /* scale of the surface-point variance, > 0 */
   int march_sub;        /* marching cells per hinge spacing: 1, 2, 4 or 8 */
+  int bias_feature;     /* 1: phi carries the trailing 1, one bias weight per block (Sec. IV-A.1); 0: no bias */
 } ksdf_bhm_params;
 
 typedef struct ksdf_bhm ksdf_bhm;

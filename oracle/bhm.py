@@ -58,7 +58,8 @@ Readings where the paper is silent or garbled:
     with u_p, u_x those of p and x; the positions x_j = o + u_j h are only used for the kernel distances.
   - Marching cells: nu = floor(m u) per axis (m a power of two, so m u is exact).
   - The paper does not fix the prior, the free-sample spacing, the gap before the hit, alpha, beta or the
-    marching resolution: they are parameters here.
+    marching resolution: they are parameters here.  The per-block bias can be switched off (bias_feature = 0):
+    with it, a block whose samples are mostly free drags the log-odds of its unobserved interior down.
 """
 from __future__ import annotations
 
@@ -86,6 +87,7 @@ class BHMParams:
     tau_init: float = 0.0
     beta: float = 1.0
     march_sub: int = 2
+    bias_feature: int = 1          # 1: the trailing 1 of phi, one bias weight per block; 0: no bias feature
 
 
 def sigmoid(v):
@@ -212,7 +214,7 @@ class BHMOracle:
                 out.append((w, float(phi[k]), gk))
         b = self.block_of_u(u)
         s = self.slot.get(b)
-        if s is not None:
+        if s is not None and self.P.bias_feature:
             out.append(((s, self.nw - 1), 1.0, None))
         return out
 

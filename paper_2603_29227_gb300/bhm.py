@@ -26,12 +26,12 @@ class ksdf_bhm_params(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("phi_min", ctypes.c_double), ("prior_var", ctypes.c_double),
                 ("em_iters", ctypes.c_int), ("xi_init", ctypes.c_double), ("free_step", ctypes.c_double),
                 ("free_gap", ctypes.c_double), ("tau_alpha", ctypes.c_double), ("tau_init", ctypes.c_double),
-                ("beta", ctypes.c_double), ("march_sub", ctypes.c_int)]
+                ("beta", ctypes.c_double), ("march_sub", ctypes.c_int), ("bias_feature", ctypes.c_int)]
 
 
 DEFAULTS = dict(origin=(0.0, 0.0, 0.0), hinge_spacing=0.175, block_hinges=8, gamma=41.32, phi_min=1e-3,
                 prior_var=1.0, em_iters=2, xi_init=0.0, free_step=0.175, free_gap=0.1, tau_alpha=0.1, tau_init=0.0,
-                beta=1.0, march_sub=2)
+                beta=1.0, march_sub=2, bias_feature=1)
 
 _sigs_done = False
 
@@ -76,7 +76,7 @@ def make_params(p: dict) -> ksdf_bhm_params:
     for k in ("hinge_spacing", "gamma", "phi_min", "prior_var", "xi_init", "free_step", "free_gap", "tau_alpha",
               "tau_init", "beta"):
         setattr(q, k, float(p[k]))
-    for k in ("block_hinges", "em_iters", "march_sub"):
+    for k in ("block_hinges", "em_iters", "march_sub", "bias_feature"):
         setattr(q, k, int(p[k]))
     return q
 

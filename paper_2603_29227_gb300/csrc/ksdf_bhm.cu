@@ -52,6 +52,7 @@ struct BhmDev {
   long long r2q;
   int nh, nw, msub, cdim, mask_words;
   int frame, max_blocks, max_marked;
+  int bias;
   uint64_t hcap;
   uint64_t* hkeys;
   int32_t* hvals;
@@ -202,6 +203,7 @@ __device__ __forceinline__ void for_features(const BhmDev& d, const Win& w, cons
 
 // index of the bias weight of the point's own block, or -1
 __device__ __forceinline__ int64_t bias_index(const BhmDev& d, const Win& w, const Point& pt) {
+  if (!d.bias) return -1;
   const int s = w.s[(pt.base[2] >= d.nh) * 4 + (pt.base[1] >= d.nh) * 2 + (pt.base[0] >= d.nh)];
   return s < 0 ? -1 : (int64_t)s * d.nw + d.nw - 1;
 }
@@ -754,6 +756,7 @@ BhmDev dev_view(ksdf_bhm* m) {
   d.frame = m->frame;
   d.max_blocks = (int)m->max_blocks;
   d.max_marked = (int)m->max_marked;
+  d.bias = m->p.bias_feature;
   d.hcap = m->hcap;
   d.hkeys = ptr<uint64_t>(m->hkeys);
   d.hvals = ptr<int32_t>(m->hvals);
@@ -790,7 +793,8 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
             p.prior_var > 0 && p.em_iters >= 1 && p.em_iters <= 4 && std::isfinite(p.xi_init) && p.xi_init >= 0 &&
             std::isfinite(p.free_step) && p.free_step > 0 && std::isfinite(p.free_gap) && p.free_gap >= 0 &&
             p.tau_alpha > 0 && p.tau_alpha <= 1 && std::isfinite(p.tau_init) && std::isfinite(p.beta) && p.beta > 0 &&
-            (p.march_sub == 1 || p.march_sub == 2 || p.march_sub == 4 || p.march_sub == 8) && max_blocks >= 1 &&
+            (p.march_sub == 1 || p.march_sub == 2 || p.march_sub == 4 || p.march_sub == 8) &&
+            (p.bias_feature == 0 || p.bias_feature == 1) && max_blocks >= 1 &&
             max_blocks <= (1LL << 24) && max_marked >= 0;
   for (int a = 0; a < 3; ++a) ok = ok && std::isfinite(p.origin[a]);
   if (!ok) return KSDF_ERR_ARG;

@@ -404,7 +404,7 @@ def make_city(seed: int = 3, n_boxes: int = 200, n_poses: int = 100, size: float
 # marching cells of half a hinge spacing.
 CITY_BHM = dict(origin=(0.0, 0.0, 0.0), hinge_spacing=0.175, block_hinges=8, gamma=1.0 / (2.0 * 0.11 ** 2),
                 phi_min=1e-3, prior_var=1.0, em_iters=2, xi_init=0.0, free_step=0.175, free_gap=0.1, tau_alpha=0.1,
-                tau_init=0.0, beta=1.0, march_sub=2)
+                tau_init=0.0, beta=1.0, march_sub=2, bias_feature=1)
 
 
 def city_bhm_frame(city: City, f: int, radius: float | None = None, max_hits: int | None = None, seed: int = 0):

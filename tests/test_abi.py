@@ -52,7 +52,7 @@ def test_front_end_parameters_rejected_without_cuda(lib):
            dict(good, gamma=-1.0), dict(good, phi_min=0.0), dict(good, phi_min=1.0), dict(good, prior_var=0.0),
            dict(good, em_iters=0), dict(good, em_iters=5), dict(good, xi_init=-1.0), dict(good, free_step=0.0),
            dict(good, free_gap=-0.1), dict(good, tau_alpha=0.0), dict(good, tau_alpha=1.5), dict(good, beta=0.0),
-           dict(good, march_sub=3), dict(good, gamma=1.0),  # window wider than two hinges
+           dict(good, march_sub=3), dict(good, bias_feature=2), dict(good, gamma=1.0),  # window beyond 2 hinges
            dict(good, block_hinges=4)]  # 2 r + 1 > n_h
     for p in bad:
         h = ctypes.c_void_p()
