@@ -4,14 +4,18 @@
 // C ABI in include/ksdf_bhm.h, which also states the definitions every kernel here follows.
 //
 // Data layout in HBM (one map):
-//   W[slot * NW + i]  float4 {mu, P, B, A} per weight (NW = n_h^3 + 1, the bias last): mean and precision of the map
-//                     before the running update, and the update's two accumulators -- B = sum (t - 1/2) phi and
-//                     A = sum c(xi) phi^2 of odd EM rounds; PB[slot * NW + i] holds A of even rounds
+//   Wmp[slot * NW + i] float2 {mu, P} per weight (NW = n_h^3 + 1, the bias last): mean and precision of the map
+//                     before the running update; A0, A1, B[slot * NW + i] floats: the update's accumulators,
+//                     A = sum c(xi) phi^2 of odd (A0) and even (A1) EM rounds and B = sum (t - 1/2) phi
 //   hash table        block key -> slot (open addressing, linear probing), 4x the block capacity
 //   per block         packed key, active flag, the frame stamps of the touched / marked lists, its marked-cell index
 //   masks             one bit per marching cell of each marked block ((n_h m)^3 bits)
-// Every EM round is one launch over the rays (one thread per ray walks its samples; blocks without a hit are
-// skipped a whole block at a time), so no sample is ever stored.
+//   samples           one 32-byte record per sample of the running update (lattice cell, 32-bit fraction, label)
+// An update walks every ray twice (one thread per ray; blocks without a hit are skipped a whole block at a time):
+// once to count its samples, once, after a scan of the counts, to write them.  Each EM round is then one launch
+// in which a warp takes 32 consecutive samples and, for each, splits the sample's candidate hinges (the offsets a
+// point of the cell can reach, tabulated once per map) across its lanes: the M-step is a warp reduction and the
+// E-step's atomics of one warp instruction fall on neighbouring weights.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -36,6 +40,7 @@ struct BhmState {
   int32_t n_blocks, n_new, n_touched, n_marked;
   int32_t n_out, pad0, pad1, pad2;
   unsigned long long n_samples;
+  unsigned long long n_features;
   double lsum;
   double tau;
   uint32_t status;
@@ -52,7 +57,7 @@ struct BhmDev {
   long long r2q;
   int nh, nw, msub, cdim, mask_words;
   int frame, max_blocks, max_marked;
-  int bias;
+  int bias, rw;
   uint64_t hcap;
   uint64_t* hkeys;
   int32_t* hvals;
@@ -60,11 +65,23 @@ struct BhmDev {
   uint8_t* active;
   int32_t *stamp_touch, *stamp_mark, *mark_idx;
   int32_t *new_list, *touched, *marked;
-  float4* W;
-  float* PB;
+  float2* Wmp;
+  float *A0, *A1, *Bacc;
+  const int32_t* cand;  // candidate offsets (dz + 8) << 16 | (dy + 8) << 8 | (dx + 8), z-major
+  int ncand;
   uint32_t* masks;
   BhmState* st;
 };
+
+struct __align__(16) Sample {
+  int g[3];        // floor of the lattice coordinate
+  uint32_t fq[3];  // fraction u - floor(u) as floor(2^32 (u - floor(u)))
+  int t;           // label: 1 hit, 0 free
+  int pad;
+};
+
+constexpr int kMaxRounds = 7;  // candidate rounds of 32 lanes: (2 r + 2)^3 <= 216 offsets for r <= 2
+constexpr int kNoCand = -1;
 
 __device__ __forceinline__ double lat(double x, double o, double h) { return __ddiv_rn(__dsub_rn(x, o), h); }
 __device__ __forceinline__ bool lat_ok(double u) { return u > -kLatMax && u < kLatMax; }
@@ -215,7 +232,7 @@ __device__ void bhm_eval(const BhmDev& d, Win& w, const double u[3], float& l, f
   point_setup<RW, false>(d, w, u, pt);
   float sl = 0.f, gx = 0.f, gy = 0.f, gz = 0.f, sv = 0.f;
   for_features<RW>(d, w, pt, [&](int64_t idx, float phi, float dx, float dy, float dz) {
-    const float2 r = *reinterpret_cast<const float2*>(&d.W[idx]);
+    const float2 r = d.Wmp[idx];
     const float mp = r.x * phi;
     sl += mp;
     if (GRAD) {
@@ -227,7 +244,7 @@ __device__ void bhm_eval(const BhmDev& d, Win& w, const double u[3], float& l, f
   });
   const int64_t b = bias_index(d, w, pt);
   if (b >= 0) {
-    const float2 r = *reinterpret_cast<const float2*>(&d.W[b]);
+    const float2 r = d.Wmp[b];
     sl += r.x;
     if (VAR) sv += 1.0f / r.y;
   }
@@ -288,8 +305,11 @@ __global__ void k_bhm_assign(BhmDev d) {
       d.mark_idx[id] = -1;
     }
     for (int k = threadIdx.x; k < d.nw; k += blockDim.x) {
-      d.W[(int64_t)id * d.nw + k] = make_float4(0.f, d.prior_prec, 0.f, 0.f);
-      d.PB[(int64_t)id * d.nw + k] = 0.f;
+      const int64_t i = (int64_t)id * d.nw + k;
+      d.Wmp[i] = make_float2(0.f, d.prior_prec);
+      d.A0[i] = 0.f;
+      d.A1[i] = 0.f;
+      d.Bacc[i] = 0.f;
     }
   }
 }
@@ -302,6 +322,7 @@ __global__ void k_bhm_counts(BhmDev d) {
   st->n_touched = 0;
   st->n_marked = 0;
   st->n_samples = 0ull;
+  st->n_features = 0ull;
   st->lsum = 0.0;
 }
 
@@ -314,46 +335,31 @@ __global__ void k_bhm_activate(BhmDev d, const double* __restrict__ hits, int64_
   if (s >= 0) d.active[s] = 1;
 }
 
-// One EM round over every ray's samples.  FIRST: xi = xi_init, accumulates B and A into W (and builds the
-// touched-block list).  Otherwise: the M-step for each sample from the previous round's accumulators (src: 0 = A
-// in W, 1 = PB), then the E-step statistic c(xi) phi^2 into dst.
-template <int RW, bool FIRST>
-__device__ __forceinline__ void em_sample(const BhmDev& d, Win& w, const double u[3], float tlab, int src, int dst) {
-  Point pt;
-  point_setup<RW, FIRST>(d, w, u, pt);
-  const int64_t bidx = bias_index(d, w, pt);
-  float xi = d.xi0;
-  if (!FIRST) {
-    float vs = 0.f, ms = 0.f;
-    auto mstep = [&](int64_t idx, float phi) {
-      const float4 r = d.W[idx];
-      const float a = src ? d.PB[idx] : r.w;
-      const float P = r.y + a;
-      const float mu = fmaf(r.y, r.x, r.z) / P;
-      vs = fmaf(phi * phi, 1.0f / P, vs);
-      ms = fmaf(mu, phi, ms);
-    };
-    for_features<RW>(d, w, pt, [&](int64_t idx, float phi, float, float, float) { mstep(idx, phi); });
-    if (bidx >= 0) mstep(bidx, 1.0f);
-    xi = sqrtf(fmaf(ms, ms, vs));
+__device__ __forceinline__ Sample make_sample(const double u[3], int t) {
+  Sample sm;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double fl = floor(u[a]);
+    sm.g[a] = (int)fl;
+    sm.fq[a] = (uint32_t)__dmul_rn(__dsub_rn(u[a], fl), 4294967296.0);  // exact scaling, truncation = floor
   }
-  const float c = jj_coef(xi);
-  const float tb = tlab - 0.5f;
-  auto estep = [&](int64_t idx, float phi) {
-    float* acc = dst ? &d.PB[idx] : &d.W[idx].w;
-    atomicAdd(acc, c * phi * phi);
-    if (FIRST) atomicAdd(&d.W[idx].z, tb * phi);
-  };
-  for_features<RW>(d, w, pt, [&](int64_t idx, float phi, float, float, float) { estep(idx, phi); });
-  if (bidx >= 0) estep(bidx, 1.0f);
+  sm.t = t;
+  sm.pad = 0;
+  return sm;
 }
 
-template <int RW, bool FIRST>
-__global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const double* __restrict__ hits, int64_t R, int src, int dst) {
+// The samples of every ray (one thread per ray): free samples u_j = u_p + (j sigma) du in active blocks, then the
+// hit.  COUNT: cnt[r] = the ray's sample count; otherwise the samples are written from off[r] on.
+template <bool COUNT>
+__global__ void __launch_bounds__(kT) k_bhm_walk(BhmDev d, const double* __restrict__ hits, int64_t R, int64_t* cnt,
+                                                 const int64_t* __restrict__ off, Sample* __restrict__ smp) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   double ux[3];
-  if (!hit_lattice(d, hits, r, ux)) return;
+  if (!hit_lattice(d, hits, r, ux)) {
+    if (COUNT) cnt[r] = 0;
+    return;
+  }
   const double dx = __dsub_rn(hits[3 * r], d.p[0]), dy = __dsub_rn(hits[3 * r + 1], d.p[1]),
                dz = __dsub_rn(hits[3 * r + 2], d.p[2]);
   const double L = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
@@ -367,11 +373,9 @@ __global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const double* __restric
   double du[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) du[a] = __dsub_rn(ux[a], d.up[a]);
-  Win w;
-  w.lo[0] = w.lo[1] = w.lo[2] = INT_MIN;
   int cb[3] = {INT_MIN, INT_MIN, INT_MIN};
   bool cact = false;
-  unsigned long long count = 0;
+  int64_t k = COUNT ? 0 : off[r];
   for (long long j = 1; j <= jmax; ++j) {
     const double s = __dmul_rn((double)j, sig);
     double u[3];
@@ -402,12 +406,126 @@ __global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const double* __restric
       if (jn > (double)j) j = jn < (double)jmax ? (long long)jn : jmax;
       continue;
     }
-    em_sample<RW, FIRST>(d, w, u, 0.0f, src, dst);
-    ++count;
+    if (!COUNT) smp[k] = make_sample(u, 0);
+    ++k;
   }
-  em_sample<RW, FIRST>(d, w, ux, 1.0f, src, dst);
-  ++count;
-  if (FIRST) atomicAdd(&d.st->n_samples, count);
+  if (!COUNT) smp[k] = make_sample(ux, 1);
+  ++k;
+  if (COUNT) cnt[r] = k;
+}
+
+// One EM round over the update's samples, a warp per 32 consecutive samples.  FIRST: xi = xi_init, accumulates B
+// and A into A0 (and builds the touched-block list).  Otherwise: the M-step of each sample from the previous
+// round's posterior (its A in src: 0 = A0, 1 = A1), then the E-step statistic c(xi) phi^2 into dst.
+template <bool FIRST>
+__global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const Sample* __restrict__ smp,
+                                               const unsigned long long* __restrict__ n_dev, int src, int dst) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int64_t N = (int64_t)*n_dev;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int nh = d.nh, nw = d.nw, RW = d.rw;
+  int cand[kMaxRounds];
+#pragma unroll
+  for (int r = 0; r < kMaxRounds; ++r) {
+    const int c = r * 32 + lane;
+    cand[r] = c < d.ncand ? d.cand[c] : kNoCand;
+  }
+  const float* Asrc = src ? d.A1 : d.A0;
+  float* Adst = dst ? d.A1 : d.A0;
+  int wlo[3] = {INT_MIN, INT_MIN, INT_MIN};
+  int myslot = -1;  // lanes 0..7: slot of window block lo + (lane & 1, lane >> 1 & 1, lane >> 2)
+  unsigned long long nfeat = 0;
+  for (int64_t base = gw * 32; base < N; base += nwarps * 32) {
+    Sample my = {};
+    if (base + lane < N) my = smp[base + lane];
+    const int nv = (int)(N - base < 32 ? N - base : 32);
+    for (int s = 0; s < nv; ++s) {
+      int g[3], bse[3], lo[3];
+      long long q[3];
+      float f[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        g[a] = __shfl_sync(FULL, my.g[a], s);
+        const uint32_t fq = __shfl_sync(FULL, my.fq[a], s);
+        q[a] = (long long)(fq >> 12);
+        f[a] = (float)fq * 2.3283064365386963e-10f;  // 2^-32
+        lo[a] = fdiv(g[a] - RW, nh);
+        bse[a] = g[a] - nh * lo[a];
+      }
+      const float tb = (float)__shfl_sync(FULL, my.t, s) - 0.5f;
+      if (lo[0] != wlo[0] || lo[1] != wlo[1] || lo[2] != wlo[2]) {
+        wlo[0] = lo[0];
+        wlo[1] = lo[1];
+        wlo[2] = lo[2];
+        if (lane < 8) {
+          myslot = find_block(d, lo[0] + (lane & 1), lo[1] + ((lane >> 1) & 1), lo[2] + (lane >> 2));
+          if (FIRST && myslot >= 0 && d.stamp_touch[myslot] != d.frame) {
+            if (atomicExch(&d.stamp_touch[myslot], d.frame) != d.frame)
+              d.touched[atomicAdd(&d.st->n_touched, 1)] = myslot;
+          }
+        }
+      }
+      const int bsl = __shfl_sync(FULL, myslot, (bse[2] >= nh) * 4 + (bse[1] >= nh) * 2 + (bse[0] >= nh));
+      const int bidx = (d.bias && bsl >= 0) ? bsl * nw + nw - 1 : -1;
+      float phr[kMaxRounds];
+      int idr[kMaxRounds];
+      float vs = 0.f, ms = 0.f;
+#pragma unroll
+      for (int r = 0; r < kMaxRounds; ++r) {
+        const int cd = cand[r];
+        const int ox = (cd & 255) - 8, oy = ((cd >> 8) & 255) - 8, oz = ((cd >> 16) & 255) - 8;
+        const long long tx = q[0] - ((long long)ox << kQ), ty = q[1] - ((long long)oy << kQ),
+                        tz = q[2] - ((long long)oz << kQ);
+        const int lx = bse[0] + ox, ly = bse[1] + oy, lz = bse[2] + oz;
+        const int sl = __shfl_sync(FULL, myslot, (lz >= nh) * 4 + (ly >= nh) * 2 + (lx >= nh));
+        const bool ok = cd != kNoCand && tx * tx + ty * ty + tz * tz <= d.r2q && sl >= 0;
+        const float fx = f[0] - (float)ox, fy = f[1] - (float)oy, fz = f[2] - (float)oz;
+        const float phi = expf(-d.gh2 * (fx * fx + fy * fy + fz * fz));
+        const int idx = sl * nw + ((lz - (lz >= nh ? nh : 0)) * nh + (ly - (ly >= nh ? nh : 0))) * nh +
+                        (lx - (lx >= nh ? nh : 0));
+        phr[r] = phi;
+        idr[r] = ok ? idx : -1;
+        if (!FIRST && ok) {
+          const float2 w = d.Wmp[idx];
+          const float P = w.y + Asrc[idx];
+          const float mu = fmaf(w.y, w.x, d.Bacc[idx]) / P;
+          vs = fmaf(phi * phi, 1.0f / P, vs);
+          ms = fmaf(mu, phi, ms);
+        }
+        if (FIRST) nfeat += (unsigned long long)__popc(__ballot_sync(FULL, ok));
+      }
+      float xi = d.xi0;
+      if (!FIRST) {
+        if (lane == 0 && bidx >= 0) {
+          const float2 w = d.Wmp[bidx];
+          const float P = w.y + Asrc[bidx];
+          vs += 1.0f / P;
+          ms += fmaf(w.y, w.x, d.Bacc[bidx]) / P;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          vs += __shfl_xor_sync(FULL, vs, o);
+          ms += __shfl_xor_sync(FULL, ms, o);
+        }
+        xi = sqrtf(fmaf(ms, ms, vs));
+      }
+      const float c = jj_coef(xi);
+#pragma unroll
+      for (int r = 0; r < kMaxRounds; ++r) {
+        if (idr[r] >= 0) {
+          atomicAdd(&Adst[idr[r]], c * phr[r] * phr[r]);
+          if (FIRST) atomicAdd(&d.Bacc[idr[r]], tb * phr[r]);
+        }
+      }
+      if (lane == 0 && bidx >= 0) {
+        atomicAdd(&Adst[bidx], c);
+        if (FIRST) atomicAdd(&d.Bacc[bidx], tb);
+      }
+    }
+  }
+  if (FIRST && lane == 0 && nfeat) atomicAdd(&d.st->n_features, nfeat);
 }
 
 // zero one accumulator of every touched block (between EM rounds three and four)
@@ -415,10 +533,8 @@ __global__ void k_bhm_zero_acc(BhmDev d, int which) {
   const int n = d.st->n_touched;
   for (int b = blockIdx.x; b < n; b += gridDim.x) {
     const int64_t base = (int64_t)d.touched[b] * d.nw;
-    for (int k = threadIdx.x; k < d.nw; k += blockDim.x) {
-      if (which) d.PB[base + k] = 0.f;
-      else d.W[base + k].w = 0.f;
-    }
+    float* A = which ? d.A1 : d.A0;
+    for (int k = threadIdx.x; k < d.nw; k += blockDim.x) A[base + k] = 0.f;
   }
 }
 
@@ -428,17 +544,16 @@ __global__ void k_bhm_commit(BhmDev d, int last) {
   for (int b = blockIdx.x; b < n; b += gridDim.x) {
     const int64_t base = (int64_t)d.touched[b] * d.nw;
     for (int k = threadIdx.x; k < d.nw; k += blockDim.x) {
-      float4 r = d.W[base + k];
-      const float a = last ? d.PB[base + k] : r.w;
+      const int64_t i = base + k;
+      const float a = last ? d.A1[i] : d.A0[i];
       if (a != 0.f) {
-        const float P = r.y + a;
-        r.x = fmaf(r.y, r.x, r.z) / P;
-        r.y = P;
+        const float2 w = d.Wmp[i];
+        const float P = w.y + a;
+        d.Wmp[i] = make_float2(fmaf(w.y, w.x, d.Bacc[i]) / P, P);
       }
-      r.z = 0.f;
-      r.w = 0.f;
-      d.W[base + k] = r;
-      d.PB[base + k] = 0.f;
+      d.A0[i] = 0.f;
+      d.A1[i] = 0.f;
+      d.Bacc[i] = 0.f;
     }
   }
 }
@@ -694,9 +809,11 @@ struct ksdf_bhm {
   long long r2q = 0;
   int64_t max_blocks = 0, max_marked = 0;
   uint64_t hcap = 0;
-  DevBuf hkeys, hvals, bkey, active, stamps, lists, W, PB, masks, state;
+  DevBuf hkeys, hvals, bkey, active, stamps, lists, Wmp, A0, A1, B, cand, masks, state;
   DevBuf stage_hits, mkey, mval, mx, mvar, mnrm, sort_tmp, out_stage[4], q_stage[5];
-  int64_t mcap = 0;
+  DevBuf smp, scnt, soff, scan_tmp;
+  int64_t mcap = 0, scap = 0;
+  int ncand = 0;
   double up[3] = {0, 0, 0}, p_last[3] = {0, 0, 0};
 };
 
@@ -770,8 +887,13 @@ BhmDev dev_view(ksdf_bhm* m) {
   d.new_list = li;
   d.touched = li + m->hcap;
   d.marked = li + m->hcap + m->max_blocks;
-  d.W = ptr<float4>(m->W);
-  d.PB = ptr<float>(m->PB);
+  d.Wmp = ptr<float2>(m->Wmp);
+  d.A0 = ptr<float>(m->A0);
+  d.A1 = ptr<float>(m->A1);
+  d.Bacc = ptr<float>(m->B);
+  d.cand = ptr<int32_t>(m->cand);
+  d.ncand = m->ncand;
+  d.rw = m->rw;
   d.masks = ptr<uint32_t>(m->masks);
   d.st = ptr<BhmState>(m->state);
   return d;
@@ -794,8 +916,7 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
             std::isfinite(p.free_step) && p.free_step > 0 && std::isfinite(p.free_gap) && p.free_gap >= 0 &&
             p.tau_alpha > 0 && p.tau_alpha <= 1 && std::isfinite(p.tau_init) && std::isfinite(p.beta) && p.beta > 0 &&
             (p.march_sub == 1 || p.march_sub == 2 || p.march_sub == 4 || p.march_sub == 8) &&
-            (p.bias_feature == 0 || p.bias_feature == 1) && max_blocks >= 1 &&
-            max_blocks <= (1LL << 24) && max_marked >= 0;
+            (p.bias_feature == 0 || p.bias_feature == 1) && max_blocks >= 1 && max_marked >= 0;
   for (int a = 0; a < 3; ++a) ok = ok && std::isfinite(p.origin[a]);
   if (!ok) return KSDF_ERR_ARG;
   const double r2 = std::log(1.0 / p.phi_min) / (p.gamma * p.hinge_spacing * p.hinge_spacing) * 1099511627776.0;
@@ -808,12 +929,25 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   if (rw > 2 || 2 * rw + 1 > p.block_hinges) return KSDF_ERR_ARG;
   const int cdim = p.block_hinges * p.march_sub;
   if (cdim > 64) return KSDF_ERR_ARG;
+  const int64_t nw = (int64_t)p.block_hinges * p.block_hinges * p.block_hinges + 1;
+  if (max_blocks * nw >= (1LL << 31)) return KSDF_ERR_ARG;  // weight indices are 32-bit
+  // candidate hinge offsets: those within the feature radius of some point of the unit cell (z-major order)
+  std::vector<int32_t> cand;
+  const double rr2 = (double)r2q / 1099511627776.0 + 1e-9;
+  for (int dz = -rw; dz <= rw + 1; ++dz)
+    for (int dy = -rw; dy <= rw + 1; ++dy)
+      for (int dx = -rw; dx <= rw + 1; ++dx) {
+        auto gap = [](int o) { return o < 0 ? -o : (o > 1 ? o - 1 : 0); };
+        const double g2 = (double)(gap(dx) * gap(dx) + gap(dy) * gap(dy) + gap(dz) * gap(dz));
+        if (g2 <= rr2) cand.push_back(((dz + 8) << 16) | ((dy + 8) << 8) | (dx + 8));
+      }
 
   ksdf_bhm* m = new ksdf_bhm();
   m->p = p;
   m->stream = (cudaStream_t)stream;
   m->rw = rw;
   m->r2q = r2q;
+  m->ncand = (int)cand.size();
   m->nh = p.block_hinges;
   m->nw = p.block_hinges * p.block_hinges * p.block_hinges + 1;
   m->cdim = cdim;
@@ -833,13 +967,18 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   al(m->active, (size_t)max_blocks);
   al(m->stamps, 12 * (size_t)max_blocks);
   al(m->lists, 4 * (cap + 2 * (size_t)max_blocks));  // new-key list (one per table position), touched, marked
-  al(m->W, 16 * (size_t)max_blocks * m->nw);
-  al(m->PB, 4 * (size_t)max_blocks * m->nw);
+  al(m->Wmp, 8 * (size_t)max_blocks * m->nw);
+  al(m->A0, 4 * (size_t)max_blocks * m->nw);
+  al(m->A1, 4 * (size_t)max_blocks * m->nw);
+  al(m->B, 4 * (size_t)max_blocks * m->nw);
+  al(m->cand, 4 * cand.size());
   al(m->masks, 4 * (size_t)m->max_marked * m->mask_words);
   al(m->state, sizeof(BhmState));
   if (e == cudaSuccess) e = cudaMemsetAsync(m->hkeys.p, 0xff, 8 * cap, m->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->hvals.p, 0xff, 4 * cap, m->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->state.p, 0, sizeof(BhmState), m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->cand.p, cand.data(), 4 * cand.size(), cudaMemcpyHostToDevice, m->stream);
   if (e == cudaSuccess) {
     const double tau = p.tau_init;
     e = cudaMemcpyAsync(reinterpret_cast<char*>(m->state.p) + offsetof(BhmState, tau), &tau, sizeof(double),
@@ -856,9 +995,9 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
 
 ksdf_status ksdf_bhm_destroy(ksdf_bhm* m) {
   if (!m) return KSDF_OK;
-  DevBuf* bufs[] = {&m->hkeys, &m->hvals, &m->bkey, &m->active, &m->stamps, &m->lists, &m->W, &m->PB,
-                    &m->masks, &m->state, &m->stage_hits, &m->mkey, &m->mval, &m->mx, &m->mvar, &m->mnrm,
-                    &m->sort_tmp};
+  DevBuf* bufs[] = {&m->hkeys, &m->hvals, &m->bkey, &m->active, &m->stamps, &m->lists, &m->Wmp, &m->A0,
+                    &m->A1, &m->B, &m->cand, &m->masks, &m->state, &m->stage_hits, &m->mkey, &m->mval,
+                    &m->mx, &m->mvar, &m->mnrm, &m->sort_tmp, &m->smp, &m->scnt, &m->soff, &m->scan_tmp};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : m->out_stage) release(b);
   for (DevBuf& b : m->q_stage) release(b);
@@ -899,21 +1038,31 @@ ksdf_status ksdf_bhm_update(ksdf_bhm* m, const double* p, const double* hits, in
   launch(k_bhm_counts, 1, 1, 0, st, d);
   if (R > 0) {
     launch(k_bhm_activate, g, kT, 0, st, d, dh, R);
+    // the samples: count per ray, scan, write (the count decides the buffer size: one synchronisation)
+    BHM_CUDA(m, ensure(m->scnt, 8 * (size_t)R));
+    BHM_CUDA(m, ensure(m->soff, 8 * (size_t)R));
+    int64_t* cnt = ptr<int64_t>(m->scnt);
+    int64_t* off = ptr<int64_t>(m->soff);
+    BhmState* sdev = ptr<BhmState>(m->state);
+    launch(k_bhm_walk<true>, g, kT, 0, st, d, dh, R, cnt, (const int64_t*)nullptr, (Sample*)nullptr);
+    BHM_CUDA(m, scan_i64(cnt, off, R, reinterpret_cast<int64_t*>(&sdev->n_samples), m->scan_tmp, st));
+    unsigned long long ns = 0;
+    BHM_CUDA(m, cudaMemcpyAsync(&ns, &sdev->n_samples, 8, cudaMemcpyDeviceToHost, st));
+    BHM_CUDA(m, cudaStreamSynchronize(st));
+    if ((int64_t)ns > m->scap) {
+      const int64_t want = (int64_t)ns + ((int64_t)ns >> 3) + 1024;
+      BHM_CUDA(m, ensure(m->smp, sizeof(Sample) * (size_t)want));
+      m->scap = want;
+    }
+    Sample* smp = ptr<Sample>(m->smp);
+    launch(k_bhm_walk<false>, g, kT, 0, st, d, dh, R, (int64_t*)nullptr, (const int64_t*)off, smp);
+    const unsigned ge = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)ns + 255) / 256, 152 * 16));
     const int iters = m->p.em_iters;
     for (int it = 1; it <= iters; ++it) {
       const int dst = (it - 1) & 1, src = it >= 2 ? (it - 2) & 1 : 0;
       if (it >= 3) launch(k_bhm_zero_acc, kGridStride, kT, 0, st, d, dst);
-      switch (m->rw) {
-#define EM_CASE(RWV)                                                                   \
-  case RWV:                                                                            \
-    if (it == 1) launch(k_bhm_em<RWV, true>, g, kT, 0, st, d, dh, R, src, dst);        \
-    else launch(k_bhm_em<RWV, false>, g, kT, 0, st, d, dh, R, src, dst);               \
-    break;
-        EM_CASE(0)
-        EM_CASE(1)
-        EM_CASE(2)
-#undef EM_CASE
-      }
+      if (it == 1) launch(k_bhm_em<true>, ge, kT, 0, st, d, (const Sample*)smp, &sdev->n_samples, src, dst);
+      else launch(k_bhm_em<false>, ge, kT, 0, st, d, (const Sample*)smp, &sdev->n_samples, src, dst);
     }
     launch(k_bhm_commit, kGridStride, kT, 0, st, d, (iters - 1) & 1);
     switch (m->rw) {
@@ -1057,8 +1206,8 @@ ksdf_status ksdf_bhm_get(ksdf_bhm* m, uint64_t* keys, uint8_t* active, float* mu
   if (keys) BHM_CUDA(m, cudaMemcpyAsync(keys, m->bkey.p, 8 * nb, cudaMemcpyDeviceToHost, st));
   if (active) BHM_CUDA(m, cudaMemcpyAsync(active, m->active.p, nb, cudaMemcpyDeviceToHost, st));
   if (mu || prec) {
-    std::vector<float4> w((size_t)nb * m->nw);
-    BHM_CUDA(m, cudaMemcpyAsync(w.data(), m->W.p, 16 * w.size(), cudaMemcpyDeviceToHost, st));
+    std::vector<float2> w((size_t)nb * m->nw);
+    BHM_CUDA(m, cudaMemcpyAsync(w.data(), m->Wmp.p, 8 * w.size(), cudaMemcpyDeviceToHost, st));
     BHM_CUDA(m, cudaStreamSynchronize(st));
     for (size_t i = 0; i < w.size(); ++i) {
       if (mu) mu[i] = w[i].x;
