@@ -76,7 +76,7 @@ typedef struct {
   double tau_alpha;     /* learning rate of tau, in (0, 1] */
   double tau_init;      /* initial tau */
   double beta;          /* scale of the surface-point variance, > 0 */
-  int march_sub;        /* marching cells per hinge spacing: 1, 2, 4 or 8 */
+  int march_sub;        /* marching cells per hinge spacing: 1, 2, 4 or 8, with n_h march_sub <= 32 */
   int bias_feature;     /* 1: phi carries the trailing 1, one bias weight per block (Sec. IV-A.1); 0: no bias */
 } ksdf_bhm_params;
 

@@ -658,42 +658,111 @@ struct MarchOut {
   int64_t cap;
 };
 
+// One CTA per marked block.  Shared memory: the means of every hinge the block's nodes can reach ((n_h + 2 RW + 2)^3,
+// hinge local coordinate + RW), the biases and mark indices of the 27 blocks around, the per-axis factors of a node
+// (node fractions are multiples of 1/m, so exp(-gamma h^2 (k/m - delta)^2) and the fixed-point distances are
+// tabulated per k), the processed-edge bits of the owned nodes and the log-odds of the (C + 1)^3 nodes they use.
+struct MarchSmem {
+  int nbr_mark[27];
+  float nbr_bias[27];
+};
+
+template <int RW>
+__device__ __forceinline__ float node_logodds(const BhmDev& d, const MarchSmem& sm, const float* mus, const float* te,
+                                              const long long* tq, int HN, const int gl[3], const int kk[3]) {
+  constexpr int NO = 2 * RW + 2;
+  const int m = d.msub, nh = d.nh;
+  float acc = 0.f;
+#pragma unroll 1
+  for (int iz = 0; iz < NO; ++iz) {
+    const long long dz = tq[kk[2] * NO + iz];
+    if (dz > d.r2q) continue;
+    const float ez = te[kk[2] * NO + iz];
+    const int hz = gl[2] + iz;  // (g0 + delta) + RW with delta = iz - RW
+#pragma unroll 1
+    for (int iy = 0; iy < NO; ++iy) {
+      const long long dzy = dz + tq[kk[1] * NO + iy];
+      if (dzy > d.r2q) continue;
+      const float ezy = ez * te[kk[1] * NO + iy];
+      const float* row = mus + ((hz * HN) + gl[1] + iy) * HN + gl[0];
+#pragma unroll
+      for (int ix = 0; ix < NO; ++ix) {
+        if (dzy + tq[kk[0] * NO + ix] > d.r2q) continue;
+        acc = fmaf(row[ix], ezy * te[kk[0] * NO + ix], acc);
+      }
+    }
+  }
+  (void)m;
+  // bias of the node's own block (its g0 lies in the block or on its upper faces)
+  const int bsel = ((gl[2] >= nh) + 1) * 9 + ((gl[1] >= nh) + 1) * 3 + ((gl[0] >= nh) + 1);
+  return acc + sm.nbr_bias[bsel];
+}
+
 template <int RW>
 __global__ void __launch_bounds__(kT) k_bhm_march(BhmDev d, MarchOut mo) {
-  __shared__ int nbr[27];  // mark index of the 27 blocks around (only the lower seven are read), -1 if unmarked
+  constexpr int NO = 2 * RW + 2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  MarchSmem& sm = *reinterpret_cast<MarchSmem*>(smraw);
+  const int nh = d.nh, C = d.cdim, m = d.msub, HN = nh + 2 * RW + 2, C1 = C + 1;
+  long long* tq = reinterpret_cast<long long*>(smraw + sizeof(MarchSmem) + (8 - sizeof(MarchSmem) % 8) % 8);
+  float* te = reinterpret_cast<float*>(tq + m * NO);
+  float* mus = te + m * NO;
+  float* lv = mus + HN * HN * HN;
+  uint8_t* doit = reinterpret_cast<uint8_t*>(lv + C1 * C1 * C1);
   const int nmk = min(d.st->n_marked, d.max_marked);
   const double tau = d.st->tau;
-  const int C = d.cdim;
+  const float tauf = (float)tau;
+  (void)tauf;
+  // per-axis node factors: fraction k / m, offsets delta = i - RW
+  for (int i = threadIdx.x; i < m * NO; i += blockDim.x) {
+    const int k = i / NO, delta = i % NO - RW;
+    const long long q = ((long long)k << kQ) / m;  // exact: m is a power of two
+    const long long t = q - ((long long)delta << kQ);
+    tq[i] = t * t;
+    const float df = (float)k / (float)m - (float)delta;
+    te[i] = expf(-d.gh2 * df * df);
+  }
   for (int mb = blockIdx.x; mb < nmk; mb += gridDim.x) {
     const int slot = d.marked[mb];
     int bx, by, bz;
     unpack_key(d.bkey[slot], bx, by, bz);
     __syncthreads();
+    __shared__ int nslot[27];
     if (threadIdx.x < 27) {
       const int s = find_block(d, bx + threadIdx.x % 3 - 1, by + (threadIdx.x / 3) % 3 - 1, bz + threadIdx.x / 9 - 1);
-      nbr[threadIdx.x] = (s >= 0 && d.stamp_mark[s] == d.frame) ? d.mark_idx[s] : -1;
+      nslot[threadIdx.x] = s;
+      sm.nbr_mark[threadIdx.x] = (s >= 0 && d.stamp_mark[s] == d.frame) ? d.mark_idx[s] : -1;
+      sm.nbr_bias[threadIdx.x] = (s >= 0 && d.bias) ? d.Wmp[(int64_t)s * d.nw + d.nw - 1].x : 0.f;
     }
     __syncthreads();
-    // is local cell (cx, cy, cz), each in [-1, C), marked?
+    // means of the reachable hinges: local hinge coordinate g in [-RW, nh + RW + 1], stored at g + RW
+    for (int i = threadIdx.x; i < HN * HN * HN; i += blockDim.x) {
+      const int hx = i % HN, hy = (i / HN) % HN, hz = i / (HN * HN);
+      const int g[3] = {hx - RW, hy - RW, hz - RW};
+      int o[3], loc[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        o[a] = g[a] < 0 ? -1 : (g[a] >= nh ? 1 : 0);
+        loc[a] = g[a] - nh * o[a];
+      }
+      const int s = nslot[(o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1)];
+      mus[i] = s >= 0 ? d.Wmp[(int64_t)s * d.nw + (loc[2] * nh + loc[1]) * nh + loc[0]].x : 0.f;
+    }
+    // processed-edge bits of the owned nodes: edge (n, a) when one of its four adjacent cells is marked
     auto marked = [&](int cx, int cy, int cz) -> bool {
-      const int k = nbr[(cz < 0 ? 0 : 1) * 9 + (cy < 0 ? 0 : 1) * 3 + (cx < 0 ? 0 : 1)];
+      const int k = sm.nbr_mark[(cz < 0 ? 0 : 1) * 9 + (cy < 0 ? 0 : 1) * 3 + (cx < 0 ? 0 : 1)];
       if (k < 0) return false;
       const int lx = cx < 0 ? C - 1 : cx, ly = cy < 0 ? C - 1 : cy, lz = cz < 0 ? C - 1 : cz;
       const int bitn = (lz * C + ly) * C + lx;
       return (d.masks[(int64_t)k * d.mask_words + (bitn >> 5)] >> (bitn & 31)) & 1u;
     };
-    Win w;
-    w.lo[0] = w.lo[1] = w.lo[2] = INT_MIN;
-    const int nn = C * C * C;
-    for (int n = threadIdx.x; n < nn; n += blockDim.x) {
-      const int lx = n % C, ly = (n / C) % C, lz = n / (C * C);
-      const int l3[3] = {lx, ly, lz};
-      bool doit[3];
-      bool any = false;
+    for (int n = threadIdx.x; n < C * C * C; n += blockDim.x) {
+      const int l3[3] = {n % C, (n / C) % C, n / (C * C)};
+      int bits = 0;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
-        bool m = false;
+        bool mk = false;
 #pragma unroll
         for (int ib = 0; ib < 2; ++ib)
 #pragma unroll
@@ -701,35 +770,108 @@ __global__ void __launch_bounds__(kT) k_bhm_march(BhmDev d, MarchOut mo) {
             int cc[3] = {l3[0], l3[1], l3[2]};
             cc[b] -= ib;
             cc[c] -= ic;
-            m = m || marked(cc[0], cc[1], cc[2]);
+            mk = mk || marked(cc[0], cc[1], cc[2]);
           }
-        doit[a] = m;
-        any = any || m;
+        bits |= mk ? (1 << a) : 0;
       }
-      if (!any) continue;
-      const int nu[3] = {bx * C + lx, by * C + ly, bz * C + lz};
-      double u0[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) u0[a] = __dmul_rn((double)nu[a], d.inv_m);
-      float la, lb, lv, vv;
-      float3 g;
-      bhm_eval<RW, false, false>(d, w, u0, la, g, vv);
+      doit[n] = (uint8_t)bits;
+    }
+    __syncthreads();
+    // log-odds of every node an edge uses: n itself, and n + e_a for its processed axes
+    for (int n = threadIdx.x; n < C1 * C1 * C1; n += blockDim.x) {
+      const int l3[3] = {n % C1, (n / C1) % C1, n / (C1 * C1)};
+      bool need = l3[0] < C && l3[1] < C && l3[2] < C && doit[(l3[2] * C + l3[1]) * C + l3[0]];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        if (!doit[a]) continue;
-        double u1[3] = {u0[0], u0[1], u0[2]};
-        u1[a] = __dmul_rn((double)(nu[a] + 1), d.inv_m);
-        bhm_eval<RW, false, false>(d, w, u1, lb, g, vv);
+        if (need || l3[a] == 0) continue;
+        int p3[3] = {l3[0], l3[1], l3[2]};
+        p3[a] -= 1;
+        if (p3[0] < C && p3[1] < C && p3[2] < C && (doit[(p3[2] * C + p3[1]) * C + p3[0]] >> a & 1)) need = true;
+      }
+      if (!need) continue;
+      int gl[3], kk[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        gl[a] = l3[a] / m;  // local g0 of the node (l3 >= 0)
+        kk[a] = l3[a] - m * gl[a];
+      }
+      lv[n] = node_logodds<RW>(d, sm, mus, te, tq, HN, gl, kk);
+    }
+    __syncthreads();
+    // edges: crossings of the level set, the point at the linear interpolation, its variance and normal
+    for (int n = threadIdx.x; n < C * C * C; n += blockDim.x) {
+      const int bits = doit[n];
+      if (!bits) continue;
+      const int l3[3] = {n % C, (n / C) % C, n / (C * C)};
+      const int nu[3] = {bx * C + l3[0], by * C + l3[1], bz * C + l3[2]};
+      const float la = lv[(l3[2] * C1 + l3[1]) * C1 + l3[0]];
+#pragma unroll 1
+      for (int a = 0; a < 3; ++a) {
+        if (!(bits >> a & 1)) continue;
+        int p3[3] = {l3[0], l3[1], l3[2]};
+        p3[a] += 1;
+        const float lb = lv[(p3[2] * C1 + p3[1]) * C1 + p3[0]];
         if (((double)la >= tau) == ((double)lb >= tau)) continue;
-        const double t = ((tau - (double)la) / ((double)lb - (double)la));
-        double ui[3] = {u0[0], u0[1], u0[2]};
+        const double t = (tau - (double)la) / ((double)lb - (double)la);
+        double ui[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) ui[e] = __dmul_rn((double)nu[e], d.inv_m);
         ui[a] = __dmul_rn(__dadd_rn((double)nu[a], t), d.inv_m);
-        bhm_eval<RW, true, false>(d, w, ui, lv, g, vv);
-        const float g2 = g.x * g.x + g.y * g.y + g.z * g.z;
+        // the point's features: the two other axes keep the node's tabulated factors, axis a its own
+        const double fl = floor(ui[a]);
+        const int ga = (int)fl;
+        const double fr = __dsub_rn(ui[a], fl);
+        const long long qa = (long long)__dmul_rn(fr, (double)(1 << kQ));
+        const float fa = (float)fr;
+        float ea[NO], da[NO];
+        long long qd[NO];
+#pragma unroll
+        for (int i = 0; i < NO; ++i) {
+          const long long tt = qa - ((long long)(i - RW) << kQ);
+          qd[i] = tt * tt;
+          da[i] = fa - (float)(i - RW);
+          ea[i] = expf(-d.gh2 * da[i] * da[i]);
+        }
+        int gl[3], kk[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          gl[e] = l3[e] / m;
+          kk[e] = l3[e] - m * gl[e];
+        }
+        gl[a] = ga - (a == 0 ? bx : (a == 1 ? by : bz)) * nh;
+        float sl = 0.f, g3[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int iz = 0; iz < NO; ++iz) {
+          const long long dz = a == 2 ? qd[iz] : tq[kk[2] * NO + iz];
+          if (dz > d.r2q) continue;
+          const float ez = a == 2 ? ea[iz] : te[kk[2] * NO + iz];
+          const float fz = a == 2 ? da[iz] : (float)kk[2] / (float)m - (float)(iz - RW);
+#pragma unroll 1
+          for (int iy = 0; iy < NO; ++iy) {
+            const long long dzy = dz + (a == 1 ? qd[iy] : tq[kk[1] * NO + iy]);
+            if (dzy > d.r2q) continue;
+            const float ezy = ez * (a == 1 ? ea[iy] : te[kk[1] * NO + iy]);
+            const float fy = a == 1 ? da[iy] : (float)kk[1] / (float)m - (float)(iy - RW);
+            const float* row = mus + (((gl[2] + iz) * HN) + gl[1] + iy) * HN + gl[0];
+#pragma unroll
+            for (int ix = 0; ix < NO; ++ix) {
+              if (dzy + (a == 0 ? qd[ix] : tq[kk[0] * NO + ix]) > d.r2q) continue;
+              const float fx = a == 0 ? da[ix] : (float)kk[0] / (float)m - (float)(ix - RW);
+              const float mp = row[ix] * (ezy * (a == 0 ? ea[ix] : te[kk[0] * NO + ix]));
+              sl += mp;
+              g3[0] = fmaf(mp, fx, g3[0]);
+              g3[1] = fmaf(mp, fy, g3[1]);
+              g3[2] = fmaf(mp, fz, g3[2]);
+            }
+          }
+        }
+        sl += sm.nbr_bias[((gl[2] >= nh) + 1) * 9 + ((gl[1] >= nh) + 1) * 3 + ((gl[0] >= nh) + 1)];
+        const float gx = d.g2h * g3[0], gy = d.g2h * g3[1], gz = d.g2h * g3[2];
+        const float g2 = gx * gx + gy * gy + gz * gz;
         if (!(g2 > 0.f)) continue;
         const int64_t k = atomicAdd(&d.st->n_out, 1);
         if (k >= mo.cap) continue;
-        const float dl = (float)(tau - (double)lv);
+        const float dl = (float)(tau - (double)sl);
         const float ig = rsqrtf(g2);
         mo.key[k] = ((uint64_t)(nu[2] + kEdgeBias) << 42) | ((uint64_t)(nu[1] + kEdgeBias) << 22) |
                     ((uint64_t)(nu[0] + kEdgeBias) << 2) | (uint64_t)a;
@@ -737,12 +879,20 @@ __global__ void __launch_bounds__(kT) k_bhm_march(BhmDev d, MarchOut mo) {
 #pragma unroll
         for (int e = 0; e < 3; ++e) mo.x[3 * k + e] = __dadd_rn(d.o[e], __dmul_rn(ui[e], d.h));
         mo.var[k] = d.beta * dl * dl / g2;
-        mo.nrm[3 * k] = -g.x * ig;
-        mo.nrm[3 * k + 1] = -g.y * ig;
-        mo.nrm[3 * k + 2] = -g.z * ig;
+        mo.nrm[3 * k] = -gx * ig;
+        mo.nrm[3 * k + 1] = -gy * ig;
+        mo.nrm[3 * k + 2] = -gz * ig;
       }
     }
   }
+}
+
+size_t march_smem(int nh, int rw, int m, int C) {
+  const int NO = 2 * rw + 2, HN = nh + 2 * rw + 2, C1 = C + 1;
+  size_t b = sizeof(MarchSmem);
+  b += (8 - b % 8) % 8;
+  b += (size_t)m * NO * 8 + (size_t)m * NO * 4 + (size_t)HN * HN * HN * 4 + (size_t)C1 * C1 * C1 * 4 + (size_t)C * C * C;
+  return b;
 }
 
 __global__ void k_bhm_gather(MarchOut mo, int64_t n, double* x, float* var, float* nrm, uint64_t* keys) {
@@ -928,7 +1078,7 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   const int rw = (int)(rt >> kQ);
   if (rw > 2 || 2 * rw + 1 > p.block_hinges) return KSDF_ERR_ARG;
   const int cdim = p.block_hinges * p.march_sub;
-  if (cdim > 64) return KSDF_ERR_ARG;
+  if (cdim > 32) return KSDF_ERR_ARG;  // the march keeps (cdim + 1)^3 node values in shared memory
   const int64_t nw = (int64_t)p.block_hinges * p.block_hinges * p.block_hinges + 1;
   if (max_blocks * nw >= (1LL << 31)) return KSDF_ERR_ARG;  // weight indices are 32-bit
   // candidate hinge offsets: those within the feature radius of some point of the unit cell (z-major order)
@@ -1101,10 +1251,20 @@ ksdf_status ksdf_bhm_march(ksdf_bhm* m, int64_t cap, double* x, float* var, floa
     MarchOut mo{ptr<uint64_t>(m->mkey), ptr<uint32_t>(m->mval), ptr<double>(m->mx), ptr<float>(m->mvar),
                 ptr<float>(m->mnrm), m->mcap};
     BHM_CUDA(m, cudaMemsetAsync(reinterpret_cast<char*>(m->state.p) + offsetof(BhmState, n_out), 0, 4, st));
+    const size_t smb = march_smem(m->nh, m->rw, m->p.march_sub, m->cdim);
     switch (m->rw) {
-      case 0: launch(k_bhm_march<0>, kGridStride, kT, 0, st, d, mo); break;
-      case 1: launch(k_bhm_march<1>, kGridStride, kT, 0, st, d, mo); break;
-      default: launch(k_bhm_march<2>, kGridStride, kT, 0, st, d, mo); break;
+      case 0:
+        BHM_CUDA(m, cudaFuncSetAttribute(k_bhm_march<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+        launch(k_bhm_march<0>, kGridStride, kT, smb, st, d, mo);
+        break;
+      case 1:
+        BHM_CUDA(m, cudaFuncSetAttribute(k_bhm_march<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+        launch(k_bhm_march<1>, kGridStride, kT, smb, st, d, mo);
+        break;
+      default:
+        BHM_CUDA(m, cudaFuncSetAttribute(k_bhm_march<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+        launch(k_bhm_march<2>, kGridStride, kT, smb, st, d, mo);
+        break;
     }
     BHM_CUDA(m, cudaGetLastError());
     BHM_CUDA(m, cudaMemcpyAsync(&n, reinterpret_cast<char*>(m->state.p) + offsetof(BhmState, n_out), 4,
