@@ -68,7 +68,7 @@ struct BhmDev {
   float2* Wmp;
   float *A0, *A1, *Bacc;
   const int32_t* cand;  // candidate offsets (dz + 8) << 16 | (dy + 8) << 8 | (dx + 8), z-major
-  int ncand;
+  int ncand, nrounds;  // candidate count and rounds of 32 lanes
   uint32_t* masks;
   BhmState* st;
 };
@@ -348,16 +348,20 @@ __device__ __forceinline__ Sample make_sample(const double u[3], int t) {
   return sm;
 }
 
-// The samples of every ray (one thread per ray): free samples u_j = u_p + (j sigma) du in active blocks, then the
-// hit.  COUNT: cnt[r] = the ray's sample count; otherwise the samples are written from off[r] on.
+// The samples of every ray, a warp per ray: lanes take 32 consecutive free samples u_j = u_p + (j sigma) du at a
+// time, the lowest lane of each group of lanes in the same block looks the block up, and the samples in active
+// blocks are kept in j order; then the hit.  COUNT: cnt[r] = the ray's sample count; otherwise the samples are
+// written from off[r] on.
 template <bool COUNT>
 __global__ void __launch_bounds__(kT) k_bhm_walk(BhmDev d, const double* __restrict__ hits, int64_t R, int64_t* cnt,
                                                  const int64_t* __restrict__ off, Sample* __restrict__ smp) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= R) return;  // whole warps
   double ux[3];
   if (!hit_lattice(d, hits, r, ux)) {
-    if (COUNT) cnt[r] = 0;
+    if (COUNT && lane == 0) cnt[r] = 0;
     return;
   }
   const double dx = __dsub_rn(hits[3 * r], d.p[0]), dy = __dsub_rn(hits[3 * r + 1], d.p[1]),
@@ -373,45 +377,40 @@ __global__ void __launch_bounds__(kT) k_bhm_walk(BhmDev d, const double* __restr
   double du[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) du[a] = __dsub_rn(ux[a], d.up[a]);
-  int cb[3] = {INT_MIN, INT_MIN, INT_MIN};
-  bool cact = false;
   int64_t k = COUNT ? 0 : off[r];
-  for (long long j = 1; j <= jmax; ++j) {
-    const double s = __dmul_rn((double)j, sig);
-    double u[3];
-    int b[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      u[a] = __dadd_rn(d.up[a], __dmul_rn(s, du[a]));
-      b[a] = fdiv((int)floor(u[a]), d.nh);
-    }
-    if (b[0] != cb[0] || b[1] != cb[1] || b[2] != cb[2]) {
-      cb[0] = b[0];
-      cb[1] = b[1];
-      cb[2] = b[2];
-      const int sl = find_block(d, b[0], b[1], b[2]);
-      cact = sl >= 0 && d.active[sl];
-    }
-    if (!cact) {
-      // every sample up to one step before the ray leaves this block is in it: jump there
-      double sx = 1e300;
+  const unsigned lt = (1u << lane) - 1u;
+  for (long long jb = 1; jb <= jmax; jb += 32) {
+    const long long j = jb + lane;
+    const bool valid = j <= jmax;
+    double u[3] = {0.0, 0.0, 0.0};
+    uint64_t key = ~0ull;
+    int b[3] = {0, 0, 0};
+    if (valid) {
+      const double s = __dmul_rn((double)j, sig);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        if (du[a] != 0.0) {
-          const double bnd = (double)(d.nh * (du[a] > 0.0 ? b[a] + 1 : b[a]));
-          sx = fmin(sx, (bnd - d.up[a]) / du[a]);
-        }
+        u[a] = __dadd_rn(d.up[a], __dmul_rn(s, du[a]));
+        b[a] = fdiv((int)floor(u[a]), d.nh);
       }
-      const double jn = floor(sx / sig) - 1.0;
-      if (jn > (double)j) j = jn < (double)jmax ? (long long)jn : jmax;
-      continue;
+      key = pack_key(b[0], b[1], b[2]);
     }
-    if (!COUNT) smp[k] = make_sample(u, 0);
-    ++k;
+    const unsigned grp = __match_any_sync(FULL, key);
+    const int leader = __ffs(grp) - 1;
+    int act = 0;
+    if (valid && lane == leader) {
+      const int sl = find_block(d, b[0], b[1], b[2]);
+      act = sl >= 0 && d.active[sl];
+    }
+    act = __shfl_sync(FULL, act, leader);
+    const bool keep = valid && act;
+    const unsigned bal = __ballot_sync(FULL, keep);
+    if (!COUNT && keep) smp[k + __popc(bal & lt)] = make_sample(u, 0);
+    k += __popc(bal);
   }
-  if (!COUNT) smp[k] = make_sample(ux, 1);
-  ++k;
-  if (COUNT) cnt[r] = k;
+  if (lane == 0) {
+    if (!COUNT) smp[k] = make_sample(ux, 1);
+    if (COUNT) cnt[r] = k + 1;
+  }
 }
 
 // One EM round over the update's samples, a warp per 32 consecutive samples.  FIRST: xi = xi_init, accumulates B
@@ -442,14 +441,13 @@ __global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const Sample* __restric
     if (base + lane < N) my = smp[base + lane];
     const int nv = (int)(N - base < 32 ? N - base : 32);
     for (int s = 0; s < nv; ++s) {
-      int g[3], bse[3], lo[3];
-      long long q[3];
+      int g[3], bse[3], lo[3], q[3];
       float f[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         g[a] = __shfl_sync(FULL, my.g[a], s);
         const uint32_t fq = __shfl_sync(FULL, my.fq[a], s);
-        q[a] = (long long)(fq >> 12);
+        q[a] = (int)(fq >> 12);
         f[a] = (float)fq * 2.3283064365386963e-10f;  // 2^-32
         lo[a] = fdiv(g[a] - RW, nh);
         bse[a] = g[a] - nh * lo[a];
@@ -474,24 +472,28 @@ __global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const Sample* __restric
       float vs = 0.f, ms = 0.f;
 #pragma unroll
       for (int r = 0; r < kMaxRounds; ++r) {
+        idr[r] = -1;
+        phr[r] = 0.f;
+        if (r >= d.nrounds) continue;  // uniform across the warp
         const int cd = cand[r];
         const int ox = (cd & 255) - 8, oy = ((cd >> 8) & 255) - 8, oz = ((cd >> 16) & 255) - 8;
-        const long long tx = q[0] - ((long long)ox << kQ), ty = q[1] - ((long long)oy << kQ),
-                        tz = q[2] - ((long long)oz << kQ);
+        // |fraction - offset|^2 in units of 2^-40, each term one 32 x 32 -> 64-bit product
+        const int tx = q[0] - ox * (1 << kQ), ty = q[1] - oy * (1 << kQ), tz = q[2] - oz * (1 << kQ);
+        const long long D = (long long)tx * tx + (long long)ty * ty + (long long)tz * tz;
         const int lx = bse[0] + ox, ly = bse[1] + oy, lz = bse[2] + oz;
         const int sl = __shfl_sync(FULL, myslot, (lz >= nh) * 4 + (ly >= nh) * 2 + (lx >= nh));
-        const bool ok = cd != kNoCand && tx * tx + ty * ty + tz * tz <= d.r2q && sl >= 0;
+        const bool ok = cd != kNoCand && D <= d.r2q && sl >= 0;
         const float fx = f[0] - (float)ox, fy = f[1] - (float)oy, fz = f[2] - (float)oz;
-        const float phi = expf(-d.gh2 * (fx * fx + fy * fy + fz * fz));
+        const float phi = __expf(-d.gh2 * (fx * fx + fy * fy + fz * fz));
         const int idx = sl * nw + ((lz - (lz >= nh ? nh : 0)) * nh + (ly - (ly >= nh ? nh : 0))) * nh +
                         (lx - (lx >= nh ? nh : 0));
         phr[r] = phi;
         idr[r] = ok ? idx : -1;
         if (!FIRST && ok) {
           const float2 w = d.Wmp[idx];
-          const float P = w.y + Asrc[idx];
-          const float mu = fmaf(w.y, w.x, d.Bacc[idx]) / P;
-          vs = fmaf(phi * phi, 1.0f / P, vs);
+          const float inv = __fdividef(1.0f, w.y + Asrc[idx]);
+          const float mu = fmaf(w.y, w.x, d.Bacc[idx]) * inv;
+          vs = fmaf(phi * phi, inv, vs);
           ms = fmaf(mu, phi, ms);
         }
         if (FIRST) nfeat += (unsigned long long)__popc(__ballot_sync(FULL, ok));
@@ -1043,6 +1045,7 @@ BhmDev dev_view(ksdf_bhm* m) {
   d.Bacc = ptr<float>(m->B);
   d.cand = ptr<int32_t>(m->cand);
   d.ncand = m->ncand;
+  d.nrounds = (m->ncand + 31) / 32;
   d.rw = m->rw;
   d.masks = ptr<uint32_t>(m->masks);
   d.st = ptr<BhmState>(m->state);
@@ -1194,7 +1197,8 @@ ksdf_status ksdf_bhm_update(ksdf_bhm* m, const double* p, const double* hits, in
     int64_t* cnt = ptr<int64_t>(m->scnt);
     int64_t* off = ptr<int64_t>(m->soff);
     BhmState* sdev = ptr<BhmState>(m->state);
-    launch(k_bhm_walk<true>, g, kT, 0, st, d, dh, R, cnt, (const int64_t*)nullptr, (Sample*)nullptr);
+    const unsigned gw = (unsigned)((R * 32 + kT - 1) / kT);  // a warp per ray
+    launch(k_bhm_walk<true>, gw, kT, 0, st, d, dh, R, cnt, (const int64_t*)nullptr, (Sample*)nullptr);
     BHM_CUDA(m, scan_i64(cnt, off, R, reinterpret_cast<int64_t*>(&sdev->n_samples), m->scan_tmp, st));
     unsigned long long ns = 0;
     BHM_CUDA(m, cudaMemcpyAsync(&ns, &sdev->n_samples, 8, cudaMemcpyDeviceToHost, st));
@@ -1205,7 +1209,7 @@ ksdf_status ksdf_bhm_update(ksdf_bhm* m, const double* p, const double* hits, in
       m->scap = want;
     }
     Sample* smp = ptr<Sample>(m->smp);
-    launch(k_bhm_walk<false>, g, kT, 0, st, d, dh, R, (int64_t*)nullptr, (const int64_t*)off, smp);
+    launch(k_bhm_walk<false>, gw, kT, 0, st, d, dh, R, (int64_t*)nullptr, (const int64_t*)off, smp);
     const unsigned ge = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)ns + 255) / 256, 152 * 16));
     const int iters = m->p.em_iters;
     for (int it = 1; it <= iters; ++it) {
