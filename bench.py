@@ -465,9 +465,76 @@ def other_configs(torch, dev, ksdf, main_name):
         del m
     res["city_stream"] = {"workload": "100x100 m city block, %d frames of a 64x2048 LiDAR scan (~125k hits each, range "
                                       "noise 0.02 m) on a closed path, 1M queries per frame in the 40x40x6 m box "
-                                      "around the pose; the front-end occupancy update is not built" % n_frames,
+                                      "around the pose; the GP is fed the raw hits (the BHM front-end runs on the same "
+                                      "frames in city_frontend)" % n_frames,
                           "exact": streams["exact"], "scheduled": streams["scheduled"]}
+    res["city_frontend"] = city_frontend(torch, dev, city, scans)
     return res
+
+
+def city_frontend(torch, dev, city, scans):
+    """The BHM front-end (include/ksdf_bhm.h) on every frame of the city stream: the update (samples along the
+    rays, two EM rounds, tau, marks), the surface points of the marked cells, and the BHM sign of the frame's 1M
+    queries; then the oracle on a bounded sample of one frame."""
+    import time
+
+    from paper_2603_29227_gb300 import bhm, scenes
+
+    m = bhm.BHMap(scenes.CITY_BHM, max_blocks=200_000, max_marked=100_000)
+    rec = {"update_ms": [], "march_ms": [], "sign_ms": [], "samples": [], "features": [], "points": [], "blocks": []}
+    hits_total = 0
+    for f in range(len(scans)):
+        hx = torch.from_numpy(scans[f][0]).to(dev)
+        xq = torch.from_numpy(city.queries(f, 1_000_000)).to(dev)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        m.update(city.poses[f], hx)
+        e[1].record()
+        pts = m.march(device=dev)
+        e[2].record()
+        m.query(xq, bhm.BHM_SIGN)
+        e[3].record()
+        torch.cuda.synchronize()
+        nb, ns, nf = m.size(features=True)
+        hits_total += int(hx.shape[0])
+        rec["update_ms"].append(round(e[0].elapsed_time(e[1]), 3))
+        rec["march_ms"].append(round(e[1].elapsed_time(e[2]), 3))
+        rec["sign_ms"].append(round(e[2].elapsed_time(e[3]), 3))
+        rec["samples"].append(ns)
+        rec["features"].append(nf)
+        rec["points"].append(int(len(pts[0])))
+        rec["blocks"].append(nb)
+    m.sync_status()
+    F = len(scans)
+    tot_ms = sum(rec["update_ms"]) + sum(rec["march_ms"]) + sum(rec["sign_ms"])
+    out = {"workload": "the city stream's %d LiDAR frames through the BHM map (hinge spacing 0.175 m, 8^3 hinges "
+                       "per block, l = 0.11 m, free samples every 0.175 m, 2 EM rounds, marching at 0.0875 m); per "
+                       "frame: update, surface points, sign of the 1M queries" % F,
+           "frames_per_s": F / (tot_ms * 1e-3), "hits_per_s": hits_total / (tot_ms * 1e-3),
+           "samples_per_s_update": sum(rec["samples"]) / (sum(rec["update_ms"]) * 1e-3),
+           "update_ms_mean": float(np.mean(rec["update_ms"])), "march_ms_mean": float(np.mean(rec["march_ms"])),
+           "sign_ms_mean": float(np.mean(rec["sign_ms"])),
+           "samples_per_frame": float(np.mean(rec["samples"])),
+           "features_per_sample": float(np.sum(rec["features"]) / max(1, np.sum(rec["samples"]))),
+           "points_per_frame": float(np.mean(rec["points"])), "blocks_final": rec["blocks"][-1],
+           "tau_final": m.tau, "per_frame": rec}
+    # the oracle on a bounded sample: 1,200 hits of frame 0 within 10 m of the sensor
+    try:
+        from oracle import bhm as obhm
+
+        p, hits = scenes.city_bhm_frame(city, 0, radius=10.0, max_hits=1200)
+        ob = obhm.BHMOracle(obhm.BHMParams(**scenes.CITY_BHM))
+        t0 = time.perf_counter()
+        ob.update(p, hits)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"kind": "oracle", "cores": 1, "sample": "update of 1,200 hits of frame 0 within 10 m "
+                               "(%d samples), binary64 numpy" % ob.last_samples,
+                               "value": ob.last_samples / dt, "unit": "samples/s"}
+    except Exception as exc:  # the oracle is test infrastructure; its absence must not stop the bench
+        out["cpu_baseline"] = {"unavailable": str(exc)[:200]}
+    del m
+    return out
 
 
 def parity_block(w, sel, ref, om, got):

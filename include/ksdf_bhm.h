@@ -115,11 +115,13 @@ enum { KSDF_BHM_LOGODDS = 1u, KSDF_BHM_SIGN = 2u, KSDF_BHM_GRAD = 4u, KSDF_BHM_P
 ksdf_status ksdf_bhm_query(ksdf_bhm* m, const float* xq, int64_t Q, uint32_t out_mask, float* logodds, int8_t* sign,
                            float* grad, float* prob);
 
-/* Introspection (host outputs; synchronise the stream).  *n_blocks allocated blocks; keys[n_blocks] the packed
- * block keys (as ksdf.h's cell keys: three biased 21-bit fields, z most significant), active[n_blocks] (0/1),
- * mu and prec[n_blocks x (n_h^3 + 1)] the weights' means and precisions (block slot order; within a block the
- * hinge (lx, ly, lz) at (lz n_h + ly) n_h + lx and the bias last).  Any pointer may be NULL. */
-ksdf_status ksdf_bhm_size(ksdf_bhm* m, int64_t* n_blocks, int64_t* n_samples_last);
+/* Introspection (host outputs; synchronise the stream).  ksdf_bhm_size: *n_blocks allocated blocks, the number of
+ * samples (free + hits) and of kept hinge features (phi_m >= phi_min with an allocated weight, summed over the
+ * samples; the bias not counted) of the last update; any pointer may be NULL.  ksdf_bhm_get: keys[n_blocks] the
+ * packed block keys (as ksdf.h's cell keys: three biased 21-bit fields, z most significant), active[n_blocks]
+ * (0/1), mu and prec[n_blocks x (n_h^3 + 1)] the weights' means and precisions (block slot order; within a block
+ * the hinge (lx, ly, lz) at (lz n_h + ly) n_h + lx and the bias last).  Any pointer may be NULL. */
+ksdf_status ksdf_bhm_size(ksdf_bhm* m, int64_t* n_blocks, int64_t* n_samples_last, int64_t* n_features_last);
 ksdf_status ksdf_bhm_get(ksdf_bhm* m, uint64_t* keys, uint8_t* active, float* mu, float* prec);
 ksdf_status ksdf_bhm_tau(ksdf_bhm* m, double* tau);
 

@@ -153,6 +153,7 @@ class BHMOracle:
     tau: float = 0.0
     marked: set = field(default_factory=set)       # marked cells of the last update
     last_samples: int = 0
+    last_features: int = 0                          # kept hinge features (no bias) over the last update's samples
 
     def __post_init__(self):
         self.tau = float(self.P.tau_init)
@@ -293,8 +294,10 @@ class BHMOracle:
         # 3. EM on the flattened weight vector
         nw = self.nw
         rows, t = [], []
+        self.last_features = 0
         for u, x, tk in smp:
             f = self.features_u(u, x)
+            self.last_features += sum(1 for _, _, g in f if g is not None)
             rows.append((np.array([s * nw + i for (s, i), _, _ in f], dtype=np.int64),
                          np.array([phi for _, phi, _ in f])))
             t.append(tk)

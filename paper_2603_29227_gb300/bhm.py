@@ -48,7 +48,7 @@ def load():
             "ksdf_bhm_update": [P, P, P, I64],
             "ksdf_bhm_march": [P, I64, P, P, P, P, ctypes.POINTER(I64)],
             "ksdf_bhm_query": [P, P, I64, U32, P, P, P, P],
-            "ksdf_bhm_size": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
+            "ksdf_bhm_size": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
             "ksdf_bhm_get": [P, P, P, P, P],
             "ksdf_bhm_tau": [P, ctypes.POINTER(ctypes.c_double)],
             "ksdf_bhm_sync_status": [P],
@@ -120,13 +120,13 @@ def ksdf_bhm_query(h, xq, Q, out_mask, logodds=None, sign=None, grad=None, prob=
 
 
 def ksdf_bhm_size(h):
-    nb, ns = ctypes.c_int64(0), ctypes.c_int64(0)
-    _check(h, load().ksdf_bhm_size(h, ctypes.byref(nb), ctypes.byref(ns)), "ksdf_bhm_size")
-    return int(nb.value), int(ns.value)
+    nb, ns, nf = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(h, load().ksdf_bhm_size(h, ctypes.byref(nb), ctypes.byref(ns), ctypes.byref(nf)), "ksdf_bhm_size")
+    return int(nb.value), int(ns.value), int(nf.value)
 
 
 def ksdf_bhm_get(h, nw):
-    nb, _ = ksdf_bhm_size(h)
+    nb, _, _ = ksdf_bhm_size(h)
     keys = np.empty(nb, dtype=np.uint64)
     act = np.empty(nb, dtype=np.uint8)
     mu = np.empty((nb, nw), dtype=np.float32)
@@ -210,8 +210,10 @@ class BHMap:
                        out["prob"] if out_mask & BHM_PROB else None)
         return out
 
-    def size(self):
-        return ksdf_bhm_size(self.h)
+    def size(self, features=False):
+        """(allocated blocks, samples of the last update[, hinge features of the last update's samples])."""
+        nb, ns, nf = ksdf_bhm_size(self.h)
+        return (nb, ns, nf) if features else (nb, ns)
 
     def weights(self):
         """(keys, active, mu, prec) of the allocated blocks, numpy, slot order."""

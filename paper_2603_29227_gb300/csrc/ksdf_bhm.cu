@@ -1351,20 +1351,21 @@ ksdf_status ksdf_bhm_query(ksdf_bhm* m, const float* xq, int64_t Q, uint32_t out
   return KSDF_OK;
 }
 
-ksdf_status ksdf_bhm_size(ksdf_bhm* m, int64_t* n_blocks, int64_t* n_samples_last) {
+ksdf_status ksdf_bhm_size(ksdf_bhm* m, int64_t* n_blocks, int64_t* n_samples_last, int64_t* n_features_last) {
   if (!m) return KSDF_ERR_ARG;
   BhmState s;
   BHM_CUDA(m, cudaMemcpyAsync(&s, m->state.p, sizeof(s), cudaMemcpyDeviceToHost, m->stream));
   BHM_CUDA(m, cudaStreamSynchronize(m->stream));
   if (n_blocks) *n_blocks = s.n_blocks;
   if (n_samples_last) *n_samples_last = (int64_t)s.n_samples;
+  if (n_features_last) *n_features_last = (int64_t)s.n_features;
   return KSDF_OK;
 }
 
 ksdf_status ksdf_bhm_get(ksdf_bhm* m, uint64_t* keys, uint8_t* active, float* mu, float* prec) {
   if (!m) return KSDF_ERR_ARG;
   int64_t nb = 0;
-  ksdf_status s = ksdf_bhm_size(m, &nb, nullptr);
+  ksdf_status s = ksdf_bhm_size(m, &nb, nullptr, nullptr);
   if (s != KSDF_OK) return s;
   cudaStream_t st = m->stream;
   if (keys) BHM_CUDA(m, cudaMemcpyAsync(keys, m->bkey.p, 8 * nb, cudaMemcpyDeviceToHost, st));

@@ -2,12 +2,17 @@
 for an external profiler:
 
     python -m paper_2603_29227_gb300.profile_step <workload> [steps] [--autotune]
+    python -m paper_2603_29227_gb300.profile_step city_frontend [frames]
     python -m paper_2603_29227_gb300.profile_step --summarize <ncu launch list .csv>
 
 The second form turns an ncu CSV launch list of such a run (gpu__time_duration.sum, optionally
 dram__bytes_read.sum and dram__bytes_write.sum) into a per-kernel table of its last step, each kernel assigned to
 the stage that launched it (fit, query, adjoint), with the DRAM bytes of the query and adjoint kernels and a digest
 of their sources.
+
+city_frontend runs the BHM front-end (include/ksdf_bhm.h) on the first frames of the city stream -- per frame the
+update, the surface points and the sign of the frame's 1M queries -- on a map sized for a profiler (40,000 blocks,
+about 0.4 GB).
 
 The library must have been built (``__graft_entry__.build()``).  Each step runs ksdf_fit, ksdf_query and
 ksdf_query_backward once, eagerly, on the library's stream; the first step doubles as the warm-up.  The script
@@ -22,6 +27,28 @@ import sys
 import numpy as np
 
 
+def frontend(frames):
+    import torch
+
+    from paper_2603_29227_gb300 import bhm, scenes
+
+    city = scenes.make_city()
+    dev = torch.device("cuda:0")
+    m = bhm.BHMap(scenes.CITY_BHM, max_blocks=40000, max_marked=20000)
+    for f in range(frames):
+        x, _, _ = city.scan(f)
+        hits = torch.from_numpy(x).to(dev)
+        xq = torch.from_numpy(city.queries(f, 1_000_000)).to(dev)
+        m.update(city.poses[f], hits)
+        pts = m.march(device=dev)
+        m.query(xq, bhm.BHM_SIGN)
+        torch.cuda.synchronize()
+        nb, ns, nf = m.size(features=True)
+        print("frame %d hits %d samples %d features %d points %d blocks %d" % (f, len(x), ns, nf, len(pts[0]), nb))
+    m.sync_status()
+    print("ok city_frontend", frames)
+
+
 def main(argv):
     import torch
 
@@ -29,6 +56,8 @@ def main(argv):
 
     args = [a for a in argv if not a.startswith("--")]
     name = args[0] if args else "scale3d"
+    if name == "city_frontend":
+        return frontend(int(args[1]) if len(args) > 1 else 2)
     steps = int(args[1]) if len(args) > 1 else 2
     tune = "--autotune" in argv
     w = scenes.workload(name)

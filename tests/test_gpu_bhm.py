@@ -98,7 +98,9 @@ def two_frames(dev):
         o.update(p, hits)
         m.update(p, torch.from_numpy(hits).to(dev))
         m.sync_status()
-        snaps.append((p, hits, m.size()[1], o.last_samples, m.tau, o.tau))
+        nb, ns, nf = m.size(features=True)
+        assert nf == o.last_features  # the kept-feature decisions are exact
+        snaps.append((p, hits, ns, o.last_samples, m.tau, o.tau))
         if f == 0:
             _compare_maps(o, m)  # after the first frame
     return o, m, snaps
