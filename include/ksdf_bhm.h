@@ -34,8 +34,10 @@
  *   feature kept         |u - g|^2 <= ln(1 / phi_min) / (gamma h^2) decided in fixed point: each fraction
  *                        u - floor(u) truncated to 2^-20, both sides of the comparison in units of 2^-40;
  *   samples of a ray     sensor p, hit x, L = |x - p|, sigma = free_step / L, u_p and u_x the lattice coordinates
- *                        of p and x: free samples u_j = u_p + (j sigma) (u_x - u_p) for j = 1 .. floor((L -
- *                        free_gap) / free_step), kept when their block is active; then the hit itself;
+ *                        of p and x, stepped in 2^-32 fixed point: U_p = rint(2^32 u_p), U_x = rint(2^32 u_x),
+ *                        D = rint((U_x - U_p) sigma) per axis (round half to even), free samples u_j = (U_p + j D)
+ *                        / 2^32 for j = 1 .. floor((L - free_gap) / free_step), kept when their block is active;
+ *                        then the hit itself (at u_x);
  *   marching grid        spacing h / march_sub; cell nu = floor(march_sub u); node nu at lattice coordinate
  *                        nu / march_sub; an update marks the cells of its hits and their 26 neighbours; an edge
  *                        (node nu, axis a) joins nu and nu + e_a and is processed when one of its four adjacent

@@ -19,7 +19,7 @@ What it computes, in the paper's order and notation:
   Sec. IV-A.2 has nothing left to do.  A new weight has the prior N(0, prior_var).
 
   Samples (Sec. IV-A.1, IV-A.2).  For a sensor position p and a hit x, the ray has length L = |x - p|; the free
-  samples are x_j = p + s_j (x - p) for j = 1 .. floor((L - free_gap) / free_step), s_j = j (free_step / L),
+  samples are x_j = p + s_j (x - p) for j = 1 .. floor((L - free_gap) / free_step), s_j = j free_step / L,
   labelled y = -1 (free) and kept when their block is active (the ray pruning of Sec. IV-A.2); the hit itself is
   an occupied sample, y = +1.  Rays are taken in input order, each ray's free samples before its hit.
 
@@ -54,8 +54,10 @@ Readings where the paper is silent or garbled:
     coordinate's fraction u - floor(u) first truncated to 2^-20).  It equals phi_m >= phi_min up to that
     quantisation, and the GPU takes the same integer decision.
   - Lattice coordinates: u = (x - o) / h per axis in binary64 (subtraction, then division), g0 = floor(u),
-    block = floor(g0 / n_h); a sample's lattice coordinates are u_j = u_p + s_j (u_x - u_p) (multiply, then add),
-    with u_p, u_x those of p and x; the positions x_j = o + u_j h are only used for the kernel distances.
+    block = floor(g0 / n_h).  A free sample's lattice coordinates are stepped in 2^-32 fixed point, exactly, in
+    integers: U_p = rint(2^32 u_p), U_x = rint(2^32 u_x), D = rint((U_x - U_p) (free_step / L)) per axis (binary64
+    product, round half to even), U_j = U_p + j D and u_j = U_j / 2^32 -- within 2^-32 j hinge spacings of
+    u_p + s_j (u_x - u_p).  The positions x_j = o + u_j h are only used for the kernel distances.
   - Marching cells: nu = floor(m u) per axis (m a power of two, so m u is exact).
   - The paper does not fix the prior, the free-sample spacing, the gap before the hit, alpha, beta or the
     marching resolution: they are parameters here.  The per-block bias can be switched off (bias_feature = 0):
@@ -255,6 +257,7 @@ class BHMOracle:
         P = self.P
         o, h = P.origin, P.hinge_spacing
         up = self.lattice(p)
+        Up = [int(np.rint(up[a] * 2.0 ** 32)) for a in range(3)]
         out = []
         for xh in hits:
             xh = tuple(float(c) for c in xh)
@@ -262,13 +265,14 @@ class BHMOracle:
             dx, dy, dz = xh[0] - p[0], xh[1] - p[1], xh[2] - p[2]
             L = math.sqrt(dx * dx + dy * dy + dz * dz)
             jmax = int(math.floor((L - P.free_gap) / P.free_step)) if L > 0 else 0
-            if L > 0:
+            if jmax > 0:
                 sig = P.free_step / L
-            du = tuple(ux[a] - up[a] for a in range(3))
+                Ux = [int(np.rint(ux[a] * 2.0 ** 32)) for a in range(3)]
+                D = [int(np.rint(float(Ux[a] - Up[a]) * sig)) for a in range(3)]
             for j in range(1, jmax + 1):
-                s = j * sig
-                u = tuple(up[a] + s * du[a] for a in range(3))
-                b = self.block_of_u(u)
+                U = [Up[a] + j * D[a] for a in range(3)]
+                u = tuple(U[a] / 2.0 ** 32 for a in range(3))
+                b = tuple(_floor_div(U[a] >> 32, P.block_hinges) for a in range(3))
                 sl = self.slot.get(b)
                 if sl is None or not self.active[sl]:
                     continue

@@ -49,6 +49,7 @@ struct BhmState {
 
 struct BhmDev {
   double o[3], h, p[3], up[3];
+  long long Up[3];          // rint(2^32 u_p): the sensor's lattice coordinate in 2^-32 fixed point
   double fstep, fgap;
   double tau_a, tau_b;      // tau <- tau_a tau + tau_b sum_k l(x_k)
   double inv_m;             // 1 / march_sub (exact: a power of two)
@@ -348,9 +349,9 @@ __device__ __forceinline__ Sample make_sample(const double u[3], int t) {
   return sm;
 }
 
-// The samples of every ray, a warp per ray: lanes take 32 consecutive free samples u_j = u_p + (j sigma) du at a
-// time, the lowest lane of each group of lanes in the same block looks the block up, and the samples in active
-// blocks are kept in j order; then the hit.  COUNT: cnt[r] = the ray's sample count; otherwise the samples are
+// The samples of every ray, a warp per ray: lanes take 32 consecutive free samples U_j = U_p + j D (lattice
+// coordinates in 2^-32 fixed point, exact integer steps) at a time, the lowest lane of each group of lanes in the
+// same block looks the block up, and the samples in active blocks are kept in j order; then the hit.  COUNT: cnt[r] = the ray's sample count; otherwise the samples are
 // written from off[r] on.
 template <bool COUNT>
 __global__ void __launch_bounds__(kT) k_bhm_walk(BhmDev d, const double* __restrict__ hits, int64_t R, int64_t* cnt,
@@ -374,23 +375,28 @@ __global__ void __launch_bounds__(kT) k_bhm_walk(BhmDev d, const double* __restr
     jmax = t > 0.0 ? (long long)t : 0;
     sig = __ddiv_rn(d.fstep, L);
   }
-  double du[3];
+  // free samples in 2^-32 fixed point: U_j = U_p + j D, D = rint((U_x - U_p) sigma), exact in integers
+  long long D[3] = {0, 0, 0};
+  if (jmax > 0) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) du[a] = __dsub_rn(ux[a], d.up[a]);
+    for (int a = 0; a < 3; ++a) {
+      const long long Ux = __double2ll_rn(__dmul_rn(ux[a], 4294967296.0));
+      D[a] = __double2ll_rn(__dmul_rn((double)(Ux - d.Up[a]), sig));
+    }
+  }
   int64_t k = COUNT ? 0 : off[r];
   const unsigned lt = (1u << lane) - 1u;
   for (long long jb = 1; jb <= jmax; jb += 32) {
     const long long j = jb + lane;
     const bool valid = j <= jmax;
-    double u[3] = {0.0, 0.0, 0.0};
+    long long U[3] = {0, 0, 0};
     uint64_t key = ~0ull;
     int b[3] = {0, 0, 0};
     if (valid) {
-      const double s = __dmul_rn((double)j, sig);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        u[a] = __dadd_rn(d.up[a], __dmul_rn(s, du[a]));
-        b[a] = fdiv((int)floor(u[a]), d.nh);
+        U[a] = d.Up[a] + j * D[a];
+        b[a] = fdiv((int)(U[a] >> 32), d.nh);
       }
       key = pack_key(b[0], b[1], b[2]);
     }
@@ -404,7 +410,17 @@ __global__ void __launch_bounds__(kT) k_bhm_walk(BhmDev d, const double* __restr
     act = __shfl_sync(FULL, act, leader);
     const bool keep = valid && act;
     const unsigned bal = __ballot_sync(FULL, keep);
-    if (!COUNT && keep) smp[k + __popc(bal & lt)] = make_sample(u, 0);
+    if (!COUNT && keep) {
+      Sample sm;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        sm.g[a] = (int)(U[a] >> 32);
+        sm.fq[a] = (uint32_t)(U[a] & 0xffffffffLL);
+      }
+      sm.t = 0;
+      sm.pad = 0;
+      smp[k + __popc(bal & lt)] = sm;
+    }
     k += __popc(bal);
   }
   if (lane == 0) {
@@ -967,6 +983,7 @@ struct ksdf_bhm {
   int64_t mcap = 0, scap = 0;
   int ncand = 0;
   double up[3] = {0, 0, 0}, p_last[3] = {0, 0, 0};
+  long long Up[3] = {0, 0, 0};
 };
 
 namespace {
@@ -1006,6 +1023,7 @@ BhmDev dev_view(ksdf_bhm* m) {
     d.o[a] = m->p.origin[a];
     d.p[a] = m->p_last[a];
     d.up[a] = m->up[a];
+    d.Up[a] = m->Up[a];
   }
   d.h = m->p.hinge_spacing;
   d.fstep = m->p.free_step;
@@ -1172,6 +1190,7 @@ ksdf_status ksdf_bhm_update(ksdf_bhm* m, const double* p, const double* hits, in
     const double u = (p[a] - m->p.origin[a]) / m->p.hinge_spacing;
     if (!(u > -kLatMax && u < kLatMax)) return berr(m, KSDF_ERR_ARG, "ksdf_bhm_update: sensor position out of range");
     m->up[a] = u;
+    m->Up[a] = std::llrint(u * 4294967296.0);  // round half to even
     m->p_last[a] = p[a];
   }
   const double* dh = hits;

@@ -309,3 +309,74 @@ def test_front_end_feeds_the_back_end(dev):
     o = gp.query(xq, sgn)
     pos = float((o["sdf"] > 0).float().mean())
     assert free_bhm > 0.97 and pos > 0.97, (free_bhm, pos)
+
+
+def test_full_frame_properties(dev):
+    """A whole city frame (~125k hits, ~2.3M samples), checked by properties that hold at any size: tau is the
+    moving average of the hits' log-odds (queried back from the map), the sign is l < tau, and every surface point
+    sits on its edge between nodes on opposite sides of tau, with the variance and normal of the field there."""
+    import torch
+    from paper_2603_29227_gb300 import bhm, scenes
+
+    city = scenes.make_city()
+    P = _params()
+    p, hits = scenes.city_bhm_frame(city, 0)
+    assert len(hits) > 100000
+    m = bhm.BHMap(P, max_blocks=60000)
+    m.update(p, torch.from_numpy(hits).to(dev))
+    x, var, nrm, keys = m.march(device=dev)
+    m.sync_status()
+    nb, ns, nf = m.size(features=True)
+    assert ns > 2_000_000 and nf > 40 * ns
+    tau = m.tau
+    # tau = (1 - alpha) tau0 + alpha mean l(hits): the query's binary32 log-odds at the binary32-rounded hits
+    q = m.query(torch.from_numpy(hits.astype(np.float32)).to(dev), bhm.BHM_LOGODDS | bhm.BHM_SIGN)
+    lh = q["logodds"].double().cpu().numpy()
+    want = (1 - P["tau_alpha"]) * P["tau_init"] + P["tau_alpha"] * lh.mean()
+    assert abs(tau - want) <= 1e-3 * (1.0 + np.abs(lh).mean()), (tau, want)
+    sg = q["sign"].cpu().numpy()
+    far = np.abs(lh - tau) > 1e-4 * (1 + np.abs(lh))
+    assert np.all(sg[far] == np.where(lh[far] < tau, 1, -1))
+    # surface points
+    n = len(x)
+    assert n > 50000
+    rng = np.random.default_rng(5)
+    sel = torch.from_numpy(rng.choice(n, size=4000, replace=False)).to(dev)
+    xs = x[sel].cpu().numpy()
+    ks = keys[sel].cpu().numpy().view(np.uint64).astype(np.uint64)
+    vs = var[sel].double().cpu().numpy()
+    ns_ = nrm[sel].double().cpu().numpy()
+    B = np.uint64(1 << 19)
+    M20 = np.uint64((1 << 20) - 1)
+    axis = (ks & np.uint64(3)).astype(np.int64)
+    nu = np.stack([((ks >> np.uint64(2)) & M20), ((ks >> np.uint64(22)) & M20), ((ks >> np.uint64(42)) & M20)], 1)
+    nu = nu.astype(np.int64) - int(B)
+    step = P["hinge_spacing"] / P["march_sub"]
+    x0 = nu * step
+    d = xs - x0
+    onax = d[np.arange(len(d)), axis]
+    d[np.arange(len(d)), axis] = 0.0
+    assert np.all(np.abs(d) < 1e-9) and np.all(onax >= -1e-9) and np.all(onax <= step + 1e-9)
+    x1 = x0.copy()
+    x1[np.arange(len(x1)), axis] += step
+    la = m.query(torch.from_numpy(x0.astype(np.float32)).to(dev), bhm.BHM_LOGODDS)["logodds"].double().cpu().numpy()
+    lb = m.query(torch.from_numpy(x1.astype(np.float32)).to(dev), bhm.BHM_LOGODDS)["logodds"].double().cpu().numpy()
+    # binary32 query points can fall across a block face (another bias) or a feature threshold (a jump of about
+    # 1e-3 |mu|): leave out points on block faces and values within a margin of tau
+    C = P["block_hinges"] * P["march_sub"]
+    face = np.any(nu % C == 0, axis=1) | ((nu[np.arange(len(nu)), axis] + 1) % C == 0)
+    sure = ~face & (np.abs(la - tau) > 0.05 + 1e-3 * np.abs(la)) & (np.abs(lb - tau) > 0.05 + 1e-3 * np.abs(lb))
+    assert sure.sum() > 1000
+    assert np.all((la[sure] >= tau) != (lb[sure] >= tau))
+    qi = m.query(torch.from_numpy(xs.astype(np.float32)).to(dev), bhm.BHM_LOGODDS | bhm.BHM_GRAD)
+    li = qi["logodds"].double().cpu().numpy()
+    gi = qi["grad"].double().cpu().numpy()
+    gn = np.linalg.norm(gi, axis=1)
+    ok = (gn > 1e-2 * np.median(gn)) & ~face
+    # binary32 positions move the field by about |grad l| 1e-5 m (and, rarely, across a feature threshold);
+    # sigma = sqrt(beta) |tau - l| / |grad l|, the normal -grad l / |grad l|
+    sig_q = np.sqrt(P["beta"]) * np.abs(tau - li) / gn
+    good = np.abs(np.sqrt(vs[ok]) - sig_q[ok]) <= 1e-3 * (1 + sig_q[ok]) + 2e-5
+    assert good.mean() > 0.99, good.mean()
+    goodn = np.max(np.abs(ns_[ok] + gi[ok] / gn[ok, None]), axis=1) < 1e-3
+    assert goodn.mean() > 0.99, goodn.mean()

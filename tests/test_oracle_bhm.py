@@ -234,7 +234,7 @@ def test_samples_lie_on_the_ray_at_the_free_step():
             u, x, t = smp[k]
             assert t == 0
             want = np.asarray(p) + j * P.free_step * d
-            assert np.max(np.abs(np.asarray(x) - want)) < 1e-12
+            assert np.max(np.abs(np.asarray(x) - want)) < 1e-8  # fixed-point stepping: 2^-32 j hinge spacings
             k += 1
         assert smp[k][2] == 1 and np.array_equal(np.asarray(smp[k][1]), xh)
         k += 1
