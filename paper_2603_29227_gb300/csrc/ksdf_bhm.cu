@@ -81,6 +81,14 @@ struct __align__(16) Sample {
   int pad;
 };
 
+// per-ray set-up of the walk (binary64 once per ray, one thread each): the free-sample count, the fixed-point
+// step, and the hit's own sample record (t = -1: the hit was invalid and the ray has no samples)
+struct __align__(16) RayInfo {
+  long long D[3];
+  long long jmax;
+  Sample hit;
+};
+
 constexpr int kMaxRounds = 7;  // candidate rounds of 32 lanes: (2 r + 2)^3 <= 216 offsets for r <= 2
 constexpr int kNoCand = -1;
 
@@ -349,41 +357,56 @@ __device__ __forceinline__ Sample make_sample(const double u[3], int t) {
   return sm;
 }
 
-// The samples of every ray, a warp per ray: lanes take 32 consecutive free samples U_j = U_p + j D (lattice
-// coordinates in 2^-32 fixed point, exact integer steps) at a time, the lowest lane of each group of lanes in the
-// same block looks the block up, and the samples in active blocks are kept in j order; then the hit.  COUNT: cnt[r] = the ray's sample count; otherwise the samples are
-// written from off[r] on.
-template <bool COUNT>
-__global__ void __launch_bounds__(kT) k_bhm_walk(BhmDev d, const double* __restrict__ hits, int64_t R, int64_t* cnt,
-                                                 const int64_t* __restrict__ off, Sample* __restrict__ smp) {
-  constexpr unsigned FULL = 0xffffffffu;
-  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (r >= R) return;  // whole warps
+__global__ void k_bhm_rays(BhmDev d, const double* __restrict__ hits, int64_t R, RayInfo* __restrict__ ri) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  RayInfo o;
+  o.D[0] = o.D[1] = o.D[2] = 0;
+  o.jmax = 0;
   double ux[3];
   if (!hit_lattice(d, hits, r, ux)) {
-    if (COUNT && lane == 0) cnt[r] = 0;
+    o.hit.t = -1;
+    ri[r] = o;
     return;
   }
   const double dx = __dsub_rn(hits[3 * r], d.p[0]), dy = __dsub_rn(hits[3 * r + 1], d.p[1]),
                dz = __dsub_rn(hits[3 * r + 2], d.p[2]);
   const double L = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-  long long jmax = 0;
-  double sig = 0.0;
   if (L > 0.0) {
     const double t = floor(__ddiv_rn(__dsub_rn(L, d.fgap), d.fstep));
-    jmax = t > 0.0 ? (long long)t : 0;
-    sig = __ddiv_rn(d.fstep, L);
+    o.jmax = t > 0.0 ? (long long)t : 0;
   }
   // free samples in 2^-32 fixed point: U_j = U_p + j D, D = rint((U_x - U_p) sigma), exact in integers
-  long long D[3] = {0, 0, 0};
-  if (jmax > 0) {
+  if (o.jmax > 0) {
+    const double sig = __ddiv_rn(d.fstep, L);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const long long Ux = __double2ll_rn(__dmul_rn(ux[a], 4294967296.0));
-      D[a] = __double2ll_rn(__dmul_rn((double)(Ux - d.Up[a]), sig));
+      o.D[a] = __double2ll_rn(__dmul_rn((double)(Ux - d.Up[a]), sig));
     }
   }
+  o.hit = make_sample(ux, 1);
+  ri[r] = o;
+}
+
+// The samples of every ray, a warp per ray: lanes take 32 consecutive free samples U_j = U_p + j D (lattice
+// coordinates in 2^-32 fixed point, exact integer steps) at a time, the lowest lane of each group of lanes in the
+// same block looks the block up, and the samples in active blocks are kept in j order; then the hit.  COUNT:
+// cnt[r] = the ray's sample count; otherwise the samples are written from off[r] on.
+template <bool COUNT>
+__global__ void __launch_bounds__(kT) k_bhm_walk(BhmDev d, const RayInfo* __restrict__ ri, int64_t R, int64_t* cnt,
+                                                 const int64_t* __restrict__ off, Sample* __restrict__ smp) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= R) return;  // whole warps
+  const long long jmax = ri[r].jmax;
+  const int hit_t = ri[r].hit.t;
+  if (hit_t < 0) {
+    if (COUNT && lane == 0) cnt[r] = 0;
+    return;
+  }
+  const long long D[3] = {ri[r].D[0], ri[r].D[1], ri[r].D[2]};
   int64_t k = COUNT ? 0 : off[r];
   const unsigned lt = (1u << lane) - 1u;
   for (long long jb = 1; jb <= jmax; jb += 32) {
@@ -424,7 +447,7 @@ __global__ void __launch_bounds__(kT) k_bhm_walk(BhmDev d, const double* __restr
     k += __popc(bal);
   }
   if (lane == 0) {
-    if (!COUNT) smp[k] = make_sample(ux, 1);
+    if (!COUNT) smp[k] = ri[r].hit;
     if (COUNT) cnt[r] = k + 1;
   }
 }
@@ -979,7 +1002,7 @@ struct ksdf_bhm {
   uint64_t hcap = 0;
   DevBuf hkeys, hvals, bkey, active, stamps, lists, Wmp, A0, A1, B, cand, masks, state;
   DevBuf stage_hits, mkey, mval, mx, mvar, mnrm, sort_tmp, out_stage[4], q_stage[5];
-  DevBuf smp, scnt, soff, scan_tmp;
+  DevBuf smp, scnt, soff, scan_tmp, rays;
   int64_t mcap = 0, scap = 0;
   int ncand = 0;
   double up[3] = {0, 0, 0}, p_last[3] = {0, 0, 0};
@@ -1168,7 +1191,8 @@ ksdf_status ksdf_bhm_destroy(ksdf_bhm* m) {
   if (!m) return KSDF_OK;
   DevBuf* bufs[] = {&m->hkeys, &m->hvals, &m->bkey, &m->active, &m->stamps, &m->lists, &m->Wmp, &m->A0,
                     &m->A1, &m->B, &m->cand, &m->masks, &m->state, &m->stage_hits, &m->mkey, &m->mval,
-                    &m->mx, &m->mvar, &m->mnrm, &m->sort_tmp, &m->smp, &m->scnt, &m->soff, &m->scan_tmp};
+                    &m->mx, &m->mvar, &m->mnrm, &m->sort_tmp, &m->smp, &m->scnt, &m->soff, &m->scan_tmp,
+                    &m->rays};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : m->out_stage) release(b);
   for (DevBuf& b : m->q_stage) release(b);
@@ -1216,8 +1240,11 @@ ksdf_status ksdf_bhm_update(ksdf_bhm* m, const double* p, const double* hits, in
     int64_t* cnt = ptr<int64_t>(m->scnt);
     int64_t* off = ptr<int64_t>(m->soff);
     BhmState* sdev = ptr<BhmState>(m->state);
+    BHM_CUDA(m, ensure(m->rays, sizeof(RayInfo) * (size_t)R));
+    RayInfo* ri = ptr<RayInfo>(m->rays);
+    launch(k_bhm_rays, g, kT, 0, st, d, dh, R, ri);
     const unsigned gw = (unsigned)((R * 32 + kT - 1) / kT);  // a warp per ray
-    launch(k_bhm_walk<true>, gw, kT, 0, st, d, dh, R, cnt, (const int64_t*)nullptr, (Sample*)nullptr);
+    launch(k_bhm_walk<true>, gw, kT, 0, st, d, (const RayInfo*)ri, R, cnt, (const int64_t*)nullptr, (Sample*)nullptr);
     BHM_CUDA(m, scan_i64(cnt, off, R, reinterpret_cast<int64_t*>(&sdev->n_samples), m->scan_tmp, st));
     unsigned long long ns = 0;
     BHM_CUDA(m, cudaMemcpyAsync(&ns, &sdev->n_samples, 8, cudaMemcpyDeviceToHost, st));
@@ -1228,7 +1255,7 @@ ksdf_status ksdf_bhm_update(ksdf_bhm* m, const double* p, const double* hits, in
       m->scap = want;
     }
     Sample* smp = ptr<Sample>(m->smp);
-    launch(k_bhm_walk<false>, gw, kT, 0, st, d, dh, R, (int64_t*)nullptr, (const int64_t*)off, smp);
+    launch(k_bhm_walk<false>, gw, kT, 0, st, d, (const RayInfo*)ri, R, (int64_t*)nullptr, (const int64_t*)off, smp);
     const unsigned ge = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)ns + 255) / 256, 152 * 16));
     const int iters = m->p.em_iters;
     for (int it = 1; it <= iters; ++it) {
