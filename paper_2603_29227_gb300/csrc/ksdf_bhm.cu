@@ -68,8 +68,10 @@ struct BhmDev {
   int32_t *new_list, *touched, *marked;
   float2* Wmp;
   float *A0, *A1, *Bacc;
-  const int32_t* cand;  // candidate offsets (dz + 8) << 16 | (dy + 8) << 8 | (dx + 8), z-major
+  const int32_t* cand;  // candidate offsets (dz + 8) << 16 | (dy + 8) << 8 | (dx + 8), z-major, for the whole cell
   int ncand, nrounds;  // candidate count and rounds of 32 lanes
+  const int32_t* ocand;  // the same per octant of the fraction (8 tables of ostride entries, kNoCand padded)
+  int ostride;           // entries per octant table, a multiple of 32
   uint32_t* masks;
   BhmState* st;
 };
@@ -464,12 +466,11 @@ __global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const Sample* __restric
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int nh = d.nh, nw = d.nw, RW = d.rw;
-  int cand[kMaxRounds];
-#pragma unroll
-  for (int r = 0; r < kMaxRounds; ++r) {
-    const int c = r * 32 + lane;
-    cand[r] = c < d.ncand ? d.cand[c] : kNoCand;
-  }
+  // the candidate offsets of each octant of the fraction (a sample's octant is the top bit of each fraction)
+  __shared__ int s_cand[8 * kMaxRounds * 32];
+  for (int i = threadIdx.x; i < 8 * d.ostride; i += blockDim.x) s_cand[i] = d.ocand[i];
+  __syncthreads();
+  const int nrounds = d.ostride / 32;
   const float* Asrc = src ? d.A1 : d.A0;
   float* Adst = dst ? d.A1 : d.A0;
   int wlo[3] = {INT_MIN, INT_MIN, INT_MIN};
@@ -492,6 +493,7 @@ __global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const Sample* __restric
         bse[a] = g[a] - nh * lo[a];
       }
       const float tb = (float)__shfl_sync(FULL, my.t, s) - 0.5f;
+      const int* oc = s_cand + (((q[2] >> 19) << 2) | ((q[1] >> 19) << 1) | (q[0] >> 19)) * d.ostride;
       if (lo[0] != wlo[0] || lo[1] != wlo[1] || lo[2] != wlo[2]) {
         wlo[0] = lo[0];
         wlo[1] = lo[1];
@@ -513,8 +515,8 @@ __global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const Sample* __restric
       for (int r = 0; r < kMaxRounds; ++r) {
         idr[r] = -1;
         phr[r] = 0.f;
-        if (r >= d.nrounds) continue;  // uniform across the warp
-        const int cd = cand[r];
+        if (r >= nrounds) continue;  // uniform across the warp
+        const int cd = oc[r * 32 + lane];
         const int ox = (cd & 255) - 8, oy = ((cd >> 8) & 255) - 8, oz = ((cd >> 16) & 255) - 8;
         // |fraction - offset|^2 in units of 2^-40, each term one 32 x 32 -> 64-bit product
         const int tx = q[0] - ox * (1 << kQ), ty = q[1] - oy * (1 << kQ), tz = q[2] - oz * (1 << kQ);
@@ -1000,11 +1002,11 @@ struct ksdf_bhm {
   long long r2q = 0;
   int64_t max_blocks = 0, max_marked = 0;
   uint64_t hcap = 0;
-  DevBuf hkeys, hvals, bkey, active, stamps, lists, Wmp, A0, A1, B, cand, masks, state;
+  DevBuf hkeys, hvals, bkey, active, stamps, lists, Wmp, A0, A1, B, cand, ocand, masks, state;
   DevBuf stage_hits, mkey, mval, mx, mvar, mnrm, sort_tmp, out_stage[4], q_stage[5];
   DevBuf smp, scnt, soff, scan_tmp, rays;
   int64_t mcap = 0, scap = 0;
-  int ncand = 0;
+  int ncand = 0, ostride = 0;
   double up[3] = {0, 0, 0}, p_last[3] = {0, 0, 0};
   long long Up[3] = {0, 0, 0};
 };
@@ -1087,6 +1089,8 @@ BhmDev dev_view(ksdf_bhm* m) {
   d.cand = ptr<int32_t>(m->cand);
   d.ncand = m->ncand;
   d.nrounds = (m->ncand + 31) / 32;
+  d.ocand = ptr<int32_t>(m->ocand);
+  d.ostride = m->ostride;
   d.rw = m->rw;
   d.masks = ptr<uint32_t>(m->masks);
   d.st = ptr<BhmState>(m->state);
@@ -1128,6 +1132,27 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   // candidate hinge offsets: those within the feature radius of some point of the unit cell (z-major order)
   std::vector<int32_t> cand;
   const double rr2 = (double)r2q / 1099511627776.0 + 1e-9;
+  // per octant of the fraction ([0, 1/2] or [1/2, 1] per axis): the offsets within reach of that sub-cube
+  std::vector<int32_t> ocand[8];
+  size_t omax = 0;
+  for (int o = 0; o < 8; ++o) {
+    for (int dz = -rw; dz <= rw + 1; ++dz)
+      for (int dy = -rw; dy <= rw + 1; ++dy)
+        for (int dx = -rw; dx <= rw + 1; ++dx) {
+          const int dd[3] = {dx, dy, dz};
+          double g2 = 0.0;
+          for (int a = 0; a < 3; ++a) {
+            const double lo = 0.5 * ((o >> a) & 1), hi = lo + 0.5;
+            const double gap = dd[a] < lo ? lo - dd[a] : (dd[a] > hi ? dd[a] - hi : 0.0);
+            g2 += gap * gap;
+          }
+          if (g2 <= rr2) ocand[o].push_back(((dz + 8) << 16) | ((dy + 8) << 8) | (dx + 8));
+        }
+    omax = std::max(omax, ocand[o].size());
+  }
+  const int ostride = (int)((omax + 31) / 32 * 32);
+  std::vector<int32_t> otab((size_t)8 * ostride, -1);
+  for (int o = 0; o < 8; ++o) std::copy(ocand[o].begin(), ocand[o].end(), otab.begin() + (size_t)o * ostride);
   for (int dz = -rw; dz <= rw + 1; ++dz)
     for (int dy = -rw; dy <= rw + 1; ++dy)
       for (int dx = -rw; dx <= rw + 1; ++dx) {
@@ -1142,6 +1167,7 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   m->rw = rw;
   m->r2q = r2q;
   m->ncand = (int)cand.size();
+  m->ostride = ostride;
   m->nh = p.block_hinges;
   m->nw = p.block_hinges * p.block_hinges * p.block_hinges + 1;
   m->cdim = cdim;
@@ -1166,6 +1192,7 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   al(m->A1, 4 * (size_t)max_blocks * m->nw);
   al(m->B, 4 * (size_t)max_blocks * m->nw);
   al(m->cand, 4 * cand.size());
+  al(m->ocand, 4 * (size_t)8 * ostride);
   al(m->masks, 4 * (size_t)m->max_marked * m->mask_words);
   al(m->state, sizeof(BhmState));
   if (e == cudaSuccess) e = cudaMemsetAsync(m->hkeys.p, 0xff, 8 * cap, m->stream);
@@ -1173,6 +1200,8 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   if (e == cudaSuccess) e = cudaMemsetAsync(m->state.p, 0, sizeof(BhmState), m->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->cand.p, cand.data(), 4 * cand.size(), cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->ocand.p, otab.data(), 4 * otab.size(), cudaMemcpyHostToDevice, m->stream);
   if (e == cudaSuccess) {
     const double tau = p.tau_init;
     e = cudaMemcpyAsync(reinterpret_cast<char*>(m->state.p) + offsetof(BhmState, tau), &tau, sizeof(double),
@@ -1190,7 +1219,7 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
 ksdf_status ksdf_bhm_destroy(ksdf_bhm* m) {
   if (!m) return KSDF_OK;
   DevBuf* bufs[] = {&m->hkeys, &m->hvals, &m->bkey, &m->active, &m->stamps, &m->lists, &m->Wmp, &m->A0,
-                    &m->A1, &m->B, &m->cand, &m->masks, &m->state, &m->stage_hits, &m->mkey, &m->mval,
+                    &m->A1, &m->B, &m->cand, &m->ocand, &m->masks, &m->state, &m->stage_hits, &m->mkey, &m->mval,
                     &m->mx, &m->mvar, &m->mnrm, &m->sort_tmp, &m->smp, &m->scnt, &m->soff, &m->scan_tmp,
                     &m->rays};
   for (DevBuf* b : bufs) release(*b);
