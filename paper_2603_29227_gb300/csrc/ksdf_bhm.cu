@@ -952,38 +952,126 @@ __global__ void k_bhm_gather(MarchOut mo, int64_t n, double* x, float* var, floa
 
 // ---- prediction --------------------------------------------------------------------------------------------
 
-template <int RW>
-__global__ void k_bhm_query(BhmDev d, const float* __restrict__ xq, int64_t Q, uint32_t mask, float* lo, int8_t* sg,
-                            float* gr, float* pr) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Q) return;
-  double u[3];
-  bool ok = true;
+// Prediction, a warp per 32 points: each lane sets up one point (binary64 lattice coordinate, fixed-point and
+// binary32 fraction), then the warp takes the points one at a time, its lanes splitting the point's candidate
+// offsets (the octant table of the EM); sums by warp reduction; each lane writes its own point's outputs.
+template <bool GV>
+__global__ void __launch_bounds__(kT) k_bhm_query(BhmDev d, const float* __restrict__ xq, int64_t Q, uint32_t mask,
+                                                  float* lo_out, int8_t* sg, float* gr, float* pr) {
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ int s_cand[8 * kMaxRounds * 32];
+  for (int i = threadIdx.x; i < 8 * d.ostride; i += blockDim.x) s_cand[i] = d.ocand[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int nh = d.nh, nw = d.nw, RW = d.rw, nrounds = d.ostride / 32;
+  const double tau = d.st->tau;
+  int wlo[3] = {INT_MIN, INT_MIN, INT_MIN};
+  int myslot = -1;
+  for (int64_t base = gw * 32; base < Q; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    int g[3] = {0, 0, 0}, q[3] = {0, 0, 0};
+    float f[3] = {0.f, 0.f, 0.f};
+    bool ok = i < Q;
+    if (ok) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    u[a] = lat((double)xq[3 * i + a], d.o[a], d.h);
-    ok = ok && lat_ok(u[a]);
+      for (int a = 0; a < 3; ++a) {
+        const double u = lat((double)xq[3 * i + a], d.o[a], d.h);
+        ok = ok && lat_ok(u);
+        const double fl = ok ? floor(u) : 0.0;
+        const double fr = ok ? __dsub_rn(u, fl) : 0.0;
+        g[a] = (int)fl;
+        q[a] = (int)__dmul_rn(fr, (double)(1 << kQ));
+        f[a] = (float)fr;
+      }
+      if (!ok) set_status(d.st, ST_NONFINITE);
+    }
+    float my_l = 0.f, my_v = 0.f, my_g[3] = {0.f, 0.f, 0.f};
+    const int nv = (int)(Q - base < 32 ? Q - base : 32);
+    for (int s = 0; s < nv; ++s) {
+      if (!__shfl_sync(FULL, (int)ok, s)) continue;  // uniform
+      int gg[3], qq[3], bse[3], lo[3];
+      float ff[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        gg[a] = __shfl_sync(FULL, g[a], s);
+        qq[a] = __shfl_sync(FULL, q[a], s);
+        ff[a] = __shfl_sync(FULL, f[a], s);
+        lo[a] = fdiv(gg[a] - RW, nh);
+        bse[a] = gg[a] - nh * lo[a];
+      }
+      if (lo[0] != wlo[0] || lo[1] != wlo[1] || lo[2] != wlo[2]) {
+        wlo[0] = lo[0];
+        wlo[1] = lo[1];
+        wlo[2] = lo[2];
+        if (lane < 8) myslot = find_block(d, lo[0] + (lane & 1), lo[1] + ((lane >> 1) & 1), lo[2] + (lane >> 2));
+      }
+      const int* oc = s_cand + (((qq[2] >> 19) << 2) | ((qq[1] >> 19) << 1) | (qq[0] >> 19)) * d.ostride;
+      float sl = 0.f, sv = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+      for (int r = 0; r < kMaxRounds; ++r) {
+        if (r >= nrounds) continue;  // uniform
+        const int cd = oc[r * 32 + lane];
+        const int ox = (cd & 255) - 8, oy = ((cd >> 8) & 255) - 8, oz = ((cd >> 16) & 255) - 8;
+        const int tx = qq[0] - ox * (1 << kQ), ty = qq[1] - oy * (1 << kQ), tz = qq[2] - oz * (1 << kQ);
+        const long long D = (long long)tx * tx + (long long)ty * ty + (long long)tz * tz;
+        const int lx = bse[0] + ox, ly = bse[1] + oy, lz = bse[2] + oz;
+        const int slt = __shfl_sync(FULL, myslot, (lz >= nh) * 4 + (ly >= nh) * 2 + (lx >= nh));
+        if (cd == kNoCand || D > d.r2q || slt < 0) continue;
+        const float fx = ff[0] - (float)ox, fy = ff[1] - (float)oy, fz = ff[2] - (float)oz;
+        const float phi = expf(-d.gh2 * (fx * fx + fy * fy + fz * fz));
+        const int idx = slt * nw + ((lz - (lz >= nh ? nh : 0)) * nh + (ly - (ly >= nh ? nh : 0))) * nh +
+                        (lx - (lx >= nh ? nh : 0));
+        const float2 w = d.Wmp[idx];
+        const float mp = w.x * phi;
+        sl += mp;
+        if (GV) {
+          sx = fmaf(mp, fx, sx);
+          sy = fmaf(mp, fy, sy);
+          sz = fmaf(mp, fz, sz);
+          sv = fmaf(phi * phi, 1.0f / w.y, sv);
+        }
+      }
+      const int bsl = __shfl_sync(FULL, myslot, (bse[2] >= nh) * 4 + (bse[1] >= nh) * 2 + (bse[0] >= nh));
+      if (lane == 0 && d.bias && bsl >= 0) {
+        const float2 w = d.Wmp[(int64_t)bsl * nw + nw - 1];
+        sl += w.x;
+        if (GV) sv += 1.0f / w.y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sl += __shfl_xor_sync(FULL, sl, o);
+        if (GV) {
+          sv += __shfl_xor_sync(FULL, sv, o);
+          sx += __shfl_xor_sync(FULL, sx, o);
+          sy += __shfl_xor_sync(FULL, sy, o);
+          sz += __shfl_xor_sync(FULL, sz, o);
+        }
+      }
+      if (lane == s) {
+        my_l = sl;
+        my_v = sv;
+        my_g[0] = d.g2h * sx;
+        my_g[1] = d.g2h * sy;
+        my_g[2] = d.g2h * sz;
+      }
+    }
+    if (i < Q) {
+      if (!ok) {
+        my_l = my_v = __int_as_float(0x7fc00000);
+        my_g[0] = my_g[1] = my_g[2] = my_l;
+      }
+      if (mask & KSDF_BHM_LOGODDS) lo_out[i] = my_l;
+      if (mask & KSDF_BHM_SIGN) sg[i] = (!ok || (double)my_l < tau) ? (int8_t)1 : (int8_t)-1;
+      if (mask & KSDF_BHM_GRAD) {
+        gr[3 * i] = my_g[0];
+        gr[3 * i + 1] = my_g[1];
+        gr[3 * i + 2] = my_g[2];
+      }
+      if (mask & KSDF_BHM_PROB) pr[i] = 1.0f / (1.0f + expf(-my_l / sqrtf(1.0f + 0.39269908169872414f * my_v)));
+    }
   }
-  float l, v;
-  float3 g;
-  if (!ok) {
-    set_status(d.st, ST_NONFINITE);
-    l = v = __int_as_float(0x7fc00000);
-    g = make_float3(l, l, l);
-  } else {
-    Win w;
-    w.lo[0] = w.lo[1] = w.lo[2] = INT_MIN;
-    if (mask & (KSDF_BHM_GRAD | KSDF_BHM_PROB)) bhm_eval<RW, true, true>(d, w, u, l, g, v);
-    else bhm_eval<RW, false, false>(d, w, u, l, g, v);
-  }
-  if (mask & KSDF_BHM_LOGODDS) lo[i] = l;
-  if (mask & KSDF_BHM_SIGN) sg[i] = (ok && (double)l < d.st->tau) || !ok ? (int8_t)1 : (int8_t)-1;
-  if (mask & KSDF_BHM_GRAD) {
-    gr[3 * i] = g.x;
-    gr[3 * i + 1] = g.y;
-    gr[3 * i + 2] = g.z;
-  }
-  if (mask & KSDF_BHM_PROB) pr[i] = 1.0f / (1.0f + expf(-l / sqrtf(1.0f + 0.39269908169872414f * v)));
 }
 
 }  // namespace
@@ -1407,17 +1495,13 @@ ksdf_status ksdf_bhm_query(ksdf_bhm* m, const float* xq, int64_t Q, uint32_t out
     }
   }
   BhmDev d = dev_view(m);
-  switch (m->rw) {
-#define Q_CASE(RWV)                                                                                    \
-  case RWV:                                                                                            \
-    launch(k_bhm_query<RWV>, nblk(Q), kT, 0, st, d, dq, Q, out_mask & 15u, (float*)dv[0], (int8_t*)dv[1], \
-           (float*)dv[2], (float*)dv[3]);                                                              \
-    break;
-    Q_CASE(0)
-    Q_CASE(1)
-    Q_CASE(2)
-#undef Q_CASE
-  }
+  const unsigned gq = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Q * 32 + kT - 1) / kT / 32 + 1, 152 * 16));
+  if (out_mask & (KSDF_BHM_GRAD | KSDF_BHM_PROB))
+    launch(k_bhm_query<true>, gq, kT, 0, st, d, dq, Q, out_mask & 15u, (float*)dv[0], (int8_t*)dv[1], (float*)dv[2],
+           (float*)dv[3]);
+  else
+    launch(k_bhm_query<false>, gq, kT, 0, st, d, dq, Q, out_mask & 15u, (float*)dv[0], (int8_t*)dv[1],
+           (float*)dv[2], (float*)dv[3]);
   BHM_CUDA(m, cudaGetLastError());
   for (int i = 0; i < 4; ++i)
     if (outs[i] && dv[i] != outs[i])
