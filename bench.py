@@ -472,6 +472,42 @@ def other_configs(torch, dev, ksdf, main_name):
     return res
 
 
+def city_pipeline(torch, dev, city, scans, n_frames):
+    """The paper's per-frame data flow on the first frames of the city stream: the BHM update and its surface points
+    (with sigma_i^2), a fit of the GPs on those points, and the SDF query of the frame's 1M points signed by the BHM.
+    The GPs are refitted from the frame's surface points each frame (no map of earlier frames' points)."""
+    from paper_2603_29227_gb300 import bhm, ksdf, scenes
+
+    m = bhm.BHMap(scenes.CITY_BHM, max_blocks=200_000, max_marked=100_000)
+    gp = ksdf.KernelSDF(dict(city.params, sign_mode=0))
+    ms = {"frontend": [], "fit": [], "query": []}
+    finite = []
+    for f in range(n_frames):
+        hx = torch.from_numpy(scans[f][0]).to(dev)
+        xq = torch.from_numpy(city.queries(f, 1_000_000)).to(dev)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        m.update(city.poses[f], hx)
+        x, var, _, _ = m.march(device=dev)
+        sg = m.query(xq, bhm.BHM_SIGN)["sign"]
+        e[1].record()
+        gp.fit(x, var, None)
+        e[2].record()
+        o = gp.query(xq, sg, ksdf.OUT_SDF | ksdf.OUT_GRAD | ksdf.OUT_VAR_SDF | ksdf.OUT_WINNER | ksdf.OUT_FLAGS)
+        e[3].record()
+        torch.cuda.synchronize()
+        ms["frontend"].append(e[0].elapsed_time(e[1]))
+        ms["fit"].append(e[1].elapsed_time(e[2]))
+        ms["query"].append(e[2].elapsed_time(e[3]))
+        finite.append(float(torch.isfinite(o["sdf"]).float().mean()))
+    m.sync_status()
+    tot = sum(sum(v) for v in ms.values())
+    return {"frames": n_frames, "frames_per_s": n_frames / (tot * 1e-3),
+            "frontend_ms_mean": float(np.mean(ms["frontend"])), "fit_ms_mean": float(np.mean(ms["fit"])),
+            "query_ms_mean": float(np.mean(ms["query"])), "finite_sdf_fraction": float(np.mean(finite))}
+
+
 def city_frontend(torch, dev, city, scans):
     """The BHM front-end (include/ksdf_bhm.h) on every frame of the city stream: the update (samples along the
     rays, two EM rounds, tau, marks), the surface points of the marked cells, and the BHM sign of the frame's 1M
@@ -508,6 +544,7 @@ def city_frontend(torch, dev, city, scans):
     m.sync_status()
     F = len(scans)
     tot_ms = sum(rec["update_ms"]) + sum(rec["march_ms"]) + sum(rec["sign_ms"])
+    pipeline = city_pipeline(torch, dev, city, scans, 20)
     out = {"workload": "the city stream's %d LiDAR frames through the BHM map (hinge spacing 0.175 m, 8^3 hinges "
                        "per block, l = 0.11 m, free samples every 0.175 m, 2 EM rounds, marching at 0.0875 m); per "
                        "frame: update, surface points, sign of the 1M queries" % F,
@@ -518,7 +555,7 @@ def city_frontend(torch, dev, city, scans):
            "samples_per_frame": float(np.mean(rec["samples"])),
            "features_per_sample": float(np.sum(rec["features"]) / max(1, np.sum(rec["samples"]))),
            "points_per_frame": float(np.mean(rec["points"])), "blocks_final": rec["blocks"][-1],
-           "tau_final": m.tau, "per_frame": rec}
+           "tau_final": m.tau, "pipeline": pipeline, "per_frame": rec}
     # the oracle on a bounded sample: 1,200 hits of frame 0 within 10 m of the sensor
     try:
         from oracle import bhm as obhm

@@ -68,9 +68,9 @@ struct BhmDev {
   int32_t *new_list, *touched, *marked;
   float2* Wmp;
   float *A0, *A1, *Bacc;
-  const int32_t* cand;  // candidate offsets (dz + 8) << 16 | (dy + 8) << 8 | (dx + 8), z-major, for the whole cell
-  int ncand, nrounds;  // candidate count and rounds of 32 lanes
-  const int32_t* ocand;  // the same per octant of the fraction (8 tables of ostride entries, kNoCand padded)
+  // candidate hinge offsets (dz + 8) << 16 | (dy + 8) << 8 | (dx + 8), z-major, per octant of the fraction (the
+  // offsets within reach of that half-cell sub-cube): 8 tables of ostride entries, kNoCand padded
+  const int32_t* ocand;
   int ostride;           // entries per octant table, a multiple of 32
   uint32_t* masks;
   BhmState* st;
@@ -1090,11 +1090,11 @@ struct ksdf_bhm {
   long long r2q = 0;
   int64_t max_blocks = 0, max_marked = 0;
   uint64_t hcap = 0;
-  DevBuf hkeys, hvals, bkey, active, stamps, lists, Wmp, A0, A1, B, cand, ocand, masks, state;
+  DevBuf hkeys, hvals, bkey, active, stamps, lists, Wmp, A0, A1, B, ocand, masks, state;
   DevBuf stage_hits, mkey, mval, mx, mvar, mnrm, sort_tmp, out_stage[4], q_stage[5];
   DevBuf smp, scnt, soff, scan_tmp, rays;
   int64_t mcap = 0, scap = 0;
-  int ncand = 0, ostride = 0;
+  int ostride = 0;
   double up[3] = {0, 0, 0}, p_last[3] = {0, 0, 0};
   long long Up[3] = {0, 0, 0};
 };
@@ -1174,9 +1174,6 @@ BhmDev dev_view(ksdf_bhm* m) {
   d.A0 = ptr<float>(m->A0);
   d.A1 = ptr<float>(m->A1);
   d.Bacc = ptr<float>(m->B);
-  d.cand = ptr<int32_t>(m->cand);
-  d.ncand = m->ncand;
-  d.nrounds = (m->ncand + 31) / 32;
   d.ocand = ptr<int32_t>(m->ocand);
   d.ostride = m->ostride;
   d.rw = m->rw;
@@ -1217,8 +1214,6 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   if (cdim > 32) return KSDF_ERR_ARG;  // the march keeps (cdim + 1)^3 node values in shared memory
   const int64_t nw = (int64_t)p.block_hinges * p.block_hinges * p.block_hinges + 1;
   if (max_blocks * nw >= (1LL << 31)) return KSDF_ERR_ARG;  // weight indices are 32-bit
-  // candidate hinge offsets: those within the feature radius of some point of the unit cell (z-major order)
-  std::vector<int32_t> cand;
   const double rr2 = (double)r2q / 1099511627776.0 + 1e-9;
   // per octant of the fraction ([0, 1/2] or [1/2, 1] per axis): the offsets within reach of that sub-cube
   std::vector<int32_t> ocand[8];
@@ -1241,20 +1236,12 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   const int ostride = (int)((omax + 31) / 32 * 32);
   std::vector<int32_t> otab((size_t)8 * ostride, -1);
   for (int o = 0; o < 8; ++o) std::copy(ocand[o].begin(), ocand[o].end(), otab.begin() + (size_t)o * ostride);
-  for (int dz = -rw; dz <= rw + 1; ++dz)
-    for (int dy = -rw; dy <= rw + 1; ++dy)
-      for (int dx = -rw; dx <= rw + 1; ++dx) {
-        auto gap = [](int o) { return o < 0 ? -o : (o > 1 ? o - 1 : 0); };
-        const double g2 = (double)(gap(dx) * gap(dx) + gap(dy) * gap(dy) + gap(dz) * gap(dz));
-        if (g2 <= rr2) cand.push_back(((dz + 8) << 16) | ((dy + 8) << 8) | (dx + 8));
-      }
 
   ksdf_bhm* m = new ksdf_bhm();
   m->p = p;
   m->stream = (cudaStream_t)stream;
   m->rw = rw;
   m->r2q = r2q;
-  m->ncand = (int)cand.size();
   m->ostride = ostride;
   m->nh = p.block_hinges;
   m->nw = p.block_hinges * p.block_hinges * p.block_hinges + 1;
@@ -1279,15 +1266,12 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
   al(m->A0, 4 * (size_t)max_blocks * m->nw);
   al(m->A1, 4 * (size_t)max_blocks * m->nw);
   al(m->B, 4 * (size_t)max_blocks * m->nw);
-  al(m->cand, 4 * cand.size());
   al(m->ocand, 4 * (size_t)8 * ostride);
   al(m->masks, 4 * (size_t)m->max_marked * m->mask_words);
   al(m->state, sizeof(BhmState));
   if (e == cudaSuccess) e = cudaMemsetAsync(m->hkeys.p, 0xff, 8 * cap, m->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->hvals.p, 0xff, 4 * cap, m->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->state.p, 0, sizeof(BhmState), m->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(m->cand.p, cand.data(), 4 * cand.size(), cudaMemcpyHostToDevice, m->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->ocand.p, otab.data(), 4 * otab.size(), cudaMemcpyHostToDevice, m->stream);
   if (e == cudaSuccess) {
@@ -1307,7 +1291,7 @@ ksdf_status ksdf_bhm_create(const ksdf_bhm_params* prm, int64_t max_blocks, int6
 ksdf_status ksdf_bhm_destroy(ksdf_bhm* m) {
   if (!m) return KSDF_OK;
   DevBuf* bufs[] = {&m->hkeys, &m->hvals, &m->bkey, &m->active, &m->stamps, &m->lists, &m->Wmp, &m->A0,
-                    &m->A1, &m->B, &m->cand, &m->ocand, &m->masks, &m->state, &m->stage_hits, &m->mkey, &m->mval,
+                    &m->A1, &m->B, &m->ocand, &m->masks, &m->state, &m->stage_hits, &m->mkey, &m->mval,
                     &m->mx, &m->mvar, &m->mnrm, &m->sort_tmp, &m->smp, &m->scnt, &m->soff, &m->scan_tmp,
                     &m->rays};
   for (DevBuf* b : bufs) release(*b);
