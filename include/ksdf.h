@@ -146,6 +146,17 @@ ksdf_status ksdf_fit(ksdf_ctx* ctx, const double* x, const float* var, const flo
 ksdf_status ksdf_update(ksdf_ctx* ctx, const double* x_new, const float* var_new, const float* normals_new,
                         int64_t S_new, int64_t* n_cells_refit);
 
+/* Streaming update with replacement: the GP training-data buffer update of Sec. IV-C / App. G.  When a region is
+ * marched again, its surface points replace the ones it gave before.  drop (S bytes, host or device, S of the
+ * current model; non-zero = remove) flags model samples to remove.  The samples that stay keep their order and
+ * are renumbered 0..S_kept-1; the S_new new ones follow.  The result is the model ksdf_fit would build from the
+ * kept samples followed by the new ones.  A cell whose training set is unchanged, in members and order, under the
+ * new numbering takes its fit from the previous model.  A cell that lost a member is always fitted, even under a
+ * refit budget.  Arguments, errors and synchronisation as ksdf_update; KSDF_ERR_ARG for a NULL drop or if no
+ * sample would remain. */
+ksdf_status ksdf_update_replace(ksdf_ctx* ctx, const uint8_t* drop, const double* x_new, const float* var_new,
+                                const float* normals_new, int64_t S_new, int64_t* n_cells_refit);
+
 /* Refit scheduling of ksdf_update (the training queue of Sec. IV-C / App. G).  Every cell carries a query counter
  * c0 -- each query that fuses the cell (the cell is one of its bin's K candidates) adds one, capped at 10000 --
  * and training marks c2 -- each update in which the cell's training set changed adds one.  With max_refit > 0 an

@@ -107,6 +107,13 @@ ksdf_status ksdf_bhm_update(ksdf_bhm* m, const double* p, const double* hits, in
 ksdf_status ksdf_bhm_march(ksdf_bhm* m, int64_t cap, double* x, float* var, float* normals, uint64_t* keys,
                            int64_t* n_out);
 
+/* Which of n edge keys (host or device uint64, as ksdf_bhm_march returns them) the last update's marks process:
+ * out[i] = 1 when one of the edge's four adjacent marching cells is marked, else 0 (n bytes, host or device).  A
+ * caller that keeps the back-end's surface samples with their edge keys drops the flagged ones and appends the new
+ * march (ksdf_update_replace): every processed edge then contributes its current point, or none (the GP buffer
+ * update of Sec. IV-C).  Asynchronous unless out is host memory.  KSDF_ERR_ARG for n < 0 or a NULL array. */
+ksdf_status ksdf_bhm_edges_marked(ksdf_bhm* m, const uint64_t* keys, int64_t n, uint8_t* out);
+
 /* out_mask bits of ksdf_bhm_query */
 enum { KSDF_BHM_LOGODDS = 1u, KSDF_BHM_SIGN = 2u, KSDF_BHM_GRAD = 4u, KSDF_BHM_PROB = 8u };
 

@@ -18,7 +18,7 @@ BHM_LOGODDS, BHM_SIGN, BHM_GRAD, BHM_PROB = 1, 2, 4, 8
 # every entry point declared in include/ksdf_bhm.h
 BHM_ABI_FUNCTIONS = ("ksdf_bhm_create", "ksdf_bhm_destroy", "ksdf_bhm_set_stream", "ksdf_bhm_update",
                      "ksdf_bhm_march", "ksdf_bhm_query", "ksdf_bhm_size", "ksdf_bhm_get", "ksdf_bhm_tau",
-                     "ksdf_bhm_sync_status", "ksdf_bhm_last_error")
+                     "ksdf_bhm_sync_status", "ksdf_bhm_last_error", "ksdf_bhm_edges_marked")
 
 
 class ksdf_bhm_params(ctypes.Structure):
@@ -52,6 +52,7 @@ def load():
             "ksdf_bhm_get": [P, P, P, P, P],
             "ksdf_bhm_tau": [P, ctypes.POINTER(ctypes.c_double)],
             "ksdf_bhm_sync_status": [P],
+            "ksdf_bhm_edges_marked": [P, P, I64, P],
             "ksdf_bhm_last_error": [P],
         }
         for name, args in sig.items():
@@ -117,6 +118,10 @@ def ksdf_bhm_query(h, xq, Q, out_mask, logodds=None, sign=None, grad=None, prob=
     _check(h, load().ksdf_bhm_query(h, _ptr(xq, np.float32), int(Q), int(out_mask), _ptr(logodds, np.float32),
                                     _ptr(sign, np.int8), _ptr(grad, np.float32), _ptr(prob, np.float32)),
            "ksdf_bhm_query")
+
+
+def ksdf_bhm_edges_marked(h, keys, n, out):
+    _check(h, load().ksdf_bhm_edges_marked(h, _ptr(keys, np.uint64), int(n), _ptr(out)), "ksdf_bhm_edges_marked")
 
 
 def ksdf_bhm_size(h):
@@ -208,6 +213,18 @@ class BHMap:
         ksdf_bhm_query(self.h, xq, Q, out_mask, out["logodds"] if out_mask & BHM_LOGODDS else None,
                        out["sign"] if out_mask & BHM_SIGN else None, out["grad"] if out_mask & BHM_GRAD else None,
                        out["prob"] if out_mask & BHM_PROB else None)
+        return out
+
+    def edges_marked(self, keys):
+        """uint8 flags: 1 for each edge key (as march returns them) processed by the last update's marks."""
+        n = int(keys.shape[0])
+        if isinstance(keys, np.ndarray):
+            out = np.empty(n, dtype=np.uint8)
+        else:
+            import torch
+
+            out = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        ksdf_bhm_edges_marked(self.h, keys, n, out)
         return out
 
     def size(self, features=False):

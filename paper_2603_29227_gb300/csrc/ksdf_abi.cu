@@ -287,52 +287,137 @@ ksdf_status ksdf_reserve(ksdf_ctx* c, int64_t max_samples, int64_t max_queries) 
   return KSDF_OK;
 }
 
-ksdf_status ksdf_update(ksdf_ctx* c, const double* x_new, const float* var_new, const float* normals_new,
-                        int64_t S_new, int64_t* n_cells_refit) {
+namespace ksdf {
+namespace {
+
+// replace: keep[i] = 1 for a sample that stays (int64, for the scan that numbers the kept samples)
+__global__ void k_keep_flags(const uint8_t* drop, int64_t S, int64_t* keep) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < S) keep[i] = drop[i] ? 0 : 1;
+}
+
+// replace: the kept samples, compacted in their order (newid = exclusive scan of keep)
+__global__ void k_compact_samples(const int64_t* keep, const int64_t* newid, int64_t S, int dim, const double* x,
+                                  const float* var, const float* nrm, double* ux, float* uv, float* un) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S || !keep[i]) return;
+  const int64_t j = newid[i];
+  for (int a = 0; a < dim; ++a) ux[j * dim + a] = x[i * dim + a];
+  uv[j] = var[i];
+  if (nrm)
+    for (int a = 0; a < dim; ++a) un[j * dim + a] = nrm[i * dim + a];
+}
+
+// replace: the current model's training sets in the new sample ids (a warp per cell); a cell that lost a member has
+// no usable fit any more (status EMPTY), so the update fits it again and never keeps its old training set
+__global__ void k_remap_members(const int64_t* ts_off, int64_t G, const int64_t* keep, const int64_t* newid,
+                                int32_t* mgid, int32_t* status) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= G) return;
+  bool lost = false;
+  for (int64_t i = ts_off[g] + lane; i < ts_off[g + 1]; i += 32) {
+    const int32_t id = mgid[i];
+    if (keep[id]) {
+      mgid[i] = (int32_t)newid[id];
+    } else {
+      mgid[i] = -1;
+      lost = true;
+    }
+  }
+  if (__any_sync(0xffffffffu, lost) && lane == 0) status[g] = KSDF_CELL_EMPTY;
+}
+
+ksdf_status update_impl(ksdf_ctx* c, const uint8_t* drop, const double* x_new, const float* var_new,
+                        const float* normals_new, int64_t S_new, int64_t* n_cells_refit) {
   if (!c) return KSDF_ERR_ARG;
   if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "ksdf_update: no model to update (call ksdf_fit first)");
   if (S_new < 0 || (S_new > 0 && !x_new)) return set_err(c, KSDF_ERR_ARG, "ksdf_update: need x_new for S_new > 0");
   Model& m = c->m;
-  if (S_new == 0 && c->sched_max <= 0) {  // nothing new, and no deferred cells without a budget
+  if (S_new == 0 && !drop && c->sched_max <= 0) {  // nothing new, and no deferred cells without a budget
     if (n_cells_refit) *n_cells_refit = 0;
     return KSDF_OK;
   }
   if (S_new > 0 && (normals_new != nullptr) != m.has_normals)
     return set_err(c, KSDF_ERR_ARG, "ksdf_update: normals must be given exactly when the model has normals");
   const int dim = c->p.dim;
-  const int64_t S0 = m.S, S = S0 + S_new;
-  if (S >= (1LL << 31)) return set_err(c, KSDF_ERR_CAPACITY, "ksdf_update: S must stay below 2^31");
-  const void *dx, *dv, *dn;
+  const int64_t S_old = m.S;
+  cudaStream_t st = c->stream;
   ksdf_status s;
+  // the samples that stay: all of them, or those not flagged in `drop`, compacted in their order
+  int64_t S0 = S_old;
+  const int64_t* keep = nullptr;
+  const int64_t* newid = nullptr;
+  if (drop) {
+    const void* dd;
+    if ((s = stage_in(c, 5, drop, (size_t)S_old, &dd))) return s;
+    KSDF_CUDA(c, ensure(c->ws[WS_KEEP], sizeof(int64_t) * (2 * S_old + 2)));
+    int64_t* kp = ptr<int64_t>(c->ws[WS_KEEP]);
+    int64_t* ni = kp + S_old;
+    int64_t* tot = ni + S_old;
+    if (S_old > 0) launch(k_keep_flags, ceil_div(S_old, 256), 256, 0, st, (const uint8_t*)dd, S_old, kp);
+    KSDF_CUDA(c, scan_i64(kp, ni, S_old, tot, c->ws[WS_SCAN], st));
+    KSDF_CUDA(c, cudaMemcpyAsync(&S0, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    KSDF_CUDA(c, cudaStreamSynchronize(st));
+    keep = kp;
+    newid = ni;
+  }
+  const int64_t S = S0 + S_new;
+  if (S >= (1LL << 31)) return set_err(c, KSDF_ERR_CAPACITY, "ksdf_update: S must stay below 2^31");
+  if (S <= 0) return set_err(c, KSDF_ERR_ARG, "ksdf_update_replace: no sample would remain");
+  const void *dx, *dv, *dn;
   if ((s = stage_in(c, 0, x_new, sizeof(double) * S_new * dim, &dx))) return s;
   if ((s = stage_in(c, 1, var_new, sizeof(float) * S_new, &dv))) return s;
   if ((s = stage_in(c, 2, normals_new, sizeof(float) * S_new * dim, &dn))) return s;
-  // the union: the model's samples first (their ids are kept), then the new ones
-  cudaStream_t st = c->stream;
+  // the union: the model's (kept) samples first, in their order, then the new ones
   KSDF_CUDA(c, ensure(c->ws[WS_UX], sizeof(double) * S * dim));
   KSDF_CUDA(c, ensure(c->ws[WS_UV], sizeof(float) * S));
   double* ux = ptr<double>(c->ws[WS_UX]);
   float* uv = ptr<float>(c->ws[WS_UV]);
   float* un = nullptr;
-  KSDF_CUDA(c, cudaMemcpyAsync(ux, m.x.p, sizeof(double) * S0 * dim, cudaMemcpyDeviceToDevice, st));
-  if (S_new > 0)
-    KSDF_CUDA(c, cudaMemcpyAsync(ux + S0 * dim, dx, sizeof(double) * S_new * dim, cudaMemcpyDeviceToDevice, st));
-  KSDF_CUDA(c, cudaMemcpyAsync(uv, m.var_all.p, sizeof(float) * S0, cudaMemcpyDeviceToDevice, st));
-  if (dv) KSDF_CUDA(c, cudaMemcpyAsync(uv + S0, dv, sizeof(float) * S_new, cudaMemcpyDeviceToDevice, st));
-  else if (S_new > 0) KSDF_CUDA(c, cudaMemsetAsync(uv + S0, 0, sizeof(float) * S_new, st));
   if (m.has_normals) {
     KSDF_CUDA(c, ensure(c->ws[WS_UN], sizeof(float) * S * dim));
     un = ptr<float>(c->ws[WS_UN]);
-    KSDF_CUDA(c, cudaMemcpyAsync(un, m.nrm_all.p, sizeof(float) * S0 * dim, cudaMemcpyDeviceToDevice, st));
-    if (S_new > 0)
-      KSDF_CUDA(c, cudaMemcpyAsync(un + S0 * dim, dn, sizeof(float) * S_new * dim, cudaMemcpyDeviceToDevice, st));
   }
+  if (drop) {
+    if (S_old > 0)
+      launch(k_compact_samples, ceil_div(S_old, 256), 256, 0, st, keep, newid, S_old, dim, ptr<double>(m.x),
+             ptr<float>(m.var_all), m.has_normals ? ptr<float>(m.nrm_all) : (const float*)nullptr, ux, uv, un);
+    // the current model's training sets in the new ids, before it becomes the previous model
+    launch(k_remap_members, ceil_div(m.G * 32, 256), 256, 0, st, ptr<int64_t>(m.ts_off), m.G, keep, newid,
+           ptr<int32_t>(m.mgid), ptr<int32_t>(m.status));
+  } else {
+    KSDF_CUDA(c, cudaMemcpyAsync(ux, m.x.p, sizeof(double) * S0 * dim, cudaMemcpyDeviceToDevice, st));
+    KSDF_CUDA(c, cudaMemcpyAsync(uv, m.var_all.p, sizeof(float) * S0, cudaMemcpyDeviceToDevice, st));
+    if (m.has_normals)
+      KSDF_CUDA(c, cudaMemcpyAsync(un, m.nrm_all.p, sizeof(float) * S0 * dim, cudaMemcpyDeviceToDevice, st));
+  }
+  if (S_new > 0)
+    KSDF_CUDA(c, cudaMemcpyAsync(ux + S0 * dim, dx, sizeof(double) * S_new * dim, cudaMemcpyDeviceToDevice, st));
+  if (dv) KSDF_CUDA(c, cudaMemcpyAsync(uv + S0, dv, sizeof(float) * S_new, cudaMemcpyDeviceToDevice, st));
+  else if (S_new > 0) KSDF_CUDA(c, cudaMemsetAsync(uv + S0, 0, sizeof(float) * S_new, st));
+  if (m.has_normals && S_new > 0)
+    KSDF_CUDA(c, cudaMemcpyAsync(un + S0 * dim, dn, sizeof(float) * S_new * dim, cudaMemcpyDeviceToDevice, st));
   // the current model becomes the previous one; the new model reuses the buffers of the one before
   std::swap(c->m, c->m_prev);
   int64_t nref = 0;
   s = fit_model(c, ux, uv, un, S, &c->m_prev, &nref);
   if (n_cells_refit) *n_cells_refit = nref;
   return s;
+}
+
+}  // namespace
+}  // namespace ksdf
+
+ksdf_status ksdf_update(ksdf_ctx* c, const double* x_new, const float* var_new, const float* normals_new,
+                        int64_t S_new, int64_t* n_cells_refit) {
+  return ksdf::update_impl(c, nullptr, x_new, var_new, normals_new, S_new, n_cells_refit);
+}
+
+ksdf_status ksdf_update_replace(ksdf_ctx* c, const uint8_t* drop, const double* x_new, const float* var_new,
+                                const float* normals_new, int64_t S_new, int64_t* n_cells_refit) {
+  if (c && !drop) return set_err(c, KSDF_ERR_ARG, "ksdf_update_replace: need the drop flags (S bytes)");
+  return ksdf::update_impl(c, drop, x_new, var_new, normals_new, S_new, n_cells_refit);
 }
 
 ksdf_status ksdf_set_schedule(ksdf_ctx* c, int64_t max_refit, double eta) {

@@ -1074,6 +1074,34 @@ __global__ void __launch_bounds__(kT) k_bhm_query(BhmDev d, const float* __restr
   }
 }
 
+// whether the last update's marks process edge `key`: one of its four adjacent cells is marked (a thread per key)
+__global__ void k_bhm_edges_marked(BhmDev d, const uint64_t* __restrict__ keys, int64_t n, uint8_t* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t k = keys[i];
+  const int a = (int)(k & 3ull);
+  const int nu[3] = {(int)((k >> 2) & 0xFFFFFull) - (int)kEdgeBias, (int)((k >> 22) & 0xFFFFFull) - (int)kEdgeBias,
+                     (int)((k >> 42) & 0xFFFFFull) - (int)kEdgeBias};
+  uint8_t hit = 0;
+  if (a < 3) {
+    const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+    for (int ib = 0; ib < 2 && !hit; ++ib)
+      for (int ic = 0; ic < 2 && !hit; ++ic) {
+        int cc[3] = {nu[0], nu[1], nu[2]};
+        cc[b] -= ib;
+        cc[c] -= ic;
+        const int bx = fdiv(cc[0], d.cdim), by = fdiv(cc[1], d.cdim), bz = fdiv(cc[2], d.cdim);
+        const int s = find_block(d, bx, by, bz);
+        if (s < 0 || d.stamp_mark[s] != d.frame) continue;
+        const int mk = d.mark_idx[s];
+        if (mk < 0) continue;
+        const int bitn = ((cc[2] - bz * d.cdim) * d.cdim + (cc[1] - by * d.cdim)) * d.cdim + (cc[0] - bx * d.cdim);
+        hit = (uint8_t)((d.masks[(int64_t)mk * d.mask_words + (bitn >> 5)] >> (bitn & 31)) & 1u);
+      }
+  }
+  out[i] = hit;
+}
+
 }  // namespace
 }  // namespace ksdf
 
@@ -1491,6 +1519,37 @@ ksdf_status ksdf_bhm_query(ksdf_bhm* m, const float* xq, int64_t Q, uint32_t out
     if (outs[i] && dv[i] != outs[i])
       BHM_CUDA(m, cudaMemcpyAsync(outs[i], dv[i], bytes[i], cudaMemcpyDeviceToHost, st));
   if (host_out) BHM_CUDA(m, cudaStreamSynchronize(st));
+  return KSDF_OK;
+}
+
+ksdf_status ksdf_bhm_edges_marked(ksdf_bhm* m, const uint64_t* keys, int64_t n, uint8_t* out) {
+  if (!m) return KSDF_ERR_ARG;
+  if (n < 0 || (n > 0 && (!keys || !out))) return berr(m, KSDF_ERR_ARG, "ksdf_bhm_edges_marked: bad n or NULL array");
+  if (n == 0) return KSDF_OK;
+  cudaStream_t st = m->stream;
+  if (m->frame < 0) {  // nothing marked yet
+    if (dev_ptr(out)) BHM_CUDA(m, cudaMemsetAsync(out, 0, (size_t)n, st));
+    else memset(out, 0, (size_t)n);
+    return KSDF_OK;
+  }
+  const uint64_t* dk = keys;
+  if (!dev_ptr(keys)) {
+    BHM_CUDA(m, ensure(m->q_stage[0], 8 * (size_t)n));
+    BHM_CUDA(m, cudaMemcpyAsync(m->q_stage[0].p, keys, 8 * (size_t)n, cudaMemcpyHostToDevice, st));
+    dk = ptr<uint64_t>(m->q_stage[0]);
+  }
+  uint8_t* dout = out;
+  const bool host_out = !dev_ptr(out);
+  if (host_out) {
+    BHM_CUDA(m, ensure(m->q_stage[1], (size_t)n));
+    dout = ptr<uint8_t>(m->q_stage[1]);
+  }
+  launch(k_bhm_edges_marked, nblk(n), kT, 0, st, dev_view(m), dk, n, dout);
+  BHM_CUDA(m, cudaGetLastError());
+  if (host_out) {
+    BHM_CUDA(m, cudaMemcpyAsync(out, dout, (size_t)n, cudaMemcpyDeviceToHost, st));
+    BHM_CUDA(m, cudaStreamSynchronize(st));
+  }
   return KSDF_OK;
 }
 

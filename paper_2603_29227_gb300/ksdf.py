@@ -29,7 +29,8 @@ KERNEL_RBF, KERNEL_MATERN32 = 0, 1  # kernel table of Sec. IV-B.2
 KERNELS = {"rbf": KERNEL_RBF, "matern32": KERNEL_MATERN32}
 
 # every entry point declared in include/ksdf.h
-ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_update", "ksdf_query",
+ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_update",
+                 "ksdf_update_replace", "ksdf_query",
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
                  "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math",
@@ -69,6 +70,7 @@ def load(path: str = LIB_PATH):
         "ksdf_reserve": [P, I64, I64],
         "ksdf_fit": [P, P, P, P, I64],
         "ksdf_update": [P, P, P, P, I64, ctypes.POINTER(I64)],
+        "ksdf_update_replace": [P, P, P, P, P, I64, ctypes.POINTER(I64)],
         "ksdf_query": [P, P, I64, P, U32, P, P, P, P, P, P, P],
         "ksdf_query_f64": [P, P, I64, P, U32, P, P, P, P, P, P, P],
         "ksdf_query_backward": [P, P, I64, P, P, P, P, P, P],
@@ -256,6 +258,17 @@ def ksdf_update(h, x_new, var_new, normals_new, S_new, allow_not_pd=True):
     return rc, int(n.value)
 
 
+def ksdf_update_replace(h, drop, x_new, var_new, normals_new, S_new, allow_not_pd=True):
+    """Remove the samples flagged in drop (S uint8), append S_new samples, refit the changed cells; returns
+    (status, number of cells refitted)."""
+    n = ctypes.c_int64(0)
+    rc = load().ksdf_update_replace(h, _ptr(drop), _ptr(x_new, np.float64), _ptr(var_new, np.float32),
+                                    _ptr(normals_new, np.float32), int(S_new), ctypes.byref(n))
+    if not (rc == KSDF_ERR_NOT_PD and allow_not_pd):
+        _check(h, rc, "ksdf_update_replace")
+    return rc, int(n.value)
+
+
 def ksdf_query(h, xq, Q, sign, out_mask, sdf, grad, var_sdf, var_f, winner, flags, var_grad=None):
     rc = load().ksdf_query(h, _ptr(xq, np.float32), int(Q), _ptr(sign, np.int8), int(out_mask), _ptr(sdf, np.float32),
                            _ptr(grad, np.float32), _ptr(var_sdf, np.float32), _ptr(var_f, np.float32),
@@ -433,6 +446,17 @@ class KernelSDF:
         n_new = int(x_new.shape[0]) if x_new is not None else int(S_new or 0)
         self.fit_status, n = ksdf_update(self.h, x_new, var, normals, n_new)
         self.S += n_new
+        return n
+
+    def update_replace(self, drop, x_new, var=None, normals=None):
+        """Remove the model's samples flagged in `drop` (S uint8: a tensor or array; the kept samples keep their
+        order and are renumbered), append x_new after them, and refit the cells whose training set changed;
+        returns the number of cells refitted."""
+        self._stream()
+        n_new = int(x_new.shape[0]) if x_new is not None else 0
+        n_drop = int(drop.sum())
+        self.fit_status, n = ksdf_update_replace(self.h, drop, x_new, var, normals, n_new)
+        self.S += n_new - n_drop
         return n
 
     def query(self, xq, sign=None, mask=OUT_ALL, f64=False):

@@ -380,3 +380,62 @@ def test_full_frame_properties(dev):
     assert good.mean() > 0.99, good.mean()
     goodn = np.max(np.abs(ns_[ok] + gi[ok] / gn[ok, None]), axis=1) < 1e-3
     assert goodn.mean() > 0.99, goodn.mean()
+
+
+def test_edges_marked_and_persistent_surface_map(dev):
+    """ksdf_bhm_edges_marked flags exactly the oracle's processed edges; and a GP buffer kept across frames by
+    dropping the re-marched edges' points and appending the new march (ksdf_update_replace) holds one point per
+    edge and equals a fresh fit of those points."""
+    import torch
+    from paper_2603_29227_gb300 import bhm, ksdf, scenes
+
+    P = _params()
+    p, hits = _frame(150, f=4, radius=8.0, seed=3)
+    o = _oracle(P)
+    o.update(p, hits)
+    m = bhm.BHMap(P, max_blocks=20000)
+    m.update(p, torch.from_numpy(hits).to(dev))
+    B = 1 << 19
+    edges = sorted(o.marked_edges())
+    kin = np.array([((nu[2] + B) << 42) | ((nu[1] + B) << 22) | ((nu[0] + B) << 2) | a for nu, a in edges],
+                   dtype=np.uint64)
+    rng = np.random.default_rng(2)
+    # other edges near them: shifted by a few cells
+    sh = np.array([((nu[2] + 3 + B) << 42) | ((nu[1] - 2 + B) << 22) | ((nu[0] + 5 + B) << 2) | a
+                   for nu, a in [edges[i] for i in rng.choice(len(edges), 500)]], dtype=np.uint64)
+    marked = {int(k) for k in kin}
+    keys = np.concatenate([kin, sh])
+    got = m.edges_marked(keys)
+    want = np.array([int(k) in marked for k in keys], dtype=np.uint8)
+    assert np.array_equal(got, want)
+    got_dev = m.edges_marked(torch.from_numpy(keys.view(np.int64)).to(dev)).cpu().numpy()
+    assert np.array_equal(got_dev, want)
+
+    # a persistent buffer over three city frames
+    city = scenes.make_city()
+    fm = bhm.BHMap(P, max_blocks=200000)
+    gp = None
+    gkeys = None
+    for f in range(3):
+        p, hits = scenes.city_bhm_frame(city, f, radius=12.0)
+        fm.update(p, torch.from_numpy(hits).to(dev))
+        x, var, _, k = fm.march(device=dev)
+        if gp is None:
+            gp = ksdf.KernelSDF(dict(city.params, sign_mode=0))
+            gp.fit(x, var, None)
+            gkeys, gx, gv = k.clone(), x.clone(), var.clone()
+        else:
+            drop = fm.edges_marked(gkeys)
+            gp.update_replace(drop, x, var)
+            kept = drop == 0
+            gkeys = torch.cat([gkeys[kept], k])
+            gx = torch.cat([gx[kept], x])
+            gv = torch.cat([gv[kept], var])
+    fm.sync_status()
+    assert len(torch.unique(gkeys)) == len(gkeys)  # one point per edge
+    assert gp.S == len(gx)
+    fresh = ksdf.KernelSDF(dict(city.params, sign_mode=0))
+    fresh.fit(gx.contiguous(), gv.contiguous(), None)
+    a1, c1, _ = gp.fit_arrays()
+    a2, c2, _ = fresh.fit_arrays()
+    assert np.array_equal(a1, a2) and np.array_equal(c1, c2)

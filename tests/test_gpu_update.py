@@ -92,3 +92,84 @@ def test_update_arguments():
     assert m.update(_t(w.x[500:500])) == 0  # an empty batch is a no-op
     n = m.update(_t(w.x[500:600]), _t(w.var[500:600]), _t(w.normals[500:600]))
     assert n > 0
+
+
+def _remapped(before, keep):
+    """`before`'s cells with their members renumbered as ksdf_update_replace numbers the kept samples (a dropped
+    member makes the cell unusable for reuse)."""
+    newid = np.cumsum(keep) - 1
+    out = dict(before)
+    mem = before["mem"].copy()
+    st = before["status"].copy()
+    for g in range(len(before["keys"])):
+        m = mem[before["off"][g]:before["off"][g + 1]]
+        if np.any(~keep[m]):
+            st[g] = ksdf.CELL_EMPTY
+        mem[before["off"][g]:before["off"][g + 1]] = np.where(keep[m], newid[m], -1)
+    out["mem"], out["status"] = mem, st
+    return out
+
+
+@pytest.mark.parametrize("name", ["room3d", "plane2d"])
+def test_update_replace_equals_fresh_fit(name):
+    """Dropping samples and appending others (the GP buffer update of Sec. IV-C) gives the model a fresh fit of
+    the kept samples followed by the new ones would give, bit for bit, and refits exactly the changed cells."""
+    w = scenes.workload(name, n_samples=24000 if name == "room3d" else None, n_queries=20011)
+    x, var, nrm = w.x, w.var, w.normals
+    rng = np.random.default_rng(11)
+    # the model first holds 80% of the samples; a region of it is replaced by the rest (a re-marched region)
+    base = np.sort(rng.choice(len(x), size=int(0.8 * len(x)), replace=False))
+    rest = np.setdiff1d(np.arange(len(x)), base)
+    drop = (x[base, 0] > np.quantile(x[:, 0], 0.6)) & (x[base, 0] < np.quantile(x[:, 0], 0.8))
+    keep = ~drop
+    xk = np.concatenate([x[base][keep], x[rest]])
+    vk = np.concatenate([var[base][keep], var[rest]])
+    nk = np.concatenate([nrm[base][keep], nrm[rest]])
+    fresh = ksdf.KernelSDF(w.params)
+    fresh.fit(_t(xk), _t(vk), _t(nk))
+    ref = _state(fresh, w.xq)
+
+    m = ksdf.KernelSDF(w.params)
+    m.fit(_t(x[base]), _t(var[base]), _t(nrm[base]))
+    s0 = _state(m, w.xq)
+    n = m.update_replace(_t(drop.astype(np.uint8)), _t(x[rest]), _t(var[rest]), _t(nrm[rest]))
+    got = _state(m, w.xq)
+    assert m.S == len(xk)
+    for key in ("keys", "status", "off", "mem", "alpha", "chol", "linv", "sdf", "grad", "var_sdf", "var_f", "winner",
+                "flags"):
+        assert np.array_equal(ref[key], got[key]), (name, key)
+    assert n == _changed_cells(_remapped(s0, keep), got), name
+    assert 0 < n < len(got["keys"]), name  # some cells kept their fit
+    # host drop flags, and a drop of nothing, give the same
+    m2 = ksdf.KernelSDF(w.params)
+    m2.fit(_t(x[base]), _t(var[base]), _t(nrm[base]))
+    m2.update_replace(drop.astype(np.uint8), x[rest], var[rest], nrm[rest])
+    assert np.array_equal(_state(m2, w.xq)["chol"], ref["chol"])
+    n0 = m2.update_replace(np.zeros(m2.S, dtype=np.uint8), None)
+    assert n0 == 0 and np.array_equal(_state(m2, w.xq)["sdf"], ref["sdf"])
+
+
+def test_update_replace_under_a_budget_refits_cells_that_lost_samples():
+    """With a refit budget of one cell, every cell that lost a member is still fitted (it cannot keep a training
+    set with a removed sample), and the model stays usable."""
+    w = scenes.workload("room3d", n_samples=24000, n_queries=20011)
+    m = ksdf.KernelSDF(w.params)
+    m.fit(_t(w.x), _t(w.var), _t(w.normals))
+    ksdf.ksdf_set_schedule(m.h, 1, 1e-3)
+    drop = np.zeros(len(w.x), dtype=np.uint8)
+    drop[::97] = 1
+    s0 = _state(m, w.xq)
+    n = m.update_replace(_t(drop), None)
+    got = _state(m, w.xq)
+    lost = _remapped(s0, drop == 0)
+    # cells that lost a member and still exist (a cell whose own samples were all dropped is gone)
+    still = np.isin(s0["keys"], got["keys"])
+    n_lost = int(np.sum((lost["status"] != s0["status"]) & still))
+    assert n >= n_lost > 0
+    gone_lost = int(np.sum((lost["status"] != s0["status"]) & ~still))
+    assert len(got["keys"]) + gone_lost >= len(s0["keys"]) - np.sum(~still)
+    _, _, refit = ksdf.ksdf_get_schedule(m.h)
+    assert int(refit.sum()) == n
+    assert np.all(np.isfinite(got["sdf"][got["winner"] >= 0]))
+    kept = np.nonzero(drop == 0)[0]
+    assert np.all(np.isin(got["mem"], np.arange(len(kept))))
