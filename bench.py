@@ -473,15 +473,17 @@ def other_configs(torch, dev, ksdf, main_name):
 
 
 def city_pipeline(torch, dev, city, scans, n_frames):
-    """The paper's per-frame data flow on the first frames of the city stream: the BHM update and its surface points
-    (with sigma_i^2), a fit of the GPs on those points, and the SDF query of the frame's 1M points signed by the BHM.
-    The GPs are refitted from the frame's surface points each frame (no map of earlier frames' points)."""
+    """The paper's data flow on the first frames of the city stream, with a persistent map: per frame, the BHM
+    update and its surface points (with sigma_i^2); the GP buffer update -- the points of re-marched edges are
+    replaced by the new march (ksdf_bhm_edges_marked, ksdf_update_replace), every changed cell refitted -- and the
+    SDF query of the frame's 1M points signed by the BHM."""
     from paper_2603_29227_gb300 import bhm, ksdf, scenes
 
     m = bhm.BHMap(scenes.CITY_BHM, max_blocks=200_000, max_marked=100_000)
     gp = ksdf.KernelSDF(dict(city.params, sign_mode=0))
-    ms = {"frontend": [], "fit": [], "query": []}
-    finite = []
+    ms = {"frontend": [], "gp_update": [], "query": []}
+    finite, refit, S = [], [], []
+    gkeys = None
     for f in range(n_frames):
         hx = torch.from_numpy(scans[f][0]).to(dev)
         xq = torch.from_numpy(city.queries(f, 1_000_000)).to(dev)
@@ -489,23 +491,34 @@ def city_pipeline(torch, dev, city, scans, n_frames):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record()
         m.update(city.poses[f], hx)
-        x, var, _, _ = m.march(device=dev)
+        x, var, _, k = m.march(device=dev)
         sg = m.query(xq, bhm.BHM_SIGN)["sign"]
         e[1].record()
-        gp.fit(x, var, None)
+        if gkeys is None:
+            gp.fit(x, var, None)
+            n = len(x)
+            gkeys = k.clone()
+        else:
+            drop = m.edges_marked(gkeys)
+            n = gp.update_replace(drop, x, var)
+            gkeys = torch.cat([gkeys[drop == 0], k])
         e[2].record()
         o = gp.query(xq, sg, ksdf.OUT_SDF | ksdf.OUT_GRAD | ksdf.OUT_VAR_SDF | ksdf.OUT_WINNER | ksdf.OUT_FLAGS)
         e[3].record()
         torch.cuda.synchronize()
         ms["frontend"].append(e[0].elapsed_time(e[1]))
-        ms["fit"].append(e[1].elapsed_time(e[2]))
+        ms["gp_update"].append(e[1].elapsed_time(e[2]))
         ms["query"].append(e[2].elapsed_time(e[3]))
         finite.append(float(torch.isfinite(o["sdf"]).float().mean()))
+        refit.append(int(n))
+        S.append(int(gp.S))
     m.sync_status()
     tot = sum(sum(v) for v in ms.values())
     return {"frames": n_frames, "frames_per_s": n_frames / (tot * 1e-3),
-            "frontend_ms_mean": float(np.mean(ms["frontend"])), "fit_ms_mean": float(np.mean(ms["fit"])),
-            "query_ms_mean": float(np.mean(ms["query"])), "finite_sdf_fraction": float(np.mean(finite))}
+            "frontend_ms_mean": float(np.mean(ms["frontend"])),
+            "gp_update_ms_mean": float(np.mean(ms["gp_update"][1:])), "query_ms_mean": float(np.mean(ms["query"])),
+            "cells_refit_mean": float(np.mean(refit[1:])), "gp_samples_final": S[-1],
+            "finite_sdf_fraction": float(np.mean(finite))}
 
 
 def city_frontend(torch, dev, city, scans):
