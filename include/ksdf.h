@@ -256,6 +256,10 @@ const char* ksdf_last_error(const ksdf_ctx* ctx);
 
 /* ---- introspection of the fitted model (host outputs; synchronise the stream) ---- */
 
+/* Number of samples S the model holds (after ksdf_fit, ksdf_update, ksdf_update_replace or ksdf_load); host output,
+ * no synchronisation.  KSDF_ERR_NOT_FITTED without a model. */
+ksdf_status ksdf_model_samples(ksdf_ctx* ctx, int64_t* S);
+
 /* Number of cells G and of training-set members (sum of N_g). */
 ksdf_status ksdf_model_size(ksdf_ctx* ctx, int64_t* n_cells, int64_t* n_members);
 /* keys[G] (packed (cz,cy,cx) as three biased 21-bit fields, z most significant), status[G], ts_off[G+1],

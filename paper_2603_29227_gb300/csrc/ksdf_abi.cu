@@ -414,6 +414,13 @@ ksdf_status ksdf_update(ksdf_ctx* c, const double* x_new, const float* var_new, 
   return ksdf::update_impl(c, nullptr, x_new, var_new, normals_new, S_new, n_cells_refit);
 }
 
+ksdf_status ksdf_model_samples(ksdf_ctx* c, int64_t* S) {
+  if (!c || !S) return KSDF_ERR_ARG;
+  if (!c->fitted) return set_err(c, KSDF_ERR_NOT_FITTED, "ksdf_model_samples: no model");
+  *S = c->m.S;
+  return KSDF_OK;
+}
+
 ksdf_status ksdf_update_replace(ksdf_ctx* c, const uint8_t* drop, const double* x_new, const float* var_new,
                                 const float* normals_new, int64_t S_new, int64_t* n_cells_refit) {
   if (c && !drop) return set_err(c, KSDF_ERR_ARG, "ksdf_update_replace: need the drop flags (S bytes)");

@@ -30,7 +30,7 @@ KERNELS = {"rbf": KERNEL_RBF, "matern32": KERNEL_MATERN32}
 
 # every entry point declared in include/ksdf.h
 ABI_FUNCTIONS = ("ksdf_create", "ksdf_destroy", "ksdf_set_stream", "ksdf_reserve", "ksdf_fit", "ksdf_update",
-                 "ksdf_update_replace", "ksdf_query",
+                 "ksdf_update_replace", "ksdf_model_samples", "ksdf_query",
                  "ksdf_query_f64", "ksdf_query_backward", "ksdf_sync_status", "ksdf_last_error", "ksdf_model_size",
                  "ksdf_get_cells", "ksdf_get_fit", "ksdf_bin", "ksdf_candidates", "ksdf_profile", "ksdf_profile_read",
                  "ksdf_fit_gp_noalloc", "ksdf_autotune", "ksdf_autotune_tables", "ksdf_device_math",
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
         "ksdf_fit": [P, P, P, P, I64],
         "ksdf_update": [P, P, P, P, I64, ctypes.POINTER(I64)],
         "ksdf_update_replace": [P, P, P, P, P, I64, ctypes.POINTER(I64)],
+        "ksdf_model_samples": [P, ctypes.POINTER(I64)],
         "ksdf_query": [P, P, I64, P, U32, P, P, P, P, P, P, P],
         "ksdf_query_f64": [P, P, I64, P, U32, P, P, P, P, P, P, P],
         "ksdf_query_backward": [P, P, I64, P, P, P, P, P, P],
@@ -454,9 +455,10 @@ class KernelSDF:
         returns the number of cells refitted."""
         self._stream()
         n_new = int(x_new.shape[0]) if x_new is not None else 0
-        n_drop = int(drop.sum())
         self.fit_status, n = ksdf_update_replace(self.h, drop, x_new, var, normals, n_new)
-        self.S += n_new - n_drop
+        S = ctypes.c_int64(0)
+        _check(self.h, load().ksdf_model_samples(self.h, ctypes.byref(S)), "ksdf_model_samples")
+        self.S = int(S.value)
         return n
 
     def query(self, xq, sign=None, mask=OUT_ALL, f64=False):
