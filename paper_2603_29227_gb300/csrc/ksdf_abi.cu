@@ -351,8 +351,10 @@ ksdf_status update_impl(ksdf_ctx* c, const uint8_t* drop, const double* x_new, c
   if (drop) {
     const void* dd;
     if ((s = stage_in(c, 5, drop, (size_t)S_old, &dd))) return s;
-    KSDF_CUDA(c, ensure(c->ws[WS_KEEP], sizeof(int64_t) * (2 * S_old + 2)));
-    int64_t* kp = ptr<int64_t>(c->ws[WS_KEEP]);
+    // the keep flags and new ids live in the query's coarse-order workspace: nothing else uses it before the
+    // refit below has consumed them
+    KSDF_CUDA(c, ensure(c->ws[WS_BORD], sizeof(int64_t) * (2 * S_old + 2)));
+    int64_t* kp = ptr<int64_t>(c->ws[WS_BORD]);
     int64_t* ni = kp + S_old;
     int64_t* tot = ni + S_old;
     if (S_old > 0) launch(k_keep_flags, ceil_div(S_old, 256), 256, 0, st, (const uint8_t*)dd, S_old, kp);

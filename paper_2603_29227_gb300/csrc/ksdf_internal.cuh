@@ -231,7 +231,7 @@ struct ksdf_ctx {
   std::vector<ksdf::FitClassCfg> fit_cls;  // the fit's size classes (empty: the default table); ksdf_autotune
   // workspaces
   ksdf::DevBuf status_word;       // uint32 device status
-  ksdf::DevBuf ws[33];            // general workspaces (grow only), indexed by role
+  ksdf::DevBuf ws[32];            // general workspaces (grow only), indexed by role
   int qt_chunks = 128;            // query tile shapes (ksdf_autotune_query): phase A's shared-memory budget in
   int qt_tc_small = 96;           // chunks of 8 samples, and the largest cell of phase B's 128-column TMEM class
   int64_t sched_max = 0;          // refit budget of ksdf_update (cells per update; 0 = every changed cell)
@@ -350,8 +350,7 @@ enum WsRole {
   WS_UN = 28,
   WS_BRICK = 29,  // brick build: rank of each cell within its brick
   WS_SCHED = 30,  // refit scheduling: priority keys, cell ids, changed flags, previous ids
-  WS_BORD = 31,   // query bins in coarse spatial order: coarse keys, ranks, order; bucket counts
-  WS_KEEP = 32    // update with replacement: keep flags and new ids of the model's samples
+  WS_BORD = 31    // query bins in coarse spatial order: coarse keys, ranks, order; bucket counts
 };
 constexpr int kQueryCounterCap = 10000;  // cap of the per-cell query counter (App. G)
 
