@@ -240,7 +240,7 @@ ksdf_status ksdf_query_f64(ksdf_ctx* ctx, const double* xq, int64_t Q, const int
                            double* sdf, double* grad, double* var_sdf, double* var_f, double* var_grad,
                            int32_t* winner, uint32_t* flags);
 
-/* Adjoint of the query (the spec differentiation path): given the cotangents d_sdf[Q] and
+/* Adjoint of the query (the differentiation path): given the cotangents d_sdf[Q] and
  * (optionally, may be NULL) d_grad[Q x dim] of the sdf and grad outputs, write d_xq[Q x dim] (overwritten)
  * and ADD the sample-position gradient into d_x[S x dim] (S of the last fit, ids in the fit's order).
  * winner is the array the forward query returned for the same xq and sign.  Per-cell recomputation:
