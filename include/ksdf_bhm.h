@@ -94,7 +94,8 @@ ksdf_status ksdf_bhm_set_stream(ksdf_bhm* m, void* stream);
 
 /* One scan (Sec. IV-A.1 to IV-A.4): sensor position p (3 host doubles) and R hits (R x 3 float64, host or device).
  * Activates and allocates blocks, generates the samples, runs em_iters EM rounds, updates tau from the hits and
- * marks the marching cells of the hits.  Asynchronous on the map's stream.  Device-detected failures go to the
+ * marks the marching cells of the hits.  Runs on the map's stream and synchronises it once, after counting the
+ * samples (the count sizes the sample buffer).  Device-detected failures go to the
  * status word: a hit that is NaN/Inf or out of range (KSDF_ERR_NONFINITE; that hit is skipped), more blocks than
  * max_blocks or marked blocks than max_marked (KSDF_ERR_CAPACITY; the blocks beyond are not created or not
  * marched).  R = 0 is allowed (tau is then unchanged).  KSDF_ERR_ARG for a NULL p or R < 0. */
