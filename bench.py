@@ -14,7 +14,10 @@ tensor cores and HBM, from algorithmic counts of this run's model and queries, a
 live by the probes of libksdf_peaks.so), the per-kernel rooflines and stage times, the plain FP64 GPU
 query of the same inputs, the end-to-end rate through the C ABI with pinned host buffers, the CPU FP64
 oracle on a bounded sample (cpu_baseline) with a parity check of this run's outputs on that sample, SM
-clocks sampled during the timed region, the number of kernel launches, and the other workloads.
+clocks sampled during the timed region, the number of kernel launches, and the other workloads.  Among them,
+city_frontend runs the BHM front-end (Sec. IV-A) over the city stream's 100 LiDAR frames (update, surface
+points, sign), and its pipeline the paper's per-frame data flow with a persistent GP map: the BHM's surface
+points replace the re-marched ones in the GPs, and the SDF query is signed by the BHM.
 
 --impl reference times the CPU FP64 oracle itself (the reference arm; the paper ships no implementation
 to run) with the same per-step protocol as cpu_baseline.
