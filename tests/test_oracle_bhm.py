@@ -390,3 +390,40 @@ def test_scanned_plane_gives_an_upward_surface_at_the_ground():
     assert sel.sum() > 50
     assert abs(np.median(X[sel, 2])) < 0.08
     assert np.median(N[sel, 2]) > 0.9
+
+
+def test_surface_variance_is_the_first_order_distance_to_the_level_set():
+    """Eq. surface_point_uncertainty comes from a first-order Taylor step: sqrt(sigma^2 / beta) = |tau - l(x_i)| /
+    |grad l(x_i)| is the distance from x_i to the tau level set along the gradient.  Found here by bisection on the
+    field itself (bias off, so the field has no jumps at block faces); the rest is the field's curvature, second
+    order in sigma."""
+    P = bhm.BHMParams(tau_alpha=1.0, bias_feature=0, beta=2.0)
+    o = bhm.BHMOracle(P)
+    rng = np.random.default_rng(21)
+    p = np.array([0.3, 0.2, 1.8])
+    n = 400
+    ang = rng.uniform(0, 2 * np.pi, n)
+    r = np.sqrt(rng.uniform(4.0, 9.0, n))
+    hits = np.stack([p[0] + r * np.cos(ang), p[1] + r * np.sin(ang), rng.normal(0, 0.02, n)], 1)
+    o.update(p, hits)
+    X, V, _, _ = o.march()
+    rel = []
+    for k in range(0, len(X), 9):
+        x = X[k]
+        _, g, _ = o.eval_u(o.lattice(x), tuple(x))
+        d = g / np.linalg.norm(g)
+        sig = math.sqrt(V[k] / P.beta)
+        if not 1e-5 < sig < 0.02:
+            continue
+        f = lambda t: o.eval_u(o.lattice(x + t * d), tuple(x + t * d))[0] - o.tau  # noqa: E731
+        lo, hi = -3 * sig - 1e-4, 3 * sig + 1e-4
+        assert f(lo) * f(hi) <= 0
+        for _ in range(40):
+            mid = 0.5 * (lo + hi)
+            if f(lo) * f(mid) <= 0:
+                hi = mid
+            else:
+                lo = mid
+        rel.append(abs(abs(0.5 * (lo + hi)) - sig) / sig)
+    assert len(rel) > 40
+    assert np.median(rel) < 0.02 and np.quantile(rel, 0.9) < 0.1, (np.median(rel), np.quantile(rel, 0.9))
