@@ -11,11 +11,12 @@
 //   per block         packed key, active flag, the frame stamps of the touched / marked lists, its marked-cell index
 //   masks             one bit per marching cell of each marked block ((n_h m)^3 bits)
 //   samples           one 32-byte record per sample of the running update (lattice cell, 32-bit fraction, label)
-// An update walks every ray twice (one thread per ray; blocks without a hit are skipped a whole block at a time):
-// once to count its samples, once, after a scan of the counts, to write them.  Each EM round is then one launch
-// in which a warp takes 32 consecutive samples and, for each, splits the sample's candidate hinges (the offsets a
-// point of the cell can reach, tabulated once per map) across its lanes: the M-step is a warp reduction and the
-// E-step's atomics of one warp instruction fall on neighbouring weights.
+// An update sets up each ray once (one thread per ray, binary64: its sample count and fixed-point step), then walks
+// every ray twice (a warp per ray, 32 samples per step, integers only): once to count its samples, once, after a
+// scan of the counts, to write them.  Each EM round is then one launch in which a warp takes 32 consecutive samples
+// and, for each, splits the sample's candidate hinges (the offsets a point of that octant of the cell can reach,
+// tabulated once per map) across its lanes: the M-step is a warp reduction and the E-step's atomics of one warp
+// instruction fall on neighbouring weights.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(kT) k_bhm_em(BhmDev d, const Sample* __restric
   if (FIRST && lane == 0 && nfeat) atomicAdd(&d.st->n_features, nfeat);
 }
 
-// zero one accumulator of every touched block (between EM rounds three and four)
+// zero one accumulator of every touched block (before EM rounds three and four, which reuse them)
 __global__ void k_bhm_zero_acc(BhmDev d, int which) {
   const int n = d.st->n_touched;
   for (int b = blockIdx.x; b < n; b += gridDim.x) {
